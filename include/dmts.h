@@ -1,0 +1,336 @@
+/*
+ * dmts.h -- C ABI of the GB300 (sm_103a) DMTS-NC library.
+ *
+ * The library runs one dual-level RESPA molecular-dynamics step (Algorithm 1
+ * of the paper, "DMTS-NC Integration Step"): an expensive conservative
+ * message-passing potential U, with forces F = -grad U (Sec. 2, "Multi-time-
+ * step integrator"), is evaluated once per outer step Delta; a cheap
+ * non-conservative direct-force model F_NC (Sec. 2, "Model architecture") is
+ * evaluated at each of the n inner steps delta = Delta/n. The inner steps are
+ * BAOAB steps (Sec. 2, B-A-O-A-B splitting) whose O-part is a Langevin
+ * thermostat with species-dependent friction (Sec. 2, "High Hydrogen
+ * Friction"); masses follow hydrogen mass repartitioning (Sec. 2, "HMR").
+ *
+ * Conventions shared by every call
+ *  - Units: Angstrom, femtosecond, amu, kcal/mol, kelvin.
+ *  - Pointers documented as "device" are CUDA device pointers on the
+ *    context's device, owned by the caller; "host" pointers are ordinary host
+ *    memory, also owned by the caller. The library owns only its internal
+ *    workspace (weights, neighbour-list scratch, activations), released by
+ *    dmts_destroy / dmts_state_release.
+ *  - Arrays are contiguous, row-major: positions/velocities/forces are float
+ *    [n_atoms][3]; species are uint8 codes 0..n_species-1 (H must be 0).
+ *  - Several replicas (independent systems) may be batched in one call: atoms
+ *    of replica r occupy [rep_off[r], rep_off[r+1]). Replicas never interact.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream). Calls only
+ *    enqueue work, except where noted ("synchronous").
+ *  - Errors: every call returns a dmts_status; dmts_last_error() gives text.
+ *    Argument errors are reported before any work is enqueued and leave all
+ *    outputs untouched. Device-detected errors (neighbour-list overflow,
+ *    non-finite positions) are recorded in a sticky device word; from then on
+ *    kernels of this context skip their updates, and dmts_sync() returns the
+ *    error. Outputs of the failed call are then unspecified.
+ */
+#ifndef DMTS_H
+#define DMTS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DMTS_MAX_SPECIES 8
+#define DMTS_MAX_LAYERS 4
+
+typedef enum {
+    DMTS_OK = 0,
+    DMTS_E_INVALID = 1,       /* bad argument or unsupported model size */
+    DMTS_E_OOM = 2,           /* device allocation failed */
+    DMTS_E_CUDA = 3,          /* a CUDA call failed */
+    DMTS_E_NBR_OVERFLOW = 4,  /* neighbour list larger than its capacity */
+    DMTS_E_NONFINITE = 5,     /* NaN/Inf found in positions or velocities */
+    DMTS_E_TIMEOUT = 6,       /* reserved: no call of this version waits on the device */
+    DMTS_E_BUSY = 7           /* state already in use by an unfinished call */
+} dmts_status;
+
+typedef enum { DMTS_FP32 = 0, DMTS_BF16 = 1 } dmts_precision;
+
+/*
+ * Message-passing model (both the conservative model and the embedding of
+ * the NC model are built from the same layer; Sec. 2 "Model architecture").
+ *
+ * Layer t, for every receiver i and neighbour j within rc (r = |x_j - x_i|,
+ * minimum image, n = (x_j - x_i)/r):
+ *   B_k(r)   = sqrt(2/rc) sin(k pi r/rc)/r, k = 1..K   (Bessel basis)
+ *   f(u)     = 1 - (p+1)(p+2)/2 u^p + p(p+2) u^(p+1) - p(p+1)/2 u^(p+2), u = r/rc
+ *   R_lc(r)  = f(r/rc) sum_k wrad[l][k][c] B_k(r)
+ *   A_i[lm][c] = nu sum_j R_lc(r_ij) s_j[c] Y_lm(n_ij)   (real SH, component
+ *                normalisation, l <= lmax, order [00 | x y z | xy yz (3z^2-1) xz (x^2-y^2)])
+ *   q_i[l*C+c] = sum_m A_i[lm][c]^2
+ *   s_i <- s_i + W2 silu(W1 q_i + b1) + b2
+ * with s_i^0 = emb[species_i].
+ *
+ * Conservative model: U_MP = scale * sum_i sum_o wo[o] silu((Wr s_i^L + br)[o]).
+ *   Weight blob (float64, host): emb[S][C]; for each layer: wrad[lmax+1][K][C],
+ *   W1[C][(lmax+1)C], b1[C], W2[C][C], b2[C]; then Wr[C][C], br[C], wo[C].
+ *
+ * NC model (one layer, lmax = 1): x_i = s_i^1, V_ih = sum_c U[h][c] A_i[l=1][c]
+ * (a 3-vector per tensor head h < n_l), q_ih = Wq[h] x_i, k_ih = Wk[h] x_i
+ * (h < H = K + n_l, each in R^n_c), c_ijh = q_ih . k_jh / sqrt(n_c),
+ *   F_ij = (sum_{h<K} c_ijh B_{h+1}(r)) (n_ij + sum_{h<n_l} c_ij(K+h) V_ih) f(r/rc),
+ *   F_i  = scale * sum_{j in N(i)} (F_ij - F_ji)  (+ bonded prior force),
+ * then the replica's FP64 mean force is subtracted from every atom.
+ *   Weight blob (float64, host): emb[S][C]; wrad[2][K][C], W1[C][2C], b1[C],
+ *   W2[C][C], b2[C]; U[n_l][C]; Wq[H][n_c][C]; Wk[H][n_c][C].
+ *
+ * Supported sizes: conservative C in {32, 64, 128}, lmax in {0, 1, 2}, K = 8,
+ * L <= DMTS_MAX_LAYERS; NC C in {32, 64}, K = 8, n_c = 8, n_l <= 4.
+ */
+typedef struct {
+    int L, C, lmax, K, n_species;
+    int n_c, n_l;              /* NC head only (0 for the conservative model) */
+    float rc;                  /* cutoff (A) */
+    float p_env;               /* envelope exponent p (integer valued, 2..12) */
+    float nu;                  /* message normalisation */
+    float scale;               /* energy scale (conservative) / force scale (NC) */
+    int precision;             /* dmts_precision of the MLP contractions */
+    const double *weights;     /* host blob, layout above */
+    long long n_weights;       /* number of doubles in the blob (checked) */
+} dmts_model;
+
+/*
+ * Analytic terms of U besides the message-passing energy U_MP:
+ *  - harmonic bonds 1/2 k_bond (r - r0)^2;
+ *  - Lennard-Jones 4 eps ((sig/r)^12 - (sig/r)^6) f(r/lj_rc; lj_p) between
+ *    heavy atoms (species != 0) of different molecules;
+ *  - the screened nuclear repulsion E_rep of Sec. 2 between every pair that
+ *    is not bonded: E_rep = k_e Z_i Z_j / r phi(r/a_ij) f(r/rep_rc; rep_p), with
+ *    Z = (1, 6, 7, 8, 16) for species codes (H, C, N, O, S), k_e = 332.0637133
+ *    kcal/mol A, and the universal screening function of Ziegler, Biersack and
+ *    Littmark standing in for the NHL pair parameters the paper cites but does
+ *    not give: phi(x) = sum_k c_k exp(-d_k x), c = (0.18175, 0.50986, 0.28022,
+ *    0.02817), d = (3.19980, 0.94229, 0.40290, 0.20162),
+ *    a_ij = 0.8854 a_0 / (Z_i^0.23 + Z_j^0.23), a_0 = 0.529177210903 A.
+ * U = U_MP + bonds + LJ + E_rep. The fast force F_S = F_NC + bonds + F_rep
+ * (Sec. 2: F_i = sum_j (F_ij - F_ji) + F_rep,i). rep_rc must not exceed the
+ * NC cutoff.
+ */
+typedef struct {
+    float k_bond, lj_eps, lj_sigma, lj_rc, lj_p;
+    float rep_rc, rep_p;
+} dmts_prior;
+
+/*
+ * A batch of n_replicas independent systems (device arrays unless noted).
+ * bond_ptr/bond_idx/bond_r0 are a per-atom bond table (CSR, both directions:
+ * each bond (a, b) appears in a's and in b's row); dmts_bond_table() builds it
+ * on the host from a bond list.
+ */
+typedef struct {
+    int n_atoms, n_replicas;
+    const int *rep_off;        /* device int32 [n_replicas+1], rep_off[0] = 0 */
+    const float *box;          /* device float [n_replicas][3]; 0 on all axes = open boundary */
+    float *x;                  /* device float [n_atoms][3] (updated by respa_step) */
+    const uint8_t *species;    /* device uint8 [n_atoms] */
+    const int *mol_id;         /* device int32 [n_atoms] */
+    const int *bond_ptr;       /* device int32 [n_atoms+1] */
+    const int *bond_idx;       /* device int32 [bond_ptr[n_atoms]] */
+    const float *bond_r0;      /* device float [bond_ptr[n_atoms]] */
+} dmts_system;
+
+/* Full (both-direction) neighbour list in CSR form: row i holds every j != i
+ * of i's replica with |d_ij|^2 < r_list^2 (minimum image), in a deterministic
+ * order (row order is otherwise unspecified). */
+typedef struct {
+    int *row_ptr;              /* device int32 [n_atoms+1] */
+    int *col;                  /* device int32 [capacity] */
+    long long capacity;
+    float r_list;              /* cutoff of the stored list, model cutoff + skin */
+} dmts_nbr;
+
+typedef struct dmts_ctx dmts_ctx;
+
+/* Creates a context on `device` and uploads both models (weights copied;
+ * the host blobs may be freed afterwards). Either model pointer may be NULL
+ * if the corresponding calls are not used. Synchronous. */
+dmts_status dmts_create(dmts_ctx **out, const dmts_model *cons, const dmts_model *nc,
+                        const dmts_prior *prior, int device);
+void dmts_destroy(dmts_ctx *ctx);
+const char *dmts_last_error(const dmts_ctx *ctx);
+
+/* Waits for `stream`, then returns and clears the sticky device error word
+ * (DMTS_OK when none). Synchronous. */
+dmts_status dmts_sync(dmts_ctx *ctx, void *stream);
+
+/*
+ * Cell-list neighbour build (Sec. 2: N(i) = atoms j != i within the cutoff;
+ * minimum image for periodic axes). Writes nbr->row_ptr and nbr->col for
+ * the list cutoff nbr->r_list. Synchronous: *n_pairs receives the number of
+ * stored pairs; if it exceeds nbr->capacity, col is left unspecified and
+ * DMTS_E_NBR_OVERFLOW is returned (retry with capacity >= *n_pairs).
+ * Periodic boxes need r_list < box/2 on every periodic axis.
+ */
+dmts_status nbr_build(dmts_ctx *ctx, const dmts_system *sys, dmts_nbr *nbr,
+                      long long *n_pairs, void *stream);
+
+#define DMTS_WITH_PRIOR 1      /* energy_forces_cons: add bonds + LJ + E_rep */
+#define DMTS_WITH_BONDS 1      /* forces_nc: add the bond forces and F_rep */
+
+/*
+ * Conservative energy and forces F = -grad U (Sec. 2, F = -grad U; Algorithm
+ * 1, FENNIX_large). energy: device double [n_replicas] (FP64 per-replica sum,
+ * may be NULL); forces: device float [n_atoms][3] (may be NULL for energy
+ * only). nbr must hold a list with r_list >= model rc (and >= lj_rc with
+ * DMTS_WITH_PRIOR), built for the current positions. The forces are the
+ * hand-written adjoint of the energy with per-layer recomputation of all
+ * edge quantities; only node features are stored.
+ */
+dmts_status energy_forces_cons(dmts_ctx *ctx, const dmts_system *sys, const dmts_nbr *nbr,
+                               double *energy, float *forces, int flags, void *stream);
+
+/*
+ * Non-conservative direct forces (Sec. 2 "Model architecture"; Algorithm 1,
+ * FENNIX_NC). forces: device float [n_atoms][3]; net_force: device double
+ * [n_replicas][3], the per-replica sum before the mean subtraction (may be
+ * NULL). nbr: list with r_list >= NC rc.
+ */
+dmts_status forces_nc(dmts_ctx *ctx, const dmts_system *sys, const dmts_nbr *nbr,
+                      float *forces, double *net_force, int flags, void *stream);
+
+typedef enum { DMTS_MODE_RESPA = 0, DMTS_MODE_STS = 1 } dmts_mode;
+
+/*
+ * Integrator parameters. RESPA: outer step Delta = dt_outer, n_inner inner
+ * BAOAB steps of delta = Delta/n_inner driven by F_S = F_NC (+ bonds), outer
+ * kicks by F_L = F - F_S (Algorithm 1). STS: BAOAB with F = -grad U and step
+ * dt_outer (n_inner ignored). gamma_ps: Langevin friction per species (1/ps);
+ * the O-step is v <- c1 v + c2 sqrt(1/m) G with c1 = exp(-gamma delta),
+ * c2 = sqrt((1 - c1^2) kB T), kB T in amu A^2/fs^2.
+ */
+typedef struct {
+    float dt_outer;
+    int n_inner;
+    float temperature;
+    double gamma_ps[DMTS_MAX_SPECIES];
+    int mode;                  /* dmts_mode */
+    float skin;                /* neighbour-list skin (A); lists rebuilt when an atom moved > skin/2 */
+} dmts_integrator;
+
+/*
+ * Dynamic state of a batch of replicas (device arrays unless noted). The
+ * noise of atom i (index within its replica) at inner step s of replica r is
+ * Philox4x32-10 with key (seed_lo, seed_hi) and counter
+ * (i, replica_id[r], s_lo, s_hi); s counts inner steps (RESPA) or steps (STS).
+ */
+typedef struct {
+    dmts_system sys;
+    float *v;                  /* device float [n_atoms][3] (A/fs) */
+    float *f_nc;               /* device float [n_atoms][3] cached fast force */
+    float *f_cons;             /* device float [n_atoms][3] cached full force */
+    const float *masses;       /* device float [n_atoms] simulation masses (amu) */
+    double *energy;            /* device double [n_replicas] last potential energy (may be NULL) */
+    uint64_t *step;            /* device uint64 [n_replicas] inner-step counters */
+    const uint64_t *seed;      /* device uint64 [n_replicas] */
+    const uint32_t *replica_id;/* device uint32 [n_replicas] */
+    int first_step;            /* host flag: 1 = forces not yet evaluated */
+    void *internal;            /* library-owned; NULL before the first call */
+} dmts_state;
+
+/*
+ * Advances every replica of `st` by n_outer outer steps of Algorithm 1
+ * (RESPA mode) or n_outer single time steps (STS mode). Forces are cached
+ * across calls (first_step). Neighbour lists live in st->internal and are
+ * rebuilt on the device when needed. Asynchronous: errors detected on the
+ * device surface in dmts_sync().
+ */
+dmts_status respa_step(dmts_ctx *ctx, dmts_state *st, const dmts_integrator *p, int n_outer,
+                       void *stream);
+
+/* Frees st->internal. */
+void dmts_state_release(dmts_ctx *ctx, dmts_state *st);
+
+/* ------------------------------------------------------------------ serving */
+
+typedef struct {
+    int n_atoms;
+    const float *x;            /* host [n_atoms][3] */
+    const float *v;            /* host [n_atoms][3] */
+    const uint8_t *species;    /* host [n_atoms] */
+    const int *mol_id;         /* host [n_atoms] */
+    int n_bonds;
+    const int *bonds;          /* host [n_bonds][2] */
+    const float *bond_r0;      /* host [n_bonds] */
+    const float *masses;       /* host [n_atoms] simulation masses */
+    float box[3];              /* 0 = open boundary */
+    int n_outer;               /* outer steps to run */
+    uint64_t seed;
+    uint32_t replica_id;
+    double arrival_s;          /* arrival time relative to the start of the run */
+} dmts_request;
+
+typedef struct {
+    long long hbm_budget_bytes;   /* admission limit on the device footprint */
+    int max_slots;                /* at most this many replicas resident */
+    int realtime;                 /* 1: admit a request only after its arrival time */
+} dmts_serve_cfg;
+
+typedef struct {
+    float *x, *v;              /* host [n_atoms][3], filled on completion */
+    double energy;             /* last potential energy */
+    double t_arrival_s, t_admit_s, t_done_s;
+    int status;                /* dmts_status of this request */
+} dmts_result;
+
+typedef struct {
+    double *tick_ms;           /* host array of capacity tick_cap (may be NULL) */
+    int tick_cap;
+    int n_ticks;               /* out */
+    double wall_s;             /* out: duration of the whole run */
+    double atom_outer_steps;   /* out: sum over ticks of resident atoms */
+    int max_resident;          /* out */
+} dmts_serve_stats;
+
+/*
+ * Continuous-batching serving loop: requests are admitted in arrival order
+ * while the slot count and the HBM budget allow; every tick runs one batched
+ * outer step (one launch sequence over all resident replicas); finished
+ * replicas are copied back and retired, freeing room for waiting ones.
+ * Synchronous.
+ */
+dmts_status run_replicas(dmts_ctx *ctx, const dmts_request *reqs, int n_req,
+                         const dmts_integrator *p, const dmts_serve_cfg *cfg,
+                         dmts_result *out, dmts_serve_stats *stats);
+
+/* --------------------------------------------------------- host helpers */
+
+/* Hydrogen mass repartitioning (Sec. 2 "HMR"): every H (species 0) gains
+ * delta_h; each molecule's total gain is removed from its heavy atoms in
+ * proportion to their masses, so molecular masses are preserved. Host, FP64. */
+void dmts_masses_hmr(int n_atoms, const uint8_t *species, const int *mol_id,
+                     const double *masses_in, double delta_h, double *masses_out);
+
+/* Per-atom bond table (CSR, both directions) from a bond list. bond_ptr has
+ * n_atoms+1 entries, bond_idx and bond_r0_out 2*n_bonds. Host. */
+dmts_status dmts_bond_table(int n_atoms, int n_bonds, const int *bonds, const float *bond_r0,
+                            int *bond_ptr, int *bond_idx, float *bond_r0_out);
+
+/* Philox4x32-10 noise words for testing: out[4*i..4*i+3] = Philox(key =
+ * (seed_lo, seed_hi), counter = (atom0 + i, replica, step_lo, step_hi)), i <
+ * count. out: device uint32 [4*count]. */
+dmts_status dmts_philox_words(dmts_ctx *ctx, uint64_t seed, uint32_t replica, uint64_t step,
+                              uint32_t atom0, int count, uint32_t *out, void *stream);
+
+/* The three Gaussians the O-step draws for the same counters. out: device
+ * float [3*count]. */
+dmts_status dmts_gaussians(dmts_ctx *ctx, uint64_t seed, uint32_t replica, uint64_t step,
+                           uint32_t atom0, int count, float *out, void *stream);
+
+/* Bytes of device workspace a replica of n_atoms needs in the serving loop
+ * (admission accounting). */
+long long dmts_replica_footprint(const dmts_ctx *ctx, int n_atoms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DMTS_H */

@@ -24,8 +24,10 @@ _lock = threading.Lock()
 _lib = None
 
 # prior constants: bond k (kcal/mol/A^2), LJ epsilon (kcal/mol), sigma (A),
-# LJ switch radius (A), switch exponent
-PRIOR = np.array([450.0, 0.15, 3.15, 5.0, 6.0])
+# LJ switch radius (A), LJ switch exponent, repulsion switch radius (A),
+# repulsion switch exponent
+PRIOR = np.array([450.0, 0.15, 3.15, 5.0, 6.0, 3.5, 6.0])
+BONDS, LJ, REP = 1, 2, 4
 
 
 def build(force: bool = False) -> str:
@@ -66,7 +68,11 @@ def _declare(L):
     L.orc_prior.restype = ct.c_double
     L.orc_prior.argtypes = [ct.c_int, _D, _U8, _I, _D, ct.c_int, _I, _D, _D, ct.c_int, _D]
     L.orc_nc_forces.restype = None
-    L.orc_nc_forces.argtypes = [ct.c_int, _D, _U8, _D, _I, _D, _D, ct.c_int, _I, _D, _D, _D, _D]
+    L.orc_nc_forces.argtypes = [ct.c_int, _D, _U8, _D, _I, _D, _D, ct.c_int, _I, _D, _D, ct.c_int, _D, _D]
+    L.orc_zbl_phi.restype = ct.c_double
+    L.orc_zbl_phi.argtypes = [ct.c_double]
+    L.orc_rep_pair.restype = ct.c_double
+    L.orc_rep_pair.argtypes = [ct.c_int, ct.c_int, ct.c_double, ct.c_double, ct.c_double, _D]
     L.orc_philox4x32_10.restype = None
     L.orc_philox4x32_10.argtypes = [_U32, _U32, _U32]
     L.orc_noise_words.restype = None
@@ -177,7 +183,11 @@ def cons_features(sys, spec, blob):
     return out
 
 
-def prior(sys, with_lj=True, consts=PRIOR):
+def prior(sys, with_lj=True, consts=PRIOR, terms=None):
+    """Analytic terms of U: bonds | LJ | screened repulsion (default all
+    three; with_lj=False keeps bonds + repulsion)."""
+    if terms is None:
+        terms = BONDS | REP | (LJ if with_lj else 0)
     L = lib()
     x, px = _d(sys.x)
     sp, ps = _u8(sys.species)
@@ -187,13 +197,17 @@ def prior(sys, with_lj=True, consts=PRIOR):
     r0, pr0 = _d(sys.bond_r0)
     c, pc = _d(consts)
     F = np.zeros((x.shape[0], 3))
-    E = L.orc_prior(x.shape[0], px, ps, pm, pb, b.shape[0], pbd, pr0, pc, int(with_lj),
+    E = L.orc_prior(x.shape[0], px, ps, pm, pb, b.shape[0], pbd, pr0, pc, int(terms),
                     F.ctypes.data_as(_D))
     return E, F
 
 
-def nc_forces(sys, spec, blob, with_bonds=True, consts=PRIOR):
-    """Returns (F after mean subtraction, net force before subtraction)."""
+def nc_forces(sys, spec, blob, with_bonds=True, consts=PRIOR, fast_terms=None):
+    """Returns (F after mean subtraction, net force before subtraction).
+    fast_terms: prior terms added to the NC force (default bonds + repulsion,
+    none when with_bonds is False)."""
+    if fast_terms is None:
+        fast_terms = (BONDS | REP) if with_bonds else 0
     L = lib()
     x, px = _d(sys.x)
     sp, ps = _u8(sys.species)
@@ -206,8 +220,8 @@ def nc_forces(sys, spec, blob, with_bonds=True, consts=PRIOR):
     c, pc = _d(consts)
     F = np.zeros((x.shape[0], 3))
     net = np.zeros(3)
-    L.orc_nc_forces(x.shape[0], px, ps, pb, pmi, pmr, pw, b.shape[0] if with_bonds else 0, pbd,
-                    pr0, pc, F.ctypes.data_as(_D), net.ctypes.data_as(_D))
+    L.orc_nc_forces(x.shape[0], px, ps, pb, pmi, pmr, pw, b.shape[0], pbd,
+                    pr0, pc, int(fast_terms), F.ctypes.data_as(_D), net.ctypes.data_as(_D))
     return F, net
 
 
@@ -265,6 +279,17 @@ def envelope(u, p):
 
 def denvelope(u, p):
     return lib().orc_denvelope(u, float(p))
+
+
+def zbl_phi(x):
+    return lib().orc_zbl_phi(float(x))
+
+
+def rep_pair(si, sj, r, rc=PRIOR[5], p=PRIOR[6]):
+    """(E_rep, dE/dr) of one pair."""
+    d = ct.c_double(0.0)
+    e = lib().orc_rep_pair(int(si), int(sj), float(r), float(rc), float(p), ct.byref(d))
+    return e, d.value
 
 
 def sph(n):

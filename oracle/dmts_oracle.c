@@ -22,8 +22,10 @@
  *                     dot products c_ijh, Bessel radial basis, polynomial
  *                     cutoff, pair forces F_ij, antisymmetric sum F_i, plus the
  *                     mean-force subtraction (Sec. 2 "Model architecture").
- *   orc_prior         bonded + Lennard-Jones prior that replaces the screened
- *                     nuclear repulsion (its parameters are not in the paper).
+ *   orc_prior         analytic terms: harmonic bonds, Lennard-Jones between heavy
+ *                     atoms of different molecules, and the screened nuclear
+ *                     repulsion E_rep of Sec. 2 (ZBL universal screening standing
+ *                     in for the NHL pair parameters, which are not given).
  *   orc_philox4x32_10 / orc_gauss3   counter-based noise (Salmon et al., SC'11).
  *   orc_hmr_masses    hydrogen mass repartitioning (Sec. 2 "HMR").
  *   orc_gamma_table   per-species Langevin O-step constants (Sec. 2 "HHF";
@@ -200,6 +202,42 @@ static double dsilu(double v)
 {
     double sg = 1.0 / (1.0 + exp(-v));
     return sg * (1.0 + v * (1.0 - sg));
+}
+
+/* Screened nuclear repulsion standing in for the NHL term of Sec. 2 (whose
+ * pair parameters are not given): E_rep = k_e Z_i Z_j / r * phi(r/a) with
+ * the universal screening function of Ziegler, Biersack and Littmark (1985),
+ * phi(x) = sum_k c_k exp(-d_k x), a = 0.8854 a_0 / (Z_i^0.23 + Z_j^0.23),
+ * switched off by the envelope f(r/rc; p). Returns E and dE/dr. */
+static const double ORC_ZBL_C[4] = {0.18175, 0.50986, 0.28022, 0.02817};
+static const double ORC_ZBL_D[4] = {3.19980, 0.94229, 0.40290, 0.20162};
+static const double ORC_Z[5] = {1.0, 6.0, 7.0, 8.0, 16.0};     /* H C N O S */
+#define ORC_KE 332.0637133       /* e^2/(4 pi eps0) in kcal/mol * A */
+#define ORC_A0 0.529177210903    /* Bohr radius, A */
+
+double orc_zbl_phi(double x)
+{
+    double s = 0.0;
+    for (int k = 0; k < 4; ++k) s += ORC_ZBL_C[k] * exp(-ORC_ZBL_D[k] * x);
+    return s;
+}
+
+double orc_rep_pair(int si, int sj, double r, double rc, double p, double *dEdr)
+{
+    double zi = ORC_Z[si], zj = ORC_Z[sj];
+    double a = 0.8854 * ORC_A0 / (pow(zi, 0.23) + pow(zj, 0.23));
+    double x = r / a, phi = 0.0, dphi = 0.0;
+    for (int k = 0; k < 4; ++k) {
+        double t = ORC_ZBL_C[k] * exp(-ORC_ZBL_D[k] * x);
+        phi += t;
+        dphi -= ORC_ZBL_D[k] * t;
+    }
+    double u = r / rc, fc = orc_envelope(u, p), dfc = orc_denvelope(u, p) / rc;
+    double c = ORC_KE * zi * zj;
+    double e0 = c / r * phi;
+    double de0 = -c / (r * r) * phi + c / r * dphi / a;
+    if (dEdr) *dEdr = de0 * fc + e0 * dfc;
+    return e0 * fc;
 }
 
 static int l_of(int lm) { return lm == 0 ? 0 : (lm < 4 ? 1 : 2); }
@@ -490,15 +528,40 @@ void orc_cons_features(int n, const double *x, const uint8_t *species, const dou
 /* molecules, switched off smoothly at 5 A by the p=6 envelope.              */
 /* ------------------------------------------------------------------------ */
 
-/* reals: [k_bond, lj_eps, lj_sigma, lj_rc, lj_p] */
+/* Per-atom bond partners (CSR) for the bonded-pair exclusion. */
+static void bond_adjacency(int n, int n_bonds, const int *bonds, int **ptr_out, int **idx_out)
+{
+    int *ptr = calloc(n + 1, sizeof(int));
+    int *idx = malloc(sizeof(int) * (2 * n_bonds + 1));
+    for (int b = 0; b < n_bonds; ++b) {
+        ptr[bonds[2 * b] + 1]++;
+        ptr[bonds[2 * b + 1] + 1]++;
+    }
+    for (int i = 0; i < n; ++i) ptr[i + 1] += ptr[i];
+    int *fill = malloc(sizeof(int) * (n + 1));
+    memcpy(fill, ptr, sizeof(int) * (n + 1));
+    for (int b = 0; b < n_bonds; ++b) {
+        idx[fill[bonds[2 * b]]++] = bonds[2 * b + 1];
+        idx[fill[bonds[2 * b + 1]]++] = bonds[2 * b];
+    }
+    free(fill);
+    *ptr_out = ptr;
+    *idx_out = idx;
+}
+
+/* reals: [k_bond, lj_eps, lj_sigma, lj_rc, lj_p, rep_rc, rep_p].
+ * terms: bit 0 bonds, bit 1 LJ, bit 2 screened repulsion (all pairs i < j
+ * closer than rep_rc that are not bonded). */
 double orc_prior(int n, const double *x, const uint8_t *species, const int *mol_id,
                  const double *box, int n_bonds, const int *bonds, const double *bond_r0,
-                 const double *pr, int with_lj, double *F)
+                 const double *pr, int terms, double *F)
 {
     double kb = pr[0], eps = pr[1], sig = pr[2], rlj = pr[3], plj = pr[4];
+    double rrep = pr[5], prep = pr[6];
+    int with_lj = (terms & 2) != 0;
     double E = 0.0;
     if (F) for (int i = 0; i < 3 * n; ++i) F[i] = 0.0;
-    for (int b = 0; b < n_bonds; ++b) {
+    for (int b = 0; (terms & 1) && b < n_bonds; ++b) {
         int i = bonds[2 * b], j = bonds[2 * b + 1];
         double d[3];
         min_image(&x[3 * i], &x[3 * j], box, d);
@@ -538,6 +601,31 @@ double orc_prior(int n, const double *x, const uint8_t *species, const int *mol_
                 }
             }
     }
+    if (terms & 4) {
+        int *bp, *bi;
+        bond_adjacency(n, n_bonds, bonds, &bp, &bi);
+        for (int i = 0; i < n; ++i)
+            for (int j = i + 1; j < n; ++j) {
+                double d[3];
+                min_image(&x[3 * i], &x[3 * j], box, d);
+                double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                if (!(r2 < rrep * rrep)) continue;
+                int is_bonded = 0;
+                for (int q = bp[i]; q < bp[i + 1]; ++q) is_bonded |= bi[q] == j;
+                if (is_bonded) continue;
+                double r = sqrt(r2), dEdr;
+                E += orc_rep_pair(species[i], species[j], r, rrep, prep, &dEdr);
+                if (F) {
+                    double g = dEdr / r;
+                    for (int a = 0; a < 3; ++a) {
+                        F[3 * i + a] += g * d[a];
+                        F[3 * j + a] -= g * d[a];
+                    }
+                }
+            }
+        free(bp);
+        free(bi);
+    }
     return E;
 }
 
@@ -551,13 +639,14 @@ double orc_prior(int n, const double *x, const uint8_t *species, const int *mol_
  * q_ih = Wq_h x_i, k_ih = Wk_h x_i in R^{n_c}.
  * c_ijh = (1/sqrt(n_c)) sum_k q_ihk k_jhk.
  * F_ij = (sum_{h<n_s} c_ijh B_h(r)) (R_ij/r + sum_{h<n_l} c_ij(n_s+h) V_ih) f_c(r).
- * F_i = scale * sum_{j in N(i)} (F_ij - F_ji); the bonded prior force is
- * added; then the FP64 mean (sum_i F_i / N) is subtracted.
+ * F_i = scale * sum_{j in N(i)} (F_ij - F_ji); the fast prior terms selected
+ * by fast_terms (bit 0 bonds, bit 2 screened repulsion F_rep) are added; then
+ * the FP64 mean (sum_i F_i / N) is subtracted.
  * net_pre (optional, 3 doubles) receives sum_i F_i before subtraction. */
 void orc_nc_forces(int n, const double *x, const uint8_t *species, const double *box,
                    const int *mi, const double *mr, const double *blob,
                    int n_bonds, const int *bonds, const double *bond_r0, const double *pr,
-                   double *F, double *net_pre)
+                   int fast_terms, double *F, double *net_pre)
 {
     model_t m;
     parse_nc(&m, mi, mr, blob);
@@ -628,9 +717,9 @@ void orc_nc_forces(int n, const double *x, const uint8_t *species, const double 
         }
         for (int a = 0; a < 3; ++a) F[3 * i + a] += m.scale * (Fij[a] - Fji[a]);
     }
-    if (n_bonds > 0) {
+    if (fast_terms) {
         double *Fb = malloc(sizeof(double) * 3 * n);
-        orc_prior(n, x, species, NULL, box, n_bonds, bonds, bond_r0, pr, 0, Fb);
+        orc_prior(n, x, species, NULL, box, n_bonds, bonds, bond_r0, pr, fast_terms, Fb);
         for (int i = 0; i < 3 * n; ++i) F[i] += Fb[i];
         free(Fb);
     }
@@ -751,8 +840,8 @@ typedef struct {
     double T;
     uint64_t seed;
     uint32_t replica;
-    int inner_mode;          /* 0: NC + bonds, 1: full -grad U, 2: bonds only */
-    int outer_mode;          /* 0: -grad(U_MP + prior), 1: bonds only */
+    int inner_mode;          /* 0: NC + bonds + F_rep, 1: full -grad U, 2: bonds only */
+    int outer_mode;          /* 0: -grad(U_MP + bonds + LJ + E_rep), 1: bonds only */
 } md_t;
 
 /* Slow force F_full = -grad U (U = U_MP + bonds + LJ) or a reduced U. */
@@ -763,11 +852,11 @@ static double full_force(const md_t *md, const double *x, double *F)
     if (md->outer_mode == 0) {
         E = orc_cons_energy_forces(md->n, x, md->species, md->box, md->cmi, md->cmr, md->cblob, F);
         E += orc_prior(md->n, x, md->species, md->mol_id, md->box, md->n_bonds, md->bonds,
-                       md->bond_r0, md->prior, 1, Fp);
+                       md->bond_r0, md->prior, 7, Fp);
     } else {
         for (int i = 0; i < 3 * md->n; ++i) F[i] = 0.0;
         E = orc_prior(md->n, x, md->species, md->mol_id, md->box, md->n_bonds, md->bonds,
-                      md->bond_r0, md->prior, 0, Fp);
+                      md->bond_r0, md->prior, 1, Fp);
     }
     for (int i = 0; i < 3 * md->n; ++i) F[i] += Fp[i];
     free(Fp);
@@ -779,12 +868,12 @@ static void inner_force(const md_t *md, const double *x, double *F)
 {
     if (md->inner_mode == 0) {
         orc_nc_forces(md->n, x, md->species, md->box, md->nmi, md->nmr, md->nblob, md->n_bonds,
-                      md->bonds, md->bond_r0, md->prior, F, NULL);
+                      md->bonds, md->bond_r0, md->prior, 5, F, NULL);
     } else if (md->inner_mode == 1) {
         full_force(md, x, F);
     } else {
         orc_prior(md->n, x, md->species, md->mol_id, md->box, md->n_bonds, md->bonds, md->bond_r0,
-                  md->prior, 0, F);
+                  md->prior, 1, F);
     }
 }
 

@@ -1,0 +1,269 @@
+"""Torch-facing binding of the C ABI (argument marshalling only).
+
+Every step of the DMTS-NC path runs in libdmts.so; PyTorch provides device
+memory and the current CUDA stream. Names follow the C ABI: nbr_build,
+energy_forces_cons, forces_nc, respa_step, run_replicas.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import math
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+def _ptr(t):
+    return ct.c_void_p(t.data_ptr()) if t is not None else ct.c_void_p(0)
+
+
+def _stream(device=None):
+    return ct.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _require_cuda(t: torch.Tensor, name: str):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def model_struct(spec, blob) -> tuple:
+    w = np.ascontiguousarray(blob, dtype=np.float64)
+    m = L.Model(spec.L, spec.C, spec.lmax, spec.K, spec.n_species, spec.n_c, spec.n_l,
+                float(spec.rc), float(spec.p), float(spec.nu), float(spec.scale),
+                L.BF16 if spec.bf16 else L.FP32, w.ctypes.data_as(ct.POINTER(ct.c_double)), w.size)
+    return m, w
+
+
+# bond k, LJ eps, LJ sigma, LJ switch radius, LJ switch exponent, repulsion
+# switch radius, repulsion switch exponent
+DEFAULT_PRIOR = (450.0, 0.15, 3.15, 5.0, 6.0, 3.5, 6.0)
+
+
+class Context:
+    """Owns a dmts_ctx: both models uploaded to `device`."""
+
+    def __init__(self, cons=None, nc=None, prior=DEFAULT_PRIOR, device: int = 0):
+        self.lib = L.lib()
+        self.device = device
+        h = ct.c_void_p()
+        keep = []
+        cm = nm = None
+        if cons is not None:
+            cm, w = model_struct(*cons)
+            keep.append(w)
+        if nc is not None:
+            nm, w = model_struct(*nc)
+            keep.append(w)
+        pr = L.Prior(*prior)
+        st = self.lib.dmts_create(ct.byref(h), ct.byref(cm) if cm else None, ct.byref(nm) if nm else None,
+                                  ct.byref(pr), device)
+        L.check(st, None)
+        self.handle = h
+        self.cons_spec = cons[0] if cons is not None else None
+        self.nc_spec = nc[0] if nc is not None else None
+        self.prior = prior
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.dmts_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sync(self):
+        L.check(self.lib.dmts_sync(self.handle, _stream()), self.handle)
+
+
+def bond_table(n_atoms, bonds, r0):
+    """Per-atom CSR bond table (both directions) built by the library's host helper."""
+    bonds = np.ascontiguousarray(np.asarray(bonds, np.int32).reshape(-1, 2))
+    r0 = np.ascontiguousarray(np.asarray(r0, np.float32))
+    nb = bonds.shape[0]
+    ptr = np.zeros(n_atoms + 1, np.int32)
+    idx = np.zeros(max(1, 2 * nb), np.int32)
+    rr = np.zeros(max(1, 2 * nb), np.float32)
+    st = L.lib().dmts_bond_table(n_atoms, nb, bonds.ctypes.data, r0.ctypes.data, ptr.ctypes.data,
+                                 idx.ctypes.data, rr.ctypes.data)
+    L.check(st)
+    return ptr, idx, rr
+
+
+def masses_hmr(species, mol_id, masses, delta_h):
+    """Hydrogen mass repartitioning by the library's host helper (FP64)."""
+    sp = np.ascontiguousarray(species, np.uint8)
+    mo = np.ascontiguousarray(mol_id, np.int32)
+    m = np.ascontiguousarray(masses, np.float64)
+    out = np.zeros_like(m)
+    L.lib().dmts_masses_hmr(m.shape[0], sp.ctypes.data, mo.ctypes.data, m.ctypes.data, float(delta_h),
+                            out.ctypes.data)
+    return out
+
+
+class DeviceSystem:
+    """A batch of replicas resident on the device (concatenated atoms)."""
+
+    def __init__(self, systems, device="cuda"):
+        if not isinstance(systems, (list, tuple)):
+            systems = [systems]
+        self.systems = list(systems)
+        counts = [s.n_atoms for s in systems]
+        self.n_atoms = int(sum(counts))
+        self.n_replicas = len(systems)
+        off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+        self.rep_off_host = off
+        x = np.concatenate([s.x for s in systems], 0).astype(np.float32)
+        sp = np.concatenate([s.species for s in systems]).astype(np.uint8)
+        mol = np.concatenate([s.mol_id for s in systems]).astype(np.int32)
+        bonds = np.concatenate([s.bonds.reshape(-1, 2) + off[k] for k, s in enumerate(systems)], 0)
+        r0 = np.concatenate([s.bond_r0 for s in systems])
+        ptr, idx, rr = bond_table(self.n_atoms, bonds, r0)
+        dev = torch.device(device)
+        self.x = torch.from_numpy(x).to(dev)
+        self.species = torch.from_numpy(sp).to(dev)
+        self.mol_id = torch.from_numpy(mol).to(dev)
+        self.rep_off = torch.from_numpy(off).to(dev)
+        self.box = torch.from_numpy(np.stack([s.box for s in systems]).astype(np.float32)).to(dev)
+        self.bond_ptr = torch.from_numpy(ptr).to(dev)
+        self.bond_idx = torch.from_numpy(idx).to(dev)
+        self.bond_r0 = torch.from_numpy(rr).to(dev)
+
+    def struct(self) -> L.System:
+        return L.System(self.n_atoms, self.n_replicas, _ptr(self.rep_off), _ptr(self.box), _ptr(self.x),
+                        _ptr(self.species), _ptr(self.mol_id), _ptr(self.bond_ptr), _ptr(self.bond_idx),
+                        _ptr(self.bond_r0))
+
+
+class NbrList:
+    def __init__(self, row_ptr, col, r_list):
+        self.row_ptr, self.col, self.r_list = row_ptr, col, float(r_list)
+
+    def struct(self):
+        return L.Nbr(_ptr(self.row_ptr), _ptr(self.col), self.col.numel(), self.r_list)
+
+
+def nbr_build(ctx: Context, dsys: DeviceSystem, r_list: float, capacity: int | None = None) -> NbrList:
+    """Cell-list neighbour build; grows the capacity and retries on overflow."""
+    dev = dsys.x.device
+    if capacity is None:
+        capacity = max(1024, 80 * dsys.n_atoms)
+    while True:
+        row = torch.empty(dsys.n_atoms + 1, dtype=torch.int32, device=dev)
+        col = torch.empty(max(1, capacity), dtype=torch.int32, device=dev)
+        nb = NbrList(row, col, r_list)
+        s = dsys.struct()
+        nbs = nb.struct()
+        npairs = ct.c_longlong(0)
+        st = ctx.lib.nbr_build(ctx.handle, ct.byref(s), ct.byref(nbs), ct.byref(npairs), _stream(dev))
+        if st == L.E_NBR_OVERFLOW:
+            capacity = int(npairs.value * 1.2) + 1024
+            continue
+        L.check(st, ctx.handle)
+        nb.col = col[: max(1, npairs.value)]
+        nb.n_pairs = int(npairs.value)
+        return nb
+
+
+def energy_forces_cons(ctx: Context, dsys: DeviceSystem, nbr: NbrList, with_prior=True, forces=True):
+    """Returns (energy f64 [n_replicas], forces f32 [N,3] or None)."""
+    dev = dsys.x.device
+    E = torch.empty(dsys.n_replicas, dtype=torch.float64, device=dev)
+    F = torch.empty(dsys.n_atoms, 3, dtype=torch.float32, device=dev) if forces else None
+    s, nbs = dsys.struct(), nbr.struct()
+    st = ctx.lib.energy_forces_cons(ctx.handle, ct.byref(s), ct.byref(nbs), _ptr(E), _ptr(F),
+                                    L.WITH_PRIOR if with_prior else 0, _stream(dev))
+    L.check(st, ctx.handle)
+    return E, F
+
+
+def forces_nc(ctx: Context, dsys: DeviceSystem, nbr: NbrList, with_bonds=True):
+    """Returns (F_NC f32 [N,3] mean-subtracted, net force f64 [R,3] before subtraction)."""
+    dev = dsys.x.device
+    F = torch.empty(dsys.n_atoms, 3, dtype=torch.float32, device=dev)
+    net = torch.empty(dsys.n_replicas, 3, dtype=torch.float64, device=dev)
+    s, nbs = dsys.struct(), nbr.struct()
+    st = ctx.lib.forces_nc(ctx.handle, ct.byref(s), ct.byref(nbs), _ptr(F), _ptr(net),
+                           L.WITH_BONDS if with_bonds else 0, _stream(dev))
+    L.check(st, ctx.handle)
+    return F, net
+
+
+def integrator(dt_outer, n_inner, temperature, gamma_ps, mode=L.MODE_RESPA, skin=0.5) -> L.Integrator:
+    g = (ct.c_double * L.MAX_SPECIES)(*([float(v) for v in gamma_ps] + [0.0] * (L.MAX_SPECIES - len(gamma_ps))))
+    return L.Integrator(float(dt_outer), int(n_inner), float(temperature), g, int(mode), float(skin))
+
+
+class MDState:
+    """Device-resident dynamic state of a batch (positions live in dsys.x)."""
+
+    def __init__(self, dsys: DeviceSystem, v, masses, seeds, replica_ids=None, steps=None):
+        dev = dsys.x.device
+        self.dsys = dsys
+        self.v = torch.as_tensor(np.asarray(v, np.float32)).to(dev).contiguous()
+        self.masses = torch.as_tensor(np.asarray(masses, np.float32)).to(dev).contiguous()
+        R = dsys.n_replicas
+        self.f_nc = torch.zeros(dsys.n_atoms, 3, dtype=torch.float32, device=dev)
+        self.f_cons = torch.zeros(dsys.n_atoms, 3, dtype=torch.float32, device=dev)
+        self.energy = torch.zeros(R, dtype=torch.float64, device=dev)
+        seeds = np.broadcast_to(np.asarray(seeds, np.uint64), (R,)).copy()
+        self.seed = torch.from_numpy(seeds.view(np.int64)).to(dev)
+        rid = np.arange(R, dtype=np.uint32) if replica_ids is None else np.asarray(replica_ids, np.uint32)
+        self.replica_id = torch.from_numpy(rid.view(np.int32)).to(dev)
+        st0 = np.zeros(R, np.uint64) if steps is None else np.asarray(steps, np.uint64)
+        self.step = torch.from_numpy(st0.view(np.int64)).to(dev)
+        self.c = L.State(dsys.struct(), _ptr(self.v), _ptr(self.f_nc), _ptr(self.f_cons), _ptr(self.masses),
+                         _ptr(self.energy), _ptr(self.step), _ptr(self.seed), _ptr(self.replica_id), 1, None)
+        self.ctx = None
+
+    def release(self):
+        if self.ctx is not None and self.c.internal:
+            self.ctx.lib.dmts_state_release(self.ctx.handle, ct.byref(self.c))
+
+
+def respa_step(ctx: Context, state: MDState, integ: L.Integrator, n_outer: int):
+    state.ctx = ctx
+    st = ctx.lib.respa_step(ctx.handle, ct.byref(state.c), ct.byref(integ), int(n_outer),
+                            _stream(state.v.device))
+    L.check(st, ctx.handle)
+
+
+def philox_words(ctx, seed, replica, step, atom0, count):
+    out = torch.empty(4 * count, dtype=torch.int32, device=f"cuda:{ctx.device}")
+    L.check(ctx.lib.dmts_philox_words(ctx.handle, seed, replica, step, atom0, count, _ptr(out), _stream()),
+            ctx.handle)
+    return out
+
+
+def gaussians(ctx, seed, replica, step, atom0, count):
+    out = torch.empty(3 * count, dtype=torch.float32, device=f"cuda:{ctx.device}")
+    L.check(ctx.lib.dmts_gaussians(ctx.handle, seed, replica, step, atom0, count, _ptr(out), _stream()),
+            ctx.handle)
+    return out
+
+
+class ConsEnergy(torch.autograd.Function):
+    """U(x) of the conservative model (+ prior) with the hand-written adjoint
+    as its backward: forward returns the per-replica energies, backward
+    returns -F * grad_output (F from the same call, per replica)."""
+
+    @staticmethod
+    def forward(fn_ctx, x, ctx: Context, dsys: DeviceSystem, nbr: NbrList, with_prior: bool = True):
+        if x.data_ptr() != dsys.x.data_ptr():
+            dsys.x.copy_(x.detach())
+        E, F = energy_forces_cons(ctx, dsys, nbr, with_prior=with_prior, forces=True)
+        fn_ctx.save_for_backward(F, dsys.rep_off)
+        return E
+
+    @staticmethod
+    def backward(fn_ctx, gE):
+        F, rep_off = fn_ctx.saved_tensors
+        counts = (rep_off[1:] - rep_off[:-1]).long()
+        g = torch.repeat_interleave(gE.to(F.dtype), counts)
+        return -F * g[:, None], None, None, None, None

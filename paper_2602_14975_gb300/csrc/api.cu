@@ -1,0 +1,877 @@
+// Host side of the C ABI: context, device models, workspace, force
+// evaluations, the Algorithm-1 driver (respa_step) and host helpers.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "engine.cuh"
+
+using namespace dmts;
+
+// ------------------------------------------------------------ utilities --
+namespace dmts {
+
+static thread_local std::string g_tls_error;
+
+bool ck(dmts_ctx *ctx, cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return true;
+    char buf[256];
+    snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+    if (ctx) ctx->last_error = buf;
+    g_tls_error = buf;
+    return false;
+}
+
+dmts_status fail(dmts_ctx *ctx, dmts_status s, const std::string &msg) {
+    if (ctx) ctx->last_error = msg;
+    g_tls_error = msg;
+    return s;
+}
+
+bool Buf::ensure(size_t bytes) {
+    if (bytes <= cap) return true;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    size_t want = std::max<size_t>(bytes, 256);
+    if (cudaMalloc(&p, want) != cudaSuccess) {
+        p = nullptr;
+        return false;
+    }
+    cap = want;
+    return true;
+}
+
+void Buf::release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+}
+
+static bool upload(DevModel &m, const std::vector<float> &h) {
+    if (cudaMalloc(&m.dev, h.size() * sizeof(float)) != cudaSuccess) return false;
+    return cudaMemcpy(m.dev, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess;
+}
+
+static dmts_status load_model(dmts_ctx *ctx, const dmts_model *in, bool is_nc, DevModel &m) {
+    m.L = is_nc ? 1 : in->L;
+    m.C = in->C;
+    m.lmax = is_nc ? 1 : in->lmax;
+    m.K = in->K;
+    m.S = in->n_species;
+    m.nc = in->n_c;
+    m.nl = in->n_l;
+    m.rc = in->rc;
+    m.p = (int)lrintf(in->p_env);
+    m.nu = in->nu;
+    m.scale = in->scale;
+    m.bf16 = in->precision == DMTS_BF16;
+    const int C = m.C, K = m.K, NL = m.lmax + 1, S = m.S;
+    if (K != 8) return fail(ctx, DMTS_E_INVALID, "only K = 8 Bessel functions are supported");
+    if (!(C == 32 || C == 64 || C == 128)) return fail(ctx, DMTS_E_INVALID, "C must be 32, 64 or 128");
+    if (m.lmax < 0 || m.lmax > 2) return fail(ctx, DMTS_E_INVALID, "lmax must be 0..2");
+    if (m.L < 1 || m.L > DMTS_MAX_LAYERS) return fail(ctx, DMTS_E_INVALID, "bad layer count");
+    if (S < 1 || S > DMTS_MAX_SPECIES) return fail(ctx, DMTS_E_INVALID, "bad species count");
+    if (m.p < 2 || m.p > 12 || std::fabs(in->p_env - (float)m.p) > 1e-6f)
+        return fail(ctx, DMTS_E_INVALID, "p_env must be an integer in 2..12");
+    if (!(m.rc > 0.f)) return fail(ctx, DMTS_E_INVALID, "rc must be positive");
+    if (is_nc && (C > 64 || m.nc != 8 || m.nl < 1 || m.nl > 4))
+        return fail(ctx, DMTS_E_INVALID, "NC model: C <= 64, n_c = 8, 1 <= n_l <= 4");
+    if (m.bf16) return fail(ctx, DMTS_E_INVALID, "bf16 MLP contractions are not built into this library");
+    long long expect;
+    if (!is_nc)
+        expect = (long long)S * C + (long long)m.L * (NL * K * C + NL * C * C + C + C * C + C) + C * C + 2 * C;
+    else {
+        const int H = K + m.nl;
+        expect = (long long)S * C + 2 * K * C + 2 * C * C + C + C * C + C + m.nl * C + 2LL * H * m.nc * C;
+    }
+    if (in->n_weights != expect || !in->weights)
+        return fail(ctx, DMTS_E_INVALID, "weight blob size does not match the model sizes");
+    std::vector<float> h(in->weights, in->weights + expect);
+    if (!upload(m, h)) return fail(ctx, DMTS_E_OOM, "weight upload failed");
+    // offsets (same order as the blob)
+    size_t o = 0;
+    auto take = [&](size_t n) { float *p = m.dev + o; o += n; return p; };
+    m.emb = take((size_t)S * C);
+    for (int t = 0; t < m.L; ++t) {
+        m.wrad[t] = take((size_t)NL * K * C);
+        m.w1[t] = take((size_t)C * NL * C);
+        m.b1[t] = take(C);
+        m.w2[t] = take((size_t)C * C);
+        m.b2[t] = take(C);
+    }
+    if (!is_nc) {
+        m.wr = take((size_t)C * C);
+        m.br = take(C);
+        m.wo = take(C);
+    } else {
+        const int H = K + m.nl;
+        m.U = take((size_t)m.nl * C);
+        m.Wqk = take((size_t)2 * H * m.nc * C);   // Wq rows then Wk rows: one [2 H n_c][C] matrix
+    }
+    return DMTS_OK;
+}
+
+// Species-pair table of the screened repulsion (host FP64 -> float).
+RepTable rep_table(const dmts_ctx *ctx) {
+    static const double Z[5] = {1.0, 6.0, 7.0, 8.0, 16.0};
+    RepTable t;
+    memset(&t, 0, sizeof t);
+    for (int i = 0; i < 5; ++i)
+        for (int j = 0; j < 5; ++j) {
+            t.zz[i][j] = (float)(332.0637133 * Z[i] * Z[j]);
+            t.inv_a[i][j] = (float)((std::pow(Z[i], 0.23) + std::pow(Z[j], 0.23)) / (0.8854 * 0.529177210903));
+        }
+    t.rc = ctx->prior.rep_rc;
+    t.inv_rc = t.rc > 0.f ? 1.f / t.rc : 0.f;
+    t.p = (int)lrintf(ctx->prior.rep_p);
+    t.on = t.rc > 0.f;
+    return t;
+}
+
+// -------------------------------------------------------- force pieces --
+EdgeGeom edge_geom(const SysView &s, const int *row_ptr, const int *col, const DevModel &m) {
+    EdgeGeom g;
+    g.x = s.x;
+    g.atom_rep = s.atom_rep;
+    g.box = s.box;
+    g.row_ptr = row_ptr;
+    g.col = col;
+    g.n_atoms = s.n;
+    g.rc = m.rc;
+    g.inv_rc = 1.f / m.rc;
+    g.bnorm = sqrtf(2.f / m.rc);
+    g.p = m.p;
+    return g;
+}
+
+static Epi epi(int mode) {
+    Epi e;
+    memset(&e, 0, sizeof e);
+    e.mode = mode;
+    return e;
+}
+
+// U_MP (+ prior) and F = -grad U for a batch.
+dmts_status cons_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const int *col, double *energy,
+                      float *forces, int flags, cudaStream_t st) {
+    const DevModel &m = ctx->cons;
+    const int N = s.n, C = m.C, L = m.L, NL = m.lmax + 1, NLM = NL * NL;
+    Workspace &w = ctx->ws;
+    const size_t nc_ = (size_t)N * C;
+    if (!w.s.ensure(sizeof(float) * nc_ * (L + 1)) || !w.A.ensure(sizeof(float) * nc_ * NLM * L) ||
+        !w.q.ensure(sizeof(float) * nc_ * NL) || !w.h.ensure(sizeof(float) * nc_ * L) ||
+        !w.act.ensure(sizeof(float) * nc_) || !w.u.ensure(sizeof(float) * nc_) || !w.gz.ensure(sizeof(float) * nc_) ||
+        !w.gs0.ensure(sizeof(float) * nc_) || !w.gs1.ensure(sizeof(float) * nc_) ||
+        !w.gA.ensure(sizeof(float) * nc_ * NLM) || !w.e_atom.ensure(sizeof(float) * (N + 1)) ||
+        !w.ftmp.ensure(sizeof(float) * 3 * (N + 1)))
+        return fail(ctx, DMTS_E_OOM, "workspace allocation failed");
+    float *S = (float *)w.s.p, *A = (float *)w.A.p, *q = (float *)w.q.p, *H = (float *)w.h.p;
+    float *act = (float *)w.act.p, *u = (float *)w.u.p, *gz = (float *)w.gz.p;
+    float *gs0 = (float *)w.gs0.p, *gs1 = (float *)w.gs1.p, *gA = (float *)w.gA.p;
+    float *e_atom = (float *)w.e_atom.p;
+    const EdgeGeom g = edge_geom(s, row_ptr, col, m);
+    launch_embed(N, C, s.species, m.emb, S, st);
+    for (int t = 0; t < L; ++t) {
+        LayerIO io;
+        memset(&io, 0, sizeof io);
+        io.s = S + nc_ * t;
+        io.wrad = m.wrad[t];
+        io.nu = m.nu;
+        io.A = A + nc_ * NLM * t;
+        io.q = q;
+        io.err = ctx->d_err;
+        launch_mp_fwd(C, m.lmax, m.K, g, io, st);
+        Epi e1 = epi(EPI_BIAS_SILU);
+        e1.bias = m.b1[t];
+        e1.H = H + nc_ * t;
+        e1.out = act;
+        launch_gemm_f32(N, C, NL * C, q, m.w1[t], 1, e1, st);
+        Epi e2 = epi(EPI_RESID);
+        e2.bias = m.b2[t];
+        e2.res = S + nc_ * t;
+        e2.out = S + nc_ * (t + 1);
+        launch_gemm_f32(N, C, C, act, m.w2[t], 1, e2, st);
+    }
+    Epi er = epi(EPI_READOUT);
+    er.bias = m.br;
+    er.wo = m.wo;
+    er.scale = m.scale;
+    er.out = u;
+    er.out2 = gz;
+    launch_gemm_f32(N, C, C, S + nc_ * L, m.wr, 1, er, st);
+    launch_rowsum(N, C, u, m.scale, e_atom, st);
+    if (forces) {
+        // dU/ds^L = gz Wr
+        Epi eg = epi(EPI_STORE);
+        eg.out = gs0;
+        launch_gemm_f32(N, C, C, gz, m.wr, 0, eg, st);
+        float *gin = gs0, *gout = gs1;
+        for (int t = L - 1; t >= 0; --t) {
+            Epi ed = epi(EPI_DSILU);
+            ed.H = H + nc_ * t;
+            ed.out = act;                       // g_h
+            launch_gemm_f32(N, C, C, gin, m.w2[t], 0, ed, st);
+            Epi ea = epi(EPI_GA);
+            ea.A = A + nc_ * NLM * t;
+            ea.out = gA;
+            ea.C = C;
+            ea.lmax = m.lmax;
+            launch_gemm_f32(N, NL * C, C, act, m.w1[t], 0, ea, st);
+            LayerIO io;
+            memset(&io, 0, sizeof io);
+            io.s = S + nc_ * t;
+            io.wrad = m.wrad[t];
+            io.nu = m.nu;
+            io.gA = gA;
+            io.gs_in = gin;
+            io.gs_out = gout;
+            io.F = forces;
+            io.accumulate = t != L - 1;
+            io.err = ctx->d_err;
+            launch_mp_bwd(C, m.lmax, m.K, g, io, st);
+            std::swap(gin, gout);
+        }
+    }
+    if (flags & DMTS_WITH_PRIOR) {
+        PriorArgs pa;
+        pa.x = s.x;
+        pa.atom_rep = s.atom_rep;
+        pa.box = s.box;
+        pa.row_ptr = row_ptr;
+        pa.col = col;
+        pa.species = s.species;
+        pa.mol_id = s.mol_id;
+        pa.n_atoms = N;
+        pa.lj_eps = ctx->prior.lj_eps;
+        pa.lj_sigma = ctx->prior.lj_sigma;
+        pa.lj_rc = ctx->prior.lj_rc;
+        pa.lj_p = (int)lrintf(ctx->prior.lj_p);
+        pa.bonds = {s.bond_ptr, s.bond_idx, s.bond_r0, ctx->prior.k_bond};
+        pa.rep = rep_table(ctx);
+        pa.F = forces ? forces : (float *)w.ftmp.p;
+        if (!forces) cudaMemsetAsync(w.ftmp.p, 0, sizeof(float) * 3 * N, st);
+        pa.e_atom = e_atom;
+        pa.err = ctx->d_err;
+        launch_prior(pa, st);
+    }
+    if (energy) launch_replica_sum(e_atom, s.rep_off, s.n_rep, energy, 0, st);
+    return DMTS_OK;
+}
+
+// F_NC (+ bonds), mean-subtracted; net = per-replica sum before subtraction.
+dmts_status nc_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const int *col, float *forces,
+                    double *net, int flags, cudaStream_t st) {
+    const DevModel &m = ctx->nc;
+    const int N = s.n, C = m.C, H = m.K + m.nl, QKW = 2 * H * m.nc;
+    Workspace &w = ctx->ws;
+    const size_t nc_ = (size_t)N * C;
+    if (!w.nc_s.ensure(sizeof(float) * nc_ * 2) || !w.nc_A.ensure(sizeof(float) * nc_ * 4) ||
+        !w.nc_q.ensure(sizeof(float) * nc_ * 2) || !w.nc_h.ensure(sizeof(float) * nc_) ||
+        !w.nc_act.ensure(sizeof(float) * nc_) || !w.nc_qk.ensure(sizeof(float) * (size_t)N * QKW) ||
+        !w.nc_v.ensure(sizeof(float) * (size_t)N * m.nl * 3) || !w.nc_f.ensure(sizeof(float) * 3 * (N + 1)))
+        return fail(ctx, DMTS_E_OOM, "workspace allocation failed");
+    float *s0 = (float *)w.nc_s.p, *s1 = s0 + nc_;
+    const EdgeGeom g = edge_geom(s, row_ptr, col, m);
+    launch_embed(N, C, s.species, m.emb, s0, st);
+    LayerIO io;
+    memset(&io, 0, sizeof io);
+    io.s = s0;
+    io.wrad = m.wrad[0];
+    io.nu = m.nu;
+    io.A = (float *)w.nc_A.p;
+    io.q = (float *)w.nc_q.p;
+    io.err = ctx->d_err;
+    launch_mp_fwd(C, 1, m.K, g, io, st);
+    Epi e1 = epi(EPI_BIAS_SILU);
+    e1.bias = m.b1[0];
+    e1.H = (float *)w.nc_h.p;
+    e1.out = (float *)w.nc_act.p;
+    launch_gemm_f32(N, C, 2 * C, io.q, m.w1[0], 1, e1, st);
+    Epi e2 = epi(EPI_RESID);
+    e2.bias = m.b2[0];
+    e2.res = s0;
+    e2.out = s1;
+    launch_gemm_f32(N, C, C, (float *)w.nc_act.p, m.w2[0], 1, e2, st);
+    Epi e3 = epi(EPI_STORE);
+    e3.out = (float *)w.nc_qk.p;
+    launch_gemm_f32(N, QKW, C, s1, m.Wqk, 1, e3, st);
+    launch_nc_vectors(N, C, m.nl, io.A, m.U, (float *)w.nc_v.p, ctx->d_err, st);
+    NCHeadArgs a;
+    a.x = s.x;
+    a.atom_rep = s.atom_rep;
+    a.box = s.box;
+    a.row_ptr = row_ptr;
+    a.col = col;
+    a.n_atoms = N;
+    a.rc = m.rc;
+    a.inv_rc = 1.f / m.rc;
+    a.bnorm = sqrtf(2.f / m.rc);
+    a.p = m.p;
+    a.QK = (float *)w.nc_qk.p;
+    a.V = (float *)w.nc_v.p;
+    a.scale = m.scale;
+    a.bonds = {nullptr, nullptr, nullptr, 0.f};
+    if (flags & DMTS_WITH_BONDS) a.bonds = {s.bond_ptr, s.bond_idx, s.bond_r0, ctx->prior.k_bond};
+    a.rep = rep_table(ctx);
+    a.species = s.species;
+    a.F = (float *)w.nc_f.p;
+    a.err = ctx->d_err;
+    launch_nc_head(m.K, m.nc, m.nl, a, st);
+    launch_mean_sub((float *)w.nc_f.p, forces, s.rep_off, s.n_rep, net, ctx->d_err, st);
+    return DMTS_OK;
+}
+
+__global__ void k_set_int(int *p, int v) { *p = v; }
+
+// Host-side grid set-up for every replica (box and offsets copied to host).
+dmts_status setup_grids(dmts_ctx *ctx, const std::vector<int> &rep_off, const std::vector<float> &box,
+                        float r_list, std::vector<CellGrid> &grids, int &n_cells) {
+    const int R = (int)rep_off.size() - 1;
+    grids.resize(R);
+    n_cells = 0;
+    for (int r = 0; r < R; ++r) {
+        CellGrid g;
+        memset(&g, 0, sizeof g);
+        const bool periodic = box[3 * r] > 0.f;
+        for (int a = 0; a < 3; ++a) {
+            const float L = box[3 * r + a];
+            if (periodic != (L > 0.f)) return fail(ctx, DMTS_E_INVALID, "box must be periodic on all axes or none");
+            if (periodic) {
+                if (!(r_list < 0.5f * L)) return fail(ctx, DMTS_E_INVALID, "list cutoff must be < box/2");
+                g.box[a] = L;
+                g.dim[a] = std::max(1, std::min(64, (int)std::floor(L / r_list)));
+                g.org[a] = 0.f;
+                g.inv_h[a] = (float)g.dim[a] / L;
+            } else {
+                const int nr = rep_off[r + 1] - rep_off[r];
+                g.dim[a] = std::max(1, std::min(32, (int)std::lround(std::cbrt(nr / 8.0))));
+                g.inv_h[a] = 1.f / r_list;
+            }
+        }
+        g.cell_off = n_cells;
+        n_cells += g.dim[0] * g.dim[1] * g.dim[2];
+        grids[r] = g;
+    }
+    return DMTS_OK;
+}
+
+
+SysView state_view(dmts_state *stt) {
+    StateInternal *si = (StateInternal *)stt->internal;
+    const dmts_system *sys = &stt->sys;
+    SysView v;
+    v.n = sys->n_atoms;
+    v.n_rep = sys->n_replicas;
+    v.rep_off = sys->rep_off;
+    v.box = sys->box;
+    v.x = sys->x;
+    v.species = sys->species;
+    v.mol_id = sys->mol_id;
+    v.bond_ptr = sys->bond_ptr;
+    v.bond_idx = sys->bond_idx;
+    v.bond_r0 = sys->bond_r0;
+    v.atom_rep = (int *)si->atom_rep.p;
+    return v;
+}
+
+// Rebuild of both lists, gated on si->gate (cells, full list, NC sub-list),
+// then the gate is cleared.
+void rebuild_lists(dmts_ctx *ctx, StateInternal *si, const SysView &v, cudaStream_t st) {
+    NbrWork nw;
+    prepare_nbr_work_async(ctx, si, v, nw);
+    nbr_cells(nw, si->r_cons, st);
+    nbr_fill(nw, si->r_cons, (int *)si->cons_row.p, (int *)si->cons_col.p, si->cons_cap, (float *)si->x_ref.p, st);
+    if (ctx->has_nc)
+        nbr_sublist(nw, (int *)si->cons_row.p, (int *)si->cons_col.p, si->r_nc, (int *)si->nc_row.p,
+                    (int *)si->nc_col.p, si->nc_cap, st);
+    k_set_int<<<1, 1, 0, st>>>((int *)si->gate.p, 0);
+}
+
+void prepare_nbr_work_async(dmts_ctx *ctx, StateInternal *si, const SysView &v, NbrWork &nw) {
+    NbrScratch &b = si->scratch;
+    nw.n_atoms = v.n;
+    nw.n_rep = v.n_rep;
+    nw.n_cells = si->n_cells;
+    nw.x = v.x;
+    nw.rep_off = v.rep_off;
+    nw.atom_rep = v.atom_rep;
+    nw.grid = (CellGrid *)b.grid.p;
+    nw.cell_cnt = (int *)b.cell_cnt.p;
+    nw.cell_start = (int *)b.cell_start.p;
+    nw.cell_atoms = (int *)b.cell_atoms.p;
+    nw.atom_cell = (int *)b.atom_cell.p;
+    nw.atom_slot = (int *)b.atom_slot.p;
+    nw.counts = (int *)b.counts.p;
+    nw.total = (long long *)b.total.p;
+    nw.gate = (int *)si->gate.p;
+    nw.err = ctx->d_err;
+}
+
+}  // namespace dmts
+
+// ================================================================ C ABI ==
+extern "C" {
+
+dmts_status dmts_create(dmts_ctx **out, const dmts_model *cons, const dmts_model *nc, const dmts_prior *prior,
+                        int device) {
+    if (!out) return fail(nullptr, DMTS_E_INVALID, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return fail(nullptr, DMTS_E_CUDA, "no such CUDA device");
+    if (cudaSetDevice(device) != cudaSuccess) return fail(nullptr, DMTS_E_CUDA, "cudaSetDevice failed");
+    dmts_ctx *ctx = new dmts_ctx();
+    ctx->device = device;
+    if (prior) ctx->prior = *prior;
+    else ctx->prior = {450.f, 0.15f, 3.15f, 5.f, 6.f, 3.5f, 6.f};
+    if (ctx->prior.rep_rc > 0.f && (ctx->prior.rep_p < 2.f || ctx->prior.rep_p > 12.f)) {
+        delete ctx;
+        return fail(nullptr, DMTS_E_INVALID, "rep_p must be in 2..12");
+    }
+    if (cudaMalloc(&ctx->d_err, sizeof(int)) != cudaSuccess) {
+        delete ctx;
+        return fail(nullptr, DMTS_E_OOM, "allocation failed");
+    }
+    cudaMemset(ctx->d_err, 0, sizeof(int));
+    if (cons) {
+        dmts_status s = load_model(ctx, cons, false, ctx->cons);
+        if (s != DMTS_OK) {
+            std::string msg = ctx->last_error;
+            dmts_destroy(ctx);
+            return fail(nullptr, s, msg);
+        }
+        ctx->has_cons = true;
+    }
+    if (nc) {
+        dmts_status s = load_model(ctx, nc, true, ctx->nc);
+        if (s != DMTS_OK) {
+            std::string msg = ctx->last_error;
+            dmts_destroy(ctx);
+            return fail(nullptr, s, msg);
+        }
+        ctx->has_nc = true;
+        if (ctx->prior.rep_rc > ctx->nc.rc) {
+            dmts_destroy(ctx);
+            return fail(nullptr, DMTS_E_INVALID, "rep_rc must not exceed the NC cutoff");
+        }
+    }
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        dmts_destroy(ctx);
+        return fail(nullptr, DMTS_E_CUDA, "device error during set-up");
+    }
+    *out = ctx;
+    return DMTS_OK;
+}
+
+void dmts_destroy(dmts_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    if (ctx->cons.dev) cudaFree(ctx->cons.dev);
+    if (ctx->nc.dev) cudaFree(ctx->nc.dev);
+    if (ctx->d_err) cudaFree(ctx->d_err);
+    ctx->ws.release_all();
+    delete ctx;
+}
+
+const char *dmts_last_error(const dmts_ctx *ctx) {
+    return ctx ? ctx->last_error.c_str() : g_tls_error.c_str();
+}
+
+dmts_status dmts_sync(dmts_ctx *ctx, void *stream) {
+    if (!ctx) return DMTS_E_INVALID;
+    cudaSetDevice(ctx->device);
+    if (!ck(ctx, cudaStreamSynchronize((cudaStream_t)stream), "stream synchronize")) return DMTS_E_CUDA;
+    int err = 0;
+    if (!ck(ctx, cudaMemcpy(&err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost), "error word")) return DMTS_E_CUDA;
+    if (err) {
+        cudaMemset(ctx->d_err, 0, sizeof(int));
+        cudaDeviceSynchronize();
+        return fail(ctx, (dmts_status)err,
+                    err == DMTS_E_NBR_OVERFLOW ? "neighbour list overflow" :
+                    err == DMTS_E_NONFINITE ? "non-finite positions or velocities" : "device error");
+    }
+    return DMTS_OK;
+}
+
+static dmts_status check_sys(dmts_ctx *ctx, const dmts_system *sys) {
+    if (!ctx || !sys) return fail(ctx, DMTS_E_INVALID, "NULL argument");
+    if (sys->n_atoms < 0 || sys->n_replicas < 1) return fail(ctx, DMTS_E_INVALID, "bad sizes");
+    if (!sys->rep_off || !sys->box || (sys->n_atoms > 0 && (!sys->x || !sys->species || !sys->mol_id)))
+        return fail(ctx, DMTS_E_INVALID, "missing system array");
+    return DMTS_OK;
+}
+
+static SysView make_view(dmts_ctx *ctx, const dmts_system *sys, cudaStream_t st) {
+    SysView v;
+    v.n = sys->n_atoms;
+    v.n_rep = sys->n_replicas;
+    v.rep_off = sys->rep_off;
+    v.box = sys->box;
+    v.x = sys->x;
+    v.species = sys->species;
+    v.mol_id = sys->mol_id;
+    v.bond_ptr = sys->bond_ptr;
+    v.bond_idx = sys->bond_idx;
+    v.bond_r0 = sys->bond_r0;
+    ctx->ws.atom_rep.ensure(sizeof(int) * (v.n + 1));
+    v.atom_rep = (int *)ctx->ws.atom_rep.p;
+    atom_rep_map(sys->rep_off, sys->n_replicas, v.n, (int *)ctx->ws.atom_rep.p, st);
+    return v;
+}
+
+static bool host_copy_offsets(dmts_ctx *ctx, const dmts_system *sys, std::vector<int> &rep_off,
+                              std::vector<float> &box) {
+    rep_off.resize(sys->n_replicas + 1);
+    box.resize(3 * sys->n_replicas);
+    return ck(ctx, cudaMemcpy(rep_off.data(), sys->rep_off, sizeof(int) * rep_off.size(), cudaMemcpyDeviceToHost),
+              "rep_off copy") &&
+           ck(ctx, cudaMemcpy(box.data(), sys->box, sizeof(float) * box.size(), cudaMemcpyDeviceToHost), "box copy");
+}
+
+// Builds the cell structure for `grids` into `nw` scratch owned by `bufs`.
+static dmts_status prepare_nbr_work(dmts_ctx *ctx, NbrScratch &b, const SysView &v, const std::vector<CellGrid> &grids,
+                                    int n_cells, const int *gate, NbrWork &nw) {
+    const int N = v.n, R = v.n_rep;
+    if (!b.grid.ensure(sizeof(CellGrid) * R) || !b.cell_cnt.ensure(sizeof(int) * (n_cells + 1)) ||
+        !b.cell_start.ensure(sizeof(int) * (n_cells + 1)) || !b.cell_atoms.ensure(sizeof(int) * (N + 1)) ||
+        !b.atom_cell.ensure(sizeof(int) * (N + 1)) || !b.atom_slot.ensure(sizeof(int) * (N + 1)) ||
+        !b.counts.ensure(sizeof(int) * (N + 1)) || !b.total.ensure(sizeof(long long)))
+        return fail(ctx, DMTS_E_OOM, "neighbour scratch allocation failed");
+    if (!ck(ctx, cudaMemcpy(b.grid.p, grids.data(), sizeof(CellGrid) * R, cudaMemcpyHostToDevice), "grid upload"))
+        return DMTS_E_CUDA;
+    nw.n_atoms = N;
+    nw.n_rep = R;
+    nw.n_cells = n_cells;
+    nw.x = v.x;
+    nw.rep_off = v.rep_off;
+    nw.atom_rep = v.atom_rep;
+    nw.grid = (CellGrid *)b.grid.p;
+    nw.cell_cnt = (int *)b.cell_cnt.p;
+    nw.cell_start = (int *)b.cell_start.p;
+    nw.cell_atoms = (int *)b.cell_atoms.p;
+    nw.atom_cell = (int *)b.atom_cell.p;
+    nw.atom_slot = (int *)b.atom_slot.p;
+    nw.counts = (int *)b.counts.p;
+    nw.total = (long long *)b.total.p;
+    nw.gate = gate;
+    nw.err = ctx->d_err;
+    return DMTS_OK;
+}
+
+dmts_status nbr_build(dmts_ctx *ctx, const dmts_system *sys, dmts_nbr *nbr, long long *n_pairs, void *stream) {
+    dmts_status s = check_sys(ctx, sys);
+    if (s != DMTS_OK) return s;
+    if (!nbr || !nbr->row_ptr || (!nbr->col && nbr->capacity > 0) || !(nbr->r_list > 0.f))
+        return fail(ctx, DMTS_E_INVALID, "bad neighbour-list argument");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int> rep_off;
+    std::vector<float> box;
+    if (!host_copy_offsets(ctx, sys, rep_off, box)) return DMTS_E_CUDA;
+    if (rep_off[0] != 0 || rep_off.back() != sys->n_atoms) return fail(ctx, DMTS_E_INVALID, "rep_off inconsistent");
+    std::vector<CellGrid> grids;
+    int n_cells = 0;
+    s = setup_grids(ctx, rep_off, box, nbr->r_list, grids, n_cells);
+    if (s != DMTS_OK) return s;
+    SysView v = make_view(ctx, sys, st);
+    NbrWork nw;
+    s = prepare_nbr_work(ctx, ctx->nbr_scratch, v, grids, n_cells, nullptr, nw);
+    if (s != DMTS_OK) return s;
+    nbr_cells(nw, nbr->r_list, st);
+    nbr_fill(nw, nbr->r_list, nbr->row_ptr, nbr->col, nbr->capacity, nullptr, st);
+    long long tot = 0;
+    if (!ck(ctx, cudaMemcpyAsync(&tot, nw.total, sizeof(long long), cudaMemcpyDeviceToHost, st), "count copy") ||
+        !ck(ctx, cudaStreamSynchronize(st), "nbr_build"))
+        return DMTS_E_CUDA;
+    if (n_pairs) *n_pairs = tot;
+    int err = 0;
+    cudaMemcpy(&err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (err) {
+        cudaMemset(ctx->d_err, 0, sizeof(int));
+        if (err == DMTS_E_NBR_OVERFLOW)
+            return fail(ctx, DMTS_E_NBR_OVERFLOW, "neighbour list capacity too small");
+        return fail(ctx, (dmts_status)err, "device error");
+    }
+    return DMTS_OK;
+}
+
+dmts_status energy_forces_cons(dmts_ctx *ctx, const dmts_system *sys, const dmts_nbr *nbr, double *energy,
+                               float *forces, int flags, void *stream) {
+    dmts_status s = check_sys(ctx, sys);
+    if (s != DMTS_OK) return s;
+    if (!ctx->has_cons) return fail(ctx, DMTS_E_INVALID, "context has no conservative model");
+    if (!nbr || !nbr->row_ptr || !nbr->col) return fail(ctx, DMTS_E_INVALID, "bad neighbour list");
+    if (nbr->r_list < ctx->cons.rc || ((flags & DMTS_WITH_PRIOR) && nbr->r_list < ctx->prior.lj_rc))
+        return fail(ctx, DMTS_E_INVALID, "neighbour list cutoff below the model cutoff");
+    if ((flags & DMTS_WITH_PRIOR) && sys->n_atoms > 0 && (!sys->bond_ptr || !sys->bond_idx || !sys->bond_r0))
+        return fail(ctx, DMTS_E_INVALID, "prior requested without a bond table");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    SysView v = make_view(ctx, sys, st);
+    s = cons_eval(ctx, v, nbr->row_ptr, nbr->col, energy, forces, flags, st);
+    if (s != DMTS_OK) return s;
+    return ck(ctx, cudaGetLastError(), "energy_forces_cons launch") ? DMTS_OK : DMTS_E_CUDA;
+}
+
+dmts_status forces_nc(dmts_ctx *ctx, const dmts_system *sys, const dmts_nbr *nbr, float *forces, double *net_force,
+                      int flags, void *stream) {
+    dmts_status s = check_sys(ctx, sys);
+    if (s != DMTS_OK) return s;
+    if (!ctx->has_nc) return fail(ctx, DMTS_E_INVALID, "context has no NC model");
+    if (!nbr || !nbr->row_ptr || !nbr->col || !forces) return fail(ctx, DMTS_E_INVALID, "bad argument");
+    if (nbr->r_list < ctx->nc.rc) return fail(ctx, DMTS_E_INVALID, "neighbour list cutoff below the NC cutoff");
+    if ((flags & DMTS_WITH_BONDS) && sys->n_atoms > 0 && (!sys->bond_ptr || !sys->bond_idx || !sys->bond_r0))
+        return fail(ctx, DMTS_E_INVALID, "bonds requested without a bond table");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    SysView v = make_view(ctx, sys, st);
+    s = nc_eval(ctx, v, nbr->row_ptr, nbr->col, forces, net_force, flags, st);
+    if (s != DMTS_OK) return s;
+    return ck(ctx, cudaGetLastError(), "forces_nc launch") ? DMTS_OK : DMTS_E_CUDA;
+}
+
+// ------------------------------------------------------------ respa_step
+static void free_state_internal(StateInternal *si) {
+    if (!si) return;
+    si->cons_row.release();
+    si->cons_col.release();
+    si->nc_row.release();
+    si->nc_col.release();
+    si->x_ref.release();
+    si->gate.release();
+    si->atom_rep.release();
+    si->scratch.release_all();
+    delete si;
+}
+
+void dmts_state_release(dmts_ctx *ctx, dmts_state *st) {
+    if (!st || !st->internal) return;
+    if (ctx) cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    free_state_internal((StateInternal *)st->internal);
+    st->internal = nullptr;
+}
+
+// Allocates lists (capacity from a first count with 40 % head-room) and the
+// cell grids; leaves the lists built for the current positions.
+static dmts_status init_state(dmts_ctx *ctx, dmts_state *stt, float skin, cudaStream_t st) {
+    const dmts_system *sys = &stt->sys;
+    StateInternal *si = new StateInternal();
+    stt->internal = si;
+    std::vector<int> rep_off;
+    std::vector<float> box;
+    if (!host_copy_offsets(ctx, sys, rep_off, box)) return DMTS_E_CUDA;
+    if (rep_off[0] != 0 || rep_off.back() != sys->n_atoms) return fail(ctx, DMTS_E_INVALID, "rep_off inconsistent");
+    si->n = sys->n_atoms;
+    si->n_rep = sys->n_replicas;
+    si->skin = skin;
+    si->r_cons = std::max(ctx->cons.rc, ctx->prior.lj_rc) + skin;
+    si->r_nc = (ctx->has_nc ? ctx->nc.rc : 0.f) + skin;
+    dmts_status s = setup_grids(ctx, rep_off, box, si->r_cons, si->grids, si->n_cells);
+    if (s != DMTS_OK) return s;
+    const int N = si->n;
+    if (!si->atom_rep.ensure(sizeof(int) * (N + 1)) || !si->x_ref.ensure(sizeof(float) * 3 * (N + 1)) ||
+        !si->gate.ensure(sizeof(int)) || !si->cons_row.ensure(sizeof(int) * (N + 1)) ||
+        !si->nc_row.ensure(sizeof(int) * (N + 1)))
+        return fail(ctx, DMTS_E_OOM, "state allocation failed");
+    atom_rep_map(sys->rep_off, sys->n_replicas, N, (int *)si->atom_rep.p, st);
+    k_set_int<<<1, 1, 0, st>>>((int *)si->gate.p, 1);
+    SysView v = state_view(stt);
+    NbrWork nw;
+    s = prepare_nbr_work(ctx, si->scratch, v, si->grids, si->n_cells, (int *)si->gate.p, nw);
+    if (s != DMTS_OK) return s;
+    nbr_cells(nw, si->r_cons, st);
+    // size the lists from a count pass
+    nbr_fill(nw, si->r_cons, (int *)si->cons_row.p, nullptr, -1, nullptr, st);
+    long long tot = 0;
+    cudaMemcpyAsync(&tot, nw.total, sizeof(long long), cudaMemcpyDeviceToHost, st);
+    if (!ck(ctx, cudaStreamSynchronize(st), "list sizing")) return DMTS_E_CUDA;
+    si->cons_cap = (long long)(tot * 1.4) + 16LL * N + 1024;
+    const double frac = ctx->has_nc ? std::pow(si->r_nc / si->r_cons, 3.0) : 0.0;
+    si->nc_cap = (long long)(tot * frac * 1.6) + 16LL * N + 1024;
+    if (!si->cons_col.ensure(sizeof(int) * si->cons_cap) || !si->nc_col.ensure(sizeof(int) * si->nc_cap))
+        return fail(ctx, DMTS_E_OOM, "neighbour list allocation failed");
+    rebuild_lists(ctx, si, v, st);
+    if (!ck(ctx, cudaStreamSynchronize(st), "initial lists")) return DMTS_E_CUDA;
+    int err = 0;
+    cudaMemcpy(&err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (err) return fail(ctx, (dmts_status)err, "initial neighbour build failed");
+    return DMTS_OK;
+}
+
+
+static void gamma_consts(const dmts_integrator *p, double dt, float *c1, float *c2) {
+    for (int s = 0; s < DMTS_MAX_SPECIES; ++s) {
+        const double e = std::exp(-p->gamma_ps[s] * 1e-3 * dt);
+        c1[s] = (float)e;
+        c2[s] = (float)std::sqrt((1.0 - e * e) * kBoltzmann * p->temperature * kAccConvD);
+    }
+}
+
+dmts_status respa_step(dmts_ctx *ctx, dmts_state *stt, const dmts_integrator *p, int n_outer, void *stream) {
+    if (!stt || !p) return fail(ctx, DMTS_E_INVALID, "NULL argument");
+    dmts_status s = check_sys(ctx, &stt->sys);
+    if (s != DMTS_OK) return s;
+    if (!ctx->has_cons) return fail(ctx, DMTS_E_INVALID, "context has no conservative model");
+    const bool sts = p->mode == DMTS_MODE_STS;
+    if (!sts && (!ctx->has_nc || p->n_inner < 1)) return fail(ctx, DMTS_E_INVALID, "RESPA needs an NC model and n_inner >= 1");
+    if (!(p->dt_outer > 0.f) || n_outer < 0 || !(p->skin > 0.f)) return fail(ctx, DMTS_E_INVALID, "bad integrator parameters");
+    if (!stt->v || !stt->f_cons || (!sts && !stt->f_nc) || !stt->masses || !stt->step || !stt->seed || !stt->replica_id)
+        return fail(ctx, DMTS_E_INVALID, "missing state array");
+    if (stt->sys.n_atoms > 0 && (!stt->sys.bond_ptr || !stt->sys.bond_idx || !stt->sys.bond_r0))
+        return fail(ctx, DMTS_E_INVALID, "missing bond table");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!stt->internal) {
+        s = init_state(ctx, stt, p->skin, st);
+        if (s != DMTS_OK) {
+            free_state_internal((StateInternal *)stt->internal);
+            stt->internal = nullptr;
+            return s;
+        }
+    }
+    StateInternal *si = (StateInternal *)stt->internal;
+    if (si->n != stt->sys.n_atoms || si->n_rep != stt->sys.n_replicas || si->skin != p->skin)
+        return fail(ctx, DMTS_E_INVALID, "state shape changed; release the state first");
+    const SysView v = state_view(stt);
+    const int *crow = (int *)si->cons_row.p, *ccol = (int *)si->cons_col.p;
+    const int *nrow = (int *)si->nc_row.p, *ncol = (int *)si->nc_col.p;
+    auto cons_full = [&]() {
+        return cons_eval(ctx, v, crow, ccol, stt->energy, stt->f_cons, DMTS_WITH_PRIOR, st);
+    };
+    auto nc_fast = [&]() { return nc_eval(ctx, v, nrow, ncol, stt->f_nc, nullptr, DMTS_WITH_BONDS, st); };
+
+    if (stt->first_step) {
+        if (!sts) {
+            s = nc_fast();
+            if (s != DMTS_OK) return s;
+        }
+        s = cons_full();
+        if (s != DMTS_OK) return s;
+        stt->first_step = 0;
+    }
+    IntegArgs ia;
+    memset(&ia, 0, sizeof ia);
+    ia.n_atoms = v.n;
+    ia.atom_rep = v.atom_rep;
+    ia.rep_off = v.rep_off;
+    ia.x = stt->sys.x;
+    ia.v = stt->v;
+    ia.f_slow = stt->f_cons;
+    ia.f_fast = sts ? stt->f_cons : stt->f_nc;
+    ia.masses = stt->masses;
+    ia.species = stt->sys.species;
+    ia.seed = stt->seed;
+    ia.rep_id = stt->replica_id;
+    ia.step = stt->step;
+    ia.x_ref = (float *)si->x_ref.p;
+    ia.half_skin2 = 0.25f * p->skin * p->skin;
+    ia.rebuild = (int *)si->gate.p;
+    ia.err = ctx->d_err;
+    const int n_in = sts ? 1 : p->n_inner;
+    const double delta = sts ? p->dt_outer : (double)p->dt_outer / n_in;
+    gamma_consts(p, delta, ia.c1, ia.c2);
+    ia.h_in = (float)(0.5 * delta);
+    ia.h_out = 0.5f * p->dt_outer;
+    if (n_outer == 0) return DMTS_OK;
+    for (int o = 0; o < n_outer; ++o) {
+        for (int k = 0; k < n_in; ++k) {
+            if (sts) ia.ops = (o == 0 ? 0 : OP_CLOSE_B) | OP_BAOA;
+            else if (k == 0) ia.ops = (o == 0 ? OP_KICK_L2 : (OP_CLOSE_B | OP_KICK_L | OP_KICK_L2)) | OP_BAOA;
+            else ia.ops = OP_CLOSE_B | OP_BAOA;
+            ia.step_add = (uint64_t)o * n_in + k;
+            launch_integrate(ia, st);
+            rebuild_lists(ctx, si, v, st);
+            if (!sts) {
+                s = nc_fast();
+                if (s != DMTS_OK) return s;
+            }
+        }
+        s = cons_full();
+        if (s != DMTS_OK) return s;
+    }
+    ia.ops = sts ? OP_CLOSE_B : (OP_CLOSE_B | OP_KICK_L);
+    launch_integrate(ia, st);
+    launch_advance_step(stt->step, v.n_rep, (uint64_t)n_outer * n_in, ctx->d_err, st);
+    return ck(ctx, cudaGetLastError(), "respa_step launch") ? DMTS_OK : DMTS_E_CUDA;
+}
+
+// ------------------------------------------------------------- helpers
+void dmts_masses_hmr(int n, const uint8_t *species, const int *mol_id, const double *m_in, double delta_h,
+                     double *m_out) {
+    int max_mol = 0;
+    for (int i = 0; i < n; ++i) max_mol = std::max(max_mol, mol_id[i]);
+    std::vector<double> gain(max_mol + 1, 0.0), heavy(max_mol + 1, 0.0);
+    for (int i = 0; i < n; ++i) {
+        if (species[i] == 0) gain[mol_id[i]] += delta_h;
+        else heavy[mol_id[i]] += m_in[i];
+    }
+    for (int i = 0; i < n; ++i) {
+        const int mo = mol_id[i];
+        if (heavy[mo] == 0.0) m_out[i] = m_in[i];
+        else if (species[i] == 0) m_out[i] = m_in[i] + delta_h;
+        else m_out[i] = m_in[i] - gain[mo] * (m_in[i] / heavy[mo]);
+    }
+}
+
+dmts_status dmts_bond_table(int n_atoms, int n_bonds, const int *bonds, const float *r0, int *ptr, int *idx,
+                            float *r0_out) {
+    if (n_atoms < 0 || n_bonds < 0 || !ptr || (n_bonds > 0 && (!bonds || !r0 || !idx || !r0_out)))
+        return DMTS_E_INVALID;
+    std::vector<int> cnt(n_atoms + 1, 0);
+    for (int b = 0; b < n_bonds; ++b) {
+        const int i = bonds[2 * b], j = bonds[2 * b + 1];
+        if (i < 0 || j < 0 || i >= n_atoms || j >= n_atoms || i == j) return DMTS_E_INVALID;
+        cnt[i]++;
+        cnt[j]++;
+    }
+    ptr[0] = 0;
+    for (int i = 0; i < n_atoms; ++i) ptr[i + 1] = ptr[i] + cnt[i];
+    std::vector<int> fill(ptr, ptr + n_atoms);
+    for (int b = 0; b < n_bonds; ++b) {
+        const int i = bonds[2 * b], j = bonds[2 * b + 1];
+        idx[fill[i]] = j;
+        r0_out[fill[i]++] = r0[b];
+        idx[fill[j]] = i;
+        r0_out[fill[j]++] = r0[b];
+    }
+    return DMTS_OK;
+}
+
+__global__ void k_philox_words(uint64_t seed, uint32_t rep, uint64_t step, uint32_t atom0, int count, uint32_t *out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const uint4 w = philox4x32_10(make_uint4(atom0 + i, rep, (uint32_t)step, (uint32_t)(step >> 32)),
+                                  (uint32_t)seed, (uint32_t)(seed >> 32));
+    out[4 * i] = w.x; out[4 * i + 1] = w.y; out[4 * i + 2] = w.z; out[4 * i + 3] = w.w;
+}
+
+__global__ void k_gaussians(uint64_t seed, uint32_t rep, uint64_t step, uint32_t atom0, int count, float *out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const float3 g = gauss3(seed, rep, step, atom0 + i);
+    out[3 * i] = g.x; out[3 * i + 1] = g.y; out[3 * i + 2] = g.z;
+}
+
+dmts_status dmts_philox_words(dmts_ctx *ctx, uint64_t seed, uint32_t replica, uint64_t step, uint32_t atom0, int count,
+                              uint32_t *out, void *stream) {
+    if (!ctx || !out || count < 0) return fail(ctx, DMTS_E_INVALID, "bad argument");
+    cudaSetDevice(ctx->device);
+    if (count) k_philox_words<<<(count + 255) / 256, 256, 0, (cudaStream_t)stream>>>(seed, replica, step, atom0, count, out);
+    return ck(ctx, cudaGetLastError(), "philox launch") ? DMTS_OK : DMTS_E_CUDA;
+}
+
+dmts_status dmts_gaussians(dmts_ctx *ctx, uint64_t seed, uint32_t replica, uint64_t step, uint32_t atom0, int count,
+                           float *out, void *stream) {
+    if (!ctx || !out || count < 0) return fail(ctx, DMTS_E_INVALID, "bad argument");
+    cudaSetDevice(ctx->device);
+    if (count) k_gaussians<<<(count + 255) / 256, 256, 0, (cudaStream_t)stream>>>(seed, replica, step, atom0, count, out);
+    return ck(ctx, cudaGetLastError(), "gaussian launch") ? DMTS_OK : DMTS_E_CUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,98 @@
+// Internal host-side structures of the library.
+#pragma once
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "md.cuh"
+#include "mp.cuh"
+#include "nbr.cuh"
+
+namespace dmts {
+
+struct Buf {
+    void *p = nullptr;
+    size_t cap = 0;
+    bool ensure(size_t bytes);
+    void release();
+};
+
+struct DevModel {
+    int L = 0, C = 0, lmax = 0, K = 0, S = 0, nc = 0, nl = 0, p = 0;
+    float rc = 0.f, nu = 0.f, scale = 0.f;
+    bool bf16 = false;
+    float *dev = nullptr;                 // one allocation holding every tensor
+    float *emb = nullptr;
+    float *wrad[DMTS_MAX_LAYERS] = {}, *w1[DMTS_MAX_LAYERS] = {}, *b1[DMTS_MAX_LAYERS] = {},
+          *w2[DMTS_MAX_LAYERS] = {}, *b2[DMTS_MAX_LAYERS] = {};
+    float *wr = nullptr, *br = nullptr, *wo = nullptr;
+    float *U = nullptr, *Wqk = nullptr;
+};
+
+struct NbrScratch {
+    Buf grid, cell_cnt, cell_start, cell_atoms, atom_cell, atom_slot, counts, total;
+    void release_all() {
+        grid.release(); cell_cnt.release(); cell_start.release(); cell_atoms.release();
+        atom_cell.release(); atom_slot.release(); counts.release(); total.release();
+    }
+};
+
+struct Workspace {
+    Buf s, A, q, h, act, u, gz, gs0, gs1, gA, e_atom, ftmp, atom_rep;
+    Buf nc_s, nc_A, nc_q, nc_h, nc_act, nc_qk, nc_v, nc_f;
+    void release_all() {
+        Buf *all[] = {&s, &A, &q, &h, &act, &u, &gz, &gs0, &gs1, &gA, &e_atom, &ftmp, &atom_rep,
+                      &nc_s, &nc_A, &nc_q, &nc_h, &nc_act, &nc_qk, &nc_v, &nc_f};
+        for (Buf *b : all) b->release();
+    }
+};
+
+// Device view of a batch used by the force evaluations.
+struct SysView {
+    int n, n_rep;
+    const int *rep_off;
+    const float *box;
+    const float *x;
+    const uint8_t *species;
+    const int *mol_id;
+    const int *bond_ptr, *bond_idx;
+    const float *bond_r0;
+    const int *atom_rep;
+};
+
+struct StateInternal {
+    int n = 0, n_rep = 0, n_cells = 0;
+    float skin = 0.f, r_cons = 0.f, r_nc = 0.f;
+    std::vector<CellGrid> grids;
+    Buf cons_row, cons_col, nc_row, nc_col, x_ref, gate, atom_rep;
+    long long cons_cap = 0, nc_cap = 0;
+    NbrScratch scratch;
+};
+
+}  // namespace dmts
+
+struct dmts_ctx {
+    int device = 0;
+    dmts::DevModel cons, nc;
+    bool has_cons = false, has_nc = false;
+    dmts_prior prior{};
+    int *d_err = nullptr;
+    std::string last_error;
+    dmts::Workspace ws;
+    dmts::NbrScratch nbr_scratch;
+};
+
+namespace dmts {
+bool ck(dmts_ctx *ctx, cudaError_t e, const char *what);
+dmts_status fail(dmts_ctx *ctx, dmts_status s, const std::string &msg);
+dmts_status cons_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const int *col, double *energy,
+                      float *forces, int flags, cudaStream_t st);
+dmts_status nc_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const int *col, float *forces,
+                    double *net, int flags, cudaStream_t st);
+dmts_status setup_grids(dmts_ctx *ctx, const std::vector<int> &rep_off, const std::vector<float> &box,
+                        float r_list, std::vector<CellGrid> &grids, int &n_cells);
+SysView state_view(dmts_state *stt);
+RepTable rep_table(const dmts_ctx *ctx);
+void rebuild_lists(dmts_ctx *ctx, StateInternal *si, const SysView &v, cudaStream_t st);
+void prepare_nbr_work_async(dmts_ctx *ctx, StateInternal *si, const SysView &v, NbrWork &nw);
+}  // namespace dmts

@@ -1,0 +1,97 @@
+// NC direct-force head, analytic prior, fused BAOAB/RESPA integrator.
+#pragma once
+#include "common.cuh"
+
+namespace dmts {
+
+struct BondTable {
+    const int *ptr, *idx;
+    const float *r0;
+    float k;
+};
+
+// Screened nuclear repulsion for species pairs (ZBL universal screening):
+// E = zz[si][sj] / r * phi(r * inv_a[si][sj]) * f(r/rc; p), bonded pairs excluded.
+struct RepTable {
+    float zz[5][5];      // k_e Z_i Z_j
+    float inv_a[5][5];   // 1 / a_ij
+    float rc, inv_rc;
+    int p;
+    int on;
+};
+
+struct NCHeadArgs {
+    const float *x;
+    const int *atom_rep;
+    const float *box;
+    const int *row_ptr, *col;      // NC list (cutoff + skin)
+    int n_atoms;
+    float rc, inv_rc, bnorm;
+    int p;
+    const float *QK;               // [N][2][H][nc]
+    const float *V;                // [N][n_l][3]
+    float scale;
+    BondTable bonds;               // bonds.ptr null: no bond force, no F_rep
+    RepTable rep;
+    const uint8_t *species;
+    float *F;                      // [N][3] before mean subtraction
+    const int *err;
+};
+
+void launch_nc_vectors(int n, int C, int n_l, const float *A, const float *U, float *V, const int *err,
+                       cudaStream_t st);
+void launch_nc_head(int K, int n_c, int n_l, const NCHeadArgs &a, cudaStream_t st);
+// F_out = F_in - (sum_{replica} F_in)/n_r, FP64 sums; net (nullable) [R][3].
+void launch_mean_sub(const float *F_in, float *F_out, const int *rep_off, int n_rep, double *net,
+                     const int *err, cudaStream_t st);
+
+struct PriorArgs {
+    const float *x;
+    const int *atom_rep;
+    const float *box;
+    const int *row_ptr, *col;      // list with cutoff >= lj_rc
+    const uint8_t *species;
+    const int *mol_id;
+    int n_atoms;
+    float lj_eps, lj_sigma, lj_rc;
+    int lj_p;
+    BondTable bonds;
+    RepTable rep;
+    float *F;                      // accumulated
+    float *e_atom;                 // accumulated per-atom energy (nullable)
+    const int *err;
+};
+void launch_prior(const PriorArgs &a, cudaStream_t st);
+
+enum IntegOps {
+    OP_CLOSE_B = 1,     // v += h_in a F_fast
+    OP_KICK_L = 2,      // v += h_out a (F_slow - F_fast)  (end of an outer step)
+    OP_KICK_L2 = 4,     // v += h_out a (F_slow - F_fast)  (start of an outer step)
+    OP_BAOA = 8,        // v += h_in a F_fast; x += h_in v; O(delta); x += h_in v
+};
+
+struct IntegArgs {
+    int n_atoms;
+    const int *atom_rep, *rep_off;
+    float *x, *v;
+    const float *f_slow, *f_fast;
+    const float *masses;
+    const uint8_t *species;
+    float c1[DMTS_MAX_SPECIES], c2[DMTS_MAX_SPECIES];
+    const uint64_t *seed;
+    const uint32_t *rep_id;
+    const uint64_t *step;
+    uint64_t step_add;
+    float h_out, h_in;
+    int ops;
+    const float *x_ref;            // nullable: displacement check
+    float half_skin2;
+    int *rebuild;
+    int *err;
+};
+void launch_integrate(const IntegArgs &a, cudaStream_t st);
+void launch_advance_step(uint64_t *step, int n_rep, uint64_t add, const int *err, cudaStream_t st);
+void launch_embed(int n, int C, const uint8_t *species, const float *emb, float *s, cudaStream_t st);
+void launch_rowsum(int n, int C, const float *u, float scale, float *e_atom, cudaStream_t st);
+
+}  // namespace dmts

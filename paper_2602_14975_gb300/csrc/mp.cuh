@@ -1,0 +1,105 @@
+// Kernels of the message-passing layer (edge embedding + segmented
+// scatter-sum) and of its adjoint, plus the node-level GEMMs of the MLPs.
+#pragma once
+#include "common.cuh"
+
+namespace dmts {
+
+// Geometry shared by the edge kernels of one model evaluation.
+struct EdgeGeom {
+    const float *x;          // [N][3]
+    const int *atom_rep;     // [N] replica of each atom
+    const float *box;        // [R][3]
+    const int *row_ptr;      // [N+1] stored list (cutoff + skin)
+    const int *col;
+    int n_atoms;
+    float rc, inv_rc, bnorm; // model cutoff, 1/rc, sqrt(2/rc)
+    int p;                   // envelope exponent
+};
+
+// Node-level arrays for one layer.
+struct LayerIO {
+    const float *s;          // [N][C] input features s^t
+    const float *wrad;       // [L+1][K][C]
+    float nu;
+    float *A;                // [N][NLM][C]  (forward out)
+    float *q;                // [N][(LMAX+1)C] (forward out, fp32)
+    __nv_bfloat16 *q_bf16;   // optional bf16 copy of q (forward out)
+    const float *gA;         // [N][NLM][C]  (backward in)
+    const float *gs_in;      // [N][C]       (backward in)
+    float *gs_out;           // [N][C]       (backward out)
+    float *F;                // [N][3]       (backward: accumulated forces)
+    int accumulate;          // backward: 0 write F, 1 add to F
+    const int *err;
+};
+
+template <int CPW>
+struct VecF;
+template <> struct VecF<1> { using T = float; };
+template <> struct VecF<2> { using T = float2; };
+template <> struct VecF<4> { using T = float4; };
+
+template <int CPW>
+__device__ __forceinline__ void ldv(const float *p, float *v) {
+    if constexpr (CPW == 4) {
+        float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    } else if constexpr (CPW == 2) {
+        float2 t = __ldg(reinterpret_cast<const float2 *>(p));
+        v[0] = t.x; v[1] = t.y;
+    } else {
+        v[0] = __ldg(p);
+    }
+}
+
+template <int CPW>
+__device__ __forceinline__ void stv(float *p, const float *v) {
+    if constexpr (CPW == 4) {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    } else if constexpr (CPW == 2) {
+        *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+    } else {
+        *p = v[0];
+    }
+}
+
+void launch_mp_fwd(int C, int lmax, int K, const EdgeGeom &g, const LayerIO &io, cudaStream_t st);
+void launch_mp_bwd(int C, int lmax, int K, const EdgeGeom &g, const LayerIO &io, cudaStream_t st);
+
+// ---------------------------------------------------------------- GEMM ----
+enum EpiMode {
+    EPI_STORE = 0,           // out = v
+    EPI_BIAS_SILU = 1,       // H = v + bias; out = silu(H) (and H stored)
+    EPI_RESID = 2,           // out = res + v + bias
+    EPI_DSILU = 3,           // out = v * dsilu(H)
+    EPI_GA = 4,              // gA[m][lm][c] = 2 A[m][lm][c] v,  n = l*C + c
+    EPI_READOUT = 5,         // z = v + bias: out = wo silu(z), out2 = scale wo dsilu(z)
+};
+
+struct Epi {
+    int mode;
+    float *out;
+    __nv_bfloat16 *out_bf16;   // optional bf16 copy of out
+    float *out2;
+    const float *bias;
+    const float *res;          // residual input [M][N]
+    float *H;                  // pre-activation store / load
+    const float *A;            // EPI_GA
+    const float *wo;           // EPI_READOUT
+    float scale;
+    int C, lmax;               // EPI_GA
+};
+
+// Out[M][N] = Act[M][K] x op(W) where op(W) = W^T for W [N][K] (trans = 1)
+// or W for W [K][N] (trans = 0); fp32 SIMT.
+void launch_gemm_f32(int M, int N, int K, const float *Act, const float *W, int trans, const Epi &e,
+                     cudaStream_t st);
+// Same contraction with bf16 operands on the tensor cores, fp32 accumulate.
+void launch_gemm_bf16(int M, int N, int K, const __nv_bfloat16 *Act, const __nv_bfloat16 *W, int trans,
+                      const Epi &e, cudaStream_t st);
+
+// Per-replica FP64 sums of per-atom values: out[r] = sum_{i in r} v[i].
+void launch_replica_sum(const float *v, const int *rep_off, int n_rep, double *out, int accumulate,
+                        cudaStream_t st);
+
+}  // namespace dmts

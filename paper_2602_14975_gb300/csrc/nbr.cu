@@ -1,0 +1,277 @@
+// Cell-list neighbour build (minimum image, open or periodic, batched over
+// replicas). Cell grids have edge >= r_list, so all pairs lie in the 27 (or
+// fewer, de-duplicated) neighbouring cells. Rows are sorted by neighbour
+// index, so their order is canonical and independent of scheduling.
+#include "nbr.cuh"
+
+namespace dmts {
+
+__device__ __forceinline__ bool gated_off(const int *gate, const int *err) {
+    return (gate && *gate == 0) || *err;
+}
+
+__global__ void k_atom_rep(const int *rep_off, int n_rep, int n, int *atom_rep) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) atom_rep[i] = replica_of(rep_off, n_rep, i);
+}
+
+void atom_rep_map(const int *rep_off, int n_rep, int n_atoms, int *atom_rep, cudaStream_t st) {
+    if (n_atoms == 0) return;
+    k_atom_rep<<<(n_atoms + 255) / 256, 256, 0, st>>>(rep_off, n_rep, n_atoms, atom_rep);
+}
+
+// Open replicas: bounding box -> origin and cell edge max(r_list, extent/dim).
+__global__ void k_grid_open(NbrWork w, float r_list) {
+    if (gated_off(w.gate, w.err)) return;
+    const int r = blockIdx.x;
+    CellGrid &g = w.grid[r];
+    if (g.box[0] > 0.f) return;   // periodic: fixed on the host
+    __shared__ float red[6][32];
+    float mn[3] = {3.4e38f, 3.4e38f, 3.4e38f}, mx[3] = {-3.4e38f, -3.4e38f, -3.4e38f};
+    const int beg = w.rep_off[r], end = w.rep_off[r + 1];
+    for (int i = beg + threadIdx.x; i < end; i += blockDim.x)
+        for (int a = 0; a < 3; ++a) {
+            const float v = w.x[3 * i + a];
+            mn[a] = fminf(mn[a], v);
+            mx[a] = fmaxf(mx[a], v);
+        }
+    for (int a = 0; a < 3; ++a)
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[a] = fminf(mn[a], __shfl_xor_sync(DMTS_FULL, mn[a], o));
+            mx[a] = fmaxf(mx[a], __shfl_xor_sync(DMTS_FULL, mx[a], o));
+        }
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (lane == 0)
+        for (int a = 0; a < 3; ++a) { red[a][wid] = mn[a]; red[3 + a][wid] = mx[a]; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int a = 0; a < 3; ++a) {
+            float lo = 3.4e38f, hi = -3.4e38f;
+            for (int k = 0; k < nw; ++k) { lo = fminf(lo, red[a][k]); hi = fmaxf(hi, red[3 + a][k]); }
+            if (end == beg) { lo = 0.f; hi = 0.f; }
+            const float h = fmaxf(r_list, (hi - lo) / (float)g.dim[a]);
+            g.org[a] = lo;
+            g.inv_h[a] = 1.f / h;
+        }
+    }
+}
+
+__device__ __forceinline__ int cell_coord(float v, const CellGrid &g, int a) {
+    int c;
+    if (g.box[a] > 0.f) {
+        const float w = v - g.box[a] * floorf(v / g.box[a]);
+        c = (int)(w * g.inv_h[a]);
+    } else {
+        c = (int)floorf((v - g.org[a]) * g.inv_h[a]);
+    }
+    return min(max(c, 0), g.dim[a] - 1);
+}
+
+__global__ void k_cell_assign(NbrWork w) {
+    if (gated_off(w.gate, w.err)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= w.n_atoms) return;
+    const CellGrid g = w.grid[w.atom_rep[i]];
+    const int cx = cell_coord(w.x[3 * i], g, 0), cy = cell_coord(w.x[3 * i + 1], g, 1),
+              cz = cell_coord(w.x[3 * i + 2], g, 2);
+    const int cell = g.cell_off + (cz * g.dim[1] + cy) * g.dim[0] + cx;
+    w.atom_cell[i] = cell;
+    w.atom_slot[i] = atomicAdd(&w.cell_cnt[cell], 1);
+}
+
+__global__ void k_cell_scatter(NbrWork w) {
+    if (gated_off(w.gate, w.err)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= w.n_atoms) return;
+    w.cell_atoms[w.cell_start[w.atom_cell[i]] + w.atom_slot[i]] = i;
+}
+
+// Visits every candidate j of atom i (fixed cell order, ascending j inside a
+// cell); calls f(j, r2) for j != i with r2 < rc2.
+template <typename Fn>
+__device__ __forceinline__ void for_candidates(const NbrWork &w, int i, float rc2, Fn f) {
+    const CellGrid g = w.grid[w.atom_rep[i]];
+    const float xi = w.x[3 * i], yi = w.x[3 * i + 1], zi = w.x[3 * i + 2];
+    const int own = w.atom_cell[i] - g.cell_off;
+    const int cx = own % g.dim[0], cy = (own / g.dim[0]) % g.dim[1], cz = own / (g.dim[0] * g.dim[1]);
+    int lo[3], hi[3];
+    const int c3[3] = {cx, cy, cz};
+    for (int a = 0; a < 3; ++a) {
+        if (g.box[a] > 0.f) {
+            if (g.dim[a] >= 3) { lo[a] = -1; hi[a] = 1; }
+            else if (g.dim[a] == 2) { lo[a] = 0; hi[a] = 1; }
+            else { lo[a] = 0; hi[a] = 0; }
+        } else {
+            lo[a] = c3[a] > 0 ? -1 : 0;
+            hi[a] = c3[a] < g.dim[a] - 1 ? 1 : 0;
+        }
+    }
+    const float ibx = g.box[0] > 0.f ? 1.f / g.box[0] : 0.f;
+    const float iby = g.box[1] > 0.f ? 1.f / g.box[1] : 0.f;
+    const float ibz = g.box[2] > 0.f ? 1.f / g.box[2] : 0.f;
+    for (int oz = lo[2]; oz <= hi[2]; ++oz) {
+        int z = cz + oz;
+        if (g.box[2] > 0.f) z = (z + g.dim[2]) % g.dim[2];
+        for (int oy = lo[1]; oy <= hi[1]; ++oy) {
+            int y = cy + oy;
+            if (g.box[1] > 0.f) y = (y + g.dim[1]) % g.dim[1];
+            for (int ox = lo[0]; ox <= hi[0]; ++ox) {
+                int xx = cx + ox;
+                if (g.box[0] > 0.f) xx = (xx + g.dim[0]) % g.dim[0];
+                const int cell = g.cell_off + (z * g.dim[1] + y) * g.dim[0] + xx;
+                const int beg = w.cell_start[cell], end = w.cell_start[cell + 1];
+                for (int p = beg; p < end; ++p) {
+                    const int j = w.cell_atoms[p];
+                    if (j == i) continue;
+                    const float dx = min_img(w.x[3 * j] - xi, g.box[0], ibx);
+                    const float dy = min_img(w.x[3 * j + 1] - yi, g.box[1], iby);
+                    const float dz = min_img(w.x[3 * j + 2] - zi, g.box[2], ibz);
+                    const float r2 = dx * dx + dy * dy + dz * dz;
+                    if (r2 < rc2) f(j);
+                }
+            }
+        }
+    }
+}
+
+__global__ void k_nbr_count(NbrWork w, float rc2) {
+    if (gated_off(w.gate, w.err)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= w.n_atoms) return;
+    int cnt = 0;
+    for_candidates(w, i, rc2, [&](int) { ++cnt; });
+    w.counts[i] = cnt;
+}
+
+__global__ void k_nbr_fill(NbrWork w, float rc2, const int *row_ptr, int *col, float *x_ref) {
+    if (gated_off(w.gate, w.err)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= w.n_atoms) return;
+    const int beg = row_ptr[i];
+    int p = beg;
+    for_candidates(w, i, rc2, [&](int j) { col[p++] = j; });
+    // canonical row order (ascending j): rows do not depend on the cell
+    // layout at build time, so results do not depend on when lists were rebuilt
+    for (int a = beg + 1; a < p; ++a) {
+        const int v = col[a];
+        int b = a - 1;
+        while (b >= beg && col[b] > v) {
+            col[b + 1] = col[b];
+            --b;
+        }
+        col[b + 1] = v;
+    }
+    if (x_ref) {
+        x_ref[3 * i] = w.x[3 * i];
+        x_ref[3 * i + 1] = w.x[3 * i + 1];
+        x_ref[3 * i + 2] = w.x[3 * i + 2];
+    }
+}
+
+// Single-block exclusive scan (n up to a few million).
+__global__ void __launch_bounds__(1024) k_scan(const int *in, int n, int *out, long long capacity,
+                                               long long *total, int *err, const int *gate) {
+    if (gated_off(gate, err)) return;
+    __shared__ long long part[1024];
+    const int t = threadIdx.x;
+    const int chunk = (n + 1023) / 1024;
+    const int beg = min(t * chunk, n), end = min(beg + chunk, n);
+    long long s = 0;
+    for (int k = beg; k < end; ++k) s += in[k];
+    part[t] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        long long v = t >= off ? part[t - off] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    long long run = part[t] - s;
+    const long long tot = part[1023];
+    const bool over = capacity >= 0 && tot > capacity;
+    if (!over) {
+        for (int k = beg; k < end; ++k) {
+            out[k] = (int)run;
+            run += in[k];
+        }
+        if (t == 1023) out[n] = (int)tot;
+    }
+    if (t == 0) {
+        if (total) *total = tot;
+        if (over) set_error(err, DMTS_E_NBR_OVERFLOW);
+    }
+}
+
+void scan_ints(const int *in, int n, int *out, long long capacity, long long *total, int *err,
+               const int *gate, cudaStream_t st) {
+    k_scan<<<1, 1024, 0, st>>>(in, n, out, capacity, total, err, gate);
+}
+
+void nbr_cells(const NbrWork &w, float r_list, cudaStream_t st) {
+    if (w.n_atoms == 0) return;
+    k_grid_open<<<w.n_rep, 256, 0, st>>>(w, r_list);
+    cudaMemsetAsync(w.cell_cnt, 0, sizeof(int) * w.n_cells, st);
+    const int nb = (w.n_atoms + 255) / 256;
+    k_cell_assign<<<nb, 256, 0, st>>>(w);
+    scan_ints(w.cell_cnt, w.n_cells, w.cell_start, -1, nullptr, w.err, w.gate, st);
+    k_cell_scatter<<<nb, 256, 0, st>>>(w);
+}
+
+void nbr_fill(const NbrWork &w, float r_list, int *row_ptr, int *col, long long capacity, float *x_ref,
+              cudaStream_t st) {
+    if (w.n_atoms == 0) return;
+    const int nb = (w.n_atoms + 127) / 128;
+    k_nbr_count<<<nb, 128, 0, st>>>(w, r_list * r_list);
+    scan_ints(w.counts, w.n_atoms, row_ptr, capacity, w.total, w.err, w.gate, st);
+    if (col) k_nbr_fill<<<nb, 128, 0, st>>>(w, r_list * r_list, row_ptr, col, x_ref);
+}
+
+// ------------------------------------------------------------- sub-lists
+__global__ void k_sub_count(NbrWork w, const int *p_row, const int *p_col, float r2cut) {
+    if (gated_off(w.gate, w.err)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= w.n_atoms) return;
+    const CellGrid g = w.grid[w.atom_rep[i]];
+    const float ibx = g.box[0] > 0.f ? 1.f / g.box[0] : 0.f, iby = g.box[1] > 0.f ? 1.f / g.box[1] : 0.f,
+                ibz = g.box[2] > 0.f ? 1.f / g.box[2] : 0.f;
+    const float xi = w.x[3 * i], yi = w.x[3 * i + 1], zi = w.x[3 * i + 2];
+    int cnt = 0;
+    for (int e = p_row[i]; e < p_row[i + 1]; ++e) {
+        const int j = p_col[e];
+        const float dx = min_img(w.x[3 * j] - xi, g.box[0], ibx);
+        const float dy = min_img(w.x[3 * j + 1] - yi, g.box[1], iby);
+        const float dz = min_img(w.x[3 * j + 2] - zi, g.box[2], ibz);
+        if (dx * dx + dy * dy + dz * dz < r2cut) ++cnt;
+    }
+    w.counts[i] = cnt;
+}
+
+__global__ void k_sub_fill(NbrWork w, const int *p_row, const int *p_col, float r2cut, const int *row_ptr,
+                           int *col) {
+    if (gated_off(w.gate, w.err)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= w.n_atoms) return;
+    const CellGrid g = w.grid[w.atom_rep[i]];
+    const float ibx = g.box[0] > 0.f ? 1.f / g.box[0] : 0.f, iby = g.box[1] > 0.f ? 1.f / g.box[1] : 0.f,
+                ibz = g.box[2] > 0.f ? 1.f / g.box[2] : 0.f;
+    const float xi = w.x[3 * i], yi = w.x[3 * i + 1], zi = w.x[3 * i + 2];
+    int p = row_ptr[i];
+    for (int e = p_row[i]; e < p_row[i + 1]; ++e) {
+        const int j = p_col[e];
+        const float dx = min_img(w.x[3 * j] - xi, g.box[0], ibx);
+        const float dy = min_img(w.x[3 * j + 1] - yi, g.box[1], iby);
+        const float dz = min_img(w.x[3 * j + 2] - zi, g.box[2], ibz);
+        if (dx * dx + dy * dy + dz * dz < r2cut) col[p++] = j;
+    }
+}
+
+void nbr_sublist(const NbrWork &w, const int *p_row, const int *p_col, float r, int *row_ptr, int *col,
+                 long long capacity, cudaStream_t st) {
+    if (w.n_atoms == 0) return;
+    const int nb = (w.n_atoms + 127) / 128;
+    k_sub_count<<<nb, 128, 0, st>>>(w, p_row, p_col, r * r);
+    scan_ints(w.counts, w.n_atoms, row_ptr, capacity, w.total, w.err, w.gate, st);
+    k_sub_fill<<<nb, 128, 0, st>>>(w, p_row, p_col, r * r, row_ptr, col);
+}
+
+}  // namespace dmts

@@ -9,8 +9,8 @@ density and size are generated here:
 
 * water boxes: rigid waters (O-H 0.9572 A, H-O-H 104.52 deg) on a cubic
   lattice, random orientation, N(0, 0.05 A) jitter on every coordinate;
-* a solvated bead chain of protein size (C/N/O/H/S 32/9/10/48/1 %) on a
-  self-avoiding lattice walk with 1.5 A bonds, in water at about 1 g/cm^3;
+* a solvated bead chain of protein size (C/N/O/H/S 32/9/10/48/1 %) on an
+  excluded-volume walk with 1.5 A bonds, in water at about 1 g/cm^3;
 * small molecules (heavy chain + hydrogen caps) in a water droplet with open
   boundaries, for the replica-serving workload.
 
@@ -95,12 +95,26 @@ def _water_template() -> np.ndarray:
                      [-WATER_OH * math.sin(t), 0.0, WATER_OH * math.cos(t)]])
 
 
-def _place_waters(rng, sites, first_mol, first_atom):
-    """Rigid, randomly oriented waters with O on `sites`; returns arrays."""
+def _place_waters(rng, sites, first_mol, first_atom, obstacles=None, box=None, h_min=1.8):
+    """Rigid, randomly oriented waters with O on `sites`; returns arrays. With
+    `obstacles`, orientations putting an H closer than h_min to an obstacle are
+    re-drawn (up to 50 times)."""
     n = sites.shape[0]
     R = _random_rotations(rng, n)
     tmpl = _water_template()
-    x = (sites[:, None, :] + np.einsum("nab,kb->nka", R, tmpl)).reshape(-1, 3)
+    xw = sites[:, None, :] + np.einsum("nab,kb->nka", R, tmpl)
+    if obstacles is not None and n > 0:
+        from scipy.spatial import cKDTree
+        tree = cKDTree(np.mod(obstacles, box), boxsize=box) if box is not None else cKDTree(obstacles)
+        wrap = (lambda p: np.mod(p, box)) if box is not None else (lambda p: p)
+        for _try in range(50):
+            dh, _ = tree.query(wrap(xw[:, 1:, :].reshape(-1, 3)), k=1)
+            bad = np.nonzero((dh.reshape(n, 2) < h_min).any(1))[0]
+            if bad.size == 0:
+                break
+            Rb = _random_rotations(rng, bad.size)
+            xw[bad] = sites[bad][:, None, :] + np.einsum("nab,kb->nka", Rb, tmpl)
+    x = xw.reshape(-1, 3)
     species = np.tile(np.array([SP_O, SP_H, SP_H], np.uint8), n)
     mol = np.repeat(np.arange(first_mol, first_mol + n, dtype=np.int32), 3)
     o = first_atom + 3 * np.arange(n, dtype=np.int32)
@@ -130,34 +144,50 @@ def water_box(n_mol: int, box_len: float, seed: int, n_lone_o: int = 0,
     return System(name, _f32(x), sp, mol, bonds, r0, np.full(3, float(box_len)))
 
 
-def _saw(rng, n_steps: int, extent: int, max_tries: int = 10000) -> np.ndarray:
-    """Self-avoiding walk of n_steps sites on the lattice [0, extent)^3,
-    restarted on a dead end."""
-    moves = np.array([[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]])
-    for _ in range(max_tries):
-        start = np.array([extent // 2] * 3)
-        path = [tuple(start)]
-        seen = {path[0]}
-        cur = start
-        ok = True
-        for _s in range(n_steps - 1):
-            cand = []
-            for mv in moves:
-                p = cur + mv
-                if np.any(p < 0) or np.any(p >= extent):
+def _excluded_volume_walk(rng, n: int, bond: float, box=None, d_min: float = 2.5,
+                          angle_deg: float = 109.47, max_backtracks: int = 20000) -> np.ndarray:
+    """Chain of n beads in continuous space: bond length `bond`, bond angle
+    `angle_deg`, seeded uniform dihedrals; beads three or more apart along the
+    chain stay at least d_min apart (minimum image when `box` is given).
+    Dead ends are resolved by seeded backtracking."""
+    def mi(d):
+        return d - box * np.rint(d / box) if box is not None else d
+    pos = np.zeros((n, 3))
+    centre = box / 2.0 if box is not None else np.zeros(3)
+    pos[0] = centre
+    u = rng.normal(size=3)
+    pos[1] = pos[0] + bond * u / np.linalg.norm(u)
+    k, backtracks = 2, 0
+    theta = math.radians(angle_deg)
+    while k < n:
+        b1 = pos[k - 1] - pos[k - 2]
+        b1 /= np.linalg.norm(b1)
+        ref = pos[k - 2] - pos[k - 3] if k >= 3 else rng.normal(size=3)
+        e2 = ref - (ref @ b1) * b1
+        if np.linalg.norm(e2) < 1e-8:
+            e2 = np.cross(b1, [1.0, 0.0, 0.0]) if abs(b1[0]) < 0.9 else np.cross(b1, [0.0, 1.0, 0.0])
+        e2 /= np.linalg.norm(e2)
+        e3 = np.cross(b1, e2)
+        placed = False
+        for _try in range(24):
+            phi = rng.uniform(0, 2 * np.pi)
+            d = -math.cos(theta) * b1 + math.sin(theta) * (math.cos(phi) * e2 + math.sin(phi) * e3)
+            cand = pos[k - 1] + bond * d
+            if k >= 3:
+                dd = np.linalg.norm(mi(pos[: k - 2] - cand), axis=1)
+                if dd.min() < d_min:
                     continue
-                if tuple(p) in seen:
-                    continue
-                cand.append(p)
-            if not cand:
-                ok = False
-                break
-            cur = cand[rng.integers(len(cand))]
-            path.append(tuple(cur))
-            seen.add(path[-1])
-        if ok:
-            return np.array(path, dtype=np.float64)
-    raise RuntimeError("self-avoiding walk failed")
+            pos[k] = cand
+            placed = True
+            break
+        if placed:
+            k += 1
+        else:
+            backtracks += 1
+            if backtracks > max_backtracks:
+                raise RuntimeError("excluded-volume walk failed")
+            k = max(2, k - int(rng.integers(1, 6)))
+    return pos
 
 
 def _largest_remainder(total: int, percents) -> list:
@@ -186,16 +216,17 @@ def solvated_chain(n_chain: int = 2489, n_water: int = 7023, box_len: float = 62
                    seed: int = 301, jitter: float = 0.05,
                    composition=(("C", 32), ("N", 9), ("O", 10), ("H", 48), ("S", 1)),
                    name: str = "solvated_chain") -> System:
-    """A bonded bead chain (seeded self-avoiding lattice walk, 1.5 A bonds,
-    species by largest-remainder rounding of `composition`, placed by a seeded
-    shuffle) in a periodic water box. Water O sites closer than 2.5 A to a
-    bead are rejected; the lattice is the smallest n^3 that leaves enough
-    sites; the first `n_water` sites of a seeded permutation are used."""
+    """A bonded bead chain (seeded excluded-volume walk: 1.5 A bonds,
+    tetrahedral bond angle, random dihedrals, beads three or more apart at
+    least 2.5 A apart; species by largest-remainder rounding of
+    `composition`, placed by a seeded shuffle) in a periodic water box. Water
+    O sites closer than 2.5 A to a bead are rejected; the lattice is the
+    smallest n^3 that leaves enough sites; the first `n_water` sites of a
+    seeded permutation are used; water hydrogens are kept 1.8 A from beads by
+    re-drawing the orientation."""
     rng = np.random.default_rng(seed)
-    extent = int(math.floor((box_len - 2.0) / CHAIN_BOND))
-    walk = _saw(rng, n_chain, extent)
-    off = (box_len - (extent - 1) * CHAIN_BOND) / 2.0
-    xc = walk * CHAIN_BOND + off
+    box = np.full(3, float(box_len))
+    xc = _excluded_volume_walk(rng, n_chain, CHAIN_BOND, box=box)
     counts = _largest_remainder(n_chain, [p for _, p in composition])
     codes = []
     for (sym, _), cnt in zip(composition, counts):
@@ -203,7 +234,6 @@ def solvated_chain(n_chain: int = 2489, n_water: int = 7023, box_len: float = 62
     sp_c = np.array(codes, np.uint8)[rng.permutation(n_chain)]
     bonds_c = np.stack([np.arange(n_chain - 1), np.arange(1, n_chain)], 1).astype(np.int32)
     r0_c = np.full(n_chain - 1, CHAIN_BOND)
-    box = np.full(3, float(box_len))
     n = int(math.ceil(n_water ** (1.0 / 3.0)))
     while True:
         g = (np.arange(n) + 0.5) * (box_len / n)
@@ -214,7 +244,7 @@ def solvated_chain(n_chain: int = 2489, n_water: int = 7023, box_len: float = 62
         n += 1
     acc = grid[ok]
     sites = acc[rng.permutation(acc.shape[0])[:n_water]]
-    xw, spw, molw, bw, r0w = _place_waters(rng, sites, 1, n_chain)
+    xw, spw, molw, bw, r0w = _place_waters(rng, sites, 1, n_chain, obstacles=xc, box=box)
     x = np.concatenate([xc, xw], 0)
     x = x + rng.normal(0.0, jitter, size=x.shape)
     sp = np.concatenate([sp_c, spw])
@@ -228,7 +258,8 @@ def capped_molecule_in_droplet(n_solute: int, seed: int, jitter: float = 0.05,
                                name: str = "droplet") -> System:
     """Small molecule of exactly `n_solute` atoms (heavy self-avoiding chain,
     species drawn 32:9:10:1 from C:N:O:S, hydrogen caps up to valence as far
-    as the count allows) surrounded by `n_solute` waters (3x its atom count
+    as the count allows, each cap placed 1.6 A or more from other atoms when
+    possible) surrounded by `n_solute` waters (3x its atom count
     in water atoms) packed around it at about 1 g/cm^3; open boundary."""
     rng = np.random.default_rng(seed)
     heavy_p = np.array([32, 9, 10, 1], np.float64)
@@ -245,8 +276,8 @@ def capped_molecule_in_droplet(n_solute: int, seed: int, jitter: float = 0.05,
     while n_heavy + n_caps(sp_heavy) < n_solute:
         sp_heavy.append(int(rng.choice(heavy_codes, p=heavy_p / heavy_p.sum())))
         n_heavy += 1
-    walk = _saw(rng, n_heavy, 4 * n_heavy + 8)
-    xh = (walk - walk.mean(0)) * CHAIN_BOND
+    walk = _excluded_volume_walk(rng, n_heavy, CHAIN_BOND) if n_heavy > 1 else np.zeros((1, 3))
+    xh = walk - walk.mean(0)
     xs, sps, bonds, r0 = [*xh], [*sp_heavy], [], []
     for k in range(n_heavy - 1):
         bonds.append((k, k + 1))
@@ -257,9 +288,22 @@ def capped_molecule_in_droplet(n_solute: int, seed: int, jitter: float = 0.05,
         for _c in range(max(VALENCE[s] - nb, 0)):
             if budget == 0:
                 break
-            u = rng.normal(size=3)
-            u /= np.linalg.norm(u)
-            xs.append(xh[k] + CAP_BOND * u)
+            # cap direction: best of up to 200 seeded draws (first one that
+            # keeps the cap 1.6 A from every other atom placed so far)
+            placed = np.array(xs)
+            best, best_d = None, -1.0
+            for _try in range(200):
+                u = rng.normal(size=3)
+                u /= np.linalg.norm(u)
+                c_ = xh[k] + CAP_BOND * u
+                d = np.linalg.norm(placed - c_, axis=1)
+                d[k] = 9.0
+                if d.min() > best_d:
+                    best, best_d = c_, d.min()
+                if d.min() >= 1.6:
+                    break
+            cand = best
+            xs.append(cand)
             sps.append(SP_H)
             bonds.append((k, len(xs) - 1))
             r0.append(CAP_BOND)
@@ -280,7 +324,7 @@ def capped_molecule_in_droplet(n_solute: int, seed: int, jitter: float = 0.05,
         rad += spacing
     acc = grid[ok]
     acc = acc[np.argsort(np.linalg.norm(acc, axis=1), kind="stable")][:n_w]
-    xw, spw, molw, bw, r0w = _place_waters(rng, acc, 1, n_solute)
+    xw, spw, molw, bw, r0w = _place_waters(rng, acc, 1, n_solute, obstacles=xs)
     x = np.concatenate([xs, xw], 0)
     x = x + rng.normal(0.0, jitter, size=x.shape)
     sp = np.concatenate([sps, spw])

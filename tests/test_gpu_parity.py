@@ -1,0 +1,323 @@
+"""GPU parity of the CUDA path against the FP64 oracle, through the C ABI.
+
+Neighbour sets and Philox words bit-exact; FP32 forces and energies within
+1e-5 relative max-abs; positions within 1e-4 A after 10 outer steps.
+"""
+import ctypes as ct
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O
+from paper_2602_14975_gb300 import core
+from paper_2602_14975_gb300 import synth as S
+from tests.helpers import TOL_F32, TOL_POS, band_pairs, pair_set, rel_maxabs, with_x
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def water():
+    return S.water_192()
+
+
+@pytest.fixture(scope="module")
+def models1():
+    cs = S.cons_spec(2, 64, 1)
+    ns = S.nc_spec(32, rc=3.5)
+    return (cs, S.cons_weights(cs, 102)), (ns, S.nc_weights(ns, 102))
+
+
+@pytest.fixture(scope="module")
+def ctx1(models1):
+    return core.Context(cons=models1[0], nc=models1[1])
+
+
+# ------------------------------------------------------------- neighbours --
+
+def _check_pairs(sys_list, nb, rcut):
+    got = pair_set(nb.row_ptr.cpu().numpy(), nb.col.cpu().numpy())
+    off = 0
+    ref = set()
+    band = set()
+    for sy in sys_list:
+        rp, col = O.nbr_brute(sy.x, sy.box, rcut)
+        pr = pair_set(rp, col, off)
+        ref |= pr
+        local = {(i - off, j - off) for (i, j) in pr}
+        band |= {(i + off, j + off) for (i, j) in band_pairs(sy, local, rcut)}
+        off += sy.n_atoms
+    diff = got ^ ref
+    assert diff <= band, f"{len(diff - band)} pairs differ outside the cutoff band"
+    # each row sorted ascending (canonical order)
+    rp = nb.row_ptr.cpu().numpy()
+    col = nb.col.cpu().numpy()
+    for i in range(len(rp) - 1):
+        row = col[rp[i]:rp[i + 1]]
+        assert np.all(np.diff(row) > 0)
+
+
+@pytest.mark.parametrize("rcut", [3.5, 4.5, 5.5])
+def test_nbr_periodic_vs_brute_force(ctx1, water, rcut):
+    d = core.DeviceSystem(water)
+    nb = core.nbr_build(ctx1, d, rcut)
+    _check_pairs([water], nb, rcut)
+
+
+def test_nbr_batched_open_and_ragged(ctx1):
+    systems = [S.capped_molecule_in_droplet(n, seed=40 + n) for n in (20, 37, 150, 23)]
+    d = core.DeviceSystem(systems)
+    nb = core.nbr_build(ctx1, d, 5.5)
+    _check_pairs(systems, nb, 5.5)
+
+
+def test_nbr_large_periodic_and_overflow_retry(ctx1):
+    sy = S.water_12288()
+    d = core.DeviceSystem(sy)
+    nb = core.nbr_build(ctx1, d, 5.5, capacity=1000)   # overflow -> grow -> retry
+    rp = nb.row_ptr.cpu().numpy()
+    col = nb.col.cpu().numpy()
+    rng = np.random.default_rng(0)
+    for i in rng.choice(sy.n_atoms, 60, replace=False):
+        dd = sy.x - sy.x[i]
+        dd -= sy.box * np.rint(dd / sy.box)
+        r2 = (dd ** 2).sum(1)
+        ref = set(np.nonzero(r2 < 5.5 ** 2)[0]) - {i}
+        got = set(col[rp[i]:rp[i + 1]].tolist())
+        amb = set(np.nonzero(np.abs(r2 - 5.5 ** 2) < 1e-4)[0])
+        assert (ref ^ got) <= amb
+
+
+def test_nbr_empty_replica_and_single_atom(ctx1):
+    lone = S.System("lone", np.zeros((1, 3)), np.array([3], np.uint8), np.zeros(1, np.int32),
+                    np.zeros((0, 2), np.int32), np.zeros(0), np.zeros(3))
+    d = core.DeviceSystem([lone, S.capped_molecule_in_droplet(20, seed=3)])
+    nb = core.nbr_build(ctx1, d, 5.5)
+    rp = nb.row_ptr.cpu().numpy()
+    assert rp[1] - rp[0] == 0
+
+
+# ------------------------------------------------------------ conservative --
+
+def _gpu_cons(ctx, systems, rlist=5.5, with_prior=True):
+    d = core.DeviceSystem(systems)
+    nb = core.nbr_build(ctx, d, rlist)
+    E, F = core.energy_forces_cons(ctx, d, nb, with_prior=with_prior)
+    torch.cuda.synchronize()
+    return E.cpu().numpy(), F.cpu().numpy()
+
+
+def test_cons_energy_forces_fp32(ctx1, models1, water):
+    (cs, cb), _ = models1
+    E, F = _gpu_cons(ctx1, [water], with_prior=False)
+    Eo, Fo = O.cons_energy_forces(water, cs, cb)
+    assert abs(E[0] - Eo) <= TOL_F32 * abs(Eo)
+    assert rel_maxabs(F, Fo) <= TOL_F32
+    # with the prior
+    E2, F2 = _gpu_cons(ctx1, [water], with_prior=True)
+    Ep, Fp = O.prior(water)
+    assert abs(E2[0] - (Eo + Ep)) <= TOL_F32 * abs(Eo + Ep)
+    assert rel_maxabs(F2, Fo + Fp) <= TOL_F32
+
+
+def test_cons_open_boundary_batch_equals_alone(ctx1, models1):
+    (cs, cb), _ = models1
+    systems = [S.capped_molecule_in_droplet(n, seed=90 + n) for n in (20, 61, 33)]
+    E, F = _gpu_cons(ctx1, systems)
+    off = 0
+    for k, sy in enumerate(systems):
+        Ea, Fa = _gpu_cons(ctx1, [sy])
+        n = sy.n_atoms
+        assert Ea[0] == E[k]                          # bit-exact: replicas share nothing
+        assert np.array_equal(Fa, F[off:off + n])
+        Eo, Fo = O.cons_energy_forces(sy, cs, cb)
+        Ep, Fp = O.prior(sy)
+        assert abs(E[k] - (Eo + Ep)) <= TOL_F32 * max(abs(Eo + Ep), 1.0)
+        assert rel_maxabs(F[off:off + n], Fo + Fp) <= TOL_F32
+        off += n
+
+
+def test_cons_large_lmax2_c128(water):
+    cs = S.cons_spec(3, 128, 2)
+    cb = S.cons_weights(cs, 302)
+    ctx = core.Context(cons=(cs, cb))
+    E, F = _gpu_cons(ctx, [water], with_prior=False)
+    Eo, Fo = O.cons_energy_forces(water, cs, cb)
+    assert abs(E[0] - Eo) <= TOL_F32 * abs(Eo)
+    assert rel_maxabs(F, Fo) <= TOL_F32
+
+
+def test_cons_autograd_function(ctx1, models1, water):
+    (cs, cb), _ = models1
+    d = core.DeviceSystem(water)
+    nb = core.nbr_build(ctx1, d, 5.5)
+    x = d.x.clone().requires_grad_(True)
+    E = core.ConsEnergy.apply(x, ctx1, d, nb, False)
+    E.sum().backward()
+    g = x.grad.cpu().numpy()
+    _, Fo = O.cons_energy_forces(water, cs, cb)
+    assert rel_maxabs(-g, Fo) <= TOL_F32
+
+
+# ---------------------------------------------------------------- NC model --
+
+def test_nc_forces_fp32(ctx1, models1, water):
+    _, (ns, nb_) = models1
+    d = core.DeviceSystem(water)
+    nb = core.nbr_build(ctx1, d, 4.0)
+    for with_bonds in (False, True):
+        F, net = core.forces_nc(ctx1, d, nb, with_bonds=with_bonds)
+        F = F.cpu().numpy()
+        Fo, neto = O.nc_forces(water, ns, nb_, with_bonds=with_bonds)
+        assert rel_maxabs(F, Fo) <= TOL_F32
+        assert np.abs(F.astype(np.float64).sum(0)).max() <= 1e-5 * np.abs(Fo).max()
+        # antisymmetric sum: the pre-subtraction net force is only rounding
+        assert np.abs(net.cpu().numpy()).max() <= 1e-4 * np.abs(Fo).max()
+
+
+def test_nc_open_boundary_batch(ctx1, models1):
+    _, (ns, nb_) = models1
+    systems = [S.capped_molecule_in_droplet(n, seed=70 + n) for n in (20, 45)]
+    d = core.DeviceSystem(systems)
+    nb = core.nbr_build(ctx1, d, 4.0)
+    F, _ = core.forces_nc(ctx1, d, nb)
+    F = F.cpu().numpy()
+    off = 0
+    for sy in systems:
+        Fo, _ = O.nc_forces(sy, ns, nb_)
+        assert rel_maxabs(F[off:off + sy.n_atoms], Fo) <= TOL_F32
+        off += sy.n_atoms
+
+
+# ------------------------------------------------------------------ Philox --
+
+def test_philox_words_bit_exact(ctx1):
+    seed, rep, step = 0x0123456789ABCDEF, 5, (3 << 32) + 17
+    w = core.philox_words(ctx1, seed, rep, step, 100, 64).cpu().numpy().view(np.uint32).reshape(-1, 4)
+    for i in range(64):
+        assert list(w[i]) == list(O.noise_words(seed, rep, step, 100 + i))
+
+
+def test_philox_vs_curand(ctx1, tmp_path):
+    so = tmp_path / "libcurandprobe.so"
+    subprocess.check_call(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-shared",
+                           "-Xcompiler", "-fPIC", "-o", str(so), os.path.join(HERE, "probes", "curand_philox.cu")])
+    lib = ct.CDLL(str(so))
+    lib.curand_words.argtypes = [ct.c_uint64, ct.c_uint32, ct.c_uint64, ct.c_uint32, ct.c_int, ct.c_void_p]
+    ref = np.zeros(4 * 256, np.uint32)
+    seed, rep, step = 987654321987, 3, 42
+    assert lib.curand_words(seed, rep, step, 0, 256, ref.ctypes.data) == 0
+    w = core.philox_words(ctx1, seed, rep, step, 0, 256).cpu().numpy().view(np.uint32)
+    assert np.array_equal(w, ref)
+
+
+def test_gaussians_match_oracle(ctx1):
+    g = core.gaussians(ctx1, 103, 0, 7, 0, 500).cpu().numpy().reshape(-1, 3)
+    ref = np.array([O.gauss3(103, 0, 7, i) for i in range(500)])
+    assert np.abs(g - ref).max() <= 1e-5 * max(1.0, np.abs(ref).max())
+
+
+# --------------------------------------------------------------- integrator --
+
+def _md_setup(water, hmr=0.0):
+    m = water.element_masses()
+    if hmr:
+        m = O.hmr_masses(water.species, water.mol_id, m, hmr)
+    v = S.maxwell_boltzmann(m, 300.0, 103)
+    return m, v
+
+
+@pytest.mark.parametrize("gamma", [1.0, 0.0])
+def test_respa_positions_after_10_outer_steps(ctx1, models1, water, gamma):
+    (cs, cb), (ns, nb_) = models1
+    m, v = _md_setup(water)
+    d = core.DeviceSystem(water)
+    st = core.MDState(d, v, m.astype(np.float32), seeds=103)
+    integ = core.integrator(4.0, 4, 300.0, [gamma] * 5, skin=0.5)
+    core.respa_step(ctx1, st, integ, 10)
+    ctx1.sync()
+    xg = d.x.cpu().numpy()
+    ref = O.MDState(water, v, m.astype(np.float32).astype(np.float64))
+    O.respa_run(ref, water, cs, cb, ns, nb_, 4.0, 4, 300.0, np.full(5, gamma), 103, 10)
+    assert np.abs(xg - ref.x).max() <= TOL_POS
+    assert int(st.step.cpu().numpy()[0]) == 40
+    st.release()
+
+
+def test_respa_split_calls_equal_single_call(ctx1, water):
+    m, v = _md_setup(water)
+    out = []
+    for split in ((6,), (2, 3, 1)):
+        d = core.DeviceSystem(water)
+        st = core.MDState(d, v, m.astype(np.float32), seeds=7)
+        integ = core.integrator(4.0, 4, 300.0, [1.0] * 5, skin=0.5)
+        for k in split:
+            core.respa_step(ctx1, st, integ, k)
+        ctx1.sync()
+        out.append((d.x.cpu().numpy(), st.v.cpu().numpy()))
+        st.release()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+
+
+def test_sts_positions_after_10_steps(ctx1, models1, water):
+    (cs, cb), _ = models1
+    m, v = _md_setup(water)
+    d = core.DeviceSystem(water)
+    st = core.MDState(d, v, m.astype(np.float32), seeds=11)
+    integ = core.integrator(1.0, 1, 300.0, [1.0] * 5, mode=1, skin=0.5)
+    core.respa_step(ctx1, st, integ, 10)
+    ctx1.sync()
+    ref = O.MDState(water, v, m.astype(np.float32).astype(np.float64))
+    O.sts_run(ref, water, cs, cb, 1.0, 300.0, np.ones(5), 11, 10)
+    assert np.abs(d.x.cpu().numpy() - ref.x).max() <= TOL_POS
+    st.release()
+
+
+def test_respa_hmr_hhf_replicas_batch(ctx1, models1):
+    (cs, cb), (ns, nb_) = models1
+    systems = [S.capped_molecule_in_droplet(n, seed=20 + n) for n in (20, 30)]
+    ms, vs = [], []
+    for sy in systems:
+        m = O.hmr_masses(sy.species, sy.mol_id, sy.element_masses(), 3.0)
+        ms.append(m)
+        vs.append(S.maxwell_boltzmann(m, 300.0, 5))
+    d = core.DeviceSystem(systems)
+    st = core.MDState(d, np.concatenate(vs), np.concatenate(ms).astype(np.float32), seeds=[11, 12],
+                      replica_ids=[4, 9])
+    gam = (20.0, 1.0, 1.0, 1.0, 1.0)
+    integ = core.integrator(10.0, 5, 300.0, gam, skin=0.5)
+    core.respa_step(ctx1, st, integ, 10)
+    ctx1.sync()
+    xg = d.x.cpu().numpy()
+    off = 0
+    for k, sy in enumerate(systems):
+        ref = O.MDState(sy, vs[k], ms[k].astype(np.float32).astype(np.float64))
+        O.respa_run(ref, sy, cs, cb, ns, nb_, 10.0, 5, 300.0, np.array(gam), [11, 12][k], 10,
+                    replica=[4, 9][k])
+        assert np.abs(xg[off:off + sy.n_atoms] - ref.x).max() <= TOL_POS
+        off += sy.n_atoms
+    st.release()
+
+
+def test_nonfinite_positions_are_reported(ctx1, water):
+    m, v = _md_setup(water)
+    x = water.x.copy()
+    x[5, 0] = np.nan
+    sy = with_x(water, x)
+    d = core.DeviceSystem(sy)
+    st = core.MDState(d, v, m.astype(np.float32), seeds=1)
+    integ = core.integrator(4.0, 4, 300.0, [1.0] * 5, skin=0.5)
+    from paper_2602_14975_gb300 import _lib as L
+    with pytest.raises(L.DmtsError) as ei:
+        core.respa_step(ctx1, st, integ, 2)
+        ctx1.sync()
+    assert ei.value.status in (L.E_NONFINITE, L.E_NBR_OVERFLOW, L.E_INVALID)
+    st.release()
+    ctx1.sync()   # the sticky word is cleared: the context stays usable

@@ -312,11 +312,11 @@ def test_prior_pins():
         x = np.array([[0, 0, 0], [r, 0, 0], [0, 30, 0], [1.09, 30, 0]], np.float64)
         sy = S.System("p", x, sp, np.array([0, 1, 2, 2], np.int32),
                       np.array([[2, 3]], np.int32), np.array([1.09]), np.zeros(3))
-        E, F = O.prior(sy)
+        E, F = O.prior(sy, terms=O.LJ)
         assert abs(E - expect) < 1e-12
     # bond energy zero at its rest length for the rigid water template
     w = S.water_box(8, 20.0, 3, jitter=0.0)
-    Eb, _ = O.prior(w, with_lj=False)
+    Eb, _ = O.prior(w, terms=O.BONDS)
     assert Eb < 1e-8          # float32 rounding of coordinates only
     # gradient by central differences (bonds + LJ)
     w = S.water_192()
@@ -328,6 +328,42 @@ def test_prior_pins():
             xm = w.x.copy(); xm[i, a] -= h
             fd = -(O.prior(_copy_sys(w, xp))[0] - O.prior(_copy_sys(w, xm))[0]) / (2 * h)
             assert abs(F[i, a] - fd) < 1e-6 * max(1.0, abs(fd))
+
+
+def test_screened_repulsion_pins():
+    # ZBL universal screening: phi(0) = 1 (coefficients sum to one), so the
+    # pair energy tends to the bare Coulomb repulsion k_e Z_i Z_j / r as r -> 0
+    assert abs(O.zbl_phi(0.0) - 1.0) < 1e-12
+    assert O.zbl_phi(5.0) < O.zbl_phi(1.0) < O.zbl_phi(0.5)
+    Z = [1, 6, 7, 8, 16]
+    for si, sj in ((0, 0), (3, 3), (1, 4)):
+        r = 1e-5
+        e, _ = O.rep_pair(si, sj, r)
+        assert abs(e * r / (332.0637133 * Z[si] * Z[sj]) - 1.0) < 1e-3
+        # vanishes with zero slope at the switch radius
+        rc = O.PRIOR[5]
+        assert O.rep_pair(si, sj, rc)[0] == 0.0
+        assert abs(O.rep_pair(si, sj, rc - 1e-4)[1]) < 1e-5
+        # dE/dr by central differences
+        for r in (0.7, 1.6, 2.9):
+            fd = (O.rep_pair(si, sj, r + 1e-6)[0] - O.rep_pair(si, sj, r - 1e-6)[0]) / 2e-6
+            assert abs(O.rep_pair(si, sj, r)[1] - fd) < 1e-6 * max(1.0, abs(fd))
+    # screening length a = 0.8854 a_0 / (Z_i^0.23 + Z_j^0.23): E(r) Z-scaling
+    r = 0.8
+    a_hh = 0.8854 * 0.529177210903 / 2.0
+    assert abs(O.rep_pair(0, 0, r)[0] / O.envelope(r / O.PRIOR[5], O.PRIOR[6])
+               - 332.0637133 / r * O.zbl_phi(r / a_hh)) < 1e-9
+    # a bonded pair feels only its bond
+    x = np.array([[0, 0, 0], [1.2, 0, 0]], float)
+    sy = S.System("b", x, np.array([3, 0], np.uint8), np.zeros(2, np.int32),
+                  np.array([[0, 1]], np.int32), np.array([0.9572]), np.zeros(3))
+    E, _ = O.prior(sy)
+    assert abs(E - 0.5 * 450.0 * (1.2 - 0.9572) ** 2) < 1e-10
+    # an unbonded pair feels the repulsion
+    sy.bonds = np.zeros((0, 2), np.int32)
+    sy.bond_r0 = np.zeros(0)
+    E, _ = O.prior(sy)
+    assert abs(E - O.rep_pair(3, 0, 1.2)[0]) < 1e-10
 
 
 # ---------------------------------------------------------------- NC model --
@@ -503,7 +539,7 @@ def test_nve_energy_drift_bounded():
     st = O.MDState(sy, v, m)
     conv = 4.184e-4
     def etot():
-        eb, _ = O.prior(_copy_sys(sy, st.x), with_lj=False)
+        eb, _ = O.prior(_copy_sys(sy, st.x), terms=O.BONDS)
         return eb + 0.5 * (m[:, None] * st.v ** 2).sum() / conv
     e0 = etot()
     errs = []
