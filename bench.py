@@ -1,0 +1,361 @@
+"""Benchmark of the DMTS-NC hot path on one GB300 (or N, one replica each).
+
+One step = one outer step of Algorithm 1 (one conservative evaluation with
+its adjoint forces, n = 5 NC evaluations, the fused integrator, neighbour
+rebuilds) on the 23,558-atom solvated bead chain in water. The same GPU also
+runs single-time-step BAOAB (1 fs, no HMR) for the ns/day ratio.
+
+Prints one JSON line (rank 0). `--impl reference` times the FP64 CPU oracle
+instead, on a bounded cut-out of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = "solvated_chain_23558"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    return ap.parse_args()
+
+
+def ns_per_day(fs_per_step, steps_per_s):
+    return fs_per_step * steps_per_s * 86400.0 / 1e6
+
+
+# ----------------------------------------------------------------- clocks --
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, flags in rows for k, f in enumerate(flags) if f == "Active"})
+        return {"sm_mhz": float(np.median([r[0] for r in rows])), "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "reasons": reasons}
+
+
+# ------------------------------------------------------------- CPU oracle --
+def cutout(sy, frac_edge):
+    """Atoms of whole molecules whose first atom lies in [0, frac_edge*L)^3
+    (wrapped); bonds re-indexed; same box."""
+    from paper_2602_14975_gb300 import synth as S
+    xw = np.mod(sy.x, sy.box)
+    lim = frac_edge * sy.box
+    keep_mol = set()
+    seen = set()
+    for i in range(sy.n_atoms):
+        m = int(sy.mol_id[i])
+        if m in seen:
+            continue
+        seen.add(m)
+        if np.all(xw[i] < lim):
+            keep_mol.add(m)
+    keep = np.array([int(sy.mol_id[i]) in keep_mol for i in range(sy.n_atoms)])
+    if sy.mol_id[0] == 0 and 0 not in keep_mol:
+        # the chain is one molecule: keep its beads inside the cut-out region
+        keep |= (sy.mol_id == 0) & np.all(xw < lim, axis=1)
+    idx = np.nonzero(keep)[0]
+    remap = -np.ones(sy.n_atoms, np.int64)
+    remap[idx] = np.arange(idx.size)
+    b = sy.bonds
+    bm = keep[b[:, 0]] & keep[b[:, 1]]
+    return S.System(sy.name + "_cutout", sy.x[idx], sy.species[idx], sy.mol_id[idx],
+                    remap[b[bm]].astype(np.int32), sy.bond_r0[bm], sy.box)
+
+
+def oracle_outer_step_seconds(sy, W, frac_edge):
+    """Times the oracle's force evaluations of one DMTS-NC outer step (one
+    conservative energy+forces, n NC evaluations) on a cut-out; returns
+    (seconds per outer step scaled to the full system, sample description)."""
+    import oracle as O
+    from paper_2602_14975_gb300 import synth as S
+    sub = cutout(sy, frac_edge)
+    cs, ns = W["cons"](), W["nc"]()
+    cb, nb = S.cons_weights(cs, W["w_seed"]), S.nc_weights(ns, W["w_seed"])
+    n_in = W["dmts"].n_inner
+    t0 = time.perf_counter()
+    O.cons_energy_forces(sub, cs, cb)
+    O.prior(sub)
+    t1 = time.perf_counter()
+    O.nc_forces(sub, ns, nb)
+    t2 = time.perf_counter()
+    per_outer = (t1 - t0) + n_in * (t2 - t1)
+    scale = sy.n_atoms / sub.n_atoms
+    desc = (f"oracle (FP64 C, 1 thread): 1 conservative E+F + 1 NC evaluation timed on a "
+            f"{sub.n_atoms}-atom cut-out ({frac_edge:.3f} of the box edge) of {sy.name}; "
+            f"outer step = t_cons + {n_in} t_nc, scaled x{scale:.2f} to {sy.n_atoms} atoms")
+    return per_outer * scale, desc
+
+
+# ------------------------------------------------------------------ main --
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2602_14975_gb300 import synth as S
+    W = S.WORKLOADS[args.workload]
+    I = W["dmts"]
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        sy = W["system"]()
+        # size the per-step cut-out so that warm-up + timed steps take about
+        # two minutes (cost grows linearly with the cut-out's atom count)
+        t_cal, _ = oracle_outer_step_seconds(sy, W, 0.25)
+        n_cal = cutout(sy, 0.25).n_atoms
+        t_cal_sample = t_cal * n_cal / sy.n_atoms
+        budget = 120.0 / max(1, args.steps + args.warmup)
+        frac = min(1.0 / 3.0, 0.25 * (budget / max(t_cal_sample, 1e-3)) ** (1.0 / 3.0))
+        for _ in range(args.warmup):
+            oracle_outer_step_seconds(sy, W, frac)
+        t0 = time.perf_counter()
+        per = []
+        for _ in range(args.steps):
+            s, desc = oracle_outer_step_seconds(sy, W, frac)
+            per.append(s)
+        wall = time.perf_counter() - t0
+        t_outer = float(np.mean(per))
+        val = ns_per_day(I.dt_outer, 1.0 / t_outer)
+        line = {"impl": "reference", "metric": "ns/day (DMTS-NC)", "value": val, "unit": "ns/day",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": t_outer * 1e3, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": sy.name, "n_atoms": sy.n_atoms},
+                "cpu_baseline": {"value": val, "unit": "ns/day", "cores": 1, "kind": "oracle", "sample": desc},
+                "e2e": {"value": val, "unit": "ns/day", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                "wall_s": wall}
+        print(json.dumps(line), flush=True)
+        return 0
+
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    from paper_2602_14975_gb300 import core
+
+    sy = W["system"]()
+    cs, ns = W["cons"](), W["nc"]()
+    cs.bf16 = ns.bf16 = False          # this build runs the MLP contractions in fp32
+    cb, nb = S.cons_weights(cs, W["w_seed"]), S.nc_weights(ns, W["w_seed"])
+    ctx = core.Context(cons=(cs, cb), nc=(ns, nb), device=local)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # algorithmic work of the dominant kernels (active edges within the cutoffs)
+    d0 = core.DeviceSystem(sy)
+    e_cons = core.nbr_build(ctx, d0, cs.rc).n_pairs
+    e_nc = core.nbr_build(ctx, d0, ns.rc).n_pairs
+    del d0
+
+    # ---------------------------------------------------------- DMTS-NC
+    m_hmr = core.masses_hmr(sy.species, sy.mol_id, sy.element_masses(), I.hmr_delta)
+    v0 = S.maxwell_boltzmann(m_hmr, I.temperature, W["rng_seed"])
+    dsys = core.DeviceSystem(sy)
+    st = core.MDState(dsys, v0, m_hmr.astype(np.float32), seeds=I.seed, replica_ids=[rank])
+    integ = core.integrator(I.dt_outer, I.n_inner, I.temperature, I.gamma_ps, skin=0.5)
+    core.respa_step(ctx, st, integ, args.warmup)
+    ctx.sync()
+    clocks = ClockSampler(local)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    core.profile_enable(ctx, True)
+    barrier()
+    clocks.start()
+    e0.record(stream)
+    core.respa_step(ctx, st, integ, args.steps)
+    e1.record(stream)
+    barrier()
+    ck = clocks.stop()
+    ctx.sync()
+    prof = core.profile_read(ctx)
+    core.profile_enable(ctx, False)
+    ms_dmts = max_over_ranks(e0.elapsed_time(e1)) / args.steps
+    n_launches = sum(v[0] for v in prof.values())
+    st.release()
+
+    # --------------------------------------------------------------- STS
+    sts = W["sts"]
+    m_el = sy.element_masses()
+    sy2 = W["system"]()
+    d2 = core.DeviceSystem(sy2)
+    st2 = core.MDState(d2, S.maxwell_boltzmann(m_el, sts.temperature, W["rng_seed"]),
+                       m_el.astype(np.float32), seeds=sts.seed, replica_ids=[rank])
+    integ2 = core.integrator(sts.dt_outer, 1, sts.temperature, sts.gamma_ps, mode=1, skin=0.5)
+    n_sts = max(10, args.steps)
+    core.respa_step(ctx, st2, integ2, args.warmup)
+    ctx.sync()
+    barrier()
+    e0.record(stream)
+    core.respa_step(ctx, st2, integ2, n_sts)
+    e1.record(stream)
+    barrier()
+    ctx.sync()
+    ms_sts = max_over_ranks(e0.elapsed_time(e1)) / n_sts
+    st2.release()
+
+    # --------------------------------------------------------------- e2e
+    # state held on the host (pinned): every step copies x, v in, runs one
+    # outer step through the public API and reads x, v and the energy back
+    d3 = core.DeviceSystem(W["system"]())
+    st3 = core.MDState(d3, v0, m_hmr.astype(np.float32), seeds=I.seed, replica_ids=[rank])
+    hx = torch.from_numpy(sy.x.astype(np.float32)).pin_memory()
+    hv = torch.from_numpy(v0.astype(np.float32)).pin_memory()
+    he = torch.zeros(1, dtype=torch.float64).pin_memory()
+    core.respa_step(ctx, st3, integ, 2)
+    ctx.sync()
+    n_e2e = max(5, args.steps // 4)
+    barrier()
+    t0 = time.perf_counter()
+    e0.record(stream)
+    for _ in range(n_e2e):
+        d3.x.copy_(hx, non_blocking=True)
+        st3.v.copy_(hv, non_blocking=True)
+        core.respa_step(ctx, st3, integ, 1)
+        hx.copy_(d3.x, non_blocking=True)
+        hv.copy_(st3.v, non_blocking=True)
+        he.copy_(st3.energy[:1], non_blocking=True)
+    e1.record(stream)
+    barrier()
+    ctx.sync()
+    ms_e2e = max_over_ranks(e0.elapsed_time(e1)) / n_e2e
+    st3.release()
+    bytes_in = 2 * sy.n_atoms * 12
+    bytes_out = 2 * sy.n_atoms * 12 + 8
+
+    # ---------------------------------------------------------- roofline
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = json.load(open(pk_path))
+    top = max(prof.items(), key=lambda kv: kv[1][1]) if prof else ("none", (1, 0.0))
+    name, (launches, tot_ms) = top
+    per_launch_s = tot_ms / max(launches, 1) * 1e-3
+    C = cs.C
+    # algorithmic FLOP per active edge (one layer), counted as 2 per FMA:
+    # forward: radial 3*8 FMA + 3 mul + 9 FMA per channel;
+    # adjoint: radial and derivative 48 FMA + 18 + 9 + 3 + 9 + 9 + 3 per
+    # channel, plus 30 FMA per lane for the direction derivatives.
+    flop_edge = {"mp_fwd": 2 * 36 * C, "mp_bwd": 2 * 99 * C + 2 * 30 * 32}
+    fp32_peak_tflops = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
+    if name in flop_edge:
+        achieved = flop_edge[name] * e_cons / per_launch_s / 1e12
+        roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
+                "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops, "traffic": None,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz (nominal unit counts and max clock)",
+                "work_per_launch": f"{flop_edge[name]} FLOP x {e_cons} active edges"}
+    else:
+        roof = {"kernel": name, "bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"),
+                "unit": "GB/s", "frac": None, "traffic": None}
+    shares = {k: {"launches": v[0], "ms_per_step": v[1] / args.steps,
+                  "share": v[1] / max(sum(x[1] for x in prof.values()), 1e-9)} for k, v in prof.items()}
+
+    val = ns_per_day(I.dt_outer, 1e3 / ms_dmts) * world
+    sts_val = ns_per_day(sts.dt_outer, 1e3 / ms_sts) * world
+    line = {
+        "metric": "ns/day (DMTS-NC)", "value": val, "unit": "ns/day", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_dmts, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": sy.name, "n_atoms": sy.n_atoms,
+                   "integrator": f"DMTS-NC outer {I.dt_outer} fs / {I.n_inner} inner, HMR +{I.hmr_delta} amu on H, "
+                                 f"gamma_H {I.gamma_ps[0]}/ps, gamma_heavy {I.gamma_ps[1]}/ps",
+                   "cons_model": f"L={cs.L} C={cs.C} lmax={cs.lmax} K={cs.K} rc={cs.rc}",
+                   "nc_model": f"C={ns.C} lmax=1 rc={ns.rc} n_c={ns.n_c} n_l={ns.n_l}",
+                   "precision": "fp32 throughout (bf16 MLP path not built)",
+                   "l2": "inputs larger than L2: about 0.5 GB of node and edge data per outer step",
+                   "parallelism": "replicas only (one replica per GPU)"},
+        "atom_steps_per_s": sy.n_atoms * 1e3 / ms_dmts * world,
+        "sts": {"ns_per_day": sts_val, "ms_per_step": ms_sts, "dt_fs": sts.dt_outer,
+                "atom_steps_per_s": sy.n_atoms * 1e3 / ms_sts * world},
+        "speedup_vs_sts": val / sts_val,
+        "e2e": {"value": ns_per_day(I.dt_outer, 1e3 / ms_e2e) * world, "unit": "ns/day",
+                "h2d_bytes_per_step": bytes_in, "d2h_bytes_per_step": bytes_out, "steps": n_e2e},
+        "gpu_launches": n_launches,
+        "clocks": ck,
+        "roofline": roof,
+        "kernels": shares,
+        "active_edges": {"cons": e_cons, "nc": e_nc},
+    }
+    if rank == 0 and not args.no_cpu and world == 1:
+        t_outer, desc = oracle_outer_step_seconds(sy, W, 0.6)
+        line["cpu_baseline"] = {"value": ns_per_day(I.dt_outer, 1.0 / t_outer), "unit": "ns/day",
+                                "cores": 1, "kind": "oracle", "sample": desc}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -330,6 +330,17 @@ dmts_status dmts_gaussians(dmts_ctx *ctx, uint64_t seed, uint32_t replica, uint6
  * (admission accounting). */
 long long dmts_replica_footprint(const dmts_ctx *ctx, int n_atoms);
 
+/* ------------------------------------------------------ instrumentation */
+/* (No counterpart in the paper: measurement support.) While enabled, every
+ * kernel launch of the context is bracketed by a pair of CUDA events on its
+ * own stream. dmts_profile_read() synchronises the device and returns, for
+ * kernel slot `idx` (0 <= idx < count returned by a call with idx = -1), the
+ * kernel's name, number of launches and summed duration in ms since the last
+ * enable. Disabling clears nothing; enabling clears the table. */
+dmts_status dmts_profile_enable(dmts_ctx *ctx, int enable);
+int dmts_profile_read(dmts_ctx *ctx, int idx, char *name, int name_cap, long long *launches,
+                      double *total_ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -267,3 +267,21 @@ class ConsEnergy(torch.autograd.Function):
         counts = (rep_off[1:] - rep_off[:-1]).long()
         g = torch.repeat_interleave(gE.to(F.dtype), counts)
         return -F * g[:, None], None, None, None, None
+
+
+def profile_enable(ctx: Context, on: bool = True):
+    """Per-kernel CUDA-event timing inside the library (measurement support)."""
+    L.check(ctx.lib.dmts_profile_enable(ctx.handle, 1 if on else 0), ctx.handle)
+
+
+def profile_read(ctx: Context) -> dict:
+    """{kernel: (launches, total_ms)} since the last profile_enable(True)."""
+    n = ctx.lib.dmts_profile_read(ctx.handle, -1, None, 0, None, None)
+    out = {}
+    buf = ct.create_string_buffer(64)
+    for k in range(max(n, 0)):
+        la = ct.c_longlong(0)
+        ms = ct.c_double(0.0)
+        ctx.lib.dmts_profile_read(ctx.handle, k, buf, 64, ct.byref(la), ct.byref(ms))
+        out[buf.value.decode()] = (int(la.value), float(ms.value))
+    return out

@@ -174,7 +174,7 @@ dmts_status cons_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const
     float *gs0 = (float *)w.gs0.p, *gs1 = (float *)w.gs1.p, *gA = (float *)w.gA.p;
     float *e_atom = (float *)w.e_atom.p;
     const EdgeGeom g = edge_geom(s, row_ptr, col, m);
-    launch_embed(N, C, s.species, m.emb, S, st);
+    { ProfScope ps(ctx, "embed", st); launch_embed(N, C, s.species, m.emb, S, st); }
     for (int t = 0; t < L; ++t) {
         LayerIO io;
         memset(&io, 0, sizeof io);
@@ -184,17 +184,17 @@ dmts_status cons_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const
         io.A = A + nc_ * NLM * t;
         io.q = q;
         io.err = ctx->d_err;
-        launch_mp_fwd(C, m.lmax, m.K, g, io, st);
+        { ProfScope ps(ctx, "mp_fwd", st); launch_mp_fwd(C, m.lmax, m.K, g, io, st); }
         Epi e1 = epi(EPI_BIAS_SILU);
         e1.bias = m.b1[t];
         e1.H = H + nc_ * t;
         e1.out = act;
-        launch_gemm_f32(N, C, NL * C, q, m.w1[t], 1, e1, st);
+        { ProfScope ps(ctx, "gemm", st); launch_gemm_f32(N, C, NL * C, q, m.w1[t], 1, e1, st); }
         Epi e2 = epi(EPI_RESID);
         e2.bias = m.b2[t];
         e2.res = S + nc_ * t;
         e2.out = S + nc_ * (t + 1);
-        launch_gemm_f32(N, C, C, act, m.w2[t], 1, e2, st);
+        { ProfScope ps(ctx, "gemm", st); launch_gemm_f32(N, C, C, act, m.w2[t], 1, e2, st); }
     }
     Epi er = epi(EPI_READOUT);
     er.bias = m.br;
@@ -202,25 +202,25 @@ dmts_status cons_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const
     er.scale = m.scale;
     er.out = u;
     er.out2 = gz;
-    launch_gemm_f32(N, C, C, S + nc_ * L, m.wr, 1, er, st);
-    launch_rowsum(N, C, u, m.scale, e_atom, st);
+    { ProfScope ps(ctx, "gemm", st); launch_gemm_f32(N, C, C, S + nc_ * L, m.wr, 1, er, st); }
+    { ProfScope ps(ctx, "rowsum", st); launch_rowsum(N, C, u, m.scale, e_atom, st); }
     if (forces) {
         // dU/ds^L = gz Wr
         Epi eg = epi(EPI_STORE);
         eg.out = gs0;
-        launch_gemm_f32(N, C, C, gz, m.wr, 0, eg, st);
+        { ProfScope ps(ctx, "gemm", st); launch_gemm_f32(N, C, C, gz, m.wr, 0, eg, st); }
         float *gin = gs0, *gout = gs1;
         for (int t = L - 1; t >= 0; --t) {
             Epi ed = epi(EPI_DSILU);
             ed.H = H + nc_ * t;
             ed.out = act;                       // g_h
-            launch_gemm_f32(N, C, C, gin, m.w2[t], 0, ed, st);
+            { ProfScope ps(ctx, "gemm", st); launch_gemm_f32(N, C, C, gin, m.w2[t], 0, ed, st); }
             Epi ea = epi(EPI_GA);
             ea.A = A + nc_ * NLM * t;
             ea.out = gA;
             ea.C = C;
             ea.lmax = m.lmax;
-            launch_gemm_f32(N, NL * C, C, act, m.w1[t], 0, ea, st);
+            { ProfScope ps(ctx, "gemm", st); launch_gemm_f32(N, NL * C, C, act, m.w1[t], 0, ea, st); }
             LayerIO io;
             memset(&io, 0, sizeof io);
             io.s = S + nc_ * t;
@@ -232,7 +232,7 @@ dmts_status cons_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const
             io.F = forces;
             io.accumulate = t != L - 1;
             io.err = ctx->d_err;
-            launch_mp_bwd(C, m.lmax, m.K, g, io, st);
+            { ProfScope ps(ctx, "mp_bwd", st); launch_mp_bwd(C, m.lmax, m.K, g, io, st); }
             std::swap(gin, gout);
         }
     }
@@ -256,9 +256,9 @@ dmts_status cons_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const
         if (!forces) cudaMemsetAsync(w.ftmp.p, 0, sizeof(float) * 3 * N, st);
         pa.e_atom = e_atom;
         pa.err = ctx->d_err;
-        launch_prior(pa, st);
+        { ProfScope ps(ctx, "prior", st); launch_prior(pa, st); }
     }
-    if (energy) launch_replica_sum(e_atom, s.rep_off, s.n_rep, energy, 0, st);
+    if (energy) { ProfScope ps(ctx, "replica_sum", st); launch_replica_sum(e_atom, s.rep_off, s.n_rep, energy, 0, st); }
     return DMTS_OK;
 }
 
@@ -276,7 +276,7 @@ dmts_status nc_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const i
         return fail(ctx, DMTS_E_OOM, "workspace allocation failed");
     float *s0 = (float *)w.nc_s.p, *s1 = s0 + nc_;
     const EdgeGeom g = edge_geom(s, row_ptr, col, m);
-    launch_embed(N, C, s.species, m.emb, s0, st);
+    { ProfScope ps(ctx, "embed", st); launch_embed(N, C, s.species, m.emb, s0, st); }
     LayerIO io;
     memset(&io, 0, sizeof io);
     io.s = s0;
@@ -285,21 +285,21 @@ dmts_status nc_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const i
     io.A = (float *)w.nc_A.p;
     io.q = (float *)w.nc_q.p;
     io.err = ctx->d_err;
-    launch_mp_fwd(C, 1, m.K, g, io, st);
+    { ProfScope ps(ctx, "nc_mp_fwd", st); launch_mp_fwd(C, 1, m.K, g, io, st); }
     Epi e1 = epi(EPI_BIAS_SILU);
     e1.bias = m.b1[0];
     e1.H = (float *)w.nc_h.p;
     e1.out = (float *)w.nc_act.p;
-    launch_gemm_f32(N, C, 2 * C, io.q, m.w1[0], 1, e1, st);
+    { ProfScope ps(ctx, "nc_gemm", st); launch_gemm_f32(N, C, 2 * C, io.q, m.w1[0], 1, e1, st); }
     Epi e2 = epi(EPI_RESID);
     e2.bias = m.b2[0];
     e2.res = s0;
     e2.out = s1;
-    launch_gemm_f32(N, C, C, (float *)w.nc_act.p, m.w2[0], 1, e2, st);
+    { ProfScope ps(ctx, "nc_gemm", st); launch_gemm_f32(N, C, C, (float *)w.nc_act.p, m.w2[0], 1, e2, st); }
     Epi e3 = epi(EPI_STORE);
     e3.out = (float *)w.nc_qk.p;
-    launch_gemm_f32(N, QKW, C, s1, m.Wqk, 1, e3, st);
-    launch_nc_vectors(N, C, m.nl, io.A, m.U, (float *)w.nc_v.p, ctx->d_err, st);
+    { ProfScope ps(ctx, "nc_gemm", st); launch_gemm_f32(N, QKW, C, s1, m.Wqk, 1, e3, st); }
+    { ProfScope ps(ctx, "nc_vectors", st); launch_nc_vectors(N, C, m.nl, io.A, m.U, (float *)w.nc_v.p, ctx->d_err, st); }
     NCHeadArgs a;
     a.x = s.x;
     a.atom_rep = s.atom_rep;
@@ -320,8 +320,8 @@ dmts_status nc_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const i
     a.species = s.species;
     a.F = (float *)w.nc_f.p;
     a.err = ctx->d_err;
-    launch_nc_head(m.K, m.nc, m.nl, a, st);
-    launch_mean_sub((float *)w.nc_f.p, forces, s.rep_off, s.n_rep, net, ctx->d_err, st);
+    { ProfScope ps(ctx, "nc_head", st); launch_nc_head(m.K, m.nc, m.nl, a, st); }
+    { ProfScope ps(ctx, "mean_sub", st); launch_mean_sub((float *)w.nc_f.p, forces, s.rep_off, s.n_rep, net, ctx->d_err, st); }
     return DMTS_OK;
 }
 
@@ -383,11 +383,13 @@ SysView state_view(dmts_state *stt) {
 void rebuild_lists(dmts_ctx *ctx, StateInternal *si, const SysView &v, cudaStream_t st) {
     NbrWork nw;
     prepare_nbr_work_async(ctx, si, v, nw);
-    nbr_cells(nw, si->r_cons, st);
-    nbr_fill(nw, si->r_cons, (int *)si->cons_row.p, (int *)si->cons_col.p, si->cons_cap, (float *)si->x_ref.p, st);
-    if (ctx->has_nc)
+    { ProfScope ps(ctx, "nbr_cells", st); nbr_cells(nw, si->r_cons, st); }
+    { ProfScope ps(ctx, "nbr_fill", st); nbr_fill(nw, si->r_cons, (int *)si->cons_row.p, (int *)si->cons_col.p, si->cons_cap, (float *)si->x_ref.p, st); }
+    if (ctx->has_nc) {
+        ProfScope ps(ctx, "nbr_sublist", st);
         nbr_sublist(nw, (int *)si->cons_row.p, (int *)si->cons_col.p, si->r_nc, (int *)si->nc_row.p,
                     (int *)si->nc_col.p, si->nc_cap, st);
+    }
     k_set_int<<<1, 1, 0, st>>>((int *)si->gate.p, 0);
 }
 
@@ -475,6 +477,8 @@ void dmts_destroy(dmts_ctx *ctx) {
     if (ctx->nc.dev) cudaFree(ctx->nc.dev);
     if (ctx->d_err) cudaFree(ctx->d_err);
     ctx->ws.release_all();
+    ctx->nbr_scratch.release_all();
+    ctx->prof.release();
     delete ctx;
 }
 
@@ -785,7 +789,7 @@ dmts_status respa_step(dmts_ctx *ctx, dmts_state *stt, const dmts_integrator *p,
             else if (k == 0) ia.ops = (o == 0 ? OP_KICK_L2 : (OP_CLOSE_B | OP_KICK_L | OP_KICK_L2)) | OP_BAOA;
             else ia.ops = OP_CLOSE_B | OP_BAOA;
             ia.step_add = (uint64_t)o * n_in + k;
-            launch_integrate(ia, st);
+            { ProfScope ps(ctx, "integrate", st); launch_integrate(ia, st); }
             rebuild_lists(ctx, si, v, st);
             if (!sts) {
                 s = nc_fast();
@@ -796,7 +800,7 @@ dmts_status respa_step(dmts_ctx *ctx, dmts_state *stt, const dmts_integrator *p,
         if (s != DMTS_OK) return s;
     }
     ia.ops = sts ? OP_CLOSE_B : (OP_CLOSE_B | OP_KICK_L);
-    launch_integrate(ia, st);
+    { ProfScope ps(ctx, "integrate", st); launch_integrate(ia, st); }
     launch_advance_step(stt->step, v.n_rep, (uint64_t)n_outer * n_in, ctx->d_err, st);
     return ck(ctx, cudaGetLastError(), "respa_step launch") ? DMTS_OK : DMTS_E_CUDA;
 }

@@ -69,6 +69,39 @@ struct StateInternal {
     NbrScratch scratch;
 };
 
+struct ProfSlot {
+    std::string name;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+    long long launches;
+    double ms;
+};
+
+struct Profiler {
+    bool on = false;
+    std::vector<ProfSlot> slots;
+    std::vector<cudaEvent_t> pool;
+    int slot(const char *name);
+    cudaEvent_t take();
+    void flush();
+    void clear();
+    void release();
+};
+
+}  // namespace dmts
+
+struct dmts_ctx;
+
+namespace dmts {
+// Brackets the launches issued in its lifetime with CUDA events when the
+// context's profiler is on.
+struct ProfScope {
+    Profiler *p;
+    cudaStream_t s;
+    int k;
+    cudaEvent_t start = nullptr;
+    ProfScope(dmts_ctx *ctx, const char *name, cudaStream_t st);
+    ~ProfScope();
+};
 }  // namespace dmts
 
 struct dmts_ctx {
@@ -80,6 +113,7 @@ struct dmts_ctx {
     std::string last_error;
     dmts::Workspace ws;
     dmts::NbrScratch nbr_scratch;
+    dmts::Profiler prof;
 };
 
 namespace dmts {
