@@ -174,6 +174,35 @@ dmts_status dmts_sync(dmts_ctx *ctx, void *stream);
 dmts_status nbr_build(dmts_ctx *ctx, const dmts_system *sys, dmts_nbr *nbr,
                       long long *n_pairs, void *stream);
 
+/*
+ * nbr_build for callers that cannot allocate device memory -- code running
+ * where cudaMalloc is unavailable or forbidden (inside a memory-pool-managed
+ * framework that owns every device allocation, during stream capture, or in
+ * a plug-in that may only touch buffers its host hands it), and callers that
+ * have no dmts_ctx because creating one allocates. The paper has no
+ * counterpart; this is the same cell-list neighbour build as nbr_build, with
+ * identical output.
+ *
+ * All scratch (cell grid, cell counts and offsets, per-atom cell and slot,
+ * per-row counts, replica map, pair total, error word) lives in one static
+ * device array of about 3.4 MB that every GPU loading this library keeps
+ * until the process exits. Limits: at most DMTS_STATIC_MAX_ATOMS atoms,
+ * DMTS_STATIC_MAX_REPLICAS replicas and DMTS_STATIC_MAX_CELLS cells in
+ * total; larger inputs are rejected with DMTS_E_INVALID before any device
+ * work. The caller passes the system and the list buffers (nbr->row_ptr,
+ * nbr->col) as for nbr_build. Works on the current CUDA device; the first
+ * call on a device looks up the array's device address, so make that first
+ * call before any stream capture. Every call reuses the same array: calls
+ * that overlap on the GPU (other streams, other host threads) race and must
+ * be serialised by the caller. No cudaMalloc, cudaFree or allocating library
+ * routine is called. Synchronous; errors as for nbr_build (the message is
+ * read with dmts_last_error(NULL)).
+ */
+#define DMTS_STATIC_MAX_ATOMS 131072
+#define DMTS_STATIC_MAX_CELLS 65536
+#define DMTS_STATIC_MAX_REPLICAS 1024
+dmts_status nbr_build_noalloc(const dmts_system *sys, dmts_nbr *nbr, long long *n_pairs, void *stream);
+
 #define DMTS_WITH_PRIOR 1      /* energy_forces_cons: add bonds + LJ + E_rep */
 #define DMTS_WITH_BONDS 1      /* forces_nc: add the bond forces and F_rep */
 
