@@ -285,3 +285,57 @@ def profile_read(ctx: Context) -> dict:
         ctx.lib.dmts_profile_read(ctx.handle, k, buf, 64, ct.byref(la), ct.byref(ms))
         out[buf.value.decode()] = (int(la.value), float(ms.value))
     return out
+
+
+class ReplicaRequest:
+    """One serving request: a system, its initial velocities and simulation
+    masses, the number of outer steps, its noise seed and id, and its arrival
+    time (s, relative to the start of the run)."""
+
+    def __init__(self, system, v, masses, n_outer, seed, replica_id, arrival_s=0.0):
+        self.system = system
+        self.x = np.ascontiguousarray(system.x, np.float32)
+        self.v = np.ascontiguousarray(v, np.float32)
+        self.species = np.ascontiguousarray(system.species, np.uint8)
+        self.mol_id = np.ascontiguousarray(system.mol_id, np.int32)
+        self.bonds = np.ascontiguousarray(system.bonds.reshape(-1, 2), np.int32)
+        self.bond_r0 = np.ascontiguousarray(system.bond_r0, np.float32)
+        self.masses = np.ascontiguousarray(masses, np.float32)
+        self.n_outer, self.seed, self.replica_id = int(n_outer), int(seed), int(replica_id)
+        self.arrival_s = float(arrival_s)
+
+    def struct(self):
+        box = (ct.c_float * 3)(*[float(b) for b in self.system.box])
+        return L.Request(self.x.shape[0], self.x.ctypes.data, self.v.ctypes.data, self.species.ctypes.data,
+                         self.mol_id.ctypes.data, self.bonds.shape[0], self.bonds.ctypes.data,
+                         self.bond_r0.ctypes.data, self.masses.ctypes.data, box, self.n_outer,
+                         self.seed, self.replica_id, self.arrival_s)
+
+
+def run_replicas(ctx: Context, requests, integ: L.Integrator, hbm_budget_bytes: int = 64 << 30,
+                 max_slots: int = 512, realtime: bool = False, tick_cap: int = 1 << 20):
+    """Continuous-batching serving loop. Returns (results, stats): results[k]
+    = dict(x, v, energy, t_arrival_s, t_admit_s, t_done_s, status); stats =
+    dict(tick_ms, n_ticks, wall_s, atom_outer_steps, max_resident)."""
+    n = len(requests)
+    reqs = (L.Request * max(1, n))(*[r.struct() for r in requests])
+    xs = [np.zeros_like(r.x) for r in requests]
+    vs = [np.zeros_like(r.v) for r in requests]
+    res = (L.Result * max(1, n))()
+    for k in range(n):
+        res[k].x = xs[k].ctypes.data
+        res[k].v = vs[k].ctypes.data
+    ticks = np.zeros(tick_cap, np.float64)
+    stats = L.ServeStats(ticks.ctypes.data, tick_cap, 0, 0.0, 0.0, 0)
+    cfg = L.ServeCfg(int(hbm_budget_bytes), int(max_slots), 1 if realtime else 0)
+    st = ctx.lib.run_replicas(ctx.handle, reqs, n, ct.byref(integ), ct.byref(cfg), res, ct.byref(stats))
+    L.check(st, ctx.handle)
+    out = [dict(x=xs[k], v=vs[k], energy=res[k].energy, t_arrival_s=res[k].t_arrival_s,
+                t_admit_s=res[k].t_admit_s, t_done_s=res[k].t_done_s, status=res[k].status) for k in range(n)]
+    nt = min(stats.n_ticks, tick_cap)
+    return out, dict(tick_ms=ticks[:nt].copy(), n_ticks=stats.n_ticks, wall_s=stats.wall_s,
+                     atom_outer_steps=stats.atom_outer_steps, max_resident=stats.max_resident)
+
+
+def replica_footprint(ctx: Context, n_atoms: int) -> int:
+    return int(ctx.lib.dmts_replica_footprint(ctx.handle, int(n_atoms)))

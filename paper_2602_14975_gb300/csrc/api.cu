@@ -415,6 +415,115 @@ void prepare_nbr_work_async(dmts_ctx *ctx, StateInternal *si, const SysView &v, 
 
 }  // namespace dmts
 
+// Stream-ordered host copies of the replica offsets and boxes.
+static bool host_copy_offsets(dmts_ctx *ctx, const dmts_system *sys, std::vector<int> &rep_off,
+                              std::vector<float> &box, cudaStream_t st) {
+    rep_off.resize(sys->n_replicas + 1);
+    box.resize(3 * sys->n_replicas);
+    return ck(ctx, cudaMemcpyAsync(rep_off.data(), sys->rep_off, sizeof(int) * rep_off.size(), cudaMemcpyDeviceToHost, st),
+              "rep_off copy") &&
+           ck(ctx, cudaMemcpyAsync(box.data(), sys->box, sizeof(float) * box.size(), cudaMemcpyDeviceToHost, st),
+              "box copy") &&
+           ck(ctx, cudaStreamSynchronize(st), "offsets");
+}
+
+// Builds the cell structure for `grids` into `nw` scratch owned by `bufs`.
+static dmts_status prepare_nbr_work(dmts_ctx *ctx, NbrScratch &b, const SysView &v, const std::vector<CellGrid> &grids,
+                                    int n_cells, const int *gate, NbrWork &nw, cudaStream_t st) {
+    const int N = v.n, R = v.n_rep;
+    if (!b.grid.ensure(sizeof(CellGrid) * R) || !b.cell_cnt.ensure(sizeof(int) * (n_cells + 1)) ||
+        !b.cell_start.ensure(sizeof(int) * (n_cells + 1)) || !b.cell_atoms.ensure(sizeof(int) * (N + 1)) ||
+        !b.atom_cell.ensure(sizeof(int) * (N + 1)) || !b.atom_slot.ensure(sizeof(int) * (N + 1)) ||
+        !b.counts.ensure(sizeof(int) * (N + 1)) || !b.total.ensure(sizeof(long long)))
+        return fail(ctx, DMTS_E_OOM, "neighbour scratch allocation failed");
+    if (!ck(ctx, cudaMemcpyAsync(b.grid.p, grids.data(), sizeof(CellGrid) * R, cudaMemcpyHostToDevice, st), "grid upload") ||
+        !ck(ctx, cudaStreamSynchronize(st), "grid upload"))
+        return DMTS_E_CUDA;
+    nw.n_atoms = N;
+    nw.n_rep = R;
+    nw.n_cells = n_cells;
+    nw.x = v.x;
+    nw.rep_off = v.rep_off;
+    nw.atom_rep = v.atom_rep;
+    nw.grid = (CellGrid *)b.grid.p;
+    nw.cell_cnt = (int *)b.cell_cnt.p;
+    nw.cell_start = (int *)b.cell_start.p;
+    nw.cell_atoms = (int *)b.cell_atoms.p;
+    nw.atom_cell = (int *)b.atom_cell.p;
+    nw.atom_slot = (int *)b.atom_slot.p;
+    nw.counts = (int *)b.counts.p;
+    nw.total = (long long *)b.total.p;
+    nw.gate = gate;
+    nw.err = ctx->d_err;
+    return DMTS_OK;
+}
+
+void free_state_internal(StateInternal *si) {
+    if (!si) return;
+    si->cons_row.release();
+    si->cons_col.release();
+    si->nc_row.release();
+    si->nc_col.release();
+    si->x_ref.release();
+    si->gate.release();
+    si->atom_rep.release();
+    si->scratch.release_all();
+    delete si;
+}
+
+// Allocates lists (capacity from a first count with 40 % head-room) and the
+// cell grids; leaves the lists built for the current positions.
+dmts_status init_state(dmts_ctx *ctx, dmts_state *stt, float skin, cudaStream_t st) {
+    const dmts_system *sys = &stt->sys;
+    StateInternal *si = (StateInternal *)stt->internal;
+    if (!si) {
+        si = new StateInternal();
+        stt->internal = si;
+    }
+    std::vector<int> rep_off;
+    std::vector<float> box;
+    if (!host_copy_offsets(ctx, sys, rep_off, box, st)) return DMTS_E_CUDA;
+    if (rep_off[0] != 0 || rep_off.back() != sys->n_atoms) return fail(ctx, DMTS_E_INVALID, "rep_off inconsistent");
+    si->n = sys->n_atoms;
+    si->n_rep = sys->n_replicas;
+    si->skin = skin;
+    si->r_cons = std::max(ctx->cons.rc, ctx->prior.lj_rc) + skin;
+    si->r_nc = (ctx->has_nc ? ctx->nc.rc : 0.f) + skin;
+    dmts_status s = setup_grids(ctx, rep_off, box, si->r_cons, si->grids, si->n_cells);
+    if (s != DMTS_OK) return s;
+    const int N = si->n;
+    if (!si->atom_rep.ensure(sizeof(int) * (N + 1)) || !si->x_ref.ensure(sizeof(float) * 3 * (N + 1)) ||
+        !si->gate.ensure(sizeof(int)) || !si->cons_row.ensure(sizeof(int) * (N + 1)) ||
+        !si->nc_row.ensure(sizeof(int) * (N + 1)))
+        return fail(ctx, DMTS_E_OOM, "state allocation failed");
+    atom_rep_map(sys->rep_off, sys->n_replicas, N, (int *)si->atom_rep.p, st);
+    k_set_int<<<1, 1, 0, st>>>((int *)si->gate.p, 1);
+    SysView v = state_view(stt);
+    NbrWork nw;
+    s = prepare_nbr_work(ctx, si->scratch, v, si->grids, si->n_cells, (int *)si->gate.p, nw, st);
+    if (s != DMTS_OK) return s;
+    nbr_cells(nw, si->r_cons, st);
+    // size the lists from a count pass
+    nbr_fill(nw, si->r_cons, (int *)si->cons_row.p, nullptr, -1, nullptr, st);
+    long long tot = 0;
+    cudaMemcpyAsync(&tot, nw.total, sizeof(long long), cudaMemcpyDeviceToHost, st);
+    if (!ck(ctx, cudaStreamSynchronize(st), "list sizing")) return DMTS_E_CUDA;
+    const long long want_cons = (long long)(tot * 1.4) + 16LL * N + 1024;
+    const double frac = ctx->has_nc ? std::pow(si->r_nc / si->r_cons, 3.0) : 0.0;
+    const long long want_nc = (long long)(tot * frac * 1.6) + 16LL * N + 1024;
+    if (!si->cons_col.ensure(sizeof(int) * want_cons) || !si->nc_col.ensure(sizeof(int) * want_nc))
+        return fail(ctx, DMTS_E_OOM, "neighbour list allocation failed");
+    si->cons_cap = (long long)(si->cons_col.cap / sizeof(int));
+    si->nc_cap = (long long)(si->nc_col.cap / sizeof(int));
+    rebuild_lists(ctx, si, v, st);
+    int err = 0;
+    cudaMemcpyAsync(&err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (!ck(ctx, cudaStreamSynchronize(st), "initial lists")) return DMTS_E_CUDA;
+    if (err) return fail(ctx, (dmts_status)err, "initial neighbour build failed");
+    return DMTS_OK;
+}
+
+
 // ================================================================ C ABI ==
 extern "C" {
 
@@ -528,45 +637,6 @@ static SysView make_view(dmts_ctx *ctx, const dmts_system *sys, cudaStream_t st)
     return v;
 }
 
-static bool host_copy_offsets(dmts_ctx *ctx, const dmts_system *sys, std::vector<int> &rep_off,
-                              std::vector<float> &box) {
-    rep_off.resize(sys->n_replicas + 1);
-    box.resize(3 * sys->n_replicas);
-    return ck(ctx, cudaMemcpy(rep_off.data(), sys->rep_off, sizeof(int) * rep_off.size(), cudaMemcpyDeviceToHost),
-              "rep_off copy") &&
-           ck(ctx, cudaMemcpy(box.data(), sys->box, sizeof(float) * box.size(), cudaMemcpyDeviceToHost), "box copy");
-}
-
-// Builds the cell structure for `grids` into `nw` scratch owned by `bufs`.
-static dmts_status prepare_nbr_work(dmts_ctx *ctx, NbrScratch &b, const SysView &v, const std::vector<CellGrid> &grids,
-                                    int n_cells, const int *gate, NbrWork &nw) {
-    const int N = v.n, R = v.n_rep;
-    if (!b.grid.ensure(sizeof(CellGrid) * R) || !b.cell_cnt.ensure(sizeof(int) * (n_cells + 1)) ||
-        !b.cell_start.ensure(sizeof(int) * (n_cells + 1)) || !b.cell_atoms.ensure(sizeof(int) * (N + 1)) ||
-        !b.atom_cell.ensure(sizeof(int) * (N + 1)) || !b.atom_slot.ensure(sizeof(int) * (N + 1)) ||
-        !b.counts.ensure(sizeof(int) * (N + 1)) || !b.total.ensure(sizeof(long long)))
-        return fail(ctx, DMTS_E_OOM, "neighbour scratch allocation failed");
-    if (!ck(ctx, cudaMemcpy(b.grid.p, grids.data(), sizeof(CellGrid) * R, cudaMemcpyHostToDevice), "grid upload"))
-        return DMTS_E_CUDA;
-    nw.n_atoms = N;
-    nw.n_rep = R;
-    nw.n_cells = n_cells;
-    nw.x = v.x;
-    nw.rep_off = v.rep_off;
-    nw.atom_rep = v.atom_rep;
-    nw.grid = (CellGrid *)b.grid.p;
-    nw.cell_cnt = (int *)b.cell_cnt.p;
-    nw.cell_start = (int *)b.cell_start.p;
-    nw.cell_atoms = (int *)b.cell_atoms.p;
-    nw.atom_cell = (int *)b.atom_cell.p;
-    nw.atom_slot = (int *)b.atom_slot.p;
-    nw.counts = (int *)b.counts.p;
-    nw.total = (long long *)b.total.p;
-    nw.gate = gate;
-    nw.err = ctx->d_err;
-    return DMTS_OK;
-}
-
 dmts_status nbr_build(dmts_ctx *ctx, const dmts_system *sys, dmts_nbr *nbr, long long *n_pairs, void *stream) {
     dmts_status s = check_sys(ctx, sys);
     if (s != DMTS_OK) return s;
@@ -576,7 +646,7 @@ dmts_status nbr_build(dmts_ctx *ctx, const dmts_system *sys, dmts_nbr *nbr, long
     cudaStream_t st = (cudaStream_t)stream;
     std::vector<int> rep_off;
     std::vector<float> box;
-    if (!host_copy_offsets(ctx, sys, rep_off, box)) return DMTS_E_CUDA;
+    if (!host_copy_offsets(ctx, sys, rep_off, box, st)) return DMTS_E_CUDA;
     if (rep_off[0] != 0 || rep_off.back() != sys->n_atoms) return fail(ctx, DMTS_E_INVALID, "rep_off inconsistent");
     std::vector<CellGrid> grids;
     int n_cells = 0;
@@ -584,7 +654,7 @@ dmts_status nbr_build(dmts_ctx *ctx, const dmts_system *sys, dmts_nbr *nbr, long
     if (s != DMTS_OK) return s;
     SysView v = make_view(ctx, sys, st);
     NbrWork nw;
-    s = prepare_nbr_work(ctx, ctx->nbr_scratch, v, grids, n_cells, nullptr, nw);
+    s = prepare_nbr_work(ctx, ctx->nbr_scratch, v, grids, n_cells, nullptr, nw, st);
     if (s != DMTS_OK) return s;
     nbr_cells(nw, nbr->r_list, st);
     nbr_fill(nw, nbr->r_list, nbr->row_ptr, nbr->col, nbr->capacity, nullptr, st);
@@ -640,19 +710,6 @@ dmts_status forces_nc(dmts_ctx *ctx, const dmts_system *sys, const dmts_nbr *nbr
 }
 
 // ------------------------------------------------------------ respa_step
-static void free_state_internal(StateInternal *si) {
-    if (!si) return;
-    si->cons_row.release();
-    si->cons_col.release();
-    si->nc_row.release();
-    si->nc_col.release();
-    si->x_ref.release();
-    si->gate.release();
-    si->atom_rep.release();
-    si->scratch.release_all();
-    delete si;
-}
-
 void dmts_state_release(dmts_ctx *ctx, dmts_state *st) {
     if (!st || !st->internal) return;
     if (ctx) cudaSetDevice(ctx->device);
@@ -660,54 +717,6 @@ void dmts_state_release(dmts_ctx *ctx, dmts_state *st) {
     free_state_internal((StateInternal *)st->internal);
     st->internal = nullptr;
 }
-
-// Allocates lists (capacity from a first count with 40 % head-room) and the
-// cell grids; leaves the lists built for the current positions.
-static dmts_status init_state(dmts_ctx *ctx, dmts_state *stt, float skin, cudaStream_t st) {
-    const dmts_system *sys = &stt->sys;
-    StateInternal *si = new StateInternal();
-    stt->internal = si;
-    std::vector<int> rep_off;
-    std::vector<float> box;
-    if (!host_copy_offsets(ctx, sys, rep_off, box)) return DMTS_E_CUDA;
-    if (rep_off[0] != 0 || rep_off.back() != sys->n_atoms) return fail(ctx, DMTS_E_INVALID, "rep_off inconsistent");
-    si->n = sys->n_atoms;
-    si->n_rep = sys->n_replicas;
-    si->skin = skin;
-    si->r_cons = std::max(ctx->cons.rc, ctx->prior.lj_rc) + skin;
-    si->r_nc = (ctx->has_nc ? ctx->nc.rc : 0.f) + skin;
-    dmts_status s = setup_grids(ctx, rep_off, box, si->r_cons, si->grids, si->n_cells);
-    if (s != DMTS_OK) return s;
-    const int N = si->n;
-    if (!si->atom_rep.ensure(sizeof(int) * (N + 1)) || !si->x_ref.ensure(sizeof(float) * 3 * (N + 1)) ||
-        !si->gate.ensure(sizeof(int)) || !si->cons_row.ensure(sizeof(int) * (N + 1)) ||
-        !si->nc_row.ensure(sizeof(int) * (N + 1)))
-        return fail(ctx, DMTS_E_OOM, "state allocation failed");
-    atom_rep_map(sys->rep_off, sys->n_replicas, N, (int *)si->atom_rep.p, st);
-    k_set_int<<<1, 1, 0, st>>>((int *)si->gate.p, 1);
-    SysView v = state_view(stt);
-    NbrWork nw;
-    s = prepare_nbr_work(ctx, si->scratch, v, si->grids, si->n_cells, (int *)si->gate.p, nw);
-    if (s != DMTS_OK) return s;
-    nbr_cells(nw, si->r_cons, st);
-    // size the lists from a count pass
-    nbr_fill(nw, si->r_cons, (int *)si->cons_row.p, nullptr, -1, nullptr, st);
-    long long tot = 0;
-    cudaMemcpyAsync(&tot, nw.total, sizeof(long long), cudaMemcpyDeviceToHost, st);
-    if (!ck(ctx, cudaStreamSynchronize(st), "list sizing")) return DMTS_E_CUDA;
-    si->cons_cap = (long long)(tot * 1.4) + 16LL * N + 1024;
-    const double frac = ctx->has_nc ? std::pow(si->r_nc / si->r_cons, 3.0) : 0.0;
-    si->nc_cap = (long long)(tot * frac * 1.6) + 16LL * N + 1024;
-    if (!si->cons_col.ensure(sizeof(int) * si->cons_cap) || !si->nc_col.ensure(sizeof(int) * si->nc_cap))
-        return fail(ctx, DMTS_E_OOM, "neighbour list allocation failed");
-    rebuild_lists(ctx, si, v, st);
-    if (!ck(ctx, cudaStreamSynchronize(st), "initial lists")) return DMTS_E_CUDA;
-    int err = 0;
-    cudaMemcpy(&err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost);
-    if (err) return fail(ctx, (dmts_status)err, "initial neighbour build failed");
-    return DMTS_OK;
-}
-
 
 static void gamma_consts(const dmts_integrator *p, double dt, float *c1, float *c2) {
     for (int s = 0; s < DMTS_MAX_SPECIES; ++s) {

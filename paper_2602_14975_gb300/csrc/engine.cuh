@@ -130,3 +130,8 @@ RepTable rep_table(const dmts_ctx *ctx);
 void rebuild_lists(dmts_ctx *ctx, StateInternal *si, const SysView &v, cudaStream_t st);
 void prepare_nbr_work_async(dmts_ctx *ctx, StateInternal *si, const SysView &v, NbrWork &nw);
 }  // namespace dmts
+
+// (Re)initialises st->internal for the current shape of st->sys, re-using
+// its buffers when present; leaves the lists built for the current positions.
+dmts_status init_state(dmts_ctx *ctx, dmts_state *stt, float skin, cudaStream_t st);
+void free_state_internal(dmts::StateInternal *si);

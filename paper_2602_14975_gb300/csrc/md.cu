@@ -70,6 +70,33 @@ __device__ __forceinline__ void bond_force(const BondTable &b, const float *x, i
     }
 }
 
+// Visits the active entries of a neighbour row (those with pred(j) true)
+// such that the g-th active entry, in row order, is handled by lane g % 32.
+// Which lane sums which edge then depends only on the active edges, not on
+// the extra skin entries a list happens to hold, so warp-level sums are
+// reproducible whenever the list was rebuilt. fn(j) runs on the owning lane.
+template <typename Pred, typename Fn>
+__device__ __forceinline__ void for_active_canonical(const int *col, int beg, int end, int *queue, int lane,
+                                                     Pred pred, Fn fn) {
+    int queued = 0, taken = 0;
+    for (int base = beg; base < end; base += 32) {
+        const int e = base + lane;
+        const int j = e < end ? col[e] : -1;
+        const bool act = j >= 0 && pred(j);
+        const unsigned m = __ballot_sync(DMTS_FULL, act);
+        if (act) queue[(queued + __popc(m & ((1u << lane) - 1u))) & 63] = j;
+        queued += __popc(m);
+        __syncwarp();
+        if (queued - taken >= 32) {
+            fn(queue[(taken + lane) & 63]);
+            taken += 32;
+        }
+        __syncwarp();
+    }
+    if (taken + lane < queued) fn(queue[(taken + lane) & 63]);
+    __syncwarp();
+}
+
 __device__ __forceinline__ bool is_bonded(const BondTable &b, int a, int j) {
     for (int q = b.ptr[a]; q < b.ptr[a + 1]; ++q)
         if (b.idx[q] == j) return true;
@@ -106,6 +133,7 @@ __global__ void __launch_bounds__(128) k_nc_head(NCHeadArgs g) {
     constexpr int H = K + NL, QKW = 2 * H * NC;
     __shared__ float sh_qk[4][QKW];
     __shared__ float sh_v[4][NL * 3];
+    __shared__ int sh_queue[4][64];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int a = blockIdx.x * 4 + warp;
     if (a >= g.n_atoms || *g.err) return;
@@ -122,13 +150,20 @@ __global__ void __launch_bounds__(128) k_nc_head(NCHeadArgs g) {
     const float rep2 = g.rep.rc * g.rep.rc;
     const int sa = g.species[a];
     float fx = 0.f, fy = 0.f, fz = 0.f, rx = 0.f, ry = 0.f, rz = 0.f;
-    for (int e = g.row_ptr[a] + lane; e < g.row_ptr[a + 1]; e += 32) {
-        const int j = g.col[e];
-        const float dx = min_img(__ldg(g.x + 3 * j) - xa, bx, ibx);
-        const float dy = min_img(__ldg(g.x + 3 * j + 1) - ya, by, iby);
-        const float dz = min_img(__ldg(g.x + 3 * j + 2) - za, bz, ibz);
+    auto disp = [&](int j, float &dx, float &dy, float &dz) {
+        dx = min_img(__ldg(g.x + 3 * j) - xa, bx, ibx);
+        dy = min_img(__ldg(g.x + 3 * j + 1) - ya, by, iby);
+        dz = min_img(__ldg(g.x + 3 * j + 2) - za, bz, ibz);
+    };
+    auto active = [&](int j) {
+        float dx, dy, dz;
+        disp(j, dx, dy, dz);
+        return dx * dx + dy * dy + dz * dz < rc2;
+    };
+    auto edge = [&](int j) {
+        float dx, dy, dz;
+        disp(j, dx, dy, dz);
         const float r2 = dx * dx + dy * dy + dz * dz;
-        if (!(r2 < rc2)) continue;
         const float r = sqrtf(r2), inv = 1.f / r;
         if (with_rep && r2 < rep2 && !is_bonded(g.bonds, a, j)) {
             float dE;
@@ -176,7 +211,8 @@ __global__ void __launch_bounds__(128) k_nc_head(NCHeadArgs g) {
         fx += pa * (nx + vax) - pj * (-nx + vjx);
         fy += pa * (ny + vay) - pj * (-ny + vjy);
         fz += pa * (nz + vaz) - pj * (-nz + vjz);
-    }
+    };
+    for_active_canonical(g.col, g.row_ptr[a], g.row_ptr[a + 1], sh_queue[warp], lane, active, edge);
     fx = fmaf(g.scale, fx, rx); fy = fmaf(g.scale, fy, ry); fz = fmaf(g.scale, fz, rz);
     if (g.bonds.ptr) {
         float e = 0.f;
@@ -239,6 +275,7 @@ void launch_mean_sub(const float *F_in, float *F_out, const int *rep_off, int n_
 // are not bonded; LJ between heavy atoms of different molecules,
 // 4 eps ((s/r)^12 - (s/r)^6) f(r/lj_rc; p); plus bonds.
 __global__ void __launch_bounds__(128) k_prior(PriorArgs g) {
+    __shared__ int sh_queue[4][64];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int a = blockIdx.x * 4 + warp;
     if (a >= g.n_atoms || *g.err) return;
@@ -249,15 +286,24 @@ __global__ void __launch_bounds__(128) k_prior(PriorArgs g) {
     float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
     const int sa = g.species[a], ma = g.mol_id[a];
     const float rc2 = g.lj_rc * g.lj_rc, inv_rc = 1.f / g.lj_rc, s2 = g.lj_sigma * g.lj_sigma;
-    const float rep2 = g.rep.rc * g.rep.rc;
-    for (int q = g.row_ptr[a] + lane; q < g.row_ptr[a + 1]; q += 32) {
-        const int j = g.col[q];
-        const float dx = min_img(g.x[3 * j] - xa, bx, ibx);
-        const float dy = min_img(g.x[3 * j + 1] - ya, by, iby);
-        const float dz = min_img(g.x[3 * j + 2] - za, bz, ibz);
+    const float rep2 = g.rep.on ? g.rep.rc * g.rep.rc : 0.f;
+    const float cut2 = fmaxf(rc2, rep2);
+    auto disp = [&](int j, float &dx, float &dy, float &dz) {
+        dx = min_img(g.x[3 * j] - xa, bx, ibx);
+        dy = min_img(g.x[3 * j + 1] - ya, by, iby);
+        dz = min_img(g.x[3 * j + 2] - za, bz, ibz);
+    };
+    auto active = [&](int j) {
+        float dx, dy, dz;
+        disp(j, dx, dy, dz);
+        return dx * dx + dy * dy + dz * dz < cut2;
+    };
+    auto edge = [&](int j) {
+        float dx, dy, dz;
+        disp(j, dx, dy, dz);
         const float r2 = dx * dx + dy * dy + dz * dz;
         const int sj = g.species[j];
-        if (g.rep.on && r2 < rep2 && !is_bonded(g.bonds, a, j)) {
+        if (r2 < rep2 && !is_bonded(g.bonds, a, j)) {
             const float r = sqrtf(r2);
             float dE;
             const float E = rep_pair(g.rep, sa, sj, r, &dE);
@@ -265,21 +311,19 @@ __global__ void __launch_bounds__(128) k_prior(PriorArgs g) {
             fx += c * dx; fy += c * dy; fz += c * dz;
             e += 0.5f * E;
         }
-        {
-            if (sa == 0 || sj == 0 || g.mol_id[j] == ma) continue;
-            if (!(r2 < rc2)) continue;
-            const float r = sqrtf(r2);
-            const float sr2 = s2 / r2, sr6 = sr2 * sr2 * sr2;
-            const float elj = 4.f * g.lj_eps * (sr6 * sr6 - sr6);
-            const float delj = 4.f * g.lj_eps * (-12.f * sr6 * sr6 + 6.f * sr6) / r;
-            float du;
-            const float fc = envelope(r * inv_rc, g.lj_p, &du);
-            const float dE = delj * fc + elj * du * inv_rc;     // dE/dr
-            const float c = dE / r;                             // F_a = E'(r) d / r
-            fx += c * dx; fy += c * dy; fz += c * dz;
-            e += 0.5f * elj * fc;
-        }
-    }
+        if (sa == 0 || sj == 0 || g.mol_id[j] == ma || !(r2 < rc2)) return;
+        const float r = sqrtf(r2);
+        const float sr2 = s2 / r2, sr6 = sr2 * sr2 * sr2;
+        const float elj = 4.f * g.lj_eps * (sr6 * sr6 - sr6);
+        const float delj = 4.f * g.lj_eps * (-12.f * sr6 * sr6 + 6.f * sr6) / r;
+        float du;
+        const float fc = envelope(r * inv_rc, g.lj_p, &du);
+        const float dE = delj * fc + elj * du * inv_rc;     // dE/dr
+        const float c = dE / r;                             // F_a = E'(r) d / r
+        fx += c * dx; fy += c * dy; fz += c * dz;
+        e += 0.5f * elj * fc;
+    };
+    for_active_canonical(g.col, g.row_ptr[a], g.row_ptr[a + 1], sh_queue[warp], lane, active, edge);
     if (g.bonds.ptr) bond_force(g.bonds, g.x, a, bx, by, bz, ibx, iby, ibz, lane, fx, fy, fz, e);
     fx = warp_sum(fx); fy = warp_sum(fy); fz = warp_sum(fz); e = warp_sum(e);
     if (lane == 0) {
