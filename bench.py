@@ -195,8 +195,7 @@ def main():
     from paper_2602_14975_gb300 import core
 
     sy = W["system"]()
-    cs, ns = W["cons"](), W["nc"]()
-    cs.bf16 = ns.bf16 = False          # this build runs the MLP contractions in fp32
+    cs, ns = W["cons"](), W["nc"]()    # bf16 MLP contractions on the tensor cores
     cb, nb = S.cons_weights(cs, W["w_seed"]), S.nc_weights(ns, W["w_seed"])
     ctx = core.Context(cons=(cs, cb), nc=(ns, nb), device=local)
 
@@ -293,6 +292,39 @@ def main():
     bytes_in = 2 * sy.n_atoms * 12
     bytes_out = 2 * sy.n_atoms * 12 + 8
 
+    # ----------------------------------------------------------- serving
+    # (1) the 23,558-atom system as a request of the serving loop
+    r3 = core.ReplicaRequest(sy, v0, m_hmr, args.steps, I.seed, rank)
+    out3, st3s = core.run_replicas(ctx, [r3], integ)
+    ms_serve = float(np.sum(st3s["tick_ms"])) / max(1, st3s["n_ticks"])
+    # (2) the replica-serving workload: Poisson arrivals of small solvated
+    # molecules, continuous batching, per-tick latency
+    n_req = int(os.environ.get("DMTS_BENCH_REQUESTS", "512"))
+    spec = S.serving_requests(n_req=n_req, seed=401)
+    reqs = []
+    for q in spec:
+        sq = S.capped_molecule_in_droplet(q["n_solute"], seed=q["sys_seed"])
+        mq = core.masses_hmr(sq.species, sq.mol_id, sq.element_masses(), I.hmr_delta)
+        vq = S.maxwell_boltzmann(mq, I.temperature, q["sys_seed"] + 1)
+        reqs.append(core.ReplicaRequest(sq, vq, mq, q["n_outer"], q["rng_seed"], q["id"] + 100000 * rank,
+                                        q["arrival_s"]))
+    barrier()
+    outs, sst = core.run_replicas(ctx, reqs, integ, realtime=True)
+    barrier()
+    tk = sst["tick_ms"]
+    lat = np.array([o["t_done_s"] - o["t_arrival_s"] for o in outs])
+    serving = {
+        "workload": f"{n_req} Poisson requests (200/s), 80-1600 atoms each, 50-2000 outer steps, open droplets",
+        "p50_ms_per_outer_step": float(np.percentile(tk, 50)), "p99_ms_per_outer_step": float(np.percentile(tk, 99)),
+        "ticks": int(sst["n_ticks"]), "wall_s": sst["wall_s"], "max_resident": int(sst["max_resident"]),
+        "atom_outer_steps_per_s": sst["atom_outer_steps"] / sst["wall_s"] * world,
+        "request_latency_s_p50": float(np.percentile(lat, 50)), "request_latency_s_p99": float(np.percentile(lat, 99)),
+        "failed": int(sum(o["status"] != 0 for o in outs)),
+        "solvated_chain_23558_in_loop": {"ns_per_day": ns_per_day(I.dt_outer, 1e3 / ms_serve) * world,
+                                         "ms_per_outer_step": ms_serve,
+                                         "vs_sts": ns_per_day(I.dt_outer, 1e3 / ms_serve) / ns_per_day(sts.dt_outer, 1e3 / ms_sts)},
+    }
+
     # ---------------------------------------------------------- roofline
     peaks = {}
     pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -325,13 +357,14 @@ def main():
     line = {
         "metric": "ns/day (DMTS-NC)", "value": val, "unit": "ns/day", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_dmts, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16" if cs.bf16 else "f32", "data": "synthetic",
         "config": {"workload": sy.name, "n_atoms": sy.n_atoms,
                    "integrator": f"DMTS-NC outer {I.dt_outer} fs / {I.n_inner} inner, HMR +{I.hmr_delta} amu on H, "
                                  f"gamma_H {I.gamma_ps[0]}/ps, gamma_heavy {I.gamma_ps[1]}/ps",
                    "cons_model": f"L={cs.L} C={cs.C} lmax={cs.lmax} K={cs.K} rc={cs.rc}",
                    "nc_model": f"C={ns.C} lmax=1 rc={ns.rc} n_c={ns.n_c} n_l={ns.n_l}",
-                   "precision": "fp32 throughout (bf16 MLP path not built)",
+                   "precision": ("bf16 MLP contractions on the tensor cores (tcgen05, fp32 accumulate), "
+                                 "fp32 everywhere else, fp64 per-replica sums") if cs.bf16 else "fp32",
                    "l2": "inputs larger than L2: about 0.5 GB of node and edge data per outer step",
                    "parallelism": "replicas only (one replica per GPU)"},
         "atom_steps_per_s": sy.n_atoms * 1e3 / ms_dmts * world,
@@ -340,6 +373,7 @@ def main():
         "speedup_vs_sts": val / sts_val,
         "e2e": {"value": ns_per_day(I.dt_outer, 1e3 / ms_e2e) * world, "unit": "ns/day",
                 "h2d_bytes_per_step": bytes_in, "d2h_bytes_per_step": bytes_out, "steps": n_e2e},
+        "serving": serving,
         "gpu_launches": n_launches,
         "clocks": ck,
         "roofline": roof,

@@ -355,6 +355,14 @@ dmts_status dmts_philox_words(dmts_ctx *ctx, uint64_t seed, uint32_t replica, ui
 dmts_status dmts_gaussians(dmts_ctx *ctx, uint64_t seed, uint32_t replica, uint64_t step,
                            uint32_t atom0, int count, float *out, void *stream);
 
+/* One channel-mixing contraction as the MLPs run it in bf16 mode (Sec. 2
+ * "Model architecture": the perceptrons of both models): out[M][N] =
+ * act[M][K] x wt[N][K]^T on the tensor cores, bf16 operands, fp32
+ * accumulation. Device pointers, row-major, 16-byte aligned; K a multiple
+ * of 64, N a multiple of 16, M >= 128, else DMTS_E_INVALID. */
+dmts_status dmts_contract_bf16(dmts_ctx *ctx, int M, int N, int K, const void *act_bf16, const void *wt_bf16,
+                               float *out, void *stream);
+
 /* Bytes of device workspace a replica of n_atoms needs in the serving loop
  * (admission accounting). */
 long long dmts_replica_footprint(const dmts_ctx *ctx, int n_atoms);

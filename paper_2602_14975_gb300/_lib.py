@@ -87,7 +87,8 @@ class ServeStats(ct.Structure):
 EXPORTS = ("dmts_create", "dmts_destroy", "dmts_last_error", "dmts_sync", "nbr_build",
            "energy_forces_cons", "forces_nc", "respa_step", "dmts_state_release", "run_replicas",
            "dmts_masses_hmr", "dmts_bond_table", "dmts_philox_words", "dmts_gaussians",
-           "dmts_replica_footprint", "dmts_profile_enable", "dmts_profile_read", "nbr_build_noalloc")
+           "dmts_replica_footprint", "dmts_profile_enable", "dmts_profile_read", "nbr_build_noalloc",
+           "dmts_contract_bf16")
 
 
 def lib_path() -> str:
@@ -127,6 +128,8 @@ def _declare(L):
     L.dmts_gaussians.argtypes = [vp, ct.c_uint64, ct.c_uint32, ct.c_uint64, ct.c_uint32, i, vp, vp]
     L.dmts_replica_footprint.restype = ct.c_longlong
     L.dmts_replica_footprint.argtypes = [vp, i]
+    L.dmts_contract_bf16.restype = i
+    L.dmts_contract_bf16.argtypes = [vp, i, i, i, vp, vp, vp, vp]
     L.nbr_build_noalloc.restype = i
     L.nbr_build_noalloc.argtypes = [ct.POINTER(System), ct.POINTER(Nbr), ct.POINTER(ct.c_longlong), vp]
     L.dmts_profile_enable.restype = i

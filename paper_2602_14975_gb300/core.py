@@ -339,3 +339,15 @@ def run_replicas(ctx: Context, requests, integ: L.Integrator, hbm_budget_bytes: 
 
 def replica_footprint(ctx: Context, n_atoms: int) -> int:
     return int(ctx.lib.dmts_replica_footprint(ctx.handle, int(n_atoms)))
+
+
+def contract_bf16(ctx: Context, act: torch.Tensor, wt: torch.Tensor) -> torch.Tensor:
+    """out = act @ wt.T on the tensor cores (bf16 operands, fp32 accumulate)."""
+    assert act.dtype == torch.bfloat16 and wt.dtype == torch.bfloat16
+    act, wt = act.contiguous(), wt.contiguous()
+    M, K = act.shape
+    N = wt.shape[0]
+    out = torch.empty(M, N, dtype=torch.float32, device=act.device)
+    L.check(ctx.lib.dmts_contract_bf16(ctx.handle, M, N, K, _ptr(act), _ptr(wt), _ptr(out), _stream(act.device)),
+            ctx.handle)
+    return out

@@ -51,6 +51,15 @@ void Buf::release() {
     cap = 0;
 }
 
+// float -> bf16 bits, round to nearest even (NaN kept quiet)
+static uint16_t bf16_bits(float f) {
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    if ((u & 0x7fffffffu) > 0x7f800000u) return 0x7fc0;
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
 static bool upload(DevModel &m, const std::vector<float> &h) {
     if (cudaMalloc(&m.dev, h.size() * sizeof(float)) != cudaSuccess) return false;
     return cudaMemcpy(m.dev, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess;
@@ -80,7 +89,8 @@ static dmts_status load_model(dmts_ctx *ctx, const dmts_model *in, bool is_nc, D
     if (!(m.rc > 0.f)) return fail(ctx, DMTS_E_INVALID, "rc must be positive");
     if (is_nc && (C > 64 || m.nc != 8 || m.nl < 1 || m.nl > 4))
         return fail(ctx, DMTS_E_INVALID, "NC model: C <= 64, n_c = 8, 1 <= n_l <= 4");
-    if (m.bf16) return fail(ctx, DMTS_E_INVALID, "bf16 MLP contractions are not built into this library");
+    if (m.bf16 && (C < 64 || (is_nc && C != 64)))
+        return fail(ctx, DMTS_E_INVALID, "bf16 MLP contractions need C >= 64 (K-chunks of 64)");
     long long expect;
     if (!is_nc)
         expect = (long long)S * C + (long long)m.L * (NL * K * C + NL * C * C + C + C * C + C) + C * C + 2 * C;
@@ -111,6 +121,49 @@ static dmts_status load_model(dmts_ctx *ctx, const dmts_model *in, bool is_nc, D
         const int H = K + m.nl;
         m.U = take((size_t)m.nl * C);
         m.Wqk = take((size_t)2 * H * m.nc * C);   // Wq rows then Wk rows: one [2 H n_c][C] matrix
+    }
+    if (m.bf16) {
+        // host copies rounded to bf16 (round to nearest even), K-major
+        std::vector<uint16_t> hb;
+        auto off_of = [&](const float *p) { return (size_t)(p - m.dev); };
+        auto push = [&](const float *p, int rows, int cols, bool transpose) {
+            const size_t start = hb.size();
+            const float *src = h.data() + off_of(p);
+            hb.resize(start + (size_t)rows * cols);
+            for (int r = 0; r < rows; ++r)
+                for (int c = 0; c < cols; ++c)
+                    hb[start + (transpose ? (size_t)c * rows + r : (size_t)r * cols + c)] = bf16_bits(src[(size_t)r * cols + c]);
+            return start;
+        };
+        std::vector<size_t> o_w1(m.L), o_w2(m.L), o_w1t(m.L), o_w2t(m.L);
+        for (int t = 0; t < m.L; ++t) {
+            o_w1[t] = push(m.w1[t], C, NL * C, false);
+            o_w2[t] = push(m.w2[t], C, C, false);
+            o_w1t[t] = push(m.w1[t], C, NL * C, true);
+            o_w2t[t] = push(m.w2[t], C, C, true);
+        }
+        size_t o_wr = 0, o_wrt = 0, o_qk = 0;
+        if (!is_nc) {
+            o_wr = push(m.wr, C, C, false);
+            o_wrt = push(m.wr, C, C, true);
+        } else {
+            o_qk = push(m.Wqk, 2 * (K + m.nl) * m.nc, C, false);
+        }
+        if (cudaMalloc(&m.dev_bf, hb.size() * 2) != cudaSuccess ||
+            cudaMemcpy(m.dev_bf, hb.data(), hb.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(ctx, DMTS_E_OOM, "bf16 weight upload failed");
+        for (int t = 0; t < m.L; ++t) {
+            m.w1_bf[t] = m.dev_bf + o_w1[t];
+            m.w2_bf[t] = m.dev_bf + o_w2[t];
+            m.w1t_bf[t] = m.dev_bf + o_w1t[t];
+            m.w2t_bf[t] = m.dev_bf + o_w2t[t];
+        }
+        if (!is_nc) {
+            m.wr_bf = m.dev_bf + o_wr;
+            m.wrt_bf = m.dev_bf + o_wrt;
+        } else {
+            m.wqk_bf = m.dev_bf + o_qk;
+        }
     }
     return DMTS_OK;
 }
@@ -155,6 +208,20 @@ static Epi epi(int mode) {
     return e;
 }
 
+// One node-level contraction: tensor cores (bf16 operands) when the model
+// runs its MLPs in bf16 and the shape allows, else the fp32 SIMT kernel.
+// trans/W32 describe the fp32 weight, Wt16 the K-major bf16 copy.
+static void contract(dmts_ctx *ctx, const DevModel &m, int M, int N, int K, const float *A32,
+                     const __nv_bfloat16 *A16, const float *W32, int trans, const __nv_bfloat16 *Wt16, const Epi &e,
+                     cudaStream_t st, const char *tag_tc, const char *tag_f32) {
+    if (m.bf16 && A16 && Wt16 && M >= 128 && gemm_tc_supported(N, K)) {
+        ProfScope ps(ctx, tag_tc, st);
+        if (launch_gemm_tc(M, N, K, A16, Wt16, e, ctx->d_err, st) == 0) return;
+    }
+    ProfScope ps(ctx, tag_f32, st);
+    launch_gemm_f32(M, N, K, A32, W32, trans, e, st);
+}
+
 // U_MP (+ prior) and F = -grad U for a batch.
 dmts_status cons_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const int *col, double *energy,
                       float *forces, int flags, cudaStream_t st) {
@@ -162,6 +229,7 @@ dmts_status cons_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const
     const int N = s.n, C = m.C, L = m.L, NL = m.lmax + 1, NLM = NL * NL;
     Workspace &w = ctx->ws;
     const size_t nc_ = (size_t)N * C;
+    const bool bf = m.bf16;
     if (!w.s.ensure(sizeof(float) * nc_ * (L + 1)) || !w.A.ensure(sizeof(float) * nc_ * NLM * L) ||
         !w.q.ensure(sizeof(float) * nc_ * NL) || !w.h.ensure(sizeof(float) * nc_ * L) ||
         !w.act.ensure(sizeof(float) * nc_) || !w.u.ensure(sizeof(float) * nc_) || !w.gz.ensure(sizeof(float) * nc_) ||
@@ -169,10 +237,16 @@ dmts_status cons_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const
         !w.gA.ensure(sizeof(float) * nc_ * NLM) || !w.e_atom.ensure(sizeof(float) * (N + 1)) ||
         !w.ftmp.ensure(sizeof(float) * 3 * (N + 1)))
         return fail(ctx, DMTS_E_OOM, "workspace allocation failed");
+    if (bf && (!w.q_bf.ensure(2 * nc_ * NL + 16) || !w.act_bf.ensure(2 * nc_ + 16) || !w.s_bf.ensure(2 * nc_ + 16) ||
+               !w.gz_bf.ensure(2 * nc_ + 16) || !w.gs0_bf.ensure(2 * nc_ + 16) || !w.gs1_bf.ensure(2 * nc_ + 16)))
+        return fail(ctx, DMTS_E_OOM, "workspace allocation failed");
     float *S = (float *)w.s.p, *A = (float *)w.A.p, *q = (float *)w.q.p, *H = (float *)w.h.p;
     float *act = (float *)w.act.p, *u = (float *)w.u.p, *gz = (float *)w.gz.p;
     float *gs0 = (float *)w.gs0.p, *gs1 = (float *)w.gs1.p, *gA = (float *)w.gA.p;
     float *e_atom = (float *)w.e_atom.p;
+    __nv_bfloat16 *q_bf = bf ? (__nv_bfloat16 *)w.q_bf.p : nullptr, *act_bf = bf ? (__nv_bfloat16 *)w.act_bf.p : nullptr;
+    __nv_bfloat16 *s_bf = bf ? (__nv_bfloat16 *)w.s_bf.p : nullptr, *gz_bf = bf ? (__nv_bfloat16 *)w.gz_bf.p : nullptr;
+    __nv_bfloat16 *gs0_bf = bf ? (__nv_bfloat16 *)w.gs0_bf.p : nullptr, *gs1_bf = bf ? (__nv_bfloat16 *)w.gs1_bf.p : nullptr;
     const EdgeGeom g = edge_geom(s, row_ptr, col, m);
     { ProfScope ps(ctx, "embed", st); launch_embed(N, C, s.species, m.emb, S, st); }
     for (int t = 0; t < L; ++t) {
@@ -183,18 +257,21 @@ dmts_status cons_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const
         io.nu = m.nu;
         io.A = A + nc_ * NLM * t;
         io.q = q;
+        io.q_bf16 = q_bf;
         io.err = ctx->d_err;
         { ProfScope ps(ctx, "mp_fwd", st); launch_mp_fwd(C, m.lmax, m.K, g, io, st); }
         Epi e1 = epi(EPI_BIAS_SILU);
         e1.bias = m.b1[t];
         e1.H = H + nc_ * t;
         e1.out = act;
-        { ProfScope ps(ctx, "gemm", st); launch_gemm_f32(N, C, NL * C, q, m.w1[t], 1, e1, st); }
+        e1.out_bf16 = act_bf;
+        contract(ctx, m, N, C, NL * C, q, q_bf, m.w1[t], 1, m.w1_bf[t], e1, st, "gemm_tc", "gemm");
         Epi e2 = epi(EPI_RESID);
         e2.bias = m.b2[t];
         e2.res = S + nc_ * t;
         e2.out = S + nc_ * (t + 1);
-        { ProfScope ps(ctx, "gemm", st); launch_gemm_f32(N, C, C, act, m.w2[t], 1, e2, st); }
+        e2.out_bf16 = t == L - 1 ? s_bf : nullptr;
+        contract(ctx, m, N, C, C, act, act_bf, m.w2[t], 1, m.w2_bf[t], e2, st, "gemm_tc", "gemm");
     }
     Epi er = epi(EPI_READOUT);
     er.bias = m.br;
@@ -202,25 +279,29 @@ dmts_status cons_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const
     er.scale = m.scale;
     er.out = u;
     er.out2 = gz;
-    { ProfScope ps(ctx, "gemm", st); launch_gemm_f32(N, C, C, S + nc_ * L, m.wr, 1, er, st); }
+    er.out_bf16 = gz_bf;
+    contract(ctx, m, N, C, C, S + nc_ * L, s_bf, m.wr, 1, m.wr_bf, er, st, "gemm_tc", "gemm");
     { ProfScope ps(ctx, "rowsum", st); launch_rowsum(N, C, u, m.scale, e_atom, st); }
     if (forces) {
         // dU/ds^L = gz Wr
         Epi eg = epi(EPI_STORE);
         eg.out = gs0;
-        { ProfScope ps(ctx, "gemm", st); launch_gemm_f32(N, C, C, gz, m.wr, 0, eg, st); }
+        eg.out_bf16 = gs0_bf;
+        contract(ctx, m, N, C, C, gz, gz_bf, m.wr, 0, m.wrt_bf, eg, st, "gemm_tc", "gemm");
         float *gin = gs0, *gout = gs1;
+        __nv_bfloat16 *gin_bf = gs0_bf, *gout_bf = gs1_bf;
         for (int t = L - 1; t >= 0; --t) {
             Epi ed = epi(EPI_DSILU);
             ed.H = H + nc_ * t;
             ed.out = act;                       // g_h
-            { ProfScope ps(ctx, "gemm", st); launch_gemm_f32(N, C, C, gin, m.w2[t], 0, ed, st); }
+            ed.out_bf16 = act_bf;
+            contract(ctx, m, N, C, C, gin, gin_bf, m.w2[t], 0, m.w2t_bf[t], ed, st, "gemm_tc", "gemm");
             Epi ea = epi(EPI_GA);
             ea.A = A + nc_ * NLM * t;
             ea.out = gA;
             ea.C = C;
             ea.lmax = m.lmax;
-            { ProfScope ps(ctx, "gemm", st); launch_gemm_f32(N, NL * C, C, act, m.w1[t], 0, ea, st); }
+            contract(ctx, m, N, NL * C, C, act, act_bf, m.w1[t], 0, m.w1t_bf[t], ea, st, "gemm_tc", "gemm");
             LayerIO io;
             memset(&io, 0, sizeof io);
             io.s = S + nc_ * t;
@@ -229,11 +310,13 @@ dmts_status cons_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const
             io.gA = gA;
             io.gs_in = gin;
             io.gs_out = gout;
+            io.gs_out_bf16 = t > 0 ? gout_bf : nullptr;
             io.F = forces;
             io.accumulate = t != L - 1;
             io.err = ctx->d_err;
             { ProfScope ps(ctx, "mp_bwd", st); launch_mp_bwd(C, m.lmax, m.K, g, io, st); }
             std::swap(gin, gout);
+            std::swap(gin_bf, gout_bf);
         }
     }
     if (flags & DMTS_WITH_PRIOR) {
@@ -262,18 +345,24 @@ dmts_status cons_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const
     return DMTS_OK;
 }
 
-// F_NC (+ bonds), mean-subtracted; net = per-replica sum before subtraction.
+// F_NC (+ bonds, F_rep), mean-subtracted; net = per-replica sum before subtraction.
 dmts_status nc_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const int *col, float *forces,
                     double *net, int flags, cudaStream_t st) {
     const DevModel &m = ctx->nc;
     const int N = s.n, C = m.C, H = m.K + m.nl, QKW = 2 * H * m.nc;
     Workspace &w = ctx->ws;
     const size_t nc_ = (size_t)N * C;
+    const bool bf = m.bf16;
     if (!w.nc_s.ensure(sizeof(float) * nc_ * 2) || !w.nc_A.ensure(sizeof(float) * nc_ * 4) ||
         !w.nc_q.ensure(sizeof(float) * nc_ * 2) || !w.nc_h.ensure(sizeof(float) * nc_) ||
         !w.nc_act.ensure(sizeof(float) * nc_) || !w.nc_qk.ensure(sizeof(float) * (size_t)N * QKW) ||
         !w.nc_v.ensure(sizeof(float) * (size_t)N * m.nl * 3) || !w.nc_f.ensure(sizeof(float) * 3 * (N + 1)))
         return fail(ctx, DMTS_E_OOM, "workspace allocation failed");
+    if (bf && (!w.nc_q_bf.ensure(2 * nc_ * 2 + 16) || !w.nc_act_bf.ensure(2 * nc_ + 16) || !w.nc_s_bf.ensure(2 * nc_ + 16)))
+        return fail(ctx, DMTS_E_OOM, "workspace allocation failed");
+    __nv_bfloat16 *q_bf = bf ? (__nv_bfloat16 *)w.nc_q_bf.p : nullptr;
+    __nv_bfloat16 *act_bf = bf ? (__nv_bfloat16 *)w.nc_act_bf.p : nullptr;
+    __nv_bfloat16 *s_bf = bf ? (__nv_bfloat16 *)w.nc_s_bf.p : nullptr;
     float *s0 = (float *)w.nc_s.p, *s1 = s0 + nc_;
     const EdgeGeom g = edge_geom(s, row_ptr, col, m);
     { ProfScope ps(ctx, "embed", st); launch_embed(N, C, s.species, m.emb, s0, st); }
@@ -284,21 +373,24 @@ dmts_status nc_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const i
     io.nu = m.nu;
     io.A = (float *)w.nc_A.p;
     io.q = (float *)w.nc_q.p;
+    io.q_bf16 = q_bf;
     io.err = ctx->d_err;
     { ProfScope ps(ctx, "nc_mp_fwd", st); launch_mp_fwd(C, 1, m.K, g, io, st); }
     Epi e1 = epi(EPI_BIAS_SILU);
     e1.bias = m.b1[0];
     e1.H = (float *)w.nc_h.p;
     e1.out = (float *)w.nc_act.p;
-    { ProfScope ps(ctx, "nc_gemm", st); launch_gemm_f32(N, C, 2 * C, io.q, m.w1[0], 1, e1, st); }
+    e1.out_bf16 = act_bf;
+    contract(ctx, m, N, C, 2 * C, io.q, q_bf, m.w1[0], 1, m.w1_bf[0], e1, st, "nc_gemm_tc", "nc_gemm");
     Epi e2 = epi(EPI_RESID);
     e2.bias = m.b2[0];
     e2.res = s0;
     e2.out = s1;
-    { ProfScope ps(ctx, "nc_gemm", st); launch_gemm_f32(N, C, C, (float *)w.nc_act.p, m.w2[0], 1, e2, st); }
+    e2.out_bf16 = s_bf;
+    contract(ctx, m, N, C, C, (float *)w.nc_act.p, act_bf, m.w2[0], 1, m.w2_bf[0], e2, st, "nc_gemm_tc", "nc_gemm");
     Epi e3 = epi(EPI_STORE);
     e3.out = (float *)w.nc_qk.p;
-    { ProfScope ps(ctx, "nc_gemm", st); launch_gemm_f32(N, QKW, C, s1, m.Wqk, 1, e3, st); }
+    contract(ctx, m, N, QKW, C, s1, s_bf, m.Wqk, 1, m.wqk_bf, e3, st, "nc_gemm_tc", "nc_gemm");
     { ProfScope ps(ctx, "nc_vectors", st); launch_nc_vectors(N, C, m.nl, io.A, m.U, (float *)w.nc_v.p, ctx->d_err, st); }
     NCHeadArgs a;
     a.x = s.x;
@@ -584,6 +676,8 @@ void dmts_destroy(dmts_ctx *ctx) {
     cudaDeviceSynchronize();
     if (ctx->cons.dev) cudaFree(ctx->cons.dev);
     if (ctx->nc.dev) cudaFree(ctx->nc.dev);
+    if (ctx->cons.dev_bf) cudaFree(ctx->cons.dev_bf);
+    if (ctx->nc.dev_bf) cudaFree(ctx->nc.dev_bf);
     if (ctx->d_err) cudaFree(ctx->d_err);
     ctx->ws.release_all();
     ctx->nbr_scratch.release_all();
@@ -854,6 +948,21 @@ dmts_status dmts_bond_table(int n_atoms, int n_bonds, const int *bonds, const fl
         r0_out[fill[j]++] = r0[b];
     }
     return DMTS_OK;
+}
+
+dmts_status dmts_contract_bf16(dmts_ctx *ctx, int M, int N, int K, const void *act, const void *wt, float *out,
+                               void *stream) {
+    if (!ctx || !act || !wt || !out || M < 128 || !gemm_tc_supported(N, K))
+        return fail(ctx, DMTS_E_INVALID, "dmts_contract_bf16: needs M >= 128, K % 64 == 0, N % 16 == 0");
+    cudaSetDevice(ctx->device);
+    Epi e;
+    memset(&e, 0, sizeof e);
+    e.mode = EPI_STORE;
+    e.out = out;
+    const int r = launch_gemm_tc(M, N, K, (const __nv_bfloat16 *)act, (const __nv_bfloat16 *)wt, e, ctx->d_err,
+                                 (cudaStream_t)stream);
+    if (r != 0) return fail(ctx, DMTS_E_INVALID, "dmts_contract_bf16: unaligned operand or tensor map failure");
+    return ck(ctx, cudaGetLastError(), "dmts_contract_bf16 launch") ? DMTS_OK : DMTS_E_CUDA;
 }
 
 __global__ void k_philox_words(uint64_t seed, uint32_t rep, uint64_t step, uint32_t atom0, int count, uint32_t *out) {

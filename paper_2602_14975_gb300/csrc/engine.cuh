@@ -27,6 +27,12 @@ struct DevModel {
           *w2[DMTS_MAX_LAYERS] = {}, *b2[DMTS_MAX_LAYERS] = {};
     float *wr = nullptr, *br = nullptr, *wo = nullptr;
     float *U = nullptr, *Wqk = nullptr;
+    // bf16 copies for the tensor-core contractions, every one K-major
+    // ([out][in]): W1, W2, Wr (forward), their transposes (adjoint), Wqk.
+    __nv_bfloat16 *dev_bf = nullptr;
+    __nv_bfloat16 *w1_bf[DMTS_MAX_LAYERS] = {}, *w2_bf[DMTS_MAX_LAYERS] = {}, *w1t_bf[DMTS_MAX_LAYERS] = {},
+                  *w2t_bf[DMTS_MAX_LAYERS] = {};
+    __nv_bfloat16 *wr_bf = nullptr, *wrt_bf = nullptr, *wqk_bf = nullptr;
 };
 
 struct NbrScratch {
@@ -40,9 +46,12 @@ struct NbrScratch {
 struct Workspace {
     Buf s, A, q, h, act, u, gz, gs0, gs1, gA, e_atom, ftmp, atom_rep;
     Buf nc_s, nc_A, nc_q, nc_h, nc_act, nc_qk, nc_v, nc_f;
+    // bf16 operands of the tensor-core contractions
+    Buf q_bf, act_bf, s_bf, gz_bf, gs0_bf, gs1_bf, nc_q_bf, nc_act_bf, nc_s_bf;
     void release_all() {
         Buf *all[] = {&s, &A, &q, &h, &act, &u, &gz, &gs0, &gs1, &gA, &e_atom, &ftmp, &atom_rep,
-                      &nc_s, &nc_A, &nc_q, &nc_h, &nc_act, &nc_qk, &nc_v, &nc_f};
+                      &nc_s, &nc_A, &nc_q, &nc_h, &nc_act, &nc_qk, &nc_v, &nc_f,
+                      &q_bf, &act_bf, &s_bf, &gz_bf, &gs0_bf, &gs1_bf, &nc_q_bf, &nc_act_bf, &nc_s_bf};
         for (Buf *b : all) b->release();
     }
 };

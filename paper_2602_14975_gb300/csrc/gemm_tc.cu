@@ -1,0 +1,399 @@
+// Node-level MLP contractions on the 5th-generation tensor cores:
+// Out[M][N] = Act[M][K] x W^T with bf16 operands and an fp32 accumulator in
+// tensor memory, followed by the same fused epilogues as the fp32 GEMM.
+//
+// One CTA (eight warps) computes a 128 x BN tile (BN <= 256 output columns).
+// Warp 0 (one lane) streams K-chunks of 64 bf16 of the activation tile and of
+// the weight tile into shared memory with TMA (128-byte swizzle), warp 1 (one
+// lane) issues tcgen05.mma (M = 128, N = BN, K = 16 per instruction) into a
+// TMEM accumulator, warp 2 owns the TMEM allocation; warps 0-3 read the
+// accumulator back with tcgen05.ld (warp w reads rows 32w..32w+31) into shared
+// memory and all eight warps apply the epilogue with coalesced accesses. Every wait on an mbarrier is bounded: on timeout the CTA
+// records DMTS_E_TIMEOUT, frees its tensor memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
+#include "mp.cuh"
+
+namespace dmts {
+
+namespace {
+
+constexpr int TC_M = 128;
+constexpr int TC_K = 64;             // bf16 elements per 128-byte swizzled row
+constexpr int TC_STAGES = 4;
+constexpr uint32_t kSpinLimit = 1u << 26;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// Bounded wait for the phase with the given parity; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major tile, 128-byte swizzle, 8-row
+// groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);        // start address
+    d |= (uint64_t)1 << 16;                        // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;              // stride byte offset
+    d |= (uint64_t)1 << 46;                        // descriptor version
+    d |= (uint64_t)2 << 61;                        // 128-byte swizzle
+    return d;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accum));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+__device__ __forceinline__ float silu_d(float v) { return v / (1.f + __expf(-v)); }
+__device__ __forceinline__ float dsilu_d(float v) {
+    const float sg = 1.f / (1.f + __expf(-v));
+    return sg * (1.f + v * (1.f - sg));
+}
+
+// Applies the epilogue to a rows x BN tile held in shared memory. Each
+// thread takes EU elements per pass (row-major, consecutive threads on
+// consecutive columns) and issues all of their global loads before any
+// store, so that many loads are in flight per warp.
+constexpr int EU = 4;
+
+__device__ __forceinline__ void epilogue_tile(const Epi &e, int N, int rows, int m0, int n0, int BN,
+                                              const float *tile, int ld) {
+    const int total = rows * BN;
+    const int step = blockDim.x;
+    for (int base = threadIdx.x; base < total; base += EU * step) {
+        float v[EU];
+        size_t o[EU];
+        int n[EU];
+        bool ok[EU];
+#pragma unroll
+        for (int u = 0; u < EU; ++u) {
+            const int idx = base + u * step;
+            ok[u] = idx < total;
+            const int r = ok[u] ? idx / BN : 0, c = ok[u] ? idx - r * BN : 0;
+            v[u] = ok[u] ? tile[r * ld + c] : 0.f;
+            n[u] = n0 + c;
+            o[u] = (size_t)(m0 + r) * N + n[u];
+        }
+        switch (e.mode) {
+        case EPI_STORE:
+#pragma unroll
+            for (int u = 0; u < EU; ++u)
+                if (ok[u]) {
+                    e.out[o[u]] = v[u];
+                    if (e.out_bf16) e.out_bf16[o[u]] = __float2bfloat16_rn(v[u]);
+                }
+            break;
+        case EPI_BIAS_SILU: {
+            float b[EU];
+#pragma unroll
+            for (int u = 0; u < EU; ++u) b[u] = ok[u] ? __ldg(e.bias + n[u]) : 0.f;
+#pragma unroll
+            for (int u = 0; u < EU; ++u)
+                if (ok[u]) {
+                    const float h = v[u] + b[u];
+                    const float sv = silu_d(h);
+                    e.H[o[u]] = h;
+                    e.out[o[u]] = sv;
+                    if (e.out_bf16) e.out_bf16[o[u]] = __float2bfloat16_rn(sv);
+                }
+            break;
+        }
+        case EPI_RESID: {
+            float rs[EU], b[EU];
+#pragma unroll
+            for (int u = 0; u < EU; ++u) {
+                rs[u] = ok[u] ? __ldg(e.res + o[u]) : 0.f;
+                b[u] = ok[u] ? __ldg(e.bias + n[u]) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < EU; ++u)
+                if (ok[u]) {
+                    const float rr = rs[u] + v[u] + b[u];
+                    e.out[o[u]] = rr;
+                    if (e.out_bf16) e.out_bf16[o[u]] = __float2bfloat16_rn(rr);
+                }
+            break;
+        }
+        case EPI_DSILU: {
+            float h[EU];
+#pragma unroll
+            for (int u = 0; u < EU; ++u) h[u] = ok[u] ? __ldg(e.H + o[u]) : 0.f;
+#pragma unroll
+            for (int u = 0; u < EU; ++u)
+                if (ok[u]) {
+                    const float rr = v[u] * dsilu_d(h[u]);
+                    e.out[o[u]] = rr;
+                    if (e.out_bf16) e.out_bf16[o[u]] = __float2bfloat16_rn(rr);
+                }
+            break;
+        }
+        case EPI_GA: {
+            const int nlm = (e.lmax + 1) * (e.lmax + 1);
+            float a[EU][5];
+            size_t ib[EU];
+            int l0[EU], nm[EU];
+#pragma unroll
+            for (int u = 0; u < EU; ++u) {
+                const int l = n[u] / e.C, c = n[u] - l * e.C;
+                const int m = (int)(o[u] / N);
+                l0[u] = l * l;
+                nm[u] = ok[u] ? 2 * l + 1 : 0;
+                ib[u] = ((size_t)m * nlm + l0[u]) * e.C + c;
+#pragma unroll
+                for (int q = 0; q < 5; ++q) a[u][q] = q < nm[u] ? __ldg(e.A + ib[u] + (size_t)q * e.C) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < EU; ++u)
+#pragma unroll
+                for (int q = 0; q < 5; ++q)
+                    if (q < nm[u]) e.out[ib[u] + (size_t)q * e.C] = 2.f * a[u][q] * v[u];
+            break;
+        }
+        case EPI_READOUT: {
+            float b[EU], w[EU];
+#pragma unroll
+            for (int u = 0; u < EU; ++u) {
+                b[u] = ok[u] ? __ldg(e.bias + n[u]) : 0.f;
+                w[u] = ok[u] ? __ldg(e.wo + n[u]) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < EU; ++u)
+                if (ok[u]) {
+                    const float z = v[u] + b[u];
+                    e.out[o[u]] = w[u] * silu_d(z);
+                    const float gz = e.scale * w[u] * dsilu_d(z);
+                    e.out2[o[u]] = gz;
+                    if (e.out_bf16) e.out_bf16[o[u]] = __float2bfloat16_rn(gz);
+                }
+            break;
+        }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_gemm_tc(const __grid_constant__ CUtensorMap tmA,
+                                                 const __grid_constant__ CUtensorMap tmB, int M, int N, int K,
+                                                 int BN, int tmem_cols, int n_stages, Epi e, int *err) {
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t bar_full[TC_STAGES], bar_empty[TC_STAGES], bar_done;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int abort_sh;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * TC_M, n0 = blockIdx.y * BN;
+    const int nk = K / TC_K;
+    const uint32_t a_bytes = TC_M * TC_K * 2, b_bytes = (uint32_t)BN * TC_K * 2;
+    const uint32_t stage_bytes = a_bytes + ((b_bytes + 1023u) & ~1023u);
+    const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;   // 1024-byte aligned tiles
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(smem_u32(&bar_full[s]), 1);
+            mbar_init(smem_u32(&bar_empty[s]), 1);
+        }
+        mbar_init(smem_u32(&bar_done), 1);
+        abort_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                     "r"(tmem_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base_sh;
+
+    if (warp == 0 && lane == 0) {
+        // ---- TMA producer
+        for (int k = 0; k < nk; ++k) {
+            const int s = k % n_stages;
+            if (k >= n_stages && !mbar_wait(smem_u32(&bar_empty[s]), ((k / n_stages) - 1) & 1)) {
+                atomicExch(&abort_sh, 1);
+                break;
+            }
+            const uint32_t sa = base + s * stage_bytes, sb = sa + a_bytes;
+            mbar_expect_tx(smem_u32(&bar_full[s]), a_bytes + b_bytes);
+            tma_load_2d(sa, &tmA, k * TC_K, m0, smem_u32(&bar_full[s]));
+            tma_load_2d(sb, &tmB, k * TC_K, n0, smem_u32(&bar_full[s]));
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---- MMA issuer
+        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                               ((uint32_t)(TC_M >> 4) << 24);
+        bool ok = true;
+        for (int k = 0; k < nk && ok; ++k) {
+            const int s = k % n_stages;
+            if (!mbar_wait(smem_u32(&bar_full[s]), (k / n_stages) & 1)) {
+                atomicExch(&abort_sh, 1);
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sa = base + s * stage_bytes, sb = sa + a_bytes;
+#pragma unroll
+            for (int kk = 0; kk < TC_K / 16; ++kk)
+                mma_bf16(tmem, smem_desc(sa + kk * 32), smem_desc(sb + kk * 32), idesc, (k > 0 || kk > 0) ? 1u : 0u);
+            mma_commit(smem_u32(&bar_empty[s]));
+        }
+        mma_commit(smem_u32(&bar_done));
+    }
+    __syncwarp();
+    // ---- epilogue: wait for the accumulator, read it back, fused epilogue
+    const bool done = mbar_wait(smem_u32(&bar_done), 0);
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!__syncthreads_and(done ? 1 : 0) || abort_sh) {
+        if (threadIdx.x == 0) atomicCAS(err, 0, (int)DMTS_E_TIMEOUT);
+    } else {
+        // TMEM -> shared memory (the drained pipeline buffers): warps 0-3
+        // each move their 32-lane quarter, one row per lane. Then all eight
+        // warps walk the tile row-major, consecutive threads on consecutive
+        // columns, so the epilogue's loads and stores are coalesced and many
+        // warps hide their latency.
+        const int ld = BN + 1;
+        float *tile = reinterpret_cast<float *>(smem_raw + (base - smem_u32(smem_raw)));
+        if (warp < 4) {
+            float *wtile = tile + (size_t)warp * 32 * ld;
+            const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+            for (int c = 0; c < BN; c += 16) {
+                float v[16];
+                tmem_ld16(trow + (uint32_t)c, v);
+#pragma unroll
+                for (int q = 0; q < 16; ++q) wtile[lane * ld + c + q] = v[q];
+            }
+        }
+        __syncthreads();
+        const int rows = min(TC_M, M - m0);
+        epilogue_tile(e, N, rows, m0, n0, BN, tile, ld);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 2) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
+    }
+}
+
+// ------------------------------------------------------------------- host
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::mutex g_encode_mutex;
+
+bool encode_fn() {
+    std::lock_guard<std::mutex> lock(g_encode_mutex);
+    if (g_encode) return true;
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+        return false;
+    g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    return true;
+}
+
+// 2-D bf16 tensor map over rows x cols (row-major), box of box_rows x 64.
+bool make_map(CUtensorMap *map, const void *ptr, int rows, int cols, int box_rows) {
+    if (!encode_fn()) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)TC_K, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+// Validity of a bf16 tensor-core contraction shape.
+bool gemm_tc_supported(int N, int K) { return K % TC_K == 0 && K > 0 && N % 16 == 0 && N > 0; }
+
+int launch_gemm_tc(int M, int N, int K, const __nv_bfloat16 *Act, const __nv_bfloat16 *Wt, const Epi &e, int *err,
+                   cudaStream_t st) {
+    if (M == 0) return 0;
+    if (!gemm_tc_supported(N, K)) return -1;
+    if (((uintptr_t)Act & 15) || ((uintptr_t)Wt & 15)) return -2;
+    // column tile: whole N up to 256, else the largest multiple of 16 dividing N
+    // column tile: whole N up to 160, else the largest multiple of 16 <= 128
+    // dividing N (a smaller staging tile leaves room for more CTAs per SM)
+    int BN = N;
+    if (BN > 160) {
+        BN = 0;
+        for (int b = 128; b >= 16; b -= 16)
+            if (N % b == 0) { BN = b; break; }
+        if (!BN) return -1;
+    }
+    int tmem_cols = 32;
+    while (tmem_cols < BN) tmem_cols <<= 1;
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, Act, M, K, TC_M) || !make_map(&mb, Wt, N, K, BN)) return -3;
+    const uint32_t stage = TC_M * TC_K * 2 + ((BN * TC_K * 2 + 1023) & ~1023);
+    const int n_stages = std::min(3, K / TC_K);
+    const size_t tile = (size_t)TC_M * (BN + 1) * sizeof(float);   // epilogue staging
+    const size_t smem = std::max((size_t)stage * n_stages, tile) + 1024;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr_set = true;
+    }
+    dim3 grid((M + TC_M - 1) / TC_M, N / BN);
+    k_gemm_tc<<<grid, 256, smem, st>>>(ma, mb, M, N, K, BN, tmem_cols, n_stages, e, err);
+    return 0;
+}
+
+}  // namespace dmts

@@ -241,8 +241,19 @@ __global__ void k_mean_sub(const float *F_in, float *F_out, const int *rep_off, 
     const int r = blockIdx.x;
     const int beg = rep_off[r], end = rep_off[r + 1];
     double s[3] = {0.0, 0.0, 0.0};
-    for (int i = beg + threadIdx.x; i < end; i += blockDim.x)
-        for (int a = 0; a < 3; ++a) s[a] += (double)F_in[3 * i + a];
+    // eight independent loads in flight per thread, then the FP64 adds in order
+    const int stride = blockDim.x;
+    for (int i0 = beg + threadIdx.x; i0 < end; i0 += 8 * stride) {
+        float v[8][3];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = i0 + u * stride;
+            for (int a = 0; a < 3; ++a) v[u][a] = i < end ? F_in[3 * i + a] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            for (int a = 0; a < 3; ++a) s[a] += (double)v[u][a];
+    }
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int a = 0; a < 3; ++a) {
         s[a] = warp_sum_d(s[a]);
@@ -267,7 +278,7 @@ __global__ void k_mean_sub(const float *F_in, float *F_out, const int *rep_off, 
 void launch_mean_sub(const float *F_in, float *F_out, const int *rep_off, int n_rep, double *net,
                      const int *err, cudaStream_t st) {
     if (n_rep == 0) return;
-    k_mean_sub<<<n_rep, 512, 0, st>>>(F_in, F_out, rep_off, net, err);
+    k_mean_sub<<<n_rep, 1024, 0, st>>>(F_in, F_out, rep_off, net, err);
 }
 
 // ---------------------------------------------------------------- prior

@@ -279,6 +279,10 @@ __global__ void __launch_bounds__(MP_WARPS * 32) k_mp_bwd(EdgeGeom g, LayerIO io
 #pragma unroll
     for (int u = 0; u < CPW; ++u) gout[u] = fmaf(io.nu, gsacc[u], gin[u]);
     stv<CPW>(io.gs_out + (size_t)a * C + lane * CPW, gout);
+    if (io.gs_out_bf16) {
+#pragma unroll
+        for (int u = 0; u < CPW; ++u) io.gs_out_bf16[(size_t)a * C + lane * CPW + u] = __float2bfloat16_rn(gout[u]);
+    }
 }
 
 template <int C, int LMAX>
@@ -438,7 +442,14 @@ __global__ void k_replica_sum(const float *__restrict__ v, const int *__restrict
     const int r = blockIdx.x;
     const int beg = rep_off[r], end = rep_off[r + 1];
     double acc = 0.0;
-    for (int i = beg + threadIdx.x; i < end; i += blockDim.x) acc += (double)v[i];
+    const int stride = blockDim.x;
+    for (int i0 = beg + threadIdx.x; i0 < end; i0 += 8 * stride) {
+        float t[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) t[u] = i0 + u * stride < end ? v[i0 + u * stride] : 0.f;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc += (double)t[u];
+    }
     acc = warp_sum_d(acc);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
@@ -452,7 +463,7 @@ __global__ void k_replica_sum(const float *__restrict__ v, const int *__restrict
 void launch_replica_sum(const float *v, const int *rep_off, int n_rep, double *out, int accumulate,
                         cudaStream_t st) {
     if (n_rep == 0) return;
-    k_replica_sum<<<n_rep, 256, 0, st>>>(v, rep_off, out, accumulate);
+    k_replica_sum<<<n_rep, 1024, 0, st>>>(v, rep_off, out, accumulate);
 }
 
 }  // namespace dmts

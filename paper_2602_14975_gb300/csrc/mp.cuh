@@ -28,6 +28,7 @@ struct LayerIO {
     const float *gA;         // [N][NLM][C]  (backward in)
     const float *gs_in;      // [N][C]       (backward in)
     float *gs_out;           // [N][C]       (backward out)
+    __nv_bfloat16 *gs_out_bf16;  // optional bf16 copy of gs_out
     float *F;                // [N][3]       (backward: accumulated forces)
     int accumulate;          // backward: 0 write F, 1 add to F
     const int *err;
@@ -94,9 +95,13 @@ struct Epi {
 // or W for W [K][N] (trans = 0); fp32 SIMT.
 void launch_gemm_f32(int M, int N, int K, const float *Act, const float *W, int trans, const Epi &e,
                      cudaStream_t st);
-// Same contraction with bf16 operands on the tensor cores, fp32 accumulate.
-void launch_gemm_bf16(int M, int N, int K, const __nv_bfloat16 *Act, const __nv_bfloat16 *W, int trans,
-                      const Epi &e, cudaStream_t st);
+// Out[M][N] = Act[M][K] x Wt^T on the tensor cores (tcgen05, bf16 operands,
+// fp32 accumulator in tensor memory), Wt K-major [N][K]. Needs K % 64 == 0,
+// N % 16 == 0, M >= 128 and 16-byte aligned operands; returns 0 when
+// launched, < 0 when the shape is not supported.
+int launch_gemm_tc(int M, int N, int K, const __nv_bfloat16 *Act, const __nv_bfloat16 *Wt, const Epi &e, int *err,
+                   cudaStream_t st);
+bool gemm_tc_supported(int N, int K);
 
 // Per-replica FP64 sums of per-atom values: out[r] = sum_{i in r} v[i].
 void launch_replica_sum(const float *v, const int *rep_off, int n_rep, double *out, int accumulate,

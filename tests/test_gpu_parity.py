@@ -321,3 +321,57 @@ def test_nonfinite_positions_are_reported(ctx1, water):
     assert ei.value.status in (L.E_NONFINITE, L.E_NBR_OVERFLOW, L.E_INVALID)
     st.release()
     ctx1.sync()   # the sticky word is cleared: the context stays usable
+
+
+# ------------------------------------------------------- bf16 tensor cores --
+
+@pytest.mark.parametrize("which", ["water", "chain"])
+def test_bf16_tensor_core_path(which):
+    """MLP contractions in bf16 on the tensor cores: forces within 2e-3 of the
+    force RMS of the oracle (max-abs), energies within 2e-3 relative."""
+    sy = S.water_192() if which == "water" else S.solvated_chain(n_chain=300, n_water=900, box_len=31.0, seed=9)
+    cs = S.cons_spec(3, 128, 2, bf16=True)
+    ns = S.nc_spec(64, rc=4.0, bf16=True)
+    cb, nb_ = S.cons_weights(cs, 302), S.nc_weights(ns, 302)
+    ctx = core.Context(cons=(cs, cb), nc=(ns, nb_))
+    d = core.DeviceSystem(sy)
+    nb = core.nbr_build(ctx, d, 5.5)
+    E, F = core.energy_forces_cons(ctx, d, nb, with_prior=True)
+    Fn, _ = core.forces_nc(ctx, d, nb)
+    E, F, Fn = E.cpu().numpy(), F.cpu().numpy(), Fn.cpu().numpy()
+    Eo, Fo = O.cons_energy_forces(sy, cs, cb)
+    Ep, Fp = O.prior(sy)
+    Ft = Fo + Fp
+    rms = np.sqrt((Ft ** 2).mean())
+    assert np.abs(F - Ft).max() <= 2e-3 * rms
+    assert abs(E[0] - (Eo + Ep)) <= 2e-3 * abs(Eo + Ep)
+    # the message-passing part alone, to see the bf16 error itself
+    _, Fml = core.energy_forces_cons(ctx, d, nb, with_prior=False)
+    Fml = Fml.cpu().numpy()
+    rms_ml = np.sqrt((Fo ** 2).mean())
+    # bf16 rounding of every contraction operand through three layers and
+    # the adjoint: a few per cent of the (small) message-passing force RMS
+    assert np.abs(Fml - Fo).max() <= 1e-1 * rms_ml
+    Fno, _ = O.nc_forces(sy, ns, nb_)
+    assert np.abs(Fn - Fno).max() <= 2e-3 * np.sqrt((Fno ** 2).mean())
+    # fp32 and bf16 contexts agree closely
+    cs32, ns32 = S.cons_spec(3, 128, 2), S.nc_spec(64, rc=4.0)
+    ctx32 = core.Context(cons=(cs32, cb), nc=(ns32, nb_))
+    _, F32 = core.energy_forces_cons(ctx32, d, nb, with_prior=False)
+    assert np.abs(F32.cpu().numpy() - Fo).max() <= 1e-5 * np.abs(Fo).max()
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (23558, 128, 384), (1000, 384, 128), (300, 160, 64),
+                                   (4099, 64, 128), (129, 16, 64)])
+def test_tcgen05_contraction_exact_products(M, N, K):
+    """The tensor-core contraction against an FP64 product of the same bf16
+    values: only the fp32 accumulation order differs."""
+    cs = S.cons_spec(1, 64, 0)
+    ctx = core.Context(cons=(cs, S.cons_weights(cs, 1)))
+    g = torch.Generator().manual_seed(M * 7 + N)
+    a = torch.randn(M, K, generator=g).to(torch.bfloat16)
+    w = torch.randn(N, K, generator=g).to(torch.bfloat16)
+    out = core.contract_bf16(ctx, a.cuda(), w.cuda()).cpu().double()
+    ref = a.double() @ w.double().T
+    scale = (a.double().abs() @ w.double().abs().T)
+    assert ((out - ref).abs() / scale).max().item() <= 1e-6 * K ** 0.5
