@@ -188,6 +188,7 @@ RepTable rep_table(const dmts_ctx *ctx) {
 // -------------------------------------------------------- force pieces --
 EdgeGeom edge_geom(const SysView &s, const int *row_ptr, const int *col, const DevModel &m) {
     EdgeGeom g;
+    g.order = s.order;
     g.x = s.x;
     g.atom_rep = s.atom_rep;
     g.box = s.box;
@@ -338,6 +339,7 @@ dmts_status cons_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const
         pa.F = forces ? forces : (float *)w.ftmp.p;
         if (!forces) cudaMemsetAsync(w.ftmp.p, 0, sizeof(float) * 3 * N, st);
         pa.e_atom = e_atom;
+        pa.order = s.order;
         pa.err = ctx->d_err;
         { ProfScope ps(ctx, "prior", st); launch_prior(pa, st); }
     }
@@ -374,6 +376,9 @@ dmts_status nc_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const i
     io.A = (float *)w.nc_A.p;
     io.q = (float *)w.nc_q.p;
     io.q_bf16 = q_bf;
+    io.U = m.U;
+    io.V = (float *)w.nc_v.p;
+    io.n_l = m.nl;
     io.err = ctx->d_err;
     { ProfScope ps(ctx, "nc_mp_fwd", st); launch_mp_fwd(C, 1, m.K, g, io, st); }
     Epi e1 = epi(EPI_BIAS_SILU);
@@ -391,7 +396,6 @@ dmts_status nc_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const i
     Epi e3 = epi(EPI_STORE);
     e3.out = (float *)w.nc_qk.p;
     contract(ctx, m, N, QKW, C, s1, s_bf, m.Wqk, 1, m.wqk_bf, e3, st, "nc_gemm_tc", "nc_gemm");
-    { ProfScope ps(ctx, "nc_vectors", st); launch_nc_vectors(N, C, m.nl, io.A, m.U, (float *)w.nc_v.p, ctx->d_err, st); }
     NCHeadArgs a;
     a.x = s.x;
     a.atom_rep = s.atom_rep;
@@ -411,6 +415,7 @@ dmts_status nc_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const i
     a.rep = rep_table(ctx);
     a.species = s.species;
     a.F = (float *)w.nc_f.p;
+    a.order = s.order;
     a.err = ctx->d_err;
     { ProfScope ps(ctx, "nc_head", st); launch_nc_head(m.K, m.nc, m.nl, a, st); }
     { ProfScope ps(ctx, "mean_sub", st); launch_mean_sub((float *)w.nc_f.p, forces, s.rep_off, s.n_rep, net, ctx->d_err, st); }
@@ -467,6 +472,7 @@ SysView state_view(dmts_state *stt) {
     v.bond_idx = sys->bond_idx;
     v.bond_r0 = sys->bond_r0;
     v.atom_rep = (int *)si->atom_rep.p;
+    v.order = (const int *)si->scratch.cell_atoms.p;   // atoms sorted by cell at the last rebuild
     return v;
 }
 
@@ -727,6 +733,7 @@ static SysView make_view(dmts_ctx *ctx, const dmts_system *sys, cudaStream_t st)
     v.bond_r0 = sys->bond_r0;
     ctx->ws.atom_rep.ensure(sizeof(int) * (v.n + 1));
     v.atom_rep = (int *)ctx->ws.atom_rep.p;
+    v.order = nullptr;
     atom_rep_map(sys->rep_off, sys->n_replicas, v.n, (int *)ctx->ws.atom_rep.p, st);
     return v;
 }

@@ -67,6 +67,7 @@ struct SysView {
     const int *bond_ptr, *bond_idx;
     const float *bond_r0;
     const int *atom_rep;
+    const int *order = nullptr;   // processing order of the per-atom kernels (nullable)
 };
 
 struct StateInternal {

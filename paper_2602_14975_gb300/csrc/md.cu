@@ -135,8 +135,9 @@ __global__ void __launch_bounds__(128) k_nc_head(NCHeadArgs g) {
     __shared__ float sh_v[4][NL * 3];
     __shared__ int sh_queue[4][64];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int a = blockIdx.x * 4 + warp;
-    if (a >= g.n_atoms || *g.err) return;
+    const int wa = blockIdx.x * 4 + warp;
+    if (wa >= g.n_atoms || *g.err) return;
+    const int a = g.order ? __ldg(g.order + wa) : wa;
     for (int t = lane; t < QKW; t += 32) sh_qk[warp][t] = g.QK[(size_t)a * QKW + t];
     for (int t = lane; t < NL * 3; t += 32) sh_v[warp][t] = g.V[(size_t)a * NL * 3 + t];
     __syncwarp();
@@ -233,7 +234,8 @@ void launch_nc_head(int K, int n_c, int n_l, const NCHeadArgs &a, cudaStream_t s
     else if (K == 8 && n_c == 8 && n_l == 4) k_nc_head<8, 8, 4><<<blocks, 128, 0, st>>>(a);
 }
 
-// Block per replica: FP64 sum of F_in over the replica, then subtract the mean.
+// Block per replica: FP64 sum (of fp32 batch sums of eight atoms) of F_in
+// over the replica, then subtract the mean.
 __global__ void k_mean_sub(const float *F_in, float *F_out, const int *rep_off, double *net, const int *err) {
     if (*err) return;
     __shared__ double red[3][32];
@@ -250,9 +252,13 @@ __global__ void k_mean_sub(const float *F_in, float *F_out, const int *rep_off, 
             const int i = i0 + u * stride;
             for (int a = 0; a < 3; ++a) v[u][a] = i < end ? F_in[3 * i + a] : 0.f;
         }
+        // batch of eight summed in fp32, batch sums accumulated in fp64 (the
+        // fp64 units are few on this GPU: this keeps one block per replica fast)
+        float b[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int u = 0; u < 8; ++u)
-            for (int a = 0; a < 3; ++a) s[a] += (double)v[u][a];
+            for (int a = 0; a < 3; ++a) b[a] += v[u][a];
+        for (int a = 0; a < 3; ++a) s[a] += (double)b[a];
     }
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int a = 0; a < 3; ++a) {
@@ -288,8 +294,9 @@ void launch_mean_sub(const float *F_in, float *F_out, const int *rep_off, int n_
 __global__ void __launch_bounds__(128) k_prior(PriorArgs g) {
     __shared__ int sh_queue[4][64];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int a = blockIdx.x * 4 + warp;
-    if (a >= g.n_atoms || *g.err) return;
+    const int wa = blockIdx.x * 4 + warp;
+    if (wa >= g.n_atoms || *g.err) return;
+    const int a = g.order ? __ldg(g.order + wa) : wa;
     const int rep = g.atom_rep[a];
     const float bx = g.box[3 * rep], by = g.box[3 * rep + 1], bz = g.box[3 * rep + 2];
     const float ibx = bx > 0.f ? 1.f / bx : 0.f, iby = by > 0.f ? 1.f / by : 0.f, ibz = bz > 0.f ? 1.f / bz : 0.f;

@@ -35,6 +35,7 @@ struct NCHeadArgs {
     RepTable rep;
     const uint8_t *species;
     float *F;                      // [N][3] before mean subtraction
+    const int *order;              // nullable processing order
     const int *err;
 };
 
@@ -59,6 +60,7 @@ struct PriorArgs {
     RepTable rep;
     float *F;                      // accumulated
     float *e_atom;                 // accumulated per-atom energy (nullable)
+    const int *order;              // nullable processing order
     const int *err;
 };
 void launch_prior(const PriorArgs &a, cudaStream_t st);

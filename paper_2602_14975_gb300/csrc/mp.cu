@@ -20,8 +20,9 @@ __global__ void __launch_bounds__(MP_WARPS * 32) k_mp_fwd(EdgeGeom g, LayerIO io
     __shared__ float sh_y[MP_WARPS][32][NLM];
     __shared__ int sh_j[MP_WARPS][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int i = blockIdx.x * MP_WARPS + warp;
-    if (i >= g.n_atoms || *io.err) return;
+    const int wi = blockIdx.x * MP_WARPS + warp;
+    if (wi >= g.n_atoms || *io.err) return;
+    const int i = g.order ? __ldg(g.order + wi) : wi;   // spatially sorted: neighbours shared in cache
 
     float W[NL][K][CPW];
 #pragma unroll
@@ -111,6 +112,21 @@ __global__ void __launch_bounds__(MP_WARPS * 32) k_mp_fwd(EdgeGeom g, LayerIO io
         }
         stv<CPW>(io.A + ((size_t)i * NLM + lm) * C + lane * CPW, a);
     }
+    if (LMAX >= 1 && io.V) {
+        // vector part of the tensor heads, V_h = sum_c U[h][c] A[l=1][c]
+        for (int h = 0; h < io.n_l; ++h) {
+            float u4[CPW];
+            ldv<CPW>(io.U + (size_t)h * C + lane * CPW, u4);
+#pragma unroll
+            for (int cmp = 0; cmp < 3; ++cmp) {
+                float part = 0.f;
+#pragma unroll
+                for (int u = 0; u < CPW; ++u) part = fmaf(u4[u], io.nu * acc[1 + cmp][u], part);
+                part = warp_sum(part);
+                if (lane == 0) io.V[((size_t)i * io.n_l + h) * 3 + cmp] = part;
+            }
+        }
+    }
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
         stv<CPW>(io.q + (size_t)i * NL * C + l * C + lane * CPW, qv[l]);
@@ -138,8 +154,9 @@ __global__ void __launch_bounds__(MP_WARPS * 32) k_mp_bwd(EdgeGeom g, LayerIO io
     __shared__ int sh_j[MP_WARPS][32];
     __shared__ float sh_ga[MP_WARPS][NLM][C];   // element (lm, lane*CPW+u) at [lm][u*32+lane]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int a = blockIdx.x * MP_WARPS + warp;
-    if (a >= g.n_atoms || *io.err) return;
+    const int wa = blockIdx.x * MP_WARPS + warp;
+    if (wa >= g.n_atoms || *io.err) return;
+    const int a = g.order ? __ldg(g.order + wa) : wa;
 
     float W[NL][K][CPW];
 #pragma unroll
@@ -447,8 +464,10 @@ __global__ void k_replica_sum(const float *__restrict__ v, const int *__restrict
         float t[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) t[u] = i0 + u * stride < end ? v[i0 + u * stride] : 0.f;
+        float b = 0.f;
 #pragma unroll
-        for (int u = 0; u < 8; ++u) acc += (double)t[u];
+        for (int u = 0; u < 8; ++u) b += t[u];
+        acc += (double)b;
     }
     acc = warp_sum_d(acc);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;

@@ -15,6 +15,7 @@ struct EdgeGeom {
     int n_atoms;
     float rc, inv_rc, bnorm; // model cutoff, 1/rc, sqrt(2/rc)
     int p;                   // envelope exponent
+    const int *order;        // nullable: atoms in processing order (cell order), else identity
 };
 
 // Node-level arrays for one layer.
@@ -25,6 +26,9 @@ struct LayerIO {
     float *A;                // [N][NLM][C]  (forward out)
     float *q;                // [N][(LMAX+1)C] (forward out, fp32)
     __nv_bfloat16 *q_bf16;   // optional bf16 copy of q (forward out)
+    const float *U;          // optional: tensor-head mix U[n_l][C] (NC embedding)
+    float *V;                // optional: V[N][n_l][3] = sum_c U[h][c] A[1+a][c]
+    int n_l;
     const float *gA;         // [N][NLM][C]  (backward in)
     const float *gs_in;      // [N][C]       (backward in)
     float *gs_out;           // [N][C]       (backward out)

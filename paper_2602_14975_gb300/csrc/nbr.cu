@@ -168,6 +168,132 @@ __global__ void k_nbr_fill(NbrWork w, float rc2, const int *row_ptr, int *col, f
     }
 }
 
+// Warp-per-atom variants: lanes sweep the atoms of each neighbouring cell
+// (same cell order as above), rows are collected by ballot into shared
+// memory, sorted there by a bitonic network and written out contiguously.
+constexpr int NB_WARPS = 4;
+constexpr int NB_MAXROW = 256;
+
+template <typename Fn>
+__device__ __forceinline__ void for_candidates_warp(const NbrWork &w, int i, float rc2, int lane, Fn f) {
+    const CellGrid g = w.grid[w.atom_rep[i]];
+    const float xi = w.x[3 * i], yi = w.x[3 * i + 1], zi = w.x[3 * i + 2];
+    const int own = w.atom_cell[i] - g.cell_off;
+    const int cx = own % g.dim[0], cy = (own / g.dim[0]) % g.dim[1], cz = own / (g.dim[0] * g.dim[1]);
+    int lo[3], hi[3];
+    const int c3[3] = {cx, cy, cz};
+    for (int a = 0; a < 3; ++a) {
+        if (g.box[a] > 0.f) {
+            if (g.dim[a] >= 3) { lo[a] = -1; hi[a] = 1; }
+            else if (g.dim[a] == 2) { lo[a] = 0; hi[a] = 1; }
+            else { lo[a] = 0; hi[a] = 0; }
+        } else {
+            lo[a] = c3[a] > 0 ? -1 : 0;
+            hi[a] = c3[a] < g.dim[a] - 1 ? 1 : 0;
+        }
+    }
+    const float ibx = g.box[0] > 0.f ? 1.f / g.box[0] : 0.f;
+    const float iby = g.box[1] > 0.f ? 1.f / g.box[1] : 0.f;
+    const float ibz = g.box[2] > 0.f ? 1.f / g.box[2] : 0.f;
+    for (int oz = lo[2]; oz <= hi[2]; ++oz) {
+        int z = cz + oz;
+        if (g.box[2] > 0.f) z = (z + g.dim[2]) % g.dim[2];
+        for (int oy = lo[1]; oy <= hi[1]; ++oy) {
+            int y = cy + oy;
+            if (g.box[1] > 0.f) y = (y + g.dim[1]) % g.dim[1];
+            for (int ox = lo[0]; ox <= hi[0]; ++ox) {
+                int xx = cx + ox;
+                if (g.box[0] > 0.f) xx = (xx + g.dim[0]) % g.dim[0];
+                const int cell = g.cell_off + (z * g.dim[1] + y) * g.dim[0] + xx;
+                const int beg = w.cell_start[cell], end = w.cell_start[cell + 1];
+                for (int p0 = beg; p0 < end; p0 += 32) {
+                    const int p = p0 + lane;
+                    bool hit = false;
+                    int j = -1;
+                    if (p < end) {
+                        j = w.cell_atoms[p];
+                        if (j != i) {
+                            const float dx = min_img(w.x[3 * j] - xi, g.box[0], ibx);
+                            const float dy = min_img(w.x[3 * j + 1] - yi, g.box[1], iby);
+                            const float dz = min_img(w.x[3 * j + 2] - zi, g.box[2], ibz);
+                            hit = dx * dx + dy * dy + dz * dz < rc2;
+                        }
+                    }
+                    f(hit, j);
+                }
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(NB_WARPS * 32) k_nbr_count_warp(NbrWork w, float rc2) {
+    if (gated_off(w.gate, w.err)) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * NB_WARPS + warp;
+    if (i >= w.n_atoms) return;
+    int cnt = 0;
+    for_candidates_warp(w, i, rc2, lane, [&](bool hit, int) { cnt += __popc(__ballot_sync(DMTS_FULL, hit)); });
+    if (lane == 0) w.counts[i] = cnt;
+}
+
+__global__ void __launch_bounds__(NB_WARPS * 32) k_nbr_fill_warp(NbrWork w, float rc2, const int *row_ptr, int *col,
+                                                                 float *x_ref) {
+    if (gated_off(w.gate, w.err)) return;
+    __shared__ int buf[NB_WARPS][NB_MAXROW];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * NB_WARPS + warp;
+    if (i >= w.n_atoms) return;
+    int *sb = buf[warp];
+    const int beg = row_ptr[i], n = row_ptr[i + 1] - beg;
+    if (n <= NB_MAXROW) {
+        int cnt = 0;
+        for_candidates_warp(w, i, rc2, lane, [&](bool hit, int j) {
+            const unsigned m = __ballot_sync(DMTS_FULL, hit);
+            if (hit) sb[cnt + __popc(m & ((1u << lane) - 1u))] = j;
+            cnt += __popc(m);
+        });
+        // pad to a power of two and sort ascending (bitonic network)
+        int len = 32;
+        while (len < cnt) len <<= 1;
+        for (int t = cnt + lane; t < len; t += 32) sb[t] = 0x7fffffff;
+        __syncwarp();
+        for (int k = 2; k <= len; k <<= 1)
+            for (int jj = k >> 1; jj > 0; jj >>= 1) {
+                for (int t = lane; t < len; t += 32) {
+                    const int u = t ^ jj;
+                    if (u > t) {
+                        const int a = sb[t], b = sb[u];
+                        const bool up = (t & k) == 0;
+                        if ((a > b) == up) {
+                            sb[t] = b;
+                            sb[u] = a;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        for (int t = lane; t < cnt; t += 32) col[beg + t] = sb[t];
+    } else if (lane == 0) {
+        // rows longer than the shared buffer: serial fill + insertion sort
+        int p = beg;
+        for_candidates(w, i, rc2, [&](int j) { col[p++] = j; });
+        for (int a = beg + 1; a < p; ++a) {
+            const int v = col[a];
+            int b = a - 1;
+            while (b >= beg && col[b] > v) {
+                col[b + 1] = col[b];
+                --b;
+            }
+            col[b + 1] = v;
+        }
+    }
+    if (x_ref && lane == 0) {
+        x_ref[3 * i] = w.x[3 * i];
+        x_ref[3 * i + 1] = w.x[3 * i + 1];
+        x_ref[3 * i + 2] = w.x[3 * i + 2];
+    }
+}
+
 // Single-block exclusive scan (n up to a few million).
 __global__ void __launch_bounds__(1024) k_scan(const int *in, int n, int *out, long long capacity,
                                                long long *total, int *err, const int *gate) {
@@ -220,10 +346,10 @@ void nbr_cells(const NbrWork &w, float r_list, cudaStream_t st) {
 void nbr_fill(const NbrWork &w, float r_list, int *row_ptr, int *col, long long capacity, float *x_ref,
               cudaStream_t st) {
     if (w.n_atoms == 0) return;
-    const int nb = (w.n_atoms + 127) / 128;
-    k_nbr_count<<<nb, 128, 0, st>>>(w, r_list * r_list);
+    const int nb = (w.n_atoms + NB_WARPS - 1) / NB_WARPS;
+    k_nbr_count_warp<<<nb, NB_WARPS * 32, 0, st>>>(w, r_list * r_list);
     scan_ints(w.counts, w.n_atoms, row_ptr, capacity, w.total, w.err, w.gate, st);
-    if (col) k_nbr_fill<<<nb, 128, 0, st>>>(w, r_list * r_list, row_ptr, col, x_ref);
+    if (col) k_nbr_fill_warp<<<nb, NB_WARPS * 32, 0, st>>>(w, r_list * r_list, row_ptr, col, x_ref);
 }
 
 // ------------------------------------------------------------- sub-lists
