@@ -148,10 +148,9 @@ def oracle_outer_step_seconds(sy, W, frac_edge):
 # ------------------------------------------------------------------ main --
 def main():
     args = parse()
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2602_14975_gb300 import dist as D
     from paper_2602_14975_gb300 import synth as S
+    world, rank, local = D.world()
     W = S.WORKLOADS[args.workload]
     I = W["dmts"]
 
@@ -188,10 +187,8 @@ def main():
         return 0
 
     import torch
-    import torch.distributed as dist
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
     torch.cuda.set_device(local)
+    D.init("nccl", torch.device(f"cuda:{local}"))
     from paper_2602_14975_gb300 import core
 
     sy = W["system"]()
@@ -199,17 +196,13 @@ def main():
     cb, nb = S.cons_weights(cs, W["w_seed"]), S.nc_weights(ns, W["w_seed"])
     ctx = core.Context(cons=(cs, cb), nc=(ns, nb), device=local)
 
+    dev = torch.device(f"cuda:{local}")
+
     def barrier():
-        torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
+        D.barrier(dev)
 
     def max_over_ranks(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return D.max_over_ranks(v, dev)
 
     # algorithmic work of the dominant kernels (active edges within the cutoffs)
     d0 = core.DeviceSystem(sy)
@@ -221,8 +214,9 @@ def main():
     m_hmr = core.masses_hmr(sy.species, sy.mol_id, sy.element_masses(), I.hmr_delta)
     v0 = S.maxwell_boltzmann(m_hmr, I.temperature, W["rng_seed"])
     dsys = core.DeviceSystem(sy)
-    st = core.MDState(dsys, v0, m_hmr.astype(np.float32), seeds=I.seed, replica_ids=[rank])
-    integ = core.integrator(I.dt_outer, I.n_inner, I.temperature, I.gamma_ps, skin=0.5)
+    st = core.MDState(dsys, v0, m_hmr.astype(np.float32), seeds=I.seed, replica_ids=[D.replica_id(rank, 0)])
+    skin = 0.5    # Verlet skin (A); rebuilds are gated on half-skin displacement
+    integ = core.integrator(I.dt_outer, I.n_inner, I.temperature, I.gamma_ps, skin=skin)
     core.respa_step(ctx, st, integ, args.warmup)
     ctx.sync()
     clocks = ClockSampler(local)
@@ -249,8 +243,8 @@ def main():
     sy2 = W["system"]()
     d2 = core.DeviceSystem(sy2)
     st2 = core.MDState(d2, S.maxwell_boltzmann(m_el, sts.temperature, W["rng_seed"]),
-                       m_el.astype(np.float32), seeds=sts.seed, replica_ids=[rank])
-    integ2 = core.integrator(sts.dt_outer, 1, sts.temperature, sts.gamma_ps, mode=1, skin=0.5)
+                       m_el.astype(np.float32), seeds=sts.seed, replica_ids=[D.replica_id(rank, 0)])
+    integ2 = core.integrator(sts.dt_outer, 1, sts.temperature, sts.gamma_ps, mode=1, skin=skin)
     n_sts = max(10, args.steps)
     core.respa_step(ctx, st2, integ2, args.warmup)
     ctx.sync()
@@ -267,7 +261,7 @@ def main():
     # state held on the host (pinned): every step copies x, v in, runs one
     # outer step through the public API and reads x, v and the energy back
     d3 = core.DeviceSystem(W["system"]())
-    st3 = core.MDState(d3, v0, m_hmr.astype(np.float32), seeds=I.seed, replica_ids=[rank])
+    st3 = core.MDState(d3, v0, m_hmr.astype(np.float32), seeds=I.seed, replica_ids=[D.replica_id(rank, 0)])
     hx = torch.from_numpy(sy.x.astype(np.float32)).pin_memory()
     hv = torch.from_numpy(v0.astype(np.float32)).pin_memory()
     he = torch.zeros(1, dtype=torch.float64).pin_memory()
@@ -294,7 +288,7 @@ def main():
 
     # ----------------------------------------------------------- serving
     # (1) the 23,558-atom system as a request of the serving loop
-    r3 = core.ReplicaRequest(sy, v0, m_hmr, args.steps, I.seed, rank)
+    r3 = core.ReplicaRequest(sy, v0, m_hmr, args.steps, I.seed, D.replica_id(rank, 0))
     out3, st3s = core.run_replicas(ctx, [r3], integ)
     ms_serve = float(np.sum(st3s["tick_ms"])) / max(1, st3s["n_ticks"])
     # (2) the replica-serving workload: Poisson arrivals of small solvated
@@ -306,7 +300,7 @@ def main():
         sq = S.capped_molecule_in_droplet(q["n_solute"], seed=q["sys_seed"])
         mq = core.masses_hmr(sq.species, sq.mol_id, sq.element_masses(), I.hmr_delta)
         vq = S.maxwell_boltzmann(mq, I.temperature, q["sys_seed"] + 1)
-        reqs.append(core.ReplicaRequest(sq, vq, mq, q["n_outer"], q["rng_seed"], q["id"] + 100000 * rank,
+        reqs.append(core.ReplicaRequest(sq, vq, mq, q["n_outer"], q["rng_seed"], D.replica_id(rank, 1 + q["id"]),
                                         q["arrival_s"]))
     barrier()
     outs, sst = core.run_replicas(ctx, reqs, integ, realtime=True)
@@ -387,6 +381,7 @@ def main():
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
+        import torch.distributed as dist
         dist.destroy_process_group()
     return 0
 

@@ -236,7 +236,8 @@ void launch_nc_head(int K, int n_c, int n_l, const NCHeadArgs &a, cudaStream_t s
 
 // Block per replica: FP64 sum (of fp32 batch sums of eight atoms) of F_in
 // over the replica, then subtract the mean.
-__global__ void k_mean_sub(const float *F_in, float *F_out, const int *rep_off, double *net, const int *err) {
+__global__ void k_mean_sub(const float *__restrict__ F_in, float *__restrict__ F_out, const int *__restrict__ rep_off,
+                           double *__restrict__ net, const int *__restrict__ err) {
     if (*err) return;
     __shared__ double red[3][32];
     __shared__ double mean[3];
@@ -274,10 +275,22 @@ __global__ void k_mean_sub(const float *F_in, float *F_out, const int *rep_off, 
     }
     __syncthreads();
     const float mx = (float)mean[0], my = (float)mean[1], mz = (float)mean[2];
-    for (int i = beg + threadIdx.x; i < end; i += blockDim.x) {
-        F_out[3 * i] = F_in[3 * i] - mx;
-        F_out[3 * i + 1] = F_in[3 * i + 1] - my;
-        F_out[3 * i + 2] = F_in[3 * i + 2] - mz;
+    for (int i0 = beg + threadIdx.x; i0 < end; i0 += 8 * stride) {
+        float v[8][3];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = i0 + u * stride;
+            for (int a = 0; a < 3; ++a) v[u][a] = i < end ? F_in[3 * i + a] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = i0 + u * stride;
+            if (i < end) {
+                F_out[3 * i] = v[u][0] - mx;
+                F_out[3 * i + 1] = v[u][1] - my;
+                F_out[3 * i + 2] = v[u][2] - mz;
+            }
+        }
     }
 }
 

@@ -13,9 +13,12 @@ constexpr int MP_WARPS = 4;
 // Warp per receiver i, lane owns CPW consecutive channels c = lane*CPW + u.
 // Active edges (r < rc) of the row are compacted 32 at a time into shared
 // memory with their embedding (f_c B_k, Y_lm); every lane then sweeps them.
-template <int C, int LMAX, int K>
+// C channels are split over SPLIT thread blocks (blockIdx.y = part): a warp
+// owns CW = C / SPLIT channels, offset co = part * CW.
+template <int C, int LMAX, int K, int SPLIT>
 __global__ void __launch_bounds__(MP_WARPS * 32) k_mp_fwd(EdgeGeom g, LayerIO io) {
-    constexpr int NL = LMAX + 1, NLM = NL * NL, CPW = C / 32;
+    constexpr int NL = LMAX + 1, NLM = NL * NL, CW = C / SPLIT, CPW = CW / 32;
+    const int co = blockIdx.y * CW;
     __shared__ float sh_b[MP_WARPS][32][K];
     __shared__ float sh_y[MP_WARPS][32][NLM];
     __shared__ int sh_j[MP_WARPS][32];
@@ -28,7 +31,7 @@ __global__ void __launch_bounds__(MP_WARPS * 32) k_mp_fwd(EdgeGeom g, LayerIO io
 #pragma unroll
     for (int l = 0; l < NL; ++l)
 #pragma unroll
-        for (int k = 0; k < K; ++k) ldv<CPW>(io.wrad + (l * K + k) * C + lane * CPW, W[l][k]);
+        for (int k = 0; k < K; ++k) ldv<CPW>(io.wrad + (l * K + k) * C + co + lane * CPW, W[l][k]);
     float acc[NLM][CPW];
 #pragma unroll
     for (int lm = 0; lm < NLM; ++lm)
@@ -76,7 +79,7 @@ __global__ void __launch_bounds__(MP_WARPS * 32) k_mp_fwd(EdgeGeom g, LayerIO io
         for (int t = 0; t < na; ++t) {
             const int jt = sh_j[warp][t];
             float sj[CPW];
-            ldv<CPW>(io.s + (size_t)jt * C + lane * CPW, sj);
+            ldv<CPW>(io.s + (size_t)jt * C + co + lane * CPW, sj);
             float b[K], y[NLM];
 #pragma unroll
             for (int k = 0; k < K; ++k) b[k] = sh_b[warp][t][k];
@@ -110,13 +113,13 @@ __global__ void __launch_bounds__(MP_WARPS * 32) k_mp_fwd(EdgeGeom g, LayerIO io
             a[u] = io.nu * acc[lm][u];
             qv[l][u] = fmaf(a[u], a[u], qv[l][u]);
         }
-        stv<CPW>(io.A + ((size_t)i * NLM + lm) * C + lane * CPW, a);
+        stv<CPW>(io.A + ((size_t)i * NLM + lm) * C + co + lane * CPW, a);
     }
     if (LMAX >= 1 && io.V) {
         // vector part of the tensor heads, V_h = sum_c U[h][c] A[l=1][c]
         for (int h = 0; h < io.n_l; ++h) {
             float u4[CPW];
-            ldv<CPW>(io.U + (size_t)h * C + lane * CPW, u4);
+            ldv<CPW>(io.U + (size_t)h * C + co + lane * CPW, u4);
 #pragma unroll
             for (int cmp = 0; cmp < 3; ++cmp) {
                 float part = 0.f;
@@ -129,11 +132,11 @@ __global__ void __launch_bounds__(MP_WARPS * 32) k_mp_fwd(EdgeGeom g, LayerIO io
     }
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
-        stv<CPW>(io.q + (size_t)i * NL * C + l * C + lane * CPW, qv[l]);
+        stv<CPW>(io.q + (size_t)i * NL * C + l * C + co + lane * CPW, qv[l]);
         if (io.q_bf16) {
 #pragma unroll
             for (int u = 0; u < CPW; ++u)
-                io.q_bf16[(size_t)i * NL * C + l * C + lane * CPW + u] = __float2bfloat16_rn(qv[l][u]);
+                io.q_bf16[(size_t)i * NL * C + l * C + co + lane * CPW + u] = __float2bfloat16_rn(qv[l][u]);
         }
     }
 }
@@ -302,10 +305,18 @@ __global__ void __launch_bounds__(MP_WARPS * 32) k_mp_bwd(EdgeGeom g, LayerIO io
     }
 }
 
+// In the forward pass 128 channels are split over two blocks (64 per warp):
+// half the registers, twice the warps in flight to hide the neighbour loads.
+// The tensor-head vectors V sum over all channels, so a launch that writes V
+// keeps the channels in one warp.
 template <int C, int LMAX>
 static void fwd_c(const EdgeGeom &g, const LayerIO &io, cudaStream_t st) {
+    constexpr int SP = C >= 128 ? 2 : 1;
     const int blocks = (g.n_atoms + MP_WARPS - 1) / MP_WARPS;
-    k_mp_fwd<C, LMAX, 8><<<blocks, MP_WARPS * 32, 0, st>>>(g, io);
+    if (SP > 1 && !io.V)
+        k_mp_fwd<C, LMAX, 8, SP><<<dim3(blocks, SP), MP_WARPS * 32, 0, st>>>(g, io);
+    else
+        k_mp_fwd<C, LMAX, 8, 1><<<blocks, MP_WARPS * 32, 0, st>>>(g, io);
 }
 
 template <int C, int LMAX>
