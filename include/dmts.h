@@ -50,7 +50,8 @@ typedef enum {
     DMTS_E_CUDA = 3,          /* a CUDA call failed */
     DMTS_E_NBR_OVERFLOW = 4,  /* neighbour list larger than its capacity */
     DMTS_E_NONFINITE = 5,     /* NaN/Inf found in positions or velocities */
-    DMTS_E_TIMEOUT = 6,       /* reserved: no call of this version waits on the device */
+    DMTS_E_TIMEOUT = 6,       /* a bounded wait of a device kernel on its own asynchronous copies or
+                                 tensor-core work gave up; the context stays usable */
     DMTS_E_BUSY = 7           /* state already in use by an unfinished call */
 } dmts_status;
 

@@ -358,7 +358,8 @@ dmts_status nc_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const i
     if (!w.nc_s.ensure(sizeof(float) * nc_ * 2) || !w.nc_A.ensure(sizeof(float) * nc_ * 4) ||
         !w.nc_q.ensure(sizeof(float) * nc_ * 2) || !w.nc_h.ensure(sizeof(float) * nc_) ||
         !w.nc_act.ensure(sizeof(float) * nc_) || !w.nc_qk.ensure(sizeof(float) * (size_t)N * QKW) ||
-        !w.nc_v.ensure(sizeof(float) * (size_t)N * m.nl * 3) || !w.nc_f.ensure(sizeof(float) * 3 * (N + 1)))
+        !w.nc_v.ensure(sizeof(float) * (size_t)N * m.nl * 3) || !w.nc_f.ensure(sizeof(float) * 3 * (N + 1)) ||
+        !w.ms_scratch.ensure(mean_sub_scratch_bytes(N, s.n_rep)))
         return fail(ctx, DMTS_E_OOM, "workspace allocation failed");
     if (bf && (!w.nc_q_bf.ensure(2 * nc_ * 2 + 16) || !w.nc_act_bf.ensure(2 * nc_ + 16) || !w.nc_s_bf.ensure(2 * nc_ + 16)))
         return fail(ctx, DMTS_E_OOM, "workspace allocation failed");
@@ -418,7 +419,10 @@ dmts_status nc_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const i
     a.order = s.order;
     a.err = ctx->d_err;
     { ProfScope ps(ctx, "nc_head", st); launch_nc_head(m.K, m.nc, m.nl, a, st); }
-    { ProfScope ps(ctx, "mean_sub", st); launch_mean_sub((float *)w.nc_f.p, forces, s.rep_off, s.n_rep, net, ctx->d_err, st); }
+    {
+        ProfScope ps(ctx, "mean_sub", st);
+        launch_mean_sub((float *)w.nc_f.p, forces, s.rep_off, s.n_rep, N, net, w.ms_scratch.p, ctx->d_err, st);
+    }
     return DMTS_OK;
 }
 

@@ -1,6 +1,7 @@
 // NC direct-force head (Sec. 2 "Model architecture"), the bonded + LJ prior,
 // and the fused BAOAB/RESPA integrator with Philox4x32-10 noise (Algorithm 1).
 #include "md.cuh"
+#include "ptx.cuh"
 
 namespace dmts {
 
@@ -128,20 +129,49 @@ __device__ __forceinline__ float rep_pair(const RepTable &t, int si, int sj, flo
 //   F_aj = (sum_{h<K} c_ajh B_h) (n + sum_{h<n_l} c_aj(K+h) V_ah) f_c
 //   F_ja = (sum_{h<K} c_jah B_h) (-n + sum_{h<n_l} c_ja(K+h) V_jh) f_c
 //   F_a = scale sum_j (F_aj - F_ja) (+ bonds)
+// Active neighbours are taken 32 at a time (the g-th active entry of the row
+// on lane g % 32, as in for_active_canonical). Each lane starts one bulk copy
+// of its neighbour's q/k row into shared memory, evaluates the radial part of
+// its edge while the rows arrive, and then forms the dot products from shared
+// memory, so no load instruction gathers 32 scattered rows at once.
+constexpr int NCH_WARPS = 2;
+
 template <int K, int NC, int NL>
-__global__ void __launch_bounds__(128) k_nc_head(NCHeadArgs g) {
-    constexpr int H = K + NL, QKW = 2 * H * NC;
-    __shared__ float sh_qk[4][QKW];
-    __shared__ float sh_v[4][NL * 3];
-    __shared__ int sh_queue[4][64];
+struct NCHeadSmem {
+    static constexpr int H = K + NL, QKW = 2 * H * NC;
+    static constexpr int RSTR = QKW + 4;    // padded row stride (floats): conflict-free 16-byte reads
+    static constexpr int ROWB = QKW * 4;    // bytes copied per row
+    static constexpr size_t rows = (size_t)NCH_WARPS * 32 * RSTR * 4;
+    static constexpr size_t qk = (size_t)NCH_WARPS * QKW * 4;
+    static constexpr size_t vv = (size_t)NCH_WARPS * 4 * NL * 4;
+    static constexpr size_t queue = (size_t)NCH_WARPS * 64 * 4;
+    static constexpr size_t bytes = rows + qk + vv + queue + NCH_WARPS * 8;
+    static_assert(QKW % 16 == 0, "row stride");
+};
+
+template <int K, int NC, int NL>
+__global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
+    using SM = NCHeadSmem<K, NC, NL>;
+    constexpr int H = SM::H, QKW = SM::QKW, RSTR = SM::RSTR;
+    extern __shared__ __align__(16) unsigned char nch_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int wa = blockIdx.x * 4 + warp;
+    float *rows = reinterpret_cast<float *>(nch_smem) + (size_t)warp * 32 * RSTR;
+    float *qa = reinterpret_cast<float *>(nch_smem + SM::rows) + warp * QKW;
+    float *va = reinterpret_cast<float *>(nch_smem + SM::rows + SM::qk) + warp * 4 * NL;
+    int *queue = reinterpret_cast<int *>(nch_smem + SM::rows + SM::qk + SM::vv) + warp * 64;
+    uint64_t *bar_p = reinterpret_cast<uint64_t *>(nch_smem + SM::rows + SM::qk + SM::vv + SM::queue) + warp;
+    const uint32_t bar = smem_u32(bar_p);
+    const int wa = blockIdx.x * NCH_WARPS + warp;
     if (wa >= g.n_atoms || *g.err) return;
     const int a = g.order ? __ldg(g.order + wa) : wa;
-    for (int t = lane; t < QKW; t += 32) sh_qk[warp][t] = g.QK[(size_t)a * QKW + t];
-    for (int t = lane; t < NL * 3; t += 32) sh_v[warp][t] = g.V[(size_t)a * NL * 3 + t];
+    if (lane == 0) {
+        mbar_init(bar, 1);
+        mbar_init_fence();
+    }
+    for (int t = lane; t < QKW; t += 32) qa[t] = g.QK[(size_t)a * QKW + t];
+    for (int t = lane; t < NL * 3; t += 32) va[t] = g.V[(size_t)a * NL * 3 + t];
     __syncwarp();
-    const float *qa = sh_qk[warp], *ka = sh_qk[warp] + H * NC, *va = sh_v[warp];
+    const float *ka = qa + H * NC;
     const int rep = g.atom_rep[a];
     const float bx = g.box[3 * rep], by = g.box[3 * rep + 1], bz = g.box[3 * rep + 2];
     const float ibx = bx > 0.f ? 1.f / bx : 0.f, iby = by > 0.f ? 1.f / by : 0.f, ibz = bz > 0.f ? 1.f / bz : 0.f;
@@ -151,69 +181,110 @@ __global__ void __launch_bounds__(128) k_nc_head(NCHeadArgs g) {
     const float rep2 = g.rep.rc * g.rep.rc;
     const int sa = g.species[a];
     float fx = 0.f, fy = 0.f, fz = 0.f, rx = 0.f, ry = 0.f, rz = 0.f;
-    auto disp = [&](int j, float &dx, float &dy, float &dz) {
-        dx = min_img(__ldg(g.x + 3 * j) - xa, bx, ibx);
-        dy = min_img(__ldg(g.x + 3 * j + 1) - ya, by, iby);
-        dz = min_img(__ldg(g.x + 3 * j + 2) - za, bz, ibz);
-    };
-    auto active = [&](int j) {
-        float dx, dy, dz;
-        disp(j, dx, dy, dz);
-        return dx * dx + dy * dy + dz * dz < rc2;
-    };
-    auto edge = [&](int j) {
-        float dx, dy, dz;
-        disp(j, dx, dy, dz);
-        const float r2 = dx * dx + dy * dy + dz * dz;
-        const float r = sqrtf(r2), inv = 1.f / r;
-        if (with_rep && r2 < rep2 && !is_bonded(g.bonds, a, j)) {
-            float dE;
-            rep_pair(g.rep, sa, g.species[j], r, &dE);
-            const float c = dE * inv;              // F_a = E'(r) d / r
-            rx += c * dx; ry += c * dy; rz += c * dz;
-        }
-        const float nx = dx * inv, ny = dy * inv, nz = dz * inv;
-        float du;
-        const float fc = envelope(r * g.inv_rc, g.p, &du);
-        float B[K];
-        bessel<K, false>(r, g.inv_rc, g.bnorm, B, nullptr);
-        const float4 *qj4 = reinterpret_cast<const float4 *>(g.QK + (size_t)j * QKW);
-        const float4 *kj4 = qj4 + H * NC / 4;
-        float Saj = 0.f, Sja = 0.f;
-        float vax = 0.f, vay = 0.f, vaz = 0.f, vjx = 0.f, vjy = 0.f, vjz = 0.f;
+    uint32_t phase = 0;
+    bool alive = true;
+
+    // one batch: lanes t < nb own the queued edges taken .. taken + nb - 1
+    auto batch = [&](int taken, int nb) {
+        const int j = lane < nb ? queue[(taken + lane) & 63] : -1;
+        fence_proxy_async_smem();      // earlier reads of the rows before the copies overwrite them
+        if (lane == 0) mbar_expect_tx(bar, (uint32_t)nb * SM::ROWB);
+        __syncwarp();
+        if (j >= 0) bulk_g2s(smem_u32(rows + lane * RSTR), g.QK + (size_t)j * QKW, SM::ROWB, bar);
+        // radial part of the edge while the rows arrive
+        float dx = 0.f, dy = 0.f, dz = 0.f, r = 1.f, inv = 1.f, fc = 0.f, B[K], vj[NL * 3];
+        if (j >= 0) {
+            dx = min_img(__ldg(g.x + 3 * j) - xa, bx, ibx);
+            dy = min_img(__ldg(g.x + 3 * j + 1) - ya, by, iby);
+            dz = min_img(__ldg(g.x + 3 * j + 2) - za, bz, ibz);
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            r = sqrtf(r2);
+            inv = 1.f / r;
 #pragma unroll
-        for (int h = 0; h < H; ++h) {
-            float caj = 0.f, cja = 0.f;
-#pragma unroll
-            for (int q = 0; q < NC / 4; ++q) {
-                const float4 kj = __ldg(kj4 + h * NC / 4 + q);
-                const float4 qj = __ldg(qj4 + h * NC / 4 + q);
-                const float *qah = qa + h * NC + 4 * q, *kah = ka + h * NC + 4 * q;
-                caj = fmaf(qah[0], kj.x, fmaf(qah[1], kj.y, fmaf(qah[2], kj.z, fmaf(qah[3], kj.w, caj))));
-                cja = fmaf(qj.x, kah[0], fmaf(qj.y, kah[1], fmaf(qj.z, kah[2], fmaf(qj.w, kah[3], cja))));
+            for (int q = 0; q < NL * 3; ++q) vj[q] = __ldg(g.V + (size_t)j * NL * 3 + q);
+            if (with_rep && r2 < rep2 && !is_bonded(g.bonds, a, j)) {
+                float dE;
+                rep_pair(g.rep, sa, g.species[j], r, &dE);
+                const float c = dE * inv;              // F_a = E'(r) d / r
+                rx += c * dx; ry += c * dy; rz += c * dz;
             }
-            caj *= isnc;
-            cja *= isnc;
-            if (h < K) {
-                Saj = fmaf(caj, B[h], Saj);
-                Sja = fmaf(cja, B[h], Sja);
-            } else {
-                const int t = h - K;
-                vax = fmaf(caj, va[3 * t], vax);
-                vay = fmaf(caj, va[3 * t + 1], vay);
-                vaz = fmaf(caj, va[3 * t + 2], vaz);
-                const float *vj = g.V + ((size_t)j * NL + t) * 3;
-                vjx = fmaf(cja, __ldg(vj), vjx);
-                vjy = fmaf(cja, __ldg(vj + 1), vjy);
-                vjz = fmaf(cja, __ldg(vj + 2), vjz);
-            }
+            float du;
+            fc = envelope(r * g.inv_rc, g.p, &du);
+            bessel<K, false>(r, g.inv_rc, g.bnorm, B, nullptr);
         }
-        const float pa = Saj * fc, pj = Sja * fc;
-        fx += pa * (nx + vax) - pj * (-nx + vjx);
-        fy += pa * (ny + vay) - pj * (-ny + vjy);
-        fz += pa * (nz + vaz) - pj * (-nz + vjz);
+        const bool got = __all_sync(DMTS_FULL, mbar_wait(bar, phase));
+        phase ^= 1u;
+        if (!got) {
+            // record the timeout, give the copies in flight a last bounded
+            // wait, and stop
+            if (lane == 0) atomicCAS(g.err, 0, (int)DMTS_E_TIMEOUT);
+            mbar_wait(bar, phase ^ 1u);
+            alive = false;
+            return;
+        }
+        if (j >= 0) {
+            const float nx = dx * inv, ny = dy * inv, nz = dz * inv;
+            const float4 *qj4 = reinterpret_cast<const float4 *>(rows + lane * RSTR);
+            const float4 *kj4 = qj4 + H * NC / 4;
+            float Saj = 0.f, Sja = 0.f;
+            float vax = 0.f, vay = 0.f, vaz = 0.f, vjx = 0.f, vjy = 0.f, vjz = 0.f;
+#pragma unroll
+            for (int h = 0; h < H; ++h) {
+                float caj = 0.f, cja = 0.f;
+#pragma unroll
+                for (int q = 0; q < NC / 4; ++q) {
+                    const float4 kj = kj4[h * NC / 4 + q];
+                    const float4 qj = qj4[h * NC / 4 + q];
+                    const float *qah = qa + h * NC + 4 * q, *kah = ka + h * NC + 4 * q;
+                    caj = fmaf(qah[0], kj.x, fmaf(qah[1], kj.y, fmaf(qah[2], kj.z, fmaf(qah[3], kj.w, caj))));
+                    cja = fmaf(qj.x, kah[0], fmaf(qj.y, kah[1], fmaf(qj.z, kah[2], fmaf(qj.w, kah[3], cja))));
+                }
+                caj *= isnc;
+                cja *= isnc;
+                if (h < K) {
+                    Saj = fmaf(caj, B[h], Saj);
+                    Sja = fmaf(cja, B[h], Sja);
+                } else {
+                    const int t = h - K;
+                    vax = fmaf(caj, va[3 * t], vax);
+                    vay = fmaf(caj, va[3 * t + 1], vay);
+                    vaz = fmaf(caj, va[3 * t + 2], vaz);
+                    vjx = fmaf(cja, vj[3 * t], vjx);
+                    vjy = fmaf(cja, vj[3 * t + 1], vjy);
+                    vjz = fmaf(cja, vj[3 * t + 2], vjz);
+                }
+            }
+            const float pa = Saj * fc, pj = Sja * fc;
+            fx += pa * (nx + vax) - pj * (-nx + vjx);
+            fy += pa * (ny + vay) - pj * (-ny + vjy);
+            fz += pa * (nz + vaz) - pj * (-nz + vjz);
+        }
+        __syncwarp();
     };
-    for_active_canonical(g.col, g.row_ptr[a], g.row_ptr[a + 1], sh_queue[warp], lane, active, edge);
+
+    const int beg = g.row_ptr[a], end = g.row_ptr[a + 1];
+    int queued = 0, taken = 0;
+    for (int base = beg; base < end && alive; base += 32) {
+        const int e = base + lane;
+        const int j = e < end ? __ldg(g.col + e) : -1;
+        bool act = false;
+        if (j >= 0) {
+            const float dx = min_img(__ldg(g.x + 3 * j) - xa, bx, ibx);
+            const float dy = min_img(__ldg(g.x + 3 * j + 1) - ya, by, iby);
+            const float dz = min_img(__ldg(g.x + 3 * j + 2) - za, bz, ibz);
+            act = dx * dx + dy * dy + dz * dz < rc2;
+        }
+        const unsigned m = __ballot_sync(DMTS_FULL, act);
+        if (act) queue[(queued + __popc(m & ((1u << lane) - 1u))) & 63] = j;
+        queued += __popc(m);
+        __syncwarp();
+        if (queued - taken >= 32) {
+            batch(taken, 32);
+            taken += 32;
+        }
+    }
+    if (alive && queued > taken) batch(taken, queued - taken);
+    if (!alive) return;
     fx = fmaf(g.scale, fx, rx); fy = fmaf(g.scale, fy, ry); fz = fmaf(g.scale, fz, rz);
     if (g.bonds.ptr) {
         float e = 0.f;
@@ -225,79 +296,163 @@ __global__ void __launch_bounds__(128) k_nc_head(NCHeadArgs g) {
     }
 }
 
-void launch_nc_head(int K, int n_c, int n_l, const NCHeadArgs &a, cudaStream_t st) {
-    if (a.n_atoms == 0) return;
-    const int blocks = (a.n_atoms + 3) / 4;
-    if (K == 8 && n_c == 8 && n_l == 2) k_nc_head<8, 8, 2><<<blocks, 128, 0, st>>>(a);
-    else if (K == 8 && n_c == 8 && n_l == 1) k_nc_head<8, 8, 1><<<blocks, 128, 0, st>>>(a);
-    else if (K == 8 && n_c == 8 && n_l == 3) k_nc_head<8, 8, 3><<<blocks, 128, 0, st>>>(a);
-    else if (K == 8 && n_c == 8 && n_l == 4) k_nc_head<8, 8, 4><<<blocks, 128, 0, st>>>(a);
+template <int K, int NC, int NL>
+static void nc_head_launch(const NCHeadArgs &a, cudaStream_t st) {
+    using SM = NCHeadSmem<K, NC, NL>;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_nc_head<K, NC, NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes);
+        attr = true;
+    }
+    const int blocks = (a.n_atoms + NCH_WARPS - 1) / NCH_WARPS;
+    k_nc_head<K, NC, NL><<<blocks, NCH_WARPS * 32, SM::bytes, st>>>(a);
 }
 
-// Block per replica: FP64 sum (of fp32 batch sums of eight atoms) of F_in
-// over the replica, then subtract the mean.
-__global__ void k_mean_sub(const float *__restrict__ F_in, float *__restrict__ F_out, const int *__restrict__ rep_off,
-                           double *__restrict__ net, const int *__restrict__ err) {
-    if (*err) return;
-    __shared__ double red[3][32];
-    __shared__ double mean[3];
-    const int r = blockIdx.x;
-    const int beg = rep_off[r], end = rep_off[r + 1];
-    double s[3] = {0.0, 0.0, 0.0};
-    // eight independent loads in flight per thread, then the FP64 adds in order
-    const int stride = blockDim.x;
-    for (int i0 = beg + threadIdx.x; i0 < end; i0 += 8 * stride) {
-        float v[8][3];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int i = i0 + u * stride;
-            for (int a = 0; a < 3; ++a) v[u][a] = i < end ? F_in[3 * i + a] : 0.f;
+void launch_nc_head(int K, int n_c, int n_l, const NCHeadArgs &a, cudaStream_t st) {
+    if (a.n_atoms == 0) return;
+    if (K == 8 && n_c == 8 && n_l == 2) nc_head_launch<8, 8, 2>(a, st);
+    else if (K == 8 && n_c == 8 && n_l == 1) nc_head_launch<8, 8, 1>(a, st);
+    else if (K == 8 && n_c == 8 && n_l == 3) nc_head_launch<8, 8, 3>(a, st);
+    else if (K == 8 && n_c == 8 && n_l == 4) nc_head_launch<8, 8, 4>(a, st);
+}
+
+// Mean subtraction over each replica in three short kernels. A replica is
+// cut into parts of MS_PART atoms counted from its own first atom, so every
+// sum below depends only on the replica's atoms, never on which other
+// replicas share the batch. Within a part, thread t adds atoms t, t + 256,
+// ... in fp32 (at most four), the block then adds the thread sums in fp64 in
+// a fixed tree; the per-part fp64 sums are added in part order.
+constexpr int MS_PART = 1024, MS_THREADS = 256;
+
+// part_off[r] = sum over r' < r of ceil(len_r' / MS_PART), r = 0 .. n_rep;
+// net = 0 for replicas without atoms.
+__global__ void k_mean_part_off(const int *__restrict__ rep_off, int n_rep, int *__restrict__ part_off,
+                                double *__restrict__ net) {
+    __shared__ int carry, warp_tot[32];
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int r0 = 0; r0 < n_rep; r0 += blockDim.x) {
+        const int r = r0 + threadIdx.x;
+        const int len = r < n_rep ? rep_off[r + 1] - rep_off[r] : 0;
+        const int v = (len + MS_PART - 1) / MS_PART;
+        if (net && r < n_rep && len == 0)
+            for (int c = 0; c < 3; ++c) net[3 * r + c] = 0.0;
+        int inc = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(DMTS_FULL, inc, o);
+            if (lane >= o) inc += t;
         }
-        // batch of eight summed in fp32, batch sums accumulated in fp64 (the
-        // fp64 units are few on this GPU: this keeps one block per replica fast)
-        float b[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-            for (int a = 0; a < 3; ++a) b[a] += v[u][a];
-        for (int a = 0; a < 3; ++a) s[a] += (double)b[a];
+        if (lane == 31) warp_tot[wid] = inc;
+        __syncthreads();
+        if (wid == 0) {
+            int w = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(DMTS_FULL, w, o);
+                if (lane >= o) w += t;
+            }
+            warp_tot[lane] = w;    // inclusive over warps
+        }
+        __syncthreads();
+        const int excl = carry + (wid > 0 ? warp_tot[wid - 1] : 0) + inc - v;
+        if (r < n_rep) part_off[r] = excl;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = excl + v;
+        __syncthreads();
     }
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int a = 0; a < 3; ++a) {
-        s[a] = warp_sum_d(s[a]);
-        if (lane == 0) red[a][wid] = s[a];
+    if (threadIdx.x == 0) part_off[n_rep] = carry;
+}
+
+// Replica r and part p of block b (b < part_off[n_rep]); false for spare blocks.
+__device__ __forceinline__ bool mean_part_of(const int *part_off, int n_rep, int b, int &r, int &p) {
+    if (b >= part_off[n_rep]) return false;
+    int lo = 0, hi = n_rep;     // largest r with part_off[r] <= b
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (part_off[mid] <= b) lo = mid; else hi = mid;
+    }
+    // replicas without atoms have no parts: skip to the one that owns b
+    while (part_off[lo + 1] <= b) ++lo;
+    r = lo;
+    p = b - part_off[lo];
+    return true;
+}
+
+__global__ void __launch_bounds__(MS_THREADS) k_mean_partial(const float *__restrict__ F_in,
+                                                             const int *__restrict__ rep_off,
+                                                             const int *__restrict__ part_off, int n_rep,
+                                                             double *__restrict__ partial, const int *__restrict__ err) {
+    if (*err) return;
+    int r, p;
+    if (!mean_part_of(part_off, n_rep, blockIdx.x, r, p)) return;
+    const int lo = rep_off[r] + p * MS_PART, hi = min(rep_off[r + 1], lo + MS_PART);
+    float v[MS_PART / MS_THREADS][3];
+#pragma unroll
+    for (int k = 0; k < MS_PART / MS_THREADS; ++k) {
+        const int i = lo + threadIdx.x + k * MS_THREADS;
+        for (int c = 0; c < 3; ++c) v[k][c] = i < hi ? F_in[3 * i + c] : 0.f;
+    }
+    __shared__ double red[3][MS_THREADS / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int c = 0; c < 3; ++c) {
+        float t = 0.f;
+#pragma unroll
+        for (int k = 0; k < MS_PART / MS_THREADS; ++k) t += v[k][c];
+        const double d = warp_sum_d((double)t);
+        if (lane == 0) red[c][wid] = d;
     }
     __syncthreads();
     if (threadIdx.x < 3) {
         double t = 0.0;
-        for (int k = 0; k < nw; ++k) t += red[threadIdx.x][k];
-        if (net) net[3 * r + threadIdx.x] = t;
-        mean[threadIdx.x] = end > beg ? t / (double)(end - beg) : 0.0;
+        for (int w = 0; w < MS_THREADS / 32; ++w) t += red[threadIdx.x][w];
+        partial[3 * (size_t)blockIdx.x + threadIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(MS_THREADS) k_mean_apply(const float *__restrict__ F_in, float *__restrict__ F_out,
+                                                           const int *__restrict__ rep_off,
+                                                           const int *__restrict__ part_off, int n_rep,
+                                                           const double *__restrict__ partial,
+                                                           double *__restrict__ net, const int *__restrict__ err) {
+    if (*err) return;
+    int r, p;
+    if (!mean_part_of(part_off, n_rep, blockIdx.x, r, p)) return;
+    __shared__ float mean[3];
+    const int beg = rep_off[r], end = rep_off[r + 1];
+    if (threadIdx.x < 3) {
+        double t = 0.0;
+        for (int q = part_off[r]; q < part_off[r + 1]; ++q) t += partial[3 * (size_t)q + threadIdx.x];
+        if (net && p == 0) net[3 * r + threadIdx.x] = t;
+        mean[threadIdx.x] = (float)(t / (double)(end - beg));
     }
     __syncthreads();
-    const float mx = (float)mean[0], my = (float)mean[1], mz = (float)mean[2];
-    for (int i0 = beg + threadIdx.x; i0 < end; i0 += 8 * stride) {
-        float v[8][3];
+    const int lo = beg + p * MS_PART, hi = min(end, lo + MS_PART);
+    const float mx = mean[0], my = mean[1], mz = mean[2];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int i = i0 + u * stride;
-            for (int a = 0; a < 3; ++a) v[u][a] = i < end ? F_in[3 * i + a] : 0.f;
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int i = i0 + u * stride;
-            if (i < end) {
-                F_out[3 * i] = v[u][0] - mx;
-                F_out[3 * i + 1] = v[u][1] - my;
-                F_out[3 * i + 2] = v[u][2] - mz;
-            }
+    for (int k = 0; k < MS_PART / MS_THREADS; ++k) {
+        const int i = lo + threadIdx.x + k * MS_THREADS;
+        if (i < hi) {
+            F_out[3 * i] = F_in[3 * i] - mx;
+            F_out[3 * i + 1] = F_in[3 * i + 1] - my;
+            F_out[3 * i + 2] = F_in[3 * i + 2] - mz;
         }
     }
 }
 
-void launch_mean_sub(const float *F_in, float *F_out, const int *rep_off, int n_rep, double *net,
-                     const int *err, cudaStream_t st) {
+size_t mean_sub_scratch_bytes(int n_atoms, int n_rep) {
+    const size_t parts = (size_t)(n_atoms + MS_PART - 1) / MS_PART + (size_t)n_rep;
+    return 3 * sizeof(double) * parts + sizeof(int) * ((size_t)n_rep + 1) + 64;
+}
+
+void launch_mean_sub(const float *F_in, float *F_out, const int *rep_off, int n_rep, int n_atoms, double *net,
+                     void *scratch, const int *err, cudaStream_t st) {
     if (n_rep == 0) return;
-    k_mean_sub<<<n_rep, 1024, 0, st>>>(F_in, F_out, rep_off, net, err);
+    const int parts = (n_atoms + MS_PART - 1) / MS_PART + n_rep;   // bound on the parts of all replicas
+    double *partial = static_cast<double *>(scratch);
+    int *part_off = reinterpret_cast<int *>(partial + 3 * (size_t)parts);
+    k_mean_part_off<<<1, 1024, 0, st>>>(rep_off, n_rep, part_off, net);
+    k_mean_partial<<<parts, MS_THREADS, 0, st>>>(F_in, rep_off, part_off, n_rep, partial, err);
+    k_mean_apply<<<parts, MS_THREADS, 0, st>>>(F_in, F_out, rep_off, part_off, n_rep, partial, net, err);
 }
 
 // ---------------------------------------------------------------- prior

@@ -36,15 +36,17 @@ struct NCHeadArgs {
     const uint8_t *species;
     float *F;                      // [N][3] before mean subtraction
     const int *order;              // nullable processing order
-    const int *err;
+    int *err;                      // sticky device error word (read, and set on a timeout)
 };
 
 void launch_nc_vectors(int n, int C, int n_l, const float *A, const float *U, float *V, const int *err,
                        cudaStream_t st);
 void launch_nc_head(int K, int n_c, int n_l, const NCHeadArgs &a, cudaStream_t st);
 // F_out = F_in - (sum_{replica} F_in)/n_r, FP64 sums; net (nullable) [R][3].
-void launch_mean_sub(const float *F_in, float *F_out, const int *rep_off, int n_rep, double *net,
-                     const int *err, cudaStream_t st);
+// scratch: device memory of mean_sub_scratch_bytes(n_atoms, n_rep) bytes.
+size_t mean_sub_scratch_bytes(int n_atoms, int n_rep);
+void launch_mean_sub(const float *F_in, float *F_out, const int *rep_off, int n_rep, int n_atoms, double *net,
+                     void *scratch, const int *err, cudaStream_t st);
 
 struct PriorArgs {
     const float *x;
