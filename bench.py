@@ -26,6 +26,35 @@ if ROOT not in sys.path:
 import numpy as np  # noqa: E402
 
 WORKLOAD = "solvated_chain_23558"
+LARGE_WORKLOAD = "water_100000"
+
+# DRAM traffic per launch of the roofline kernel, dram__bytes_read.sum +
+# dram__bytes_write.sum from one ncu capture of this bench's workload (the
+# capture command and the counters are in profiles/). It is reported only
+# while the kernel's sources hash to the recorded value; after any change to
+# them it is null until a new capture is taken.
+NCU_TRAFFIC = {
+    "mp_bwd": {"bytes_per_launch": 153783552 + 15537152,
+               "sources": ["paper_2602_14975_gb300/csrc/mp.cu", "paper_2602_14975_gb300/csrc/mp.cuh",
+                           "paper_2602_14975_gb300/csrc/common.cuh", "include/dmts.h"],
+               "sha256": "3c5265f687d278eab356a30284dfd5cc3994f5e2a7f52d17ececc1ecfaa0bd64"},
+}
+
+
+def sources_sha256(paths):
+    import hashlib
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def ncu_traffic(kernel):
+    rec = NCU_TRAFFIC.get(kernel)
+    if not rec or rec["bytes_per_launch"] is None:
+        return None
+    return rec["bytes_per_launch"] if sources_sha256(rec["sources"]) == rec["sha256"] else None
 
 
 def parse():
@@ -225,9 +254,11 @@ def main():
     core.profile_enable(ctx, True)
     barrier()
     clocks.start()
+    torch.cuda.nvtx.range_push("dmts_outer_steps")    # the timed region, for ncu --nvtx-include
     e0.record(stream)
     core.respa_step(ctx, st, integ, args.steps)
     e1.record(stream)
+    torch.cuda.nvtx.range_pop()
     barrier()
     ck = clocks.stop()
     ctx.sync()
@@ -286,6 +317,52 @@ def main():
     bytes_in = 2 * sy.n_atoms * 12
     bytes_out = 2 * sy.n_atoms * 12 + 8
 
+    # ------------------------------------------------ 100,000-atom box
+    # the largest synthetic system: same models, the integrator and list
+    # kernels at a size where they stream enough bytes to be HBM-bound
+    WL = S.WORKLOADS[LARGE_WORKLOAD]
+    syL = WL["system"]()
+    csL, nsL = WL["cons"](), WL["nc"]()
+    ctxL = core.Context(cons=(csL, S.cons_weights(csL, WL["w_seed"])), nc=(nsL, S.nc_weights(nsL, WL["w_seed"])),
+                        device=local)
+    IL = WL["dmts"]
+    mL = core.masses_hmr(syL.species, syL.mol_id, syL.element_masses(), IL.hmr_delta)
+    dL = core.DeviceSystem(syL)
+    stL = core.MDState(dL, S.maxwell_boltzmann(mL, IL.temperature, WL["rng_seed"]), mL.astype(np.float32),
+                       seeds=IL.seed, replica_ids=[D.replica_id(rank, 0)])
+    integL = core.integrator(IL.dt_outer, IL.n_inner, IL.temperature, IL.gamma_ps, skin=skin)
+    n_large = max(5, min(20, args.steps // 10))
+    core.respa_step(ctxL, stL, integL, 3)
+    ctxL.sync()
+    core.profile_enable(ctxL, True)
+    barrier()
+    e0.record(stream)
+    core.respa_step(ctxL, stL, integL, n_large)
+    e1.record(stream)
+    barrier()
+    ctxL.sync()
+    profL = core.profile_read(ctxL)
+    core.profile_enable(ctxL, False)
+    ms_large = max_over_ranks(e0.elapsed_time(e1)) / n_large
+    stL.release()
+    stsL = WL["sts"]
+    mLe = syL.element_masses()
+    dL2 = core.DeviceSystem(syL)
+    stL2 = core.MDState(dL2, S.maxwell_boltzmann(mLe, stsL.temperature, WL["rng_seed"]), mLe.astype(np.float32),
+                        seeds=stsL.seed, replica_ids=[D.replica_id(rank, 0)])
+    integL2 = core.integrator(stsL.dt_outer, 1, stsL.temperature, stsL.gamma_ps, mode=1, skin=skin)
+    core.respa_step(ctxL, stL2, integL2, 3)
+    ctxL.sync()
+    barrier()
+    e0.record(stream)
+    core.respa_step(ctxL, stL2, integL2, 2 * n_large)
+    e1.record(stream)
+    barrier()
+    ctxL.sync()
+    ms_large_sts = max_over_ranks(e0.elapsed_time(e1)) / (2 * n_large)
+    stL2.release()
+    del ctxL
+
     # ----------------------------------------------------------- serving
     # (1) the 23,558-atom system as a request of the serving loop
     r3 = core.ReplicaRequest(sy, v0, m_hmr, args.steps, I.seed, D.replica_id(rank, 0))
@@ -324,9 +401,6 @@ def main():
     pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pk_path):
         peaks = json.load(open(pk_path))
-    top = max(prof.items(), key=lambda kv: kv[1][1]) if prof else ("none", (1, 0.0))
-    name, (launches, tot_ms) = top
-    per_launch_s = tot_ms / max(launches, 1) * 1e-3
     C = cs.C
     # algorithmic FLOP per active edge (one layer), counted as 2 per FMA:
     # forward: radial 3*8 FMA + 3 mul + 9 FMA per channel;
@@ -334,15 +408,67 @@ def main():
     # channel, plus 30 FMA per lane for the direction derivatives.
     flop_edge = {"mp_fwd": 2 * 36 * C, "mp_bwd": 2 * 99 * C + 2 * 30 * 32}
     fp32_peak_tflops = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
-    if name in flop_edge:
-        achieved = flop_edge[name] * e_cons / per_launch_s / 1e12
-        roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
-                "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops, "traffic": None,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz (nominal unit counts and max clock)",
-                "work_per_launch": f"{flop_edge[name]} FLOP x {e_cons} active edges"}
-    else:
-        roof = {"kernel": name, "bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"),
-                "unit": "GB/s", "frac": None, "traffic": None}
+    fp32_src = "152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz (nominal unit counts and max clock)"
+
+    def per_launch_s(pr, k):
+        v = pr.get(k)
+        return v[1] / v[0] * 1e-3 if v and v[0] else None
+
+    ranked = sorted(((k, v) for k, v in prof.items() if k in flop_edge), key=lambda kv: -kv[1][1])
+    name = ranked[0][0] if ranked else "mp_bwd"
+    pl = per_launch_s(prof, name)
+    achieved = flop_edge[name] * e_cons / pl / 1e12 if pl else None
+    roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
+            "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops if achieved else None,
+            "traffic": ncu_traffic(name), "peak_source": fp32_src,
+            "work_per_launch": f"{flop_edge[name]} FLOP x {e_cons} active edges",
+            "algorithmic_bytes_per_launch": None}
+    # node arrays once (fp32 unless noted) and the active-edge stream (4 B of
+    # column index per active entry): forward reads s, x and writes A, q
+    # (+ its bf16 copy); the adjoint reads s, gA, g_s and x and writes g_s
+    # (+ bf16 copy) and F
+    nlm = (cs.lmax + 1) ** 2
+    n_at = sy.n_atoms
+    alg_bytes = {"mp_fwd": n_at * (4 * C + 12 + 4 * nlm * C + 6 * (cs.lmax + 1) * C) + 4 * e_cons,
+                 "mp_bwd": n_at * (4 * C + 4 * nlm * C + 4 * C + 6 * C + 12 + 12) + 4 * e_cons}
+    roof["algorithmic_bytes_per_launch"] = alg_bytes[name]
+
+    # every hot kernel against its own bound (per-launch averages over the
+    # timed region; algorithmic work counts each node array once and each
+    # edge stream once)
+    hbm = peaks.get("hbm_gbs")
+    bf16_pk = peaks.get("bf16_tflops_sustained")
+    N, NL = sy.n_atoms, cs.lmax + 1
+    gemm_flop_cons = 2.0 * N * C * C * (2 * cs.L * (NL + 1) + 2)
+    Cn, qkw = ns.C, 2 * (ns.K + ns.n_l) * ns.n_c
+    gemm_flop_nc = 2.0 * N * Cn * (2 * Cn + Cn + qkw)
+
+    def rate(work, seconds, unit_scale):
+        return work / seconds / unit_scale if seconds else None
+
+    t_gemm = prof.get("gemm_tc", (0, 0.0))[1] * 1e-3 / args.steps
+    t_ncg = prof.get("nc_gemm_tc", (0, 0.0))[1] * 1e-3 / args.steps
+    nc_bytes = N * (qkw * 4 + ns.n_l * 12 + 12 + 12) + 4 * e_nc
+    kr = {}
+    for k in ("mp_fwd", "mp_bwd"):
+        a = rate(flop_edge[k] * e_cons, per_launch_s(prof, k), 1e12)
+        kr[k] = {"row": "a2+a3" if k == "mp_fwd" else "a5", "bound": "alu", "tflops": a,
+                 "frac_fp32_peak": a / fp32_peak_tflops if a else None}
+    g = rate(gemm_flop_cons, t_gemm, 1e12)
+    kr["gemm_tc"] = {"row": "a4", "bound": "tensor", "tflops": g, "frac_bf16_sustained": g / bf16_pk if g and bf16_pk else None,
+                     "flop_per_step": gemm_flop_cons}
+    g = rate(gemm_flop_nc * I.n_inner, t_ncg, 1e12)
+    kr["nc_gemm_tc"] = {"row": "a4 (NC)", "bound": "tensor", "tflops": g,
+                        "frac_bf16_sustained": g / bf16_pk if g and bf16_pk else None}
+    b = rate(nc_bytes, per_launch_s(prof, "nc_head"), 1e9)
+    kr["nc_head"] = {"row": "a7", "bound": "hbm", "gbs": b, "frac_hbm": b / hbm if b and hbm else None,
+                     "bytes_per_launch": nc_bytes}
+    b = rate(65.0 * N, per_launch_s(prof, "integrate"), 1e9)
+    kr["integrate"] = {"row": "a8", "bound": "hbm", "gbs": b, "frac_hbm": b / hbm if b and hbm else None,
+                       "bytes_per_launch": 65 * N}
+    b = rate(65.0 * syL.n_atoms, per_launch_s(profL, "integrate"), 1e9)
+    kr["integrate_100k"] = {"row": "a8", "bound": "hbm", "gbs": b, "frac_hbm": b / hbm if b and hbm else None,
+                            "bytes_per_launch": 65 * syL.n_atoms}
     shares = {k: {"launches": v[0], "ms_per_step": v[1] / args.steps,
                   "share": v[1] / max(sum(x[1] for x in prof.values()), 1e-9)} for k, v in prof.items()}
 
@@ -372,6 +498,13 @@ def main():
         "clocks": ck,
         "roofline": roof,
         "kernels": shares,
+        "kernel_roofline": kr,
+        "large_system": {"workload": syL.name, "n_atoms": syL.n_atoms, "steps": n_large,
+                         "ns_per_day": ns_per_day(IL.dt_outer, 1e3 / ms_large) * world, "ms_per_step": ms_large,
+                         "sts_ns_per_day": ns_per_day(stsL.dt_outer, 1e3 / ms_large_sts) * world,
+                         "sts_ms_per_step": ms_large_sts,
+                         "speedup_vs_sts": ns_per_day(IL.dt_outer, 1e3 / ms_large) / ns_per_day(stsL.dt_outer, 1e3 / ms_large_sts),
+                         "kernels_ms_per_step": {k: v[1] / n_large for k, v in profL.items()}},
         "active_edges": {"cons": e_cons, "nc": e_nc},
     }
     if rank == 0 and not args.no_cpu and world == 1:

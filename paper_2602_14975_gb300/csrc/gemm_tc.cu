@@ -14,6 +14,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -27,6 +28,7 @@ namespace {
 constexpr int TC_M = 128;
 constexpr int TC_K = 64;             // bf16 elements per 128-byte swizzled row
 constexpr int TC_STAGES = 4;
+constexpr int kBNTarget = 64;      // preferred column-tile width
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
     asm volatile(
@@ -340,16 +342,14 @@ int launch_gemm_tc(int M, int N, int K, const __nv_bfloat16 *Act, const __nv_bfl
     if (M == 0) return 0;
     if (!gemm_tc_supported(N, K)) return -1;
     if (((uintptr_t)Act & 15) || ((uintptr_t)Wt & 15)) return -2;
-    // column tile: whole N up to 256, else the largest multiple of 16 dividing N
-    // column tile: whole N up to 160, else the largest multiple of 16 <= 128
-    // dividing N (a smaller staging tile leaves room for more CTAs per SM)
-    int BN = N;
-    if (BN > 160) {
-        BN = 0;
-        for (int b = 128; b >= 16; b -= 16)
-            if (N % b == 0) { BN = b; break; }
-        if (!BN) return -1;
-    }
+    // column tile: the multiple of 16 dividing N closest to kBNTarget (the
+    // smaller on a tie). Narrow tiles give more CTAs per SM (a smaller
+    // epilogue staging tile) and more CTAs per contraction, which the
+    // latency-bound epilogues of these short-K contractions need.
+    int BN = 0;
+    for (int b = 16; b <= 256 && b <= N; b += 16)
+        if (N % b == 0 && (BN == 0 || std::abs(b - kBNTarget) < std::abs(BN - kBNTarget))) BN = b;
+    if (!BN) return -1;
     int tmem_cols = 32;
     while (tmem_cols < BN) tmem_cols <<= 1;
     CUtensorMap ma, mb;
