@@ -370,14 +370,21 @@ long long dmts_replica_footprint(const dmts_ctx *ctx, int n_atoms);
 
 /* ------------------------------------------------------ instrumentation */
 /* (No counterpart in the paper: measurement support.) While enabled, every
- * kernel launch of the context is bracketed by a pair of CUDA events on its
- * own stream. dmts_profile_read() synchronises the device and returns, for
- * kernel slot `idx` (0 <= idx < count returned by a call with idx = -1), the
- * kernel's name, number of launches and summed duration in ms since the last
- * enable. Disabling clears nothing; enabling clears the table. */
+ * named step of the context (one kernel, or a few that always run together,
+ * such as the cell pass of the neighbour build) is bracketed by a pair of
+ * CUDA events on its own stream. dmts_profile_read() synchronises the device
+ * and returns, for slot `idx` (0 <= idx < count returned by a call with
+ * idx = -1), the step's name, number of executions and summed duration in ms
+ * since the last enable. Disabling clears nothing; enabling clears the table. */
 dmts_status dmts_profile_enable(dmts_ctx *ctx, int enable);
 int dmts_profile_read(dmts_ctx *ctx, int idx, char *name, int name_cap, long long *launches,
                       double *total_ms);
+
+/* (No counterpart in the paper: measurement support.) Number of kernels this
+ * library has launched in this process since it was loaded, over all
+ * contexts and devices (counted on the host at each launch). The difference
+ * of two reads around a region is the region's launch count. */
+unsigned long long dmts_kernel_launches(void);
 
 #ifdef __cplusplus
 }

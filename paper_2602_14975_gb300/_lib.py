@@ -88,7 +88,7 @@ EXPORTS = ("dmts_create", "dmts_destroy", "dmts_last_error", "dmts_sync", "nbr_b
            "energy_forces_cons", "forces_nc", "respa_step", "dmts_state_release", "run_replicas",
            "dmts_masses_hmr", "dmts_bond_table", "dmts_philox_words", "dmts_gaussians",
            "dmts_replica_footprint", "dmts_profile_enable", "dmts_profile_read", "nbr_build_noalloc",
-           "dmts_contract_bf16")
+           "dmts_contract_bf16", "dmts_kernel_launches")
 
 
 def lib_path() -> str:
@@ -100,6 +100,8 @@ def _declare(L):
     L.dmts_create.restype = i
     L.dmts_create.argtypes = [ct.POINTER(vp), ct.POINTER(Model), ct.POINTER(Model), ct.POINTER(Prior), i]
     L.dmts_destroy.restype = None
+    L.dmts_kernel_launches.restype = ct.c_ulonglong
+    L.dmts_kernel_launches.argtypes = []
     L.dmts_destroy.argtypes = [vp]
     L.dmts_last_error.restype = ct.c_char_p
     L.dmts_last_error.argtypes = [vp]

@@ -274,6 +274,12 @@ def profile_enable(ctx: Context, on: bool = True):
     L.check(ctx.lib.dmts_profile_enable(ctx.handle, 1 if on else 0), ctx.handle)
 
 
+def kernel_launches(ctx: Context) -> int:
+    """Kernels the library has launched in this process so far (all
+    contexts); the difference of two reads counts a region's launches."""
+    return int(ctx.lib.dmts_kernel_launches())
+
+
 def profile_read(ctx: Context) -> dict:
     """{kernel: (launches, total_ms)} since the last profile_enable(True)."""
     n = ctx.lib.dmts_profile_read(ctx.handle, -1, None, 0, None, None)

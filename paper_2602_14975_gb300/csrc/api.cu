@@ -493,6 +493,7 @@ void rebuild_lists(dmts_ctx *ctx, StateInternal *si, const SysView &v, cudaStrea
                     (int *)si->nc_col.p, si->nc_cap, st);
     }
     k_set_int<<<1, 1, 0, st>>>((int *)si->gate.p, 0);
+    count_launch();
 }
 
 void prepare_nbr_work_async(dmts_ctx *ctx, StateInternal *si, const SysView &v, NbrWork &nw) {
@@ -600,6 +601,7 @@ dmts_status init_state(dmts_ctx *ctx, dmts_state *stt, float skin, cudaStream_t 
         return fail(ctx, DMTS_E_OOM, "state allocation failed");
     atom_rep_map(sys->rep_off, sys->n_replicas, N, (int *)si->atom_rep.p, st);
     k_set_int<<<1, 1, 0, st>>>((int *)si->gate.p, 1);
+    count_launch();
     SysView v = state_view(stt);
     NbrWork nw;
     s = prepare_nbr_work(ctx, si->scratch, v, si->grids, si->n_cells, (int *)si->gate.p, nw, st);
@@ -995,7 +997,10 @@ dmts_status dmts_philox_words(dmts_ctx *ctx, uint64_t seed, uint32_t replica, ui
                               uint32_t *out, void *stream) {
     if (!ctx || !out || count < 0) return fail(ctx, DMTS_E_INVALID, "bad argument");
     cudaSetDevice(ctx->device);
-    if (count) k_philox_words<<<(count + 255) / 256, 256, 0, (cudaStream_t)stream>>>(seed, replica, step, atom0, count, out);
+    if (count) {
+        k_philox_words<<<(count + 255) / 256, 256, 0, (cudaStream_t)stream>>>(seed, replica, step, atom0, count, out);
+        count_launch();
+    }
     return ck(ctx, cudaGetLastError(), "philox launch") ? DMTS_OK : DMTS_E_CUDA;
 }
 
@@ -1003,7 +1008,10 @@ dmts_status dmts_gaussians(dmts_ctx *ctx, uint64_t seed, uint32_t replica, uint6
                            float *out, void *stream) {
     if (!ctx || !out || count < 0) return fail(ctx, DMTS_E_INVALID, "bad argument");
     cudaSetDevice(ctx->device);
-    if (count) k_gaussians<<<(count + 255) / 256, 256, 0, (cudaStream_t)stream>>>(seed, replica, step, atom0, count, out);
+    if (count) {
+        k_gaussians<<<(count + 255) / 256, 256, 0, (cudaStream_t)stream>>>(seed, replica, step, atom0, count, out);
+        count_launch();
+    }
     return ck(ctx, cudaGetLastError(), "gaussian launch") ? DMTS_OK : DMTS_E_CUDA;
 }
 

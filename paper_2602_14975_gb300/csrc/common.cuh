@@ -15,6 +15,10 @@ constexpr double kAccConvD = 4.184e-4;
 constexpr double kBoltzmann = 8.314462618 / 4184.0;   // kcal/mol/K
 
 // Sticky device error word (one per context).
+// Host-side count of this library's kernel launches (every launch site calls
+// it right after the launch); read through dmts_kernel_launches().
+void count_launch();
+
 __device__ __forceinline__ void set_error(int *err, int code) { atomicCAS(err, 0, code); }
 
 __device__ __forceinline__ float warp_sum(float v) {

@@ -365,6 +365,7 @@ int launch_gemm_tc(int M, int N, int K, const __nv_bfloat16 *Act, const __nv_bfl
     }
     dim3 grid((M + TC_M - 1) / TC_M, N / BN);
     k_gemm_tc<<<grid, 256, smem, st>>>(ma, mb, M, N, K, BN, tmem_cols, n_stages, e, err);
+    count_launch();
     return 0;
 }
 

@@ -17,6 +17,7 @@ void launch_embed(int n, int C, const uint8_t *species, const float *emb, float 
     if (n == 0) return;
     const size_t tot = (size_t)n * C;
     k_embed<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, C, species, emb, s);
+    count_launch();
 }
 
 // e_atom[i] = scale * sum_c u[i][c]  (warp per atom)
@@ -32,6 +33,7 @@ __global__ void k_rowsum(int n, int C, const float *u, float scale, float *e_ato
 void launch_rowsum(int n, int C, const float *u, float scale, float *e_atom, cudaStream_t st) {
     if (n == 0) return;
     k_rowsum<<<(n + 7) / 8, 256, 0, st>>>(n, C, u, scale, e_atom);
+    count_launch();
 }
 
 // V[i][h][a] = sum_c U[h][c] A[i][1+a][c]   (vector part of tensor head h)
@@ -52,6 +54,7 @@ void launch_nc_vectors(int n, int C, int n_l, const float *A, const float *U, fl
                        cudaStream_t st) {
     if (n == 0) return;
     k_nc_vectors<<<(n + 7) / 8, 256, 0, st>>>(n, C, n_l, A, U, V, err);
+    count_launch();
 }
 
 __device__ __forceinline__ void bond_force(const BondTable &b, const float *x, int a, float bx, float by,
@@ -306,6 +309,7 @@ static void nc_head_launch(const NCHeadArgs &a, cudaStream_t st) {
     }
     const int blocks = (a.n_atoms + NCH_WARPS - 1) / NCH_WARPS;
     k_nc_head<K, NC, NL><<<blocks, NCH_WARPS * 32, SM::bytes, st>>>(a);
+    count_launch();
 }
 
 void launch_nc_head(int K, int n_c, int n_l, const NCHeadArgs &a, cudaStream_t st) {
@@ -451,8 +455,11 @@ void launch_mean_sub(const float *F_in, float *F_out, const int *rep_off, int n_
     double *partial = static_cast<double *>(scratch);
     int *part_off = reinterpret_cast<int *>(partial + 3 * (size_t)parts);
     k_mean_part_off<<<1, 1024, 0, st>>>(rep_off, n_rep, part_off, net);
+    count_launch();
     k_mean_partial<<<parts, MS_THREADS, 0, st>>>(F_in, rep_off, part_off, n_rep, partial, err);
+    count_launch();
     k_mean_apply<<<parts, MS_THREADS, 0, st>>>(F_in, F_out, rep_off, part_off, n_rep, partial, net, err);
+    count_launch();
 }
 
 // ---------------------------------------------------------------- prior
@@ -521,6 +528,7 @@ __global__ void __launch_bounds__(128) k_prior(PriorArgs g) {
 void launch_prior(const PriorArgs &a, cudaStream_t st) {
     if (a.n_atoms == 0) return;
     k_prior<<<(a.n_atoms + 3) / 4, 128, 0, st>>>(a);
+    count_launch();
 }
 
 // ----------------------------------------------------------- integrator
@@ -569,6 +577,7 @@ __global__ void k_integrate(IntegArgs g) {
 void launch_integrate(const IntegArgs &a, cudaStream_t st) {
     if (a.n_atoms == 0) return;
     k_integrate<<<(a.n_atoms + 255) / 256, 256, 0, st>>>(a);
+    count_launch();
 }
 
 __global__ void k_advance(uint64_t *step, int n_rep, uint64_t add, const int *err) {
@@ -580,6 +589,7 @@ __global__ void k_advance(uint64_t *step, int n_rep, uint64_t add, const int *er
 void launch_advance_step(uint64_t *step, int n_rep, uint64_t add, const int *err, cudaStream_t st) {
     if (n_rep == 0) return;
     k_advance<<<(n_rep + 127) / 128, 128, 0, st>>>(step, n_rep, add, err);
+    count_launch();
 }
 
 }  // namespace dmts

@@ -317,12 +317,14 @@ static void fwd_c(const EdgeGeom &g, const LayerIO &io, cudaStream_t st) {
         k_mp_fwd<C, LMAX, 8, SP><<<dim3(blocks, SP), MP_WARPS * 32, 0, st>>>(g, io);
     else
         k_mp_fwd<C, LMAX, 8, 1><<<blocks, MP_WARPS * 32, 0, st>>>(g, io);
+    count_launch();
 }
 
 template <int C, int LMAX>
 static void bwd_c(const EdgeGeom &g, const LayerIO &io, cudaStream_t st) {
     const int blocks = (g.n_atoms + MP_WARPS - 1) / MP_WARPS;
     k_mp_bwd<C, LMAX, 8><<<blocks, MP_WARPS * 32, 0, st>>>(g, io);
+    count_launch();
 }
 
 #define DMTS_DISPATCH(FN, C, LMAX, ...)                          \
@@ -461,6 +463,7 @@ void launch_gemm_f32(int M, int N, int K, const float *Act, const float *W, int 
     if (M == 0) return;
     dim3 grid((N + GN - 1) / GN, (M + GM - 1) / GM);
     k_gemm_f32<<<grid, 256, 0, st>>>(M, N, K, Act, W, trans, e);
+    count_launch();
 }
 
 // -------------------------------------------------- per-replica FP64 sums
@@ -494,6 +497,7 @@ void launch_replica_sum(const float *v, const int *rep_off, int n_rep, double *o
                         cudaStream_t st) {
     if (n_rep == 0) return;
     k_replica_sum<<<n_rep, 1024, 0, st>>>(v, rep_off, out, accumulate);
+    count_launch();
 }
 
 }  // namespace dmts

@@ -18,6 +18,7 @@ __global__ void k_atom_rep(const int *rep_off, int n_rep, int n, int *atom_rep) 
 void atom_rep_map(const int *rep_off, int n_rep, int n_atoms, int *atom_rep, cudaStream_t st) {
     if (n_atoms == 0) return;
     k_atom_rep<<<(n_atoms + 255) / 256, 256, 0, st>>>(rep_off, n_rep, n_atoms, atom_rep);
+    count_launch();
 }
 
 // Open replicas: bounding box -> origin and cell edge max(r_list, extent/dim).
@@ -331,16 +332,20 @@ __global__ void __launch_bounds__(1024) k_scan(const int *in, int n, int *out, l
 void scan_ints(const int *in, int n, int *out, long long capacity, long long *total, int *err,
                const int *gate, cudaStream_t st) {
     k_scan<<<1, 1024, 0, st>>>(in, n, out, capacity, total, err, gate);
+    count_launch();
 }
 
 void nbr_cells(const NbrWork &w, float r_list, cudaStream_t st) {
     if (w.n_atoms == 0) return;
     k_grid_open<<<w.n_rep, 256, 0, st>>>(w, r_list);
+    count_launch();
     cudaMemsetAsync(w.cell_cnt, 0, sizeof(int) * w.n_cells, st);
     const int nb = (w.n_atoms + 255) / 256;
     k_cell_assign<<<nb, 256, 0, st>>>(w);
+    count_launch();
     scan_ints(w.cell_cnt, w.n_cells, w.cell_start, -1, nullptr, w.err, w.gate, st);
     k_cell_scatter<<<nb, 256, 0, st>>>(w);
+    count_launch();
 }
 
 void nbr_fill(const NbrWork &w, float r_list, int *row_ptr, int *col, long long capacity, float *x_ref,
@@ -348,8 +353,12 @@ void nbr_fill(const NbrWork &w, float r_list, int *row_ptr, int *col, long long 
     if (w.n_atoms == 0) return;
     const int nb = (w.n_atoms + NB_WARPS - 1) / NB_WARPS;
     k_nbr_count_warp<<<nb, NB_WARPS * 32, 0, st>>>(w, r_list * r_list);
+    count_launch();
     scan_ints(w.counts, w.n_atoms, row_ptr, capacity, w.total, w.err, w.gate, st);
-    if (col) k_nbr_fill_warp<<<nb, NB_WARPS * 32, 0, st>>>(w, r_list * r_list, row_ptr, col, x_ref);
+    if (col) {
+        k_nbr_fill_warp<<<nb, NB_WARPS * 32, 0, st>>>(w, r_list * r_list, row_ptr, col, x_ref);
+        count_launch();
+    }
 }
 
 // ------------------------------------------------------------- sub-lists
@@ -396,8 +405,10 @@ void nbr_sublist(const NbrWork &w, const int *p_row, const int *p_col, float r, 
     if (w.n_atoms == 0) return;
     const int nb = (w.n_atoms + 127) / 128;
     k_sub_count<<<nb, 128, 0, st>>>(w, p_row, p_col, r * r);
+    count_launch();
     scan_ints(w.counts, w.n_atoms, row_ptr, capacity, w.total, w.err, w.gate, st);
     k_sub_fill<<<nb, 128, 0, st>>>(w, p_row, p_col, r * r, row_ptr, col);
+    count_launch();
 }
 
 }  // namespace dmts

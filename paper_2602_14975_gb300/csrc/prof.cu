@@ -1,10 +1,15 @@
 // Per-kernel CUDA-event timing (instrumentation of the measurement harness).
+#include <atomic>
 #include <cstring>
 #include <string>
 
 #include "engine.cuh"
 
 namespace dmts {
+
+static std::atomic<unsigned long long> g_kernel_launches{0};
+
+void count_launch() { g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
 
 int Profiler::slot(const char *name) {
     for (size_t k = 0; k < slots.size(); ++k)
@@ -100,5 +105,7 @@ int dmts_profile_read(dmts_ctx *ctx, int idx, char *name, int name_cap, long lon
     if (total_ms) *total_ms = s.ms;
     return 0;
 }
+
+unsigned long long dmts_kernel_launches(void) { return dmts::g_kernel_launches.load(std::memory_order_relaxed); }
 
 }  // extern "C"

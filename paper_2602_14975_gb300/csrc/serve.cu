@@ -316,6 +316,7 @@ dmts_status run_replicas(dmts_ctx *ctx, const dmts_request *reqs, int n_req, con
                     N, (const int *)map.p, (const float *)pk[cur].x.p, (const float *)pk[cur].v.p,
                     (const float *)pk[cur].fnc.p, (const float *)pk[cur].fcons.p, (float *)pk[nxt].x.p,
                     (float *)pk[nxt].v.p, (float *)pk[nxt].fnc.p, (float *)pk[nxt].fcons.p);
+                count_launch();
             }
             if (!waiting.empty()) {
                 const int na = astate.sys.n_atoms;

@@ -1,0 +1,157 @@
+"""Parity at the full size of the timed workload (23,558-atom solvated chain,
+conservative L = 3, C = 128, l_max = 2; NC C = 64, r_c = 4 Å), in the launch
+configuration the benchmark uses: the oracle cannot evaluate the whole
+system in a test's time for every quantity, so it checks the total energy
+once, the NC force on sampled atoms through their local environment, and the
+adjoint forces against finite differences of the energy on sampled atoms."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O
+from paper_2602_14975_gb300 import core
+from paper_2602_14975_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+W = S.WORKLOADS["solvated_chain_23558"]
+
+
+@pytest.fixture(scope="module")
+def chain():
+    return W["system"]()
+
+
+@pytest.fixture(scope="module")
+def weights():
+    cs, ns = W["cons"](), W["nc"]()
+    return S.cons_weights(cs, W["w_seed"]), S.nc_weights(ns, W["w_seed"])
+
+
+def _cluster(sy, center, radius):
+    """Atoms within `radius` (minimum image) of atom `center`, unwrapped
+    around it, as an open-boundary system; bonds inside the cluster kept.
+    Returns (system, index of the centre in it)."""
+    d = sy.x - sy.x[center]
+    d -= sy.box * np.round(d / sy.box)
+    keep = np.nonzero((d ** 2).sum(1) < radius ** 2)[0]
+    remap = -np.ones(sy.n_atoms, np.int64)
+    remap[keep] = np.arange(keep.size)
+    b = sy.bonds
+    bm = (remap[b[:, 0]] >= 0) & (remap[b[:, 1]] >= 0)
+    sub = S.System(f"{sy.name}_around_{center}", sy.x[center] + d[keep], sy.species[keep], sy.mol_id[keep],
+                   remap[b[bm]].astype(np.int32), sy.bond_r0[bm], np.zeros(3))
+    return sub, int(remap[center])
+
+
+def test_total_energy_full_size(chain, weights):
+    """U_MP + prior of the whole system: fp32 model within 1e-5 relative of
+    the oracle, bf16 contractions within 2e-3 relative."""
+    cb, _ = weights
+    d = core.DeviceSystem(chain)
+    E_or = O.cons_energy(chain, W["cons"](), cb) + O.prior(chain)[0]
+    for bf16, tol in ((False, 1e-5), (True, 2e-3)):
+        cs = S.cons_spec(3, 128, 2, bf16=bf16)
+        ctx = core.Context(cons=(cs, cb))
+        nb = core.nbr_build(ctx, d, cs.rc + 0.5)
+        E, _ = core.energy_forces_cons(ctx, d, nb, with_prior=True, forces=False)
+        assert abs(E.item() - E_or) <= tol * abs(E_or), (bf16, E.item(), E_or)
+
+
+@pytest.mark.parametrize("bf16", [False, True])
+def test_nc_forces_sampled_atoms_full_size(chain, weights, bf16):
+    """F_NC before mean subtraction on 24 sampled atoms: one NC layer plus
+    the head reach 2 r_c, so the oracle on the 8.5 Å environment of an atom
+    gives that atom's force exactly. The mean-subtracted GPU force plus the
+    reported net force over N is the force before subtraction."""
+    _, nb_w = weights
+    ns = S.nc_spec(64, rc=4.0, bf16=bf16)
+    ctx = core.Context(nc=(ns, nb_w))
+    d = core.DeviceSystem(chain)
+    nb = core.nbr_build(ctx, d, ns.rc + 0.5)
+    F, net = core.forces_nc(ctx, d, nb)
+    F = F.cpu().numpy().astype(np.float64)
+    net = net.cpu().numpy()[0]
+    pre = F + net / chain.n_atoms
+    rng = np.random.default_rng(3030)
+    sample = rng.choice(chain.n_atoms, 24, replace=False)
+    ref = np.zeros((sample.size, 3))
+    for k, i in enumerate(sample):
+        sub, c = _cluster(chain, int(i), 2 * ns.rc + 0.5)
+        Fs, net_s = O.nc_forces(sub, ns, nb_w)
+        ref[k] = Fs[c] + net_s / sub.n_atoms
+    err = np.abs(pre[sample] - ref).max()
+    if bf16:
+        assert err <= 2e-3 * np.sqrt((F ** 2).mean()), err
+    else:
+        assert err <= 1e-5 * np.abs(ref).max(), err
+    # net-force cancellation over the whole system (fp32 subtraction of an
+    # fp64 mean): the residual is rounding only
+    assert np.abs(F.sum(0)).max() <= 1e-5 * np.abs(F).sum()
+
+
+def test_adjoint_forces_vs_finite_differences_full_size(chain, weights):
+    """Adjoint forces of U_MP (fp32 contractions) against finite differences
+    of the GPU energy on 64 random atoms x 3 directions. Atoms farther than
+    L r_c from the moved atom contribute bit-identical terms to both
+    energies, but the ~3,000 atoms within it each carry fp32 rounding of
+    about 1e-6 of their energy (0.04 kcal/mol): the difference quotient
+    carries about 6e-7/h kcal/mol/A of rounding noise, and the central
+    difference an O(h^2) truncation error that at h = 1e-2 A is already of
+    the order of 1e-3 of the force (steep short-range Bessel terms). So the
+    check extrapolates (Richardson) from steps h = 1e-2 and 2h, which removes
+    the h^2 term and keeps the noise near 1e-4. (A step of 1e-4 A, right
+    for fp64 energies, would leave only rounding noise here.) The steps
+    actually taken in fp32 coordinates are used."""
+    cb, _ = weights
+    cs = S.cons_spec(3, 128, 2)
+    ctx = core.Context(cons=(cs, cb))
+    d = core.DeviceSystem(chain)
+    nb = core.nbr_build(ctx, d, cs.rc + 0.5)
+    _, F = core.energy_forces_cons(ctx, d, nb, with_prior=False)
+    F = F.cpu().numpy().astype(np.float64)
+    rng = np.random.default_rng(3031)
+    sample = rng.choice(chain.n_atoms, 64, replace=False)
+    h = 1e-2
+    x0 = d.x.clone()
+
+    def quotient(i, a, step):
+        xp, xm = x0[i, a] + step, x0[i, a] - step
+        d.x[i, a] = xp
+        Ep, _ = core.energy_forces_cons(ctx, d, nb, with_prior=False, forces=False)
+        d.x[i, a] = xm
+        Em, _ = core.energy_forces_cons(ctx, d, nb, with_prior=False, forces=False)
+        d.x[i, a] = x0[i, a]
+        return -(Ep.item() - Em.item()) / (float(xp.item()) - float(xm.item()))
+
+    fd = np.zeros((sample.size, 3))
+    for k, i in enumerate(sample):
+        for a in range(3):
+            fd[k, a] = (4.0 * quotient(i, a, h) - quotient(i, a, 2 * h)) / 3.0
+    err = np.abs(fd - F[sample]).max()
+    assert err <= 2e-3 * np.abs(F[sample]).max(), (err, np.abs(F[sample]).max())
+
+
+def test_respa_full_size_deterministic(chain, weights):
+    """Three outer steps of the timed configuration (bf16 contractions, HMR,
+    HHF) from the same state twice: bit-identical positions and velocities,
+    finite, and the atoms moved."""
+    cb, nb_w = weights
+    cs, ns = W["cons"](), W["nc"]()
+    ctx = core.Context(cons=(cs, cb), nc=(ns, nb_w))
+    I = W["dmts"]
+    m = core.masses_hmr(chain.species, chain.mol_id, chain.element_masses(), I.hmr_delta)
+    v0 = S.maxwell_boltzmann(m, I.temperature, W["rng_seed"])
+    out = []
+    for _ in range(2):
+        d = core.DeviceSystem(chain)
+        st = core.MDState(d, v0, m.astype(np.float32), seeds=I.seed, replica_ids=[0])
+        integ = core.integrator(I.dt_outer, I.n_inner, I.temperature, I.gamma_ps, skin=0.5)
+        core.respa_step(ctx, st, integ, 3)
+        ctx.sync()
+        out.append((d.x.cpu().numpy().copy(), st.v.cpu().numpy().copy()))
+        st.release()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    assert np.isfinite(out[0][0]).all() and np.isfinite(out[0][1]).all()
+    assert np.abs(out[0][0] - chain.x.astype(np.float32)).max() > 1e-3
