@@ -34,19 +34,30 @@ LARGE_WORKLOAD = "water_100000"
 # while the kernel's sources hash to the recorded value; after any change to
 # them it is null until a new capture is taken.
 NCU_TRAFFIC = {
-    "mp_bwd": {"bytes_per_launch": 153783552 + 15537152,
-               "sources": ["paper_2602_14975_gb300/csrc/mp.cu", "paper_2602_14975_gb300/csrc/mp.cuh",
-                           "paper_2602_14975_gb300/csrc/common.cuh", "include/dmts.h"],
-               "sha256": "3c5265f687d278eab356a30284dfd5cc3994f5e2a7f52d17ececc1ecfaa0bd64"},
+    "mp_bwd": {"bytes_per_launch": 153730048 + 14966272,
+               "sources": [("paper_2602_14975_gb300/csrc/mp.cu", "k_mp_bwd"),
+                           ("paper_2602_14975_gb300/csrc/mp.cuh", None),
+                           ("paper_2602_14975_gb300/csrc/common.cuh", None)],
+               "sha256": "9d4715a91d6a0a71082776a07147a2c38729014ae070fc595fffb29bb1f320d8"},
 }
 
 
-def sources_sha256(paths):
+def _kernel_text(text, name):
+    """Source text of the __global__ function `name` (from its template line
+    to the closing brace at column 0)."""
+    at = text.index(f" {name}(")
+    beg = text.rindex("template", 0, at)
+    end = text.index("\n}\n", at) + 3
+    return text[beg:end]
+
+
+def sources_sha256(sources):
     import hashlib
     h = hashlib.sha256()
-    for p in paths:
-        with open(os.path.join(ROOT, p), "rb") as f:
-            h.update(f.read())
+    for path, kernel in sources:
+        with open(os.path.join(ROOT, path), encoding="utf-8") as f:
+            text = f.read()
+        h.update((_kernel_text(text, kernel) if kernel else text).encode())
     return h.hexdigest()
 
 
