@@ -230,6 +230,12 @@ dmts_status forces_nc(dmts_ctx *ctx, const dmts_system *sys, const dmts_nbr *nbr
 
 typedef enum { DMTS_MODE_RESPA = 0, DMTS_MODE_STS = 1 } dmts_mode;
 
+/* Thermostat of the O-step (Sec. 2, "High Hydrogen Friction"): Langevin, or
+ * Fast Forward Langevin, which gives each atom the speed of the Langevin
+ * update w = c1 v + c2 sqrt(1/m) G but keeps the direction of v:
+ * v <- |w| v / |v| (per-atom 3-vector norms; an atom at rest takes w). */
+typedef enum { DMTS_LANGEVIN = 0, DMTS_FFL = 1 } dmts_thermostat;
+
 /*
  * Integrator parameters. RESPA: outer step Delta = dt_outer, n_inner inner
  * BAOAB steps of delta = Delta/n_inner driven by F_S = F_NC (+ bonds), outer
@@ -245,6 +251,7 @@ typedef struct {
     double gamma_ps[DMTS_MAX_SPECIES];
     int mode;                  /* dmts_mode */
     float skin;                /* neighbour-list skin (A); lists rebuilt when an atom moved > skin/2 */
+    int thermostat;            /* dmts_thermostat */
 } dmts_integrator;
 
 /*
@@ -279,6 +286,46 @@ dmts_status respa_step(dmts_ctx *ctx, dmts_state *st, const dmts_integrator *p, 
 
 /* Frees st->internal. */
 void dmts_state_release(dmts_ctx *ctx, dmts_state *st);
+
+/* ------------------------------------------------------------------ rewind */
+/*
+ * Guard against rare disagreements of the two force models (Sec. 2,
+ * "Preventing rare model disagreements (Rewind procedure)"): the run is cut
+ * into chunks of chunk_outer outer steps with a saved frame at the start of
+ * each. If, during a chunk, max |F - F_S| of any replica exceeds
+ * `threshold` (kcal/mol/A; measured at every outer kick) or a position or
+ * velocity became non-finite, the whole batch goes back to the saved frame
+ * and runs sts_steps single-time-step BAOAB steps of sts_dt (the same
+ * temperature, frictions, thermostat and skin, the full force -grad U),
+ * then resumes Algorithm 1 from there with fresh force caches.
+ * sts_steps * sts_dt must be a whole number m >= 1 of outer steps: the STS
+ * segment counts as m outer steps of the n_outer requested. Noise counters
+ * restart from the saved frame's, so a replayed segment is the same STS
+ * trajectory a direct STS run from the frame gives, bit for bit.
+ */
+typedef struct {
+    float threshold;           /* kcal/mol/A; +inf disables the force check */
+    int chunk_outer;           /* outer steps between saved frames (>= 1) */
+    int sts_steps;             /* STS steps after a rewind (>= 1) */
+    float sts_dt;              /* STS time step (fs) */
+} dmts_guard;
+
+typedef struct {
+    int n_rewinds;             /* out */
+    int n_chunks;              /* out: chunks of Algorithm 1 attempted */
+    float *chunk_max;          /* host [chunk_cap] (may be NULL): max |F - F_S| of each chunk */
+    int chunk_cap;
+    float *rewind_at;          /* host [rewind_cap] (may be NULL): outer steps completed at each rewind */
+    int rewind_cap;
+} dmts_guard_stats;
+
+/* n_outer outer steps of Algorithm 1 on `st` (p->mode must be RESPA) under
+ * the rewind guard. Allocates its saved frame (device, 4 N floats + per
+ * replica counters and energies) per call; synchronises the stream once per
+ * chunk to read the monitor. Returns DMTS_E_NONFINITE if the STS segment
+ * itself goes non-finite, DMTS_E_INVALID for bad parameters. */
+dmts_status respa_guarded(dmts_ctx *ctx, dmts_state *st, const dmts_integrator *p, const dmts_guard *guard,
+                          int n_outer, dmts_guard_stats *stats, void *stream);
 
 /* ------------------------------------------------------------------ serving */
 

@@ -312,13 +312,18 @@ class MDState:
         self.first = ct.c_int(1)
 
 
+LANGEVIN, FFL = 0, 1
+
+
 def respa_run(state, sys, cons_spec, cons_blob, nc_spec, nc_blob, dt_outer, n_inner, T,
-              gamma_ps, seed, n_outer, replica=0, inner_mode=0, outer_mode=0, consts=PRIOR):
+              gamma_ps, seed, n_outer, replica=0, inner_mode=0, outer_mode=0, consts=PRIOR,
+              thermostat=LANGEVIN):
     """Algorithm 1 for n_outer outer steps; returns the last potential energy.
     inner_mode: 0 NC + bonds, 1 full -grad U (collapse to BAOAB), 2 bonds only.
-    outer_mode: 0 -grad(U_MP + prior), 1 bonds only."""
+    outer_mode: 0 -grad(U_MP + prior), 1 bonds only.
+    thermostat: LANGEVIN or FFL (Fast Forward Langevin O-step)."""
     L = lib()
-    ints, pi = _i([sys.n_atoms, sys.bonds.shape[0], inner_mode, outer_mode, n_inner, replica])
+    ints, pi = _i([sys.n_atoms, sys.bonds.shape[0], inner_mode, outer_mode, n_inner, replica, thermostat])
     reals, pr = _d([dt_outer, T])
     sp, ps = _u8(sys.species)
     mol, pm = _i(sys.mol_id)
@@ -342,10 +347,10 @@ def respa_run(state, sys, cons_spec, cons_blob, nc_spec, nc_blob, dt_outer, n_in
 
 
 def sts_run(state, sys, cons_spec, cons_blob, dt, T, gamma_ps, seed, n_steps, replica=0,
-            outer_mode=0, consts=PRIOR):
+            outer_mode=0, consts=PRIOR, thermostat=LANGEVIN):
     """Single-time-step BAOAB for n_steps steps; returns the last potential energy."""
     L = lib()
-    ints, pi = _i([sys.n_atoms, sys.bonds.shape[0], outer_mode, replica])
+    ints, pi = _i([sys.n_atoms, sys.bonds.shape[0], outer_mode, replica, thermostat])
     reals, pr = _d([dt, T])
     sp, ps = _u8(sys.species)
     mol, pm = _i(sys.mol_id)

@@ -842,6 +842,7 @@ typedef struct {
     uint32_t replica;
     int inner_mode;          /* 0: NC + bonds + F_rep, 1: full -grad U, 2: bonds only */
     int outer_mode;          /* 0: -grad(U_MP + bonds + LJ + E_rep), 1: bonds only */
+    int thermostat;          /* 0: Langevin O-step, 1: Fast Forward Langevin */
 } md_t;
 
 /* Slow force F_full = -grad U (U = U_MP + bonds + LJ) or a reduced U. */
@@ -891,24 +892,38 @@ static void drift(int n, double *x, const double *v, double h)
     for (int i = 0; i < 3 * n; ++i) x[i] += h * v[i];
 }
 
-/* O-step: v_i <- c1 v_i + c2 sqrt(1/m_i) G_i, G from Philox at (seed, replica, step, i). */
+/* O-step: w_i = c1 v_i + c2 sqrt(1/m_i) G_i, G from Philox at (seed, replica,
+ * step, i). Langevin: v_i <- w_i. Fast Forward Langevin (Sec. 2, "High
+ * Hydrogen Friction", the FFL update): v_i <- |w_i| v_i / |v_i|, the norm
+ * taken of each atom's 3-vector; an atom at rest takes w_i. */
 static void ostep(const md_t *md, double *v, double dt, uint64_t step)
 {
     double c1[16], c2[16];
     orc_gamma_table(5, md->gamma_ps, dt, md->T, c1, c2);
     for (int i = 0; i < md->n; ++i) {
-        double g[3];
+        double g[3], w[3];
         orc_gauss3(md->seed, md->replica, step, (uint32_t)i, g);
         int s = md->species[i];
         for (int a = 0; a < 3; ++a)
-            v[3 * i + a] = c1[s] * v[3 * i + a] + c2[s] * sqrt(1.0 / md->mass[i]) * g[a];
+            w[a] = c1[s] * v[3 * i + a] + c2[s] * sqrt(1.0 / md->mass[i]) * g[a];
+        double nv = 0.0, nw = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            nv += v[3 * i + a] * v[3 * i + a];
+            nw += w[a] * w[a];
+        }
+        if (md->thermostat == 1 && nv > 0.0) {
+            double f = sqrt(nw) / sqrt(nv);
+            for (int a = 0; a < 3; ++a) v[3 * i + a] *= f;
+        } else {
+            for (int a = 0; a < 3; ++a) v[3 * i + a] = w[a];
+        }
     }
 }
 
 /* Algorithm 1 (DMTS-NC integration step), repeated n_outer times.
  * state: x, v, F (full force -grad U), F_nc (fast force), *step (global inner
  * step index, advanced by n per outer step), *first (force cache flag).
- * ints: [n_atoms, n_bonds, inner_mode, outer_mode, n_inner, replica]
+ * ints: [n_atoms, n_bonds, inner_mode, outer_mode, n_inner, replica, thermostat]
  * reals: [dt_outer, T]
  * Returns the last evaluated potential energy U. */
 double orc_respa_run(const int *ints, const double *reals, uint64_t seed,
@@ -922,7 +937,7 @@ double orc_respa_run(const int *ints, const double *reals, uint64_t seed,
 {
     md_t md = {ints[0], species, mol_id, box, ints[1], bonds, bond_r0, prior,
                cmi, cmr, cblob, nmi, nmr, nblob, mass, gamma_ps, reals[1], seed,
-               (uint32_t)ints[5], ints[2], ints[3]};
+               (uint32_t)ints[5], ints[2], ints[3], ints[6]};
     int n = md.n, n_in = ints[4];
     double Delta = reals[0], delta = Delta / n_in, U = 0.0;
     if (*first) {
@@ -948,7 +963,7 @@ double orc_respa_run(const int *ints, const double *reals, uint64_t seed,
 }
 
 /* Single-time-step BAOAB with the full force, n_steps steps of dt.
- * ints: [n_atoms, n_bonds, outer_mode, replica]; reals: [dt, T]. */
+ * ints: [n_atoms, n_bonds, outer_mode, replica, thermostat]; reals: [dt, T]. */
 double orc_sts_run(const int *ints, const double *reals, uint64_t seed,
                    const uint8_t *species, const int *mol_id, const double *box,
                    const int *bonds, const double *bond_r0, const double *prior,
@@ -958,7 +973,7 @@ double orc_sts_run(const int *ints, const double *reals, uint64_t seed,
 {
     md_t md = {ints[0], species, mol_id, box, ints[1], bonds, bond_r0, prior,
                cmi, cmr, cblob, NULL, NULL, NULL, mass, gamma_ps, reals[1], seed,
-               (uint32_t)ints[3], 0, ints[2]};
+               (uint32_t)ints[3], 0, ints[2], ints[4]};
     int n = md.n;
     double dt = reals[0], U = 0.0;
     if (*first) {

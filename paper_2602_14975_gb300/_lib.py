@@ -19,6 +19,7 @@ STATUS_NAMES = {0: "OK", 1: "E_INVALID", 2: "E_OOM", 3: "E_CUDA", 4: "E_NBR_OVER
                 5: "E_NONFINITE", 6: "E_TIMEOUT", 7: "E_BUSY"}
 FP32, BF16 = 0, 1
 MODE_RESPA, MODE_STS = 0, 1
+LANGEVIN, FFL = 0, 1
 WITH_PRIOR = 1
 WITH_BONDS = 1
 
@@ -50,7 +51,18 @@ class Nbr(ct.Structure):
 
 class Integrator(ct.Structure):
     _fields_ = [("dt_outer", ct.c_float), ("n_inner", ct.c_int), ("temperature", ct.c_float),
-                ("gamma_ps", ct.c_double * MAX_SPECIES), ("mode", ct.c_int), ("skin", ct.c_float)]
+                ("gamma_ps", ct.c_double * MAX_SPECIES), ("mode", ct.c_int), ("skin", ct.c_float),
+                ("thermostat", ct.c_int)]
+
+
+class Guard(ct.Structure):
+    _fields_ = [("threshold", ct.c_float), ("chunk_outer", ct.c_int), ("sts_steps", ct.c_int),
+                ("sts_dt", ct.c_float)]
+
+
+class GuardStats(ct.Structure):
+    _fields_ = [("n_rewinds", ct.c_int), ("n_chunks", ct.c_int), ("chunk_max", ct.c_void_p),
+                ("chunk_cap", ct.c_int), ("rewind_at", ct.c_void_p), ("rewind_cap", ct.c_int)]
 
 
 class State(ct.Structure):
@@ -88,7 +100,7 @@ EXPORTS = ("dmts_create", "dmts_destroy", "dmts_last_error", "dmts_sync", "nbr_b
            "energy_forces_cons", "forces_nc", "respa_step", "dmts_state_release", "run_replicas",
            "dmts_masses_hmr", "dmts_bond_table", "dmts_philox_words", "dmts_gaussians",
            "dmts_replica_footprint", "dmts_profile_enable", "dmts_profile_read", "nbr_build_noalloc",
-           "dmts_contract_bf16", "dmts_kernel_launches")
+           "dmts_contract_bf16", "dmts_kernel_launches", "respa_guarded")
 
 
 def lib_path() -> str:
@@ -115,6 +127,9 @@ def _declare(L):
     L.forces_nc.argtypes = [vp, ct.POINTER(System), ct.POINTER(Nbr), vp, vp, i, vp]
     L.respa_step.restype = i
     L.respa_step.argtypes = [vp, ct.POINTER(State), ct.POINTER(Integrator), i, vp]
+    L.respa_guarded.restype = i
+    L.respa_guarded.argtypes = [vp, ct.POINTER(State), ct.POINTER(Integrator), ct.POINTER(Guard), i,
+                                ct.POINTER(GuardStats), vp]
     L.dmts_state_release.restype = None
     L.dmts_state_release.argtypes = [vp, ct.POINTER(State)]
     L.run_replicas.restype = i

@@ -195,9 +195,12 @@ def forces_nc(ctx: Context, dsys: DeviceSystem, nbr: NbrList, with_bonds=True):
     return F, net
 
 
-def integrator(dt_outer, n_inner, temperature, gamma_ps, mode=L.MODE_RESPA, skin=0.5) -> L.Integrator:
+def integrator(dt_outer, n_inner, temperature, gamma_ps, mode=L.MODE_RESPA, skin=0.5,
+               thermostat=L.LANGEVIN) -> L.Integrator:
+    """Integrator parameters; thermostat L.LANGEVIN or L.FFL (Fast Forward Langevin)."""
     g = (ct.c_double * L.MAX_SPECIES)(*([float(v) for v in gamma_ps] + [0.0] * (L.MAX_SPECIES - len(gamma_ps))))
-    return L.Integrator(float(dt_outer), int(n_inner), float(temperature), g, int(mode), float(skin))
+    return L.Integrator(float(dt_outer), int(n_inner), float(temperature), g, int(mode), float(skin),
+                        int(thermostat))
 
 
 class MDState:
@@ -232,6 +235,24 @@ def respa_step(ctx: Context, state: MDState, integ: L.Integrator, n_outer: int):
     st = ctx.lib.respa_step(ctx.handle, ct.byref(state.c), ct.byref(integ), int(n_outer),
                             _stream(state.v.device))
     L.check(st, ctx.handle)
+
+
+def respa_guarded(ctx: Context, state: MDState, integ: L.Integrator, n_outer: int, threshold: float,
+                  chunk_outer: int, sts_steps: int, sts_dt: float, cap: int = 4096) -> dict:
+    """Algorithm 1 under the rewind guard (saved frame every chunk_outer
+    outer steps; on max |F - F_S| > threshold or a non-finite value: back to
+    the frame, sts_steps STS steps of sts_dt, then Algorithm 1 again).
+    Returns {"n_rewinds", "n_chunks", "chunk_max", "rewind_at"}."""
+    state.ctx = ctx
+    g = L.Guard(float(threshold), int(chunk_outer), int(sts_steps), float(sts_dt))
+    cm = np.zeros(cap, np.float32)
+    ra = np.zeros(cap, np.float32)
+    stats = L.GuardStats(0, 0, cm.ctypes.data, cap, ra.ctypes.data, cap)
+    st = ctx.lib.respa_guarded(ctx.handle, ct.byref(state.c), ct.byref(integ), ct.byref(g), int(n_outer),
+                               ct.byref(stats), _stream(state.v.device))
+    L.check(st, ctx.handle)
+    return {"n_rewinds": stats.n_rewinds, "n_chunks": stats.n_chunks,
+            "chunk_max": cm[:min(stats.n_chunks, cap)].copy(), "rewind_at": ra[:min(stats.n_rewinds, cap)].copy()}
 
 
 def philox_words(ctx, seed, replica, step, atom0, count):

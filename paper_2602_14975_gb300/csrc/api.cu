@@ -428,6 +428,16 @@ dmts_status nc_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const i
 
 __global__ void k_set_int(int *p, int v) { *p = v; }
 
+// Rebuilds the state's lists now, for its current positions (after the
+// positions were replaced, e.g. by a saved frame).
+void state_force_rebuild(dmts_ctx *ctx, dmts_state *stt, cudaStream_t st) {
+    StateInternal *si = (StateInternal *)stt->internal;
+    if (!si) return;
+    k_set_int<<<1, 1, 0, st>>>((int *)si->gate.p, 1);
+    count_launch();
+    rebuild_lists(ctx, si, state_view(stt), st);
+}
+
 // Host-side grid set-up for every replica (box and offsets copied to host).
 dmts_status setup_grids(dmts_ctx *ctx, const std::vector<int> &rep_off, const std::vector<float> &box,
                         float r_list, std::vector<CellGrid> &grids, int &n_cells) {
@@ -834,19 +844,30 @@ static void gamma_consts(const dmts_integrator *p, double dt, float *c1, float *
 }
 
 dmts_status respa_step(dmts_ctx *ctx, dmts_state *stt, const dmts_integrator *p, int n_outer, void *stream) {
+    return dmts::respa_run(ctx, stt, p, n_outer, (cudaStream_t)stream, nullptr);
+}
+
+}  // extern "C"
+
+// Algorithm 1 (or STS) for n_outer outer steps; fl_max (nullable, device,
+// one per replica) receives the running maximum of |F - F_S| (float bits) at
+// every outer kick.
+dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrator *p, int n_outer, cudaStream_t st,
+                            unsigned *fl_max) {
     if (!stt || !p) return fail(ctx, DMTS_E_INVALID, "NULL argument");
     dmts_status s = check_sys(ctx, &stt->sys);
     if (s != DMTS_OK) return s;
     if (!ctx->has_cons) return fail(ctx, DMTS_E_INVALID, "context has no conservative model");
     const bool sts = p->mode == DMTS_MODE_STS;
     if (!sts && (!ctx->has_nc || p->n_inner < 1)) return fail(ctx, DMTS_E_INVALID, "RESPA needs an NC model and n_inner >= 1");
-    if (!(p->dt_outer > 0.f) || n_outer < 0 || !(p->skin > 0.f)) return fail(ctx, DMTS_E_INVALID, "bad integrator parameters");
+    if (!(p->dt_outer > 0.f) || n_outer < 0 || !(p->skin > 0.f) ||
+        (p->thermostat != DMTS_LANGEVIN && p->thermostat != DMTS_FFL))
+        return fail(ctx, DMTS_E_INVALID, "bad integrator parameters");
     if (!stt->v || !stt->f_cons || (!sts && !stt->f_nc) || !stt->masses || !stt->step || !stt->seed || !stt->replica_id)
         return fail(ctx, DMTS_E_INVALID, "missing state array");
     if (stt->sys.n_atoms > 0 && (!stt->sys.bond_ptr || !stt->sys.bond_idx || !stt->sys.bond_r0))
         return fail(ctx, DMTS_E_INVALID, "missing bond table");
     cudaSetDevice(ctx->device);
-    cudaStream_t st = (cudaStream_t)stream;
     if (!stt->internal) {
         s = init_state(ctx, stt, p->skin, st);
         if (s != DMTS_OK) {
@@ -893,6 +914,8 @@ dmts_status respa_step(dmts_ctx *ctx, dmts_state *stt, const dmts_integrator *p,
     ia.half_skin2 = 0.25f * p->skin * p->skin;
     ia.rebuild = (int *)si->gate.p;
     ia.err = ctx->d_err;
+    ia.ffl = p->thermostat == DMTS_FFL;
+    ia.fl_max = sts ? nullptr : fl_max;
     const int n_in = sts ? 1 : p->n_inner;
     const double delta = sts ? p->dt_outer : (double)p->dt_outer / n_in;
     gamma_consts(p, delta, ia.c1, ia.c2);
@@ -920,6 +943,8 @@ dmts_status respa_step(dmts_ctx *ctx, dmts_state *stt, const dmts_integrator *p,
     launch_advance_step(stt->step, v.n_rep, (uint64_t)n_outer * n_in, ctx->d_err, st);
     return ck(ctx, cudaGetLastError(), "respa_step launch") ? DMTS_OK : DMTS_E_CUDA;
 }
+
+extern "C" {
 
 // ------------------------------------------------------------- helpers
 void dmts_masses_hmr(int n, const uint8_t *species, const int *mol_id, const double *m_in, double delta_h,

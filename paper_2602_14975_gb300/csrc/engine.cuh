@@ -140,6 +140,9 @@ dmts_status setup_grids(dmts_ctx *ctx, const std::vector<int> &rep_off, const st
 SysView state_view(dmts_state *stt);
 RepTable rep_table(const dmts_ctx *ctx);
 void rebuild_lists(dmts_ctx *ctx, StateInternal *si, const SysView &v, cudaStream_t st);
+void state_force_rebuild(dmts_ctx *ctx, dmts_state *stt, cudaStream_t st);
+dmts_status respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrator *p, int n_outer, cudaStream_t st,
+                      unsigned *fl_max);
 void prepare_nbr_work_async(dmts_ctx *ctx, StateInternal *si, const SysView &v, NbrWork &nw);
 }  // namespace dmts
 

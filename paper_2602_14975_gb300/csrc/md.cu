@@ -550,6 +550,15 @@ __global__ void k_integrate(IntegArgs g) {
         const float lx = g.f_slow[3 * i] - sfx, ly = g.f_slow[3 * i + 1] - sfy, lz = g.f_slow[3 * i + 2] - sfz;
         if (g.ops & OP_KICK_L) { vx = fmaf(h, lx, vx); vy = fmaf(h, ly, vy); vz = fmaf(h, lz, vz); }
         if (g.ops & OP_KICK_L2) { vx = fmaf(h, lx, vx); vy = fmaf(h, ly, vy); vz = fmaf(h, lz, vz); }
+        if (g.fl_max) {
+            // disagreement monitor of the rewind procedure: max |F_L| per replica
+            // (non-negative floats order like their bit patterns; NaN is larger)
+            const unsigned bits = __float_as_uint(sqrtf(lx * lx + ly * ly + lz * lz));
+            const int r = g.atom_rep[i];
+            const unsigned same = __match_any_sync(__activemask(), r);
+            const unsigned top = __reduce_max_sync(same, bits);
+            if ((same & ((1u << (threadIdx.x & 31)) - 1u)) == 0u) atomicMax(g.fl_max + r, top);
+        }
     }
     if (g.ops & OP_BAOA) {
         const float h = g.h_in * am;
@@ -561,7 +570,15 @@ __global__ void k_integrate(IntegArgs g) {
         const float3 G = gauss3(g.seed[r], g.rep_id[r], g.step[r] + g.step_add, (uint32_t)local);
         const int sp = g.species[i];
         const float c1 = g.c1[sp], c2 = g.c2[sp] / sqrtf(g.masses[i]);
-        vx = fmaf(c1, vx, c2 * G.x); vy = fmaf(c1, vy, c2 * G.y); vz = fmaf(c1, vz, c2 * G.z);
+        const float wx = fmaf(c1, vx, c2 * G.x), wy = fmaf(c1, vy, c2 * G.y), wz = fmaf(c1, vz, c2 * G.z);
+        const float nv2 = vx * vx + vy * vy + vz * vz;
+        if (g.ffl && nv2 > 0.f) {
+            // Fast Forward Langevin: the speed of w, the direction of v
+            const float f = sqrtf(wx * wx + wy * wy + wz * wz) / sqrtf(nv2);
+            vx *= f; vy *= f; vz *= f;
+        } else {
+            vx = wx; vy = wy; vz = wz;
+        }
         x = fmaf(g.h_in, vx, x); y = fmaf(g.h_in, vy, y); z = fmaf(g.h_in, vz, z);
         if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(vx) && isfinite(vy) && isfinite(vz)))
             set_error(g.err, DMTS_E_NONFINITE);

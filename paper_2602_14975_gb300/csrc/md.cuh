@@ -92,6 +92,8 @@ struct IntegArgs {
     float half_skin2;
     int *rebuild;
     int *err;
+    int ffl;                       // O-step: 0 Langevin, 1 Fast Forward Langevin
+    unsigned *fl_max;              // nullable: per-replica running max of |F_slow - F_fast| (float bits)
 };
 void launch_integrate(const IntegArgs &a, cudaStream_t st);
 void launch_advance_step(uint64_t *step, int n_rep, uint64_t add, const int *err, cudaStream_t st);

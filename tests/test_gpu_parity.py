@@ -250,6 +250,37 @@ def test_respa_positions_after_10_outer_steps(ctx1, models1, water, gamma):
     st.release()
 
 
+def test_respa_ffl_positions_after_10_outer_steps(ctx1, models1, water):
+    """Fast Forward Langevin O-step (HHF frictions) against the oracle, and
+    the direction rule it follows: with plain Langevin the same run differs."""
+    (cs, cb), (ns, nb_) = models1
+    m, v = _md_setup(water)
+    gam = [20.0, 1.0, 1.0, 1.0, 1.0]
+    out = {}
+    for th in (core.L.LANGEVIN, core.L.FFL):
+        d = core.DeviceSystem(water)
+        st = core.MDState(d, v, m.astype(np.float32), seeds=113)
+        integ = core.integrator(4.0, 4, 300.0, gam, skin=0.5, thermostat=th)
+        core.respa_step(ctx1, st, integ, 10)
+        ctx1.sync()
+        out[th] = d.x.cpu().numpy()
+        st.release()
+    ref = O.MDState(water, v, m.astype(np.float32).astype(np.float64))
+    O.respa_run(ref, water, cs, cb, ns, nb_, 4.0, 4, 300.0, np.array(gam), 113, 10, thermostat=O.FFL)
+    assert np.abs(out[core.L.FFL] - ref.x).max() <= TOL_POS
+    assert np.abs(out[core.L.FFL] - out[core.L.LANGEVIN]).max() > 10 * TOL_POS
+
+
+def test_bad_thermostat_is_rejected(ctx1, water):
+    m, v = _md_setup(water)
+    d = core.DeviceSystem(water)
+    st = core.MDState(d, v, m.astype(np.float32), seeds=1)
+    integ = core.integrator(4.0, 4, 300.0, [1.0] * 5, skin=0.5, thermostat=7)
+    with pytest.raises(core.L.DmtsError):
+        core.respa_step(ctx1, st, integ, 1)
+    st.release()
+
+
 def test_respa_split_calls_equal_single_call(ctx1, water):
     m, v = _md_setup(water)
     out = []

@@ -78,9 +78,36 @@ def test_bond_table_rejects_bad_index():
         core.bond_table(3, np.array([[0, 5]]), np.array([1.0]))
 
 
-def test_header_struct_sizes_match_ctypes():
-    # the ctypes mirrors must have the C layout (x86-64 / aarch64 LP64)
-    assert ct.sizeof(L.Model) == 64
-    assert ct.sizeof(L.System) == 8 + 8 * 8
-    assert ct.sizeof(L.Integrator) == 4 + 4 + 4 + 4 + 64 + 4 + 4
-    assert ct.sizeof(L.State) == ct.sizeof(L.System) + 8 * 8 + 8 + 8
+def test_header_struct_sizes_match_ctypes(tmp_path):
+    # the ctypes mirrors must have the C layout: a C program compiled against
+    # include/dmts.h prints sizeof and the offset of every mirrored field
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    mirrors = {"dmts_model": L.Model, "dmts_prior": L.Prior, "dmts_system": L.System, "dmts_nbr": L.Nbr,
+               "dmts_integrator": L.Integrator, "dmts_state": L.State, "dmts_request": L.Request,
+               "dmts_serve_cfg": L.ServeCfg, "dmts_result": L.Result, "dmts_serve_stats": L.ServeStats,
+               "dmts_guard": L.Guard, "dmts_guard_stats": L.GuardStats}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "dmts.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([gcc, "-std=c11", "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            a, b, c = line.split()
+            got[(a, b)] = int(c)
+    for cname, py in mirrors.items():
+        assert got[(cname, "size")] == ct.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)

@@ -575,3 +575,66 @@ def test_free_particle_temperature():
     d = 3 * n
     assert abs(Ts.mean() - 300.0) < 5 * 300.0 * math.sqrt(2.0 / d) / math.sqrt(len(Ts)) * 2
     assert stats.kstest(Ts * d / 300.0, stats.chi2(d).cdf).pvalue > 1e-3
+
+
+def _free_gas(n, seed=0):
+    return S.System("gas", np.random.default_rng(seed).uniform(0, 1000, (n, 3)),
+                    np.full(n, S.SP_O, np.uint8), np.arange(n, dtype=np.int32),
+                    np.zeros((0, 2), np.int32), np.zeros(0), np.zeros(3))
+
+
+def test_ffl_keeps_each_direction():
+    # Fast Forward Langevin (Sec. 2, the FFL update): the O-step replaces an
+    # atom's speed, never its direction; plain Langevin turns the velocities
+    n = 200
+    sy = _free_gas(n, 1)
+    cs, cb = S.cons_spec(1, 4, 0), S.cons_weights(S.cons_spec(1, 4, 0), 1)
+    m = sy.element_masses()
+    v0 = S.maxwell_boltzmann(m, 300.0, 5)
+    out = {}
+    for th in (O.LANGEVIN, O.FFL):
+        st = O.MDState(sy, v0.copy(), m)
+        O.sts_run(st, sy, cs, cb, 2.0, 300.0, np.full(5, 20.0), 7, 3, outer_mode=1, thermostat=th)
+        out[th] = st.v.copy()
+    cos = (out[O.FFL] * v0).sum(1) / (np.linalg.norm(out[O.FFL], axis=1) * np.linalg.norm(v0, axis=1))
+    assert np.all(cos > 1.0 - 1e-12)
+    cos_l = (out[O.LANGEVIN] * v0).sum(1) / (np.linalg.norm(out[O.LANGEVIN], axis=1) * np.linalg.norm(v0, axis=1))
+    assert cos_l.min() < 0.99
+    # the speeds were redrawn: not all equal to the old ones
+    assert np.abs(np.linalg.norm(out[O.FFL], axis=1) - np.linalg.norm(v0, axis=1)).max() > 1e-3
+
+
+def test_ffl_from_rest_equals_langevin():
+    # an atom at rest has no direction: it takes the Langevin velocity
+    n = 50
+    sy = _free_gas(n, 2)
+    cs, cb = S.cons_spec(1, 4, 0), S.cons_weights(S.cons_spec(1, 4, 0), 1)
+    m = sy.element_masses()
+    res = []
+    for th in (O.LANGEVIN, O.FFL):
+        st = O.MDState(sy, np.zeros((n, 3)), m)
+        O.sts_run(st, sy, cs, cb, 2.0, 300.0, np.full(5, 20.0), 9, 1, outer_mode=1, thermostat=th)
+        res.append(st.v.copy())
+    assert np.array_equal(res[0], res[1])
+
+
+def test_ffl_free_particle_temperature():
+    # FFL leaves the canonical distribution invariant: free particles reach
+    # <T> = 300 K with the (T/d) chi^2_d statistics of the Langevin case
+    from scipy import stats
+    n = 400
+    sy = _free_gas(n, 0)
+    cs, cb = S.cons_spec(1, 4, 0), S.cons_weights(S.cons_spec(1, 4, 0), 1)
+    m = sy.element_masses()
+    st = O.MDState(sy, np.zeros((n, 3)), m)
+    conv, kB = 4.184e-4, 8.314462618 / 4184.0
+    Ts = []
+    for _ in range(60):
+        O.respa_run(st, sy, cs, cb, cs, cb, 10.0, 5, 300.0, np.full(5, 20.0), 1, n_outer=20,
+                    inner_mode=2, outer_mode=1, thermostat=O.FFL)
+        ke = 0.5 * (m[:, None] * st.v ** 2).sum() / conv
+        Ts.append(2 * ke / (3 * n * kB))
+    Ts = np.array(Ts[10:])
+    d = 3 * n
+    assert abs(Ts.mean() - 300.0) < 5 * 300.0 * math.sqrt(2.0 / d) / math.sqrt(len(Ts)) * 2
+    assert stats.kstest(Ts * d / 300.0, stats.chi2(d).cdf).pvalue > 1e-3
