@@ -280,6 +280,35 @@ def main():
     ms_dmts = max_over_ranks(e0.elapsed_time(e1)) / args.steps
     st.release()
 
+    # ------------------------------------- rewind guard, FFL thermostat
+    # the same outer step under the rewind guard (saved frame and monitor
+    # read every 50 outer steps, no disagreement), and with the Fast Forward
+    # Langevin O-step
+    n_side = max(10, args.steps // 2)
+    side = {}
+    for label, th in (("guarded", 0), ("ffl", 1)):
+        dg = core.DeviceSystem(W["system"]())
+        sg = core.MDState(dg, v0, m_hmr.astype(np.float32), seeds=I.seed, replica_ids=[D.replica_id(rank, 0)])
+        ig = core.integrator(I.dt_outer, I.n_inner, I.temperature, I.gamma_ps, skin=skin,
+                             thermostat=core.L.FFL if th else core.L.LANGEVIN)
+        core.respa_step(ctx, sg, ig, 2)
+        ctx.sync()
+        barrier()
+        e0.record(stream)
+        if label == "guarded":
+            gs = core.respa_guarded(ctx, sg, ig, n_side, math.inf, 50, 4 * I.n_inner, I.dt_outer / I.n_inner)
+        else:
+            core.respa_step(ctx, sg, ig, n_side)
+        e1.record(stream)
+        barrier()
+        ctx.sync()
+        ms = max_over_ranks(e0.elapsed_time(e1)) / n_side
+        side[label] = {"ns_per_day": ns_per_day(I.dt_outer, 1e3 / ms) * world, "ms_per_step": ms, "steps": n_side}
+        if label == "guarded":
+            side[label].update({"chunk_outer": 50, "rewinds": gs["n_rewinds"],
+                                "max_force_disagreement": float(np.max(gs["chunk_max"])) if gs["n_chunks"] else None})
+        sg.release()
+
     # --------------------------------------------------------------- STS
     sts = W["sts"]
     m_el = sy.element_masses()
@@ -511,6 +540,8 @@ def main():
         "roofline": roof,
         "kernels": shares,
         "kernel_roofline": kr,
+        "rewind_guard": side["guarded"],
+        "ffl": side["ffl"],
         "large_system": {"workload": syL.name, "n_atoms": syL.n_atoms, "steps": n_large,
                          "ns_per_day": ns_per_day(IL.dt_outer, 1e3 / ms_large) * world, "ms_per_step": ms_large,
                          "sts_ns_per_day": ns_per_day(stsL.dt_outer, 1e3 / ms_large_sts) * world,
