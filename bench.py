@@ -185,6 +185,32 @@ def oracle_outer_step_seconds(sy, W, frac_edge):
     return per_outer * scale, desc
 
 
+def serving_roofline(prof, atom_outer_steps, n_inner, cs):
+    """Per-kernel rates inside the serving loop, where one launch covers every
+    resident replica (often 10^5 atoms or more): the integrator against HBM
+    (65 B per atom per launch, n_inner + 1 launches per outer step) and the
+    conservative contractions against the bf16 tensor peak."""
+    pk = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        pk = json.load(open(pk_path))
+    out = {}
+    t_int = prof.get("integrate", (0, 0.0))[1] * 1e-3
+    if t_int > 0:
+        gbs = 65.0 * atom_outer_steps * (n_inner + 1) / t_int / 1e9
+        out["integrate"] = {"row": "a8", "bound": "hbm", "gbs": gbs,
+                            "frac_hbm": gbs / pk["hbm_gbs"] if pk.get("hbm_gbs") else None}
+    t_g = prof.get("gemm_tc", (0, 0.0))[1] * 1e-3
+    if t_g > 0:
+        nl = cs.lmax + 1
+        tf = 2.0 * cs.C * cs.C * (2 * cs.L * (nl + 1) + 2) * atom_outer_steps / t_g / 1e12
+        out["gemm_tc"] = {"row": "a4", "bound": "tensor", "tflops": tf,
+                          "frac_bf16_sustained": tf / pk["bf16_tflops_sustained"] if pk.get("bf16_tflops_sustained") else None}
+    tot = sum(v[1] for v in prof.values()) or 1.0
+    out["shares"] = {k: round(v[1] / tot, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+    return out
+
+
 # ------------------------------------------------------------------ main --
 def main():
     args = parse()
@@ -421,7 +447,10 @@ def main():
         reqs.append(core.ReplicaRequest(sq, vq, mq, q["n_outer"], q["rng_seed"], D.replica_id(rank, 1 + q["id"]),
                                         q["arrival_s"]))
     barrier()
+    core.profile_enable(ctx, True)
     outs, sst = core.run_replicas(ctx, reqs, integ, realtime=True)
+    prof_serve = core.profile_read(ctx)
+    core.profile_enable(ctx, False)
     barrier()
     tk = sst["tick_ms"]
     lat = np.array([o["t_done_s"] - o["t_arrival_s"] for o in outs])
@@ -432,6 +461,7 @@ def main():
         "atom_outer_steps_per_s": sst["atom_outer_steps"] / sst["wall_s"] * world,
         "request_latency_s_p50": float(np.percentile(lat, 50)), "request_latency_s_p99": float(np.percentile(lat, 99)),
         "failed": int(sum(o["status"] != 0 for o in outs)),
+        "kernel_roofline": serving_roofline(prof_serve, sst["atom_outer_steps"], I.n_inner, cs),
         "solvated_chain_23558_in_loop": {"ns_per_day": ns_per_day(I.dt_outer, 1e3 / ms_serve) * world,
                                          "ms_per_outer_step": ms_serve,
                                          "vs_sts": ns_per_day(I.dt_outer, 1e3 / ms_serve) / ns_per_day(sts.dt_outer, 1e3 / ms_sts)},

@@ -36,27 +36,6 @@ void launch_rowsum(int n, int C, const float *u, float scale, float *e_atom, cud
     count_launch();
 }
 
-// V[i][h][a] = sum_c U[h][c] A[i][1+a][c]   (vector part of tensor head h)
-__global__ void k_nc_vectors(int n, int C, int n_l, const float *A, const float *U, float *V, const int *err) {
-    if (*err) return;
-    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-    if (i >= n) return;
-    for (int h = 0; h < n_l; ++h)
-        for (int a = 0; a < 3; ++a) {
-            float s = 0.f;
-            for (int c = lane; c < C; c += 32) s += U[h * C + c] * A[((size_t)i * 4 + 1 + a) * C + c];
-            s = warp_sum(s);
-            if (lane == 0) V[((size_t)i * n_l + h) * 3 + a] = s;
-        }
-}
-
-void launch_nc_vectors(int n, int C, int n_l, const float *A, const float *U, float *V, const int *err,
-                       cudaStream_t st) {
-    if (n == 0) return;
-    k_nc_vectors<<<(n + 7) / 8, 256, 0, st>>>(n, C, n_l, A, U, V, err);
-    count_launch();
-}
-
 __device__ __forceinline__ void bond_force(const BondTable &b, const float *x, int a, float bx, float by,
                                            float bz, float ibx, float iby, float ibz, int lane, float &fx,
                                            float &fy, float &fz, float &e) {

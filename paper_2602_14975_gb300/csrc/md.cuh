@@ -39,8 +39,6 @@ struct NCHeadArgs {
     int *err;                      // sticky device error word (read, and set on a timeout)
 };
 
-void launch_nc_vectors(int n, int C, int n_l, const float *A, const float *U, float *V, const int *err,
-                       cudaStream_t st);
 void launch_nc_head(int K, int n_c, int n_l, const NCHeadArgs &a, cudaStream_t st);
 // F_out = F_in - (sum_{replica} F_in)/n_r, FP64 sums; net (nullable) [R][3].
 // scratch: device memory of mean_sub_scratch_bytes(n_atoms, n_rep) bytes.

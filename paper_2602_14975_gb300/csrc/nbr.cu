@@ -135,43 +135,11 @@ __device__ __forceinline__ void for_candidates(const NbrWork &w, int i, float rc
     }
 }
 
-__global__ void k_nbr_count(NbrWork w, float rc2) {
-    if (gated_off(w.gate, w.err)) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= w.n_atoms) return;
-    int cnt = 0;
-    for_candidates(w, i, rc2, [&](int) { ++cnt; });
-    w.counts[i] = cnt;
-}
-
-__global__ void k_nbr_fill(NbrWork w, float rc2, const int *row_ptr, int *col, float *x_ref) {
-    if (gated_off(w.gate, w.err)) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= w.n_atoms) return;
-    const int beg = row_ptr[i];
-    int p = beg;
-    for_candidates(w, i, rc2, [&](int j) { col[p++] = j; });
-    // canonical row order (ascending j): rows do not depend on the cell
-    // layout at build time, so results do not depend on when lists were rebuilt
-    for (int a = beg + 1; a < p; ++a) {
-        const int v = col[a];
-        int b = a - 1;
-        while (b >= beg && col[b] > v) {
-            col[b + 1] = col[b];
-            --b;
-        }
-        col[b + 1] = v;
-    }
-    if (x_ref) {
-        x_ref[3 * i] = w.x[3 * i];
-        x_ref[3 * i + 1] = w.x[3 * i + 1];
-        x_ref[3 * i + 2] = w.x[3 * i + 2];
-    }
-}
-
-// Warp-per-atom variants: lanes sweep the atoms of each neighbouring cell
-// (same cell order as above), rows are collected by ballot into shared
-// memory, sorted there by a bitonic network and written out contiguously.
+// Warp per atom: lanes sweep the atoms of each neighbouring cell (the cell
+// order of for_candidates), rows are collected by ballot into shared memory,
+// sorted there by a bitonic network and written out contiguously. Rows are in
+// canonical order (ascending j), so they do not depend on the cell layout at
+// build time and results do not depend on when lists were rebuilt.
 constexpr int NB_WARPS = 4;
 constexpr int NB_MAXROW = 256;
 
