@@ -208,7 +208,9 @@ __global__ void __launch_bounds__(256) k_gemm_tc(const __grid_constant__ CUtenso
     __shared__ uint32_t tmem_base_sh;
     __shared__ int abort_sh;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * TC_M, n0 = blockIdx.y * BN;
+    // column tiles in reverse order: the gA epilogue's highest-degree tiles
+    // (5 loads and stores per element for l = 2) are scheduled first
+    const int m0 = blockIdx.x * TC_M, n0 = (gridDim.y - 1 - blockIdx.y) * BN;
     const int nk = K / TC_K;
     const uint32_t a_bytes = TC_M * TC_K * 2, b_bytes = (uint32_t)BN * TC_K * 2;
     const uint32_t stage_bytes = a_bytes + ((b_bytes + 1023u) & ~1023u);
