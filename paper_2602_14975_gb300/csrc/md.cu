@@ -111,11 +111,13 @@ __device__ __forceinline__ float rep_pair(const RepTable &t, int si, int sj, flo
 //   F_aj = (sum_{h<K} c_ajh B_h) (n + sum_{h<n_l} c_aj(K+h) V_ah) f_c
 //   F_ja = (sum_{h<K} c_jah B_h) (-n + sum_{h<n_l} c_ja(K+h) V_jh) f_c
 //   F_a = scale sum_j (F_aj - F_ja) (+ bonds)
-// Active neighbours are taken 32 at a time (the g-th active entry of the row
-// on lane g % 32, as in for_active_canonical). Each lane starts one bulk copy
-// of its neighbour's q/k row into shared memory, evaluates the radial part of
-// its edge while the rows arrive, and then forms the dot products from shared
-// memory, so no load instruction gathers 32 scattered rows at once.
+// Active neighbours are taken 16 at a time (the g-th active entry of the row
+// in batch g / 16 on lanes g % 16 and g % 16 + 16). The first lane of each
+// pair starts one bulk copy of its neighbour's q/k row into shared memory;
+// both evaluate the radial part of the edge while the rows arrive, then each
+// forms the dot products of half of the heads from shared memory and the two
+// halves are added with one shuffle. No load instruction gathers scattered
+// rows, and 16-row staging keeps enough warps resident to hide the latency.
 constexpr int NCH_WARPS = 2;
 
 template <int K, int NC, int NL>
@@ -123,12 +125,15 @@ struct NCHeadSmem {
     static constexpr int H = K + NL, QKW = 2 * H * NC;
     static constexpr int RSTR = QKW + 4;    // padded row stride (floats): conflict-free 16-byte reads
     static constexpr int ROWB = QKW * 4;    // bytes copied per row
-    static constexpr size_t rows = (size_t)NCH_WARPS * 32 * RSTR * 4;
+    static constexpr int BATCH = 16;        // neighbours per staged batch
+    static constexpr int HH = (H + 1) / 2;  // heads per lane of a pair
+    static constexpr size_t rows = (size_t)NCH_WARPS * BATCH * RSTR * 4;
     static constexpr size_t qk = (size_t)NCH_WARPS * QKW * 4;
     static constexpr size_t vv = (size_t)NCH_WARPS * 4 * NL * 4;
     static constexpr size_t queue = (size_t)NCH_WARPS * 64 * 4;
     static constexpr size_t bytes = rows + qk + vv + queue + NCH_WARPS * 8;
     static_assert(QKW % 16 == 0, "row stride");
+    static_assert(HH <= K, "each lane's first heads are Bessel heads");
 };
 
 template <int K, int NC, int NL>
@@ -137,7 +142,8 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
     constexpr int H = SM::H, QKW = SM::QKW, RSTR = SM::RSTR;
     extern __shared__ __align__(16) unsigned char nch_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float *rows = reinterpret_cast<float *>(nch_smem) + (size_t)warp * 32 * RSTR;
+    constexpr int BATCH = SM::BATCH, HH = SM::HH;
+    float *rows = reinterpret_cast<float *>(nch_smem) + (size_t)warp * BATCH * RSTR;
     float *qa = reinterpret_cast<float *>(nch_smem + SM::rows) + warp * QKW;
     float *va = reinterpret_cast<float *>(nch_smem + SM::rows + SM::qk) + warp * 4 * NL;
     int *queue = reinterpret_cast<int *>(nch_smem + SM::rows + SM::qk + SM::vv) + warp * 64;
@@ -166,25 +172,25 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
     uint32_t phase = 0;
     bool alive = true;
 
-    // one batch: lanes t < nb own the queued edges taken .. taken + nb - 1
+    // one batch: lanes e and e + 16 (e < nb) own queued edge taken + e; the
+    // first stages the row and adds the repulsion, the pair splits the heads
+    const int slot = lane & (BATCH - 1), half = lane / BATCH;
     auto batch = [&](int taken, int nb) {
-        const int j = lane < nb ? queue[(taken + lane) & 63] : -1;
+        const int j = slot < nb ? queue[(taken + slot) & 63] : -1;
         fence_proxy_async_smem();      // earlier reads of the rows before the copies overwrite them
         if (lane == 0) mbar_expect_tx(bar, (uint32_t)nb * SM::ROWB);
         __syncwarp();
-        if (j >= 0) bulk_g2s(smem_u32(rows + lane * RSTR), g.QK + (size_t)j * QKW, SM::ROWB, bar);
+        if (j >= 0 && half == 0) bulk_g2s(smem_u32(rows + slot * RSTR), g.QK + (size_t)j * QKW, SM::ROWB, bar);
         // radial part of the edge while the rows arrive
-        float dx = 0.f, dy = 0.f, dz = 0.f, r = 1.f, inv = 1.f, fc = 0.f, B[K], vj[NL * 3];
+        float dx = 0.f, dy = 0.f, dz = 0.f, inv = 1.f, fc = 0.f, Bh[HH];
         if (j >= 0) {
             dx = min_img(__ldg(g.x + 3 * j) - xa, bx, ibx);
             dy = min_img(__ldg(g.x + 3 * j + 1) - ya, by, iby);
             dz = min_img(__ldg(g.x + 3 * j + 2) - za, bz, ibz);
             const float r2 = dx * dx + dy * dy + dz * dz;
-            r = sqrtf(r2);
+            const float r = sqrtf(r2);
             inv = 1.f / r;
-#pragma unroll
-            for (int q = 0; q < NL * 3; ++q) vj[q] = __ldg(g.V + (size_t)j * NL * 3 + q);
-            if (with_rep && r2 < rep2 && !is_bonded(g.bonds, a, j)) {
+            if (half == 0 && with_rep && r2 < rep2 && !is_bonded(g.bonds, a, j)) {
                 float dE;
                 rep_pair(g.rep, sa, g.species[j], r, &dE);
                 const float c = dE * inv;              // F_a = E'(r) d / r
@@ -192,7 +198,11 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
             }
             float du;
             fc = envelope(r * g.inv_rc, g.p, &du);
+            float B[K];
             bessel<K, false>(r, g.inv_rc, g.bnorm, B, nullptr);
+#pragma unroll
+            for (int hl = 0; hl < HH; ++hl)
+                Bh[hl] = half == 0 ? B[hl] : (HH + hl < K ? B[HH + hl < K ? HH + hl : 0] : 0.f);
         }
         const bool got = __all_sync(DMTS_FULL, mbar_wait(bar, phase));
         phase ^= 1u;
@@ -204,42 +214,51 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
             alive = false;
             return;
         }
+        // partial sums over this lane's heads h = half * HH + hl
+        float part[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // Saj, Sja, va (3), vj (3)
         if (j >= 0) {
-            const float nx = dx * inv, ny = dy * inv, nz = dz * inv;
-            const float4 *qj4 = reinterpret_cast<const float4 *>(rows + lane * RSTR);
-            const float4 *kj4 = qj4 + H * NC / 4;
-            float Saj = 0.f, Sja = 0.f;
-            float vax = 0.f, vay = 0.f, vaz = 0.f, vjx = 0.f, vjy = 0.f, vjz = 0.f;
+            const float *row = rows + slot * RSTR;
 #pragma unroll
-            for (int h = 0; h < H; ++h) {
-                float caj = 0.f, cja = 0.f;
+            for (int hl = 0; hl < HH; ++hl) {
+                const int h = half * HH + hl;
+                if (h < H) {
+                    const float4 *qj4 = reinterpret_cast<const float4 *>(row + h * NC);
+                    const float4 *kj4 = reinterpret_cast<const float4 *>(row + (H + h) * NC);
+                    const float *qah = qa + h * NC, *kah = ka + h * NC;
+                    float caj = 0.f, cja = 0.f;
 #pragma unroll
-                for (int q = 0; q < NC / 4; ++q) {
-                    const float4 kj = kj4[h * NC / 4 + q];
-                    const float4 qj = qj4[h * NC / 4 + q];
-                    const float *qah = qa + h * NC + 4 * q, *kah = ka + h * NC + 4 * q;
-                    caj = fmaf(qah[0], kj.x, fmaf(qah[1], kj.y, fmaf(qah[2], kj.z, fmaf(qah[3], kj.w, caj))));
-                    cja = fmaf(qj.x, kah[0], fmaf(qj.y, kah[1], fmaf(qj.z, kah[2], fmaf(qj.w, kah[3], cja))));
-                }
-                caj *= isnc;
-                cja *= isnc;
-                if (h < K) {
-                    Saj = fmaf(caj, B[h], Saj);
-                    Sja = fmaf(cja, B[h], Sja);
-                } else {
-                    const int t = h - K;
-                    vax = fmaf(caj, va[3 * t], vax);
-                    vay = fmaf(caj, va[3 * t + 1], vay);
-                    vaz = fmaf(caj, va[3 * t + 2], vaz);
-                    vjx = fmaf(cja, vj[3 * t], vjx);
-                    vjy = fmaf(cja, vj[3 * t + 1], vjy);
-                    vjz = fmaf(cja, vj[3 * t + 2], vjz);
+                    for (int q = 0; q < NC / 4; ++q) {
+                        const float4 kj = kj4[q], qj = qj4[q];
+                        caj = fmaf(qah[4 * q], kj.x, fmaf(qah[4 * q + 1], kj.y,
+                                   fmaf(qah[4 * q + 2], kj.z, fmaf(qah[4 * q + 3], kj.w, caj))));
+                        cja = fmaf(qj.x, kah[4 * q], fmaf(qj.y, kah[4 * q + 1],
+                                   fmaf(qj.z, kah[4 * q + 2], fmaf(qj.w, kah[4 * q + 3], cja))));
+                    }
+                    caj *= isnc;
+                    cja *= isnc;
+                    if (h < K) {
+                        part[0] = fmaf(caj, Bh[hl], part[0]);
+                        part[1] = fmaf(cja, Bh[hl], part[1]);
+                    } else {
+                        const int t = h - K;
+                        const float *vjt = g.V + ((size_t)j * NL + t) * 3;
+#pragma unroll
+                        for (int cmp = 0; cmp < 3; ++cmp) {
+                            part[2 + cmp] = fmaf(caj, va[3 * t + cmp], part[2 + cmp]);
+                            part[5 + cmp] = fmaf(cja, __ldg(vjt + cmp), part[5 + cmp]);
+                        }
+                    }
                 }
             }
-            const float pa = Saj * fc, pj = Sja * fc;
-            fx += pa * (nx + vax) - pj * (-nx + vjx);
-            fy += pa * (ny + vay) - pj * (-ny + vjy);
-            fz += pa * (nz + vaz) - pj * (-nz + vjz);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) part[q] += __shfl_xor_sync(DMTS_FULL, part[q], BATCH);
+        if (j >= 0 && half == 0) {
+            const float nx = dx * inv, ny = dy * inv, nz = dz * inv;
+            const float pa = part[0] * fc, pj = part[1] * fc;
+            fx += pa * (nx + part[2]) - pj * (-nx + part[5]);
+            fy += pa * (ny + part[3]) - pj * (-ny + part[6]);
+            fz += pa * (nz + part[4]) - pj * (-nz + part[7]);
         }
         __syncwarp();
     };
@@ -260,9 +279,9 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
         if (act) queue[(queued + __popc(m & ((1u << lane) - 1u))) & 63] = j;
         queued += __popc(m);
         __syncwarp();
-        if (queued - taken >= 32) {
-            batch(taken, 32);
-            taken += 32;
+        while (queued - taken >= BATCH && alive) {
+            batch(taken, BATCH);
+            taken += BATCH;
         }
     }
     if (alive && queued > taken) batch(taken, queued - taken);
