@@ -496,11 +496,15 @@ void rebuild_lists(dmts_ctx *ctx, StateInternal *si, const SysView &v, cudaStrea
     NbrWork nw;
     prepare_nbr_work_async(ctx, si, v, nw);
     { ProfScope ps(ctx, "nbr_cells", st); nbr_cells(nw, si->r_cons, st); }
-    { ProfScope ps(ctx, "nbr_fill", st); nbr_fill(nw, si->r_cons, (int *)si->cons_row.p, (int *)si->cons_col.p, si->cons_cap, (float *)si->x_ref.p, st); }
-    if (ctx->has_nc) {
-        ProfScope ps(ctx, "nbr_sublist", st);
-        nbr_sublist(nw, (int *)si->cons_row.p, (int *)si->cons_col.p, si->r_nc, (int *)si->nc_row.p,
-                    (int *)si->nc_col.p, si->nc_cap, st);
+    {
+        // the full list and, in the same pass, the NC list within r_nc + skin
+        ProfScope ps(ctx, "nbr_fill", st);
+        if (ctx->has_nc)
+            nbr_fill(nw, si->r_cons, (int *)si->cons_row.p, (int *)si->cons_col.p, si->cons_cap, (float *)si->x_ref.p,
+                     st, si->r_nc, (int *)si->nc_row.p, (int *)si->nc_col.p, si->nc_cap);
+        else
+            nbr_fill(nw, si->r_cons, (int *)si->cons_row.p, (int *)si->cons_col.p, si->cons_cap, (float *)si->x_ref.p,
+                     st);
     }
     k_set_int<<<1, 1, 0, st>>>((int *)si->gate.p, 0);
     count_launch();
@@ -521,6 +525,7 @@ void prepare_nbr_work_async(dmts_ctx *ctx, StateInternal *si, const SysView &v, 
     nw.atom_cell = (int *)b.atom_cell.p;
     nw.atom_slot = (int *)b.atom_slot.p;
     nw.counts = (int *)b.counts.p;
+    nw.counts_sub = (int *)b.counts_sub.p;
     nw.total = (long long *)b.total.p;
     nw.gate = (int *)si->gate.p;
     nw.err = ctx->d_err;
@@ -547,7 +552,8 @@ static dmts_status prepare_nbr_work(dmts_ctx *ctx, NbrScratch &b, const SysView 
     if (!b.grid.ensure(sizeof(CellGrid) * R) || !b.cell_cnt.ensure(sizeof(int) * (n_cells + 1)) ||
         !b.cell_start.ensure(sizeof(int) * (n_cells + 1)) || !b.cell_atoms.ensure(sizeof(int) * (N + 1)) ||
         !b.atom_cell.ensure(sizeof(int) * (N + 1)) || !b.atom_slot.ensure(sizeof(int) * (N + 1)) ||
-        !b.counts.ensure(sizeof(int) * (N + 1)) || !b.total.ensure(sizeof(long long)))
+        !b.counts.ensure(sizeof(int) * (N + 1)) || !b.counts_sub.ensure(sizeof(int) * (N + 1)) ||
+        !b.total.ensure(sizeof(long long)))
         return fail(ctx, DMTS_E_OOM, "neighbour scratch allocation failed");
     if (!ck(ctx, cudaMemcpyAsync(b.grid.p, grids.data(), sizeof(CellGrid) * R, cudaMemcpyHostToDevice, st), "grid upload") ||
         !ck(ctx, cudaStreamSynchronize(st), "grid upload"))
@@ -565,6 +571,7 @@ static dmts_status prepare_nbr_work(dmts_ctx *ctx, NbrScratch &b, const SysView 
     nw.atom_cell = (int *)b.atom_cell.p;
     nw.atom_slot = (int *)b.atom_slot.p;
     nw.counts = (int *)b.counts.p;
+    nw.counts_sub = (int *)b.counts_sub.p;
     nw.total = (long long *)b.total.p;
     nw.gate = gate;
     nw.err = ctx->d_err;

@@ -36,10 +36,10 @@ struct DevModel {
 };
 
 struct NbrScratch {
-    Buf grid, cell_cnt, cell_start, cell_atoms, atom_cell, atom_slot, counts, total;
+    Buf grid, cell_cnt, cell_start, cell_atoms, atom_cell, atom_slot, counts, total, counts_sub;
     void release_all() {
         grid.release(); cell_cnt.release(); cell_start.release(); cell_atoms.release();
-        atom_cell.release(); atom_slot.release(); counts.release(); total.release();
+        atom_cell.release(); atom_slot.release(); counts.release(); total.release(); counts_sub.release();
     }
 };
 

@@ -179,34 +179,69 @@ __device__ __forceinline__ void for_candidates_warp(const NbrWork &w, int i, flo
                     const int p = p0 + lane;
                     bool hit = false;
                     int j = -1;
+                    float r2 = 0.f;
                     if (p < end) {
                         j = w.cell_atoms[p];
                         if (j != i) {
                             const float dx = min_img(w.x[3 * j] - xi, g.box[0], ibx);
                             const float dy = min_img(w.x[3 * j + 1] - yi, g.box[1], iby);
                             const float dz = min_img(w.x[3 * j + 2] - zi, g.box[2], ibz);
-                            hit = dx * dx + dy * dy + dz * dz < rc2;
+                            r2 = dx * dx + dy * dy + dz * dz;
+                            hit = r2 < rc2;
                         }
                     }
-                    f(hit, j);
+                    f(hit, j, r2);
                 }
             }
         }
     }
 }
 
-__global__ void __launch_bounds__(NB_WARPS * 32) k_nbr_count_warp(NbrWork w, float rc2) {
+__global__ void __launch_bounds__(NB_WARPS * 32) k_nbr_count_warp(NbrWork w, float rc2, float rc2_sub) {
     if (gated_off(w.gate, w.err)) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = blockIdx.x * NB_WARPS + warp;
     if (i >= w.n_atoms) return;
-    int cnt = 0;
-    for_candidates_warp(w, i, rc2, lane, [&](bool hit, int) { cnt += __popc(__ballot_sync(DMTS_FULL, hit)); });
-    if (lane == 0) w.counts[i] = cnt;
+    int cnt = 0, cnt_sub = 0;
+    for_candidates_warp(w, i, rc2, lane, [&](bool hit, int, float r2) {
+        cnt += __popc(__ballot_sync(DMTS_FULL, hit));
+        if (w.counts_sub) cnt_sub += __popc(__ballot_sync(DMTS_FULL, hit && r2 < rc2_sub));
+    });
+    if (lane == 0) {
+        w.counts[i] = cnt;
+        if (w.counts_sub) w.counts_sub[i] = cnt_sub;
+    }
+}
+
+// Appends, in order, the entries of the sorted row src[0..n) within rc2_sub
+// to dst (warp-cooperative; distances recomputed exactly as in the build).
+__device__ __forceinline__ void write_sub_row(const NbrWork &w, int i, const int *src, int n, float rc2_sub,
+                                              int *dst, int lane) {
+    const CellGrid g = w.grid[w.atom_rep[i]];
+    const float ibx = g.box[0] > 0.f ? 1.f / g.box[0] : 0.f, iby = g.box[1] > 0.f ? 1.f / g.box[1] : 0.f,
+                ibz = g.box[2] > 0.f ? 1.f / g.box[2] : 0.f;
+    const float xi = w.x[3 * i], yi = w.x[3 * i + 1], zi = w.x[3 * i + 2];
+    int done = 0;
+    for (int t0 = 0; t0 < n; t0 += 32) {
+        const int t = t0 + lane;
+        bool keep = false;
+        int j = 0;
+        if (t < n) {
+            j = src[t];
+            const float dx = min_img(w.x[3 * j] - xi, g.box[0], ibx);
+            const float dy = min_img(w.x[3 * j + 1] - yi, g.box[1], iby);
+            const float dz = min_img(w.x[3 * j + 2] - zi, g.box[2], ibz);
+            keep = dx * dx + dy * dy + dz * dz < rc2_sub;
+        }
+        const unsigned m = __ballot_sync(DMTS_FULL, keep);
+        if (keep) dst[done + __popc(m & ((1u << lane) - 1u))] = j;
+        done += __popc(m);
+    }
 }
 
 __global__ void __launch_bounds__(NB_WARPS * 32) k_nbr_fill_warp(NbrWork w, float rc2, const int *row_ptr, int *col,
-                                                                 float *x_ref) {
+                                                                 float *x_ref, float rc2_sub, const int *sub_row,
+                                                                 int *sub_col) {
     if (gated_off(w.gate, w.err)) return;
     __shared__ int buf[NB_WARPS][NB_MAXROW];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -216,7 +251,7 @@ __global__ void __launch_bounds__(NB_WARPS * 32) k_nbr_fill_warp(NbrWork w, floa
     const int beg = row_ptr[i], n = row_ptr[i + 1] - beg;
     if (n <= NB_MAXROW) {
         int cnt = 0;
-        for_candidates_warp(w, i, rc2, lane, [&](bool hit, int j) {
+        for_candidates_warp(w, i, rc2, lane, [&](bool hit, int j, float) {
             const unsigned m = __ballot_sync(DMTS_FULL, hit);
             if (hit) sb[cnt + __popc(m & ((1u << lane) - 1u))] = j;
             cnt += __popc(m);
@@ -242,19 +277,24 @@ __global__ void __launch_bounds__(NB_WARPS * 32) k_nbr_fill_warp(NbrWork w, floa
                 __syncwarp();
             }
         for (int t = lane; t < cnt; t += 32) col[beg + t] = sb[t];
-    } else if (lane == 0) {
+        if (sub_col) write_sub_row(w, i, sb, cnt, rc2_sub, sub_col + sub_row[i], lane);
+    } else {
         // rows longer than the shared buffer: serial fill + insertion sort
-        int p = beg;
-        for_candidates(w, i, rc2, [&](int j) { col[p++] = j; });
-        for (int a = beg + 1; a < p; ++a) {
-            const int v = col[a];
-            int b = a - 1;
-            while (b >= beg && col[b] > v) {
-                col[b + 1] = col[b];
-                --b;
+        if (lane == 0) {
+            int p = beg;
+            for_candidates(w, i, rc2, [&](int j) { col[p++] = j; });
+            for (int a = beg + 1; a < p; ++a) {
+                const int v = col[a];
+                int b = a - 1;
+                while (b >= beg && col[b] > v) {
+                    col[b + 1] = col[b];
+                    --b;
+                }
+                col[b + 1] = v;
             }
-            col[b + 1] = v;
         }
+        __syncwarp();
+        if (sub_col) write_sub_row(w, i, col + beg, n, rc2_sub, sub_col + sub_row[i], lane);
     }
     if (x_ref && lane == 0) {
         x_ref[3 * i] = w.x[3 * i];
@@ -317,66 +357,21 @@ void nbr_cells(const NbrWork &w, float r_list, cudaStream_t st) {
 }
 
 void nbr_fill(const NbrWork &w, float r_list, int *row_ptr, int *col, long long capacity, float *x_ref,
-              cudaStream_t st) {
+              cudaStream_t st, float r_sub, int *sub_row, int *sub_col, long long sub_capacity) {
     if (w.n_atoms == 0) return;
     const int nb = (w.n_atoms + NB_WARPS - 1) / NB_WARPS;
-    k_nbr_count_warp<<<nb, NB_WARPS * 32, 0, st>>>(w, r_list * r_list);
+    NbrWork wc = w;
+    if (!sub_row) wc.counts_sub = nullptr;
+    k_nbr_count_warp<<<nb, NB_WARPS * 32, 0, st>>>(wc, r_list * r_list, r_sub * r_sub);
     count_launch();
-    scan_ints(w.counts, w.n_atoms, row_ptr, capacity, w.total, w.err, w.gate, st);
+    scan_ints(wc.counts, wc.n_atoms, row_ptr, capacity, wc.total, wc.err, wc.gate, st);
+    if (wc.counts_sub) scan_ints(wc.counts_sub, wc.n_atoms, sub_row, sub_capacity, wc.total, wc.err, wc.gate, st);
     if (col) {
-        k_nbr_fill_warp<<<nb, NB_WARPS * 32, 0, st>>>(w, r_list * r_list, row_ptr, col, x_ref);
+        k_nbr_fill_warp<<<nb, NB_WARPS * 32, 0, st>>>(wc, r_list * r_list, row_ptr, col, x_ref, r_sub * r_sub,
+                                                      wc.counts_sub ? sub_row : nullptr,
+                                                      wc.counts_sub ? sub_col : nullptr);
         count_launch();
     }
-}
-
-// ------------------------------------------------------------- sub-lists
-__global__ void k_sub_count(NbrWork w, const int *p_row, const int *p_col, float r2cut) {
-    if (gated_off(w.gate, w.err)) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= w.n_atoms) return;
-    const CellGrid g = w.grid[w.atom_rep[i]];
-    const float ibx = g.box[0] > 0.f ? 1.f / g.box[0] : 0.f, iby = g.box[1] > 0.f ? 1.f / g.box[1] : 0.f,
-                ibz = g.box[2] > 0.f ? 1.f / g.box[2] : 0.f;
-    const float xi = w.x[3 * i], yi = w.x[3 * i + 1], zi = w.x[3 * i + 2];
-    int cnt = 0;
-    for (int e = p_row[i]; e < p_row[i + 1]; ++e) {
-        const int j = p_col[e];
-        const float dx = min_img(w.x[3 * j] - xi, g.box[0], ibx);
-        const float dy = min_img(w.x[3 * j + 1] - yi, g.box[1], iby);
-        const float dz = min_img(w.x[3 * j + 2] - zi, g.box[2], ibz);
-        if (dx * dx + dy * dy + dz * dz < r2cut) ++cnt;
-    }
-    w.counts[i] = cnt;
-}
-
-__global__ void k_sub_fill(NbrWork w, const int *p_row, const int *p_col, float r2cut, const int *row_ptr,
-                           int *col) {
-    if (gated_off(w.gate, w.err)) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= w.n_atoms) return;
-    const CellGrid g = w.grid[w.atom_rep[i]];
-    const float ibx = g.box[0] > 0.f ? 1.f / g.box[0] : 0.f, iby = g.box[1] > 0.f ? 1.f / g.box[1] : 0.f,
-                ibz = g.box[2] > 0.f ? 1.f / g.box[2] : 0.f;
-    const float xi = w.x[3 * i], yi = w.x[3 * i + 1], zi = w.x[3 * i + 2];
-    int p = row_ptr[i];
-    for (int e = p_row[i]; e < p_row[i + 1]; ++e) {
-        const int j = p_col[e];
-        const float dx = min_img(w.x[3 * j] - xi, g.box[0], ibx);
-        const float dy = min_img(w.x[3 * j + 1] - yi, g.box[1], iby);
-        const float dz = min_img(w.x[3 * j + 2] - zi, g.box[2], ibz);
-        if (dx * dx + dy * dy + dz * dz < r2cut) col[p++] = j;
-    }
-}
-
-void nbr_sublist(const NbrWork &w, const int *p_row, const int *p_col, float r, int *row_ptr, int *col,
-                 long long capacity, cudaStream_t st) {
-    if (w.n_atoms == 0) return;
-    const int nb = (w.n_atoms + 127) / 128;
-    k_sub_count<<<nb, 128, 0, st>>>(w, p_row, p_col, r * r);
-    count_launch();
-    scan_ints(w.counts, w.n_atoms, row_ptr, capacity, w.total, w.err, w.gate, st);
-    k_sub_fill<<<nb, 128, 0, st>>>(w, p_row, p_col, r * r, row_ptr, col);
-    count_launch();
 }
 
 }  // namespace dmts

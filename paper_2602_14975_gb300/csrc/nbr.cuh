@@ -32,17 +32,18 @@ struct NbrWork {
     long long *total;     // [1] device: pairs needed by the last fill
     const int *gate;      // nullable: skip everything when *gate == 0
     int *err;             // sticky error word
+    int *counts_sub = nullptr;   // [n_atoms]: row lengths of the sub-list (nbr_fill with a sub-list)
 };
 
 // Builds the cell structure (assign, count, scan, scatter, sort).
 void nbr_cells(const NbrWork &w, float r_list, cudaStream_t st);
 // Count + scan + fill of a full list within r_list using the cell structure.
-// x_ref (nullable) receives the positions used.
+// x_ref (nullable) receives the positions used. With sub_col (and
+// w.counts_sub) the same pass also writes the sub-list of entries within
+// r_sub < r_list (rows in the same ascending order).
 void nbr_fill(const NbrWork &w, float r_list, int *row_ptr, int *col, long long capacity,
-              float *x_ref, cudaStream_t st);
-// Sub-list of a parent list: entries with |d|^2 < r^2.
-void nbr_sublist(const NbrWork &w, const int *p_row, const int *p_col, float r, int *row_ptr, int *col,
-                 long long capacity, cudaStream_t st);
+              float *x_ref, cudaStream_t st, float r_sub = 0.f, int *sub_row = nullptr, int *sub_col = nullptr,
+              long long sub_capacity = -1);
 // Atom -> replica map.
 void atom_rep_map(const int *rep_off, int n_rep, int n_atoms, int *atom_rep, cudaStream_t st);
 // Exclusive scan of n ints into out[n+1]; if capacity >= 0 and the total
