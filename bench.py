@@ -185,6 +185,19 @@ def oracle_outer_step_seconds(sy, W, frac_edge):
     return per_outer * scale, desc
 
 
+def workload_config(sy, I, cs, ns):
+    """The `config` of the JSON line (the same for both arms)."""
+    return {"workload": sy.name, "n_atoms": sy.n_atoms,
+            "integrator": f"DMTS-NC outer {I.dt_outer} fs / {I.n_inner} inner, HMR +{I.hmr_delta} amu on H, "
+                          f"gamma_H {I.gamma_ps[0]}/ps, gamma_heavy {I.gamma_ps[1]}/ps",
+            "cons_model": f"L={cs.L} C={cs.C} lmax={cs.lmax} K={cs.K} rc={cs.rc}",
+            "nc_model": f"C={ns.C} lmax=1 rc={ns.rc} n_c={ns.n_c} n_l={ns.n_l}",
+            "precision": ("bf16 MLP contractions on the tensor cores (tcgen05, fp32 accumulate), "
+                          "fp32 everywhere else, fp64 per-replica sums") if cs.bf16 else "fp32",
+            "l2": "inputs larger than L2: about 0.5 GB of node and edge data per outer step",
+            "parallelism": "replicas only (one replica per GPU)"}
+
+
 def serving_roofline(prof, atom_outer_steps, n_inner, cs):
     """Per-kernel rates inside the serving loop, where one launch covers every
     resident replica (often 10^5 atoms or more): the integrator against HBM
@@ -245,7 +258,7 @@ def main():
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": t_outer * 1e3, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": sy.name, "n_atoms": sy.n_atoms},
+                "config": workload_config(sy, I, W["cons"](), W["nc"]()),
                 "cpu_baseline": {"value": val, "unit": "ns/day", "cores": 1, "kind": "oracle", "sample": desc},
                 "e2e": {"value": val, "unit": "ns/day", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
                 "wall_s": wall}
@@ -549,15 +562,7 @@ def main():
         "metric": "ns/day (DMTS-NC)", "value": val, "unit": "ns/day", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_dmts, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16" if cs.bf16 else "f32", "data": "synthetic",
-        "config": {"workload": sy.name, "n_atoms": sy.n_atoms,
-                   "integrator": f"DMTS-NC outer {I.dt_outer} fs / {I.n_inner} inner, HMR +{I.hmr_delta} amu on H, "
-                                 f"gamma_H {I.gamma_ps[0]}/ps, gamma_heavy {I.gamma_ps[1]}/ps",
-                   "cons_model": f"L={cs.L} C={cs.C} lmax={cs.lmax} K={cs.K} rc={cs.rc}",
-                   "nc_model": f"C={ns.C} lmax=1 rc={ns.rc} n_c={ns.n_c} n_l={ns.n_l}",
-                   "precision": ("bf16 MLP contractions on the tensor cores (tcgen05, fp32 accumulate), "
-                                 "fp32 everywhere else, fp64 per-replica sums") if cs.bf16 else "fp32",
-                   "l2": "inputs larger than L2: about 0.5 GB of node and edge data per outer step",
-                   "parallelism": "replicas only (one replica per GPU)"},
+        "config": workload_config(sy, I, cs, ns),
         "atom_steps_per_s": sy.n_atoms * 1e3 / ms_dmts * world,
         "sts": {"ns_per_day": sts_val, "ms_per_step": ms_sts, "dt_fs": sts.dt_outer,
                 "atom_steps_per_s": sy.n_atoms * 1e3 / ms_sts * world},
