@@ -526,6 +526,8 @@ void prepare_nbr_work_async(dmts_ctx *ctx, StateInternal *si, const SysView &v, 
     nw.atom_slot = (int *)b.atom_slot.p;
     nw.counts = (int *)b.counts.p;
     nw.counts_sub = (int *)b.counts_sub.p;
+    nw.slots = b.slots.p ? (int *)b.slots.p : nullptr;
+    nw.slot_cap = kNbrSlots;
     nw.total = (long long *)b.total.p;
     nw.gate = (int *)si->gate.p;
     nw.err = ctx->d_err;
@@ -632,7 +634,8 @@ dmts_status init_state(dmts_ctx *ctx, dmts_state *stt, float skin, cudaStream_t 
     const long long want_cons = (long long)(tot * 1.4) + 16LL * N + 1024;
     const double frac = ctx->has_nc ? std::pow(si->r_nc / si->r_cons, 3.0) : 0.0;
     const long long want_nc = (long long)(tot * frac * 1.6) + 16LL * N + 1024;
-    if (!si->cons_col.ensure(sizeof(int) * want_cons) || !si->nc_col.ensure(sizeof(int) * want_nc))
+    if (!si->cons_col.ensure(sizeof(int) * want_cons) || !si->nc_col.ensure(sizeof(int) * want_nc) ||
+        !si->scratch.slots.ensure(sizeof(int) * (size_t)N * kNbrSlots))
         return fail(ctx, DMTS_E_OOM, "neighbour list allocation failed");
     si->cons_cap = (long long)(si->cons_col.cap / sizeof(int));
     si->nc_cap = (long long)(si->nc_col.cap / sizeof(int));

@@ -35,11 +35,15 @@ struct DevModel {
     __nv_bfloat16 *wr_bf = nullptr, *wrt_bf = nullptr, *wqk_bf = nullptr;
 };
 
+constexpr int kNbrSlots = 128;   // longest row kept by the count pass of a state's rebuild
+
 struct NbrScratch {
     Buf grid, cell_cnt, cell_start, cell_atoms, atom_cell, atom_slot, counts, total, counts_sub;
+    Buf slots;    // [n_atoms][kNbrSlots] sorted rows kept between the count and the fill of a rebuild
     void release_all() {
         grid.release(); cell_cnt.release(); cell_start.release(); cell_atoms.release();
         atom_cell.release(); atom_slot.release(); counts.release(); total.release(); counts_sub.release();
+        slots.release();
     }
 };
 

@@ -197,19 +197,61 @@ __device__ __forceinline__ void for_candidates_warp(const NbrWork &w, int i, flo
     }
 }
 
+constexpr unsigned SUB_FLAG = 0x80000000u;   // slot entry within the sub-list cutoff
+
+// Ascending bitonic sort of sb[0..cnt) (values compared without SUB_FLAG).
+__device__ __forceinline__ void sort_row(int *sb, int cnt, int lane) {
+    int len = 32;
+    while (len < cnt) len <<= 1;
+    for (int t = cnt + lane; t < len; t += 32) sb[t] = 0x7fffffff;
+    __syncwarp();
+    for (int k = 2; k <= len; k <<= 1)
+        for (int jj = k >> 1; jj > 0; jj >>= 1) {
+            for (int t = lane; t < len; t += 32) {
+                const int u = t ^ jj;
+                if (u > t) {
+                    const int a = sb[t], b = sb[u];
+                    const bool up = (t & k) == 0;
+                    if (((a & 0x7fffffff) > (b & 0x7fffffff)) == up) {
+                        sb[t] = b;
+                        sb[u] = a;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+}
+
+// Row lengths (and sub-list row lengths). With w.slots the sorted row, sub
+// entries flagged, is also kept for the fill, which then only copies it.
 __global__ void __launch_bounds__(NB_WARPS * 32) k_nbr_count_warp(NbrWork w, float rc2, float rc2_sub) {
     if (gated_off(w.gate, w.err)) return;
+    __shared__ int buf[NB_WARPS][NB_MAXROW];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = blockIdx.x * NB_WARPS + warp;
     if (i >= w.n_atoms) return;
+    int *sb = buf[warp];
+    const bool keep = w.slots != nullptr;
     int cnt = 0, cnt_sub = 0;
-    for_candidates_warp(w, i, rc2, lane, [&](bool hit, int, float r2) {
-        cnt += __popc(__ballot_sync(DMTS_FULL, hit));
-        if (w.counts_sub) cnt_sub += __popc(__ballot_sync(DMTS_FULL, hit && r2 < rc2_sub));
+    for_candidates_warp(w, i, rc2, lane, [&](bool hit, int j, float r2) {
+        const bool sub = hit && r2 < rc2_sub;
+        const unsigned m = __ballot_sync(DMTS_FULL, hit);
+        if (keep && hit) {
+            const int pos = cnt + __popc(m & ((1u << lane) - 1u));
+            if (pos < NB_MAXROW) sb[pos] = (int)((unsigned)j | (sub && w.counts_sub ? SUB_FLAG : 0u));
+        }
+        cnt += __popc(m);
+        if (w.counts_sub) cnt_sub += __popc(__ballot_sync(DMTS_FULL, sub));
     });
     if (lane == 0) {
         w.counts[i] = cnt;
         if (w.counts_sub) w.counts_sub[i] = cnt_sub;
+    }
+    if (keep && cnt <= w.slot_cap && cnt <= NB_MAXROW) {
+        __syncwarp();
+        sort_row(sb, cnt, lane);
+        int *dst = w.slots + (size_t)i * w.slot_cap;
+        for (int t = lane; t < cnt; t += 32) dst[t] = sb[t];
     }
 }
 
@@ -249,33 +291,30 @@ __global__ void __launch_bounds__(NB_WARPS * 32) k_nbr_fill_warp(NbrWork w, floa
     if (i >= w.n_atoms) return;
     int *sb = buf[warp];
     const int beg = row_ptr[i], n = row_ptr[i + 1] - beg;
-    if (n <= NB_MAXROW) {
+    if (w.slots && n <= w.slot_cap && n <= NB_MAXROW) {
+        // the count pass kept the sorted row: copy it, sub entries by their flag
+        const int *src = w.slots + (size_t)i * w.slot_cap;
+        int done = 0;
+        for (int t0 = 0; t0 < n; t0 += 32) {
+            const int t = t0 + lane;
+            const unsigned v = t < n ? (unsigned)src[t] : 0u;
+            const int j = (int)(v & ~SUB_FLAG);
+            if (t < n) col[beg + t] = j;
+            if (sub_col) {
+                const bool in = t < n && (v & SUB_FLAG);
+                const unsigned m = __ballot_sync(DMTS_FULL, in);
+                if (in) sub_col[sub_row[i] + done + __popc(m & ((1u << lane) - 1u))] = j;
+                done += __popc(m);
+            }
+        }
+    } else if (n <= NB_MAXROW) {
         int cnt = 0;
         for_candidates_warp(w, i, rc2, lane, [&](bool hit, int j, float) {
             const unsigned m = __ballot_sync(DMTS_FULL, hit);
             if (hit) sb[cnt + __popc(m & ((1u << lane) - 1u))] = j;
             cnt += __popc(m);
         });
-        // pad to a power of two and sort ascending (bitonic network)
-        int len = 32;
-        while (len < cnt) len <<= 1;
-        for (int t = cnt + lane; t < len; t += 32) sb[t] = 0x7fffffff;
-        __syncwarp();
-        for (int k = 2; k <= len; k <<= 1)
-            for (int jj = k >> 1; jj > 0; jj >>= 1) {
-                for (int t = lane; t < len; t += 32) {
-                    const int u = t ^ jj;
-                    if (u > t) {
-                        const int a = sb[t], b = sb[u];
-                        const bool up = (t & k) == 0;
-                        if ((a > b) == up) {
-                            sb[t] = b;
-                            sb[u] = a;
-                        }
-                    }
-                }
-                __syncwarp();
-            }
+        sort_row(sb, cnt, lane);
         for (int t = lane; t < cnt; t += 32) col[beg + t] = sb[t];
         if (sub_col) write_sub_row(w, i, sb, cnt, rc2_sub, sub_col + sub_row[i], lane);
     } else {

@@ -33,6 +33,8 @@ struct NbrWork {
     const int *gate;      // nullable: skip everything when *gate == 0
     int *err;             // sticky error word
     int *counts_sub = nullptr;   // [n_atoms]: row lengths of the sub-list (nbr_fill with a sub-list)
+    int *slots = nullptr;        // [n_atoms][slot_cap] (nullable): sorted rows kept by the count pass
+    int slot_cap = 0;
 };
 
 // Builds the cell structure (assign, count, scan, scatter, sort).

@@ -147,8 +147,9 @@ long long dmts_replica_footprint(const dmts_ctx *ctx, int n_atoms) {
     if (!ctx || n_atoms <= 0) return 0;
     // per-atom state (x, v, two force caches, x_ref, masses, species, mol, bonds)
     long long b = (long long)n_atoms * (4 * 12 + 12 + 4 + 1 + 4 + 4 * 4);
-    // neighbour lists (about 80 + 40 entries per atom with head-room)
-    b += (long long)n_atoms * 4 * 160;
+    // neighbour lists (about 80 + 40 entries per atom with head-room) and the
+    // sorted rows kept between the count and the fill of a rebuild
+    b += (long long)n_atoms * 4 * (160 + kNbrSlots);
     // activations of the conservative model
     const DevModel &m = ctx->cons;
     const int nlm = (m.lmax + 1) * (m.lmax + 1);
