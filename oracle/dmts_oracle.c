@@ -33,6 +33,9 @@
  *   orc_respa_run     Algorithm 1 (DMTS-NC integration step), force caching
  *                     across outer steps.
  *   orc_sts_run       single-time-step BAOAB (Sec. 2, Sec. 3 setup).
+ *   Both take the O-step's thermostat: Langevin, or the Fast Forward Langevin
+ *   update of Sec. 2 "High Hydrogen Friction" (the Langevin speed, the old
+ *   direction, per-atom norms).
  */
 #include <math.h>
 #include <stdint.h>
