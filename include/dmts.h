@@ -223,10 +223,14 @@ dmts_status energy_forces_cons(dmts_ctx *ctx, const dmts_system *sys, const dmts
  * Non-conservative direct forces (Sec. 2 "Model architecture"; Algorithm 1,
  * FENNIX_NC). forces: device float [n_atoms][3]; net_force: device double
  * [n_replicas][3], the per-replica sum before the mean subtraction (may be
- * NULL). nbr: list with r_list >= NC rc.
+ * NULL); virial: device double [n_replicas] (may be NULL), the proxy
+ * -sum_i F_i . q_i of Sec. 2 "Computation of the virial term in NPT" in its
+ * pair form sum_i sum_{j in N(i)} (F_ij + F_pair,ij / 2) . r_ij, F_pair the
+ * repulsion and (with DMTS_WITH_BONDS) bond pair forces. nbr: list with
+ * r_list >= NC rc.
  */
 dmts_status forces_nc(dmts_ctx *ctx, const dmts_system *sys, const dmts_nbr *nbr,
-                      float *forces, double *net_force, int flags, void *stream);
+                      float *forces, double *net_force, double *virial, int flags, void *stream);
 
 typedef enum { DMTS_MODE_RESPA = 0, DMTS_MODE_STS = 1 } dmts_mode;
 
@@ -272,6 +276,9 @@ typedef struct {
     const uint32_t *replica_id;/* device uint32 [n_replicas] */
     int first_step;            /* host flag: 1 = forces not yet evaluated */
     void *internal;            /* library-owned; NULL before the first call */
+    double *virial_nc;         /* device double [n_replicas] (may be NULL): RESPA only, after each outer
+                                  step the average over its n inner steps of the fast force's virial
+                                  proxy (see forces_nc; Sec. 2 "Computation of the virial term in NPT") */
 } dmts_state;
 
 /*

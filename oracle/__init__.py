@@ -66,9 +66,9 @@ def _declare(L):
     L.orc_cons_features.restype = None
     L.orc_cons_features.argtypes = [ct.c_int, _D, _U8, _D, _I, _D, _D, _D]
     L.orc_prior.restype = ct.c_double
-    L.orc_prior.argtypes = [ct.c_int, _D, _U8, _I, _D, ct.c_int, _I, _D, _D, ct.c_int, _D]
+    L.orc_prior.argtypes = [ct.c_int, _D, _U8, _I, _D, ct.c_int, _I, _D, _D, ct.c_int, _D, _D]
     L.orc_nc_forces.restype = None
-    L.orc_nc_forces.argtypes = [ct.c_int, _D, _U8, _D, _I, _D, _D, ct.c_int, _I, _D, _D, ct.c_int, _D, _D]
+    L.orc_nc_forces.argtypes = [ct.c_int, _D, _U8, _D, _I, _D, _D, ct.c_int, _I, _D, _D, ct.c_int, _D, _D, _D]
     L.orc_zbl_phi.restype = ct.c_double
     L.orc_zbl_phi.argtypes = [ct.c_double]
     L.orc_rep_pair.restype = ct.c_double
@@ -96,7 +96,7 @@ def _declare(L):
     L.orc_respa_run.restype = ct.c_double
     L.orc_respa_run.argtypes = [_I, _D, ct.c_uint64, _U8, _I, _D, _I, _D, _D,
                                 _I, _D, _D, _I, _D, _D, _D, _D,
-                                ct.c_int, _D, _D, _D, _D, _U64, _I]
+                                ct.c_int, _D, _D, _D, _D, _U64, _I, _D]
     L.orc_sts_run.restype = ct.c_double
     L.orc_sts_run.argtypes = [_I, _D, ct.c_uint64, _U8, _I, _D, _I, _D, _D,
                               _I, _D, _D, _D, _D, ct.c_int, _D, _D, _D, _U64, _I]
@@ -198,12 +198,30 @@ def prior(sys, with_lj=True, consts=PRIOR, terms=None):
     c, pc = _d(consts)
     F = np.zeros((x.shape[0], 3))
     E = L.orc_prior(x.shape[0], px, ps, pm, pb, b.shape[0], pbd, pr0, pc, int(terms),
-                    F.ctypes.data_as(_D))
+                    F.ctypes.data_as(_D), None)
     return E, F
 
 
-def nc_forces(sys, spec, blob, with_bonds=True, consts=PRIOR, fast_terms=None):
-    """Returns (F after mean subtraction, net force before subtraction).
+def prior_virial(sys, terms, consts=PRIOR):
+    """Virial proxy -sum_i F_i . q_i of the analytic terms, in pair form
+    (sum over pairs of r dE/dr)."""
+    L = lib()
+    x, px = _d(sys.x)
+    sp, ps = _u8(sys.species)
+    mol, pm = _i(sys.mol_id)
+    box, pb = _d(sys.box)
+    b, pbd = _i(sys.bonds.reshape(-1, 2))
+    r0, pr0 = _d(sys.bond_r0)
+    c, pc = _d(consts)
+    W = ct.c_double(0.0)
+    L.orc_prior(x.shape[0], px, ps, pm, pb, b.shape[0], pbd, pr0, pc, int(terms), None, ct.byref(W))
+    return W.value
+
+
+def nc_forces(sys, spec, blob, with_bonds=True, consts=PRIOR, fast_terms=None, with_virial=False):
+    """Returns (F after mean subtraction, net force before subtraction), and
+    the virial proxy sum_i sum_j F_ij . r_ij (+ pair form of the fast terms)
+    as a third value with with_virial.
     fast_terms: prior terms added to the NC force (default bonds + repulsion,
     none when with_bonds is False)."""
     if fast_terms is None:
@@ -220,9 +238,10 @@ def nc_forces(sys, spec, blob, with_bonds=True, consts=PRIOR, fast_terms=None):
     c, pc = _d(consts)
     F = np.zeros((x.shape[0], 3))
     net = np.zeros(3)
+    W = ct.c_double(0.0)
     L.orc_nc_forces(x.shape[0], px, ps, pb, pmi, pmr, pw, b.shape[0], pbd,
-                    pr0, pc, int(fast_terms), F.ctypes.data_as(_D), net.ctypes.data_as(_D))
-    return F, net
+                    pr0, pc, int(fast_terms), F.ctypes.data_as(_D), net.ctypes.data_as(_D), ct.byref(W))
+    return (F, net, W.value) if with_virial else (F, net)
 
 
 def philox4x32_10(ctr, key):
@@ -317,8 +336,10 @@ LANGEVIN, FFL = 0, 1
 
 def respa_run(state, sys, cons_spec, cons_blob, nc_spec, nc_blob, dt_outer, n_inner, T,
               gamma_ps, seed, n_outer, replica=0, inner_mode=0, outer_mode=0, consts=PRIOR,
-              thermostat=LANGEVIN):
+              thermostat=LANGEVIN, virial_avg=None):
     """Algorithm 1 for n_outer outer steps; returns the last potential energy.
+    virial_avg (a ctypes double, optional) receives the average virial proxy
+    of the fast force over the inner steps of the last outer step.
     inner_mode: 0 NC + bonds, 1 full -grad U (collapse to BAOAB), 2 bonds only.
     outer_mode: 0 -grad(U_MP + prior), 1 bonds only.
     thermostat: LANGEVIN or FFL (Fast Forward Langevin O-step)."""
@@ -343,7 +364,8 @@ def respa_run(state, sys, cons_spec, cons_blob, nc_spec, nc_blob, dt_outer, n_in
                            pcmi, pcmr, pcb, pnmi, pnmr, pnb, pmm, pg, int(n_outer),
                            state.x.ctypes.data_as(_D), state.v.ctypes.data_as(_D),
                            state.F.ctypes.data_as(_D), state.F_nc.ctypes.data_as(_D),
-                           ct.byref(state.step), ct.byref(state.first))
+                           ct.byref(state.step), ct.byref(state.first),
+                           ct.byref(virial_avg) if virial_avg is not None else None)
 
 
 def sts_run(state, sys, cons_spec, cons_blob, dt, T, gamma_ps, seed, n_steps, replica=0,

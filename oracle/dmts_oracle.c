@@ -557,8 +557,11 @@ static void bond_adjacency(int n, int n_bonds, const int *bonds, int **ptr_out, 
  * closer than rep_rc that are not bonded). */
 double orc_prior(int n, const double *x, const uint8_t *species, const int *mol_id,
                  const double *box, int n_bonds, const int *bonds, const double *bond_r0,
-                 const double *pr, int terms, double *F)
+                 const double *pr, int terms, double *F, double *virial)
 {
+    /* virial (nullable): -sum_i F_i . q_i written with pair terms, the sum
+     * over pairs of r dE/dr (Sec. 2 "Computation of the virial term in NPT") */
+    if (virial) *virial = 0.0;
     double kb = pr[0], eps = pr[1], sig = pr[2], rlj = pr[3], plj = pr[4];
     double rrep = pr[5], prep = pr[6];
     int with_lj = (terms & 2) != 0;
@@ -571,6 +574,7 @@ double orc_prior(int n, const double *x, const uint8_t *species, const int *mol_
         double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
         double dr = r - bond_r0[b];
         E += 0.5 * kb * dr * dr;
+        if (virial) *virial += kb * dr * r;
         if (F) {
             double g = kb * dr / r;   /* dE/dd = g d */
             for (int a = 0; a < 3; ++a) {
@@ -595,6 +599,7 @@ double orc_prior(int n, const double *x, const uint8_t *species, const int *mol_
                 double u = r / rlj;
                 double fc = orc_envelope(u, plj), dfc = orc_denvelope(u, plj) / rlj;
                 E += elj * fc;
+                if (virial) *virial += (delj * fc + elj * dfc) * r;
                 if (F) {
                     double g = (delj * fc + elj * dfc) / r;
                     for (int a = 0; a < 3; ++a) {
@@ -618,6 +623,7 @@ double orc_prior(int n, const double *x, const uint8_t *species, const int *mol_
                 if (is_bonded) continue;
                 double r = sqrt(r2), dEdr;
                 E += orc_rep_pair(species[i], species[j], r, rrep, prep, &dEdr);
+                if (virial) *virial += dEdr * r;
                 if (F) {
                     double g = dEdr / r;
                     for (int a = 0; a < 3; ++a) {
@@ -649,8 +655,12 @@ double orc_prior(int n, const double *x, const uint8_t *species, const int *mol_
 void orc_nc_forces(int n, const double *x, const uint8_t *species, const double *box,
                    const int *mi, const double *mr, const double *blob,
                    int n_bonds, const int *bonds, const double *bond_r0, const double *pr,
-                   int fast_terms, double *F, double *net_pre)
+                   int fast_terms, double *F, double *net_pre, double *virial)
 {
+    /* virial (nullable): the proxy -sum_i F_i . q_i of Sec. 2 "Computation of
+     * the virial term in NPT", as sum_i sum_{j in N(i)} F_ij . r_ij (scaled
+     * like the forces) plus the pair form of the fast analytic terms */
+    double W = 0.0;
     model_t m;
     parse_nc(&m, mi, mr, blob);
     int C = m.C, K = m.K, nl = m.nl, nc = m.nc, H = K + nl, nlm = m.nlm;
@@ -719,13 +729,16 @@ void orc_nc_forces(int n, const double *x, const uint8_t *species, const double 
             for (int a = 0; a < 3; ++a) out[a] = S * vec[a] * fc;
         }
         for (int a = 0; a < 3; ++a) F[3 * i + a] += m.scale * (Fij[a] - Fji[a]);
+        for (int a = 0; a < 3; ++a) W += m.scale * Fij[a] * E.d[3 * e + a];
     }
     if (fast_terms) {
-        double *Fb = malloc(sizeof(double) * 3 * n);
-        orc_prior(n, x, species, NULL, box, n_bonds, bonds, bond_r0, pr, fast_terms, Fb);
+        double *Fb = malloc(sizeof(double) * 3 * n), Wb = 0.0;
+        orc_prior(n, x, species, NULL, box, n_bonds, bonds, bond_r0, pr, fast_terms, Fb, &Wb);
         for (int i = 0; i < 3 * n; ++i) F[i] += Fb[i];
+        W += Wb;
         free(Fb);
     }
+    if (virial) *virial = W;
     double net[3] = {0, 0, 0};
     for (int i = 0; i < n; ++i)
         for (int a = 0; a < 3; ++a) net[a] += F[3 * i + a];
@@ -856,29 +869,32 @@ static double full_force(const md_t *md, const double *x, double *F)
     if (md->outer_mode == 0) {
         E = orc_cons_energy_forces(md->n, x, md->species, md->box, md->cmi, md->cmr, md->cblob, F);
         E += orc_prior(md->n, x, md->species, md->mol_id, md->box, md->n_bonds, md->bonds,
-                       md->bond_r0, md->prior, 7, Fp);
+                       md->bond_r0, md->prior, 7, Fp, NULL);
     } else {
         for (int i = 0; i < 3 * md->n; ++i) F[i] = 0.0;
         E = orc_prior(md->n, x, md->species, md->mol_id, md->box, md->n_bonds, md->bonds,
-                      md->bond_r0, md->prior, 1, Fp);
+                      md->bond_r0, md->prior, 1, Fp, NULL);
     }
     for (int i = 0; i < 3 * md->n; ++i) F[i] += Fp[i];
     free(Fp);
     return E;
 }
 
-/* Fast (inner) force F_S. */
-static void inner_force(const md_t *md, const double *x, double *F)
+/* Fast (inner) force F_S; returns its virial proxy (pair form; 0 for the
+ * full force, which has no pair form). */
+static double inner_force(const md_t *md, const double *x, double *F)
 {
+    double W = 0.0;
     if (md->inner_mode == 0) {
         orc_nc_forces(md->n, x, md->species, md->box, md->nmi, md->nmr, md->nblob, md->n_bonds,
-                      md->bonds, md->bond_r0, md->prior, 5, F, NULL);
+                      md->bonds, md->bond_r0, md->prior, 5, F, NULL, &W);
     } else if (md->inner_mode == 1) {
         full_force(md, x, F);
     } else {
         orc_prior(md->n, x, md->species, md->mol_id, md->box, md->n_bonds, md->bonds, md->bond_r0,
-                  md->prior, 1, F);
+                  md->prior, 1, F, &W);
     }
+    return W;
 }
 
 static void kick(int n, double *v, const double *F, const double *F2, double h, const double *mass)
@@ -926,6 +942,9 @@ static void ostep(const md_t *md, double *v, double dt, uint64_t step)
 /* Algorithm 1 (DMTS-NC integration step), repeated n_outer times.
  * state: x, v, F (full force -grad U), F_nc (fast force), *step (global inner
  * step index, advanced by n per outer step), *first (force cache flag).
+ * virial_avg (nullable): average over the n inner force evaluations of the
+ * last outer step of the fast force's virial proxy (Sec. 2 "Computation of
+ * the virial term in NPT").
  * ints: [n_atoms, n_bonds, inner_mode, outer_mode, n_inner, replica, thermostat]
  * reals: [dt_outer, T]
  * Returns the last evaluated potential energy U. */
@@ -936,7 +955,7 @@ double orc_respa_run(const int *ints, const double *reals, uint64_t seed,
                      const int *nmi, const double *nmr, const double *nblob,
                      const double *mass, const double *gamma_ps,
                      int n_outer, double *x, double *v, double *F, double *F_nc,
-                     uint64_t *step, int *first)
+                     uint64_t *step, int *first, double *virial_avg)
 {
     md_t md = {ints[0], species, mol_id, box, ints[1], bonds, bond_r0, prior,
                cmi, cmr, cblob, nmi, nmr, nblob, mass, gamma_ps, reals[1], seed,
@@ -949,18 +968,20 @@ double orc_respa_run(const int *ints, const double *reals, uint64_t seed,
         *first = 0;
     }
     for (int o = 0; o < n_outer; ++o) {
+        double wsum = 0.0;
         kick(n, v, F, F_nc, Delta / 2.0, mass);                /* v += D/2 M^-1 (F - F_NC) */
         for (int k = 0; k < n_in; ++k) {
             kick(n, v, F_nc, NULL, delta / 2.0, mass);          /* B */
             drift(n, x, v, delta / 2.0);                        /* A */
             ostep(&md, v, delta, *step);                        /* O, Thermostat(v, D/n) */
             drift(n, x, v, delta / 2.0);                        /* A */
-            inner_force(&md, x, F_nc);                          /* F_NC <- NC(x) */
+            wsum += inner_force(&md, x, F_nc);                  /* F_NC <- NC(x) */
             kick(n, v, F_nc, NULL, delta / 2.0, mass);          /* B */
             *step += 1;
         }
         U = full_force(&md, x, F);                              /* F <- large(x) */
         kick(n, v, F, F_nc, Delta / 2.0, mass);                 /* v += D/2 M^-1 (F - F_NC) */
+        if (virial_avg) *virial_avg = wsum / n_in;
     }
     return U;
 }

@@ -183,16 +183,19 @@ def energy_forces_cons(ctx: Context, dsys: DeviceSystem, nbr: NbrList, with_prio
     return E, F
 
 
-def forces_nc(ctx: Context, dsys: DeviceSystem, nbr: NbrList, with_bonds=True):
-    """Returns (F_NC f32 [N,3] mean-subtracted, net force f64 [R,3] before subtraction)."""
+def forces_nc(ctx: Context, dsys: DeviceSystem, nbr: NbrList, with_bonds=True, with_virial=False):
+    """Returns (F_NC f32 [N,3] mean-subtracted, net force f64 [R,3] before
+    subtraction), and with with_virial the virial proxy f64 [R] as a third
+    value."""
     dev = dsys.x.device
     F = torch.empty(dsys.n_atoms, 3, dtype=torch.float32, device=dev)
     net = torch.empty(dsys.n_replicas, 3, dtype=torch.float64, device=dev)
+    W = torch.empty(dsys.n_replicas, dtype=torch.float64, device=dev) if with_virial else None
     s, nbs = dsys.struct(), nbr.struct()
-    st = ctx.lib.forces_nc(ctx.handle, ct.byref(s), ct.byref(nbs), _ptr(F), _ptr(net),
+    st = ctx.lib.forces_nc(ctx.handle, ct.byref(s), ct.byref(nbs), _ptr(F), _ptr(net), _ptr(W),
                            L.WITH_BONDS if with_bonds else 0, _stream(dev))
     L.check(st, ctx.handle)
-    return F, net
+    return (F, net, W) if with_virial else (F, net)
 
 
 def integrator(dt_outer, n_inner, temperature, gamma_ps, mode=L.MODE_RESPA, skin=0.5,
@@ -206,7 +209,7 @@ def integrator(dt_outer, n_inner, temperature, gamma_ps, mode=L.MODE_RESPA, skin
 class MDState:
     """Device-resident dynamic state of a batch (positions live in dsys.x)."""
 
-    def __init__(self, dsys: DeviceSystem, v, masses, seeds, replica_ids=None, steps=None):
+    def __init__(self, dsys: DeviceSystem, v, masses, seeds, replica_ids=None, steps=None, virial=False):
         dev = dsys.x.device
         self.dsys = dsys
         self.v = torch.as_tensor(np.asarray(v, np.float32)).to(dev).contiguous()
@@ -221,8 +224,12 @@ class MDState:
         self.replica_id = torch.from_numpy(rid.view(np.int32)).to(dev)
         st0 = np.zeros(R, np.uint64) if steps is None else np.asarray(steps, np.uint64)
         self.step = torch.from_numpy(st0.view(np.int64)).to(dev)
+        # with virial=True: average virial proxy of the fast force over the
+        # inner steps of the last outer step (RESPA), per replica
+        self.virial_nc = torch.zeros(R, dtype=torch.float64, device=dev) if virial else None
         self.c = L.State(dsys.struct(), _ptr(self.v), _ptr(self.f_nc), _ptr(self.f_cons), _ptr(self.masses),
-                         _ptr(self.energy), _ptr(self.step), _ptr(self.seed), _ptr(self.replica_id), 1, None)
+                         _ptr(self.energy), _ptr(self.step), _ptr(self.seed), _ptr(self.replica_id), 1, None,
+                         _ptr(self.virial_nc))
         self.ctx = None
 
     def release(self):

@@ -349,7 +349,7 @@ dmts_status cons_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const
 
 // F_NC (+ bonds, F_rep), mean-subtracted; net = per-replica sum before subtraction.
 dmts_status nc_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const int *col, float *forces,
-                    double *net, int flags, cudaStream_t st) {
+                    double *net, int flags, cudaStream_t st, double *virial, int virial_accumulate) {
     const DevModel &m = ctx->nc;
     const int N = s.n, C = m.C, H = m.K + m.nl, QKW = 2 * H * m.nc;
     Workspace &w = ctx->ws;
@@ -359,7 +359,8 @@ dmts_status nc_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const i
         !w.nc_q.ensure(sizeof(float) * nc_ * 2) || !w.nc_h.ensure(sizeof(float) * nc_) ||
         !w.nc_act.ensure(sizeof(float) * nc_) || !w.nc_qk.ensure(sizeof(float) * (size_t)N * QKW) ||
         !w.nc_v.ensure(sizeof(float) * (size_t)N * m.nl * 3) || !w.nc_f.ensure(sizeof(float) * 3 * (N + 1)) ||
-        !w.ms_scratch.ensure(mean_sub_scratch_bytes(N, s.n_rep)))
+        !w.ms_scratch.ensure(mean_sub_scratch_bytes(N, s.n_rep)) ||
+        (virial && !w.nc_w.ensure(sizeof(float) * (N + 1))))
         return fail(ctx, DMTS_E_OOM, "workspace allocation failed");
     if (bf && (!w.nc_q_bf.ensure(2 * nc_ * 2 + 16) || !w.nc_act_bf.ensure(2 * nc_ + 16) || !w.nc_s_bf.ensure(2 * nc_ + 16)))
         return fail(ctx, DMTS_E_OOM, "workspace allocation failed");
@@ -416,12 +417,17 @@ dmts_status nc_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const i
     a.rep = rep_table(ctx);
     a.species = s.species;
     a.F = (float *)w.nc_f.p;
+    a.W = virial ? (float *)w.nc_w.p : nullptr;
     a.order = s.order;
     a.err = ctx->d_err;
     { ProfScope ps(ctx, "nc_head", st); launch_nc_head(m.K, m.nc, m.nl, a, st); }
     {
         ProfScope ps(ctx, "mean_sub", st);
         launch_mean_sub((float *)w.nc_f.p, forces, s.rep_off, s.n_rep, N, net, w.ms_scratch.p, ctx->d_err, st);
+    }
+    if (virial) {
+        ProfScope ps(ctx, "replica_sum", st);
+        launch_replica_sum((const float *)w.nc_w.p, s.rep_off, s.n_rep, virial, virial_accumulate, st);
     }
     return DMTS_OK;
 }
@@ -820,7 +826,7 @@ dmts_status energy_forces_cons(dmts_ctx *ctx, const dmts_system *sys, const dmts
 }
 
 dmts_status forces_nc(dmts_ctx *ctx, const dmts_system *sys, const dmts_nbr *nbr, float *forces, double *net_force,
-                      int flags, void *stream) {
+                      double *virial, int flags, void *stream) {
     dmts_status s = check_sys(ctx, sys);
     if (s != DMTS_OK) return s;
     if (!ctx->has_nc) return fail(ctx, DMTS_E_INVALID, "context has no NC model");
@@ -831,7 +837,7 @@ dmts_status forces_nc(dmts_ctx *ctx, const dmts_system *sys, const dmts_nbr *nbr
     cudaSetDevice(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     SysView v = make_view(ctx, sys, st);
-    s = nc_eval(ctx, v, nbr->row_ptr, nbr->col, forces, net_force, flags, st);
+    s = nc_eval(ctx, v, nbr->row_ptr, nbr->col, forces, net_force, flags, st, virial, 0);
     if (s != DMTS_OK) return s;
     return ck(ctx, cudaGetLastError(), "forces_nc launch") ? DMTS_OK : DMTS_E_CUDA;
 }
@@ -895,11 +901,16 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
     auto cons_full = [&]() {
         return cons_eval(ctx, v, crow, ccol, stt->energy, stt->f_cons, DMTS_WITH_PRIOR, st);
     };
-    auto nc_fast = [&]() { return nc_eval(ctx, v, nrow, ncol, stt->f_nc, nullptr, DMTS_WITH_BONDS, st); };
+    // fast force; inside the inner loop it also adds its virial proxy to the
+    // per-replica average of the outer step (Sec. 2, virial term in NPT)
+    auto nc_fast = [&](bool with_virial) {
+        return nc_eval(ctx, v, nrow, ncol, stt->f_nc, nullptr, DMTS_WITH_BONDS, st,
+                       with_virial ? stt->virial_nc : nullptr, 1);
+    };
 
     if (stt->first_step) {
         if (!sts) {
-            s = nc_fast();
+            s = nc_fast(false);
             if (s != DMTS_OK) return s;
         }
         s = cons_full();
@@ -933,6 +944,9 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
     ia.h_out = 0.5f * p->dt_outer;
     if (n_outer == 0) return DMTS_OK;
     for (int o = 0; o < n_outer; ++o) {
+        if (!sts && stt->virial_nc &&
+            !ck(ctx, cudaMemsetAsync(stt->virial_nc, 0, sizeof(double) * v.n_rep, st), "virial reset"))
+            return DMTS_E_CUDA;
         for (int k = 0; k < n_in; ++k) {
             if (sts) ia.ops = (o == 0 ? 0 : OP_CLOSE_B) | OP_BAOA;
             else if (k == 0) ia.ops = (o == 0 ? OP_KICK_L2 : (OP_CLOSE_B | OP_KICK_L | OP_KICK_L2)) | OP_BAOA;
@@ -941,10 +955,11 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
             { ProfScope ps(ctx, "integrate", st); launch_integrate(ia, st); }
             rebuild_lists(ctx, si, v, st);
             if (!sts) {
-                s = nc_fast();
+                s = nc_fast(stt->virial_nc != nullptr);
                 if (s != DMTS_OK) return s;
             }
         }
+        if (!sts && stt->virial_nc) launch_scale_d(stt->virial_nc, v.n_rep, 1.0 / n_in, st);
         s = cons_full();
         if (s != DMTS_OK) return s;
     }

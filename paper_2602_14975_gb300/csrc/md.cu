@@ -38,7 +38,7 @@ void launch_rowsum(int n, int C, const float *u, float scale, float *e_atom, cud
 
 __device__ __forceinline__ void bond_force(const BondTable &b, const float *x, int a, float bx, float by,
                                            float bz, float ibx, float iby, float ibz, int lane, float &fx,
-                                           float &fy, float &fz, float &e) {
+                                           float &fy, float &fz, float &e, float *w = nullptr) {
     const float xa = x[3 * a], ya = x[3 * a + 1], za = x[3 * a + 2];
     for (int q = b.ptr[a] + lane; q < b.ptr[a + 1]; q += 32) {
         const int j = b.idx[q];
@@ -50,6 +50,7 @@ __device__ __forceinline__ void bond_force(const BondTable &b, const float *x, i
         const float g = b.k * dr / r;     // F_a = k (r - r0) d / r, d = x_j - x_a
         fx += g * dx; fy += g * dy; fz += g * dz;
         e += 0.25f * b.k * dr * dr;       // each bond is listed by both atoms
+        if (w) *w += 0.5f * g * r * r;    // pair-form virial, half per listed direction
     }
 }
 
@@ -169,6 +170,7 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
     const float rep2 = g.rep.rc * g.rep.rc;
     const int sa = g.species[a];
     float fx = 0.f, fy = 0.f, fz = 0.f, rx = 0.f, ry = 0.f, rz = 0.f;
+    float wv = 0.f, wr = 0.f;   // virial proxy: sum_j F_aj . d_aj, and the repulsion's half pair terms
     uint32_t phase = 0;
     bool alive = true;
 
@@ -195,6 +197,7 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
                 rep_pair(g.rep, sa, g.species[j], r, &dE);
                 const float c = dE * inv;              // F_a = E'(r) d / r
                 rx += c * dx; ry += c * dy; rz += c * dz;
+                wr += 0.5f * c * r2;
             }
             float du;
             fc = envelope(r * g.inv_rc, g.p, &du);
@@ -259,6 +262,7 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
             fx += pa * (nx + part[2]) - pj * (-nx + part[5]);
             fy += pa * (ny + part[3]) - pj * (-ny + part[6]);
             fz += pa * (nz + part[4]) - pj * (-nz + part[7]);
+            wv += pa * ((nx + part[2]) * dx + (ny + part[3]) * dy + (nz + part[4]) * dz);
         }
         __syncwarp();
     };
@@ -287,13 +291,16 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
     if (alive && queued > taken) batch(taken, queued - taken);
     if (!alive) return;
     fx = fmaf(g.scale, fx, rx); fy = fmaf(g.scale, fy, ry); fz = fmaf(g.scale, fz, rz);
+    float w = fmaf(g.scale, wv, wr);
     if (g.bonds.ptr) {
         float e = 0.f;
-        bond_force(g.bonds, g.x, a, bx, by, bz, ibx, iby, ibz, lane, fx, fy, fz, e);
+        bond_force(g.bonds, g.x, a, bx, by, bz, ibx, iby, ibz, lane, fx, fy, fz, e, &w);
     }
     fx = warp_sum(fx); fy = warp_sum(fy); fz = warp_sum(fz);
+    if (g.W) w = warp_sum(w);
     if (lane == 0) {
         g.F[3 * a] = fx; g.F[3 * a + 1] = fy; g.F[3 * a + 2] = fz;
+        if (g.W) g.W[a] = w;
     }
 }
 
@@ -316,6 +323,17 @@ void launch_nc_head(int K, int n_c, int n_l, const NCHeadArgs &a, cudaStream_t s
     else if (K == 8 && n_c == 8 && n_l == 1) nc_head_launch<8, 8, 1>(a, st);
     else if (K == 8 && n_c == 8 && n_l == 3) nc_head_launch<8, 8, 3>(a, st);
     else if (K == 8 && n_c == 8 && n_l == 4) nc_head_launch<8, 8, 4>(a, st);
+}
+
+__global__ void k_scale_d(double *v, int n, double f) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] *= f;
+}
+
+void launch_scale_d(double *v, int n, double f, cudaStream_t st) {
+    if (n == 0) return;
+    k_scale_d<<<(n + 255) / 256, 256, 0, st>>>(v, n, f);
+    count_launch();
 }
 
 // Mean subtraction over each replica in three short kernels. A replica is

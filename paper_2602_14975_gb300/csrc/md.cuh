@@ -35,11 +35,14 @@ struct NCHeadArgs {
     RepTable rep;
     const uint8_t *species;
     float *F;                      // [N][3] before mean subtraction
+    float *W;                      // nullable [N]: per-atom virial proxy (pair form)
     const int *order;              // nullable processing order
     int *err;                      // sticky device error word (read, and set on a timeout)
 };
 
 void launch_nc_head(int K, int n_c, int n_l, const NCHeadArgs &a, cudaStream_t st);
+// v[i] *= f, i < n.
+void launch_scale_d(double *v, int n, double f, cudaStream_t st);
 // F_out = F_in - (sum_{replica} F_in)/n_r, FP64 sums; net (nullable) [R][3].
 // scratch: device memory of mean_sub_scratch_bytes(n_atoms, n_rep) bytes.
 size_t mean_sub_scratch_bytes(int n_atoms, int n_rep);

@@ -195,6 +195,49 @@ def test_nc_open_boundary_batch(ctx1, models1):
         off += sy.n_atoms
 
 
+def _virial_tol(sy, ns, nb_, with_bonds=True):
+    # fp32 per-atom terms summed in fp64: 1e-5 of the sum of |F_i| times the
+    # list radius bounds the rounding of sum_i w_i
+    F, net = O.nc_forces(sy, ns, nb_, with_bonds=with_bonds)
+    return 1e-5 * np.abs(F + net / sy.n_atoms).sum() * (ns.rc + 0.5)
+
+
+def test_nc_virial_matches_oracle(ctx1, models1, water):
+    """Virial proxy of the fast force (Sec. 2, virial term in NPT), periodic
+    box and an open-boundary batch, with and without the analytic terms."""
+    _, (ns, nb_) = models1
+    d = core.DeviceSystem(water)
+    nb = core.nbr_build(ctx1, d, 4.0)
+    for with_bonds in (False, True):
+        _, _, W = core.forces_nc(ctx1, d, nb, with_bonds=with_bonds, with_virial=True)
+        _, _, Wo = O.nc_forces(water, ns, nb_, with_bonds=with_bonds, with_virial=True)
+        assert abs(W.item() - Wo) <= _virial_tol(water, ns, nb_, with_bonds), (W.item(), Wo)
+    systems = [S.capped_molecule_in_droplet(n, seed=80 + n) for n in (20, 45)]
+    d = core.DeviceSystem(systems)
+    nb = core.nbr_build(ctx1, d, 4.0)
+    _, _, W = core.forces_nc(ctx1, d, nb, with_virial=True)
+    for r, sy in enumerate(systems):
+        _, _, Wo = O.nc_forces(sy, ns, nb_, with_virial=True)
+        assert abs(W[r].item() - Wo) <= _virial_tol(sy, ns, nb_), (r, W[r].item(), Wo)
+
+
+def test_respa_virial_average_matches_oracle(ctx1, models1, water):
+    """The state's virial_nc after each outer step is the average over its
+    inner steps of the fast force's virial proxy."""
+    (cs, cb), (ns, nb_) = models1
+    m, v = _md_setup(water)
+    d = core.DeviceSystem(water)
+    st = core.MDState(d, v, m.astype(np.float32), seeds=151, virial=True)
+    core.respa_step(ctx1, st, core.integrator(4.0, 4, 300.0, [1.0] * 5, skin=0.5), 3)
+    ctx1.sync()
+    W = st.virial_nc.cpu().numpy()[0]
+    st.release()
+    ref = O.MDState(water, v, m.astype(np.float32).astype(np.float64))
+    wav = ct.c_double(0.0)
+    O.respa_run(ref, water, cs, cb, ns, nb_, 4.0, 4, 300.0, np.full(5, 1.0), 151, 3, virial_avg=wav)
+    assert abs(W - wav.value) <= _virial_tol(water, ns, nb_), (W, wav.value)
+
+
 # ------------------------------------------------------------------ Philox --
 
 def test_philox_words_bit_exact(ctx1):

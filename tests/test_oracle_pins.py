@@ -638,3 +638,51 @@ def test_ffl_free_particle_temperature():
     d = 3 * n
     assert abs(Ts.mean() - 300.0) < 5 * 300.0 * math.sqrt(2.0 / d) / math.sqrt(len(Ts)) * 2
     assert stats.kstest(Ts * d / 300.0, stats.chi2(d).cdf).pvalue > 1e-3
+
+
+# ------------------------------------------------------------ NPT virial --
+
+def test_nc_virial_pair_form_is_minus_sum_of_F_dot_q():
+    # Sec. 2 "Computation of the virial term in NPT": with symmetric
+    # neighbour lists and antisymmetric pair terms, -sum_i F_i . q_i equals
+    # sum_i sum_j (F_ij + F_pair,ij / 2) . r_ij; in an open droplet q_i are
+    # the plain coordinates, so both sides can be evaluated
+    sy = S.capped_molecule_in_droplet(30, seed=5)
+    ns = S.nc_spec(32, rc=3.5)
+    nb = S.nc_weights(ns, 7)
+    F, net, W = O.nc_forces(sy, ns, nb, with_virial=True)
+    F_pre = F + net / sy.n_atoms
+    direct = -(F_pre * sy.x).sum()
+    assert abs(W - direct) <= 1e-10 * abs(direct)
+    # and without the analytic fast terms
+    F0, net0, W0 = O.nc_forces(sy, ns, nb, with_bonds=False, with_virial=True)
+    assert abs(W0 + ((F0 + net0 / sy.n_atoms) * sy.x).sum()) <= 1e-10 * abs(W0)
+
+
+def test_prior_virial_is_the_scaling_derivative_of_the_energy():
+    # for any potential, d U(lambda q, lambda L) / d lambda at lambda = 1 is
+    # sum_i grad_i U . q_i = -sum_i F_i . q_i; central difference of the
+    # energy against the pair form, periodic (box scaled too) and open
+    for sy in (S.water_192(), S.capped_molecule_in_droplet(25, seed=3)):
+        for terms in (O.BONDS, O.LJ, O.REP, O.BONDS | O.LJ | O.REP):
+            W = O.prior_virial(sy, terms)
+            h = 1e-6
+            Ep, _ = O.prior(_scaled(sy, 1 + h), terms=terms)
+            Em, _ = O.prior(_scaled(sy, 1 - h), terms=terms)
+            fd = (Ep - Em) / (2 * h)
+            assert abs(fd - W) <= 1e-6 * max(1.0, abs(W)), (terms, fd, W)
+
+
+def _scaled(sy, lam):
+    return S.System(sy.name, sy.x * lam, sy.species, sy.mol_id, sy.bonds, sy.bond_r0, sy.box * lam)
+
+
+def test_nc_virial_is_translation_invariant_under_pbc():
+    sy = S.water_192()
+    ns = S.nc_spec(32, rc=3.5)
+    nb = S.nc_weights(ns, 7)
+    _, _, W = O.nc_forces(sy, ns, nb, with_virial=True)
+    shifted = S.System(sy.name, sy.x + np.array([3.7, -11.2, 5.05]), sy.species, sy.mol_id, sy.bonds,
+                       sy.bond_r0, sy.box)
+    _, _, W2 = O.nc_forces(shifted, ns, nb, with_virial=True)
+    assert abs(W2 - W) <= 1e-9 * abs(W)
