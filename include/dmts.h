@@ -214,10 +214,14 @@ dmts_status nbr_build_noalloc(const dmts_system *sys, dmts_nbr *nbr, long long *
  * only). nbr must hold a list with r_list >= model rc (and >= lj_rc with
  * DMTS_WITH_PRIOR), built for the current positions. The forces are the
  * hand-written adjoint of the energy with per-layer recomputation of all
- * edge quantities; only node features are stored.
+ * edge quantities; only node features are stored. virial: device double
+ * [n_replicas] (may be NULL; needs forces): -sum_i F_i . q_i in pair form,
+ * sum over directed edges of dU/dd_ij . d_ij plus the analytic pair terms
+ * (Sec. 2 "Computation of the virial term in NPT": the estimator at the
+ * end of an outer step).
  */
 dmts_status energy_forces_cons(dmts_ctx *ctx, const dmts_system *sys, const dmts_nbr *nbr,
-                               double *energy, float *forces, int flags, void *stream);
+                               double *energy, float *forces, double *virial, int flags, void *stream);
 
 /*
  * Non-conservative direct forces (Sec. 2 "Model architecture"; Algorithm 1,
@@ -279,6 +283,8 @@ typedef struct {
     double *virial_nc;         /* device double [n_replicas] (may be NULL): RESPA only, after each outer
                                   step the average over its n inner steps of the fast force's virial
                                   proxy (see forces_nc; Sec. 2 "Computation of the virial term in NPT") */
+    double *virial_cons;       /* device double [n_replicas] (may be NULL): virial of the full force
+                                  -grad U at the last evaluation (see energy_forces_cons) */
 } dmts_state;
 
 /*

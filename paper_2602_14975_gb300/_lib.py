@@ -69,7 +69,7 @@ class State(ct.Structure):
     _fields_ = [("sys", System), ("v", ct.c_void_p), ("f_nc", ct.c_void_p), ("f_cons", ct.c_void_p),
                 ("masses", ct.c_void_p), ("energy", ct.c_void_p), ("step", ct.c_void_p),
                 ("seed", ct.c_void_p), ("replica_id", ct.c_void_p), ("first_step", ct.c_int),
-                ("internal", ct.c_void_p), ("virial_nc", ct.c_void_p)]
+                ("internal", ct.c_void_p), ("virial_nc", ct.c_void_p), ("virial_cons", ct.c_void_p)]
 
 
 class Request(ct.Structure):
@@ -122,7 +122,7 @@ def _declare(L):
     L.nbr_build.restype = i
     L.nbr_build.argtypes = [vp, ct.POINTER(System), ct.POINTER(Nbr), ct.POINTER(ct.c_longlong), vp]
     L.energy_forces_cons.restype = i
-    L.energy_forces_cons.argtypes = [vp, ct.POINTER(System), ct.POINTER(Nbr), vp, vp, i, vp]
+    L.energy_forces_cons.argtypes = [vp, ct.POINTER(System), ct.POINTER(Nbr), vp, vp, vp, i, vp]
     L.forces_nc.restype = i
     L.forces_nc.argtypes = [vp, ct.POINTER(System), ct.POINTER(Nbr), vp, vp, vp, i, vp]
     L.respa_step.restype = i

@@ -171,16 +171,20 @@ def nbr_build(ctx: Context, dsys: DeviceSystem, r_list: float, capacity: int | N
         return nb
 
 
-def energy_forces_cons(ctx: Context, dsys: DeviceSystem, nbr: NbrList, with_prior=True, forces=True):
-    """Returns (energy f64 [n_replicas], forces f32 [N,3] or None)."""
+def energy_forces_cons(ctx: Context, dsys: DeviceSystem, nbr: NbrList, with_prior=True, forces=True,
+                       with_virial=False):
+    """Returns (energy f64 [n_replicas], forces f32 [N,3] or None), and with
+    with_virial the virial -sum_i F_i . q_i (pair form) f64 [n_replicas] as
+    a third value."""
     dev = dsys.x.device
     E = torch.empty(dsys.n_replicas, dtype=torch.float64, device=dev)
     F = torch.empty(dsys.n_atoms, 3, dtype=torch.float32, device=dev) if forces else None
+    W = torch.empty(dsys.n_replicas, dtype=torch.float64, device=dev) if with_virial else None
     s, nbs = dsys.struct(), nbr.struct()
-    st = ctx.lib.energy_forces_cons(ctx.handle, ct.byref(s), ct.byref(nbs), _ptr(E), _ptr(F),
+    st = ctx.lib.energy_forces_cons(ctx.handle, ct.byref(s), ct.byref(nbs), _ptr(E), _ptr(F), _ptr(W),
                                     L.WITH_PRIOR if with_prior else 0, _stream(dev))
     L.check(st, ctx.handle)
-    return E, F
+    return (E, F, W) if with_virial else (E, F)
 
 
 def forces_nc(ctx: Context, dsys: DeviceSystem, nbr: NbrList, with_bonds=True, with_virial=False):
@@ -225,11 +229,13 @@ class MDState:
         st0 = np.zeros(R, np.uint64) if steps is None else np.asarray(steps, np.uint64)
         self.step = torch.from_numpy(st0.view(np.int64)).to(dev)
         # with virial=True: average virial proxy of the fast force over the
-        # inner steps of the last outer step (RESPA), per replica
+        # inner steps of the last outer step (RESPA), and the virial of the
+        # full force at its last evaluation, per replica
         self.virial_nc = torch.zeros(R, dtype=torch.float64, device=dev) if virial else None
+        self.virial_cons = torch.zeros(R, dtype=torch.float64, device=dev) if virial else None
         self.c = L.State(dsys.struct(), _ptr(self.v), _ptr(self.f_nc), _ptr(self.f_cons), _ptr(self.masses),
                          _ptr(self.energy), _ptr(self.step), _ptr(self.seed), _ptr(self.replica_id), 1, None,
-                         _ptr(self.virial_nc))
+                         _ptr(self.virial_nc), _ptr(self.virial_cons))
         self.ctx = None
 
     def release(self):

@@ -225,7 +225,7 @@ static void contract(dmts_ctx *ctx, const DevModel &m, int M, int N, int K, cons
 
 // U_MP (+ prior) and F = -grad U for a batch.
 dmts_status cons_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const int *col, double *energy,
-                      float *forces, int flags, cudaStream_t st) {
+                      float *forces, int flags, cudaStream_t st, double *virial) {
     const DevModel &m = ctx->cons;
     const int N = s.n, C = m.C, L = m.L, NL = m.lmax + 1, NLM = NL * NL;
     Workspace &w = ctx->ws;
@@ -236,7 +236,7 @@ dmts_status cons_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const
         !w.act.ensure(sizeof(float) * nc_) || !w.u.ensure(sizeof(float) * nc_) || !w.gz.ensure(sizeof(float) * nc_) ||
         !w.gs0.ensure(sizeof(float) * nc_) || !w.gs1.ensure(sizeof(float) * nc_) ||
         !w.gA.ensure(sizeof(float) * nc_ * NLM) || !w.e_atom.ensure(sizeof(float) * (N + 1)) ||
-        !w.ftmp.ensure(sizeof(float) * 3 * (N + 1)))
+        !w.ftmp.ensure(sizeof(float) * 3 * (N + 1)) || (virial && !w.cons_w.ensure(sizeof(float) * (N + 1))))
         return fail(ctx, DMTS_E_OOM, "workspace allocation failed");
     if (bf && (!w.q_bf.ensure(2 * nc_ * NL + 16) || !w.act_bf.ensure(2 * nc_ + 16) || !w.s_bf.ensure(2 * nc_ + 16) ||
                !w.gz_bf.ensure(2 * nc_ + 16) || !w.gs0_bf.ensure(2 * nc_ + 16) || !w.gs1_bf.ensure(2 * nc_ + 16)))
@@ -314,6 +314,7 @@ dmts_status cons_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const
             io.gs_out_bf16 = t > 0 ? gout_bf : nullptr;
             io.F = forces;
             io.accumulate = t != L - 1;
+            io.W = virial ? (float *)w.cons_w.p : nullptr;
             io.err = ctx->d_err;
             { ProfScope ps(ctx, "mp_bwd", st); launch_mp_bwd(C, m.lmax, m.K, g, io, st); }
             std::swap(gin, gout);
@@ -339,11 +340,16 @@ dmts_status cons_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const
         pa.F = forces ? forces : (float *)w.ftmp.p;
         if (!forces) cudaMemsetAsync(w.ftmp.p, 0, sizeof(float) * 3 * N, st);
         pa.e_atom = e_atom;
+        pa.W = virial ? (float *)w.cons_w.p : nullptr;
         pa.order = s.order;
         pa.err = ctx->d_err;
         { ProfScope ps(ctx, "prior", st); launch_prior(pa, st); }
     }
     if (energy) { ProfScope ps(ctx, "replica_sum", st); launch_replica_sum(e_atom, s.rep_off, s.n_rep, energy, 0, st); }
+    if (virial) {
+        ProfScope ps(ctx, "replica_sum", st);
+        launch_replica_sum((const float *)w.cons_w.p, s.rep_off, s.n_rep, virial, 0, st);
+    }
     return DMTS_OK;
 }
 
@@ -808,11 +814,12 @@ dmts_status nbr_build(dmts_ctx *ctx, const dmts_system *sys, dmts_nbr *nbr, long
 }
 
 dmts_status energy_forces_cons(dmts_ctx *ctx, const dmts_system *sys, const dmts_nbr *nbr, double *energy,
-                               float *forces, int flags, void *stream) {
+                               float *forces, double *virial, int flags, void *stream) {
     dmts_status s = check_sys(ctx, sys);
     if (s != DMTS_OK) return s;
     if (!ctx->has_cons) return fail(ctx, DMTS_E_INVALID, "context has no conservative model");
     if (!nbr || !nbr->row_ptr || !nbr->col) return fail(ctx, DMTS_E_INVALID, "bad neighbour list");
+    if (virial && !forces) return fail(ctx, DMTS_E_INVALID, "the virial needs the forces");
     if (nbr->r_list < ctx->cons.rc || ((flags & DMTS_WITH_PRIOR) && nbr->r_list < ctx->prior.lj_rc))
         return fail(ctx, DMTS_E_INVALID, "neighbour list cutoff below the model cutoff");
     if ((flags & DMTS_WITH_PRIOR) && sys->n_atoms > 0 && (!sys->bond_ptr || !sys->bond_idx || !sys->bond_r0))
@@ -820,7 +827,7 @@ dmts_status energy_forces_cons(dmts_ctx *ctx, const dmts_system *sys, const dmts
     cudaSetDevice(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     SysView v = make_view(ctx, sys, st);
-    s = cons_eval(ctx, v, nbr->row_ptr, nbr->col, energy, forces, flags, st);
+    s = cons_eval(ctx, v, nbr->row_ptr, nbr->col, energy, forces, flags, st, virial);
     if (s != DMTS_OK) return s;
     return ck(ctx, cudaGetLastError(), "energy_forces_cons launch") ? DMTS_OK : DMTS_E_CUDA;
 }
@@ -899,7 +906,7 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
     const int *crow = (int *)si->cons_row.p, *ccol = (int *)si->cons_col.p;
     const int *nrow = (int *)si->nc_row.p, *ncol = (int *)si->nc_col.p;
     auto cons_full = [&]() {
-        return cons_eval(ctx, v, crow, ccol, stt->energy, stt->f_cons, DMTS_WITH_PRIOR, st);
+        return cons_eval(ctx, v, crow, ccol, stt->energy, stt->f_cons, DMTS_WITH_PRIOR, st, stt->virial_cons);
     };
     // fast force; inside the inner loop it also adds its virial proxy to the
     // per-replica average of the outer step (Sec. 2, virial term in NPT)

@@ -54,11 +54,12 @@ struct Workspace {
     Buf q_bf, act_bf, s_bf, gz_bf, gs0_bf, gs1_bf, nc_q_bf, nc_act_bf, nc_s_bf;
     Buf ms_scratch;   // per-part sums of the mean subtraction
     Buf nc_w;         // per-atom virial proxy of the fast force
+    Buf cons_w;       // per-atom virial of the conservative force
     void release_all() {
         Buf *all[] = {&s, &A, &q, &h, &act, &u, &gz, &gs0, &gs1, &gA, &e_atom, &ftmp, &atom_rep,
                       &nc_s, &nc_A, &nc_q, &nc_h, &nc_act, &nc_qk, &nc_v, &nc_f,
                       &q_bf, &act_bf, &s_bf, &gz_bf, &gs0_bf, &gs1_bf, &nc_q_bf, &nc_act_bf, &nc_s_bf,
-                      &ms_scratch, &nc_w};
+                      &ms_scratch, &nc_w, &cons_w};
         for (Buf *b : all) b->release();
     }
 };
@@ -137,7 +138,7 @@ namespace dmts {
 bool ck(dmts_ctx *ctx, cudaError_t e, const char *what);
 dmts_status fail(dmts_ctx *ctx, dmts_status s, const std::string &msg);
 dmts_status cons_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const int *col, double *energy,
-                      float *forces, int flags, cudaStream_t st);
+                      float *forces, int flags, cudaStream_t st, double *virial = nullptr);
 dmts_status nc_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const int *col, float *forces,
                     double *net, int flags, cudaStream_t st, double *virial = nullptr, int virial_accumulate = 0);
 dmts_status setup_grids(dmts_ctx *ctx, const std::vector<int> &rep_off, const std::vector<float> &box,

@@ -492,7 +492,7 @@ __global__ void __launch_bounds__(128) k_prior(PriorArgs g) {
     const float bx = g.box[3 * rep], by = g.box[3 * rep + 1], bz = g.box[3 * rep + 2];
     const float ibx = bx > 0.f ? 1.f / bx : 0.f, iby = by > 0.f ? 1.f / by : 0.f, ibz = bz > 0.f ? 1.f / bz : 0.f;
     const float xa = g.x[3 * a], ya = g.x[3 * a + 1], za = g.x[3 * a + 2];
-    float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
+    float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f, w = 0.f;
     const int sa = g.species[a], ma = g.mol_id[a];
     const float rc2 = g.lj_rc * g.lj_rc, inv_rc = 1.f / g.lj_rc, s2 = g.lj_sigma * g.lj_sigma;
     const float rep2 = g.rep.on ? g.rep.rc * g.rep.rc : 0.f;
@@ -519,6 +519,7 @@ __global__ void __launch_bounds__(128) k_prior(PriorArgs g) {
             const float c = dE / r;
             fx += c * dx; fy += c * dy; fz += c * dz;
             e += 0.5f * E;
+            w += 0.5f * c * r2;
         }
         if (sa == 0 || sj == 0 || g.mol_id[j] == ma || !(r2 < rc2)) return;
         const float r = sqrtf(r2);
@@ -531,13 +532,16 @@ __global__ void __launch_bounds__(128) k_prior(PriorArgs g) {
         const float c = dE / r;                             // F_a = E'(r) d / r
         fx += c * dx; fy += c * dy; fz += c * dz;
         e += 0.5f * elj * fc;
+        w += 0.5f * c * r2;
     };
     for_active_canonical(g.col, g.row_ptr[a], g.row_ptr[a + 1], sh_queue[warp], lane, active, edge);
-    if (g.bonds.ptr) bond_force(g.bonds, g.x, a, bx, by, bz, ibx, iby, ibz, lane, fx, fy, fz, e);
+    if (g.bonds.ptr) bond_force(g.bonds, g.x, a, bx, by, bz, ibx, iby, ibz, lane, fx, fy, fz, e, &w);
     fx = warp_sum(fx); fy = warp_sum(fy); fz = warp_sum(fz); e = warp_sum(e);
+    if (g.W) w = warp_sum(w);
     if (lane == 0) {
         g.F[3 * a] += fx; g.F[3 * a + 1] += fy; g.F[3 * a + 2] += fz;
         if (g.e_atom) g.e_atom[a] += e;
+        if (g.W) g.W[a] += w;
     }
 }
 

@@ -63,6 +63,7 @@ struct PriorArgs {
     RepTable rep;
     float *F;                      // accumulated
     float *e_atom;                 // accumulated per-atom energy (nullable)
+    float *W;                      // accumulated per-atom virial proxy, pair form (nullable)
     const int *order;              // nullable processing order
     const int *err;
 };

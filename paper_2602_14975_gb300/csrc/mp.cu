@@ -149,10 +149,10 @@ __global__ void __launch_bounds__(MP_WARPS * 32) k_mp_fwd(EdgeGeom g, LayerIO io
 // and the feature gradient of the sender role is
 //   g_s_a[c] += nu sum_j sum_l (-1)^l R_lc sum_m gA_j[lm][c] Y_lm.
 // (Edge j->a has d_ja = -d_aj, Y_lm(-n) = (-1)^l Y_lm(n).)
-template <int C, int LMAX, int K>
+template <int C, int LMAX, int K, bool VIR>
 __global__ void __launch_bounds__(MP_WARPS * 32) k_mp_bwd(EdgeGeom g, LayerIO io) {
     constexpr int NL = LMAX + 1, NLM = NL * NL, CPW = C / 32;
-    constexpr int STRIDE = 2 * K + NLM + 3 * NLM + 3;   // b, db, Y, dY, n
+    constexpr int STRIDE = 2 * K + NLM + 3 * NLM + 3 + (VIR ? 1 : 0);   // b, db, Y, dY, n (, r)
     __shared__ float sh_e[MP_WARPS][32][STRIDE];
     __shared__ int sh_j[MP_WARPS][32];
     __shared__ float sh_ga[MP_WARPS][NLM][C];   // element (lm, lane*CPW+u) at [lm][u*32+lane]
@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(MP_WARPS * 32) k_mp_bwd(EdgeGeom g, LayerIO io
     ldv<CPW>(io.s + (size_t)a * C + lane * CPW, sa);
 #pragma unroll
     for (int u = 0; u < CPW; ++u) gsacc[u] = 0.f;
-    float fx = 0.f, fy = 0.f, fz = 0.f;
+    float fx = 0.f, fy = 0.f, fz = 0.f, wv = 0.f;
 
     const int rep = g.atom_rep[a];
     const float bx = g.box[3 * rep], by = g.box[3 * rep + 1], bz = g.box[3 * rep + 2];
@@ -225,6 +225,7 @@ __global__ void __launch_bounds__(MP_WARPS * 32) k_mp_bwd(EdgeGeom g, LayerIO io
             se[2 * K + 4 * NLM] = nx;
             se[2 * K + 4 * NLM + 1] = ny;
             se[2 * K + 4 * NLM + 2] = nz;
+            if (VIR) se[2 * K + 4 * NLM + 3] = r;
             sh_j[warp][pos] = j;
         }
         __syncwarp();
@@ -282,16 +283,23 @@ __global__ void __launch_bounds__(MP_WARPS * 32) k_mp_bwd(EdgeGeom g, LayerIO io
                 ez = fmaf(beta[lm], dY[3 * lm + 2], ez);
             }
             fx += ex; fy += ey; fz += ez;
+            // virial proxy: each directed edge's dU/dd . d is counted from both
+            // ends of the pair, hence the half
+            if (VIR) wv = fmaf(0.5f * se[2 * K + 4 * NLM + 3],
+                               ex * se[2 * K + 4 * NLM] + ey * se[2 * K + 4 * NLM + 1] + ez * se[2 * K + 4 * NLM + 2], wv);
         }
         __syncwarp();
     }
     fx = warp_sum(fx); fy = warp_sum(fy); fz = warp_sum(fz);
+    if (VIR) wv = warp_sum(wv);
     if (lane == 0) {
         const float nu = io.nu;
         if (io.accumulate) {
             io.F[3 * a] += nu * fx; io.F[3 * a + 1] += nu * fy; io.F[3 * a + 2] += nu * fz;
+            if (VIR) io.W[a] += nu * wv;
         } else {
             io.F[3 * a] = nu * fx; io.F[3 * a + 1] = nu * fy; io.F[3 * a + 2] = nu * fz;
+            if (VIR) io.W[a] = nu * wv;
         }
     }
     float gin[CPW], gout[CPW];
@@ -320,10 +328,15 @@ static void fwd_c(const EdgeGeom &g, const LayerIO &io, cudaStream_t st) {
     count_launch();
 }
 
+// The virial variant (io.W set) is a separate instantiation, so that the
+// force-only adjoint carries no extra register or instruction.
 template <int C, int LMAX>
 static void bwd_c(const EdgeGeom &g, const LayerIO &io, cudaStream_t st) {
     const int blocks = (g.n_atoms + MP_WARPS - 1) / MP_WARPS;
-    k_mp_bwd<C, LMAX, 8><<<blocks, MP_WARPS * 32, 0, st>>>(g, io);
+    if (io.W)
+        k_mp_bwd<C, LMAX, 8, true><<<blocks, MP_WARPS * 32, 0, st>>>(g, io);
+    else
+        k_mp_bwd<C, LMAX, 8, false><<<blocks, MP_WARPS * 32, 0, st>>>(g, io);
     count_launch();
 }
 

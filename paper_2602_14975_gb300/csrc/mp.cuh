@@ -34,7 +34,8 @@ struct LayerIO {
     float *gs_out;           // [N][C]       (backward out)
     __nv_bfloat16 *gs_out_bf16;  // optional bf16 copy of gs_out
     float *F;                // [N][3]       (backward: accumulated forces)
-    int accumulate;          // backward: 0 write F, 1 add to F
+    int accumulate;          // backward: 0 write F, 1 add to F (and W)
+    float *W;                // [N] (backward, nullable): per-atom virial proxy, pair form
     const int *err;
 };
 

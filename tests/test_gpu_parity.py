@@ -238,6 +238,54 @@ def test_respa_virial_average_matches_oracle(ctx1, models1, water):
     assert abs(W - wav.value) <= _virial_tol(water, ns, nb_), (W, wav.value)
 
 
+def _cons_virial_scale(F, rlist):
+    return 1e-5 * np.abs(F).sum() * rlist
+
+
+def test_cons_virial_matches_oracle(ctx1, models1, water):
+    """Virial of the full force -grad(U_MP + prior) in pair form (Sec. 2,
+    virial term in NPT). Open droplets: equal to -sum_i F_i . q_i of the
+    oracle's forces. Periodic water: equal to the oracle's dU(lambda q,
+    lambda L)/dlambda by central differences."""
+    (cs, cb), _ = models1
+    systems = [S.capped_molecule_in_droplet(n, seed=90 + n) for n in (25, 40)]
+    d = core.DeviceSystem(systems)
+    nb = core.nbr_build(ctx1, d, 5.5)
+    _, F, W = core.energy_forces_cons(ctx1, d, nb, with_prior=True, with_virial=True)
+    for r, sy in enumerate(systems):
+        _, Fo = O.cons_energy_forces(sy, cs, cb)
+        _, Fp = O.prior(sy)
+        Ft = Fo + Fp
+        ref = -(Ft * sy.x).sum()
+        assert abs(W[r].item() - ref) <= _cons_virial_scale(Ft, 5.5), (r, W[r].item(), ref)
+    d = core.DeviceSystem(water)
+    nb = core.nbr_build(ctx1, d, 5.5)
+    _, F, W = core.energy_forces_cons(ctx1, d, nb, with_prior=True, with_virial=True)
+
+    def energy(lam):
+        sy = S.System(water.name, water.x * lam, water.species, water.mol_id, water.bonds, water.bond_r0,
+                      water.box * lam)
+        return O.cons_energy(sy, cs, cb) + O.prior(sy)[0]
+
+    h = 1e-6
+    fd = (energy(1 + h) - energy(1 - h)) / (2 * h)
+    Ft = O.cons_energy_forces(water, cs, cb)[1] + O.prior(water)[1]
+    assert abs(W.item() - fd) <= _cons_virial_scale(Ft, 5.5), (W.item(), fd)
+
+
+def test_respa_keeps_the_last_full_force_virial(ctx1, water):
+    m, v = _md_setup(water)
+    d = core.DeviceSystem(water)
+    st = core.MDState(d, v, m.astype(np.float32), seeds=161, virial=True)
+    core.respa_step(ctx1, st, core.integrator(4.0, 4, 300.0, [1.0] * 5, skin=0.5), 2)
+    ctx1.sync()
+    Wst = st.virial_cons.cpu().numpy()[0]
+    st.release()
+    nb = core.nbr_build(ctx1, d, 5.5)
+    _, _, W = core.energy_forces_cons(ctx1, d, nb, with_prior=True, with_virial=True)
+    assert abs(W.item() - Wst) <= 1e-9 * abs(Wst)
+
+
 # ------------------------------------------------------------------ Philox --
 
 def test_philox_words_bit_exact(ctx1):
