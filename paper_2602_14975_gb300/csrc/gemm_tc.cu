@@ -2,14 +2,15 @@
 // Out[M][N] = Act[M][K] x W^T with bf16 operands and an fp32 accumulator in
 // tensor memory, followed by the same fused epilogues as the fp32 GEMM.
 //
-// One CTA (eight warps) computes a 128 x BN tile (BN <= 256 output columns).
-// Warp 0 (one lane) streams K-chunks of 64 bf16 of the activation tile and of
-// the weight tile into shared memory with TMA (128-byte swizzle), warp 1 (one
-// lane) issues tcgen05.mma (M = 128, N = BN, K = 16 per instruction) into a
-// TMEM accumulator, warp 2 owns the TMEM allocation; warps 0-3 read the
-// accumulator back with tcgen05.ld (warp w reads rows 32w..32w+31) into shared
-// memory and all eight warps apply the epilogue with coalesced accesses. Every wait on an mbarrier is bounded: on timeout the CTA
-// records DMTS_E_TIMEOUT, frees its tensor memory and returns.
+// One CTA (eight warps) computes a 128 x BN tile (BN a multiple of 16 that
+// divides N, near 64). Warp 0 (one lane) streams K-chunks of 64 bf16 of the
+// activation tile and of the weight tile into shared memory with TMA
+// (128-byte swizzle), warp 1 (one lane) issues tcgen05.mma (M = 128, N = BN,
+// K = 16 per instruction) into a TMEM accumulator, warp 2 owns the TMEM
+// allocation; warps 0-3 read the accumulator back with tcgen05.ld (warp w
+// reads rows 32w..32w+31) into shared memory and all eight warps apply the
+// epilogue with coalesced accesses. Every wait on an mbarrier is bounded: on
+// timeout the CTA records DMTS_E_TIMEOUT, frees its tensor memory and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 

@@ -1,4 +1,5 @@
-// Cell-list neighbour build and sub-list extraction.
+// Cell-list neighbour build: a full list and, in the same pass, the sub-list
+// of its entries within a shorter cutoff.
 #pragma once
 #include "common.cuh"
 
