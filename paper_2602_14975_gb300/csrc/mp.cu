@@ -3,11 +3,68 @@
 // and feature gradients) written as an atomic-free gather over the symmetric
 // neighbour list. Node-level MLP contractions: SIMT fp32 GEMM with fused
 // epilogues.
+#include <type_traits>
+
 #include "mp.cuh"
 
 namespace dmts {
 
 constexpr int MP_WARPS = 4;
+
+// ------------------------------------------------------------ channel packs
+// A lane owns CPW consecutive channels. With CPW even they are processed as
+// pairs in packed fp32 arithmetic (fma.rn.f32x2 / mul.rn.f32x2 of sm_100 and
+// later: one instruction issues two channels, each element rounded exactly as
+// fmaf / a plain product), with CPW = 1 as scalars. Quantities that multiply
+// every channel alike (radial basis, harmonics) are stored in shared memory
+// already duplicated into both halves of a pair.
+template <int CPW>
+struct Pack {
+    static constexpr int W = CPW % 2 == 0 ? 2 : 1;   // channels per pack
+    static constexpr int NP = CPW / W;               // packs per lane
+    using T = typename std::conditional<W == 2, float2, float>::type;
+};
+
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float vmul(float a, float b) { return a * b; }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float vadd(float a, float b) { return a + b; }
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float vsub(float a, float b) { return a - b; }
+__device__ __forceinline__ float2 vneg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float vneg(float a) { return -a; }
+__device__ __forceinline__ float vsum(float2 v) { return v.x + v.y; }
+__device__ __forceinline__ float vsum(float v) { return v; }
+__device__ __forceinline__ float vget(float2 v, int h) { return h ? v.y : v.x; }
+__device__ __forceinline__ float vget(float v, int) { return v; }
+template <class T>
+__device__ __forceinline__ T vdup(float v) {
+    if constexpr (std::is_same<T, float2>::value) return make_float2(v, v);
+    else return v;
+}
+
+// CPW consecutive floats at p (aligned to 4 * CPW bytes) as packs, and back.
+template <int CPW, class T>
+__device__ __forceinline__ void ldp(const float *p, T *v) {
+    if constexpr (CPW == 4) {
+        const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+        v[0] = make_float2(t.x, t.y);
+        v[1] = make_float2(t.z, t.w);
+    } else if constexpr (CPW == 2) {
+        v[0] = __ldg(reinterpret_cast<const float2 *>(p));
+    } else {
+        v[0] = __ldg(p);
+    }
+}
+
+template <int CPW, class T>
+__device__ __forceinline__ void stp(float *p, const T *v) {
+    if constexpr (CPW == 4) *reinterpret_cast<float4 *>(p) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+    else if constexpr (CPW == 2) *reinterpret_cast<float2 *>(p) = v[0];
+    else *p = v[0];
+}
 
 // ------------------------------------------------------------------ forward
 // Warp per receiver i, lane owns CPW consecutive channels c = lane*CPW + u.
@@ -18,25 +75,27 @@ constexpr int MP_WARPS = 4;
 template <int C, int LMAX, int K, int SPLIT>
 __global__ void __launch_bounds__(MP_WARPS * 32) k_mp_fwd(EdgeGeom g, LayerIO io) {
     constexpr int NL = LMAX + 1, NLM = NL * NL, CW = C / SPLIT, CPW = CW / 32;
+    using T = typename Pack<CPW>::T;
+    constexpr int NP = Pack<CPW>::NP, PW = Pack<CPW>::W;
+    constexpr int RS = (K + NLM) | 1;   // odd record stride: conflict-free writes
     const int co = blockIdx.y * CW;
-    __shared__ float sh_b[MP_WARPS][32][K];
-    __shared__ float sh_y[MP_WARPS][32][NLM];
+    __shared__ T sh_r[MP_WARPS][32][RS];
     __shared__ int sh_j[MP_WARPS][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wi = blockIdx.x * MP_WARPS + warp;
     if (wi >= g.n_atoms || *io.err) return;
     const int i = g.order ? __ldg(g.order + wi) : wi;   // spatially sorted: neighbours shared in cache
 
-    float W[NL][K][CPW];
+    T W[NL][K][NP];
 #pragma unroll
     for (int l = 0; l < NL; ++l)
 #pragma unroll
-        for (int k = 0; k < K; ++k) ldv<CPW>(io.wrad + (l * K + k) * C + co + lane * CPW, W[l][k]);
-    float acc[NLM][CPW];
+        for (int k = 0; k < K; ++k) ldp<CPW>(io.wrad + (l * K + k) * C + co + lane * CPW, W[l][k]);
+    T acc[NLM][NP];
 #pragma unroll
     for (int lm = 0; lm < NLM; ++lm)
 #pragma unroll
-        for (int u = 0; u < CPW; ++u) acc[lm][u] = 0.f;
+        for (int p = 0; p < NP; ++p) acc[lm][p] = vdup<T>(0.f);
 
     const int rep = g.atom_rep[i];
     const float bx = g.box[3 * rep], by = g.box[3 * rep + 1], bz = g.box[3 * rep + 2];
@@ -60,17 +119,18 @@ __global__ void __launch_bounds__(MP_WARPS * 32) k_mp_fwd(EdgeGeom g, LayerIO io
         const unsigned m = __ballot_sync(DMTS_FULL, act);
         if (act) {
             const int pos = __popc(m & ((1u << lane) - 1u));
+            T *rec = sh_r[warp][pos];
             const float r = sqrtf(r2), inv = 1.f / r;
             float du;
             const float fc = envelope(r * g.inv_rc, g.p, &du);
             float B[K];
             bessel<K, false>(r, g.inv_rc, g.bnorm, B, nullptr);
 #pragma unroll
-            for (int k = 0; k < K; ++k) sh_b[warp][pos][k] = fc * B[k];
+            for (int k = 0; k < K; ++k) rec[k] = vdup<T>(fc * B[k]);
             float Y[NLM];
             sph<LMAX>(dx * inv, dy * inv, dz * inv, Y);
 #pragma unroll
-            for (int lm = 0; lm < NLM; ++lm) sh_y[warp][pos][lm] = Y[lm];
+            for (int lm = 0; lm < NLM; ++lm) rec[K + lm] = vdup<T>(Y[lm]);
             sh_j[warp][pos] = j;
         }
         __syncwarp();
@@ -78,53 +138,62 @@ __global__ void __launch_bounds__(MP_WARPS * 32) k_mp_fwd(EdgeGeom g, LayerIO io
 #pragma unroll 2
         for (int t = 0; t < na; ++t) {
             const int jt = sh_j[warp][t];
-            float sj[CPW];
-            ldv<CPW>(io.s + (size_t)jt * C + co + lane * CPW, sj);
-            float b[K], y[NLM];
+            const T *rec = sh_r[warp][t];
+            T sj[NP];
+            ldp<CPW>(io.s + (size_t)jt * C + co + lane * CPW, sj);
+            T b[K], y[NLM];
 #pragma unroll
-            for (int k = 0; k < K; ++k) b[k] = sh_b[warp][t][k];
+            for (int k = 0; k < K; ++k) b[k] = rec[k];
 #pragma unroll
-            for (int lm = 0; lm < NLM; ++lm) y[lm] = sh_y[warp][t][lm];
+            for (int lm = 0; lm < NLM; ++lm) y[lm] = rec[K + lm];
 #pragma unroll
-            for (int u = 0; u < CPW; ++u)
+            for (int p = 0; p < NP; ++p)
 #pragma unroll
                 for (int l = 0; l < NL; ++l) {
-                    float R = 0.f;
+                    T Ra = vdup<T>(0.f), Rb = vdup<T>(0.f);
 #pragma unroll
-                    for (int k = 0; k < K; ++k) R = fmaf(W[l][k][u], b[k], R);
-                    const float msg = R * sj[u];
+                    for (int k = 0; k < K; k += 2) {
+                        Ra = vfma(W[l][k][p], b[k], Ra);
+                        Rb = vfma(W[l][k + 1][p], b[k + 1], Rb);
+                    }
+                    const T R = vadd(Ra, Rb);
+                    const T msg = vmul(R, sj[p]);
 #pragma unroll
-                    for (int lm = l * l; lm < (l + 1) * (l + 1); ++lm) acc[lm][u] = fmaf(msg, y[lm], acc[lm][u]);
+                    for (int lm = l * l; lm < (l + 1) * (l + 1); ++lm) acc[lm][p] = vfma(msg, y[lm], acc[lm][p]);
                 }
         }
         __syncwarp();
     }
-    float qv[NL][CPW];
+    const T nu = vdup<T>(io.nu);
+    T qv[NL][NP];
 #pragma unroll
     for (int l = 0; l < NL; ++l)
 #pragma unroll
-        for (int u = 0; u < CPW; ++u) qv[l][u] = 0.f;
+        for (int p = 0; p < NP; ++p) qv[l][p] = vdup<T>(0.f);
 #pragma unroll
     for (int lm = 0; lm < NLM; ++lm) {
         const int l = lm == 0 ? 0 : (lm < 4 ? 1 : 2);
-        float a[CPW];
+        T a[NP];
 #pragma unroll
-        for (int u = 0; u < CPW; ++u) {
-            a[u] = io.nu * acc[lm][u];
-            qv[l][u] = fmaf(a[u], a[u], qv[l][u]);
+        for (int p = 0; p < NP; ++p) {
+            a[p] = vmul(nu, acc[lm][p]);
+            qv[l][p] = vfma(a[p], a[p], qv[l][p]);
         }
-        stv<CPW>(io.A + ((size_t)i * NLM + lm) * C + co + lane * CPW, a);
+        stp<CPW>(io.A + ((size_t)i * NLM + lm) * C + co + lane * CPW, a);
     }
     if (LMAX >= 1 && io.V) {
         // vector part of the tensor heads, V_h = sum_c U[h][c] A[l=1][c]
         for (int h = 0; h < io.n_l; ++h) {
-            float u4[CPW];
-            ldv<CPW>(io.U + (size_t)h * C + co + lane * CPW, u4);
+            T u4[NP];
+            ldp<CPW>(io.U + (size_t)h * C + co + lane * CPW, u4);
 #pragma unroll
             for (int cmp = 0; cmp < 3; ++cmp) {
                 float part = 0.f;
 #pragma unroll
-                for (int u = 0; u < CPW; ++u) part = fmaf(u4[u], io.nu * acc[1 + cmp][u], part);
+                for (int p = 0; p < NP; ++p)
+#pragma unroll
+                    for (int hh = 0; hh < PW; ++hh)
+                        part = fmaf(vget(u4[p], hh), io.nu * vget(acc[1 + cmp][p], hh), part);
                 part = warp_sum(part);
                 if (lane == 0) io.V[((size_t)i * io.n_l + h) * 3 + cmp] = part;
             }
@@ -132,11 +201,14 @@ __global__ void __launch_bounds__(MP_WARPS * 32) k_mp_fwd(EdgeGeom g, LayerIO io
     }
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
-        stv<CPW>(io.q + (size_t)i * NL * C + l * C + co + lane * CPW, qv[l]);
+        stp<CPW>(io.q + (size_t)i * NL * C + l * C + co + lane * CPW, qv[l]);
         if (io.q_bf16) {
 #pragma unroll
-            for (int u = 0; u < CPW; ++u)
-                io.q_bf16[(size_t)i * NL * C + l * C + co + lane * CPW + u] = __float2bfloat16_rn(qv[l][u]);
+            for (int p = 0; p < NP; ++p)
+#pragma unroll
+                for (int hh = 0; hh < PW; ++hh)
+                    io.q_bf16[(size_t)i * NL * C + l * C + co + lane * CPW + p * PW + hh] =
+                        __float2bfloat16_rn(vget(qv[l][p], hh));
         }
     }
 }
@@ -149,34 +221,60 @@ __global__ void __launch_bounds__(MP_WARPS * 32) k_mp_fwd(EdgeGeom g, LayerIO io
 // and the feature gradient of the sender role is
 //   g_s_a[c] += nu sum_j sum_l (-1)^l R_lc sum_m gA_j[lm][c] Y_lm.
 // (Edge j->a has d_ja = -d_aj, Y_lm(-n) = (-1)^l Y_lm(n).)
+//
+// Shared memory per block (dynamic: above the 48 KB static limit at C = 128,
+// l_max = 2): per warp 32 edge records of packs (f_c B_k, its r-derivative,
+// Y_lm) and of scalars (dY_lm/dd, n, and r for the virial), the receiver's
+// gA_a as packs, and the 32 neighbour indices.
+template <int C, int LMAX, int K, bool VIR>
+struct BwdSmem {
+    static constexpr int NL = LMAX + 1, NLM = NL * NL, CPW = C / 32;
+    using T = typename Pack<CPW>::T;
+    static constexpr int NP = Pack<CPW>::NP;
+    static constexpr int RS = (2 * K + NLM) | 1;
+    static constexpr int GS = (3 * NLM + 3 + (VIR ? 1 : 0)) | 1;
+    static constexpr size_t r_bytes = sizeof(T) * MP_WARPS * 32 * RS;
+    static constexpr size_t ga_bytes = sizeof(T) * MP_WARPS * NLM * NP * 32;
+    static constexpr size_t g_bytes = sizeof(float) * MP_WARPS * 32 * GS;
+    static constexpr size_t bytes = r_bytes + ga_bytes + g_bytes + sizeof(int) * MP_WARPS * 32;
+};
+
 template <int C, int LMAX, int K, bool VIR>
 __global__ void __launch_bounds__(MP_WARPS * 32) k_mp_bwd(EdgeGeom g, LayerIO io) {
-    constexpr int NL = LMAX + 1, NLM = NL * NL, CPW = C / 32;
-    constexpr int STRIDE = 2 * K + NLM + 3 * NLM + 3 + (VIR ? 1 : 0);   // b, db, Y, dY, n (, r)
-    __shared__ float sh_e[MP_WARPS][32][STRIDE];
-    __shared__ int sh_j[MP_WARPS][32];
-    __shared__ float sh_ga[MP_WARPS][NLM][C];   // element (lm, lane*CPW+u) at [lm][u*32+lane]
+    using S = BwdSmem<C, LMAX, K, VIR>;
+    using T = typename S::T;
+    constexpr int NL = S::NL, NLM = S::NLM, CPW = S::CPW, NP = S::NP, PW = Pack<CPW>::W;
+    constexpr int RS = S::RS, GS = S::GS;
+    extern __shared__ __align__(16) unsigned char mp_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T (*sh_r)[RS] = reinterpret_cast<T (*)[RS]>(mp_smem) + warp * 32;
+    T (*sh_ga)[NP * 32] = reinterpret_cast<T (*)[NP * 32]>(mp_smem + S::r_bytes) + warp * NLM;
+    float (*sh_g)[GS] = reinterpret_cast<float (*)[GS]>(mp_smem + S::r_bytes + S::ga_bytes) + warp * 32;
+    int *sh_j = reinterpret_cast<int *>(mp_smem + S::r_bytes + S::ga_bytes + S::g_bytes) + warp * 32;
     const int wa = blockIdx.x * MP_WARPS + warp;
     if (wa >= g.n_atoms || *io.err) return;
     const int a = g.order ? __ldg(g.order + wa) : wa;
 
-    float W[NL][K][CPW];
+    T W[NL][K][NP];
 #pragma unroll
     for (int l = 0; l < NL; ++l)
 #pragma unroll
-        for (int k = 0; k < K; ++k) ldv<CPW>(io.wrad + (l * K + k) * C + lane * CPW, W[l][k]);
+        for (int k = 0; k < K; ++k) ldp<CPW>(io.wrad + (l * K + k) * C + lane * CPW, W[l][k]);
 #pragma unroll
     for (int lm = 0; lm < NLM; ++lm) {
-        float t[CPW];
-        ldv<CPW>(io.gA + ((size_t)a * NLM + lm) * C + lane * CPW, t);
+        T t[NP];
+        ldp<CPW>(io.gA + ((size_t)a * NLM + lm) * C + lane * CPW, t);
 #pragma unroll
-        for (int u = 0; u < CPW; ++u) sh_ga[warp][lm][u * 32 + lane] = t[u];
+        for (int p = 0; p < NP; ++p) sh_ga[lm][p * 32 + lane] = t[p];
     }
-    float sa[CPW], gsacc[CPW];
-    ldv<CPW>(io.s + (size_t)a * C + lane * CPW, sa);
+    T sa[NP], san[NP], gse[NP], gso[NP];   // s_a, -s_a; sender-role sums over even and odd l
+    ldp<CPW>(io.s + (size_t)a * C + lane * CPW, sa);
 #pragma unroll
-    for (int u = 0; u < CPW; ++u) gsacc[u] = 0.f;
+    for (int p = 0; p < NP; ++p) {
+        san[p] = vneg(sa[p]);
+        gse[p] = vdup<T>(0.f);
+        gso[p] = vdup<T>(0.f);
+    }
     float fx = 0.f, fy = 0.f, fz = 0.f, wv = 0.f;
 
     const int rep = g.atom_rep[a];
@@ -202,7 +300,8 @@ __global__ void __launch_bounds__(MP_WARPS * 32) k_mp_bwd(EdgeGeom g, LayerIO io
         const unsigned m = __ballot_sync(DMTS_FULL, act);
         if (act) {
             const int pos = __popc(m & ((1u << lane) - 1u));
-            float *se = sh_e[warp][pos];
+            T *rec = sh_r[pos];
+            float *ge = sh_g[pos];
             const float r = sqrtf(r2), inv = 1.f / r;
             float du;
             const float fc = envelope(r * g.inv_rc, g.p, &du);
@@ -211,82 +310,86 @@ __global__ void __launch_bounds__(MP_WARPS * 32) k_mp_bwd(EdgeGeom g, LayerIO io
             bessel<K, true>(r, g.inv_rc, g.bnorm, B, dB);
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-                se[k] = fc * B[k];
-                se[K + k] = dfc * B[k] + fc * dB[k];
+                rec[k] = vdup<T>(fc * B[k]);
+                rec[K + k] = vdup<T>(dfc * B[k] + fc * dB[k]);
             }
             const float nx = dx * inv, ny = dy * inv, nz = dz * inv;
             float Y[NLM], dY[3 * NLM];
             sph<LMAX>(nx, ny, nz, Y);
             sph_grad<LMAX>(nx, ny, nz, inv, dY);
 #pragma unroll
-            for (int lm = 0; lm < NLM; ++lm) se[2 * K + lm] = Y[lm];
+            for (int lm = 0; lm < NLM; ++lm) rec[2 * K + lm] = vdup<T>(Y[lm]);
 #pragma unroll
-            for (int q = 0; q < 3 * NLM; ++q) se[2 * K + NLM + q] = dY[q];
-            se[2 * K + 4 * NLM] = nx;
-            se[2 * K + 4 * NLM + 1] = ny;
-            se[2 * K + 4 * NLM + 2] = nz;
-            if (VIR) se[2 * K + 4 * NLM + 3] = r;
-            sh_j[warp][pos] = j;
+            for (int q = 0; q < 3 * NLM; ++q) ge[q] = dY[q];
+            ge[3 * NLM] = nx;
+            ge[3 * NLM + 1] = ny;
+            ge[3 * NLM + 2] = nz;
+            if (VIR) ge[3 * NLM + 3] = r;
+            sh_j[pos] = j;
         }
         __syncwarp();
         const int na = __popc(m);
+#pragma unroll 2
         for (int t = 0; t < na; ++t) {
-            const int jt = sh_j[warp][t];
-            const float *se = sh_e[warp][t];
-            float sj[CPW];
-            ldv<CPW>(io.s + (size_t)jt * C + lane * CPW, sj);
-            float gj[NLM][CPW];
+            const int jt = sh_j[t];
+            const T *rec = sh_r[t];
+            const float *ge = sh_g[t];
+            T sj[NP];
+            ldp<CPW>(io.s + (size_t)jt * C + lane * CPW, sj);
+            T gj[NLM][NP];
 #pragma unroll
-            for (int lm = 0; lm < NLM; ++lm) ldv<CPW>(io.gA + ((size_t)jt * NLM + lm) * C + lane * CPW, gj[lm]);
-            float y[NLM];
+            for (int lm = 0; lm < NLM; ++lm) ldp<CPW>(io.gA + ((size_t)jt * NLM + lm) * C + lane * CPW, gj[lm]);
+            T y[NLM];
 #pragma unroll
-            for (int lm = 0; lm < NLM; ++lm) y[lm] = se[2 * K + lm];
-            float rho = 0.f, beta[NLM];
+            for (int lm = 0; lm < NLM; ++lm) y[lm] = rec[2 * K + lm];
+            T rho = vdup<T>(0.f), beta[NLM];
 #pragma unroll
-            for (int lm = 0; lm < NLM; ++lm) beta[lm] = 0.f;
+            for (int lm = 0; lm < NLM; ++lm) beta[lm] = vdup<T>(0.f);
 #pragma unroll
-            for (int u = 0; u < CPW; ++u) {
-                float R[NL], Rp[NL];
+            for (int p = 0; p < NP; ++p) {
+                T R[NL], Rp[NL];
 #pragma unroll
                 for (int l = 0; l < NL; ++l) {
-                    float s0 = 0.f, s1 = 0.f;
+                    T s0 = vdup<T>(0.f), s1 = vdup<T>(0.f), s2 = vdup<T>(0.f), s3 = vdup<T>(0.f);
 #pragma unroll
-                    for (int k = 0; k < K; ++k) {
-                        s0 = fmaf(W[l][k][u], se[k], s0);
-                        s1 = fmaf(W[l][k][u], se[K + k], s1);
+                    for (int k = 0; k < K; k += 2) {
+                        s0 = vfma(W[l][k][p], rec[k], s0);
+                        s1 = vfma(W[l][k][p], rec[K + k], s1);
+                        s2 = vfma(W[l][k + 1][p], rec[k + 1], s2);
+                        s3 = vfma(W[l][k + 1][p], rec[K + k + 1], s3);
                     }
-                    R[l] = s0;
-                    Rp[l] = s1;
+                    R[l] = vadd(s0, s2);
+                    Rp[l] = vadd(s1, s3);
                 }
 #pragma unroll
                 for (int l = 0; l < NL; ++l) {
-                    const float sgn = (l & 1) ? -1.f : 1.f;
-                    float tl = 0.f, wl = 0.f;
+                    const T sas = (l & 1) ? san[p] : sa[p];
+                    T tl = vdup<T>(0.f), wl = vdup<T>(0.f);
 #pragma unroll
                     for (int lm = l * l; lm < (l + 1) * (l + 1); ++lm) {
-                        const float gal = sh_ga[warp][lm][u * 32 + lane];
-                        const float gam = fmaf(gal, sj[u], sgn * gj[lm][u] * sa[u]);
-                        tl = fmaf(gam, y[lm], tl);
-                        beta[lm] = fmaf(gam, R[l], beta[lm]);
-                        wl = fmaf(gj[lm][u], y[lm], wl);
+                        const T gam = vfma(sh_ga[lm][p * 32 + lane], sj[p], vmul(gj[lm][p], sas));
+                        tl = vfma(gam, y[lm], tl);
+                        beta[lm] = vfma(gam, R[l], beta[lm]);
+                        wl = vfma(gj[lm][p], y[lm], wl);
                     }
-                    rho = fmaf(Rp[l], tl, rho);
-                    gsacc[u] = fmaf(sgn * R[l], wl, gsacc[u]);
+                    rho = vfma(Rp[l], tl, rho);
+                    if (l & 1) gso[p] = vfma(R[l], wl, gso[p]);
+                    else gse[p] = vfma(R[l], wl, gse[p]);
                 }
             }
-            const float *dY = se + 2 * K + NLM;
-            float ex = rho * se[2 * K + 4 * NLM], ey = rho * se[2 * K + 4 * NLM + 1], ez = rho * se[2 * K + 4 * NLM + 2];
+            const float rh = vsum(rho);
+            float ex = rh * ge[3 * NLM], ey = rh * ge[3 * NLM + 1], ez = rh * ge[3 * NLM + 2];
 #pragma unroll
             for (int lm = 1; lm < NLM; ++lm) {
-                ex = fmaf(beta[lm], dY[3 * lm], ex);
-                ey = fmaf(beta[lm], dY[3 * lm + 1], ey);
-                ez = fmaf(beta[lm], dY[3 * lm + 2], ez);
+                const float bl = vsum(beta[lm]);
+                ex = fmaf(bl, ge[3 * lm], ex);
+                ey = fmaf(bl, ge[3 * lm + 1], ey);
+                ez = fmaf(bl, ge[3 * lm + 2], ez);
             }
             fx += ex; fy += ey; fz += ez;
             // virial proxy: each directed edge's dU/dd . d is counted from both
             // ends of the pair, hence the half
-            if (VIR) wv = fmaf(0.5f * se[2 * K + 4 * NLM + 3],
-                               ex * se[2 * K + 4 * NLM] + ey * se[2 * K + 4 * NLM + 1] + ez * se[2 * K + 4 * NLM + 2], wv);
+            if (VIR) wv = fmaf(0.5f * ge[3 * NLM + 3], ex * ge[3 * NLM] + ey * ge[3 * NLM + 1] + ez * ge[3 * NLM + 2], wv);
         }
         __syncwarp();
     }
@@ -302,14 +405,17 @@ __global__ void __launch_bounds__(MP_WARPS * 32) k_mp_bwd(EdgeGeom g, LayerIO io
             if (VIR) io.W[a] = nu * wv;
         }
     }
-    float gin[CPW], gout[CPW];
-    ldv<CPW>(io.gs_in + (size_t)a * C + lane * CPW, gin);
+    T gin[NP], gout[NP];
+    ldp<CPW>(io.gs_in + (size_t)a * C + lane * CPW, gin);
 #pragma unroll
-    for (int u = 0; u < CPW; ++u) gout[u] = fmaf(io.nu, gsacc[u], gin[u]);
-    stv<CPW>(io.gs_out + (size_t)a * C + lane * CPW, gout);
+    for (int p = 0; p < NP; ++p) gout[p] = vfma(vdup<T>(io.nu), vsub(gse[p], gso[p]), gin[p]);
+    stp<CPW>(io.gs_out + (size_t)a * C + lane * CPW, gout);
     if (io.gs_out_bf16) {
 #pragma unroll
-        for (int u = 0; u < CPW; ++u) io.gs_out_bf16[(size_t)a * C + lane * CPW + u] = __float2bfloat16_rn(gout[u]);
+        for (int p = 0; p < NP; ++p)
+#pragma unroll
+            for (int hh = 0; hh < PW; ++hh)
+                io.gs_out_bf16[(size_t)a * C + lane * CPW + p * PW + hh] = __float2bfloat16_rn(vget(gout[p], hh));
     }
 }
 
@@ -328,16 +434,22 @@ static void fwd_c(const EdgeGeom &g, const LayerIO &io, cudaStream_t st) {
     count_launch();
 }
 
+template <int C, int LMAX, bool VIR>
+static void bwd_launch(const EdgeGeom &g, const LayerIO &io, cudaStream_t st) {
+    constexpr size_t smem = BwdSmem<C, LMAX, 8, VIR>::bytes;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_mp_bwd<C, LMAX, 8, VIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int blocks = (g.n_atoms + MP_WARPS - 1) / MP_WARPS;
+    k_mp_bwd<C, LMAX, 8, VIR><<<blocks, MP_WARPS * 32, smem, st>>>(g, io);
+    count_launch();
+}
+
 // The virial variant (io.W set) is a separate instantiation, so that the
 // force-only adjoint carries no extra register or instruction.
 template <int C, int LMAX>
 static void bwd_c(const EdgeGeom &g, const LayerIO &io, cudaStream_t st) {
-    const int blocks = (g.n_atoms + MP_WARPS - 1) / MP_WARPS;
-    if (io.W)
-        k_mp_bwd<C, LMAX, 8, true><<<blocks, MP_WARPS * 32, 0, st>>>(g, io);
-    else
-        k_mp_bwd<C, LMAX, 8, false><<<blocks, MP_WARPS * 32, 0, st>>>(g, io);
-    count_launch();
+    if (io.W) bwd_launch<C, LMAX, true>(g, io, st);
+    else bwd_launch<C, LMAX, false>(g, io, st);
 }
 
 #define DMTS_DISPATCH(FN, C, LMAX, ...)                          \
