@@ -285,6 +285,12 @@ typedef struct {
                                   proxy (see forces_nc; Sec. 2 "Computation of the virial term in NPT") */
     double *virial_cons;       /* device double [n_replicas] (may be NULL): virial of the full force
                                   -grad U at the last evaluation (see energy_forces_cons) */
+    double *virial_est;        /* device double [n_replicas] (may be NULL; needs virial_cons and, in RESPA
+                                  mode, virial_nc): after each outer step the virial estimator of Sec. 2
+                                  "Computation of the virial term in NPT": the full force's virial at the
+                                  end of the outer step with the fast force's share at that configuration
+                                  replaced by its average over the inner steps,
+                                  virial_cons - W_NC(q_end) + virial_nc; in STS mode virial_cons */
 } dmts_state;
 
 /*

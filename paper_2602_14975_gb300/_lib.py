@@ -69,7 +69,8 @@ class State(ct.Structure):
     _fields_ = [("sys", System), ("v", ct.c_void_p), ("f_nc", ct.c_void_p), ("f_cons", ct.c_void_p),
                 ("masses", ct.c_void_p), ("energy", ct.c_void_p), ("step", ct.c_void_p),
                 ("seed", ct.c_void_p), ("replica_id", ct.c_void_p), ("first_step", ct.c_int),
-                ("internal", ct.c_void_p), ("virial_nc", ct.c_void_p), ("virial_cons", ct.c_void_p)]
+                ("internal", ct.c_void_p), ("virial_nc", ct.c_void_p), ("virial_cons", ct.c_void_p),
+                ("virial_est", ct.c_void_p)]
 
 
 class Request(ct.Structure):

@@ -229,13 +229,15 @@ class MDState:
         st0 = np.zeros(R, np.uint64) if steps is None else np.asarray(steps, np.uint64)
         self.step = torch.from_numpy(st0.view(np.int64)).to(dev)
         # with virial=True: average virial proxy of the fast force over the
-        # inner steps of the last outer step (RESPA), and the virial of the
-        # full force at its last evaluation, per replica
+        # inner steps of the last outer step (RESPA), the virial of the full
+        # force at its last evaluation, and the estimator that combines them
+        # at the end of each outer step, per replica
         self.virial_nc = torch.zeros(R, dtype=torch.float64, device=dev) if virial else None
         self.virial_cons = torch.zeros(R, dtype=torch.float64, device=dev) if virial else None
+        self.virial_est = torch.zeros(R, dtype=torch.float64, device=dev) if virial else None
         self.c = L.State(dsys.struct(), _ptr(self.v), _ptr(self.f_nc), _ptr(self.f_cons), _ptr(self.masses),
                          _ptr(self.energy), _ptr(self.step), _ptr(self.seed), _ptr(self.replica_id), 1, None,
-                         _ptr(self.virial_nc), _ptr(self.virial_cons))
+                         _ptr(self.virial_nc), _ptr(self.virial_cons), _ptr(self.virial_est))
         self.ctx = None
 
     def release(self):

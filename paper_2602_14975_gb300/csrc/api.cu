@@ -890,7 +890,11 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
         return fail(ctx, DMTS_E_INVALID, "missing state array");
     if (stt->sys.n_atoms > 0 && (!stt->sys.bond_ptr || !stt->sys.bond_idx || !stt->sys.bond_r0))
         return fail(ctx, DMTS_E_INVALID, "missing bond table");
+    if (stt->virial_est && (!stt->virial_cons || (!sts && !stt->virial_nc)))
+        return fail(ctx, DMTS_E_INVALID, "virial_est needs virial_cons and virial_nc");
     cudaSetDevice(ctx->device);
+    if (stt->virial_est && !sts && !ctx->ws.nc_w_last.ensure(sizeof(double) * stt->sys.n_replicas))
+        return fail(ctx, DMTS_E_OOM, "workspace allocation failed");
     if (!stt->internal) {
         s = init_state(ctx, stt, p->skin, st);
         if (s != DMTS_OK) {
@@ -964,11 +968,25 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
             if (!sts) {
                 s = nc_fast(stt->virial_nc != nullptr);
                 if (s != DMTS_OK) return s;
+                // the fast force's virial at the end of the outer step, for the estimator
+                if (stt->virial_est && k == n_in - 1)
+                    launch_replica_sum((const float *)ctx->ws.nc_w.p, v.rep_off, v.n_rep, (double *)ctx->ws.nc_w_last.p,
+                                       0, st);
             }
         }
         if (!sts && stt->virial_nc) launch_scale_d(stt->virial_nc, v.n_rep, 1.0 / n_in, st);
         s = cons_full();
         if (s != DMTS_OK) return s;
+        if (stt->virial_est) {
+            if (sts) {
+                if (!ck(ctx, cudaMemcpyAsync(stt->virial_est, stt->virial_cons, sizeof(double) * v.n_rep,
+                                             cudaMemcpyDeviceToDevice, st), "virial copy"))
+                    return DMTS_E_CUDA;
+            } else {
+                launch_virial_estimate(stt->virial_est, stt->virial_cons, (const double *)ctx->ws.nc_w_last.p,
+                                       stt->virial_nc, v.n_rep, st);
+            }
+        }
     }
     ia.ops = sts ? OP_CLOSE_B : (OP_CLOSE_B | OP_KICK_L);
     { ProfScope ps(ctx, "integrate", st); launch_integrate(ia, st); }

@@ -336,6 +336,21 @@ void launch_scale_d(double *v, int n, double f, cudaStream_t st) {
     count_launch();
 }
 
+// Virial estimator of a RESPA outer step (Sec. 2, "Computation of the virial
+// term in NPT"): the full force's virial at the step's end, with the fast
+// force's share there replaced by its average over the inner steps.
+__global__ void k_virial_estimate(double *est, const double *cons, const double *last, const double *avg, int n) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) est[r] = cons[r] - last[r] + avg[r];
+}
+
+void launch_virial_estimate(double *est, const double *cons, const double *last, const double *avg, int n,
+                            cudaStream_t st) {
+    if (n == 0) return;
+    k_virial_estimate<<<(n + 255) / 256, 256, 0, st>>>(est, cons, last, avg, n);
+    count_launch();
+}
+
 // Mean subtraction over each replica in three short kernels. A replica is
 // cut into parts of MS_PART atoms counted from its own first atom, so every
 // sum below depends only on the replica's atoms, never on which other

@@ -43,6 +43,9 @@ struct NCHeadArgs {
 void launch_nc_head(int K, int n_c, int n_l, const NCHeadArgs &a, cudaStream_t st);
 // v[i] *= f, i < n.
 void launch_scale_d(double *v, int n, double f, cudaStream_t st);
+// est[r] = cons[r] - last[r] + avg[r]
+void launch_virial_estimate(double *est, const double *cons, const double *last, const double *avg, int n,
+                            cudaStream_t st);
 // F_out = F_in - (sum_{replica} F_in)/n_r, FP64 sums; net (nullable) [R][3].
 // scratch: device memory of mean_sub_scratch_bytes(n_atoms, n_rep) bytes.
 size_t mean_sub_scratch_bytes(int n_atoms, int n_rep);

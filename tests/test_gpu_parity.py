@@ -286,6 +286,55 @@ def test_respa_keeps_the_last_full_force_virial(ctx1, water):
     assert abs(W.item() - Wst) <= 1e-9 * abs(Wst)
 
 
+def test_respa_virial_estimator(ctx1, models1, water):
+    """Virial estimator of an outer step (Sec. 2, virial term in NPT): the
+    full force's virial at the end of the outer step with the fast force's
+    share there replaced by its inner-step average. GPU state against (i) its
+    own parts, with W_NC(q_end) evaluated afresh at the final positions, and
+    (ii) the oracle's trajectory: the average from its RESPA run, W_NC from
+    its fast force at its final positions and the full force's virial from
+    dU(lambda q, lambda L)/dlambda there by central differences."""
+    (cs, cb), (ns, nb_) = models1
+    m, v = _md_setup(water)
+    d = core.DeviceSystem(water)
+    st = core.MDState(d, v, m.astype(np.float32), seeds=171, virial=True)
+    core.respa_step(ctx1, st, core.integrator(4.0, 4, 300.0, [1.0] * 5, skin=0.5), 2)
+    ctx1.sync()
+    est, cons, avg = (float(t.cpu().numpy()[0]) for t in (st.virial_est, st.virial_cons, st.virial_nc))
+    st.release()
+    nb = core.nbr_build(ctx1, d, 4.0)
+    _, _, Wl = core.forces_nc(ctx1, d, nb, with_virial=True)
+    tol = _virial_tol(water, ns, nb_)
+    assert abs(est - (cons - Wl.item() + avg)) <= tol, (est, cons, Wl.item(), avg)
+    assert avg != Wl.item()   # the correction is not empty
+
+    ref = O.MDState(water, v, m.astype(np.float32).astype(np.float64))
+    wav = ct.c_double(0.0)
+    O.respa_run(ref, water, cs, cb, ns, nb_, 4.0, 4, 300.0, np.full(5, 1.0), 171, 2, virial_avg=wav)
+    end = S.System(water.name, ref.x.copy(), water.species, water.mol_id, water.bonds, water.bond_r0, water.box)
+    _, _, Wl_o = O.nc_forces(end, ns, nb_, with_virial=True)
+
+    def energy(lam):
+        sy = S.System(end.name, end.x * lam, end.species, end.mol_id, end.bonds, end.bond_r0, end.box * lam)
+        return O.cons_energy(sy, cs, cb) + O.prior(sy)[0]
+
+    h = 1e-6
+    cons_o = (energy(1 + h) - energy(1 - h)) / (2 * h)
+    est_o = cons_o - Wl_o + wav.value
+    Ft = O.cons_energy_forces(end, cs, cb)[1] + O.prior(end)[1]
+    assert abs(est - est_o) <= _cons_virial_scale(Ft, 5.5) + tol, (est, est_o)
+
+
+def test_virial_estimator_needs_its_parts(ctx1, water):
+    m, v = _md_setup(water)
+    d = core.DeviceSystem(water)
+    st = core.MDState(d, v, m.astype(np.float32), seeds=171, virial=True)
+    st.c.virial_nc = None
+    with pytest.raises(core.L.DmtsError):
+        core.respa_step(ctx1, st, core.integrator(4.0, 4, 300.0, [1.0] * 5, skin=0.5), 1)
+    st.release()
+
+
 # ------------------------------------------------------------------ Philox --
 
 def test_philox_words_bit_exact(ctx1):
