@@ -201,9 +201,152 @@ __device__ __forceinline__ void epilogue_tile(const Epi &e, int N, int rows, int
     }
 }
 
+// Vector form of the epilogue, used when every array it touches is 16-byte
+// aligned (bf16 copies 8-byte): each thread takes groups of four
+// consecutive columns of a row, so global loads and stores are 16-byte
+// vectors, and the row / column of its next group follow by additions.
+__device__ __forceinline__ float4 ld4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+__device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+__device__ __forceinline__ void st4_bf16(__nv_bfloat16 *p, float4 v) {
+    const __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
+    uint2 u;
+    u.x = *reinterpret_cast<const uint32_t *>(&lo);
+    u.y = *reinterpret_cast<const uint32_t *>(&hi);
+    *reinterpret_cast<uint2 *>(p) = u;
+}
+__device__ __forceinline__ float4 bias4(const float *b, int n) {
+    return make_float4(__ldg(b + n), __ldg(b + n + 1), __ldg(b + n + 2), __ldg(b + n + 3));
+}
+__device__ __forceinline__ float4 silu4(float4 h) { return make_float4(silu_d(h.x), silu_d(h.y), silu_d(h.z), silu_d(h.w)); }
+
+constexpr int EU4 = 2;   // groups per thread and pass
+
+__device__ __forceinline__ void epilogue_tile_v4(const Epi &e, int N, int rows, int m0, int n0, int BN,
+                                                 const float *tile, int ld) {
+    const int G = BN / 4, total = rows * G, step = blockDim.x;
+    const int dr = step / G, dc = step - dr * G;
+    int r = threadIdx.x / G, c = threadIdx.x - (threadIdx.x / G) * G;
+    const int nlm = (e.lmax + 1) * (e.lmax + 1);
+    for (int base = threadIdx.x; base < total; base += EU4 * step) {
+        float4 v[EU4];
+        int rr[EU4], cc[EU4];
+        bool ok[EU4];
+#pragma unroll
+        for (int u = 0; u < EU4; ++u) {
+            ok[u] = base + u * step < total;
+            rr[u] = r;
+            cc[u] = c;
+            const float *t = tile + r * ld + 4 * c;
+            v[u] = ok[u] ? make_float4(t[0], t[1], t[2], t[3]) : make_float4(0.f, 0.f, 0.f, 0.f);
+            r += dr;
+            c += dc;
+            if (c >= G) { c -= G; ++r; }
+        }
+        switch (e.mode) {
+        case EPI_STORE:
+#pragma unroll
+            for (int u = 0; u < EU4; ++u)
+                if (ok[u]) {
+                    const size_t o = (size_t)(m0 + rr[u]) * N + n0 + 4 * cc[u];
+                    st4(e.out + o, v[u]);
+                    if (e.out_bf16) st4_bf16(e.out_bf16 + o, v[u]);
+                }
+            break;
+        case EPI_BIAS_SILU:
+#pragma unroll
+            for (int u = 0; u < EU4; ++u)
+                if (ok[u]) {
+                    const int n = n0 + 4 * cc[u];
+                    const size_t o = (size_t)(m0 + rr[u]) * N + n;
+                    const float4 b = bias4(e.bias, n);
+                    const float4 h = make_float4(v[u].x + b.x, v[u].y + b.y, v[u].z + b.z, v[u].w + b.w);
+                    const float4 sv = silu4(h);
+                    st4(e.H + o, h);
+                    st4(e.out + o, sv);
+                    if (e.out_bf16) st4_bf16(e.out_bf16 + o, sv);
+                }
+            break;
+        case EPI_RESID: {
+            float4 rs[EU4];
+#pragma unroll
+            for (int u = 0; u < EU4; ++u)
+                rs[u] = ok[u] ? ld4(e.res + (size_t)(m0 + rr[u]) * N + n0 + 4 * cc[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < EU4; ++u)
+                if (ok[u]) {
+                    const int n = n0 + 4 * cc[u];
+                    const size_t o = (size_t)(m0 + rr[u]) * N + n;
+                    const float4 b = bias4(e.bias, n);
+                    const float4 o4 = make_float4(rs[u].x + v[u].x + b.x, rs[u].y + v[u].y + b.y,
+                                                  rs[u].z + v[u].z + b.z, rs[u].w + v[u].w + b.w);
+                    st4(e.out + o, o4);
+                    if (e.out_bf16) st4_bf16(e.out_bf16 + o, o4);
+                }
+            break;
+        }
+        case EPI_DSILU: {
+            float4 h[EU4];
+#pragma unroll
+            for (int u = 0; u < EU4; ++u)
+                h[u] = ok[u] ? ld4(e.H + (size_t)(m0 + rr[u]) * N + n0 + 4 * cc[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < EU4; ++u)
+                if (ok[u]) {
+                    const size_t o = (size_t)(m0 + rr[u]) * N + n0 + 4 * cc[u];
+                    const float4 o4 = make_float4(v[u].x * dsilu_d(h[u].x), v[u].y * dsilu_d(h[u].y),
+                                                  v[u].z * dsilu_d(h[u].z), v[u].w * dsilu_d(h[u].w));
+                    st4(e.out + o, o4);
+                    if (e.out_bf16) st4_bf16(e.out_bf16 + o, o4);
+                }
+            break;
+        }
+        case EPI_GA: {
+            // n = l C + c: the four columns share l (C % 4 == 0)
+            float4 a[EU4][5];
+            size_t ib[EU4];
+            int nm[EU4];
+#pragma unroll
+            for (int u = 0; u < EU4; ++u) {
+                const int n = n0 + 4 * cc[u];
+                const int l = n / e.C, cch = n - l * e.C;
+                nm[u] = ok[u] ? 2 * l + 1 : 0;
+                ib[u] = ((size_t)(m0 + rr[u]) * nlm + l * l) * e.C + cch;
+#pragma unroll
+                for (int q = 0; q < 5; ++q)
+                    a[u][q] = q < nm[u] ? ld4(e.A + ib[u] + (size_t)q * e.C) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < EU4; ++u)
+#pragma unroll
+                for (int q = 0; q < 5; ++q)
+                    if (q < nm[u])
+                        st4(e.out + ib[u] + (size_t)q * e.C,
+                            make_float4(2.f * a[u][q].x * v[u].x, 2.f * a[u][q].y * v[u].y, 2.f * a[u][q].z * v[u].z,
+                                        2.f * a[u][q].w * v[u].w));
+            break;
+        }
+        case EPI_READOUT:
+#pragma unroll
+            for (int u = 0; u < EU4; ++u)
+                if (ok[u]) {
+                    const int n = n0 + 4 * cc[u];
+                    const size_t o = (size_t)(m0 + rr[u]) * N + n;
+                    const float4 b = bias4(e.bias, n), w = bias4(e.wo, n);
+                    const float4 z = make_float4(v[u].x + b.x, v[u].y + b.y, v[u].z + b.z, v[u].w + b.w);
+                    st4(e.out + o, make_float4(w.x * silu_d(z.x), w.y * silu_d(z.y), w.z * silu_d(z.z), w.w * silu_d(z.w)));
+                    const float4 gz = make_float4(e.scale * w.x * dsilu_d(z.x), e.scale * w.y * dsilu_d(z.y),
+                                                  e.scale * w.z * dsilu_d(z.z), e.scale * w.w * dsilu_d(z.w));
+                    st4(e.out2 + o, gz);
+                    if (e.out_bf16) st4_bf16(e.out_bf16 + o, gz);
+                }
+            break;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256) k_gemm_tc(const __grid_constant__ CUtensorMap tmA,
                                                  const __grid_constant__ CUtensorMap tmB, int M, int N, int K,
-                                                 int BN, int tmem_cols, int n_stages, Epi e, int *err) {
+                                                 int BN, int tmem_cols, int n_stages, int vec, Epi e, int *err) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t bar_full[TC_STAGES], bar_empty[TC_STAGES], bar_done;
     __shared__ uint32_t tmem_base_sh;
@@ -297,7 +440,8 @@ __global__ void __launch_bounds__(256) k_gemm_tc(const __grid_constant__ CUtenso
         }
         __syncthreads();
         const int rows = min(TC_M, M - m0);
-        epilogue_tile(e, N, rows, m0, n0, BN, tile, ld);
+        if (vec) epilogue_tile_v4(e, N, rows, m0, n0, BN, tile, ld);
+        else epilogue_tile(e, N, rows, m0, n0, BN, tile, ld);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -366,8 +510,11 @@ int launch_gemm_tc(int M, int N, int K, const __nv_bfloat16 *Act, const __nv_bfl
         cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr_set = true;
     }
+    auto al = [](const void *p, uintptr_t a) { return ((uintptr_t)p & (a - 1)) == 0; };
+    const int vec = al(e.out, 16) && al(e.out2, 16) && al(e.H, 16) && al(e.res, 16) && al(e.A, 16) &&
+                    al(e.out_bf16, 8) && (e.mode != EPI_GA || e.C % 4 == 0);
     dim3 grid((M + TC_M - 1) / TC_M, N / BN);
-    k_gemm_tc<<<grid, 256, smem, st>>>(ma, mb, M, N, K, BN, tmem_cols, n_stages, e, err);
+    k_gemm_tc<<<grid, 256, smem, st>>>(ma, mb, M, N, K, BN, tmem_cols, n_stages, vec, e, err);
     count_launch();
     return 0;
 }
