@@ -143,6 +143,12 @@ __device__ __forceinline__ void for_candidates(const NbrWork &w, int i, float rc
 constexpr int NB_WARPS = 4;
 constexpr int NB_MAXROW = 256;
 
+// Warp sweep over the candidates of atom i. Cells are numbered x-fastest, so
+// for each (z, y) row of neighbouring cells the x-run of cells is one
+// contiguous range of cell_atoms (two where it wraps a periodic x boundary).
+// Lane s holds range s (at most 18 for the 3 x 3 rows); the ranges are
+// concatenated by a warp scan and the lanes walk the concatenation 32
+// candidates at a time, so no lane idles at the end of a short cell.
 template <typename Fn>
 __device__ __forceinline__ void for_candidates_warp(const NbrWork &w, int i, float rc2, int lane, Fn f) {
     const CellGrid g = w.grid[w.atom_rep[i]];
@@ -164,36 +170,64 @@ __device__ __forceinline__ void for_candidates_warp(const NbrWork &w, int i, flo
     const float ibx = g.box[0] > 0.f ? 1.f / g.box[0] : 0.f;
     const float iby = g.box[1] > 0.f ? 1.f / g.box[1] : 0.f;
     const float ibz = g.box[2] > 0.f ? 1.f / g.box[2] : 0.f;
+    // x-run [x0, x1] of cells, split at a periodic wrap into [a0, b0] and [a1, b1]
+    int a0 = cx + lo[0], b0 = cx + hi[0], a1 = 0, b1 = -1;
+    if (a0 < 0) { a1 = a0 + g.dim[0]; b1 = g.dim[0] - 1; a0 = 0; }
+    else if (b0 >= g.dim[0]) { a1 = 0; b1 = b0 - g.dim[0]; b0 = g.dim[0] - 1; }
+    int seg_beg = 0, seg_len = 0, sidx = 0;
     for (int oz = lo[2]; oz <= hi[2]; ++oz) {
         int z = cz + oz;
         if (g.box[2] > 0.f) z = (z + g.dim[2]) % g.dim[2];
         for (int oy = lo[1]; oy <= hi[1]; ++oy) {
             int y = cy + oy;
             if (g.box[1] > 0.f) y = (y + g.dim[1]) % g.dim[1];
-            for (int ox = lo[0]; ox <= hi[0]; ++ox) {
-                int xx = cx + ox;
-                if (g.box[0] > 0.f) xx = (xx + g.dim[0]) % g.dim[0];
-                const int cell = g.cell_off + (z * g.dim[1] + y) * g.dim[0] + xx;
-                const int beg = w.cell_start[cell], end = w.cell_start[cell + 1];
-                for (int p0 = beg; p0 < end; p0 += 32) {
-                    const int p = p0 + lane;
-                    bool hit = false;
-                    int j = -1;
-                    float r2 = 0.f;
-                    if (p < end) {
-                        j = w.cell_atoms[p];
-                        if (j != i) {
-                            const float dx = min_img(w.x[3 * j] - xi, g.box[0], ibx);
-                            const float dy = min_img(w.x[3 * j + 1] - yi, g.box[1], iby);
-                            const float dz = min_img(w.x[3 * j + 2] - zi, g.box[2], ibz);
-                            r2 = dx * dx + dy * dy + dz * dz;
-                            hit = r2 < rc2;
-                        }
-                    }
-                    f(hit, j, r2);
+            const int row = g.cell_off + (z * g.dim[1] + y) * g.dim[0];
+            if (lane == sidx) {
+                seg_beg = w.cell_start[row + a0];
+                seg_len = w.cell_start[row + b0 + 1] - seg_beg;
+            }
+            ++sidx;
+            if (b1 >= a1) {
+                if (lane == sidx) {
+                    seg_beg = w.cell_start[row + a1];
+                    seg_len = w.cell_start[row + b1 + 1] - seg_beg;
                 }
+                ++sidx;
             }
         }
+    }
+    int incl = seg_len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(DMTS_FULL, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const int total = __shfl_sync(DMTS_FULL, incl, 31);
+    const int excl = incl - seg_len;
+    for (int q0 = 0; q0 < total; q0 += 32) {
+        const int q = q0 + lane;
+        // range of q: the last lane whose start is <= q (starts never decrease)
+        int sl = 0;
+#pragma unroll
+        for (int st = 16; st > 0; st >>= 1) {
+            const int e = __shfl_sync(DMTS_FULL, excl, sl + st);
+            if (e <= q) sl += st;
+        }
+        const int pb = __shfl_sync(DMTS_FULL, seg_beg, sl), pe = __shfl_sync(DMTS_FULL, excl, sl);
+        bool hit = false;
+        int j = -1;
+        float r2 = 0.f;
+        if (q < total) {
+            j = w.cell_atoms[pb + (q - pe)];
+            if (j != i) {
+                const float dx = min_img(w.x[3 * j] - xi, g.box[0], ibx);
+                const float dy = min_img(w.x[3 * j + 1] - yi, g.box[1], iby);
+                const float dz = min_img(w.x[3 * j + 2] - zi, g.box[2], ibz);
+                r2 = dx * dx + dy * dy + dz * dz;
+                hit = r2 < rc2;
+            }
+        }
+        f(hit, j, r2);
     }
 }
 
