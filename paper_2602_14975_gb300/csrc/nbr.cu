@@ -256,6 +256,30 @@ __device__ __forceinline__ void sort_row(int *sb, int cnt, int lane) {
         }
 }
 
+// Writes the entries of sb[0..cnt) (distinct keys, compared without
+// SUB_FLAG) to dst in ascending order: each entry goes to the position given
+// by the number of smaller keys. A lane ranks entries lane, lane + 32, ...;
+// every key is read once per lane. cnt <= 128.
+__device__ __forceinline__ void rank_scatter(const int *sb, int cnt, int *dst, int lane) {
+    int v[4], k[4], r[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int t = lane + 32 * q;
+        v[q] = t < cnt ? sb[t] : 0;
+        k[q] = t < cnt ? (v[q] & 0x7fffffff) : -1;
+        r[q] = 0;
+    }
+#pragma unroll 4
+    for (int u = 0; u < cnt; ++u) {
+        const int ku = sb[u] & 0x7fffffff;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) r[q] += ku < k[q] ? 1 : 0;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (lane + 32 * q < cnt) dst[r[q]] = v[q];
+}
+
 // Row lengths (and sub-list row lengths). With w.slots the sorted row, sub
 // entries flagged, is also kept for the fill, which then only copies it.
 __global__ void __launch_bounds__(NB_WARPS * 32) k_nbr_count_warp(NbrWork w, float rc2, float rc2_sub) {
@@ -283,9 +307,13 @@ __global__ void __launch_bounds__(NB_WARPS * 32) k_nbr_count_warp(NbrWork w, flo
     }
     if (keep && cnt <= w.slot_cap && cnt <= NB_MAXROW) {
         __syncwarp();
-        sort_row(sb, cnt, lane);
         int *dst = w.slots + (size_t)i * w.slot_cap;
-        for (int t = lane; t < cnt; t += 32) dst[t] = sb[t];
+        if (cnt <= 128) {
+            rank_scatter(sb, cnt, dst, lane);
+        } else {
+            sort_row(sb, cnt, lane);
+            for (int t = lane; t < cnt; t += 32) dst[t] = sb[t];
+        }
     }
 }
 
