@@ -135,11 +135,12 @@ __device__ __forceinline__ void for_candidates(const NbrWork &w, int i, float rc
     }
 }
 
-// Warp per atom: lanes sweep the atoms of each neighbouring cell (the cell
-// order of for_candidates), rows are collected by ballot into shared memory,
-// sorted there by a bitonic network and written out contiguously. Rows are in
-// canonical order (ascending j), so they do not depend on the cell layout at
-// build time and results do not depend on when lists were rebuilt.
+// Warp per atom: lanes sweep the candidates of the neighbouring cells, hits
+// are collected by ballot into shared memory and written out in ascending j
+// (placed by rank; a bitonic network for rows longer than 128 and in the
+// fill pass without kept rows). Rows are in canonical order, so they do not
+// depend on the cell layout at build time and results do not depend on when
+// lists were rebuilt.
 constexpr int NB_WARPS = 4;
 constexpr int NB_MAXROW = 256;
 
