@@ -34,11 +34,11 @@ LARGE_WORKLOAD = "water_100000"
 # while the kernel's sources hash to the recorded value; after any change to
 # them it is null until a new capture is taken.
 NCU_TRAFFIC = {
-    "mp_bwd": {"bytes_per_launch": 153755904 + 15438592,
+    "mp_bwd": {"bytes_per_launch": (153771520 + 15115008 + 154084864 + 12173312 + 141766912 + 233728) / 3,
                "sources": [("paper_2602_14975_gb300/csrc/mp.cu", None),
                            ("paper_2602_14975_gb300/csrc/mp.cuh", None),
                            ("paper_2602_14975_gb300/csrc/common.cuh", None)],
-               "sha256": "fbe35f786e0879fd351ae9bbc37301ba2220c91337452ded4b59efdfe252271f"},
+               "sha256": "0985154b1474782a8813ffff37348ca16d0c7c78e484aca7e22afb157b1b612d"},
 }
 
 
@@ -489,8 +489,13 @@ def main():
     # algorithmic FLOP per active edge (one layer), counted as 2 per FMA:
     # forward: radial 3*8 FMA + 3 mul + 9 FMA per channel;
     # adjoint: radial and derivative 48 FMA + 18 + 9 + 3 + 9 + 9 + 3 per
-    # channel, plus 30 FMA per lane for the direction derivatives.
-    flop_edge = {"mp_fwd": 2 * 36 * C, "mp_bwd": 2 * 99 * C + 2 * 30 * 32}
+    # channel, plus 30 FMA per lane for the direction derivatives; layer 0
+    # has no sender-role gradient (its inputs are the species embedding), so
+    # 87 FMA per channel there. mp_bwd is the average over the L launches of
+    # one evaluation, as the per-launch time is.
+    Lc = cs.L
+    flop_edge = {"mp_fwd": 2 * 36 * C,
+                 "mp_bwd": (2 * 99 * C * (Lc - 1) + 2 * 87 * C) / Lc + 2 * 30 * 32}
     fp32_peak_tflops = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
     fp32_src = "152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz (nominal unit counts and max clock)"
 
@@ -514,7 +519,7 @@ def main():
     nlm = (cs.lmax + 1) ** 2
     n_at = sy.n_atoms
     alg_bytes = {"mp_fwd": n_at * (4 * C + 12 + 4 * nlm * C + 6 * (cs.lmax + 1) * C) + 4 * e_cons,
-                 "mp_bwd": n_at * (4 * C + 4 * nlm * C + 4 * C + 6 * C + 12 + 12) + 4 * e_cons}
+                 "mp_bwd": n_at * (4 * C + 4 * nlm * C + 12 + 12 + (Lc - 1) / Lc * (4 * C + 6 * C)) + 4 * e_cons}
     roof["algorithmic_bytes_per_launch"] = alg_bytes[name]
 
     # every hot kernel against its own bound (per-launch averages over the

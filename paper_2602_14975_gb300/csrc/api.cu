@@ -310,7 +310,7 @@ dmts_status cons_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const
             io.nu = m.nu;
             io.gA = gA;
             io.gs_in = gin;
-            io.gs_out = gout;
+            io.gs_out = t > 0 ? gout : nullptr;   // layer 0's inputs are the species embedding
             io.gs_out_bf16 = t > 0 ? gout_bf : nullptr;
             io.F = forces;
             io.accumulate = t != L - 1;

@@ -505,11 +505,8 @@ int launch_gemm_tc(int M, int N, int K, const __nv_bfloat16 *Act, const __nv_bfl
     const int n_stages = std::min(3, K / TC_K);
     const size_t tile = (size_t)TC_M * (BN + 1) * sizeof(float);   // epilogue staging
     const size_t smem = std::max((size_t)stage * n_stages, tile) + 1024;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_set = true;
-    }
+    // per launch: the attribute belongs to the current device's context
+    cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     auto al = [](const void *p, uintptr_t a) { return ((uintptr_t)p & (a - 1)) == 0; };
     const int vec = al(e.out, 16) && al(e.out2, 16) && al(e.H, 16) && al(e.res, 16) && al(e.A, 16) &&
                     al(e.out_bf16, 8) && (e.mode != EPI_GA || e.C % 4 == 0);

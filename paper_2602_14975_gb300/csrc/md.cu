@@ -307,11 +307,8 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
 template <int K, int NC, int NL>
 static void nc_head_launch(const NCHeadArgs &a, cudaStream_t st) {
     using SM = NCHeadSmem<K, NC, NL>;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_nc_head<K, NC, NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes);
-        attr = true;
-    }
+    // per launch: the attribute belongs to the current device's context
+    cudaFuncSetAttribute(k_nc_head<K, NC, NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes);
     const int blocks = (a.n_atoms + NCH_WARPS - 1) / NCH_WARPS;
     k_nc_head<K, NC, NL><<<blocks, NCH_WARPS * 32, SM::bytes, st>>>(a);
     count_launch();

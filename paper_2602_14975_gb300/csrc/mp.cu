@@ -239,7 +239,10 @@ struct BwdSmem {
     static constexpr size_t bytes = r_bytes + ga_bytes + g_bytes + sizeof(int) * MP_WARPS * 32;
 };
 
-template <int C, int LMAX, int K, bool VIR>
+// SG = false (io.gs_out == nullptr) skips the sender-role gradient: the
+// first layer's input features are the species embedding, constant in the
+// positions, so nothing consumes it there.
+template <int C, int LMAX, int K, bool VIR, bool SG>
 __global__ void __launch_bounds__(MP_WARPS * 32) k_mp_bwd(EdgeGeom g, LayerIO io) {
     using S = BwdSmem<C, LMAX, K, VIR>;
     using T = typename S::T;
@@ -370,11 +373,13 @@ __global__ void __launch_bounds__(MP_WARPS * 32) k_mp_bwd(EdgeGeom g, LayerIO io
                         const T gam = vfma(sh_ga[lm][p * 32 + lane], sj[p], vmul(gj[lm][p], sas));
                         tl = vfma(gam, y[lm], tl);
                         beta[lm] = vfma(gam, R[l], beta[lm]);
-                        wl = vfma(gj[lm][p], y[lm], wl);
+                        if (SG) wl = vfma(gj[lm][p], y[lm], wl);
                     }
                     rho = vfma(Rp[l], tl, rho);
-                    if (l & 1) gso[p] = vfma(R[l], wl, gso[p]);
-                    else gse[p] = vfma(R[l], wl, gse[p]);
+                    if (SG) {
+                        if (l & 1) gso[p] = vfma(R[l], wl, gso[p]);
+                        else gse[p] = vfma(R[l], wl, gse[p]);
+                    }
                 }
             }
             const float rh = vsum(rho);
@@ -405,6 +410,7 @@ __global__ void __launch_bounds__(MP_WARPS * 32) k_mp_bwd(EdgeGeom g, LayerIO io
             if (VIR) io.W[a] = nu * wv;
         }
     }
+    if (!SG) return;
     T gin[NP], gout[NP];
     ldp<CPW>(io.gs_in + (size_t)a * C + lane * CPW, gin);
 #pragma unroll
@@ -434,22 +440,24 @@ static void fwd_c(const EdgeGeom &g, const LayerIO &io, cudaStream_t st) {
     count_launch();
 }
 
-template <int C, int LMAX, bool VIR>
+template <int C, int LMAX, bool VIR, bool SG>
 static void bwd_launch(const EdgeGeom &g, const LayerIO &io, cudaStream_t st) {
     constexpr size_t smem = BwdSmem<C, LMAX, 8, VIR>::bytes;
     if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_mp_bwd<C, LMAX, 8, VIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_mp_bwd<C, LMAX, 8, VIR, SG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int blocks = (g.n_atoms + MP_WARPS - 1) / MP_WARPS;
-    k_mp_bwd<C, LMAX, 8, VIR><<<blocks, MP_WARPS * 32, smem, st>>>(g, io);
+    k_mp_bwd<C, LMAX, 8, VIR, SG><<<blocks, MP_WARPS * 32, smem, st>>>(g, io);
     count_launch();
 }
 
-// The virial variant (io.W set) is a separate instantiation, so that the
-// force-only adjoint carries no extra register or instruction.
+// The virial variant (io.W set) and the variant without the sender-role
+// gradient (io.gs_out null) are separate instantiations, so that each
+// carries no register or instruction it does not use.
 template <int C, int LMAX>
 static void bwd_c(const EdgeGeom &g, const LayerIO &io, cudaStream_t st) {
-    if (io.W) bwd_launch<C, LMAX, true>(g, io, st);
-    else bwd_launch<C, LMAX, false>(g, io, st);
+    const bool gs = io.gs_out != nullptr;
+    if (io.W) gs ? bwd_launch<C, LMAX, true, true>(g, io, st) : bwd_launch<C, LMAX, true, false>(g, io, st);
+    else gs ? bwd_launch<C, LMAX, false, true>(g, io, st) : bwd_launch<C, LMAX, false, false>(g, io, st);
 }
 
 #define DMTS_DISPATCH(FN, C, LMAX, ...)                          \

@@ -31,7 +31,7 @@ struct LayerIO {
     int n_l;
     const float *gA;         // [N][NLM][C]  (backward in)
     const float *gs_in;      // [N][C]       (backward in)
-    float *gs_out;           // [N][C]       (backward out)
+    float *gs_out;           // [N][C]       (backward out; nullable: not computed)
     __nv_bfloat16 *gs_out_bf16;  // optional bf16 copy of gs_out
     float *F;                // [N][3]       (backward: accumulated forces)
     int accumulate;          // backward: 0 write F, 1 add to F (and W)
