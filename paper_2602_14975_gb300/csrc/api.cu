@@ -361,8 +361,8 @@ dmts_status nc_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const i
     Workspace &w = ctx->ws;
     const size_t nc_ = (size_t)N * C;
     const bool bf = m.bf16;
-    if (!w.nc_s.ensure(sizeof(float) * nc_ * 2) || !w.nc_A.ensure(sizeof(float) * nc_ * 4) ||
-        !w.nc_q.ensure(sizeof(float) * nc_ * 2) || !w.nc_h.ensure(sizeof(float) * nc_) ||
+    if (!w.nc_s.ensure(sizeof(float) * nc_ * 2) ||
+        !w.nc_q.ensure(sizeof(float) * nc_ * 2) ||
         !w.nc_act.ensure(sizeof(float) * nc_) || !w.nc_qk.ensure(sizeof(float) * (size_t)N * QKW) ||
         !w.nc_v.ensure(sizeof(float) * (size_t)N * m.nl * 3) || !w.nc_f.ensure(sizeof(float) * 3 * (N + 1)) ||
         !w.ms_scratch.ensure(mean_sub_scratch_bytes(N, s.n_rep)) ||
@@ -381,7 +381,7 @@ dmts_status nc_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const i
     io.s = s0;
     io.wrad = m.wrad[0];
     io.nu = m.nu;
-    io.A = (float *)w.nc_A.p;
+    io.A = nullptr;   // the direct-force head needs q and V only (no adjoint)
     io.q = (float *)w.nc_q.p;
     io.q_bf16 = q_bf;
     io.U = m.U;
@@ -391,7 +391,7 @@ dmts_status nc_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const i
     { ProfScope ps(ctx, "nc_mp_fwd", st); launch_mp_fwd(C, 1, m.K, g, io, st); }
     Epi e1 = epi(EPI_BIAS_SILU);
     e1.bias = m.b1[0];
-    e1.H = (float *)w.nc_h.p;
+    e1.H = nullptr;   // no backward through the NC model
     e1.out = (float *)w.nc_act.p;
     e1.out_bf16 = act_bf;
     contract(ctx, m, N, C, 2 * C, io.q, q_bf, m.w1[0], 1, m.w1_bf[0], e1, st, "nc_gemm_tc", "nc_gemm");

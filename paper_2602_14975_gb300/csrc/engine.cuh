@@ -49,7 +49,7 @@ struct NbrScratch {
 
 struct Workspace {
     Buf s, A, q, h, act, u, gz, gs0, gs1, gA, e_atom, ftmp, atom_rep;
-    Buf nc_s, nc_A, nc_q, nc_h, nc_act, nc_qk, nc_v, nc_f;
+    Buf nc_s, nc_q, nc_act, nc_qk, nc_v, nc_f;
     // bf16 operands of the tensor-core contractions
     Buf q_bf, act_bf, s_bf, gz_bf, gs0_bf, gs1_bf, nc_q_bf, nc_act_bf, nc_s_bf;
     Buf ms_scratch;   // per-part sums of the mean subtraction
@@ -58,7 +58,7 @@ struct Workspace {
     Buf nc_w_last;    // per-replica fast-force virial of the last inner step
     void release_all() {
         Buf *all[] = {&s, &A, &q, &h, &act, &u, &gz, &gs0, &gs1, &gA, &e_atom, &ftmp, &atom_rep,
-                      &nc_s, &nc_A, &nc_q, &nc_h, &nc_act, &nc_qk, &nc_v, &nc_f,
+                      &nc_s, &nc_q, &nc_act, &nc_qk, &nc_v, &nc_f,
                       &q_bf, &act_bf, &s_bf, &gz_bf, &gs0_bf, &gs1_bf, &nc_q_bf, &nc_act_bf, &nc_s_bf,
                       &ms_scratch, &nc_w, &cons_w, &nc_w_last};
         for (Buf *b : all) b->release();

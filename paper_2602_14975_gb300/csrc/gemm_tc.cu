@@ -122,7 +122,7 @@ __device__ __forceinline__ void epilogue_tile(const Epi &e, int N, int rows, int
                 if (ok[u]) {
                     const float h = v[u] + b[u];
                     const float sv = silu_d(h);
-                    e.H[o[u]] = h;
+                    if (e.H) e.H[o[u]] = h;
                     e.out[o[u]] = sv;
                     if (e.out_bf16) e.out_bf16[o[u]] = __float2bfloat16_rn(sv);
                 }
@@ -261,7 +261,7 @@ __device__ __forceinline__ void epilogue_tile_v4(const Epi &e, int N, int rows, 
                     const float4 b = bias4(e.bias, n);
                     const float4 h = make_float4(v[u].x + b.x, v[u].y + b.y, v[u].z + b.z, v[u].w + b.w);
                     const float4 sv = silu4(h);
-                    st4(e.H + o, h);
+                    if (e.H) st4(e.H + o, h);
                     st4(e.out + o, sv);
                     if (e.out_bf16) st4_bf16(e.out_bf16 + o, sv);
                 }

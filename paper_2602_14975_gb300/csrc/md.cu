@@ -132,7 +132,8 @@ struct NCHeadSmem {
     static constexpr size_t qk = (size_t)NCH_WARPS * QKW * 4;
     static constexpr size_t vv = (size_t)NCH_WARPS * 4 * NL * 4;
     static constexpr size_t queue = (size_t)NCH_WARPS * 64 * 4;
-    static constexpr size_t bytes = rows + qk + vv + queue + NCH_WARPS * 8;
+    static constexpr size_t qdisp = (size_t)NCH_WARPS * 64 * 3 * 4;   // displacement of each queued edge
+    static constexpr size_t bytes = rows + qk + vv + queue + qdisp + NCH_WARPS * 8;
     static_assert(QKW % 16 == 0, "row stride");
     static_assert(HH <= K, "each lane's first heads are Bessel heads");
 };
@@ -148,7 +149,8 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
     float *qa = reinterpret_cast<float *>(nch_smem + SM::rows) + warp * QKW;
     float *va = reinterpret_cast<float *>(nch_smem + SM::rows + SM::qk) + warp * 4 * NL;
     int *queue = reinterpret_cast<int *>(nch_smem + SM::rows + SM::qk + SM::vv) + warp * 64;
-    uint64_t *bar_p = reinterpret_cast<uint64_t *>(nch_smem + SM::rows + SM::qk + SM::vv + SM::queue) + warp;
+    float *qd = reinterpret_cast<float *>(nch_smem + SM::rows + SM::qk + SM::vv + SM::queue) + warp * 64 * 3;
+    uint64_t *bar_p = reinterpret_cast<uint64_t *>(nch_smem + SM::rows + SM::qk + SM::vv + SM::queue + SM::qdisp) + warp;
     const uint32_t bar = smem_u32(bar_p);
     const int wa = blockIdx.x * NCH_WARPS + warp;
     if (wa >= g.n_atoms || *g.err) return;
@@ -169,6 +171,19 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
     const bool with_rep = g.bonds.ptr && g.rep.on;
     const float rep2 = g.rep.rc * g.rep.rc;
     const int sa = g.species[a];
+    // bonded partners of a (up to four in registers; more fall back to the table)
+    int bp[4] = {-1, -1, -1, -1}, nbp = 0;
+    if (with_rep) {
+        const int b0 = g.bonds.ptr[a];
+        nbp = g.bonds.ptr[a + 1] - b0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (q < nbp) bp[q] = g.bonds.idx[b0 + q];
+    }
+    auto bonded = [&](int j) {
+        if (nbp > 4) return is_bonded(g.bonds, a, j);
+        return j == bp[0] || j == bp[1] || j == bp[2] || j == bp[3];
+    };
     float fx = 0.f, fy = 0.f, fz = 0.f, rx = 0.f, ry = 0.f, rz = 0.f;
     float wv = 0.f, wr = 0.f;   // virial proxy: sum_j F_aj . d_aj, and the repulsion's half pair terms
     uint32_t phase = 0;
@@ -178,7 +193,8 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
     // first stages the row and adds the repulsion, the pair splits the heads
     const int slot = lane & (BATCH - 1), half = lane / BATCH;
     auto batch = [&](int taken, int nb) {
-        const int j = slot < nb ? queue[(taken + slot) & 63] : -1;
+        const int qs = (taken + slot) & 63;
+        const int j = slot < nb ? queue[qs] : -1;
         fence_proxy_async_smem();      // earlier reads of the rows before the copies overwrite them
         if (lane == 0) mbar_expect_tx(bar, (uint32_t)nb * SM::ROWB);
         __syncwarp();
@@ -186,13 +202,13 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
         // radial part of the edge while the rows arrive
         float dx = 0.f, dy = 0.f, dz = 0.f, inv = 1.f, fc = 0.f, Bh[HH];
         if (j >= 0) {
-            dx = min_img(__ldg(g.x + 3 * j) - xa, bx, ibx);
-            dy = min_img(__ldg(g.x + 3 * j + 1) - ya, by, iby);
-            dz = min_img(__ldg(g.x + 3 * j + 2) - za, bz, ibz);
+            dx = qd[3 * qs];
+            dy = qd[3 * qs + 1];
+            dz = qd[3 * qs + 2];
             const float r2 = dx * dx + dy * dy + dz * dz;
             const float r = sqrtf(r2);
             inv = 1.f / r;
-            if (half == 0 && with_rep && r2 < rep2 && !is_bonded(g.bonds, a, j)) {
+            if (half == 0 && with_rep && r2 < rep2 && !bonded(j)) {
                 float dE;
                 rep_pair(g.rep, sa, g.species[j], r, &dE);
                 const float c = dE * inv;              // F_a = E'(r) d / r
@@ -273,14 +289,21 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
         const int e = base + lane;
         const int j = e < end ? __ldg(g.col + e) : -1;
         bool act = false;
+        float dx = 0.f, dy = 0.f, dz = 0.f;
         if (j >= 0) {
-            const float dx = min_img(__ldg(g.x + 3 * j) - xa, bx, ibx);
-            const float dy = min_img(__ldg(g.x + 3 * j + 1) - ya, by, iby);
-            const float dz = min_img(__ldg(g.x + 3 * j + 2) - za, bz, ibz);
+            dx = min_img(__ldg(g.x + 3 * j) - xa, bx, ibx);
+            dy = min_img(__ldg(g.x + 3 * j + 1) - ya, by, iby);
+            dz = min_img(__ldg(g.x + 3 * j + 2) - za, bz, ibz);
             act = dx * dx + dy * dy + dz * dz < rc2;
         }
         const unsigned m = __ballot_sync(DMTS_FULL, act);
-        if (act) queue[(queued + __popc(m & ((1u << lane) - 1u))) & 63] = j;
+        if (act) {
+            const int qs = (queued + __popc(m & ((1u << lane) - 1u))) & 63;
+            queue[qs] = j;
+            qd[3 * qs] = dx;
+            qd[3 * qs + 1] = dy;
+            qd[3 * qs + 2] = dz;
+        }
         queued += __popc(m);
         __syncwarp();
         while (queued - taken >= BATCH && alive) {

@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(MP_WARPS * 32) k_mp_fwd(EdgeGeom g, LayerIO io
             a[p] = vmul(nu, acc[lm][p]);
             qv[l][p] = vfma(a[p], a[p], qv[l][p]);
         }
-        stp<CPW>(io.A + ((size_t)i * NLM + lm) * C + co + lane * CPW, a);
+        if (io.A) stp<CPW>(io.A + ((size_t)i * NLM + lm) * C + co + lane * CPW, a);
     }
     if (LMAX >= 1 && io.V) {
         // vector part of the tensor heads, V_h = sum_c U[h][c] A[l=1][c]
@@ -497,7 +497,7 @@ __device__ __forceinline__ void epilogue(const Epi &e, int N, int m, int n, floa
         break;
     case EPI_BIAS_SILU: {
         const float h = v + e.bias[n];
-        e.H[o] = h;
+        if (e.H) e.H[o] = h;
         const float s = silu_f(h);
         e.out[o] = s;
         if (e.out_bf16) e.out_bf16[o] = __float2bfloat16_rn(s);

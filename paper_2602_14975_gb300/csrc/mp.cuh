@@ -23,7 +23,7 @@ struct LayerIO {
     const float *s;          // [N][C] input features s^t
     const float *wrad;       // [L+1][K][C]
     float nu;
-    float *A;                // [N][NLM][C]  (forward out)
+    float *A;                // [N][NLM][C]  (forward out; nullable: not stored)
     float *q;                // [N][(LMAX+1)C] (forward out, fp32)
     __nv_bfloat16 *q_bf16;   // optional bf16 copy of q (forward out)
     const float *U;          // optional: tensor-head mix U[n_l][C] (NC embedding)
@@ -89,7 +89,7 @@ struct Epi {
     float *out2;
     const float *bias;
     const float *res;          // residual input [M][N]
-    float *H;                  // pre-activation store / load
+    float *H;                  // pre-activation store (nullable) / load
     const float *A;            // EPI_GA
     const float *wo;           // EPI_READOUT
     float scale;
