@@ -35,10 +35,15 @@ LARGE_WORKLOAD = "water_100000"
 # them it is null until a new capture is taken.
 NCU_TRAFFIC = {
     "mp_bwd": {"bytes_per_launch": (153771520 + 15115008 + 154084864 + 12173312 + 141766912 + 233728) / 3,
-               "sources": [("paper_2602_14975_gb300/csrc/mp.cu", None),
-                           ("paper_2602_14975_gb300/csrc/mp.cuh", None),
+               # the adjoint's code: channel-pack helpers, kernel and launch, the
+               # argument structs, the device helpers
+               "sources": [("paper_2602_14975_gb300/csrc/mp.cu", ("// ---- channel packs", "// ---- forward")),
+                           ("paper_2602_14975_gb300/csrc/mp.cu", ("// ---- adjoint", "// In the forward pass")),
+                           ("paper_2602_14975_gb300/csrc/mp.cu", ("template <int C, int LMAX, bool VIR, bool SG>",
+                                                                  "#define DMTS_DISPATCH")),
+                           ("paper_2602_14975_gb300/csrc/mp.cuh", ("struct EdgeGeom {", "template <int CPW>")),
                            ("paper_2602_14975_gb300/csrc/common.cuh", None)],
-               "sha256": "0985154b1474782a8813ffff37348ca16d0c7c78e484aca7e22afb157b1b612d"},
+               "sha256": "2638b92428b8a377051f0e6df5cc319f49c27bb51659fe0201a89c948d978175"},
 }
 
 
@@ -51,13 +56,32 @@ def _kernel_text(text, name):
     return text[beg:end]
 
 
+def _region(text, start, end):
+    """Text from the line holding `start` up to the line holding `end`; both
+    markers are matched after collapsing runs of dashes in comment rules."""
+    import re
+    norm = re.sub(r"-{4,}", "----", text)
+    beg = norm.index(start)
+    beg = norm.rindex("\n", 0, beg) + 1
+    stop = norm.index(end, beg + len(start))
+    return norm[beg:stop]
+
+
 def sources_sha256(sources):
+    """Hash of the code a recorded capture depends on: a whole file (None), a
+    __global__ function by name, or a region between two markers."""
     import hashlib
     h = hashlib.sha256()
-    for path, kernel in sources:
+    for path, spec in sources:
         with open(os.path.join(ROOT, path), encoding="utf-8") as f:
             text = f.read()
-        h.update((_kernel_text(text, kernel) if kernel else text).encode())
+        if spec is None:
+            part = text
+        elif isinstance(spec, tuple):
+            part = _region(text, *spec)
+        else:
+            part = _kernel_text(text, spec)
+        h.update(part.encode())
     return h.hexdigest()
 
 
