@@ -306,6 +306,19 @@ dmts_status respa_step(dmts_ctx *ctx, dmts_state *st, const dmts_integrator *p, 
 /* Frees st->internal. */
 void dmts_state_release(dmts_ctx *ctx, dmts_state *st);
 
+/*
+ * Copy of the neighbour list a state holds (inspection; synchronous):
+ * which = 0 the conservative list (cutoff r_c + skin), 1 the NC list
+ * (r_NC + skin), as last built on the device (Sec. 2, neighbour lists of the
+ * two models). row_ptr: device int32 [n_atoms + 1]; col: device int32
+ * [col_capacity]; *n_pairs (host) receives the entry count and *r_list (host,
+ * may be NULL) the list radius. DMTS_E_INVALID before the state's first
+ * respa_step or for a list the state does not hold; DMTS_E_NBR_OVERFLOW with
+ * *n_pairs set when col_capacity is too small (row_ptr is written).
+ */
+dmts_status dmts_state_lists(dmts_ctx *ctx, const dmts_state *st, int which, int32_t *row_ptr, int32_t *col,
+                             int64_t col_capacity, int64_t *n_pairs, float *r_list, void *stream);
+
 /* ------------------------------------------------------------------ rewind */
 /*
  * Guard against rare disagreements of the two force models (Sec. 2,

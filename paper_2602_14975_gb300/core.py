@@ -240,6 +240,26 @@ class MDState:
                          _ptr(self.virial_nc), _ptr(self.virial_cons), _ptr(self.virial_est))
         self.ctx = None
 
+    def lists(self, which: int) -> NbrList:
+        """The neighbour list the state holds (0: conservative, 1: NC), as
+        last built on the device; valid after the first respa_step."""
+        if self.ctx is None:
+            raise ValueError("the state holds no lists before its first respa_step")
+        dev = self.dsys.x.device
+        row = torch.empty(self.dsys.n_atoms + 1, dtype=torch.int32, device=dev)
+        npairs, rl = ct.c_longlong(0), ct.c_float(0.0)
+        st = self.ctx.lib.dmts_state_lists(self.ctx.handle, ct.byref(self.c), int(which), _ptr(row), None, 0,
+                                           ct.byref(npairs), ct.byref(rl), _stream(dev))
+        if st not in (L.OK, L.E_NBR_OVERFLOW):
+            L.check(st, self.ctx.handle)
+        col = torch.empty(max(1, npairs.value), dtype=torch.int32, device=dev)
+        st = self.ctx.lib.dmts_state_lists(self.ctx.handle, ct.byref(self.c), int(which), _ptr(row), _ptr(col),
+                                           col.numel(), ct.byref(npairs), ct.byref(rl), _stream(dev))
+        L.check(st, self.ctx.handle)
+        nb = NbrList(row, col[: max(1, npairs.value)], float(rl.value))
+        nb.n_pairs = int(npairs.value)
+        return nb
+
     def release(self):
         if self.ctx is not None and self.c.internal:
             self.ctx.lib.dmts_state_release(self.ctx.handle, ct.byref(self.c))

@@ -858,6 +858,32 @@ void dmts_state_release(dmts_ctx *ctx, dmts_state *st) {
     st->internal = nullptr;
 }
 
+dmts_status dmts_state_lists(dmts_ctx *ctx, const dmts_state *st, int which, int32_t *row_ptr, int32_t *col,
+                             int64_t col_capacity, int64_t *n_pairs, float *r_list, void *stream) {
+    if (!ctx || !st || !row_ptr || !n_pairs || (which != 0 && which != 1))
+        return fail(ctx, DMTS_E_INVALID, "bad arguments");
+    const StateInternal *si = (const StateInternal *)st->internal;
+    if (!si) return fail(ctx, DMTS_E_INVALID, "the state holds no lists before its first respa_step");
+    const Buf &rb = which == 0 ? si->cons_row : si->nc_row;
+    const Buf &cb = which == 0 ? si->cons_col : si->nc_col;
+    if (!rb.p) return fail(ctx, DMTS_E_INVALID, "the state holds no such list");
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = si->n;
+    int total = 0;
+    if (!ck(ctx, cudaMemcpyAsync(row_ptr, rb.p, sizeof(int) * (n + 1), cudaMemcpyDeviceToDevice, s), "list copy") ||
+        !ck(ctx, cudaMemcpyAsync(&total, (const int *)rb.p + n, sizeof(int), cudaMemcpyDeviceToHost, s), "list size") ||
+        !ck(ctx, cudaStreamSynchronize(s), "list copy"))
+        return DMTS_E_CUDA;
+    *n_pairs = total;
+    if (r_list) *r_list = which == 0 ? si->r_cons : si->r_nc;
+    if (total > col_capacity) return fail(ctx, DMTS_E_NBR_OVERFLOW, "col_capacity too small");
+    if (total > 0 && (!col || !ck(ctx, cudaMemcpyAsync(col, cb.p, sizeof(int) * (size_t)total, cudaMemcpyDeviceToDevice, s),
+                                  "list copy")))
+        return col ? DMTS_E_CUDA : fail(ctx, DMTS_E_INVALID, "col is NULL");
+    return ck(ctx, cudaStreamSynchronize(s), "list copy") ? DMTS_OK : DMTS_E_CUDA;
+}
+
 static void gamma_consts(const dmts_integrator *p, double dt, float *c1, float *c2) {
     for (int s = 0; s < DMTS_MAX_SPECIES; ++s) {
         const double e = std::exp(-p->gamma_ps[s] * 1e-3 * dt);

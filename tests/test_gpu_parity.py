@@ -103,6 +103,54 @@ def test_nbr_empty_replica_and_single_atom(ctx1):
     assert rp[1] - rp[0] == 0
 
 
+def _state_system(systems, x):
+    """The systems with the state's current positions (batched order)."""
+    out, off = [], 0
+    for sy in systems:
+        n = sy.n_atoms
+        out.append(S.System(sy.name, x[off:off + n].astype(np.float64), sy.species, sy.mol_id, sy.bonds,
+                            sy.bond_r0, sy.box))
+        off += n
+    return out
+
+
+@pytest.mark.parametrize("which", ["periodic", "open_batch"])
+def test_state_lists_vs_brute_force(ctx1, models1, water, which):
+    """The lists the integrator builds and rebuilds on the device (cell sweep,
+    rank-ordered slot rows, the NC list flagged in the same pass), read back
+    through dmts_state_lists: right after the first build both equal the
+    brute-force pair sets at r_c + skin (rows ascending); after 12 outer steps
+    (rebuilds on the device) every pair within the model cutoff at the current
+    positions is still listed and the rows stay ascending."""
+    (cs, _), (ns, _) = models1
+    systems = [water] if which == "periodic" else [S.capped_molecule_in_droplet(n, seed=60 + n) for n in (30, 18, 45)]
+    m = np.concatenate([sy.element_masses() for sy in systems])
+    v = S.maxwell_boltzmann(m, 300.0, 103)
+    d = core.DeviceSystem(systems)
+    st = core.MDState(d, v, m.astype(np.float32), seeds=181)
+    integ = core.integrator(4.0, 4, 300.0, [1.0] * 5, skin=0.5)
+    core.respa_step(ctx1, st, integ, 0)
+    for which_list, rc in ((0, cs.rc), (1, ns.rc)):
+        nb = st.lists(which_list)
+        assert abs(nb.r_list - (rc + 0.5)) < 1e-6
+        _check_pairs(systems, nb, rc + 0.5)
+    core.respa_step(ctx1, st, integ, 12)
+    ctx1.sync()
+    now = _state_system(systems, d.x.cpu().numpy())
+    for which_list, rc in ((0, cs.rc), (1, ns.rc)):
+        nb = st.lists(which_list)
+        rp, col = nb.row_ptr.cpu().numpy(), nb.col.cpu().numpy()
+        for i in range(len(rp) - 1):
+            assert np.all(np.diff(col[rp[i]:rp[i + 1]]) > 0)
+        got = pair_set(rp, col)
+        off = 0
+        for sy in now:
+            brp, bcol = O.nbr_brute(sy.x, sy.box, rc)
+            assert pair_set(brp, bcol, off) <= got
+            off += sy.n_atoms
+    st.release()
+
+
 # ------------------------------------------------------------ conservative --
 
 def _gpu_cons(ctx, systems, rlist=5.5, with_prior=True):
