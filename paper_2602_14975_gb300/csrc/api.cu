@@ -249,7 +249,7 @@ dmts_status cons_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const
     __nv_bfloat16 *s_bf = bf ? (__nv_bfloat16 *)w.s_bf.p : nullptr, *gz_bf = bf ? (__nv_bfloat16 *)w.gz_bf.p : nullptr;
     __nv_bfloat16 *gs0_bf = bf ? (__nv_bfloat16 *)w.gs0_bf.p : nullptr, *gs1_bf = bf ? (__nv_bfloat16 *)w.gs1_bf.p : nullptr;
     const EdgeGeom g = edge_geom(s, row_ptr, col, m);
-    { ProfScope ps(ctx, "embed", st); launch_embed(N, C, s.species, m.emb, S, st); }
+    if (!(flags & kFlagEmbedded)) { ProfScope ps(ctx, "embed", st); launch_embed(N, C, s.species, m.emb, S, st); }
     for (int t = 0; t < L; ++t) {
         LayerIO io;
         memset(&io, 0, sizeof io);
@@ -375,7 +375,7 @@ dmts_status nc_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const i
     __nv_bfloat16 *s_bf = bf ? (__nv_bfloat16 *)w.nc_s_bf.p : nullptr;
     float *s0 = (float *)w.nc_s.p, *s1 = s0 + nc_;
     const EdgeGeom g = edge_geom(s, row_ptr, col, m);
-    { ProfScope ps(ctx, "embed", st); launch_embed(N, C, s.species, m.emb, s0, st); }
+    if (!(flags & kFlagEmbedded)) { ProfScope ps(ctx, "embed", st); launch_embed(N, C, s.species, m.emb, s0, st); }
     LayerIO io;
     memset(&io, 0, sizeof io);
     io.s = s0;
@@ -429,7 +429,8 @@ dmts_status nc_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const i
     { ProfScope ps(ctx, "nc_head", st); launch_nc_head(m.K, m.nc, m.nl, a, st); }
     {
         ProfScope ps(ctx, "mean_sub", st);
-        launch_mean_sub((float *)w.nc_f.p, forces, s.rep_off, s.n_rep, N, net, w.ms_scratch.p, ctx->d_err, st);
+        launch_mean_sub((float *)w.nc_f.p, forces, s.rep_off, s.n_rep, N, net, w.ms_scratch.p, ctx->d_err, st,
+                        s.ms_part_off);
     }
     if (virial) {
         ProfScope ps(ctx, "replica_sum", st);
@@ -499,6 +500,7 @@ SysView state_view(dmts_state *stt) {
     v.bond_r0 = sys->bond_r0;
     v.atom_rep = (int *)si->atom_rep.p;
     v.order = (const int *)si->scratch.cell_atoms.p;   // atoms sorted by cell at the last rebuild
+    v.ms_part_off = (const int *)si->ms_part.p;
     return v;
 }
 
@@ -601,6 +603,7 @@ void free_state_internal(StateInternal *si) {
     si->x_ref.release();
     si->gate.release();
     si->atom_rep.release();
+    si->ms_part.release();
     si->scratch.release_all();
     delete si;
 }
@@ -628,9 +631,10 @@ dmts_status init_state(dmts_ctx *ctx, dmts_state *stt, float skin, cudaStream_t 
     const int N = si->n;
     if (!si->atom_rep.ensure(sizeof(int) * (N + 1)) || !si->x_ref.ensure(sizeof(float) * 3 * (N + 1)) ||
         !si->gate.ensure(sizeof(int)) || !si->cons_row.ensure(sizeof(int) * (N + 1)) ||
-        !si->nc_row.ensure(sizeof(int) * (N + 1)))
+        !si->nc_row.ensure(sizeof(int) * (N + 1)) || !si->ms_part.ensure(sizeof(int) * (sys->n_replicas + 1)))
         return fail(ctx, DMTS_E_OOM, "state allocation failed");
     atom_rep_map(sys->rep_off, sys->n_replicas, N, (int *)si->atom_rep.p, st);
+    launch_mean_part_off(sys->rep_off, sys->n_replicas, (int *)si->ms_part.p, st);
     k_set_int<<<1, 1, 0, st>>>((int *)si->gate.p, 1);
     count_launch();
     SysView v = state_view(stt);
@@ -827,7 +831,7 @@ dmts_status energy_forces_cons(dmts_ctx *ctx, const dmts_system *sys, const dmts
     cudaSetDevice(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     SysView v = make_view(ctx, sys, st);
-    s = cons_eval(ctx, v, nbr->row_ptr, nbr->col, energy, forces, flags, st, virial);
+    s = cons_eval(ctx, v, nbr->row_ptr, nbr->col, energy, forces, flags & ~kFlagEmbedded, st, virial);
     if (s != DMTS_OK) return s;
     return ck(ctx, cudaGetLastError(), "energy_forces_cons launch") ? DMTS_OK : DMTS_E_CUDA;
 }
@@ -844,7 +848,7 @@ dmts_status forces_nc(dmts_ctx *ctx, const dmts_system *sys, const dmts_nbr *nbr
     cudaSetDevice(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     SysView v = make_view(ctx, sys, st);
-    s = nc_eval(ctx, v, nbr->row_ptr, nbr->col, forces, net_force, flags, st, virial, 0);
+    s = nc_eval(ctx, v, nbr->row_ptr, nbr->col, forces, net_force, flags & ~kFlagEmbedded, st, virial, 0);
     if (s != DMTS_OK) return s;
     return ck(ctx, cudaGetLastError(), "forces_nc launch") ? DMTS_OK : DMTS_E_CUDA;
 }
@@ -935,14 +939,22 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
     const SysView v = state_view(stt);
     const int *crow = (int *)si->cons_row.p, *ccol = (int *)si->cons_col.p;
     const int *nrow = (int *)si->nc_row.p, *ncol = (int *)si->nc_col.p;
+    // the species embedding is computed by the first evaluation of each
+    // model in this call and kept in the workspace for the others
+    int cons_emb = 0, nc_emb = 0;
     auto cons_full = [&]() {
-        return cons_eval(ctx, v, crow, ccol, stt->energy, stt->f_cons, DMTS_WITH_PRIOR, st, stt->virial_cons);
+        const dmts_status r = cons_eval(ctx, v, crow, ccol, stt->energy, stt->f_cons, DMTS_WITH_PRIOR | cons_emb, st,
+                                        stt->virial_cons);
+        cons_emb = kFlagEmbedded;
+        return r;
     };
     // fast force; inside the inner loop it also adds its virial proxy to the
     // per-replica average of the outer step (Sec. 2, virial term in NPT)
     auto nc_fast = [&](bool with_virial) {
-        return nc_eval(ctx, v, nrow, ncol, stt->f_nc, nullptr, DMTS_WITH_BONDS, st,
-                       with_virial ? stt->virial_nc : nullptr, 1);
+        const dmts_status r = nc_eval(ctx, v, nrow, ncol, stt->f_nc, nullptr, DMTS_WITH_BONDS | nc_emb, st,
+                                      with_virial ? stt->virial_nc : nullptr, 1);
+        nc_emb = kFlagEmbedded;
+        return r;
     };
 
     if (stt->first_step) {

@@ -77,13 +77,14 @@ struct SysView {
     const float *bond_r0;
     const int *atom_rep;
     const int *order = nullptr;   // processing order of the per-atom kernels (nullable)
+    const int *ms_part_off = nullptr;   // mean-subtraction part offsets of this batch (nullable)
 };
 
 struct StateInternal {
     int n = 0, n_rep = 0, n_cells = 0;
     float skin = 0.f, r_cons = 0.f, r_nc = 0.f;
     std::vector<CellGrid> grids;
-    Buf cons_row, cons_col, nc_row, nc_col, x_ref, gate, atom_rep;
+    Buf cons_row, cons_col, nc_row, nc_col, x_ref, gate, atom_rep, ms_part;
     long long cons_cap = 0, nc_cap = 0;
     NbrScratch scratch;
 };
@@ -138,6 +139,11 @@ struct dmts_ctx {
 namespace dmts {
 bool ck(dmts_ctx *ctx, cudaError_t e, const char *what);
 dmts_status fail(dmts_ctx *ctx, dmts_status s, const std::string &msg);
+// Internal flag of cons_eval / nc_eval: the layer-0 features (the species
+// embedding) already in the workspace belong to this system, so the
+// embedding is not recomputed (set within one respa_step call, where the
+// species do not change).
+constexpr int kFlagEmbedded = 1 << 30;
 dmts_status cons_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const int *col, double *energy,
                       float *forces, int flags, cudaStream_t st, double *virial = nullptr);
 dmts_status nc_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const int *col, float *forces,

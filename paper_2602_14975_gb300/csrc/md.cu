@@ -499,14 +499,24 @@ size_t mean_sub_scratch_bytes(int n_atoms, int n_rep) {
     return 3 * sizeof(double) * parts + sizeof(int) * ((size_t)n_rep + 1) + 64;
 }
 
+void launch_mean_part_off(const int *rep_off, int n_rep, int *part_off, cudaStream_t st) {
+    if (n_rep == 0) return;
+    k_mean_part_off<<<1, 1024, 0, st>>>(rep_off, n_rep, part_off, nullptr);
+    count_launch();
+}
+
 void launch_mean_sub(const float *F_in, float *F_out, const int *rep_off, int n_rep, int n_atoms, double *net,
-                     void *scratch, const int *err, cudaStream_t st) {
+                     void *scratch, const int *err, cudaStream_t st, const int *part_off_pre) {
     if (n_rep == 0) return;
     const int parts = (n_atoms + MS_PART - 1) / MS_PART + n_rep;   // bound on the parts of all replicas
     double *partial = static_cast<double *>(scratch);
     int *part_off = reinterpret_cast<int *>(partial + 3 * (size_t)parts);
-    k_mean_part_off<<<1, 1024, 0, st>>>(rep_off, n_rep, part_off, net);
-    count_launch();
+    if (part_off_pre && !net) {
+        part_off = const_cast<int *>(part_off_pre);
+    } else {
+        k_mean_part_off<<<1, 1024, 0, st>>>(rep_off, n_rep, part_off, net);
+        count_launch();
+    }
     k_mean_partial<<<parts, MS_THREADS, 0, st>>>(F_in, rep_off, part_off, n_rep, partial, err);
     count_launch();
     k_mean_apply<<<parts, MS_THREADS, 0, st>>>(F_in, F_out, rep_off, part_off, n_rep, partial, net, err);

@@ -49,8 +49,12 @@ void launch_virial_estimate(double *est, const double *cons, const double *last,
 // F_out = F_in - (sum_{replica} F_in)/n_r, FP64 sums; net (nullable) [R][3].
 // scratch: device memory of mean_sub_scratch_bytes(n_atoms, n_rep) bytes.
 size_t mean_sub_scratch_bytes(int n_atoms, int n_rep);
+// part_off (nullable): the replicas' part offsets from launch_mean_part_off,
+// computed once for a fixed batch; then net must be NULL.
 void launch_mean_sub(const float *F_in, float *F_out, const int *rep_off, int n_rep, int n_atoms, double *net,
-                     void *scratch, const int *err, cudaStream_t st);
+                     void *scratch, const int *err, cudaStream_t st, const int *part_off = nullptr);
+// part_off: device int [n_rep + 1]
+void launch_mean_part_off(const int *rep_off, int n_rep, int *part_off, cudaStream_t st);
 
 struct PriorArgs {
     const float *x;

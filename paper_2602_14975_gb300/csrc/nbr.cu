@@ -21,11 +21,14 @@ void atom_rep_map(const int *rep_off, int n_rep, int n_atoms, int *atom_rep, cud
     count_launch();
 }
 
-// Open replicas: bounding box -> origin and cell edge max(r_list, extent/dim).
+// One block per replica: zeroes the replica's cell counts; open replicas:
+// bounding box -> origin and cell edge max(r_list, extent/dim).
 __global__ void k_grid_open(NbrWork w, float r_list) {
     if (gated_off(w.gate, w.err)) return;
     const int r = blockIdx.x;
     CellGrid &g = w.grid[r];
+    const int nc = g.dim[0] * g.dim[1] * g.dim[2];
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) w.cell_cnt[g.cell_off + c] = 0;
     if (g.box[0] > 0.f) return;   // periodic: fixed on the host
     __shared__ float red[6][32];
     float mn[3] = {3.4e38f, 3.4e38f, 3.4e38f}, mx[3] = {-3.4e38f, -3.4e38f, -3.4e38f};
@@ -449,7 +452,6 @@ void nbr_cells(const NbrWork &w, float r_list, cudaStream_t st) {
     if (w.n_atoms == 0) return;
     k_grid_open<<<w.n_rep, 256, 0, st>>>(w, r_list);
     count_launch();
-    cudaMemsetAsync(w.cell_cnt, 0, sizeof(int) * w.n_cells, st);
     const int nb = (w.n_atoms + 255) / 256;
     k_cell_assign<<<nb, 256, 0, st>>>(w);
     count_launch();
