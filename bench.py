@@ -33,6 +33,8 @@ LARGE_WORKLOAD = "water_100000"
 # capture command and the counters are in profiles/). It is reported only
 # while the kernel's sources hash to the recorded value; after any change to
 # them it is null until a new capture is taken.
+PROF_EVERY = 4   # time every 4th outer step of the timed region per kernel
+
 NCU_TRAFFIC = {
     "mp_bwd": {"bytes_per_launch": (153771520 + 15115008 + 154084864 + 12173312 + 141766912 + 233728) / 3,
                # the adjoint's code: channel-pack helpers, kernel and launch, the
@@ -325,7 +327,10 @@ def main():
     clocks = ClockSampler(local)
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    core.profile_enable(ctx, True)
+    # per-kernel events on every PROF_EVERY-th outer step of the timed
+    # region (events on every step cost about 4 % of the step time)
+    core.profile_enable(ctx, True, every=PROF_EVERY)
+    n_prof = (args.steps + PROF_EVERY - 1) // PROF_EVERY
     barrier()
     clocks.start()
     torch.cuda.nvtx.range_push("dmts_outer_steps")    # the timed region, for ncu --nvtx-include
@@ -559,8 +564,8 @@ def main():
     def rate(work, seconds, unit_scale):
         return work / seconds / unit_scale if seconds else None
 
-    t_gemm = prof.get("gemm_tc", (0, 0.0))[1] * 1e-3 / args.steps
-    t_ncg = prof.get("nc_gemm_tc", (0, 0.0))[1] * 1e-3 / args.steps
+    t_gemm = prof.get("gemm_tc", (0, 0.0))[1] * 1e-3 / n_prof
+    t_ncg = prof.get("nc_gemm_tc", (0, 0.0))[1] * 1e-3 / n_prof
     nc_bytes = N * (qkw * 4 + ns.n_l * 12 + 12 + 12) + 4 * e_nc
     kr = {}
     for k in ("mp_fwd", "mp_bwd"):
@@ -582,7 +587,7 @@ def main():
     b = rate(65.0 * syL.n_atoms, per_launch_s(profL, "integrate"), 1e9)
     kr["integrate_100k"] = {"row": "a8", "bound": "hbm", "gbs": b, "frac_hbm": b / hbm if b and hbm else None,
                             "bytes_per_launch": 65 * syL.n_atoms}
-    shares = {k: {"launches": v[0], "ms_per_step": v[1] / args.steps,
+    shares = {k: {"launches": v[0], "ms_per_step": v[1] / n_prof,
                   "share": v[1] / max(sum(x[1] for x in prof.values()), 1e-9)} for k, v in prof.items()}
 
     val = ns_per_day(I.dt_outer, 1e3 / ms_dmts) * world

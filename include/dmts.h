@@ -454,7 +454,10 @@ long long dmts_replica_footprint(const dmts_ctx *ctx, int n_atoms);
  * CUDA events on its own stream. dmts_profile_read() synchronises the device
  * and returns, for slot `idx` (0 <= idx < count returned by a call with
  * idx = -1), the step's name, number of executions and summed duration in ms
- * since the last enable. Disabling clears nothing; enabling clears the table. */
+ * since the last enable. Disabling clears nothing; enabling clears the table.
+ * enable = N > 1 times, inside respa_step and respa_guarded, only every N-th
+ * outer step counted from the enable (outer steps 0, N, 2N, ...), so that the
+ * events perturb a long run less; other calls are always timed. */
 dmts_status dmts_profile_enable(dmts_ctx *ctx, int enable);
 int dmts_profile_read(dmts_ctx *ctx, int idx, char *name, int name_cap, long long *launches,
                       double *total_ms);

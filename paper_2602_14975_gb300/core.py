@@ -325,9 +325,10 @@ class ConsEnergy(torch.autograd.Function):
         return -F * g[:, None], None, None, None, None
 
 
-def profile_enable(ctx: Context, on: bool = True):
-    """Per-kernel CUDA-event timing inside the library (measurement support)."""
-    L.check(ctx.lib.dmts_profile_enable(ctx.handle, 1 if on else 0), ctx.handle)
+def profile_enable(ctx: Context, on: bool = True, every: int = 1):
+    """Per-kernel CUDA-event timing inside the library (measurement support);
+    with every = N > 1 only every N-th outer step of respa_step is timed."""
+    L.check(ctx.lib.dmts_profile_enable(ctx.handle, max(1, int(every)) if on else 0), ctx.handle)
 
 
 def kernel_launches(ctx: Context) -> int:

@@ -992,7 +992,16 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
     ia.h_in = (float)(0.5 * delta);
     ia.h_out = 0.5f * p->dt_outer;
     if (n_outer == 0) return DMTS_OK;
+    // outer steps not timed under a sampling profiler; calls outside the loop are
+    struct ActiveReset {
+        dmts_ctx *c;
+        ~ActiveReset() { c->prof.active = true; }
+    } active_reset{ctx};
     for (int o = 0; o < n_outer; ++o) {
+        if (ctx->prof.on) {
+            ctx->prof.active = ctx->prof.every <= 1 || ctx->prof.outer % ctx->prof.every == 0;
+            ctx->prof.outer++;
+        }
         if (!sts && stt->virial_nc &&
             !ck(ctx, cudaMemsetAsync(stt->virial_nc, 0, sizeof(double) * v.n_rep, st), "virial reset"))
             return DMTS_E_CUDA;

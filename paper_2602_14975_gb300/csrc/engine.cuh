@@ -98,6 +98,9 @@ struct ProfSlot {
 
 struct Profiler {
     bool on = false;
+    int every = 1;          // inside respa_step: time every N-th outer step
+    long long outer = 0;    // outer steps seen since enabling
+    bool active = true;     // timing the current outer step
     std::vector<ProfSlot> slots;
     std::vector<cudaEvent_t> pool;
     int slot(const char *name);

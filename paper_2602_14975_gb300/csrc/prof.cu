@@ -53,7 +53,7 @@ void Profiler::release() {
 }
 
 ProfScope::ProfScope(dmts_ctx *ctx, const char *name, cudaStream_t st) : p(nullptr), s(st), k(-1) {
-    if (!ctx || !ctx->prof.on) return;
+    if (!ctx || !ctx->prof.on || !ctx->prof.active) return;
     p = &ctx->prof;
     k = p->slot(name);
     start = p->take();
@@ -86,6 +86,9 @@ dmts_status dmts_profile_enable(dmts_ctx *ctx, int enable) {
         ctx->prof.clear();
     }
     ctx->prof.on = enable != 0;
+    ctx->prof.every = enable > 1 ? enable : 1;
+    ctx->prof.outer = 0;
+    ctx->prof.active = true;
     return DMTS_OK;
 }
 
