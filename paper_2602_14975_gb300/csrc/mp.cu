@@ -78,6 +78,7 @@ __global__ void __launch_bounds__(MP_WARPS * 32) k_mp_fwd(EdgeGeom g, LayerIO io
     using T = typename Pack<CPW>::T;
     constexpr int NP = Pack<CPW>::NP, PW = Pack<CPW>::W;
     constexpr int RS = (K + NLM) | 1;   // odd record stride: conflict-free writes
+    constexpr int FWD_UNROLL = LMAX >= 2 ? 2 : 4;   // edges in flight per lane (registers allowing)
     const int co = blockIdx.y * CW;
     __shared__ T sh_r[MP_WARPS][32][RS];
     __shared__ int sh_j[MP_WARPS][32];
@@ -135,7 +136,7 @@ __global__ void __launch_bounds__(MP_WARPS * 32) k_mp_fwd(EdgeGeom g, LayerIO io
         }
         __syncwarp();
         const int na = __popc(m);
-#pragma unroll 2
+#pragma unroll FWD_UNROLL
         for (int t = 0; t < na; ++t) {
             const int jt = sh_j[warp][t];
             const T *rec = sh_r[warp][t];
