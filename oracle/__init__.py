@@ -96,7 +96,15 @@ def _declare(L):
     L.orc_respa_run.restype = ct.c_double
     L.orc_respa_run.argtypes = [_I, _D, ct.c_uint64, _U8, _I, _D, _I, _D, _D,
                                 _I, _D, _D, _I, _D, _D, _D, _D,
-                                ct.c_int, _D, _D, _D, _D, _U64, _I, _D]
+                                ct.c_int, _D, _D, _D, _D, _U64, _I, _D, _D, _D, _D]
+    L.orc_baro_mass.restype = ct.c_double
+    L.orc_baro_mass.argtypes = [ct.c_int, ct.c_double, ct.c_double]
+    L.orc_baro_force.restype = ct.c_double
+    L.orc_baro_force.argtypes = [ct.c_int, ct.c_double, ct.c_double, _D, ct.c_double]
+    L.orc_kinetic.restype = ct.c_double
+    L.orc_kinetic.argtypes = [ct.c_int, _D, _D]
+    L.orc_baro_drift.restype = None
+    L.orc_baro_drift.argtypes = [ct.c_int, _D, _D, _D, ct.c_double, ct.c_double, ct.c_double]
     L.orc_sts_run.restype = ct.c_double
     L.orc_sts_run.argtypes = [_I, _D, ct.c_uint64, _U8, _I, _D, _I, _D, _D,
                               _I, _D, _D, _D, _D, ct.c_int, _D, _D, _D, _U64, _I]
@@ -336,10 +344,13 @@ LANGEVIN, FFL = 0, 1
 
 def respa_run(state, sys, cons_spec, cons_blob, nc_spec, nc_blob, dt_outer, n_inner, T,
               gamma_ps, seed, n_outer, replica=0, inner_mode=0, outer_mode=0, consts=PRIOR,
-              thermostat=LANGEVIN, virial_avg=None):
+              thermostat=LANGEVIN, virial_avg=None, barostat=None):
     """Algorithm 1 for n_outer outer steps; returns the last potential energy.
     virial_avg (a ctypes double, optional) receives the average virial proxy
     of the fast force over the inner steps of the last outer step.
+    barostat (optional): (P_ext atm, tau_P ps, box, baro) with box a float64
+    [3] array the piston moves and baro = [p_eps, G, have_G] float64, both
+    updated in place (a periodic system only).
     inner_mode: 0 NC + bonds, 1 full -grad U (collapse to BAOAB), 2 bonds only.
     outer_mode: 0 -grad(U_MP + prior), 1 bonds only.
     thermostat: LANGEVIN or FFL (Fast Forward Langevin O-step)."""
@@ -365,7 +376,40 @@ def respa_run(state, sys, cons_spec, cons_blob, nc_spec, nc_blob, dt_outer, n_in
                            state.x.ctypes.data_as(_D), state.v.ctypes.data_as(_D),
                            state.F.ctypes.data_as(_D), state.F_nc.ctypes.data_as(_D),
                            ct.byref(state.step), ct.byref(state.first),
-                           ct.byref(virial_avg) if virial_avg is not None else None)
+                           ct.byref(virial_avg) if virial_avg is not None else None,
+                           *_baro_args(barostat))
+
+
+def _baro_args(barostat):
+    if barostat is None:
+        return None, None, None
+    p_atm, tau_ps, box_io, baro = barostat
+    assert box_io.dtype == np.float64 and baro.dtype == np.float64 and box_io.flags.c_contiguous
+    par = np.array([p_atm, tau_ps], np.float64)
+    _baro_args.keep = par
+    return par.ctypes.data_as(_D), box_io.ctypes.data_as(_D), baro.ctypes.data_as(_D)
+
+
+def baro_mass(n, T, tau_p_fs):
+    L = lib()
+    return L.orc_baro_mass(int(n), float(T), float(tau_p_fs))
+
+
+def baro_force(n, K, wvir, box, p_atm):
+    b, pb = _d(box)
+    return lib().orc_baro_force(int(n), float(K), float(wvir), pb, float(p_atm))
+
+
+def kinetic(v, mass):
+    vv, pv = _d(np.asarray(v).reshape(-1))
+    m, pm = _d(mass)
+    return lib().orc_kinetic(len(m), pv, pm)
+
+
+def baro_drift(x, v, box, h, b, a):
+    """In place on float64 arrays x [n,3], v [n,3], box [3]."""
+    lib().orc_baro_drift(x.shape[0], x.ctypes.data_as(_D), v.ctypes.data_as(_D), box.ctypes.data_as(_D),
+                         float(h), float(b), float(a))
 
 
 def sts_run(state, sys, cons_spec, cons_blob, dt, T, gamma_ps, seed, n_steps, replica=0,

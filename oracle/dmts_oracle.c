@@ -33,6 +33,11 @@
  *   orc_respa_run     Algorithm 1 (DMTS-NC integration step), force caching
  *                     across outer steps.
  *   orc_sts_run       single-time-step BAOAB (Sec. 2, Sec. 3 setup).
+ *   orc_respa_run with a barostat: isotropic Langevin piston around the outer
+ *                     step, driven by the virial estimator of Sec. 2
+ *                     "Computation of the virial term in NPT" (Sec. 3: Bussi's
+ *                     barostat, 1 atm, tau_P = 2 ps); the scheme is the reading
+ *                     stated at orc_baro_* below.
  *   Both take the O-step's thermostat: Langevin, or the Fast Forward Langevin
  *   update of Sec. 2 "High Hydrogen Friction" (the Langevin speed, the old
  *   direction, per-atom norms).
@@ -939,6 +944,77 @@ static void ostep(const md_t *md, double *v, double dt, uint64_t step)
     }
 }
 
+/* ------------------------------------------------------------------------ */
+/* Barostat                                                                  */
+/* ------------------------------------------------------------------------ */
+/* Reading of Sec. 3's "Bussi's barostat" (stochastic, isotropic): the volume
+ * follows epsilon = ln(V)/3 with a piston momentum p_eps (kcal/mol fs) of mass
+ * W = (N_f + 3) kB T tau_P^2, friction 1/tau_P and matching noise (a Langevin
+ * piston); the particles couple to it as in the isotropic Martyna-Tobias-Klein
+ * equations: dx/dt = v + (p_eps/W) x, dv/dt = ... - (1 + 3/N_f)(p_eps/W) v,
+ * dp_eps/dt = (1 + 3/N_f) 2K - Wvir - 3 V P_ext, with Wvir = -sum_i F_i . q_i
+ * the virial estimator of Sec. 2 (the pair form). Per outer step Delta:
+ * p_eps += Delta/2 G; p_eps <- c p_eps + sqrt((1 - c^2) W kB T) xi
+ * (c = exp(-Delta/tau_P), xi from Philox at (seed, replica, step, 2^32 - 1));
+ * the outer step with p_eps fixed, each A half-step of length h being
+ * x <- x e^(b h) + h phi(b h) v, v <- v e^(-a h), box <- box e^(b h)
+ * (b = p_eps/W, a = (1 + 3/N_f) b, phi(z) = (e^z - 1)/z: the exact flow of
+ * dx/dt = v + b x for constant v); then G <- its value at the step's end and
+ * p_eps += Delta/2 G. N_f = 3 n. */
+#define ORC_KCAL_PER_A3_PER_ATM (101325.0 * 6.02214076e23 * 1e-30 / 4184.0)
+
+double orc_baro_mass(int n, double T, double tau_p_fs)
+{
+    return (3.0 * n + 3.0) * ORC_KB * T * tau_p_fs * tau_p_fs;
+}
+
+/* Generalised force on the piston: (1 + 3/N_f) 2K - Wvir - 3 V P_ext. */
+double orc_baro_force(int n, double K, double wvir, const double *box, double p_atm)
+{
+    double V = box[0] * box[1] * box[2];
+    return (1.0 + 3.0 / (3.0 * n)) * 2.0 * K - wvir - 3.0 * V * p_atm * ORC_KCAL_PER_A3_PER_ATM;
+}
+
+/* Kinetic energy sum_i m_i v_i^2 / 2 in kcal/mol. */
+double orc_kinetic(int n, const double *v, const double *mass)
+{
+    double K = 0.0;
+    for (int i = 0; i < n; ++i)
+        K += 0.5 * mass[i] * (v[3 * i] * v[3 * i] + v[3 * i + 1] * v[3 * i + 1] + v[3 * i + 2] * v[3 * i + 2]);
+    return K / ORC_ACC_CONV;
+}
+
+/* A half-step with the piston: the exact flow of dx/dt = v + b x (v fixed),
+ * then v <- v e^(-a h), box <- box e^(b h). */
+void orc_baro_drift(int n, double *x, double *v, double *box, double h, double b, double a)
+{
+    double z = b * h, e = exp(z), phi = z != 0.0 ? expm1(z) / z : 1.0, s = exp(-a * h);
+    for (int i = 0; i < 3 * n; ++i) {
+        x[i] = x[i] * e + h * phi * v[i];
+        v[i] *= s;
+    }
+    for (int k = 0; k < 3; ++k) box[k] *= e;
+}
+
+/* Virial of the full force, dU(lambda q, lambda L)/dlambda at 1, by central
+ * differences (the pair form's definition; -sum_i F_i . q_i in open space). */
+static double full_virial_fd(const md_t *md, const double *x)
+{
+    const double h = 1e-6;
+    int n = md->n;
+    double *xs = malloc(sizeof(double) * 3 * n), *F = malloc(sizeof(double) * 3 * n), bs[3], U[2];
+    md_t m2 = *md;
+    m2.box = bs;
+    for (int sgn = 0; sgn < 2; ++sgn) {
+        double lam = sgn ? 1.0 - h : 1.0 + h;
+        for (int i = 0; i < 3 * n; ++i) xs[i] = x[i] * lam;
+        for (int k = 0; k < 3; ++k) bs[k] = md->box[k] * lam;
+        U[sgn] = full_force(&m2, xs, F);
+    }
+    free(xs); free(F);
+    return (U[0] - U[1]) / (2.0 * h);
+}
+
 /* Algorithm 1 (DMTS-NC integration step), repeated n_outer times.
  * state: x, v, F (full force -grad U), F_nc (fast force), *step (global inner
  * step index, advanced by n per outer step), *first (force cache flag).
@@ -955,33 +1031,65 @@ double orc_respa_run(const int *ints, const double *reals, uint64_t seed,
                      const int *nmi, const double *nmr, const double *nblob,
                      const double *mass, const double *gamma_ps,
                      int n_outer, double *x, double *v, double *F, double *F_nc,
-                     uint64_t *step, int *first, double *virial_avg)
+                     uint64_t *step, int *first, double *virial_avg,
+                     const double *baro_par, double *box_io, double *baro)
 {
     md_t md = {ints[0], species, mol_id, box, ints[1], bonds, bond_r0, prior,
                cmi, cmr, cblob, nmi, nmr, nblob, mass, gamma_ps, reals[1], seed,
                (uint32_t)ints[5], ints[2], ints[3], ints[6]};
     int n = md.n, n_in = ints[4];
     double Delta = reals[0], delta = Delta / n_in, U = 0.0;
+    /* barostat (nullable): baro_par = [P_ext atm, tau_P ps], box_io the box it
+     * moves, baro = [p_eps, G, have_G] */
+    const int npt = baro_par && box_io && baro && box_io[0] > 0.0;
+    double Wp = 0.0, cP = 0.0, b = 0.0, a = 0.0;
+    if (npt) {
+        md.box = box_io;
+        Wp = orc_baro_mass(n, md.T, baro_par[1] * 1e3);
+        cP = exp(-Delta / (baro_par[1] * 1e3));
+    }
     if (*first) {
         inner_force(&md, x, F_nc);
         U = full_force(&md, x, F);
         *first = 0;
     }
     for (int o = 0; o < n_outer; ++o) {
-        double wsum = 0.0;
+        double wsum = 0.0, wlast = 0.0;
+        if (npt) {
+            if (baro[2] == 0.0) {     /* no estimator yet: the full force's virial */
+                baro[1] = orc_baro_force(n, orc_kinetic(n, v, mass), full_virial_fd(&md, x), box_io, baro_par[0]);
+                baro[2] = 1.0;
+            }
+            double g[3];
+            orc_gauss3(md.seed, md.replica, *step, 0xFFFFFFFFu, g);
+            baro[0] += 0.5 * Delta * baro[1];
+            baro[0] = cP * baro[0] + sqrt((1.0 - cP * cP) * Wp * ORC_KB * md.T) * g[0];
+            b = baro[0] / Wp;
+            a = (1.0 + 3.0 / (3.0 * n)) * b;
+        }
         kick(n, v, F, F_nc, Delta / 2.0, mass);                /* v += D/2 M^-1 (F - F_NC) */
         for (int k = 0; k < n_in; ++k) {
             kick(n, v, F_nc, NULL, delta / 2.0, mass);          /* B */
-            drift(n, x, v, delta / 2.0);                        /* A */
+            if (npt) orc_baro_drift(n, x, v, box_io, delta / 2.0, b, a);
+            else drift(n, x, v, delta / 2.0);                   /* A */
             ostep(&md, v, delta, *step);                        /* O, Thermostat(v, D/n) */
-            drift(n, x, v, delta / 2.0);                        /* A */
-            wsum += inner_force(&md, x, F_nc);                  /* F_NC <- NC(x) */
+            if (npt) orc_baro_drift(n, x, v, box_io, delta / 2.0, b, a);
+            else drift(n, x, v, delta / 2.0);                   /* A */
+            wlast = inner_force(&md, x, F_nc);                  /* F_NC <- NC(x) */
+            wsum += wlast;
             kick(n, v, F_nc, NULL, delta / 2.0, mass);          /* B */
             *step += 1;
         }
         U = full_force(&md, x, F);                              /* F <- large(x) */
         kick(n, v, F, F_nc, Delta / 2.0, mass);                 /* v += D/2 M^-1 (F - F_NC) */
         if (virial_avg) *virial_avg = wsum / n_in;
+        if (npt) {
+            /* the estimator of Sec. 2 at the step's end: the full force's
+             * virial with the fast force's share replaced by its average */
+            double west = full_virial_fd(&md, x) - wlast + wsum / n_in;
+            baro[1] = orc_baro_force(n, orc_kinetic(n, v, mass), west, box_io, baro_par[0]);
+            baro[0] += 0.5 * Delta * baro[1];
+        }
     }
     return U;
 }

@@ -686,3 +686,71 @@ def test_nc_virial_is_translation_invariant_under_pbc():
                        sy.bond_r0, sy.box)
     _, _, W2 = O.nc_forces(shifted, ns, nb, with_virial=True)
     assert abs(W2 - W) <= 1e-9 * abs(W)
+
+
+# --------------------------------------------------------------- barostat --
+
+def test_baro_drift_is_the_exact_flow():
+    # the piston's A half-step: x(h) solves dx/dt = v + b x with v fixed
+    # (checked against an RK4 integration), velocities scale by e^(-a h),
+    # the box by e^(b h); two half-steps equal one step when a = 0
+    rng = np.random.default_rng(12)
+    x0, v0 = rng.normal(0, 5, (7, 3)), rng.normal(0, 0.01, (7, 3))
+    h, b, a = 2.0, 3e-5, 4e-5
+    x, v, box = x0.copy(), v0.copy(), np.array([20.0, 21.0, 22.0])
+    O.baro_drift(x, v, box, h, b, a)
+    sol = integrate.solve_ivp(lambda t, y: (v0.reshape(-1) + b * y), (0, h), x0.reshape(-1), method="RK45",
+                              rtol=1e-12, atol=1e-12)
+    assert np.abs(x - sol.y[:, -1].reshape(-1, 3)).max() < 1e-9
+    assert np.allclose(v, v0 * math.exp(-a * h), rtol=1e-14, atol=0)
+    assert np.allclose(box, np.array([20.0, 21.0, 22.0]) * math.exp(b * h), rtol=1e-14, atol=0)
+    x1, v1, b1 = x0.copy(), v0.copy(), np.ones(3)
+    O.baro_drift(x1, v1, b1, h, b, 0.0)
+    x2, v2, b2 = x0.copy(), v0.copy(), np.ones(3)
+    O.baro_drift(x2, v2, b2, h / 2, b, 0.0)
+    O.baro_drift(x2, v2, b2, h / 2, b, 0.0)
+    assert np.abs(x1 - x2).max() < 1e-12 and np.allclose(b1, b2, rtol=1e-14)
+    # b = 0 is the plain drift
+    x3, v3, b3 = x0.copy(), v0.copy(), np.ones(3)
+    O.baro_drift(x3, v3, b3, h, 0.0, 0.0)
+    assert np.allclose(x3, x0 + h * v0, rtol=0, atol=1e-14)
+
+
+def test_baro_pressure_units_and_force():
+    # 1 kcal/mol/A^3 = 68,568.4 atm (SI-derived tabulated value); the piston
+    # force is (1 + 3/N_f) 2K - W - 3 V P
+    c = -O.baro_force(10, 0.0, 0.0, np.ones(3), 1.0) / 3.0
+    assert abs(c * 68568.4 - 1.0) < 1e-5
+    n, K, W, box, P = 30, 40.0, -12.5, np.array([10.0, 11.0, 12.0]), 250.0
+    assert math.isclose(O.baro_force(n, K, W, box, P), (1 + 1.0 / n) * 2 * K - W - 3 * 1320.0 * P * c, rel_tol=1e-13)
+    kB = 8.314462618 / 4184.0
+    assert math.isclose(O.baro_mass(n, 300.0, 2000.0), (3 * n + 3) * kB * 300.0 * 2000.0 ** 2, rel_tol=1e-13)
+
+
+def test_baro_ideal_gas_volume_distribution():
+    # an ideal gas (no forces) under the piston samples the isothermal-
+    # isobaric volume density V^N exp(-P V / kT): <V> = (N + 1) kT / P and
+    # var(V) / <V>^2 = 1 / (N + 1)
+    n = 64
+    sy = _free_gas(n, 0)
+    sy.box = np.full(3, 10.0)
+    cs, cb = S.cons_spec(1, 4, 0), S.cons_weights(S.cons_spec(1, 4, 0), 1)
+    m = sy.element_masses()
+    kB, T = 8.314462618 / 4184.0, 300.0
+    v = S.maxwell_boltzmann(m, T, 5)
+    st = O.MDState(sy, v, m)
+    c = -O.baro_force(10, 0.0, 0.0, np.ones(3), 1.0) / 3.0    # kcal/mol/A^3 per atm
+    v_target = 1000.0
+    p_atm = (n + 1) * kB * T / v_target / c
+    box = np.full(3, 10.0)
+    baro = np.zeros(3)
+    vols = []
+    for _ in range(400):
+        O.respa_run(st, sy, cs, cb, cs, cb, 4.0, 2, T, np.full(5, 5.0), 3, n_outer=20,
+                    inner_mode=2, outer_mode=1, barostat=(p_atm, 0.2, box, baro))
+        vols.append(float(np.prod(box)))
+    vols = np.array(vols[40:])
+    rel_sd = 1.0 / math.sqrt(n + 1)
+    n_eff = len(vols) / 4.0          # samples 80 fs apart, correlation ~ tau_P = 200 fs
+    assert abs(vols.mean() / v_target - 1.0) < 4 * rel_sd / math.sqrt(n_eff)
+    assert abs(vols.var() / vols.mean() ** 2 * (n + 1) - 1.0) < 0.35
