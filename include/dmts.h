@@ -260,6 +260,23 @@ typedef struct {
     int mode;                  /* dmts_mode */
     float skin;                /* neighbour-list skin (A); lists rebuilt when an atom moved > skin/2 */
     int thermostat;            /* dmts_thermostat */
+    /* Barostat (RESPA mode, periodic replicas; Sec. 3: Bussi's barostat, target
+     * pressure and volume relaxation time), read as an isotropic Langevin
+     * piston on epsilon = ln(V)/3 with mass W = (N_f + 3) kB T tau_P^2
+     * (N_f = 3 n), friction 1/tau_P and matching noise, coupled to the atoms
+     * as in the Martyna-Tobias-Klein equations and driven by the virial
+     * estimator of Sec. 2 "Computation of the virial term in NPT". Per outer
+     * step: p_eps += Delta/2 G; p_eps <- c p_eps + sqrt((1 - c^2) W kB T) xi
+     * (c = exp(-Delta/tau_P), xi the first Gaussian of Philox at (seed,
+     * replica, step, atom slot 2^32 - 1)); every A half-step h of the outer
+     * step moves x <- x e^(b h) + h (e^(b h) - 1)/(b h) v, v <- v e^(-a h),
+     * box <- box e^(b h) (b = p_eps/W, a = (1 + 3/N_f) b); at the step's end
+     * G = (1 + 3/N_f) 2K - W_est - 3 V P and p_eps += Delta/2 G. The box of
+     * each replica (dmts_system.box) is updated in place. Needs st->baro and
+     * the three virial arrays of the state. */
+    int barostat;              /* 0 off, 1 on */
+    float pressure_atm;        /* target pressure (atm) */
+    float tau_p_ps;            /* volume relaxation time tau_P (ps) */
 } dmts_integrator;
 
 /*
@@ -291,6 +308,9 @@ typedef struct {
                                   end of the outer step with the fast force's share at that configuration
                                   replaced by its average over the inner steps,
                                   virial_cons - W_NC(q_end) + virial_nc; in STS mode virial_cons */
+    double *baro;              /* device double [n_replicas][3] (may be NULL unless the barostat is on):
+                                  p_eps (kcal/mol fs), the piston force G at the last step end, and a
+                                  flag (1 once G is set; start from zeros) */
 } dmts_state;
 
 /*

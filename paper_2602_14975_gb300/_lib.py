@@ -52,7 +52,8 @@ class Nbr(ct.Structure):
 class Integrator(ct.Structure):
     _fields_ = [("dt_outer", ct.c_float), ("n_inner", ct.c_int), ("temperature", ct.c_float),
                 ("gamma_ps", ct.c_double * MAX_SPECIES), ("mode", ct.c_int), ("skin", ct.c_float),
-                ("thermostat", ct.c_int)]
+                ("thermostat", ct.c_int), ("barostat", ct.c_int), ("pressure_atm", ct.c_float),
+                ("tau_p_ps", ct.c_float)]
 
 
 class Guard(ct.Structure):
@@ -70,7 +71,7 @@ class State(ct.Structure):
                 ("masses", ct.c_void_p), ("energy", ct.c_void_p), ("step", ct.c_void_p),
                 ("seed", ct.c_void_p), ("replica_id", ct.c_void_p), ("first_step", ct.c_int),
                 ("internal", ct.c_void_p), ("virial_nc", ct.c_void_p), ("virial_cons", ct.c_void_p),
-                ("virial_est", ct.c_void_p)]
+                ("virial_est", ct.c_void_p), ("baro", ct.c_void_p)]
 
 
 class Request(ct.Structure):

@@ -203,17 +203,20 @@ def forces_nc(ctx: Context, dsys: DeviceSystem, nbr: NbrList, with_bonds=True, w
 
 
 def integrator(dt_outer, n_inner, temperature, gamma_ps, mode=L.MODE_RESPA, skin=0.5,
-               thermostat=L.LANGEVIN) -> L.Integrator:
-    """Integrator parameters; thermostat L.LANGEVIN or L.FFL (Fast Forward Langevin)."""
+               thermostat=L.LANGEVIN, barostat=False, pressure_atm=1.0, tau_p_ps=2.0) -> L.Integrator:
+    """Integrator parameters; thermostat L.LANGEVIN or L.FFL (Fast Forward
+    Langevin); barostat: the stochastic piston at pressure_atm with relaxation
+    time tau_p_ps (the state needs virial=True, barostat=True)."""
     g = (ct.c_double * L.MAX_SPECIES)(*([float(v) for v in gamma_ps] + [0.0] * (L.MAX_SPECIES - len(gamma_ps))))
     return L.Integrator(float(dt_outer), int(n_inner), float(temperature), g, int(mode), float(skin),
-                        int(thermostat))
+                        int(thermostat), int(bool(barostat)), float(pressure_atm), float(tau_p_ps))
 
 
 class MDState:
     """Device-resident dynamic state of a batch (positions live in dsys.x)."""
 
-    def __init__(self, dsys: DeviceSystem, v, masses, seeds, replica_ids=None, steps=None, virial=False):
+    def __init__(self, dsys: DeviceSystem, v, masses, seeds, replica_ids=None, steps=None, virial=False,
+                 barostat=False):
         dev = dsys.x.device
         self.dsys = dsys
         self.v = torch.as_tensor(np.asarray(v, np.float32)).to(dev).contiguous()
@@ -235,9 +238,11 @@ class MDState:
         self.virial_nc = torch.zeros(R, dtype=torch.float64, device=dev) if virial else None
         self.virial_cons = torch.zeros(R, dtype=torch.float64, device=dev) if virial else None
         self.virial_est = torch.zeros(R, dtype=torch.float64, device=dev) if virial else None
+        # with barostat=True: per replica the piston momentum, its last force and a set flag
+        self.baro = torch.zeros(R, 3, dtype=torch.float64, device=dev) if barostat else None
         self.c = L.State(dsys.struct(), _ptr(self.v), _ptr(self.f_nc), _ptr(self.f_cons), _ptr(self.masses),
                          _ptr(self.energy), _ptr(self.step), _ptr(self.seed), _ptr(self.replica_id), 1, None,
-                         _ptr(self.virial_nc), _ptr(self.virial_cons), _ptr(self.virial_est))
+                         _ptr(self.virial_nc), _ptr(self.virial_cons), _ptr(self.virial_est), _ptr(self.baro))
         self.ctx = None
 
     def lists(self, which: int) -> NbrList:

@@ -453,7 +453,7 @@ void state_force_rebuild(dmts_ctx *ctx, dmts_state *stt, cudaStream_t st) {
 
 // Host-side grid set-up for every replica (box and offsets copied to host).
 dmts_status setup_grids(dmts_ctx *ctx, const std::vector<int> &rep_off, const std::vector<float> &box,
-                        float r_list, std::vector<CellGrid> &grids, int &n_cells) {
+                        float r_list, std::vector<CellGrid> &grids, int &n_cells, float grid_margin) {
     const int R = (int)rep_off.size() - 1;
     grids.resize(R);
     n_cells = 0;
@@ -467,7 +467,7 @@ dmts_status setup_grids(dmts_ctx *ctx, const std::vector<int> &rep_off, const st
             if (periodic) {
                 if (!(r_list < 0.5f * L)) return fail(ctx, DMTS_E_INVALID, "list cutoff must be < box/2");
                 g.box[a] = L;
-                g.dim[a] = std::max(1, std::min(64, (int)std::floor(L / r_list)));
+                g.dim[a] = std::max(1, std::min(64, (int)std::floor(L / (r_list * (1.f + grid_margin)))));
                 g.org[a] = 0.f;
                 g.inv_h[a] = (float)g.dim[a] / L;
             } else {
@@ -545,6 +545,7 @@ void prepare_nbr_work_async(dmts_ctx *ctx, StateInternal *si, const SysView &v, 
     nw.total = (long long *)b.total.p;
     nw.gate = (int *)si->gate.p;
     nw.err = ctx->d_err;
+    nw.box = v.box;
 }
 
 }  // namespace dmts
@@ -604,13 +605,16 @@ void free_state_internal(StateInternal *si) {
     si->gate.release();
     si->atom_rep.release();
     si->ms_part.release();
+    si->baro_ke.release();
+    si->baro_K.release();
+    si->baro_f.release();
     si->scratch.release_all();
     delete si;
 }
 
 // Allocates lists (capacity from a first count with 40 % head-room) and the
 // cell grids; leaves the lists built for the current positions.
-dmts_status init_state(dmts_ctx *ctx, dmts_state *stt, float skin, cudaStream_t st) {
+dmts_status init_state(dmts_ctx *ctx, dmts_state *stt, float skin, cudaStream_t st, float grid_margin) {
     const dmts_system *sys = &stt->sys;
     StateInternal *si = (StateInternal *)stt->internal;
     if (!si) {
@@ -624,9 +628,10 @@ dmts_status init_state(dmts_ctx *ctx, dmts_state *stt, float skin, cudaStream_t 
     si->n = sys->n_atoms;
     si->n_rep = sys->n_replicas;
     si->skin = skin;
+    si->grid_margin = grid_margin;
     si->r_cons = std::max(ctx->cons.rc, ctx->prior.lj_rc) + skin;
     si->r_nc = (ctx->has_nc ? ctx->nc.rc : 0.f) + skin;
-    dmts_status s = setup_grids(ctx, rep_off, box, si->r_cons, si->grids, si->n_cells);
+    dmts_status s = setup_grids(ctx, rep_off, box, si->r_cons, si->grids, si->n_cells, grid_margin);
     if (s != DMTS_OK) return s;
     const int N = si->n;
     if (!si->atom_rep.ensure(sizeof(int) * (N + 1)) || !si->x_ref.ensure(sizeof(float) * 3 * (N + 1)) ||
@@ -641,6 +646,7 @@ dmts_status init_state(dmts_ctx *ctx, dmts_state *stt, float skin, cudaStream_t 
     NbrWork nw;
     s = prepare_nbr_work(ctx, si->scratch, v, si->grids, si->n_cells, (int *)si->gate.p, nw, st);
     if (s != DMTS_OK) return s;
+    nw.box = v.box;
     nbr_cells(nw, si->r_cons, st);
     // size the lists from a count pass
     nbr_fill(nw, si->r_cons, (int *)si->cons_row.p, nullptr, -1, nullptr, st);
@@ -922,11 +928,14 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
         return fail(ctx, DMTS_E_INVALID, "missing bond table");
     if (stt->virial_est && (!stt->virial_cons || (!sts && !stt->virial_nc)))
         return fail(ctx, DMTS_E_INVALID, "virial_est needs virial_cons and virial_nc");
+    const bool npt = !sts && p->barostat;
+    if (npt && (!stt->baro || !stt->virial_est || !(p->tau_p_ps > 0.f)))
+        return fail(ctx, DMTS_E_INVALID, "the barostat needs st->baro, the virial arrays and tau_p_ps > 0");
     cudaSetDevice(ctx->device);
     if (stt->virial_est && !sts && !ctx->ws.nc_w_last.ensure(sizeof(double) * stt->sys.n_replicas))
         return fail(ctx, DMTS_E_OOM, "workspace allocation failed");
     if (!stt->internal) {
-        s = init_state(ctx, stt, p->skin, st);
+        s = init_state(ctx, stt, p->skin, st, npt ? kBaroGridMargin : 0.f);
         if (s != DMTS_OK) {
             free_state_internal((StateInternal *)stt->internal);
             stt->internal = nullptr;
@@ -936,6 +945,12 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
     StateInternal *si = (StateInternal *)stt->internal;
     if (si->n != stt->sys.n_atoms || si->n_rep != stt->sys.n_replicas || si->skin != p->skin)
         return fail(ctx, DMTS_E_INVALID, "state shape changed; release the state first");
+    if (npt && si->grid_margin < kBaroGridMargin)
+        return fail(ctx, DMTS_E_INVALID, "state built without the barostat's cell margin; release it first");
+    if (npt && (!si->baro_ke.ensure(sizeof(float) * (stt->sys.n_atoms + 1)) ||
+                !si->baro_K.ensure(sizeof(double) * stt->sys.n_replicas) ||
+                !si->baro_f.ensure(sizeof(float) * 3 * stt->sys.n_replicas)))
+        return fail(ctx, DMTS_E_OOM, "barostat workspace allocation failed");
     const SysView v = state_view(stt);
     const int *crow = (int *)si->cons_row.p, *ccol = (int *)si->cons_col.p;
     const int *nrow = (int *)si->nc_row.p, *ncol = (int *)si->nc_col.p;
@@ -992,6 +1007,34 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
     ia.h_in = (float)(0.5 * delta);
     ia.h_out = 0.5f * p->dt_outer;
     if (n_outer == 0) return DMTS_OK;
+    BaroArgs ba;
+    memset(&ba, 0, sizeof ba);
+    if (npt) {
+        ba.n_rep = v.n_rep;
+        ba.rep_off = v.rep_off;
+        ba.baro = stt->baro;
+        ba.box = const_cast<float *>(stt->sys.box);
+        ba.K = (const double *)si->baro_K.p;
+        ba.baro_f = (float *)si->baro_f.p;
+        ba.seed = stt->seed;
+        ba.rep_id = stt->replica_id;
+        ba.step = stt->step;
+        ba.delta_outer = p->dt_outer;
+        ba.h = 0.5 * delta;
+        ba.p_kcal = (double)p->pressure_atm * kKcalPerA3PerAtm;
+        ba.tau_fs = (double)p->tau_p_ps * 1e3;
+        ba.kT = kBoltzmann * p->temperature;
+        ba.err = ctx->d_err;
+        ia.baro_f = (const float *)si->baro_f.p;
+        ia.box = ba.box;
+        // kinetic energy now, for a piston force not yet set (the full force's virial)
+        IntegArgs ik = ia;
+        ik.ops = 0;
+        ik.baro_f = nullptr;
+        ik.ke = (float *)si->baro_ke.p;
+        launch_integrate(ik, st);
+        launch_replica_sum((const float *)si->baro_ke.p, v.rep_off, v.n_rep, (double *)si->baro_K.p, 0, st);
+    }
     // outer steps not timed under a sampling profiler; calls outside the loop are
     struct ActiveReset {
         dmts_ctx *c;
@@ -1005,8 +1048,14 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
         if (!sts && stt->virial_nc &&
             !ck(ctx, cudaMemsetAsync(stt->virial_nc, 0, sizeof(double) * v.n_rep, st), "virial reset"))
             return DMTS_E_CUDA;
+        if (npt) {
+            ba.wvir = stt->virial_cons;
+            ba.step_add = (uint64_t)o * n_in;
+            launch_baro_start(ba, st);
+        }
         for (int k = 0; k < n_in; ++k) {
             if (sts) ia.ops = (o == 0 ? 0 : OP_CLOSE_B) | OP_BAOA;
+            else if (k == 0 && npt) ia.ops = OP_KICK_L2 | OP_BAOA;   // the previous step closed itself
             else if (k == 0) ia.ops = (o == 0 ? OP_KICK_L2 : (OP_CLOSE_B | OP_KICK_L | OP_KICK_L2)) | OP_BAOA;
             else ia.ops = OP_CLOSE_B | OP_BAOA;
             ia.step_add = (uint64_t)o * n_in + k;
@@ -1034,9 +1083,21 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
                                        stt->virial_nc, v.n_rep, st);
             }
         }
+        if (npt) {
+            // close the outer step, then the piston's half kick with the estimator
+            ia.ops = OP_CLOSE_B | OP_KICK_L;
+            ia.ke = (float *)si->baro_ke.p;
+            { ProfScope ps(ctx, "integrate", st); launch_integrate(ia, st); }
+            ia.ke = nullptr;
+            launch_replica_sum((const float *)si->baro_ke.p, v.rep_off, v.n_rep, (double *)si->baro_K.p, 0, st);
+            ba.wvir = stt->virial_est;
+            { ProfScope ps(ctx, "barostat", st); launch_baro_end(ba, st); }
+        }
     }
-    ia.ops = sts ? OP_CLOSE_B : (OP_CLOSE_B | OP_KICK_L);
-    { ProfScope ps(ctx, "integrate", st); launch_integrate(ia, st); }
+    if (!npt) {
+        ia.ops = sts ? OP_CLOSE_B : (OP_CLOSE_B | OP_KICK_L);
+        { ProfScope ps(ctx, "integrate", st); launch_integrate(ia, st); }
+    }
     launch_advance_step(stt->step, v.n_rep, (uint64_t)n_outer * n_in, ctx->d_err, st);
     return ck(ctx, cudaGetLastError(), "respa_step launch") ? DMTS_OK : DMTS_E_CUDA;
 }

@@ -13,6 +13,7 @@ namespace dmts {
 constexpr float kAccConv = 4.184e-4f;          // (kcal/mol/A)/amu -> A/fs^2
 constexpr double kAccConvD = 4.184e-4;
 constexpr double kBoltzmann = 8.314462618 / 4184.0;   // kcal/mol/K
+constexpr double kKcalPerA3PerAtm = 101325.0 * 6.02214076e23 * 1e-30 / 4184.0;   // 1 atm in kcal/mol/A^3
 
 // Sticky device error word (one per context).
 // Host-side count of this library's kernel launches (every launch site calls

@@ -82,9 +82,10 @@ struct SysView {
 
 struct StateInternal {
     int n = 0, n_rep = 0, n_cells = 0;
-    float skin = 0.f, r_cons = 0.f, r_nc = 0.f;
+    float skin = 0.f, r_cons = 0.f, r_nc = 0.f, grid_margin = 0.f;
     std::vector<CellGrid> grids;
     Buf cons_row, cons_col, nc_row, nc_col, x_ref, gate, atom_rep, ms_part;
+    Buf baro_ke, baro_K, baro_f;   // barostat: per-atom kinetic energy, per-replica sum, drift factors
     long long cons_cap = 0, nc_cap = 0;
     NbrScratch scratch;
 };
@@ -151,8 +152,10 @@ dmts_status cons_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const
                       float *forces, int flags, cudaStream_t st, double *virial = nullptr);
 dmts_status nc_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const int *col, float *forces,
                     double *net, int flags, cudaStream_t st, double *virial = nullptr, int virial_accumulate = 0);
+// grid_margin: periodic cell edges are at least r_list (1 + grid_margin), so
+// that the box may shrink by that fraction (a barostat) before a rebuild fails.
 dmts_status setup_grids(dmts_ctx *ctx, const std::vector<int> &rep_off, const std::vector<float> &box,
-                        float r_list, std::vector<CellGrid> &grids, int &n_cells);
+                        float r_list, std::vector<CellGrid> &grids, int &n_cells, float grid_margin = 0.f);
 SysView state_view(dmts_state *stt);
 RepTable rep_table(const dmts_ctx *ctx);
 void rebuild_lists(dmts_ctx *ctx, StateInternal *si, const SysView &v, cudaStream_t st);
@@ -164,5 +167,8 @@ void prepare_nbr_work_async(dmts_ctx *ctx, StateInternal *si, const SysView &v, 
 
 // (Re)initialises st->internal for the current shape of st->sys, re-using
 // its buffers when present; leaves the lists built for the current positions.
-dmts_status init_state(dmts_ctx *ctx, dmts_state *stt, float skin, cudaStream_t st);
+dmts_status init_state(dmts_ctx *ctx, dmts_state *stt, float skin, cudaStream_t st, float grid_margin = 0.f);
+// Cell margin of states integrated with the barostat: the box may shrink by
+// this fraction before a list rebuild reports DMTS_E_INVALID.
+constexpr float kBaroGridMargin = 0.05f;
 void free_state_internal(dmts::StateInternal *si);

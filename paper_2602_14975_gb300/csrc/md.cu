@@ -629,8 +629,19 @@ __global__ void k_integrate(IntegArgs g) {
         const float h = g.h_in * am;
         vx = fmaf(h, sfx, vx); vy = fmaf(h, sfy, vy); vz = fmaf(h, sfz, vz);
         float x = g.x[3 * i], y = g.x[3 * i + 1], z = g.x[3 * i + 2];
-        x = fmaf(g.h_in, vx, x); y = fmaf(g.h_in, vy, y); z = fmaf(g.h_in, vz, z);
         const int r = g.atom_rep[i];
+        float bs = 1.f, bp = g.h_in, bv = 1.f;   // A half-step: x <- bs x + bp v, then v <- bv v
+        if (g.baro_f) {
+            bs = g.baro_f[3 * r]; bp = g.baro_f[3 * r + 1]; bv = g.baro_f[3 * r + 2];
+            x = fmaf(bp, vx, bs * x); y = fmaf(bp, vy, bs * y); z = fmaf(bp, vz, bs * z);
+            vx *= bv; vy *= bv; vz *= bv;
+            if (i == g.rep_off[r]) {
+                const float s2 = bs * bs;   // both half-steps of this inner step
+                g.box[3 * r] *= s2; g.box[3 * r + 1] *= s2; g.box[3 * r + 2] *= s2;
+            }
+        } else {
+            x = fmaf(g.h_in, vx, x); y = fmaf(g.h_in, vy, y); z = fmaf(g.h_in, vz, z);
+        }
         const int local = i - g.rep_off[r];
         const float3 G = gauss3(g.seed[r], g.rep_id[r], g.step[r] + g.step_add, (uint32_t)local);
         const int sp = g.species[i];
@@ -644,7 +655,12 @@ __global__ void k_integrate(IntegArgs g) {
         } else {
             vx = wx; vy = wy; vz = wz;
         }
-        x = fmaf(g.h_in, vx, x); y = fmaf(g.h_in, vy, y); z = fmaf(g.h_in, vz, z);
+        if (g.baro_f) {
+            x = fmaf(bp, vx, bs * x); y = fmaf(bp, vy, bs * y); z = fmaf(bp, vz, bs * z);
+            vx *= bv; vy *= bv; vz *= bv;
+        } else {
+            x = fmaf(g.h_in, vx, x); y = fmaf(g.h_in, vy, y); z = fmaf(g.h_in, vz, z);
+        }
         if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(vx) && isfinite(vy) && isfinite(vz)))
             set_error(g.err, DMTS_E_NONFINITE);
         g.x[3 * i] = x; g.x[3 * i + 1] = y; g.x[3 * i + 2] = z;
@@ -654,11 +670,70 @@ __global__ void k_integrate(IntegArgs g) {
         }
     }
     g.v[3 * i] = vx; g.v[3 * i + 1] = vy; g.v[3 * i + 2] = vz;
+    if (g.ke) g.ke[i] = 0.5f * (vx * vx + vy * vy + vz * vz) / am;   // m v^2 / 2 in kcal/mol
 }
 
 void launch_integrate(const IntegArgs &a, cudaStream_t st) {
     if (a.n_atoms == 0) return;
     k_integrate<<<(a.n_atoms + 255) / 256, 256, 0, st>>>(a);
+    count_launch();
+}
+
+// ---------------------------------------------------------------- barostat
+// One thread per replica; open replicas (box 0) keep p_eps = 0 and plain
+// drift factors. N_f = 3 n_r, W = (N_f + 3) kB T tau_P^2.
+__device__ __forceinline__ double baro_force(const BaroArgs &a, int r, int n) {
+    const double V = (double)a.box[3 * r] * a.box[3 * r + 1] * a.box[3 * r + 2];
+    return (1.0 + 1.0 / n) * 2.0 * a.K[r] - a.wvir[r] - 3.0 * V * a.p_kcal;
+}
+
+__global__ void k_baro_start(BaroArgs a) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= a.n_rep || *a.err) return;
+    const int n = a.rep_off[r + 1] - a.rep_off[r];
+    double *b = a.baro + 3 * r;
+    float *f = a.baro_f + 3 * r;
+    if (n == 0 || !(a.box[3 * r] > 0.f)) {
+        b[0] = 0.0;
+        f[0] = 1.f; f[1] = (float)a.h; f[2] = 1.f;
+        return;
+    }
+    const double W = (3.0 * n + 3.0) * a.kT * a.tau_fs * a.tau_fs;
+    if (b[2] == 0.0) {   // no estimator yet: the full force's virial
+        b[1] = baro_force(a, r, n);
+        b[2] = 1.0;
+    }
+    const double c = exp(-a.delta_outer / a.tau_fs);
+    const float3 G = gauss3(a.seed[r], a.rep_id[r], a.step[r] + a.step_add, 0xFFFFFFFFu);
+    double p = b[0] + 0.5 * a.delta_outer * b[1];
+    p = c * p + sqrt((1.0 - c * c) * W * a.kT) * (double)G.x;
+    b[0] = p;
+    const double beta = p / W, alpha = (1.0 + 1.0 / n) * beta, z = beta * a.h;
+    f[0] = (float)exp(z);
+    f[1] = (float)(z != 0.0 ? a.h * expm1(z) / z : a.h);
+    f[2] = (float)exp(-alpha * a.h);
+}
+
+__global__ void k_baro_end(BaroArgs a) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= a.n_rep || *a.err) return;
+    const int n = a.rep_off[r + 1] - a.rep_off[r];
+    double *b = a.baro + 3 * r;
+    if (n == 0 || !(a.box[3 * r] > 0.f)) return;
+    b[1] = baro_force(a, r, n);
+    b[2] = 1.0;
+    b[0] += 0.5 * a.delta_outer * b[1];
+}
+
+void launch_baro_start(const BaroArgs &a, cudaStream_t st) {
+    if (a.n_rep == 0) return;
+    k_baro_start<<<(a.n_rep + 127) / 128, 128, 0, st>>>(a);
+    count_launch();
+}
+
+void launch_baro_end(const BaroArgs &a, cudaStream_t st) {
+    if (a.n_rep == 0) return;
+    k_baro_end<<<(a.n_rep + 127) / 128, 128, 0, st>>>(a);
     count_launch();
 }
 

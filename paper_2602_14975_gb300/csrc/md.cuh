@@ -103,8 +103,32 @@ struct IntegArgs {
     int *err;
     int ffl;                       // O-step: 0 Langevin, 1 Fast Forward Langevin
     unsigned *fl_max;              // nullable: per-replica running max of |F_slow - F_fast| (float bits)
+    const float *baro_f;           // nullable: per replica [3] = e^(b h), h (e^(b h) - 1)/(b h), e^(-a h)
+    float *box;                    // with baro_f: per-replica box, scaled by e^(2 b h) per BAOA
+    float *ke;                     // nullable: per-atom kinetic energy m v^2 / 2 (kcal/mol) after the update
 };
 void launch_integrate(const IntegArgs &a, cudaStream_t st);
+
+// Barostat of the outer step (piston on epsilon = ln(V)/3; see dmts_integrator).
+struct BaroArgs {
+    int n_rep;
+    const int *rep_off;
+    double *baro;                  // [R][3]: p_eps, G, flag
+    float *box;                    // [R][3]
+    const double *K;               // [R] kinetic energy (kcal/mol)
+    const double *wvir;            // [R] virial: the estimator (end) or the full force's (first start)
+    float *baro_f;                 // [R][3] out (start): the A half-step factors
+    const uint64_t *seed;
+    const uint32_t *rep_id;
+    const uint64_t *step;
+    uint64_t step_add;
+    double delta_outer, h, p_kcal, tau_fs, kT;
+    const int *err;
+};
+// start of an outer step: G (when unset), half kick, Ornstein-Uhlenbeck step, factors
+void launch_baro_start(const BaroArgs &a, cudaStream_t st);
+// end of an outer step: G from K and the estimator, half kick
+void launch_baro_end(const BaroArgs &a, cudaStream_t st);
 void launch_advance_step(uint64_t *step, int n_rep, uint64_t add, const int *err, cudaStream_t st);
 void launch_embed(int n, int C, const uint8_t *species, const float *emb, float *s, cudaStream_t st);
 void launch_rowsum(int n, int C, const float *u, float scale, float *e_atom, cudaStream_t st);

@@ -29,7 +29,18 @@ __global__ void k_grid_open(NbrWork w, float r_list) {
     CellGrid &g = w.grid[r];
     const int nc = g.dim[0] * g.dim[1] * g.dim[2];
     for (int c = threadIdx.x; c < nc; c += blockDim.x) w.cell_cnt[g.cell_off + c] = 0;
-    if (g.box[0] > 0.f) return;   // periodic: fixed on the host
+    if (g.box[0] > 0.f) {
+        // periodic: cell counts fixed on the host; the edges follow the current box
+        if (w.box && threadIdx.x == 0)
+            for (int a = 0; a < 3; ++a) {
+                const float L = w.box[3 * r + a];
+                g.box[a] = L;
+                g.inv_h[a] = (float)g.dim[a] / L;
+                if (!(L * 1.000001f >= r_list * (float)g.dim[a]) || !(r_list < 0.5f * L))
+                    set_error(w.err, DMTS_E_INVALID);   // the box shrank below the cell grid
+            }
+        return;
+    }
     __shared__ float red[6][32];
     float mn[3] = {3.4e38f, 3.4e38f, 3.4e38f}, mx[3] = {-3.4e38f, -3.4e38f, -3.4e38f};
     const int beg = w.rep_off[r], end = w.rep_off[r + 1];

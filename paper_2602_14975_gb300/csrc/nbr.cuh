@@ -36,6 +36,8 @@ struct NbrWork {
     int *counts_sub = nullptr;   // [n_atoms]: row lengths of the sub-list (nbr_fill with a sub-list)
     int *slots = nullptr;        // [n_atoms][slot_cap] (nullable): sorted rows kept by the count pass
     int slot_cap = 0;
+    const float *box = nullptr;  // [n_rep][3] (nullable): current boxes; periodic grids follow them at each
+                                 // rebuild (a barostat moves the box)
 };
 
 // Builds the cell structure (assign, count, scan, scatter, sort).

@@ -383,6 +383,62 @@ def test_virial_estimator_needs_its_parts(ctx1, water):
     st.release()
 
 
+def _npt_start(water, models1):
+    """Initial kinetic energy, full-force virial (oracle) and the pressure in
+    atm at which the piston force starts near zero."""
+    (cs, cb), _ = models1
+    m, v = _md_setup(water)
+
+    def energy(lam):
+        sy = S.System(water.name, water.x * lam, water.species, water.mol_id, water.bonds, water.bond_r0,
+                      water.box * lam)
+        return O.cons_energy(sy, cs, cb) + O.prior(sy)[0]
+
+    h = 1e-6
+    W = (energy(1 + h) - energy(1 - h)) / (2 * h)
+    K = O.kinetic(v, m)
+    c = -O.baro_force(10, 0.0, 0.0, np.ones(3), 1.0) / 3.0
+    return m, v, (2 * K - W) / (3 * np.prod(water.box)) / c
+
+
+def test_npt_matches_oracle(ctx1, models1, water):
+    """Algorithm 1 with the barostat (piston on ln V / 3 driven by the virial
+    estimator, MTK coupling in every A half-step): 10 outer steps against the
+    oracle's trajectory, positions within the 10-step tolerance, box and
+    piston momentum close, and the box moved."""
+    (cs, cb), (ns, nb_) = models1
+    m, v, p_atm = _npt_start(water, models1)
+    tau = 0.2
+    d = core.DeviceSystem(water)
+    st = core.MDState(d, v, m.astype(np.float32), seeds=191, virial=True, barostat=True)
+    integ = core.integrator(4.0, 4, 300.0, [1.0] * 5, skin=0.5, barostat=True, pressure_atm=p_atm, tau_p_ps=tau)
+    core.respa_step(ctx1, st, integ, 6)
+    core.respa_step(ctx1, st, integ, 4)      # state (piston, box) carried across calls
+    ctx1.sync()
+    x = d.x.cpu().numpy()
+    box = d.box.cpu().numpy().reshape(-1)
+    baro = st.baro.cpu().numpy()[0]
+    st.release()
+    ref = O.MDState(water, v, m.astype(np.float32).astype(np.float64))
+    rbox, rbaro = np.array(water.box, np.float64), np.zeros(3)
+    O.respa_run(ref, water, cs, cb, ns, nb_, 4.0, 4, 300.0, np.full(5, 1.0), 191, 10,
+                barostat=(p_atm, tau, rbox, rbaro))
+    assert np.abs(x - ref.x).max() <= TOL_POS, np.abs(x - ref.x).max()
+    assert np.abs(box / rbox - 1.0).max() <= 1e-6, (box, rbox)
+    assert abs(box[0] / water.box[0] - 1.0) > 1e-6      # the piston moved the box
+    assert abs(baro[0] - rbaro[0]) <= 1e-3 * abs(rbaro[0]) + 1e-2, (baro, rbaro)
+    assert baro[2] == 1.0
+
+
+def test_npt_needs_its_arrays(ctx1, water):
+    m, v = _md_setup(water)
+    d = core.DeviceSystem(water)
+    st = core.MDState(d, v, m.astype(np.float32), seeds=191, virial=True)    # no piston state
+    with pytest.raises(core.L.DmtsError):
+        core.respa_step(ctx1, st, core.integrator(4.0, 4, 300.0, [1.0] * 5, skin=0.5, barostat=True), 1)
+    st.release()
+
+
 # ------------------------------------------------------------------ Philox --
 
 def test_philox_words_bit_exact(ctx1):
