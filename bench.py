@@ -34,6 +34,7 @@ LARGE_WORKLOAD = "water_100000"
 # while the kernel's sources hash to the recorded value; after any change to
 # them it is null until a new capture is taken.
 PROF_EVERY = 4   # time every 4th outer step of the timed region per kernel
+KCAL_A3_PER_ATM = 101325.0 * 6.02214076e23 * 1e-30 / 4184.0   # 1 atm in kcal/mol/A^3
 
 NCU_TRAFFIC = {
     "mp_bwd": {"bytes_per_launch": (153771520 + 15115008 + 154084864 + 12173312 + 141766912 + 233728) / 3,
@@ -377,6 +378,37 @@ def main():
                                 "max_force_disagreement": float(np.max(gs["chunk_max"])) if gs["n_chunks"] else None})
         sg.release()
 
+    # --------------------------------------------------------------- NPT
+    # the same outer step with the barostat (piston relaxation time 2 ps as in
+    # the paper's NPT runs). The random-weight stand-in models sit far from
+    # 1 atm, so the target is their instantaneous pressure at the start (the
+    # full force's virial and the kinetic energy), which keeps the box near
+    # its size over the run
+    dn = core.DeviceSystem(W["system"]())
+    sn = core.MDState(dn, v0, m_hmr.astype(np.float32), seeds=I.seed, replica_ids=[D.replica_id(rank, 0)],
+                      virial=True, barostat=True)
+    i_init = core.integrator(I.dt_outer, I.n_inner, I.temperature, I.gamma_ps, skin=skin, barostat=True)
+    core.respa_step(ctx, sn, i_init, 0)      # lists (with the piston's cell margin) and first forces
+    ctx.sync()
+    k_start = 0.5 * float((m_hmr[:, None] * v0 ** 2).sum()) / 4.184e-4
+    p_start = (2 * k_start - float(sn.virial_cons[0].item())) / (3 * float(np.prod(sy.box))) / KCAL_A3_PER_ATM
+    i_npt = core.integrator(I.dt_outer, I.n_inner, I.temperature, I.gamma_ps, skin=skin, barostat=True,
+                            pressure_atm=p_start, tau_p_ps=2.0)
+    core.respa_step(ctx, sn, i_npt, 2)
+    ctx.sync()
+    barrier()
+    e0.record(stream)
+    core.respa_step(ctx, sn, i_npt, n_side)
+    e1.record(stream)
+    barrier()
+    ctx.sync()
+    ms = max_over_ranks(e0.elapsed_time(e1)) / n_side
+    box_end = dn.box.cpu().numpy().reshape(-1)
+    side["npt"] = {"ns_per_day": ns_per_day(I.dt_outer, 1e3 / ms) * world, "ms_per_step": ms, "steps": n_side,
+                   "pressure_atm": p_start, "tau_p_ps": 2.0,
+                   "box_change": float(box_end[0] / sy.box[0] - 1.0)}
+    sn.release()
+
     # --------------------------------------------------------------- STS
     sts = W["sts"]
     m_el = sy.element_masses()
@@ -611,6 +643,7 @@ def main():
         "kernel_roofline": kr,
         "rewind_guard": side["guarded"],
         "ffl": side["ffl"],
+        "npt": side["npt"],
         "large_system": {"workload": syL.name, "n_atoms": syL.n_atoms, "steps": n_large,
                          "ns_per_day": ns_per_day(IL.dt_outer, 1e3 / ms_large) * world, "ms_per_step": ms_large,
                          "sts_ns_per_day": ns_per_day(stsL.dt_outer, 1e3 / ms_large_sts) * world,
