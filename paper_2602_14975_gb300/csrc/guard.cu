@@ -14,26 +14,29 @@ using namespace dmts;
 namespace {
 
 struct Frame {
-    Buf x, v, f_nc, f_cons, step, energy;
+    Buf x, v, f_nc, f_cons, step, energy, box, baro;
     int first_step = 0;
 
-    bool alloc(int n, int n_rep, bool with_energy) {
+    bool alloc(int n, int n_rep, bool with_energy, bool with_baro) {
         return x.ensure(sizeof(float) * 3 * (size_t)(n + 1)) && v.ensure(sizeof(float) * 3 * (size_t)(n + 1)) &&
                f_nc.ensure(sizeof(float) * 3 * (size_t)(n + 1)) && f_cons.ensure(sizeof(float) * 3 * (size_t)(n + 1)) &&
-               step.ensure(sizeof(uint64_t) * n_rep) && (!with_energy || energy.ensure(sizeof(double) * n_rep));
+               step.ensure(sizeof(uint64_t) * n_rep) && (!with_energy || energy.ensure(sizeof(double) * n_rep)) &&
+               (!with_baro || (box.ensure(sizeof(float) * 3 * n_rep) && baro.ensure(sizeof(double) * 3 * n_rep)));
     }
     void release() {
-        Buf *all[] = {&x, &v, &f_nc, &f_cons, &step, &energy};
+        Buf *all[] = {&x, &v, &f_nc, &f_cons, &step, &energy, &box, &baro};
         for (Buf *b : all) b->release();
     }
 };
 
+// With the barostat the frame also holds the boxes and the piston state.
 bool copy_state(dmts_ctx *ctx, Frame &f, dmts_state *s, bool save, cudaStream_t st) {
     const size_t b3 = sizeof(float) * 3 * (size_t)s->sys.n_atoms;
     const size_t br = (size_t)s->sys.n_replicas;
     struct Pair { void *frame; void *state; size_t bytes; } pairs[] = {
         {f.x.p, s->sys.x, b3}, {f.v.p, s->v, b3}, {f.f_nc.p, s->f_nc, b3}, {f.f_cons.p, s->f_cons, b3},
-        {f.step.p, s->step, sizeof(uint64_t) * br}, {f.energy.p, s->energy, sizeof(double) * br}};
+        {f.step.p, s->step, sizeof(uint64_t) * br}, {f.energy.p, s->energy, sizeof(double) * br},
+        {f.box.p, const_cast<float *>(s->sys.box), sizeof(float) * 3 * br}, {f.baro.p, s->baro, sizeof(double) * 3 * br}};
     for (const Pair &pr : pairs) {
         if (!pr.frame || !pr.state || pr.bytes == 0) continue;
         const cudaError_t e = save ? cudaMemcpyAsync(pr.frame, pr.state, pr.bytes, cudaMemcpyDeviceToDevice, st)
@@ -77,7 +80,8 @@ extern "C" dmts_status respa_guarded(dmts_ctx *ctx, dmts_state *stt, const dmts_
     }
     Frame frame;
     Buf mon;
-    if (!frame.alloc(n, R, stt->energy != nullptr) || !mon.ensure(sizeof(unsigned) * R)) {
+    const bool npt = p->barostat != 0;
+    if (!frame.alloc(n, R, stt->energy != nullptr, npt) || !mon.ensure(sizeof(unsigned) * R)) {
         frame.release();
         return fail(ctx, DMTS_E_OOM, "saved frame allocation failed");
     }
@@ -129,6 +133,10 @@ extern "C" dmts_status respa_guarded(dmts_ctx *ctx, dmts_state *stt, const dmts_
         if (e == DMTS_E_NONFINITE) { s = fail(ctx, e, "non-finite values in the single-time-step segment"); break; }
         if (e != DMTS_OK) { s = fail(ctx, e, "device error"); break; }
         stt->first_step = 1;     // the fast-force cache is stale after STS
+        // the single-time-step segment keeps the box; the piston's force is
+        // re-derived from the full force's virial at the next outer step
+        if (npt && !ck(ctx, cudaMemset2DAsync(stt->baro + 2, 3 * sizeof(double), 0, sizeof(double), R, st),
+                       "piston reset")) { s = DMTS_E_CUDA; break; }
         done += m_seg;
         if (!copy_state(ctx, frame, stt, true, st)) s = DMTS_E_CUDA;
     }

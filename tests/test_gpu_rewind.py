@@ -137,3 +137,48 @@ def test_guard_rejects_bad_parameters(ctx, water):
     with pytest.raises(core.L.DmtsError):
         core.respa_guarded(ctx, st, _sts_integ(1.0), 6, 1.0, 3, 4, DT)   # wraps RESPA only
     st.release()
+
+
+def test_rewind_under_the_barostat_restores_box_and_piston(ctx, water):
+    """With the barostat the saved frame holds the box and the piston state:
+    a rewind returns to them, and the run equals "j chunks of Algorithm 1
+    under the barostat, then STS (box fixed)" bit for bit, box included."""
+    m = water.element_masses()
+    v = S.maxwell_boltzmann(m, T, 103)
+    d0 = core.DeviceSystem(water)
+    s0 = core.MDState(d0, v, m.astype(np.float32), seeds=131, virial=True, barostat=True)
+    core.respa_step(ctx, s0, core.integrator(DT, N_IN, T, GAMMA, skin=0.5, barostat=True), 0)
+    ctx.sync()
+    K = O.kinetic(v, m)
+    c = -O.baro_force(10, 0.0, 0.0, np.ones(3), 1.0) / 3.0
+    p_atm = (2 * K - float(s0.virial_cons[0].item())) / (3 * np.prod(water.box)) / c
+    s0.release()
+
+    def npt():
+        return core.integrator(DT, N_IN, T, GAMMA, skin=0.5, barostat=True, pressure_atm=p_atm, tau_p_ps=0.2)
+
+    def fresh():
+        d = core.DeviceSystem(water)
+        return d, core.MDState(d, v, m.astype(np.float32), seeds=131, virial=True, barostat=True)
+
+    d1, s1 = fresh()
+    probe = core.respa_guarded(ctx, s1, npt(), 6 * CHUNK, math.inf, CHUNK, 4, DT)
+    s1.release()
+    cm = probe["chunk_max"]
+    j = next(k for k in range(1, len(cm)) if cm[k] > cm[:k].max())
+    thr = 0.5 * (float(cm[:j].max()) + float(cm[j]))
+    sts_steps, sts_dt = 4 * CHUNK, DT
+    d2, s2 = fresh()
+    out = core.respa_guarded(ctx, s2, npt(), (j + 1) * CHUNK, thr, CHUNK, sts_steps, sts_dt)
+    ctx.sync()
+    got = (d2.x.cpu().numpy().copy(), s2.v.cpu().numpy().copy(), d2.box.cpu().numpy().copy())
+    s2.release()
+    assert out["n_rewinds"] == 1 and out["rewind_at"][0] == j * CHUNK
+    d3, s3 = fresh()
+    core.respa_step(ctx, s3, npt(), j * CHUNK)
+    core.respa_step(ctx, s3, _sts_integ(sts_dt), sts_steps)
+    ctx.sync()
+    ref = (d3.x.cpu().numpy().copy(), s3.v.cpu().numpy().copy(), d3.box.cpu().numpy().copy())
+    s3.release()
+    assert all(np.array_equal(a, b) for a, b in zip(ref, got))
+    assert not np.array_equal(ref[2], water.box.astype(np.float32).reshape(ref[2].shape))   # the box moved
