@@ -327,6 +327,25 @@ dmts_status respa_step(dmts_ctx *ctx, dmts_state *st, const dmts_integrator *p, 
 void dmts_state_release(dmts_ctx *ctx, dmts_state *st);
 
 /*
+ * One step of on-box distillation of the NC model toward target forces (the
+ * NC model is distilled from the large model, Sec. 2 "Model architecture";
+ * here only its q/k projection W_qk, the [2 H n_c][C] matrix of the head, is
+ * fitted). With F_S the fast force of forces_nc (with DMTS_WITH_BONDS: bonds
+ * and repulsion included, mean subtracted) on `sys` and target T (device
+ * float [n_atoms][3], e.g. -grad U of the conservative model at the same
+ * positions): loss (device double [n_replicas], may be NULL) receives
+ * L = sum_i |F_S,i - T_i|^2 per replica; the gradient of sum_r L with respect
+ * to W_qk (the adjoint of the mean subtraction and of the NC head with
+ * respect to its q/k rows, then the contraction with the layer features) is
+ * written to grad (device float [2 H n_c][C], may be NULL); with lr > 0 one
+ * Adam step (beta1 0.9, beta2 0.999, eps 1e-8; adam_step = 1, 2, ... the
+ * update count, 1 resets the moments) updates the context's W_qk and its bf16
+ * copy. nbr: the NC list, cutoff >= r_NC. Asynchronous.
+ */
+dmts_status nc_distill_step(dmts_ctx *ctx, const dmts_system *sys, const dmts_nbr *nbr, const float *target,
+                            float lr, int adam_step, double *loss, float *grad, void *stream);
+
+/*
  * Copy of the neighbour list a state holds (inspection; synchronous):
  * which = 0 the conservative list (cutoff r_c + skin), 1 the NC list
  * (r_NC + skin), as last built on the device (Sec. 2, neighbour lists of the

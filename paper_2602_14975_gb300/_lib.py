@@ -99,7 +99,7 @@ class ServeStats(ct.Structure):
 
 # every entry point declared in include/dmts.h
 EXPORTS = ("dmts_create", "dmts_destroy", "dmts_last_error", "dmts_sync", "nbr_build",
-           "energy_forces_cons", "forces_nc", "respa_step", "dmts_state_release", "dmts_state_lists", "run_replicas",
+           "energy_forces_cons", "forces_nc", "respa_step", "dmts_state_release", "dmts_state_lists", "nc_distill_step", "run_replicas",
            "dmts_masses_hmr", "dmts_bond_table", "dmts_philox_words", "dmts_gaussians",
            "dmts_replica_footprint", "dmts_profile_enable", "dmts_profile_read", "nbr_build_noalloc",
            "dmts_contract_bf16", "dmts_kernel_launches", "respa_guarded")
@@ -134,6 +134,8 @@ def _declare(L):
                                 ct.POINTER(GuardStats), vp]
     L.dmts_state_release.restype = None
     L.dmts_state_release.argtypes = [vp, ct.POINTER(State)]
+    L.nc_distill_step.restype = i
+    L.nc_distill_step.argtypes = [vp, ct.POINTER(System), ct.POINTER(Nbr), vp, ct.c_float, i, vp, vp, vp]
     L.dmts_state_lists.restype = i
     L.dmts_state_lists.argtypes = [vp, ct.POINTER(State), i, vp, vp, ct.c_longlong, ct.POINTER(ct.c_longlong),
                                    ct.POINTER(ct.c_float), vp]

@@ -187,6 +187,25 @@ def energy_forces_cons(ctx: Context, dsys: DeviceSystem, nbr: NbrList, with_prio
     return (E, F, W) if with_virial else (E, F)
 
 
+def nc_distill_step(ctx: Context, dsys: DeviceSystem, nbr: NbrList, target, lr: float = 0.0, step: int = 1,
+                    with_grad: bool = False):
+    """One distillation step of the NC model's q/k projection toward target
+    forces (f32 [N,3] on the device): returns (loss f64 [n_replicas], the
+    gradient f32 [2 H n_c, C] or None); lr > 0 applies an Adam update."""
+    dev = dsys.x.device
+    target = torch.as_tensor(target, dtype=torch.float32, device=dev).contiguous()
+    loss = torch.empty(dsys.n_replicas, dtype=torch.float64, device=dev)
+    grad = None
+    if with_grad:
+        spec = ctx.nc_spec
+        grad = torch.empty(2 * (spec.K + spec.n_l) * spec.n_c, spec.C, dtype=torch.float32, device=dev)
+    s, nbs = dsys.struct(), nbr.struct()
+    st = ctx.lib.nc_distill_step(ctx.handle, ct.byref(s), ct.byref(nbs), _ptr(target), float(lr), int(step),
+                                 _ptr(loss), _ptr(grad), _stream(dev))
+    L.check(st, ctx.handle)
+    return loss, grad
+
+
 def forces_nc(ctx: Context, dsys: DeviceSystem, nbr: NbrList, with_bonds=True, with_virial=False):
     """Returns (F_NC f32 [N,3] mean-subtracted, net force f64 [R,3] before
     subtraction), and with with_virial the virial proxy f64 [R] as a third

@@ -868,6 +868,70 @@ void dmts_state_release(dmts_ctx *ctx, dmts_state *st) {
     st->internal = nullptr;
 }
 
+dmts_status nc_distill_step(dmts_ctx *ctx, const dmts_system *sys, const dmts_nbr *nbr, const float *target,
+                            float lr, int adam_step, double *loss, float *grad, void *stream) {
+    dmts_status s = check_sys(ctx, sys);
+    if (s != DMTS_OK) return s;
+    if (!ctx->has_nc) return fail(ctx, DMTS_E_INVALID, "context has no NC model");
+    if (!nbr || !nbr->row_ptr || !nbr->col || !target) return fail(ctx, DMTS_E_INVALID, "bad argument");
+    if (nbr->r_list < ctx->nc.rc) return fail(ctx, DMTS_E_INVALID, "neighbour list cutoff below the NC cutoff");
+    if (lr > 0.f && adam_step < 1) return fail(ctx, DMTS_E_INVALID, "adam_step counts from 1");
+    if (sys->n_atoms > 0 && (!sys->bond_ptr || !sys->bond_idx || !sys->bond_r0))
+        return fail(ctx, DMTS_E_INVALID, "missing bond table");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const SysView v = make_view(ctx, sys, st);
+    DevModel &m = ctx->nc;
+    Workspace &w = ctx->ws;
+    const int N = v.n, H = m.K + m.nl, QKW = 2 * H * m.nc, C = m.C;
+    const size_t nw = (size_t)QKW * C;
+    if (!w.dist_F.ensure(sizeof(float) * 3 * (N + 1)) || !w.dist_g.ensure(sizeof(float) * 3 * (N + 1)) ||
+        !w.dist_sq.ensure(sizeof(float) * (N + 1)) || !w.dist_gqkt.ensure(sizeof(float) * ((size_t)QKW * N + 1)) ||
+        !w.dist_dw.ensure(sizeof(float) * nw) || !w.adam_m.ensure(sizeof(float) * nw) ||
+        !w.adam_v.ensure(sizeof(float) * nw) || !w.ms_scratch.ensure(mean_sub_scratch_bytes(N, v.n_rep)))
+        return fail(ctx, DMTS_E_OOM, "workspace allocation failed");
+    // forward: the fast force (it leaves q/k rows, V and the layer features in the workspace)
+    s = nc_eval(ctx, v, nbr->row_ptr, nbr->col, (float *)w.dist_F.p, nullptr, DMTS_WITH_BONDS, st);
+    if (s != DMTS_OK) return s;
+    launch_distill_residual(N, (const float *)w.dist_F.p, target, (float *)w.dist_g.p, (float *)w.dist_sq.p, st);
+    if (loss) launch_replica_sum((const float *)w.dist_sq.p, v.rep_off, v.n_rep, loss, 0, st);
+    // adjoint of the mean subtraction: the gradient minus its replica mean
+    launch_mean_sub((float *)w.dist_g.p, (float *)w.dist_g.p, v.rep_off, v.n_rep, N, nullptr, w.ms_scratch.p, ctx->d_err,
+                    st);
+    NCHeadArgs a;
+    memset(&a, 0, sizeof a);
+    a.x = v.x;
+    a.atom_rep = v.atom_rep;
+    a.box = v.box;
+    a.row_ptr = nbr->row_ptr;
+    a.col = nbr->col;
+    a.n_atoms = N;
+    a.rc = m.rc;
+    a.inv_rc = 1.f / m.rc;
+    a.bnorm = sqrtf(2.f / m.rc);
+    a.p = m.p;
+    a.QK = (const float *)w.nc_qk.p;
+    a.V = (const float *)w.nc_v.p;
+    a.scale = m.scale;
+    a.order = v.order;
+    a.err = ctx->d_err;
+    launch_nc_head_bwd(m.K, m.nc, m.nl, a, (const float *)w.dist_g.p, (float *)w.dist_gqkt.p, st);
+    // dL/dW_qk[c][k] = sum_i dL/dQK[i][c] s1[i][k]
+    float *dw = grad ? grad : (float *)w.dist_dw.p;
+    const float *s1 = (const float *)w.nc_s.p + (size_t)N * C;
+    Epi es = epi(EPI_STORE);
+    es.out = dw;
+    launch_gemm_f32(QKW, C, N, (const float *)w.dist_gqkt.p, s1, 0, es, st);
+    if (lr > 0.f) {
+        if (adam_step == 1 && (!ck(ctx, cudaMemsetAsync(w.adam_m.p, 0, sizeof(float) * nw, st), "adam reset") ||
+                               !ck(ctx, cudaMemsetAsync(w.adam_v.p, 0, sizeof(float) * nw, st), "adam reset")))
+            return DMTS_E_CUDA;
+        launch_adam((int)nw, m.Wqk, dw, (float *)w.adam_m.p, (float *)w.adam_v.p, lr, adam_step, m.bf16 ? m.wqk_bf : nullptr,
+                    st);
+    }
+    return ck(ctx, cudaGetLastError(), "nc_distill_step launch") ? DMTS_OK : DMTS_E_CUDA;
+}
+
 dmts_status dmts_state_lists(dmts_ctx *ctx, const dmts_state *st, int which, int32_t *row_ptr, int32_t *col,
                              int64_t col_capacity, int64_t *n_pairs, float *r_list, void *stream) {
     if (!ctx || !st || !row_ptr || !n_pairs || (which != 0 && which != 1))

@@ -56,11 +56,13 @@ struct Workspace {
     Buf nc_w;         // per-atom virial proxy of the fast force
     Buf cons_w;       // per-atom virial of the conservative force
     Buf nc_w_last;    // per-replica fast-force virial of the last inner step
+    Buf dist_F, dist_g, dist_sq, dist_gqkt, dist_dw, adam_m, adam_v;   // distillation of the NC q/k projection
     void release_all() {
         Buf *all[] = {&s, &A, &q, &h, &act, &u, &gz, &gs0, &gs1, &gA, &e_atom, &ftmp, &atom_rep,
                       &nc_s, &nc_q, &nc_act, &nc_qk, &nc_v, &nc_f,
                       &q_bf, &act_bf, &s_bf, &gz_bf, &gs0_bf, &gs1_bf, &nc_q_bf, &nc_act_bf, &nc_s_bf,
-                      &ms_scratch, &nc_w, &cons_w, &nc_w_last};
+                      &ms_scratch, &nc_w, &cons_w, &nc_w_last,
+                      &dist_F, &dist_g, &dist_sq, &dist_gqkt, &dist_dw, &adam_m, &adam_v};
         for (Buf *b : all) b->release();
     }
 };

@@ -345,6 +345,166 @@ void launch_nc_head(int K, int n_c, int n_l, const NCHeadArgs &a, cudaStream_t s
     else if (K == 8 && n_c == 8 && n_l == 4) nc_head_launch<8, 8, 4>(a, st);
 }
 
+// ------------------------------------------------- NC head adjoint (q/k)
+// Warp per atom a. Lane h < H owns head h of c_ajh = q_ah . k_jh / sqrt(n_c)
+// (and accumulates dL/dq_ah), lane H + h owns c_jah = q_jh . k_ah / sqrt(n_c)
+// (dL/dk_ah). With F_aj = f_c S_aj (n + T_aj), S_aj = sum_{h<K} c_ajh B_h,
+// T_aj = sum_t c_aj(K+t) V_at, F_ja = f_c S_ja (-n + T_ja) and
+// F_a = scale sum_j (F_aj - F_ja) (+ terms without q/k), each directed pair
+// enters F_a with + and F_j with -, so u = scale (gF_a - gF_j) and
+//   dL/dc_ajh = f_c B_h u.(n + T_aj)   (h < K),  f_c S_aj u.V_at  (h = K + t),
+//   dL/dc_jah = -f_c B_h u.(-n + T_ja) (h < K), -f_c S_ja u.V_jt  (h = K + t).
+// Each pair is visited from both ends, so every atom gathers its own rows'
+// gradients: no atomics, deterministic.
+template <int K, int NC, int NL>
+__global__ void __launch_bounds__(128) k_nc_head_bwd(NCHeadArgs g, const float *__restrict__ gF,
+                                                    float *__restrict__ gQKT) {
+    constexpr int H = K + NL, QKW = 2 * H * NC;
+    static_assert(2 * H <= 32, "one lane per head and role");
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wa = blockIdx.x * 4 + warp;
+    if (wa >= g.n_atoms || *g.err) return;
+    const int a = g.order ? __ldg(g.order + wa) : wa;
+    const bool role_aj = lane < H, live = lane < 2 * H;
+    const int h = role_aj ? lane : (live ? lane - H : 0);
+    const float isnc = rsqrtf((float)NC);
+    // own row: q_a[h] (role aj) or k_a[h] (role ja)
+    float mine[NC], acc[NC];
+    const float *ra = g.QK + (size_t)a * QKW + (role_aj ? 0 : H * NC) + h * NC;
+#pragma unroll
+    for (int d = 0; d < NC; ++d) {
+        mine[d] = live ? ra[d] : 0.f;
+        acc[d] = 0.f;
+    }
+    float va[3 * NL];
+#pragma unroll
+    for (int t = 0; t < 3 * NL; ++t) va[t] = g.V[(size_t)a * NL * 3 + t];
+    const float gax = gF[3 * a], gay = gF[3 * a + 1], gaz = gF[3 * a + 2];
+    const int rep = g.atom_rep[a];
+    const float bx = g.box[3 * rep], by = g.box[3 * rep + 1], bz = g.box[3 * rep + 2];
+    const float ibx = bx > 0.f ? 1.f / bx : 0.f, iby = by > 0.f ? 1.f / by : 0.f, ibz = bz > 0.f ? 1.f / bz : 0.f;
+    const float xa = g.x[3 * a], ya = g.x[3 * a + 1], za = g.x[3 * a + 2];
+    const float rc2 = g.rc * g.rc;
+    for (int e = g.row_ptr[a]; e < g.row_ptr[a + 1]; ++e) {
+        const int j = __ldg(g.col + e);
+        const float dx = min_img(__ldg(g.x + 3 * j) - xa, bx, ibx);
+        const float dy = min_img(__ldg(g.x + 3 * j + 1) - ya, by, iby);
+        const float dz = min_img(__ldg(g.x + 3 * j + 2) - za, bz, ibz);
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        if (!(r2 < rc2)) continue;   // uniform over the warp
+        const float r = sqrtf(r2), inv = 1.f / r;
+        const float nx = dx * inv, ny = dy * inv, nz = dz * inv;
+        float du;
+        const float fc = envelope(r * g.inv_rc, g.p, &du);
+        float B[K];
+        bessel<K, false>(r, g.inv_rc, g.bnorm, B, nullptr);
+        float Bh = 0.f;
+#pragma unroll
+        for (int k = 0; k < K; ++k) Bh = (h == k) ? B[k] : Bh;
+        // the other atom's row: k_j[h] (role aj) or q_j[h] (role ja)
+        float other[NC];
+        const float *rj = g.QK + (size_t)j * QKW + (role_aj ? H * NC : 0) + h * NC;
+        float c = 0.f;
+#pragma unroll
+        for (int d = 0; d < NC; ++d) {
+            other[d] = live ? __ldg(rj + d) : 0.f;
+            c = fmaf(mine[d], other[d], c);
+        }
+        c *= isnc;
+        const bool bes = live && h < K;
+        const int t = h - K;
+        float vt[3] = {0.f, 0.f, 0.f};   // V_at (role aj) or V_jt (role ja) of this tensor head
+        if (live && h >= K) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+                vt[q] = role_aj ? va[3 * (t < NL ? t : 0) + q] : __ldg(g.V + ((size_t)j * NL + (t < NL ? t : 0)) * 3 + q);
+        }
+        const float sB = bes ? c * Bh : 0.f;
+        const float S_aj = warp_sum(role_aj ? sB : 0.f), S_ja = warp_sum(role_aj ? 0.f : sB);
+        float T_aj[3], T_ja[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const float cv = (live && h >= K) ? c * vt[q] : 0.f;
+            T_aj[q] = warp_sum(role_aj ? cv : 0.f);
+            T_ja[q] = warp_sum(role_aj ? 0.f : cv);
+        }
+        const float ux = g.scale * (gax - __ldg(gF + 3 * j)), uy = g.scale * (gay - __ldg(gF + 3 * j + 1)),
+                    uz = g.scale * (gaz - __ldg(gF + 3 * j + 2));
+        float G;
+        if (role_aj) {
+            G = h < K ? fc * Bh * (ux * (nx + T_aj[0]) + uy * (ny + T_aj[1]) + uz * (nz + T_aj[2]))
+                      : fc * S_aj * (ux * vt[0] + uy * vt[1] + uz * vt[2]);
+        } else {
+            G = h < K ? -fc * Bh * (ux * (-nx + T_ja[0]) + uy * (-ny + T_ja[1]) + uz * (-nz + T_ja[2]))
+                      : -fc * S_ja * (ux * vt[0] + uy * vt[1] + uz * vt[2]);
+        }
+        G *= isnc;
+#pragma unroll
+        for (int d = 0; d < NC; ++d) acc[d] = fmaf(G, other[d], acc[d]);
+    }
+    if (live) {
+        const int c0 = (role_aj ? 0 : H * NC) + h * NC;
+#pragma unroll
+        for (int d = 0; d < NC; ++d) gQKT[(size_t)(c0 + d) * g.n_atoms + a] = acc[d];
+    }
+}
+
+template <int K, int NC, int NL>
+static void nc_head_bwd_launch(const NCHeadArgs &a, const float *gF, float *gQKT, cudaStream_t st) {
+    k_nc_head_bwd<K, NC, NL><<<(a.n_atoms + 3) / 4, 128, 0, st>>>(a, gF, gQKT);
+    count_launch();
+}
+
+void launch_nc_head_bwd(int K, int n_c, int n_l, const NCHeadArgs &a, const float *gF, float *gQKT,
+                        cudaStream_t st) {
+    if (a.n_atoms == 0) return;
+    if (K == 8 && n_c == 8 && n_l == 2) nc_head_bwd_launch<8, 8, 2>(a, gF, gQKT, st);
+    else if (K == 8 && n_c == 8 && n_l == 1) nc_head_bwd_launch<8, 8, 1>(a, gF, gQKT, st);
+    else if (K == 8 && n_c == 8 && n_l == 3) nc_head_bwd_launch<8, 8, 3>(a, gF, gQKT, st);
+    else if (K == 8 && n_c == 8 && n_l == 4) nc_head_bwd_launch<8, 8, 4>(a, gF, gQKT, st);
+}
+
+__global__ void k_distill_residual(int n, const float *F, const float *T, float *g, float *sq) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float s = 0.f;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const float d = F[3 * i + q] - T[3 * i + q];
+        g[3 * i + q] = 2.f * d;
+        s = fmaf(d, d, s);
+    }
+    sq[i] = s;
+}
+
+void launch_distill_residual(int n, const float *F, const float *T, float *g, float *sq, cudaStream_t st) {
+    if (n == 0) return;
+    k_distill_residual<<<(n + 255) / 256, 256, 0, st>>>(n, F, T, g, sq);
+    count_launch();
+}
+
+// Adam (Kingma & Ba), beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected.
+__global__ void k_adam(int n, float *w, const float *grad, float *m, float *v, float lr, float c1, float c2,
+                       __nv_bfloat16 *w_bf) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gr = grad[i];
+    const float mi = 0.9f * m[i] + 0.1f * gr, vi = 0.999f * v[i] + 0.001f * gr * gr;
+    m[i] = mi;
+    v[i] = vi;
+    const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
+    w[i] = wi;
+    if (w_bf) w_bf[i] = __float2bfloat16_rn(wi);
+}
+
+void launch_adam(int n, float *w, const float *grad, float *m, float *v, float lr, int step, __nv_bfloat16 *w_bf,
+                 cudaStream_t st) {
+    if (n == 0) return;
+    const float c1 = 1.f - powf(0.9f, (float)step), c2 = 1.f - powf(0.999f, (float)step);
+    k_adam<<<(n + 255) / 256, 256, 0, st>>>(n, w, grad, m, v, lr, c1, c2, w_bf);
+    count_launch();
+}
+
 __global__ void k_scale_d(double *v, int n, double f) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) v[i] *= f;

@@ -41,6 +41,18 @@ struct NCHeadArgs {
 };
 
 void launch_nc_head(int K, int n_c, int n_l, const NCHeadArgs &a, cudaStream_t st);
+
+// Adjoint of the NC head with respect to its q/k rows (distillation): with
+// gF[i] = dL/dF_i (after the mean subtraction's adjoint) writes
+// gQKT[c][i] = dL/dQK[i][c] (transposed, [2 H n_c][N]). Uses a.x, box, lists,
+// rc, bnorm, p, QK, V, scale, order, err of the forward's arguments.
+void launch_nc_head_bwd(int K, int n_c, int n_l, const NCHeadArgs &a, const float *gF, float *gQKT,
+                        cudaStream_t st);
+// g = 2 (F - T), sq = |F - T|^2 per atom.
+void launch_distill_residual(int n, const float *F, const float *T, float *g, float *sq, cudaStream_t st);
+// Adam on n parameters (fp32, moments m, v), then the bf16 copy (nullable).
+void launch_adam(int n, float *w, const float *grad, float *m, float *v, float lr, int step, __nv_bfloat16 *w_bf,
+                 cudaStream_t st);
 // v[i] *= f, i < n.
 void launch_scale_d(double *v, int n, double f, cudaStream_t st);
 // est[r] = cons[r] - last[r] + avg[r]

@@ -439,6 +439,51 @@ def test_npt_needs_its_arrays(ctx1, water):
     st.release()
 
 
+def test_distill_gradient_matches_oracle(models1, water):
+    """On-box distillation of the NC model's q/k projection: the loss
+    L = sum_i |F_S,i - T_i|^2 (F_S the fast force with bonds and repulsion,
+    mean subtracted) and its gradient with respect to W_qk (the adjoint of the
+    mean subtraction and of the NC head, contracted with the layer features)
+    against the oracle's loss and central differences of it."""
+    (cs, cb), (ns, nb_) = models1
+    ctx = core.Context(cons=(cs, cb), nc=(ns, nb_))      # its own context: training changes the weights
+    T = O.cons_energy_forces(water, cs, cb)[1] + O.prior(water)[1]
+    d = core.DeviceSystem(water)
+    nb = core.nbr_build(ctx, d, 4.0)
+    loss, grad = core.nc_distill_step(ctx, d, nb, T.astype(np.float32), lr=0.0, with_grad=True)
+    loss, grad = loss.item(), grad.cpu().numpy().reshape(-1)
+
+    def L_oracle(blob):
+        F, _ = O.nc_forces(water, ns, blob)
+        return float(((F - T.astype(np.float32).astype(np.float64)) ** 2).sum())
+
+    L0 = L_oracle(nb_)
+    assert abs(loss - L0) <= 1e-4 * L0, (loss, L0)
+    nW = grad.size
+    rng = np.random.default_rng(44)
+    h = 1e-3
+    for k in rng.choice(nW, 8, replace=False):
+        bp, bm = nb_.copy(), nb_.copy()
+        bp[len(nb_) - nW + k] += h
+        bm[len(nb_) - nW + k] -= h
+        fd = (L_oracle(bp) - L_oracle(bm)) / (2 * h)
+        assert abs(grad[k] - fd) <= 2e-3 * np.abs(grad).max(), (k, grad[k], fd)
+
+
+def test_distill_adam_lowers_the_loss(models1, water):
+    (cs, cb), (ns, nb_) = models1
+    ctx = core.Context(cons=(cs, cb), nc=(ns, nb_))
+    T = (O.cons_energy_forces(water, cs, cb)[1] + O.prior(water)[1]).astype(np.float32)
+    d = core.DeviceSystem(water)
+    nb = core.nbr_build(ctx, d, 4.0)
+    losses = []
+    for step in range(1, 41):
+        loss, _ = core.nc_distill_step(ctx, d, nb, T, lr=2e-3, step=step)
+        losses.append(loss.item())
+    final, _ = core.nc_distill_step(ctx, d, nb, T, lr=0.0)
+    assert final.item() < 0.8 * losses[0], (losses[0], final.item())
+
+
 # ------------------------------------------------------------------ Philox --
 
 def test_philox_words_bit_exact(ctx1):
