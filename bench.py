@@ -409,6 +409,48 @@ def main():
                    "box_change": float(box_end[0] / sy.box[0] - 1.0)}
     sn.release()
 
+    # ------------------------------------------------------- distillation
+    # on-box distillation of the NC model's q/k projection toward the full
+    # force: frames 10 single time steps apart from a BAOAB run of the
+    # conservative model, 4 for training and 1 held out; |F_L| = |F - F_S| on
+    # the held-out frame before and after 60 Adam steps
+    ctxD = core.Context(cons=(cs, cb), nc=(ns, nb))
+    dF = core.DeviceSystem(W["system"]())
+    sF = core.MDState(dF, v0, m_hmr.astype(np.float32), seeds=I.seed + 7, replica_ids=[D.replica_id(rank, 0)])
+    iF = core.integrator(1.0, 1, I.temperature, I.gamma_ps, mode=1, skin=skin)
+    frames = []
+    for _ in range(5):
+        core.respa_step(ctxD, sF, iF, 10)
+        df = core.DeviceSystem(W["system"]())
+        df.x.copy_(dF.x)
+        nbc = core.nbr_build(ctxD, df, cs.rc + 0.5)
+        _, tf = core.energy_forces_cons(ctxD, df, nbc, with_prior=True)
+        frames.append((df, core.nbr_build(ctxD, df, ns.rc + 0.5), tf))
+    sF.release()
+    ctx.sync()
+
+    def f_l_rms(fr):
+        lv, _ = core.nc_distill_step(ctxD, fr[0], fr[1], fr[2], lr=0.0)
+        return math.sqrt(lv.item() / (3 * fr[0].n_atoms))
+
+    rms0 = f_l_rms(frames[4])
+    n_dist = 60
+    barrier()
+    e0.record(stream)
+    for k in range(n_dist):
+        fr = frames[k % 4]
+        core.nc_distill_step(ctxD, fr[0], fr[1], fr[2], lr=1e-3, step=k + 1)
+    e1.record(stream)
+    barrier()
+    ctx.sync()
+    ms_dist = max_over_ranks(e0.elapsed_time(e1)) / n_dist
+    rms1 = f_l_rms(frames[4])
+    side["distill"] = {"what": "NC q/k projection W_qk fitted to the full force (Adam, lr 1e-3)",
+                       "train_frames": 4, "steps": n_dist, "ms_per_step": ms_dist,
+                       "f_l_rms_held_out_before": rms0, "f_l_rms_held_out_after": rms1,
+                       "unit": "kcal/mol/A"}
+    del frames, ctxD
+
     # --------------------------------------------------------------- STS
     sts = W["sts"]
     m_el = sy.element_masses()
@@ -644,6 +686,7 @@ def main():
         "rewind_guard": side["guarded"],
         "ffl": side["ffl"],
         "npt": side["npt"],
+        "distill": side["distill"],
         "large_system": {"workload": syL.name, "n_atoms": syL.n_atoms, "steps": n_large,
                          "ns_per_day": ns_per_day(IL.dt_outer, 1e3 / ms_large) * world, "ms_per_step": ms_large,
                          "sts_ns_per_day": ns_per_day(stsL.dt_outer, 1e3 / ms_large_sts) * world,
