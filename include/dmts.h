@@ -328,22 +328,26 @@ void dmts_state_release(dmts_ctx *ctx, dmts_state *st);
 
 /*
  * One step of on-box distillation of the NC model toward target forces (the
- * NC model is distilled from the large model, Sec. 2 "Model architecture";
- * here only its q/k projection W_qk, the [2 H n_c][C] matrix of the head, is
- * fitted). With F_S the fast force of forces_nc (with DMTS_WITH_BONDS: bonds
- * and repulsion included, mean subtracted) on `sys` and target T (device
- * float [n_atoms][3], e.g. -grad U of the conservative model at the same
- * positions): loss (device double [n_replicas], may be NULL) receives
- * L = sum_i |F_S,i - T_i|^2 per replica; the gradient of sum_r L with respect
- * to W_qk (the adjoint of the mean subtraction and of the NC head with
- * respect to its q/k rows, then the contraction with the layer features) is
- * written to grad (device float [2 H n_c][C], may be NULL); with lr > 0 one
- * Adam step (beta1 0.9, beta2 0.999, eps 1e-8; adam_step = 1, 2, ... the
- * update count, 1 resets the moments) updates the context's W_qk and its bf16
- * copy. nbr: the NC list, cutoff >= r_NC. Asynchronous.
+ * NC model is distilled from the large model, Sec. 2 "Model architecture").
+ * Fitted weights (`params`, a mask): DMTS_FIT_QK the head's q/k projection
+ * W_qk ([2 H n_c][C]); DMTS_FIT_MLP the channel-mixing MLP of its layer
+ * (W1, b1, W2, b2). With F_S the fast force of forces_nc (with
+ * DMTS_WITH_BONDS: bonds and repulsion included, mean subtracted) on `sys`
+ * and target T (device float [n_atoms][3], e.g. -grad U of the conservative
+ * model at the same positions): loss (device double [n_replicas], may be
+ * NULL) receives L = sum_i |F_S,i - T_i|^2 per replica; the gradient of
+ * sum_r L (the adjoint of the mean subtraction, of the NC head with respect to
+ * its q/k rows, then of the contractions and the MLP) is written to grad
+ * (device float, the length and layout of the NC weight blob, may be NULL),
+ * zero for weights not fitted; with lr > 0 one Adam step (beta1 0.9, beta2
+ * 0.999, eps 1e-8; adam_step = 1, 2, ... the update count, 1 resets the
+ * moments) updates the fitted weights of the context's NC model and their
+ * bf16 copies. nbr: the NC list, cutoff >= r_NC. Asynchronous.
  */
+#define DMTS_FIT_QK 1
+#define DMTS_FIT_MLP 2
 dmts_status nc_distill_step(dmts_ctx *ctx, const dmts_system *sys, const dmts_nbr *nbr, const float *target,
-                            float lr, int adam_step, double *loss, float *grad, void *stream);
+                            int params, float lr, int adam_step, double *loss, float *grad, void *stream);
 
 /*
  * Copy of the neighbour list a state holds (inspection; synchronous):

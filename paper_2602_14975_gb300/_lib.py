@@ -15,6 +15,7 @@ _lib = None
 MAX_SPECIES = 8
 
 OK, E_INVALID, E_OOM, E_CUDA, E_NBR_OVERFLOW, E_NONFINITE, E_TIMEOUT, E_BUSY = range(8)
+FIT_QK, FIT_MLP = 1, 2   # nc_distill_step: weights to fit
 STATUS_NAMES = {0: "OK", 1: "E_INVALID", 2: "E_OOM", 3: "E_CUDA", 4: "E_NBR_OVERFLOW",
                 5: "E_NONFINITE", 6: "E_TIMEOUT", 7: "E_BUSY"}
 FP32, BF16 = 0, 1
@@ -135,7 +136,7 @@ def _declare(L):
     L.dmts_state_release.restype = None
     L.dmts_state_release.argtypes = [vp, ct.POINTER(State)]
     L.nc_distill_step.restype = i
-    L.nc_distill_step.argtypes = [vp, ct.POINTER(System), ct.POINTER(Nbr), vp, ct.c_float, i, vp, vp, vp]
+    L.nc_distill_step.argtypes = [vp, ct.POINTER(System), ct.POINTER(Nbr), vp, i, ct.c_float, i, vp, vp, vp]
     L.dmts_state_lists.restype = i
     L.dmts_state_lists.argtypes = [vp, ct.POINTER(State), i, vp, vp, ct.c_longlong, ct.POINTER(ct.c_longlong),
                                    ct.POINTER(ct.c_float), vp]

@@ -65,6 +65,7 @@ class Context:
         self.handle = h
         self.cons_spec = cons[0] if cons is not None else None
         self.nc_spec = nc[0] if nc is not None else None
+        self.nc_blob_len = len(nc[1]) if nc is not None else 0
         self.prior = prior
 
     def close(self):
@@ -188,20 +189,20 @@ def energy_forces_cons(ctx: Context, dsys: DeviceSystem, nbr: NbrList, with_prio
 
 
 def nc_distill_step(ctx: Context, dsys: DeviceSystem, nbr: NbrList, target, lr: float = 0.0, step: int = 1,
-                    with_grad: bool = False):
-    """One distillation step of the NC model's q/k projection toward target
-    forces (f32 [N,3] on the device): returns (loss f64 [n_replicas], the
-    gradient f32 [2 H n_c, C] or None); lr > 0 applies an Adam update."""
+                    params: int = L.FIT_QK | L.FIT_MLP, with_grad: bool = False):
+    """One distillation step of the NC model toward target forces (f32 [N,3]
+    on the device), fitting `params` (L.FIT_QK: the head's q/k projection,
+    L.FIT_MLP: its MLP): returns (loss f64 [n_replicas], the gradient f32 in
+    the NC weight blob's layout or None); lr > 0 applies an Adam update."""
     dev = dsys.x.device
     target = torch.as_tensor(target, dtype=torch.float32, device=dev).contiguous()
     loss = torch.empty(dsys.n_replicas, dtype=torch.float64, device=dev)
     grad = None
     if with_grad:
-        spec = ctx.nc_spec
-        grad = torch.empty(2 * (spec.K + spec.n_l) * spec.n_c, spec.C, dtype=torch.float32, device=dev)
+        grad = torch.empty(int(ctx.nc_blob_len), dtype=torch.float32, device=dev)
     s, nbs = dsys.struct(), nbr.struct()
-    st = ctx.lib.nc_distill_step(ctx.handle, ct.byref(s), ct.byref(nbs), _ptr(target), float(lr), int(step),
-                                 _ptr(loss), _ptr(grad), _stream(dev))
+    st = ctx.lib.nc_distill_step(ctx.handle, ct.byref(s), ct.byref(nbs), _ptr(target), int(params), float(lr),
+                                 int(step), _ptr(loss), _ptr(grad), _stream(dev))
     L.check(st, ctx.handle)
     return loss, grad
 

@@ -102,6 +102,7 @@ static dmts_status load_model(dmts_ctx *ctx, const dmts_model *in, bool is_nc, D
         return fail(ctx, DMTS_E_INVALID, "weight blob size does not match the model sizes");
     std::vector<float> h(in->weights, in->weights + expect);
     if (!upload(m, h)) return fail(ctx, DMTS_E_OOM, "weight upload failed");
+    m.n_weights = (size_t)expect;
     // offsets (same order as the blob)
     size_t o = 0;
     auto take = [&](size_t n) { float *p = m.dev + o; o += n; return p; };
@@ -391,7 +392,7 @@ dmts_status nc_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const i
     { ProfScope ps(ctx, "nc_mp_fwd", st); launch_mp_fwd(C, 1, m.K, g, io, st); }
     Epi e1 = epi(EPI_BIAS_SILU);
     e1.bias = m.b1[0];
-    e1.H = nullptr;   // no backward through the NC model
+    e1.H = (flags & kFlagKeepPre) ? (float *)w.dist_h.p : nullptr;   // kept only for the distillation
     e1.out = (float *)w.nc_act.p;
     e1.out_bf16 = act_bf;
     contract(ctx, m, N, C, 2 * C, io.q, q_bf, m.w1[0], 1, m.w1_bf[0], e1, st, "nc_gemm_tc", "nc_gemm");
@@ -869,12 +870,13 @@ void dmts_state_release(dmts_ctx *ctx, dmts_state *st) {
 }
 
 dmts_status nc_distill_step(dmts_ctx *ctx, const dmts_system *sys, const dmts_nbr *nbr, const float *target,
-                            float lr, int adam_step, double *loss, float *grad, void *stream) {
+                            int params, float lr, int adam_step, double *loss, float *grad, void *stream) {
     dmts_status s = check_sys(ctx, sys);
     if (s != DMTS_OK) return s;
     if (!ctx->has_nc) return fail(ctx, DMTS_E_INVALID, "context has no NC model");
     if (!nbr || !nbr->row_ptr || !nbr->col || !target) return fail(ctx, DMTS_E_INVALID, "bad argument");
     if (nbr->r_list < ctx->nc.rc) return fail(ctx, DMTS_E_INVALID, "neighbour list cutoff below the NC cutoff");
+    if (params & ~(DMTS_FIT_QK | DMTS_FIT_MLP)) return fail(ctx, DMTS_E_INVALID, "unknown weights to fit");
     if (lr > 0.f && adam_step < 1) return fail(ctx, DMTS_E_INVALID, "adam_step counts from 1");
     if (sys->n_atoms > 0 && (!sys->bond_ptr || !sys->bond_idx || !sys->bond_r0))
         return fail(ctx, DMTS_E_INVALID, "missing bond table");
@@ -884,14 +886,18 @@ dmts_status nc_distill_step(dmts_ctx *ctx, const dmts_system *sys, const dmts_nb
     DevModel &m = ctx->nc;
     Workspace &w = ctx->ws;
     const int N = v.n, H = m.K + m.nl, QKW = 2 * H * m.nc, C = m.C;
-    const size_t nw = (size_t)QKW * C;
+    const bool fit_mlp = params & DMTS_FIT_MLP, fit_qk = params & DMTS_FIT_QK;
+    const size_t nb = m.n_weights, part = (size_t)64 * QKW * (C + 1) + (size_t)64 * C * (2 * C + 1);
     if (!w.dist_F.ensure(sizeof(float) * 3 * (N + 1)) || !w.dist_g.ensure(sizeof(float) * 3 * (N + 1)) ||
-        !w.dist_sq.ensure(sizeof(float) * (N + 1)) || !w.dist_gqkt.ensure(sizeof(float) * ((size_t)QKW * N + 1)) ||
-        !w.dist_dw.ensure(sizeof(float) * nw) || !w.adam_m.ensure(sizeof(float) * nw) ||
-        !w.adam_v.ensure(sizeof(float) * nw) || !w.ms_scratch.ensure(mean_sub_scratch_bytes(N, v.n_rep)))
+        !w.dist_sq.ensure(sizeof(float) * (N + 1)) || !w.dist_gqk.ensure(sizeof(float) * ((size_t)QKW * N + 1)) ||
+        !w.dist_gs1.ensure(sizeof(float) * ((size_t)C * N + 1)) || !w.dist_gh.ensure(sizeof(float) * ((size_t)C * N + 1)) ||
+        !w.dist_h.ensure(sizeof(float) * ((size_t)C * N + 1)) || !w.dist_dw.ensure(sizeof(float) * nb) ||
+        !w.adam_m.ensure(sizeof(float) * nb) || !w.adam_v.ensure(sizeof(float) * nb) ||
+        !w.dist_part.ensure(sizeof(float) * part) || !w.ms_scratch.ensure(mean_sub_scratch_bytes(N, v.n_rep)))
         return fail(ctx, DMTS_E_OOM, "workspace allocation failed");
-    // forward: the fast force (it leaves q/k rows, V and the layer features in the workspace)
-    s = nc_eval(ctx, v, nbr->row_ptr, nbr->col, (float *)w.dist_F.p, nullptr, DMTS_WITH_BONDS, st);
+    // forward: the fast force (it leaves q, the MLP's activations and
+    // pre-activations, the layer features, the q/k rows and V in the workspace)
+    s = nc_eval(ctx, v, nbr->row_ptr, nbr->col, (float *)w.dist_F.p, nullptr, DMTS_WITH_BONDS | kFlagKeepPre, st);
     if (s != DMTS_OK) return s;
     launch_distill_residual(N, (const float *)w.dist_F.p, target, (float *)w.dist_g.p, (float *)w.dist_sq.p, st);
     if (loss) launch_replica_sum((const float *)w.dist_sq.p, v.rep_off, v.n_rep, loss, 0, st);
@@ -915,19 +921,42 @@ dmts_status nc_distill_step(dmts_ctx *ctx, const dmts_system *sys, const dmts_nb
     a.scale = m.scale;
     a.order = v.order;
     a.err = ctx->d_err;
-    launch_nc_head_bwd(m.K, m.nc, m.nl, a, (const float *)w.dist_g.p, (float *)w.dist_gqkt.p, st);
-    // dL/dW_qk[c][k] = sum_i dL/dQK[i][c] s1[i][k]
+    float *gqk = (float *)w.dist_gqk.p, *gs1 = (float *)w.dist_gs1.p, *gh = (float *)w.dist_gh.p;
+    launch_nc_head_bwd(m.K, m.nc, m.nl, a, (const float *)w.dist_g.p, gqk, st);
+    // weight gradients in the blob's layout (zero where not fitted)
     float *dw = grad ? grad : (float *)w.dist_dw.p;
+    if (!ck(ctx, cudaMemsetAsync(dw, 0, sizeof(float) * nb, st), "gradient reset")) return DMTS_E_CUDA;
+    auto at = [&](const float *p) { return dw + (p - m.dev); };
     const float *s1 = (const float *)w.nc_s.p + (size_t)N * C;
-    Epi es = epi(EPI_STORE);
-    es.out = dw;
-    launch_gemm_f32(QKW, C, N, (const float *)w.dist_gqkt.p, s1, 0, es, st);
-    if (lr > 0.f) {
-        if (adam_step == 1 && (!ck(ctx, cudaMemsetAsync(w.adam_m.p, 0, sizeof(float) * nw, st), "adam reset") ||
-                               !ck(ctx, cudaMemsetAsync(w.adam_v.p, 0, sizeof(float) * nw, st), "adam reset")))
+    float *part_buf = (float *)w.dist_part.p;
+    if (fit_qk) launch_atb(N, QKW, C, gqk, s1, at(m.Wqk), nullptr, part_buf, st);   // dW_qk = gQK^T s1
+    if (fit_mlp) {
+        // s1 = s0 + act W2^T + b2, act = silu(h), h = q W1^T + b1
+        Epi e = epi(EPI_STORE);
+        e.out = gs1;
+        launch_gemm_f32(N, C, QKW, gqk, m.Wqk, 0, e, st);                               // g_s1 = gQK W_qk
+        launch_atb(N, C, C, gs1, (const float *)w.nc_act.p, at(m.w2[0]), at(m.b2[0]), part_buf, st);
+        Epi ed = epi(EPI_DSILU);
+        ed.H = (float *)w.dist_h.p;
+        ed.out = gh;
+        launch_gemm_f32(N, C, C, gs1, m.w2[0], 0, ed, st);                             // g_h = (g_s1 W2) silu'(h)
+        launch_atb(N, C, 2 * C, gh, (const float *)w.nc_q.p, at(m.w1[0]), at(m.b1[0]), part_buf, st);
+    }
+    if (lr > 0.f && params) {
+        if (adam_step == 1 && (!ck(ctx, cudaMemsetAsync(w.adam_m.p, 0, sizeof(float) * nb, st), "adam reset") ||
+                               !ck(ctx, cudaMemsetAsync(w.adam_v.p, 0, sizeof(float) * nb, st), "adam reset")))
             return DMTS_E_CUDA;
-        launch_adam((int)nw, m.Wqk, dw, (float *)w.adam_m.p, (float *)w.adam_v.p, lr, adam_step, m.bf16 ? m.wqk_bf : nullptr,
-                    st);
+        auto adam = [&](float *p, size_t n, __nv_bfloat16 *bf) {
+            const size_t o = (size_t)(p - m.dev);
+            launch_adam((int)n, p, dw + o, (float *)w.adam_m.p + o, (float *)w.adam_v.p + o, lr, adam_step, bf, st);
+        };
+        if (fit_qk) adam(m.Wqk, (size_t)QKW * C, m.bf16 ? m.wqk_bf : nullptr);
+        if (fit_mlp) {
+            adam(m.w1[0], (size_t)C * 2 * C, m.bf16 ? m.w1_bf[0] : nullptr);
+            adam(m.b1[0], C, nullptr);
+            adam(m.w2[0], (size_t)C * C, m.bf16 ? m.w2_bf[0] : nullptr);
+            adam(m.b2[0], C, nullptr);
+        }
     }
     return ck(ctx, cudaGetLastError(), "nc_distill_step launch") ? DMTS_OK : DMTS_E_CUDA;
 }

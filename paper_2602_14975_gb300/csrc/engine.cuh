@@ -21,7 +21,8 @@ struct DevModel {
     int L = 0, C = 0, lmax = 0, K = 0, S = 0, nc = 0, nl = 0, p = 0;
     float rc = 0.f, nu = 0.f, scale = 0.f;
     bool bf16 = false;
-    float *dev = nullptr;                 // one allocation holding every tensor
+    float *dev = nullptr;                 // one allocation holding every tensor (the blob's order)
+    size_t n_weights = 0;                 // floats in that allocation
     float *emb = nullptr;
     float *wrad[DMTS_MAX_LAYERS] = {}, *w1[DMTS_MAX_LAYERS] = {}, *b1[DMTS_MAX_LAYERS] = {},
           *w2[DMTS_MAX_LAYERS] = {}, *b2[DMTS_MAX_LAYERS] = {};
@@ -56,13 +57,16 @@ struct Workspace {
     Buf nc_w;         // per-atom virial proxy of the fast force
     Buf cons_w;       // per-atom virial of the conservative force
     Buf nc_w_last;    // per-replica fast-force virial of the last inner step
-    Buf dist_F, dist_g, dist_sq, dist_gqkt, dist_dw, adam_m, adam_v;   // distillation of the NC q/k projection
+    // distillation of the NC model: residual, q/k-row and feature gradients,
+    // pre-activation, blob-shaped weight gradient, Adam moments, split sums
+    Buf dist_F, dist_g, dist_sq, dist_gqk, dist_gs1, dist_gh, dist_h, dist_dw, adam_m, adam_v, dist_part;
     void release_all() {
         Buf *all[] = {&s, &A, &q, &h, &act, &u, &gz, &gs0, &gs1, &gA, &e_atom, &ftmp, &atom_rep,
                       &nc_s, &nc_q, &nc_act, &nc_qk, &nc_v, &nc_f,
                       &q_bf, &act_bf, &s_bf, &gz_bf, &gs0_bf, &gs1_bf, &nc_q_bf, &nc_act_bf, &nc_s_bf,
                       &ms_scratch, &nc_w, &cons_w, &nc_w_last,
-                      &dist_F, &dist_g, &dist_sq, &dist_gqkt, &dist_dw, &adam_m, &adam_v};
+                      &dist_F, &dist_g, &dist_sq, &dist_gqk, &dist_gs1, &dist_gh, &dist_h, &dist_dw,
+                      &adam_m, &adam_v, &dist_part};
         for (Buf *b : all) b->release();
     }
 };
@@ -150,6 +154,9 @@ dmts_status fail(dmts_ctx *ctx, dmts_status s, const std::string &msg);
 // embedding is not recomputed (set within one respa_step call, where the
 // species do not change).
 constexpr int kFlagEmbedded = 1 << 30;
+// Internal flag of nc_eval: keep the MLP pre-activation (ws.dist_h) for the
+// distillation's backward pass.
+constexpr int kFlagKeepPre = 1 << 29;
 dmts_status cons_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const int *col, double *energy,
                       float *forces, int flags, cudaStream_t st, double *virial = nullptr);
 dmts_status nc_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const int *col, float *forces,

@@ -1,5 +1,6 @@
 // NC direct-force head (Sec. 2 "Model architecture"), the bonded + LJ prior,
 // and the fused BAOAB/RESPA integrator with Philox4x32-10 noise (Algorithm 1).
+#include <algorithm>
 #include "md.cuh"
 #include "ptx.cuh"
 
@@ -358,7 +359,7 @@ void launch_nc_head(int K, int n_c, int n_l, const NCHeadArgs &a, cudaStream_t s
 // gradients: no atomics, deterministic.
 template <int K, int NC, int NL>
 __global__ void __launch_bounds__(128) k_nc_head_bwd(NCHeadArgs g, const float *__restrict__ gF,
-                                                    float *__restrict__ gQKT) {
+                                                    float *__restrict__ gQK) {
     constexpr int H = K + NL, QKW = 2 * H * NC;
     static_assert(2 * H <= 32, "one lane per head and role");
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -445,23 +446,87 @@ __global__ void __launch_bounds__(128) k_nc_head_bwd(NCHeadArgs g, const float *
     if (live) {
         const int c0 = (role_aj ? 0 : H * NC) + h * NC;
 #pragma unroll
-        for (int d = 0; d < NC; ++d) gQKT[(size_t)(c0 + d) * g.n_atoms + a] = acc[d];
+        for (int d = 0; d < NC; ++d) gQK[(size_t)a * QKW + c0 + d] = acc[d];
     }
 }
 
 template <int K, int NC, int NL>
-static void nc_head_bwd_launch(const NCHeadArgs &a, const float *gF, float *gQKT, cudaStream_t st) {
-    k_nc_head_bwd<K, NC, NL><<<(a.n_atoms + 3) / 4, 128, 0, st>>>(a, gF, gQKT);
+static void nc_head_bwd_launch(const NCHeadArgs &a, const float *gF, float *gQK, cudaStream_t st) {
+    k_nc_head_bwd<K, NC, NL><<<(a.n_atoms + 3) / 4, 128, 0, st>>>(a, gF, gQK);
     count_launch();
 }
 
-void launch_nc_head_bwd(int K, int n_c, int n_l, const NCHeadArgs &a, const float *gF, float *gQKT,
+void launch_nc_head_bwd(int K, int n_c, int n_l, const NCHeadArgs &a, const float *gF, float *gQK,
                         cudaStream_t st) {
     if (a.n_atoms == 0) return;
-    if (K == 8 && n_c == 8 && n_l == 2) nc_head_bwd_launch<8, 8, 2>(a, gF, gQKT, st);
-    else if (K == 8 && n_c == 8 && n_l == 1) nc_head_bwd_launch<8, 8, 1>(a, gF, gQKT, st);
-    else if (K == 8 && n_c == 8 && n_l == 3) nc_head_bwd_launch<8, 8, 3>(a, gF, gQKT, st);
-    else if (K == 8 && n_c == 8 && n_l == 4) nc_head_bwd_launch<8, 8, 4>(a, gF, gQKT, st);
+    if (K == 8 && n_c == 8 && n_l == 2) nc_head_bwd_launch<8, 8, 2>(a, gF, gQK, st);
+    else if (K == 8 && n_c == 8 && n_l == 1) nc_head_bwd_launch<8, 8, 1>(a, gF, gQK, st);
+    else if (K == 8 && n_c == 8 && n_l == 3) nc_head_bwd_launch<8, 8, 3>(a, gF, gQK, st);
+    else if (K == 8 && n_c == 8 && n_l == 4) nc_head_bwd_launch<8, 8, 4>(a, gF, gQK, st);
+}
+
+// ------------------------------------------------ weight gradients (A^T B)
+// Block (32 x 8 threads) = a 32 x 32 output tile over one slice of atoms;
+// thread (ty, tx) sums outputs (ty + 8k, tx), k < 4, in atom order.
+constexpr int ATB_T = 32, ATB_CH = 16, ATB_SLICES = 64;
+
+__global__ void __launch_bounds__(256) k_atb_part(int N, int O, int I, const float *__restrict__ G,
+                                                 const float *__restrict__ X, float *__restrict__ part, int with_cs,
+                                                 int slices) {
+    __shared__ float Gs[ATB_CH][ATB_T], Xs[ATB_CH][ATB_T];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int o0 = blockIdx.x * ATB_T, i0 = blockIdx.y * ATB_T, sl = blockIdx.z;
+    const int per = (N + slices - 1) / slices, a0 = sl * per, a1 = min(N, a0 + per);
+    float acc[4] = {0.f, 0.f, 0.f, 0.f}, cs[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int c0 = a0; c0 < a1; c0 += ATB_CH) {
+        for (int q = threadIdx.x; q < ATB_CH * ATB_T; q += 256) {
+            const int aa = q / ATB_T, cc = q % ATB_T, at = c0 + aa;
+            Gs[aa][cc] = (at < a1 && o0 + cc < O) ? G[(size_t)at * O + o0 + cc] : 0.f;
+            Xs[aa][cc] = (at < a1 && i0 + cc < I) ? X[(size_t)at * I + i0 + cc] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int aa = 0; aa < ATB_CH; ++aa) {
+            const float xv = Xs[aa][tx];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                acc[k] = fmaf(Gs[aa][ty + 8 * k], xv, acc[k]);
+                cs[k] += Gs[aa][ty + 8 * k];
+            }
+        }
+        __syncthreads();
+    }
+    float *pp = part + (size_t)sl * O * (I + 1);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int o = o0 + ty + 8 * k, i = i0 + tx;
+        if (o < O && i < I) pp[(size_t)o * (I + 1) + i] = acc[k];
+        if (with_cs && o < O && blockIdx.y == 0 && tx == 0) pp[(size_t)o * (I + 1) + I] = cs[k];
+    }
+}
+
+__global__ void k_atb_reduce(int O, int I, const float *__restrict__ part, float *__restrict__ out,
+                             float *__restrict__ cs, int slices) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= O * (I + 1)) return;
+    const int o = q / (I + 1), i = q % (I + 1);
+    if (i == I && !cs) return;
+    float t = 0.f;
+    for (int s = 0; s < slices; ++s) t += part[(size_t)s * O * (I + 1) + q];
+    if (i < I) out[(size_t)o * I + i] = t;
+    else cs[o] = t;
+}
+
+void launch_atb(int N, int O, int I, const float *G, const float *X, float *out, float *cs, float *part,
+                cudaStream_t st) {
+    if (O == 0 || I == 0) return;
+    const int slices = std::max(1, std::min(ATB_SLICES, (N + 255) / 256));
+    dim3 grid((O + ATB_T - 1) / ATB_T, (I + ATB_T - 1) / ATB_T, slices);
+    k_atb_part<<<grid, 256, 0, st>>>(N, O, I, G, X, part, cs != nullptr, slices);
+    count_launch();
+    const int tot = O * (I + 1);
+    k_atb_reduce<<<(tot + 255) / 256, 256, 0, st>>>(O, I, part, out, cs, slices);
+    count_launch();
 }
 
 __global__ void k_distill_residual(int n, const float *F, const float *T, float *g, float *sq) {

@@ -44,10 +44,16 @@ void launch_nc_head(int K, int n_c, int n_l, const NCHeadArgs &a, cudaStream_t s
 
 // Adjoint of the NC head with respect to its q/k rows (distillation): with
 // gF[i] = dL/dF_i (after the mean subtraction's adjoint) writes
-// gQKT[c][i] = dL/dQK[i][c] (transposed, [2 H n_c][N]). Uses a.x, box, lists,
-// rc, bnorm, p, QK, V, scale, order, err of the forward's arguments.
-void launch_nc_head_bwd(int K, int n_c, int n_l, const NCHeadArgs &a, const float *gF, float *gQKT,
+// gQK[i][c] = dL/dQK[i][c] ([N][2 H n_c]). Uses a.x, box, lists, rc, bnorm,
+// p, QK, V, scale, order, err of the forward's arguments.
+void launch_nc_head_bwd(int K, int n_c, int n_l, const NCHeadArgs &a, const float *gF, float *gQK,
                         cudaStream_t st);
+// Weight gradient out[o][i] = sum_a G[a][o] X[a][i] (G [N][O], X [N][I]) and,
+// when cs is set, cs[o] = sum_a G[a][o]; atoms are split into slices whose
+// partial sums (part: O (I + 1) floats per slice, slices <= 64) are added in
+// a fixed order, so the result is deterministic.
+void launch_atb(int N, int O, int I, const float *G, const float *X, float *out, float *cs, float *part,
+                cudaStream_t st);
 // g = 2 (F - T), sq = |F - T|^2 per atom.
 void launch_distill_residual(int n, const float *F, const float *T, float *g, float *sq, cudaStream_t st);
 // Adam on n parameters (fp32, moments m, v), then the bf16 copy (nullable).

@@ -439,19 +439,33 @@ def test_npt_needs_its_arrays(ctx1, water):
     st.release()
 
 
+def _nc_offsets(ns):
+    """Offsets of the NC blob's W1, b1, W2, b2 and W_qk."""
+    S_, C, K = ns.n_species, ns.C, ns.K
+    o_w1 = S_ * C + 2 * K * C
+    o_b1 = o_w1 + 2 * C * C
+    o_w2 = o_b1 + C
+    o_b2 = o_w2 + C * C
+    o_qk = o_b2 + C + ns.n_l * C
+    return {"W1": (o_w1, 2 * C * C), "b1": (o_b1, C), "W2": (o_w2, C * C), "b2": (o_b2, C),
+            "Wqk": (o_qk, 2 * (K + ns.n_l) * ns.n_c * C)}
+
+
 def test_distill_gradient_matches_oracle(models1, water):
-    """On-box distillation of the NC model's q/k projection: the loss
-    L = sum_i |F_S,i - T_i|^2 (F_S the fast force with bonds and repulsion,
-    mean subtracted) and its gradient with respect to W_qk (the adjoint of the
-    mean subtraction and of the NC head, contracted with the layer features)
-    against the oracle's loss and central differences of it."""
+    """On-box distillation of the NC model: the loss L = sum_i |F_S,i - T_i|^2
+    (F_S the fast force with bonds and repulsion, mean subtracted) and its
+    gradient with respect to the q/k projection and the MLP (the adjoint of the
+    mean subtraction, of the NC head with respect to its q/k rows, of the
+    contractions and of the SiLU MLP) against the oracle's loss and central
+    differences of it; weights not fitted get zero."""
     (cs, cb), (ns, nb_) = models1
     ctx = core.Context(cons=(cs, cb), nc=(ns, nb_))      # its own context: training changes the weights
     T = O.cons_energy_forces(water, cs, cb)[1] + O.prior(water)[1]
     d = core.DeviceSystem(water)
     nb = core.nbr_build(ctx, d, 4.0)
     loss, grad = core.nc_distill_step(ctx, d, nb, T.astype(np.float32), lr=0.0, with_grad=True)
-    loss, grad = loss.item(), grad.cpu().numpy().reshape(-1)
+    loss, grad = loss.item(), grad.cpu().numpy()
+    assert grad.size == nb_.size
 
     def L_oracle(blob):
         F, _ = O.nc_forces(water, ns, blob)
@@ -459,15 +473,29 @@ def test_distill_gradient_matches_oracle(models1, water):
 
     L0 = L_oracle(nb_)
     assert abs(loss - L0) <= 1e-4 * L0, (loss, L0)
-    nW = grad.size
+    offs = _nc_offsets(ns)
+    fitted = np.zeros(nb_.size, bool)
+    for o, n in offs.values():
+        fitted[o:o + n] = True
+    assert not np.any(grad[~fitted])
     rng = np.random.default_rng(44)
     h = 1e-3
-    for k in rng.choice(nW, 8, replace=False):
-        bp, bm = nb_.copy(), nb_.copy()
-        bp[len(nb_) - nW + k] += h
-        bm[len(nb_) - nW + k] -= h
-        fd = (L_oracle(bp) - L_oracle(bm)) / (2 * h)
-        assert abs(grad[k] - fd) <= 2e-3 * np.abs(grad).max(), (k, grad[k], fd)
+    for name, (o, n) in offs.items():
+        gmax = np.abs(grad[o:o + n]).max()
+        assert gmax > 0, name
+        for k in o + rng.choice(n, 4, replace=False):
+            bp, bm = nb_.copy(), nb_.copy()
+            bp[k] += h
+            bm[k] -= h
+            fd = (L_oracle(bp) - L_oracle(bm)) / (2 * h)
+            assert abs(grad[k] - fd) <= 2e-3 * gmax + 1e-6 * L0, (name, k, grad[k], fd)
+    # fitting W_qk alone leaves the MLP's gradient at zero
+    _, gq = core.nc_distill_step(ctx, d, nb, T.astype(np.float32), lr=0.0, params=core.L.FIT_QK, with_grad=True)
+    gq = gq.cpu().numpy()
+    o, n = offs["W1"]
+    assert not np.any(gq[o:o + n])
+    o, n = offs["Wqk"]
+    assert np.allclose(gq[o:o + n], grad[o:o + n], rtol=1e-6, atol=1e-9)
 
 
 def test_distill_adam_lowers_the_loss(models1, water):
