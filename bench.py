@@ -410,8 +410,8 @@ def main():
     sn.release()
 
     # ------------------------------------------------------- distillation
-    # on-box distillation of the NC model's q/k projection and MLP toward the
-    # full force: frames 10 single time steps apart from a BAOAB run of the
+    # on-box distillation of the NC model (every weight but the embedding)
+    # toward the full force: frames 10 single time steps apart from a BAOAB run of the
     # conservative model, 4 for training and 1 held out; |F_L| = |F - F_S| on
     # the held-out frame before and after 60 Adam steps
     ctxD = core.Context(cons=(cs, cb), nc=(ns, nb))
@@ -445,7 +445,8 @@ def main():
     ctx.sync()
     ms_dist = max_over_ranks(e0.elapsed_time(e1)) / n_dist
     rms1 = f_l_rms(frames[4])
-    side["distill"] = {"what": "NC q/k projection W_qk and MLP (W1, b1, W2, b2) fitted to the full force (Adam, lr 1e-3)",
+    side["distill"] = {"what": "every NC weight but the species embedding (W_rad, U, W1, b1, W2, b2, W_qk) fitted to "
+                               "the full force (Adam, lr 1e-3)",
                        "train_frames": 4, "steps": n_dist, "ms_per_step": ms_dist,
                        "f_l_rms_held_out_before": rms0, "f_l_rms_held_out_after": rms1,
                        "unit": "kcal/mol/A"}

@@ -331,13 +331,16 @@ void dmts_state_release(dmts_ctx *ctx, dmts_state *st);
  * NC model is distilled from the large model, Sec. 2 "Model architecture").
  * Fitted weights (`params`, a mask): DMTS_FIT_QK the head's q/k projection
  * W_qk ([2 H n_c][C]); DMTS_FIT_MLP the channel-mixing MLP of its layer
- * (W1, b1, W2, b2). With F_S the fast force of forces_nc (with
+ * (W1, b1, W2, b2); DMTS_FIT_LAYER the message-passing layer's radial
+ * weights W_rad and the tensor-head mix U (the species embedding is not
+ * fitted). With F_S the fast force of forces_nc (with
  * DMTS_WITH_BONDS: bonds and repulsion included, mean subtracted) on `sys`
  * and target T (device float [n_atoms][3], e.g. -grad U of the conservative
  * model at the same positions): loss (device double [n_replicas], may be
  * NULL) receives L = sum_i |F_S,i - T_i|^2 per replica; the gradient of
  * sum_r L (the adjoint of the mean subtraction, of the NC head with respect to
- * its q/k rows, then of the contractions and the MLP) is written to grad
+ * its q/k rows and V, of the contractions and the MLP, and of the layer with
+ * respect to its weights) is written to grad
  * (device float, the length and layout of the NC weight blob, may be NULL),
  * zero for weights not fitted; with lr > 0 one Adam step (beta1 0.9, beta2
  * 0.999, eps 1e-8; adam_step = 1, 2, ... the update count, 1 resets the
@@ -346,6 +349,7 @@ void dmts_state_release(dmts_ctx *ctx, dmts_state *st);
  */
 #define DMTS_FIT_QK 1
 #define DMTS_FIT_MLP 2
+#define DMTS_FIT_LAYER 4
 dmts_status nc_distill_step(dmts_ctx *ctx, const dmts_system *sys, const dmts_nbr *nbr, const float *target,
                             int params, float lr, int adam_step, double *loss, float *grad, void *stream);
 

@@ -15,7 +15,7 @@ _lib = None
 MAX_SPECIES = 8
 
 OK, E_INVALID, E_OOM, E_CUDA, E_NBR_OVERFLOW, E_NONFINITE, E_TIMEOUT, E_BUSY = range(8)
-FIT_QK, FIT_MLP = 1, 2   # nc_distill_step: weights to fit
+FIT_QK, FIT_MLP, FIT_LAYER = 1, 2, 4   # nc_distill_step: weights to fit
 STATUS_NAMES = {0: "OK", 1: "E_INVALID", 2: "E_OOM", 3: "E_CUDA", 4: "E_NBR_OVERFLOW",
                 5: "E_NONFINITE", 6: "E_TIMEOUT", 7: "E_BUSY"}
 FP32, BF16 = 0, 1

@@ -189,10 +189,11 @@ def energy_forces_cons(ctx: Context, dsys: DeviceSystem, nbr: NbrList, with_prio
 
 
 def nc_distill_step(ctx: Context, dsys: DeviceSystem, nbr: NbrList, target, lr: float = 0.0, step: int = 1,
-                    params: int = L.FIT_QK | L.FIT_MLP, with_grad: bool = False):
+                    params: int = L.FIT_QK | L.FIT_MLP | L.FIT_LAYER, with_grad: bool = False):
     """One distillation step of the NC model toward target forces (f32 [N,3]
     on the device), fitting `params` (L.FIT_QK: the head's q/k projection,
-    L.FIT_MLP: its MLP): returns (loss f64 [n_replicas], the gradient f32 in
+    L.FIT_MLP: its MLP, L.FIT_LAYER: the layer's radial weights and tensor-head
+    mix): returns (loss f64 [n_replicas], the gradient f32 in
     the NC weight blob's layout or None); lr > 0 applies an Adam update."""
     dev = dsys.x.device
     target = torch.as_tensor(target, dtype=torch.float32, device=dev).contiguous()

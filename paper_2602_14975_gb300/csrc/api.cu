@@ -382,7 +382,7 @@ dmts_status nc_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const i
     io.s = s0;
     io.wrad = m.wrad[0];
     io.nu = m.nu;
-    io.A = nullptr;   // the direct-force head needs q and V only (no adjoint)
+    io.A = (flags & kFlagKeepPre) ? (float *)w.dist_A.p : nullptr;   // the head needs q and V only; kept for the distillation
     io.q = (float *)w.nc_q.p;
     io.q_bf16 = q_bf;
     io.U = m.U;
@@ -876,7 +876,7 @@ dmts_status nc_distill_step(dmts_ctx *ctx, const dmts_system *sys, const dmts_nb
     if (!ctx->has_nc) return fail(ctx, DMTS_E_INVALID, "context has no NC model");
     if (!nbr || !nbr->row_ptr || !nbr->col || !target) return fail(ctx, DMTS_E_INVALID, "bad argument");
     if (nbr->r_list < ctx->nc.rc) return fail(ctx, DMTS_E_INVALID, "neighbour list cutoff below the NC cutoff");
-    if (params & ~(DMTS_FIT_QK | DMTS_FIT_MLP)) return fail(ctx, DMTS_E_INVALID, "unknown weights to fit");
+    if (params & ~(DMTS_FIT_QK | DMTS_FIT_MLP | DMTS_FIT_LAYER)) return fail(ctx, DMTS_E_INVALID, "unknown weights to fit");
     if (lr > 0.f && adam_step < 1) return fail(ctx, DMTS_E_INVALID, "adam_step counts from 1");
     if (sys->n_atoms > 0 && (!sys->bond_ptr || !sys->bond_idx || !sys->bond_r0))
         return fail(ctx, DMTS_E_INVALID, "missing bond table");
@@ -886,14 +886,17 @@ dmts_status nc_distill_step(dmts_ctx *ctx, const dmts_system *sys, const dmts_nb
     DevModel &m = ctx->nc;
     Workspace &w = ctx->ws;
     const int N = v.n, H = m.K + m.nl, QKW = 2 * H * m.nc, C = m.C;
-    const bool fit_mlp = params & DMTS_FIT_MLP, fit_qk = params & DMTS_FIT_QK;
-    const size_t nb = m.n_weights, part = (size_t)64 * QKW * (C + 1) + (size_t)64 * C * (2 * C + 1);
+    const bool fit_mlp = params & DMTS_FIT_MLP, fit_qk = params & DMTS_FIT_QK, fit_layer = params & DMTS_FIT_LAYER;
+    const size_t nb = m.n_weights, part = std::max((size_t)64 * QKW * (C + 1) + (size_t)64 * C * (2 * C + 1),
+                                                   (size_t)1024 * 2 * m.K * C);
     if (!w.dist_F.ensure(sizeof(float) * 3 * (N + 1)) || !w.dist_g.ensure(sizeof(float) * 3 * (N + 1)) ||
         !w.dist_sq.ensure(sizeof(float) * (N + 1)) || !w.dist_gqk.ensure(sizeof(float) * ((size_t)QKW * N + 1)) ||
         !w.dist_gs1.ensure(sizeof(float) * ((size_t)C * N + 1)) || !w.dist_gh.ensure(sizeof(float) * ((size_t)C * N + 1)) ||
         !w.dist_h.ensure(sizeof(float) * ((size_t)C * N + 1)) || !w.dist_dw.ensure(sizeof(float) * nb) ||
         !w.adam_m.ensure(sizeof(float) * nb) || !w.adam_v.ensure(sizeof(float) * nb) ||
-        !w.dist_part.ensure(sizeof(float) * part) || !w.ms_scratch.ensure(mean_sub_scratch_bytes(N, v.n_rep)))
+        !w.dist_part.ensure(sizeof(float) * part) || !w.ms_scratch.ensure(mean_sub_scratch_bytes(N, v.n_rep)) ||
+        !w.dist_A.ensure(sizeof(float) * ((size_t)4 * C * N + 1)) || !w.dist_gq.ensure(sizeof(float) * ((size_t)2 * C * N + 1)) ||
+        !w.dist_gv.ensure(sizeof(float) * ((size_t)3 * m.nl * N + 1)))
         return fail(ctx, DMTS_E_OOM, "workspace allocation failed");
     // forward: the fast force (it leaves q, the MLP's activations and
     // pre-activations, the layer features, the q/k rows and V in the workspace)
@@ -922,7 +925,8 @@ dmts_status nc_distill_step(dmts_ctx *ctx, const dmts_system *sys, const dmts_nb
     a.order = v.order;
     a.err = ctx->d_err;
     float *gqk = (float *)w.dist_gqk.p, *gs1 = (float *)w.dist_gs1.p, *gh = (float *)w.dist_gh.p;
-    launch_nc_head_bwd(m.K, m.nc, m.nl, a, (const float *)w.dist_g.p, gqk, st);
+    launch_nc_head_bwd(m.K, m.nc, m.nl, a, (const float *)w.dist_g.p, gqk, fit_layer ? (float *)w.dist_gv.p : nullptr,
+                       st);
     // weight gradients in the blob's layout (zero where not fitted)
     float *dw = grad ? grad : (float *)w.dist_dw.p;
     if (!ck(ctx, cudaMemsetAsync(dw, 0, sizeof(float) * nb, st), "gradient reset")) return DMTS_E_CUDA;
@@ -930,17 +934,46 @@ dmts_status nc_distill_step(dmts_ctx *ctx, const dmts_system *sys, const dmts_nb
     const float *s1 = (const float *)w.nc_s.p + (size_t)N * C;
     float *part_buf = (float *)w.dist_part.p;
     if (fit_qk) launch_atb(N, QKW, C, gqk, s1, at(m.Wqk), nullptr, part_buf, st);   // dW_qk = gQK^T s1
-    if (fit_mlp) {
+    if (fit_mlp || fit_layer) {
         // s1 = s0 + act W2^T + b2, act = silu(h), h = q W1^T + b1
         Epi e = epi(EPI_STORE);
         e.out = gs1;
         launch_gemm_f32(N, C, QKW, gqk, m.Wqk, 0, e, st);                               // g_s1 = gQK W_qk
-        launch_atb(N, C, C, gs1, (const float *)w.nc_act.p, at(m.w2[0]), at(m.b2[0]), part_buf, st);
         Epi ed = epi(EPI_DSILU);
         ed.H = (float *)w.dist_h.p;
         ed.out = gh;
         launch_gemm_f32(N, C, C, gs1, m.w2[0], 0, ed, st);                             // g_h = (g_s1 W2) silu'(h)
-        launch_atb(N, C, 2 * C, gh, (const float *)w.nc_q.p, at(m.w1[0]), at(m.b1[0]), part_buf, st);
+        if (fit_mlp) {
+            launch_atb(N, C, C, gs1, (const float *)w.nc_act.p, at(m.w2[0]), at(m.b2[0]), part_buf, st);
+            launch_atb(N, C, 2 * C, gh, (const float *)w.nc_q.p, at(m.w1[0]), at(m.b1[0]), part_buf, st);
+        }
+    }
+    if (fit_layer) {
+        // q = (A_00^2, sum_m A_1m^2) per channel, V_t = sum_c U[t][c] A_1m[c]
+        Epi e = epi(EPI_STORE);
+        e.out = (float *)w.dist_gq.p;
+        launch_gemm_f32(N, 2 * C, C, gh, m.w1[0], 0, e, st);                           // g_q = g_h W1
+        launch_nc_dU(N, C, m.nl, (const float *)w.dist_gv.p, (const float *)w.dist_A.p, part_buf, at(m.U), st);
+        NCLayerGradArgs la;
+        la.x = v.x;
+        la.atom_rep = v.atom_rep;
+        la.box = v.box;
+        la.row_ptr = nbr->row_ptr;
+        la.col = nbr->col;
+        la.n_atoms = N;
+        la.rc = m.rc;
+        la.inv_rc = 1.f / m.rc;
+        la.bnorm = sqrtf(2.f / m.rc);
+        la.nu = m.nu;
+        la.p = m.p;
+        la.s0 = (const float *)w.nc_s.p;
+        la.A = (const float *)w.dist_A.p;
+        la.gq = (const float *)w.dist_gq.p;
+        la.gV = (const float *)w.dist_gv.p;
+        la.U = m.U;
+        la.n_l = m.nl;
+        la.err = ctx->d_err;
+        launch_nc_layer_wgrad(C, la, part_buf, at(m.wrad[0]), st);
     }
     if (lr > 0.f && params) {
         if (adam_step == 1 && (!ck(ctx, cudaMemsetAsync(w.adam_m.p, 0, sizeof(float) * nb, st), "adam reset") ||
@@ -951,6 +984,10 @@ dmts_status nc_distill_step(dmts_ctx *ctx, const dmts_system *sys, const dmts_nb
             launch_adam((int)n, p, dw + o, (float *)w.adam_m.p + o, (float *)w.adam_v.p + o, lr, adam_step, bf, st);
         };
         if (fit_qk) adam(m.Wqk, (size_t)QKW * C, m.bf16 ? m.wqk_bf : nullptr);
+        if (fit_layer) {
+            adam(m.wrad[0], (size_t)2 * m.K * C, nullptr);
+            adam(m.U, (size_t)m.nl * C, nullptr);
+        }
         if (fit_mlp) {
             adam(m.w1[0], (size_t)C * 2 * C, m.bf16 ? m.w1_bf[0] : nullptr);
             adam(m.b1[0], C, nullptr);

@@ -60,13 +60,14 @@ struct Workspace {
     // distillation of the NC model: residual, q/k-row and feature gradients,
     // pre-activation, blob-shaped weight gradient, Adam moments, split sums
     Buf dist_F, dist_g, dist_sq, dist_gqk, dist_gs1, dist_gh, dist_h, dist_dw, adam_m, adam_v, dist_part;
+    Buf dist_A, dist_gq, dist_gv;
     void release_all() {
         Buf *all[] = {&s, &A, &q, &h, &act, &u, &gz, &gs0, &gs1, &gA, &e_atom, &ftmp, &atom_rep,
                       &nc_s, &nc_q, &nc_act, &nc_qk, &nc_v, &nc_f,
                       &q_bf, &act_bf, &s_bf, &gz_bf, &gs0_bf, &gs1_bf, &nc_q_bf, &nc_act_bf, &nc_s_bf,
                       &ms_scratch, &nc_w, &cons_w, &nc_w_last,
                       &dist_F, &dist_g, &dist_sq, &dist_gqk, &dist_gs1, &dist_gh, &dist_h, &dist_dw,
-                      &adam_m, &adam_v, &dist_part};
+                      &adam_m, &adam_v, &dist_part, &dist_A, &dist_gq, &dist_gv};
         for (Buf *b : all) b->release();
     }
 };
@@ -154,8 +155,8 @@ dmts_status fail(dmts_ctx *ctx, dmts_status s, const std::string &msg);
 // embedding is not recomputed (set within one respa_step call, where the
 // species do not change).
 constexpr int kFlagEmbedded = 1 << 30;
-// Internal flag of nc_eval: keep the MLP pre-activation (ws.dist_h) for the
-// distillation's backward pass.
+// Internal flag of nc_eval: keep the layer output A (ws.dist_A) and the MLP
+// pre-activation (ws.dist_h) for the distillation's backward pass.
 constexpr int kFlagKeepPre = 1 << 29;
 dmts_status cons_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const int *col, double *energy,
                       float *forces, int flags, cudaStream_t st, double *virial = nullptr);

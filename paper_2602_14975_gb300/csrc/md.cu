@@ -359,7 +359,7 @@ void launch_nc_head(int K, int n_c, int n_l, const NCHeadArgs &a, cudaStream_t s
 // gradients: no atomics, deterministic.
 template <int K, int NC, int NL>
 __global__ void __launch_bounds__(128) k_nc_head_bwd(NCHeadArgs g, const float *__restrict__ gF,
-                                                    float *__restrict__ gQK) {
+                                                    float *__restrict__ gQK, float *__restrict__ gV) {
     constexpr int H = K + NL, QKW = 2 * H * NC;
     static_assert(2 * H <= 32, "one lane per head and role");
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(128) k_nc_head_bwd(NCHeadArgs g, const float *
     const int h = role_aj ? lane : (live ? lane - H : 0);
     const float isnc = rsqrtf((float)NC);
     // own row: q_a[h] (role aj) or k_a[h] (role ja)
-    float mine[NC], acc[NC];
+    float mine[NC], acc[NC], accv[3] = {0.f, 0.f, 0.f};   // accv: dL/dV_at on the tensor-head lanes of role aj
     const float *ra = g.QK + (size_t)a * QKW + (role_aj ? 0 : H * NC) + h * NC;
 #pragma unroll
     for (int d = 0; d < NC; ++d) {
@@ -439,9 +439,18 @@ __global__ void __launch_bounds__(128) k_nc_head_bwd(NCHeadArgs g, const float *
             G = h < K ? -fc * Bh * (ux * (-nx + T_ja[0]) + uy * (-ny + T_ja[1]) + uz * (-nz + T_ja[2]))
                       : -fc * S_ja * (ux * vt[0] + uy * vt[1] + uz * vt[2]);
         }
+        if (role_aj && h >= K) {
+            // V_at enters F_aj = f_c S_aj (n + sum_t c_aj(K+t) V_at) only
+            const float f = fc * S_aj * c;
+            accv[0] = fmaf(f, ux, accv[0]); accv[1] = fmaf(f, uy, accv[1]); accv[2] = fmaf(f, uz, accv[2]);
+        }
         G *= isnc;
 #pragma unroll
         for (int d = 0; d < NC; ++d) acc[d] = fmaf(G, other[d], acc[d]);
+    }
+    if (gV && role_aj && h >= K) {
+        float *o = gV + ((size_t)a * NL + (h - K)) * 3;
+        o[0] = accv[0]; o[1] = accv[1]; o[2] = accv[2];
     }
     if (live) {
         const int c0 = (role_aj ? 0 : H * NC) + h * NC;
@@ -451,18 +460,18 @@ __global__ void __launch_bounds__(128) k_nc_head_bwd(NCHeadArgs g, const float *
 }
 
 template <int K, int NC, int NL>
-static void nc_head_bwd_launch(const NCHeadArgs &a, const float *gF, float *gQK, cudaStream_t st) {
-    k_nc_head_bwd<K, NC, NL><<<(a.n_atoms + 3) / 4, 128, 0, st>>>(a, gF, gQK);
+static void nc_head_bwd_launch(const NCHeadArgs &a, const float *gF, float *gQK, float *gV, cudaStream_t st) {
+    k_nc_head_bwd<K, NC, NL><<<(a.n_atoms + 3) / 4, 128, 0, st>>>(a, gF, gQK, gV);
     count_launch();
 }
 
-void launch_nc_head_bwd(int K, int n_c, int n_l, const NCHeadArgs &a, const float *gF, float *gQK,
+void launch_nc_head_bwd(int K, int n_c, int n_l, const NCHeadArgs &a, const float *gF, float *gQK, float *gV,
                         cudaStream_t st) {
     if (a.n_atoms == 0) return;
-    if (K == 8 && n_c == 8 && n_l == 2) nc_head_bwd_launch<8, 8, 2>(a, gF, gQK, st);
-    else if (K == 8 && n_c == 8 && n_l == 1) nc_head_bwd_launch<8, 8, 1>(a, gF, gQK, st);
-    else if (K == 8 && n_c == 8 && n_l == 3) nc_head_bwd_launch<8, 8, 3>(a, gF, gQK, st);
-    else if (K == 8 && n_c == 8 && n_l == 4) nc_head_bwd_launch<8, 8, 4>(a, gF, gQK, st);
+    if (K == 8 && n_c == 8 && n_l == 2) nc_head_bwd_launch<8, 8, 2>(a, gF, gQK, gV, st);
+    else if (K == 8 && n_c == 8 && n_l == 1) nc_head_bwd_launch<8, 8, 1>(a, gF, gQK, gV, st);
+    else if (K == 8 && n_c == 8 && n_l == 3) nc_head_bwd_launch<8, 8, 3>(a, gF, gQK, gV, st);
+    else if (K == 8 && n_c == 8 && n_l == 4) nc_head_bwd_launch<8, 8, 4>(a, gF, gQK, gV, st);
 }
 
 // ------------------------------------------------ weight gradients (A^T B)
@@ -526,6 +535,123 @@ void launch_atb(int N, int O, int I, const float *G, const float *X, float *out,
     count_launch();
     const int tot = O * (I + 1);
     k_atb_reduce<<<(tot + 255) / 256, 256, 0, st>>>(O, I, part, out, cs, slices);
+    count_launch();
+}
+
+// ------------------------------------------- NC layer weight gradients
+// Blocks of four warps take atoms in a grid stride; lanes own channel sets
+// (C / 32 each); every lane sweeps the atom's active edges in list order.
+// Each block adds its warps' sums in warp order into its partial row, and
+// k_sum_rows adds the blocks' rows in block order: deterministic.
+constexpr int WG_BLOCKS = 1024;
+
+template <int C>
+__global__ void __launch_bounds__(128) k_nc_layer_wgrad(NCLayerGradArgs g, float *__restrict__ part) {
+    constexpr int K = 8, CPW = C / 32, NW = 2 * K * C;
+    __shared__ float red[4][NW];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float wacc[2][K][CPW];
+#pragma unroll
+    for (int l = 0; l < 2; ++l)
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+#pragma unroll
+            for (int u = 0; u < CPW; ++u) wacc[l][k][u] = 0.f;
+    const float rc2 = g.rc * g.rc;
+    for (int i = blockIdx.x * 4 + warp; i < g.n_atoms && !*g.err; i += gridDim.x * 4) {
+        float gA[4][CPW];
+#pragma unroll
+        for (int u = 0; u < CPW; ++u) {
+            const int c = lane * CPW + u;
+            const float g0 = g.gq[(size_t)i * 2 * C + c], g1 = g.gq[(size_t)i * 2 * C + C + c];
+            gA[0][u] = 2.f * g.A[((size_t)i * 4) * C + c] * g0;
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                float t = 2.f * g.A[((size_t)i * 4 + 1 + m) * C + c] * g1;
+                for (int h = 0; h < g.n_l; ++h) t = fmaf(g.U[h * C + c], g.gV[((size_t)i * g.n_l + h) * 3 + m], t);
+                gA[1 + m][u] = t;
+            }
+        }
+        const int rep = g.atom_rep[i];
+        const float bx = g.box[3 * rep], by = g.box[3 * rep + 1], bz = g.box[3 * rep + 2];
+        const float ibx = bx > 0.f ? 1.f / bx : 0.f, iby = by > 0.f ? 1.f / by : 0.f, ibz = bz > 0.f ? 1.f / bz : 0.f;
+        const float xi = g.x[3 * i], yi = g.x[3 * i + 1], zi = g.x[3 * i + 2];
+        for (int e = g.row_ptr[i]; e < g.row_ptr[i + 1]; ++e) {
+            const int j = __ldg(g.col + e);
+            const float dx = min_img(__ldg(g.x + 3 * j) - xi, bx, ibx);
+            const float dy = min_img(__ldg(g.x + 3 * j + 1) - yi, by, iby);
+            const float dz = min_img(__ldg(g.x + 3 * j + 2) - zi, bz, ibz);
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            if (!(r2 < rc2)) continue;   // uniform over the warp
+            const float r = sqrtf(r2), inv = 1.f / r;
+            float du;
+            const float fc = envelope(r * g.inv_rc, g.p, &du);
+            float B[K], Y[4];
+            bessel<K, false>(r, g.inv_rc, g.bnorm, B, nullptr);
+            sph<1>(dx * inv, dy * inv, dz * inv, Y);
+#pragma unroll
+            for (int u = 0; u < CPW; ++u) {
+                const float sj = __ldg(g.s0 + (size_t)j * C + lane * CPW + u);
+                const float z0 = gA[0][u] * Y[0] * sj * fc;
+                const float z1 = fmaf(gA[1][u], Y[1], fmaf(gA[2][u], Y[2], gA[3][u] * Y[3])) * sj * fc;
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    wacc[0][k][u] = fmaf(z0, B[k], wacc[0][k][u]);
+                    wacc[1][k][u] = fmaf(z1, B[k], wacc[1][k][u]);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int l = 0; l < 2; ++l)
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+#pragma unroll
+            for (int u = 0; u < CPW; ++u) red[warp][(l * K + k) * C + lane * CPW + u] = g.nu * wacc[l][k][u];
+    __syncthreads();
+    for (int q = threadIdx.x; q < NW; q += blockDim.x)
+        part[(size_t)blockIdx.x * NW + q] = ((red[0][q] + red[1][q]) + red[2][q]) + red[3][q];
+}
+
+__global__ void k_sum_rows(int Q, int rows, const float *__restrict__ part, float *__restrict__ out) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= Q) return;
+    float t = 0.f;
+    for (int r = 0; r < rows; ++r) t += part[(size_t)r * Q + q];
+    out[q] = t;
+}
+
+void launch_nc_layer_wgrad(int C, const NCLayerGradArgs &a, float *part, float *out, cudaStream_t st) {
+    if (a.n_atoms == 0) return;
+    const int blocks = std::max(1, std::min(WG_BLOCKS, (a.n_atoms + 3) / 4));
+    if (C == 32) k_nc_layer_wgrad<32><<<blocks, 128, 0, st>>>(a, part);
+    else if (C == 64) k_nc_layer_wgrad<64><<<blocks, 128, 0, st>>>(a, part);
+    else return;
+    count_launch();
+    const int Q = 2 * 8 * C;
+    k_sum_rows<<<(Q + 255) / 256, 256, 0, st>>>(Q, blocks, part, out);
+    count_launch();
+}
+
+__global__ void k_nc_dU_part(int n, int C, int n_l, const float *__restrict__ gV, const float *__restrict__ A,
+                             float *__restrict__ part, int slices) {
+    const int q = threadIdx.x;   // q = t C + c
+    if (q >= n_l * C) return;
+    const int t = q / C, c = q - t * C;
+    const int per = (n + slices - 1) / slices, a0 = blockIdx.x * per, a1 = min(n, a0 + per);
+    float acc = 0.f;
+    for (int i = a0; i < a1; ++i)
+#pragma unroll
+        for (int m = 0; m < 3; ++m) acc = fmaf(gV[((size_t)i * n_l + t) * 3 + m], A[((size_t)i * 4 + 1 + m) * C + c], acc);
+    part[(size_t)blockIdx.x * n_l * C + q] = acc;
+}
+
+void launch_nc_dU(int n, int C, int n_l, const float *gV, const float *A, float *part, float *out, cudaStream_t st) {
+    if (n == 0) return;
+    const int slices = std::max(1, std::min(64, (n + 255) / 256));
+    k_nc_dU_part<<<slices, 256, 0, st>>>(n, C, n_l, gV, A, part, slices);
+    count_launch();
+    k_sum_rows<<<(n_l * C + 255) / 256, 256, 0, st>>>(n_l * C, slices, part, out);
     count_launch();
 }
 

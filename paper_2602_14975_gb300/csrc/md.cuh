@@ -44,10 +44,34 @@ void launch_nc_head(int K, int n_c, int n_l, const NCHeadArgs &a, cudaStream_t s
 
 // Adjoint of the NC head with respect to its q/k rows (distillation): with
 // gF[i] = dL/dF_i (after the mean subtraction's adjoint) writes
-// gQK[i][c] = dL/dQK[i][c] ([N][2 H n_c]). Uses a.x, box, lists, rc, bnorm,
-// p, QK, V, scale, order, err of the forward's arguments.
-void launch_nc_head_bwd(int K, int n_c, int n_l, const NCHeadArgs &a, const float *gF, float *gQK,
+// gQK[i][c] = dL/dQK[i][c] ([N][2 H n_c]) and, when gV is set,
+// gV[i][t][m] = dL/dV[i][t][m] ([N][n_l][3]). Uses a.x, box, lists, rc,
+// bnorm, p, QK, V, scale, order, err of the forward's arguments.
+void launch_nc_head_bwd(int K, int n_c, int n_l, const NCHeadArgs &a, const float *gF, float *gQK, float *gV,
                         cudaStream_t st);
+// Gradients of the NC layer's weights (distillation), l_max = 1, K = 8.
+struct NCLayerGradArgs {
+    const float *x;
+    const int *atom_rep;
+    const float *box;
+    const int *row_ptr, *col;      // NC list
+    int n_atoms;
+    float rc, inv_rc, bnorm, nu;
+    int p;
+    const float *s0;               // [N][C] layer input features
+    const float *A;                // [N][4][C] layer output A = nu sum_j R Y s_j
+    const float *gq;               // [N][2][C] dL/dq (q_l = sum_m A_lm^2)
+    const float *gV;               // [N][n_l][3] dL/dV (V_t = sum_c U[t][c] A_1m[c])
+    const float *U;                // [n_l][C]
+    int n_l;
+    const int *err;
+};
+// dW_rad[l][k][c] = nu sum_i sum_j gA_i[lm][c] s_j[c] Y_lm f_c B_k (lm in l), with
+// gA_i = 2 A_i gq_i + (l = 1) sum_t U[t] gV_i[t][m]; part: >= 2 K C floats per
+// block of the launch (at most 1,024 blocks).
+void launch_nc_layer_wgrad(int C, const NCLayerGradArgs &a, float *part, float *out, cudaStream_t st);
+// dU[t][c] = sum_i sum_m gV_i[t][m] A_i[1+m][c]; part: n_l C floats per slice (<= 64).
+void launch_nc_dU(int n, int C, int n_l, const float *gV, const float *A, float *part, float *out, cudaStream_t st);
 // Weight gradient out[o][i] = sum_a G[a][o] X[a][i] (G [N][O], X [N][I]) and,
 // when cs is set, cs[o] = sum_a G[a][o]; atoms are split into slices whose
 // partial sums (part: O (I + 1) floats per slice, slices <= 64) are added in

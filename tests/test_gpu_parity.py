@@ -440,24 +440,28 @@ def test_npt_needs_its_arrays(ctx1, water):
 
 
 def _nc_offsets(ns):
-    """Offsets of the NC blob's W1, b1, W2, b2 and W_qk."""
+    """Offsets of the NC blob's W_rad, W1, b1, W2, b2, U and W_qk."""
     S_, C, K = ns.n_species, ns.C, ns.K
-    o_w1 = S_ * C + 2 * K * C
+    o_wr = S_ * C
+    o_w1 = o_wr + 2 * K * C
     o_b1 = o_w1 + 2 * C * C
     o_w2 = o_b1 + C
     o_b2 = o_w2 + C * C
-    o_qk = o_b2 + C + ns.n_l * C
-    return {"W1": (o_w1, 2 * C * C), "b1": (o_b1, C), "W2": (o_w2, C * C), "b2": (o_b2, C),
-            "Wqk": (o_qk, 2 * (K + ns.n_l) * ns.n_c * C)}
+    o_u = o_b2 + C
+    o_qk = o_u + ns.n_l * C
+    return {"Wrad": (o_wr, 2 * K * C), "W1": (o_w1, 2 * C * C), "b1": (o_b1, C), "W2": (o_w2, C * C),
+            "b2": (o_b2, C), "U": (o_u, ns.n_l * C), "Wqk": (o_qk, 2 * (K + ns.n_l) * ns.n_c * C)}
 
 
 def test_distill_gradient_matches_oracle(models1, water):
     """On-box distillation of the NC model: the loss L = sum_i |F_S,i - T_i|^2
     (F_S the fast force with bonds and repulsion, mean subtracted) and its
-    gradient with respect to the q/k projection and the MLP (the adjoint of the
-    mean subtraction, of the NC head with respect to its q/k rows, of the
-    contractions and of the SiLU MLP) against the oracle's loss and central
-    differences of it; weights not fitted get zero."""
+    gradient with respect to the q/k projection, the MLP, the radial weights
+    and the tensor-head mix (the adjoint of the mean subtraction, of the NC
+    head with respect to its q/k rows and V, of the contractions and the SiLU
+    MLP, and of the message-passing layer with respect to its weights) against
+    the oracle's loss and central differences of it; the species embedding,
+    not fitted, gets zero."""
     (cs, cb), (ns, nb_) = models1
     ctx = core.Context(cons=(cs, cb), nc=(ns, nb_))      # its own context: training changes the weights
     T = O.cons_energy_forces(water, cs, cb)[1] + O.prior(water)[1]
