@@ -37,7 +37,7 @@ PROF_EVERY = 4   # time every 4th outer step of the timed region per kernel
 KCAL_A3_PER_ATM = 101325.0 * 6.02214076e23 * 1e-30 / 4184.0   # 1 atm in kcal/mol/A^3
 
 NCU_TRAFFIC = {
-    "mp_bwd": {"bytes_per_launch": (153771520 + 15115008 + 154084864 + 12173312 + 141766912 + 233728) / 3,
+    "mp_bwd": {"bytes_per_launch": (153792768 + 14773248 + 154217472 + 12226560 + 141881088 + 280320) / 3,
                # the adjoint's code: channel-pack helpers, kernel and launch, the
                # argument structs, the device helpers
                "sources": [("paper_2602_14975_gb300/csrc/mp.cu", ("// ---- channel packs", "// ---- forward")),
@@ -46,7 +46,7 @@ NCU_TRAFFIC = {
                                                                   "#define DMTS_DISPATCH")),
                            ("paper_2602_14975_gb300/csrc/mp.cuh", ("struct EdgeGeom {", "template <int CPW>")),
                            ("paper_2602_14975_gb300/csrc/common.cuh", None)],
-               "sha256": "2638b92428b8a377051f0e6df5cc319f49c27bb51659fe0201a89c948d978175"},
+               "sha256": "3796c7e6556c549033dba13f00650618a0defe87a98c4c586074b1306b886a7e"},
 }
 
 
