@@ -63,8 +63,6 @@ def _declare(L):
         f = getattr(L, name)
         f.restype = ct.c_double
         f.argtypes = [ct.c_int, _D, _U8, _D, _I, _D, _D, _D]
-    L.orc_cons_features.restype = None
-    L.orc_cons_features.argtypes = [ct.c_int, _D, _U8, _D, _I, _D, _D, _D]
     L.orc_prior.restype = ct.c_double
     L.orc_prior.argtypes = [ct.c_int, _D, _U8, _I, _D, ct.c_int, _I, _D, _D, ct.c_int, _D, _D]
     L.orc_nc_forces.restype = None
@@ -176,19 +174,6 @@ def cons_energy_forces(sys, spec, blob):
     F = np.zeros((x.shape[0], 3))
     E = L.orc_cons_energy_forces(x.shape[0], px, ps, pb, pmi, pmr, pw, F.ctypes.data_as(_D))
     return E, F
-
-
-def cons_features(sys, spec, blob):
-    L = lib()
-    x, px = _d(sys.x)
-    sp, ps = _u8(sys.species)
-    box, pb = _d(sys.box)
-    mi, pmi = _i(model_ints(spec))
-    mr, pmr = _d(model_reals(spec))
-    w, pw = _d(blob)
-    out = np.zeros((spec.L + 1, x.shape[0], spec.C))
-    L.orc_cons_features(x.shape[0], px, ps, pb, pmi, pmr, pw, out.ctypes.data_as(_D))
-    return out
 
 
 def prior(sys, with_lj=True, consts=PRIOR, terms=None):

@@ -510,27 +510,6 @@ double orc_cons_energy_forces(int n, const double *x, const uint8_t *species, co
     return cons_eval(&m, &sy, NULL, F);
 }
 
-/* Node features of the conservative model after every layer (for tests of
- * intermediate quantities): s_out[(L+1)][n][C]. */
-void orc_cons_features(int n, const double *x, const uint8_t *species, const double *box,
-                       const int *mi, const double *mr, const double *blob, double *s_out)
-{
-    model_t m;
-    parse_cons(&m, mi, mr, blob);
-    int C = m.C, nlm = m.nlm, nl1 = m.lmax + 1;
-    edges_t E;
-    edges_build(n, x, box, m.rc, &E);
-    double *A = malloc(sizeof(double) * n * C * nlm);
-    double *q = malloc(sizeof(double) * n * nl1 * C);
-    double *h = malloc(sizeof(double) * n * C);
-    for (int i = 0; i < n; ++i)
-        for (int c = 0; c < C; ++c) s_out[(long)i * C + c] = m.emb[species[i] * C + c];
-    for (int t = 0; t < m.L; ++t)
-        mp_layer_forward(&m, t, n, &E, s_out + (long)t * n * C, A, q, h, s_out + (long)(t + 1) * n * C);
-    free(A); free(q); free(h);
-    edges_free(&E);
-}
-
 /* ------------------------------------------------------------------------ */
 /* Prior: harmonic bonds + Lennard-Jones between heavy atoms of different    */
 /* molecules, switched off smoothly at 5 A by the p=6 envelope.              */

@@ -727,6 +727,22 @@ def test_baro_pressure_units_and_force():
     assert math.isclose(O.baro_mass(n, 300.0, 2000.0), (3 * n + 3) * kB * 300.0 * 2000.0 ** 2, rel_tol=1e-13)
 
 
+def test_kinetic_energy_units_and_equipartition():
+    # 1 amu A^2 / fs^2 = 1e-3 kg/mol x 1e10 m^2/s^2 = 1e7 J/mol = 1e7 / 4184
+    # kcal/mol (CODATA amu x N_A = 1e-3 kg/mol to 4e-10); a Maxwell-Boltzmann
+    # sample at T holds 3/2 N kT on average (relative spread sqrt(2 / 3N))
+    m = np.array([2.0, 16.0])
+    v = np.array([[1.0, 2.0, 2.0], [0.0, 0.0, 0.5]])
+    amu_na = 1.66053906660e-27 * 6.02214076e23
+    e_unit = amu_na * 1e10 / 4184.0
+    assert math.isclose(O.kinetic(v, m), (0.5 * 2.0 * 9.0 + 0.5 * 16.0 * 0.25) * e_unit, rel_tol=1e-8)
+    n, T = 30000, 300.0
+    mm = np.where(np.arange(n) % 3 == 0, 15.999, 1.008)
+    vv = S.maxwell_boltzmann(mm, T, 11)
+    kB = 8.314462618 / 4184.0
+    assert abs(O.kinetic(vv, mm) / (1.5 * n * kB * T) - 1.0) < 5.0 * math.sqrt(2.0 / (3 * n))
+
+
 def test_baro_ideal_gas_volume_distribution():
     # an ideal gas (no forces) under the piston samples the isothermal-
     # isobaric volume density V^N exp(-P V / kT): <V> = (N + 1) kT / P and
