@@ -45,3 +45,19 @@ def band_pairs(sy, pairs, rcut, eps=1e-4):
         if abs(float(d @ d) - rcut * rcut) < eps:
             out.add((i, j))
     return out
+
+
+def cluster_around(sy, center, radius):
+    """Atoms within `radius` (minimum image) of atom `center`, unwrapped
+    around it, as an open-boundary system; bonds inside the cluster kept.
+    Returns (system, index of the centre in it)."""
+    d = sy.x - sy.x[center]
+    d -= sy.box * np.round(d / sy.box)
+    keep = np.nonzero((d ** 2).sum(1) < radius ** 2)[0]
+    remap = -np.ones(sy.n_atoms, np.int64)
+    remap[keep] = np.arange(keep.size)
+    b = sy.bonds
+    bm = (remap[b[:, 0]] >= 0) & (remap[b[:, 1]] >= 0)
+    sub = S.System(f"{sy.name}_around_{center}", sy.x[center] + d[keep], sy.species[keep], sy.mol_id[keep],
+                   remap[b[bm]].astype(np.int32), sy.bond_r0[bm], np.zeros(3))
+    return sub, int(remap[center])

@@ -12,6 +12,7 @@ torch = pytest.importorskip("torch")
 import oracle as O
 from paper_2602_14975_gb300 import core
 from paper_2602_14975_gb300 import synth as S
+from tests.helpers import cluster_around
 
 pytestmark = pytest.mark.gpu
 
@@ -27,22 +28,6 @@ def chain():
 def weights():
     cs, ns = W["cons"](), W["nc"]()
     return S.cons_weights(cs, W["w_seed"]), S.nc_weights(ns, W["w_seed"])
-
-
-def _cluster(sy, center, radius):
-    """Atoms within `radius` (minimum image) of atom `center`, unwrapped
-    around it, as an open-boundary system; bonds inside the cluster kept.
-    Returns (system, index of the centre in it)."""
-    d = sy.x - sy.x[center]
-    d -= sy.box * np.round(d / sy.box)
-    keep = np.nonzero((d ** 2).sum(1) < radius ** 2)[0]
-    remap = -np.ones(sy.n_atoms, np.int64)
-    remap[keep] = np.arange(keep.size)
-    b = sy.bonds
-    bm = (remap[b[:, 0]] >= 0) & (remap[b[:, 1]] >= 0)
-    sub = S.System(f"{sy.name}_around_{center}", sy.x[center] + d[keep], sy.species[keep], sy.mol_id[keep],
-                   remap[b[bm]].astype(np.int32), sy.bond_r0[bm], np.zeros(3))
-    return sub, int(remap[center])
 
 
 def test_total_energy_full_size(chain, weights):
@@ -78,7 +63,7 @@ def test_nc_forces_sampled_atoms_full_size(chain, weights, bf16):
     sample = rng.choice(chain.n_atoms, 24, replace=False)
     ref = np.zeros((sample.size, 3))
     for k, i in enumerate(sample):
-        sub, c = _cluster(chain, int(i), 2 * ns.rc + 0.5)
+        sub, c = cluster_around(chain, int(i), 2 * ns.rc + 0.5)
         Fs, net_s = O.nc_forces(sub, ns, nb_w)
         ref[k] = Fs[c] + net_s / sub.n_atoms
     err = np.abs(pre[sample] - ref).max()
