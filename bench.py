@@ -653,6 +653,13 @@ def main():
     g = rate(gemm_flop_nc * I.n_inner, t_ncg, 1e12)
     kr["nc_gemm_tc"] = {"row": "a4 (NC)", "bound": "tensor", "tflops": g,
                         "frac_bf16_sustained": g / bf16_pk if g and bf16_pk else None}
+    # the NC layer's forward: radial K(l_max+1) FMA + (l_max+1) mul +
+    # (l_max+1)^2 FMA per (edge, channel), as for the conservative layer
+    nnl = ns.lmax + 1
+    flop_nc_edge = 2 * (ns.K * nnl + nnl + nnl * nnl) * Cn
+    a = rate(flop_nc_edge * e_nc, per_launch_s(prof, "nc_mp_fwd"), 1e12)
+    kr["nc_mp_fwd"] = {"row": "a7 (NC layer: a2+a3 at NC sizes)", "bound": "alu", "tflops": a,
+                       "frac_fp32_peak": a / fp32_peak_tflops if a else None, "flop_per_edge": flop_nc_edge}
     b = rate(nc_bytes, per_launch_s(prof, "nc_head"), 1e9)
     kr["nc_head"] = {"row": "a7", "bound": "hbm", "gbs": b, "frac_hbm": b / hbm if b and hbm else None,
                      "bytes_per_launch": nc_bytes}
