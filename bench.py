@@ -225,10 +225,23 @@ def workload_config(sy, I, cs, ns):
             "parallelism": "replicas only (one replica per GPU)"}
 
 
+# Bytes per atom that one k_integrate launch reads and writes (fp32 vectors
+# of 12 B): an inner step reads the inverse-mass source (4), v, F_NC, x, the
+# replica index (4), the species (1) and the rebuild check's reference
+# positions and writes x and v: 57 + 24; the launch that also applies the
+# outer kick reads the cached full force too (69 + 24); the closing launch of
+# a call reads mass, v, F_NC and the full force and writes v (40 + 12).
+INTEG_B_INNER, INTEG_B_KICK, INTEG_B_CLOSE = 81, 93, 52
+
+
+def integ_bytes_per_outer_step(n_inner, with_close):
+    return INTEG_B_KICK + INTEG_B_INNER * (n_inner - 1) + (INTEG_B_CLOSE if with_close else 0)
+
+
 def serving_roofline(prof, atom_outer_steps, n_inner, cs):
     """Per-kernel rates inside the serving loop, where one launch covers every
     resident replica (often 10^5 atoms or more): the integrator against HBM
-    (65 B per atom per launch, n_inner + 1 launches per outer step) and the
+    (one call per outer step: n_inner launches and the closing one) and the
     conservative contractions against the bf16 tensor peak."""
     pk = {}
     pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -237,7 +250,7 @@ def serving_roofline(prof, atom_outer_steps, n_inner, cs):
     out = {}
     t_int = prof.get("integrate", (0, 0.0))[1] * 1e-3
     if t_int > 0:
-        gbs = 65.0 * atom_outer_steps * (n_inner + 1) / t_int / 1e9
+        gbs = integ_bytes_per_outer_step(n_inner, True) * atom_outer_steps / t_int / 1e9
         out["integrate"] = {"row": "a8", "bound": "hbm", "gbs": gbs,
                             "frac_hbm": gbs / pk["hbm_gbs"] if pk.get("hbm_gbs") else None}
     t_g = prof.get("gemm_tc", (0, 0.0))[1] * 1e-3
@@ -663,12 +676,15 @@ def main():
     b = rate(nc_bytes, per_launch_s(prof, "nc_head"), 1e9)
     kr["nc_head"] = {"row": "a7", "bound": "hbm", "gbs": b, "frac_hbm": b / hbm if b and hbm else None,
                      "bytes_per_launch": nc_bytes}
-    b = rate(65.0 * N, per_launch_s(prof, "integrate"), 1e9)
+    # average over the n_inner launches of an outer step (the one closing
+    # launch of a long call is left out)
+    ib = integ_bytes_per_outer_step(I.n_inner, False) / I.n_inner
+    b = rate(ib * N, per_launch_s(prof, "integrate"), 1e9)
     kr["integrate"] = {"row": "a8", "bound": "hbm", "gbs": b, "frac_hbm": b / hbm if b and hbm else None,
-                       "bytes_per_launch": 65 * N}
-    b = rate(65.0 * syL.n_atoms, per_launch_s(profL, "integrate"), 1e9)
+                       "bytes_per_launch": ib * N}
+    b = rate(ib * syL.n_atoms, per_launch_s(profL, "integrate"), 1e9)
     kr["integrate_100k"] = {"row": "a8", "bound": "hbm", "gbs": b, "frac_hbm": b / hbm if b and hbm else None,
-                            "bytes_per_launch": 65 * syL.n_atoms}
+                            "bytes_per_launch": ib * syL.n_atoms}
     shares = {k: {"launches": v[0], "ms_per_step": v[1] / n_prof,
                   "share": v[1] / max(sum(x[1] for x in prof.values()), 1e-9)} for k, v in prof.items()}
 
