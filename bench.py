@@ -226,7 +226,7 @@ def workload_config(sy, I, cs, ns):
 
 
 # Bytes per atom that one k_integrate launch reads and writes (fp32 vectors
-# of 12 B): an inner step reads the inverse-mass source (4), v, F_NC, x, the
+# of 12 B): an inner step reads the mass (4), v, F_NC, x, the
 # replica index (4), the species (1) and the rebuild check's reference
 # positions and writes x and v: 57 + 24; the launch that also applies the
 # outer kick reads the cached full force too (69 + 24); the closing launch of
