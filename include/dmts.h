@@ -399,9 +399,10 @@ typedef struct {
 } dmts_guard_stats;
 
 /* n_outer outer steps of Algorithm 1 on `st` (p->mode must be RESPA) under
- * the rewind guard. Allocates its saved frame (device, 4 N floats + per
- * replica counters and energies) per call; synchronises the stream once per
- * chunk to read the monitor. Returns DMTS_E_NONFINITE if the STS segment
+ * the rewind guard. Allocates its saved frame per call (device: x, v, F_NC
+ * and the full force, four [N][3] float arrays, the per-replica step
+ * counters and energies and, with the barostat, the boxes and piston
+ * states); synchronises the stream once per chunk to read the monitor. Returns DMTS_E_NONFINITE if the STS segment
  * itself goes non-finite, DMTS_E_INVALID for bad parameters. */
 dmts_status respa_guarded(dmts_ctx *ctx, dmts_state *st, const dmts_integrator *p, const dmts_guard *guard,
                           int n_outer, dmts_guard_stats *stats, void *stream);
