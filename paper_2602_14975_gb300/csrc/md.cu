@@ -1,5 +1,10 @@
 // NC direct-force head (Sec. 2 "Model architecture"), the bonded + LJ prior,
-// and the fused BAOAB/RESPA integrator with Philox4x32-10 noise (Algorithm 1).
+// and the fused BAOAB/RESPA integrator with Philox4x32-10 noise (Algorithm 1);
+// the replica-local mean subtraction of the fast force; the virial estimator
+// and the piston kernels of the NPT path (Sec. 2, virial term in NPT); and
+// the adjoint of the fast force with respect to its weights (head, weight
+// contractions, layer gradients) with the Adam update, for distillation of
+// the NC model (Sec. 2, "Model architecture").
 #include <algorithm>
 #include "md.cuh"
 #include "ptx.cuh"

@@ -1,4 +1,5 @@
-// NC direct-force head, analytic prior, fused BAOAB/RESPA integrator.
+// NC direct-force head, analytic prior, fused BAOAB/RESPA integrator, mean
+// subtraction, NPT piston and virial estimator, distillation gradients.
 #pragma once
 #include "common.cuh"
 
