@@ -328,7 +328,9 @@ void dmts_state_release(dmts_ctx *ctx, dmts_state *st);
 
 /*
  * One step of on-box distillation of the NC model toward target forces (the
- * NC model is distilled from the large model, Sec. 2 "Model architecture").
+ * NC model is a distilled version of the large model trained on forces the
+ * large model labels, Sec. 2 "Model training"; its weights, Sec. 2 "Model
+ * architecture").
  * Fitted weights (`params`, a mask): DMTS_FIT_QK the head's q/k projection
  * W_qk ([2 H n_c][C]); DMTS_FIT_MLP the channel-mixing MLP of its layer
  * (W1, b1, W2, b2); DMTS_FIT_LAYER the message-passing layer's radial

@@ -4,7 +4,7 @@
 // and the piston kernels of the NPT path (Sec. 2, virial term in NPT); and
 // the adjoint of the fast force with respect to its weights (head, weight
 // contractions, layer gradients) with the Adam update, for distillation of
-// the NC model (Sec. 2, "Model architecture").
+// the NC model (Sec. 2, "Model training").
 #include <algorithm>
 #include "md.cuh"
 #include "ptx.cuh"
