@@ -519,6 +519,54 @@ def test_respa_collapses_to_velocity_verlet(small_md):
     assert np.abs(st.v - vr).max() < 1e-10 * np.abs(vr).max()
 
 
+def test_sts_collapses_to_velocity_verlet_and_reverses(small_md):
+    # single-time-step BAOAB (the baseline of Sec. 3) at gamma = 0 is
+    # velocity Verlet with the full force, and is time reversible
+    sy, cs, cb, ns, nb, m, v = small_md
+    st = O.MDState(sy, v, m)
+    O.sts_run(st, sy, cs, cb, 0.5, 300.0, np.zeros(5), 1, 6)
+    xr, vr = _vv(sy, sy.x.copy(), v.copy(), m, 0.5, 6, cs, cb)
+    assert np.abs(st.x - xr).max() < 1e-12 * np.abs(xr).max()
+    assert np.abs(st.v - vr).max() < 1e-12 * np.abs(vr).max()
+    x1 = st.x.copy()
+    st.v = -st.v
+    O.sts_run(st, sy, cs, cb, 0.5, 300.0, np.zeros(5), 1, 6)
+    assert np.abs(x1 - sy.x).max() > 1e-3
+    assert np.abs(st.x - sy.x).max() < 1e-10
+
+
+def test_sts_free_particle_temperature():
+    # the O-step of single-time-step BAOAB thermalises free particles: mean
+    # temperature 300 K and (T/d) chi^2_d statistics of the samples
+    from scipy import stats
+    n = 400
+    sy = _free_gas(n, 3)
+    cs, cb = S.cons_spec(1, 4, 0), S.cons_weights(S.cons_spec(1, 4, 0), 1)
+    m = sy.element_masses()
+    st = O.MDState(sy, np.zeros((n, 3)), m)
+    conv, kB = 4.184e-4, 8.314462618 / 4184.0
+    Ts = []
+    for _ in range(60):
+        O.sts_run(st, sy, cs, cb, 2.0, 300.0, np.full(5, 20.0), 9, 50, outer_mode=1)
+        Ts.append((m[:, None] * st.v ** 2).sum() / conv / (3 * n * kB))
+    Ts = np.array(Ts[10:])
+    d = 3 * n
+    assert abs(Ts.mean() - 300.0) < 10 * 300.0 * math.sqrt(2.0 / d) / math.sqrt(len(Ts))
+    assert stats.kstest(Ts * d / 300.0, stats.chi2(d).cdf).pvalue > 1e-3
+
+
+def test_sts_equals_respa_with_one_inner_step_of_the_full_force(small_md):
+    # Algorithm 1 with n = 1 and F_S = F (inner_mode 1) is BAOAB with step
+    # Delta: the two oracle paths draw the same noise and agree to rounding
+    sy, cs, cb, ns, nb, m, v = small_md
+    a = O.MDState(sy, v, m)
+    O.sts_run(a, sy, cs, cb, 1.0, 300.0, np.full(5, 5.0), 17, 5)
+    b = O.MDState(sy, v, m)
+    O.respa_run(b, sy, cs, cb, ns, nb, 1.0, 1, 300.0, np.full(5, 5.0), 17, n_outer=5, inner_mode=1)
+    assert np.abs(a.x - b.x).max() < 1e-10
+    assert np.abs(a.v - b.v).max() < 1e-10 * np.abs(b.v).max()
+
+
 def test_respa_time_reversible(small_md):
     sy, cs, cb, ns, nb, m, v = small_md
     st = O.MDState(sy, v, m)
