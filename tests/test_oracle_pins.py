@@ -460,6 +460,15 @@ def test_hmr_preserves_molecule_mass():
     w = sy.mol_id > 0
     assert np.allclose(m1[w & (sy.species == S.SP_O)], 15.999 - 6.0)
     assert np.all(m1 > 0)
+    # the deficit is spread over a molecule's heavy atoms in proportion to
+    # their masses (Sec. 2 "Hydrogen Mass Repartitioning" fixes only the
+    # per-molecule total): one common factor per molecule
+    heavy = sy.species != S.SP_H
+    for mol in np.unique(sy.mol_id):
+        sel = (sy.mol_id == mol) & heavy
+        r = m1[sel] / m0[sel]
+        n_h = int(((sy.mol_id == mol) & ~heavy).sum())
+        assert np.allclose(r, 1.0 - 3.0 * n_h / m0[sel].sum(), rtol=0, atol=1e-13)
 
 
 def test_ostep_fluctuation_dissipation():
