@@ -52,6 +52,19 @@ def test_create_without_gpu_fails_cleanly(lib):
     assert not h.value
 
 
+def test_missing_library_raises_instead_of_falling_back():
+    # the product path has no CPU fallback: without the built library every
+    # entry point raises (checked in a child process with the loader pointed
+    # at a path that does not exist)
+    import subprocess
+    import sys
+    code = ("import paper_2602_14975_gb300._lib as L\n"
+            "L.lib_path = lambda: '/nonexistent/libdmts.so'\n"
+            "try:\n    L.lib(build_if_missing=False)\nexcept RuntimeError as e:\n    print('raised', e)\n")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=ROOT, timeout=300)
+    assert out.returncode == 0 and out.stdout.startswith("raised"), out.stdout + out.stderr
+
+
 def test_hmr_matches_oracle():
     sy = S.solvated_chain(n_chain=80, n_water=300, box_len=22.0, seed=5)
     m0 = sy.element_masses()
