@@ -29,6 +29,19 @@ def test_integrator_bytes_per_outer_step():
     assert bench.integ_bytes_per_outer_step(1, False) == 93
 
 
+def test_serving_roofline_counts_the_integrator_bytes():
+    # one tick = one call of one outer step: n_inner launches and the
+    # closing one; 1e6 atom-outer-steps in 1 ms of integrator time
+    from paper_2602_14975_gb300 import synth as S
+    cs = S.cons_spec(3, 128, 2)
+    prof = {"integrate": (6, 1.0), "gemm_tc": (14, 2.0)}
+    out = bench.serving_roofline(prof, 1e6, 5, cs)
+    assert out["integrate"]["gbs"] == pytest.approx((93 + 4 * 81 + 52) * 1e6 / 1e-3 / 1e9)
+    flop = 2.0 * 128 * 128 * (2 * 3 * 4 + 2) * 1e6
+    assert out["gemm_tc"]["tflops"] == pytest.approx(flop / 2e-3 / 1e12)
+    assert out["shares"] == {"gemm_tc": pytest.approx(2 / 3, abs=1e-4), "integrate": pytest.approx(1 / 3, abs=1e-4)}
+
+
 def test_adjoint_traffic_only_for_the_captured_sources():
     rec = bench.NCU_TRAFFIC["mp_bwd"]
     if bench.sources_sha256(rec["sources"]) == rec["sha256"]:
