@@ -55,7 +55,18 @@ typedef enum {
     DMTS_E_BUSY = 7           /* state already in use by an unfinished call */
 } dmts_status;
 
-typedef enum { DMTS_FP32 = 0, DMTS_BF16 = 1 } dmts_precision;
+/*
+ * Arithmetic of the MLP contractions (the paper states none; the stand-in
+ * models run them as follows). DMTS_FP32: fp32 SIMT products. DMTS_BF16:
+ * tensor cores, bf16 x bf16 products accumulated in fp32, each operand held
+ * as a split pair hi = rn_bf16(v), lo = rn_bf16(v - hi) and the products
+ * hi*hi + lo*hi + hi*lo accumulated (about 16 significant bits per operand;
+ * forces within 2e-3 of the model force's RMS). DMTS_BF16_PLAIN: the same
+ * kernels with the hi*hi products only (one bf16 rounding per operand,
+ * a third of the tensor-core work; forces off by a few per cent of the
+ * message-passing force's RMS).
+ */
+typedef enum { DMTS_FP32 = 0, DMTS_BF16 = 1, DMTS_BF16_PLAIN = 2 } dmts_precision;
 
 /*
  * Message-passing model (both the conservative model and the embedding of
@@ -488,10 +499,14 @@ dmts_status dmts_gaussians(dmts_ctx *ctx, uint64_t seed, uint32_t replica, uint6
 /* One channel-mixing contraction as the MLPs run it in bf16 mode (Sec. 2
  * "Model architecture": the perceptrons of both models): out[M][N] =
  * act[M][K] x wt[N][K]^T on the tensor cores, bf16 operands, fp32
- * accumulation. Device pointers, row-major, 16-byte aligned; K a multiple
- * of 64, N a multiple of 16, M >= 128, else DMTS_E_INVALID. */
+ * accumulation. split = 0: act is bf16 [M][K] and wt bf16 [N][K].
+ * split = 1: both are split pairs, act [M][2K] and wt [N][2K], each row
+ * holding the hi parts in columns [0, K) and the lo parts in [K, 2K), and
+ * out = act_hi wt_hi^T + act_lo wt_hi^T + act_hi wt_lo^T (DMTS_BF16).
+ * Device pointers, row-major, 16-byte aligned; K a multiple of 64, N a
+ * multiple of 16, M >= 1, else DMTS_E_INVALID. */
 dmts_status dmts_contract_bf16(dmts_ctx *ctx, int M, int N, int K, const void *act_bf16, const void *wt_bf16,
-                               float *out, void *stream);
+                               float *out, int split, void *stream);
 
 /* Bytes of device workspace a replica of n_atoms needs in the serving loop
  * (admission accounting). */

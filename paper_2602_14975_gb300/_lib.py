@@ -18,7 +18,7 @@ OK, E_INVALID, E_OOM, E_CUDA, E_NBR_OVERFLOW, E_NONFINITE, E_TIMEOUT, E_BUSY = r
 FIT_QK, FIT_MLP, FIT_LAYER = 1, 2, 4   # nc_distill_step: weights to fit
 STATUS_NAMES = {0: "OK", 1: "E_INVALID", 2: "E_OOM", 3: "E_CUDA", 4: "E_NBR_OVERFLOW",
                 5: "E_NONFINITE", 6: "E_TIMEOUT", 7: "E_BUSY"}
-FP32, BF16 = 0, 1
+FP32, BF16, BF16_PLAIN = 0, 1, 2
 MODE_RESPA, MODE_STS = 0, 1
 LANGEVIN, FFL = 0, 1
 WITH_PRIOR = 1
@@ -154,7 +154,7 @@ def _declare(L):
     L.dmts_replica_footprint.restype = ct.c_longlong
     L.dmts_replica_footprint.argtypes = [vp, i]
     L.dmts_contract_bf16.restype = i
-    L.dmts_contract_bf16.argtypes = [vp, i, i, i, vp, vp, vp, vp]
+    L.dmts_contract_bf16.argtypes = [vp, i, i, i, vp, vp, vp, i, vp]
     L.nbr_build_noalloc.restype = i
     L.nbr_build_noalloc.argtypes = [ct.POINTER(System), ct.POINTER(Nbr), ct.POINTER(ct.c_longlong), vp]
     L.dmts_profile_enable.restype = i

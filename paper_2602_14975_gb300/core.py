@@ -30,11 +30,18 @@ def _require_cuda(t: torch.Tensor, name: str):
         raise ValueError(f"{name} must be contiguous")
 
 
+def precision_of(spec) -> int:
+    """dmts_precision of a model spec: fp32, split-bf16 or plain bf16."""
+    if not spec.bf16:
+        return L.FP32
+    return L.BF16_PLAIN if getattr(spec, "bf16_plain", False) else L.BF16
+
+
 def model_struct(spec, blob) -> tuple:
     w = np.ascontiguousarray(blob, dtype=np.float64)
     m = L.Model(spec.L, spec.C, spec.lmax, spec.K, spec.n_species, spec.n_c, spec.n_l,
                 float(spec.rc), float(spec.p), float(spec.nu), float(spec.scale),
-                L.BF16 if spec.bf16 else L.FP32, w.ctypes.data_as(ct.POINTER(ct.c_double)), w.size)
+                precision_of(spec), w.ctypes.data_as(ct.POINTER(ct.c_double)), w.size)
     return m, w
 
 
@@ -430,13 +437,18 @@ def replica_footprint(ctx: Context, n_atoms: int) -> int:
     return int(ctx.lib.dmts_replica_footprint(ctx.handle, int(n_atoms)))
 
 
-def contract_bf16(ctx: Context, act: torch.Tensor, wt: torch.Tensor) -> torch.Tensor:
-    """out = act @ wt.T on the tensor cores (bf16 operands, fp32 accumulate)."""
+def contract_bf16(ctx: Context, act: torch.Tensor, wt: torch.Tensor, split: bool = False) -> torch.Tensor:
+    """out = act @ wt.T on the tensor cores (bf16 operands, fp32 accumulate).
+
+    split=True: act [M][2K] and wt [N][2K] hold hi | lo pairs per row and
+    out = act_hi wt_hi^T + act_lo wt_hi^T + act_hi wt_lo^T."""
     assert act.dtype == torch.bfloat16 and wt.dtype == torch.bfloat16
     act, wt = act.contiguous(), wt.contiguous()
     M, K = act.shape
     N = wt.shape[0]
+    if split:
+        K //= 2
     out = torch.empty(M, N, dtype=torch.float32, device=act.device)
-    L.check(ctx.lib.dmts_contract_bf16(ctx.handle, M, N, K, _ptr(act), _ptr(wt), _ptr(out), _stream(act.device)),
-            ctx.handle)
+    L.check(ctx.lib.dmts_contract_bf16(ctx.handle, M, N, K, _ptr(act), _ptr(wt), _ptr(out), int(split),
+                                       _stream(act.device)), ctx.handle)
     return out

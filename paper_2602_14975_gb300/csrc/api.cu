@@ -77,7 +77,10 @@ static dmts_status load_model(dmts_ctx *ctx, const dmts_model *in, bool is_nc, D
     m.p = (int)lrintf(in->p_env);
     m.nu = in->nu;
     m.scale = in->scale;
-    m.bf16 = in->precision == DMTS_BF16;
+    if (in->precision != DMTS_FP32 && in->precision != DMTS_BF16 && in->precision != DMTS_BF16_PLAIN)
+        return fail(ctx, DMTS_E_INVALID, "precision must be DMTS_FP32, DMTS_BF16 or DMTS_BF16_PLAIN");
+    m.bf16 = in->precision != DMTS_FP32;
+    m.nseg = in->precision == DMTS_BF16 ? 3 : 1;
     const int C = m.C, K = m.K, NL = m.lmax + 1, S = m.S;
     if (K != 8) return fail(ctx, DMTS_E_INVALID, "only K = 8 Bessel functions are supported");
     if (!(C == 32 || C == 64 || C == 128)) return fail(ctx, DMTS_E_INVALID, "C must be 32, 64 or 128");
@@ -124,16 +127,28 @@ static dmts_status load_model(dmts_ctx *ctx, const dmts_model *in, bool is_nc, D
         m.Wqk = take((size_t)2 * H * m.nc * C);   // Wq rows then Wk rows: one [2 H n_c][C] matrix
     }
     if (m.bf16) {
-        // host copies rounded to bf16 (round to nearest even), K-major
+        // split-bf16 host copies, K-major: each output row of the logical
+        // [rows'][K'] matrix holds hi = rn(w) in columns [0, K') and
+        // lo = rn(w - hi) in [K', 2K') (round to nearest even)
         std::vector<uint16_t> hb;
         auto off_of = [&](const float *p) { return (size_t)(p - m.dev); };
         auto push = [&](const float *p, int rows, int cols, bool transpose) {
             const size_t start = hb.size();
             const float *src = h.data() + off_of(p);
-            hb.resize(start + (size_t)rows * cols);
+            hb.resize(start + (size_t)2 * rows * cols);
+            const int kk = transpose ? rows : cols;   // logical row length of the copy
             for (int r = 0; r < rows; ++r)
-                for (int c = 0; c < cols; ++c)
-                    hb[start + (transpose ? (size_t)c * rows + r : (size_t)r * cols + c)] = bf16_bits(src[(size_t)r * cols + c]);
+                for (int c = 0; c < cols; ++c) {
+                    const float v = src[(size_t)r * cols + c];
+                    const uint16_t hi = bf16_bits(v);
+                    const uint32_t hu = (uint32_t)hi << 16;
+                    float hf;
+                    memcpy(&hf, &hu, 4);
+                    const uint16_t lo = bf16_bits(v - hf);
+                    const size_t orow = transpose ? (size_t)c : (size_t)r, ocol = transpose ? (size_t)r : (size_t)c;
+                    hb[start + orow * 2 * kk + ocol] = hi;
+                    hb[start + orow * 2 * kk + kk + ocol] = lo;
+                }
             return start;
         };
         std::vector<size_t> o_w1(m.L), o_w2(m.L), o_w1t(m.L), o_w2t(m.L);
@@ -210,18 +225,25 @@ static Epi epi(int mode) {
     return e;
 }
 
-// One node-level contraction: tensor cores (bf16 operands) when the model
-// runs its MLPs in bf16 and the shape allows, else the fp32 SIMT kernel.
-// trans/W32 describe the fp32 weight, Wt16 the K-major bf16 copy.
-static void contract(dmts_ctx *ctx, const DevModel &m, int M, int N, int K, const float *A32,
+// One node-level contraction: the tensor cores (split-bf16 operands) for a
+// model that runs its MLPs in bf16, whatever the number of rows M (a batch
+// smaller than one 128-row tile reads zero-filled rows), so that an atom's
+// arithmetic never depends on the batch it is in; the fp32 SIMT kernel for
+// an fp32 model. trans/W32 describe the fp32 weight, Wt16 the K-major
+// split-bf16 copy. False (with the context's error text set) when a bf16
+// model's contraction cannot be launched.
+static bool contract(dmts_ctx *ctx, const DevModel &m, int M, int N, int K, const float *A32,
                      const __nv_bfloat16 *A16, const float *W32, int trans, const __nv_bfloat16 *Wt16, const Epi &e,
                      cudaStream_t st, const char *tag_tc, const char *tag_f32) {
-    if (m.bf16 && A16 && Wt16 && M >= 128 && gemm_tc_supported(N, K)) {
+    if (m.bf16) {
         ProfScope ps(ctx, tag_tc, st);
-        if (launch_gemm_tc(M, N, K, A16, Wt16, e, ctx->d_err, st) == 0) return;
+        if (A16 && Wt16 && launch_gemm_tc(M, N, K, A16, Wt16, e, ctx->d_err, st, 1, m.nseg) == 0) return true;
+        fail(ctx, DMTS_E_CUDA, "tensor-core contraction could not be launched (operands or tensor map)");
+        return false;
     }
     ProfScope ps(ctx, tag_f32, st);
     launch_gemm_f32(M, N, K, A32, W32, trans, e, st);
+    return true;
 }
 
 // U_MP (+ prior) and F = -grad U for a batch.
@@ -239,8 +261,9 @@ dmts_status cons_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const
         !w.gA.ensure(sizeof(float) * nc_ * NLM) || !w.e_atom.ensure(sizeof(float) * (N + 1)) ||
         !w.ftmp.ensure(sizeof(float) * 3 * (N + 1)) || (virial && !w.cons_w.ensure(sizeof(float) * (N + 1))))
         return fail(ctx, DMTS_E_OOM, "workspace allocation failed");
-    if (bf && (!w.q_bf.ensure(2 * nc_ * NL + 16) || !w.act_bf.ensure(2 * nc_ + 16) || !w.s_bf.ensure(2 * nc_ + 16) ||
-               !w.gz_bf.ensure(2 * nc_ + 16) || !w.gs0_bf.ensure(2 * nc_ + 16) || !w.gs1_bf.ensure(2 * nc_ + 16)))
+    // split-bf16 copies: 4 bytes per logical element (hi and lo)
+    if (bf && (!w.q_bf.ensure(4 * nc_ * NL + 16) || !w.act_bf.ensure(4 * nc_ + 16) || !w.s_bf.ensure(4 * nc_ + 16) ||
+               !w.gz_bf.ensure(4 * nc_ + 16) || !w.gs0_bf.ensure(4 * nc_ + 16) || !w.gs1_bf.ensure(4 * nc_ + 16)))
         return fail(ctx, DMTS_E_OOM, "workspace allocation failed");
     float *S = (float *)w.s.p, *A = (float *)w.A.p, *q = (float *)w.q.p, *H = (float *)w.h.p;
     float *act = (float *)w.act.p, *u = (float *)w.u.p, *gz = (float *)w.gz.p;
@@ -267,13 +290,15 @@ dmts_status cons_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const
         e1.H = H + nc_ * t;
         e1.out = act;
         e1.out_bf16 = act_bf;
-        contract(ctx, m, N, C, NL * C, q, q_bf, m.w1[t], 1, m.w1_bf[t], e1, st, "gemm_tc", "gemm");
+        if (!contract(ctx, m, N, C, NL * C, q, q_bf, m.w1[t], 1, m.w1_bf[t], e1, st, "gemm_tc", "gemm"))
+            return DMTS_E_CUDA;
         Epi e2 = epi(EPI_RESID);
         e2.bias = m.b2[t];
         e2.res = S + nc_ * t;
         e2.out = S + nc_ * (t + 1);
         e2.out_bf16 = t == L - 1 ? s_bf : nullptr;
-        contract(ctx, m, N, C, C, act, act_bf, m.w2[t], 1, m.w2_bf[t], e2, st, "gemm_tc", "gemm");
+        if (!contract(ctx, m, N, C, C, act, act_bf, m.w2[t], 1, m.w2_bf[t], e2, st, "gemm_tc", "gemm"))
+            return DMTS_E_CUDA;
     }
     Epi er = epi(EPI_READOUT);
     er.bias = m.br;
@@ -282,14 +307,16 @@ dmts_status cons_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const
     er.out = u;
     er.out2 = gz;
     er.out_bf16 = gz_bf;
-    contract(ctx, m, N, C, C, S + nc_ * L, s_bf, m.wr, 1, m.wr_bf, er, st, "gemm_tc", "gemm");
+    if (!contract(ctx, m, N, C, C, S + nc_ * L, s_bf, m.wr, 1, m.wr_bf, er, st, "gemm_tc", "gemm"))
+        return DMTS_E_CUDA;
     { ProfScope ps(ctx, "rowsum", st); launch_rowsum(N, C, u, m.scale, e_atom, st); }
     if (forces) {
         // dU/ds^L = gz Wr
         Epi eg = epi(EPI_STORE);
         eg.out = gs0;
         eg.out_bf16 = gs0_bf;
-        contract(ctx, m, N, C, C, gz, gz_bf, m.wr, 0, m.wrt_bf, eg, st, "gemm_tc", "gemm");
+        if (!contract(ctx, m, N, C, C, gz, gz_bf, m.wr, 0, m.wrt_bf, eg, st, "gemm_tc", "gemm"))
+            return DMTS_E_CUDA;
         float *gin = gs0, *gout = gs1;
         __nv_bfloat16 *gin_bf = gs0_bf, *gout_bf = gs1_bf;
         for (int t = L - 1; t >= 0; --t) {
@@ -297,13 +324,15 @@ dmts_status cons_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const
             ed.H = H + nc_ * t;
             ed.out = act;                       // g_h
             ed.out_bf16 = act_bf;
-            contract(ctx, m, N, C, C, gin, gin_bf, m.w2[t], 0, m.w2t_bf[t], ed, st, "gemm_tc", "gemm");
+            if (!contract(ctx, m, N, C, C, gin, gin_bf, m.w2[t], 0, m.w2t_bf[t], ed, st, "gemm_tc", "gemm"))
+                return DMTS_E_CUDA;
             Epi ea = epi(EPI_GA);
             ea.A = A + nc_ * NLM * t;
             ea.out = gA;
             ea.C = C;
             ea.lmax = m.lmax;
-            contract(ctx, m, N, NL * C, C, act, act_bf, m.w1[t], 0, m.w1t_bf[t], ea, st, "gemm_tc", "gemm");
+            if (!contract(ctx, m, N, NL * C, C, act, act_bf, m.w1[t], 0, m.w1t_bf[t], ea, st, "gemm_tc", "gemm"))
+                return DMTS_E_CUDA;
             LayerIO io;
             memset(&io, 0, sizeof io);
             io.s = S + nc_ * t;
@@ -369,7 +398,7 @@ dmts_status nc_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const i
         !w.ms_scratch.ensure(mean_sub_scratch_bytes(N, s.n_rep)) ||
         (virial && !w.nc_w.ensure(sizeof(float) * (N + 1))))
         return fail(ctx, DMTS_E_OOM, "workspace allocation failed");
-    if (bf && (!w.nc_q_bf.ensure(2 * nc_ * 2 + 16) || !w.nc_act_bf.ensure(2 * nc_ + 16) || !w.nc_s_bf.ensure(2 * nc_ + 16)))
+    if (bf && (!w.nc_q_bf.ensure(4 * nc_ * 2 + 16) || !w.nc_act_bf.ensure(4 * nc_ + 16) || !w.nc_s_bf.ensure(4 * nc_ + 16)))
         return fail(ctx, DMTS_E_OOM, "workspace allocation failed");
     __nv_bfloat16 *q_bf = bf ? (__nv_bfloat16 *)w.nc_q_bf.p : nullptr;
     __nv_bfloat16 *act_bf = bf ? (__nv_bfloat16 *)w.nc_act_bf.p : nullptr;
@@ -395,16 +424,19 @@ dmts_status nc_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const i
     e1.H = (flags & kFlagKeepPre) ? (float *)w.dist_h.p : nullptr;   // kept only for the distillation
     e1.out = (float *)w.nc_act.p;
     e1.out_bf16 = act_bf;
-    contract(ctx, m, N, C, 2 * C, io.q, q_bf, m.w1[0], 1, m.w1_bf[0], e1, st, "nc_gemm_tc", "nc_gemm");
+    if (!contract(ctx, m, N, C, 2 * C, io.q, q_bf, m.w1[0], 1, m.w1_bf[0], e1, st, "nc_gemm_tc", "nc_gemm"))
+        return DMTS_E_CUDA;
     Epi e2 = epi(EPI_RESID);
     e2.bias = m.b2[0];
     e2.res = s0;
     e2.out = s1;
     e2.out_bf16 = s_bf;
-    contract(ctx, m, N, C, C, (float *)w.nc_act.p, act_bf, m.w2[0], 1, m.w2_bf[0], e2, st, "nc_gemm_tc", "nc_gemm");
+    if (!contract(ctx, m, N, C, C, (float *)w.nc_act.p, act_bf, m.w2[0], 1, m.w2_bf[0], e2, st, "nc_gemm_tc", "nc_gemm"))
+        return DMTS_E_CUDA;
     Epi e3 = epi(EPI_STORE);
     e3.out = (float *)w.nc_qk.p;
-    contract(ctx, m, N, QKW, C, s1, s_bf, m.Wqk, 1, m.wqk_bf, e3, st, "nc_gemm_tc", "nc_gemm");
+    if (!contract(ctx, m, N, QKW, C, s1, s_bf, m.Wqk, 1, m.wqk_bf, e3, st, "nc_gemm_tc", "nc_gemm"))
+        return DMTS_E_CUDA;
     NCHeadArgs a;
     a.x = s.x;
     a.atom_rep = s.atom_rep;
@@ -979,20 +1011,22 @@ dmts_status nc_distill_step(dmts_ctx *ctx, const dmts_system *sys, const dmts_nb
         if (adam_step == 1 && (!ck(ctx, cudaMemsetAsync(w.adam_m.p, 0, sizeof(float) * nb, st), "adam reset") ||
                                !ck(ctx, cudaMemsetAsync(w.adam_v.p, 0, sizeof(float) * nb, st), "adam reset")))
             return DMTS_E_CUDA;
-        auto adam = [&](float *p, size_t n, __nv_bfloat16 *bf) {
+        // bf: the weight's split-bf16 copy (K-major, logical row length kd), refreshed after the step
+        auto adam = [&](float *p, size_t n, __nv_bfloat16 *bf, int kd) {
             const size_t o = (size_t)(p - m.dev);
-            launch_adam((int)n, p, dw + o, (float *)w.adam_m.p + o, (float *)w.adam_v.p + o, lr, adam_step, bf, st);
+            launch_adam((int)n, p, dw + o, (float *)w.adam_m.p + o, (float *)w.adam_v.p + o, lr, adam_step, bf, kd,
+                        st);
         };
-        if (fit_qk) adam(m.Wqk, (size_t)QKW * C, m.bf16 ? m.wqk_bf : nullptr);
+        if (fit_qk) adam(m.Wqk, (size_t)QKW * C, m.bf16 ? m.wqk_bf : nullptr, C);
         if (fit_layer) {
-            adam(m.wrad[0], (size_t)2 * m.K * C, nullptr);
-            adam(m.U, (size_t)m.nl * C, nullptr);
+            adam(m.wrad[0], (size_t)2 * m.K * C, nullptr, 1);
+            adam(m.U, (size_t)m.nl * C, nullptr, 1);
         }
         if (fit_mlp) {
-            adam(m.w1[0], (size_t)C * 2 * C, m.bf16 ? m.w1_bf[0] : nullptr);
-            adam(m.b1[0], C, nullptr);
-            adam(m.w2[0], (size_t)C * C, m.bf16 ? m.w2_bf[0] : nullptr);
-            adam(m.b2[0], C, nullptr);
+            adam(m.w1[0], (size_t)C * 2 * C, m.bf16 ? m.w1_bf[0] : nullptr, 2 * C);
+            adam(m.b1[0], C, nullptr, 1);
+            adam(m.w2[0], (size_t)C * C, m.bf16 ? m.w2_bf[0] : nullptr, C);
+            adam(m.b2[0], C, nullptr, 1);
         }
     }
     return ck(ctx, cudaGetLastError(), "nc_distill_step launch") ? DMTS_OK : DMTS_E_CUDA;
@@ -1277,16 +1311,16 @@ dmts_status dmts_bond_table(int n_atoms, int n_bonds, const int *bonds, const fl
 }
 
 dmts_status dmts_contract_bf16(dmts_ctx *ctx, int M, int N, int K, const void *act, const void *wt, float *out,
-                               void *stream) {
-    if (!ctx || !act || !wt || !out || M < 128 || !gemm_tc_supported(N, K))
-        return fail(ctx, DMTS_E_INVALID, "dmts_contract_bf16: needs M >= 128, K % 64 == 0, N % 16 == 0");
+                               int split, void *stream) {
+    if (!ctx || !act || !wt || !out || M < 1 || !gemm_tc_supported(N, K) || (split != 0 && split != 1))
+        return fail(ctx, DMTS_E_INVALID, "dmts_contract_bf16: needs M >= 1, K % 64 == 0, N % 16 == 0, split 0 or 1");
     cudaSetDevice(ctx->device);
     Epi e;
     memset(&e, 0, sizeof e);
     e.mode = EPI_STORE;
     e.out = out;
     const int r = launch_gemm_tc(M, N, K, (const __nv_bfloat16 *)act, (const __nv_bfloat16 *)wt, e, ctx->d_err,
-                                 (cudaStream_t)stream);
+                                 (cudaStream_t)stream, split, split ? 3 : 1);
     if (r != 0) return fail(ctx, DMTS_E_INVALID, "dmts_contract_bf16: unaligned operand or tensor map failure");
     return ck(ctx, cudaGetLastError(), "dmts_contract_bf16 launch") ? DMTS_OK : DMTS_E_CUDA;
 }

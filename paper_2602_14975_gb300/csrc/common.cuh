@@ -22,6 +22,24 @@ void count_launch();
 
 __device__ __forceinline__ void set_error(int *err, int code) { atomicCAS(err, 0, code); }
 
+// Split-bf16 operand copies of the tensor-core contractions. A logical
+// [rows][K] fp32 operand is stored as bf16 [rows][2K]: column c holds
+// hi = rn(v) and column K + c holds lo = rn(v - hi), so hi + lo carries
+// about 16 significant bits. A contraction that accumulates hi*hi, lo*hi
+// and hi*lo products in fp32 loses only the lo*lo term and the rounding of
+// lo (relative ~2^-16), where a single bf16 rounding loses ~2^-9.
+__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
+    hi = __float2bfloat16_rn(v);
+    lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+// Element (r, c) of a split copy whose logical row length is K.
+__device__ __forceinline__ void st_split(__nv_bfloat16 *base, size_t r, int K, int c, float v) {
+    __nv_bfloat16 hi, lo;
+    split_bf16(v, hi, lo);
+    base[r * 2 * K + c] = hi;
+    base[r * 2 * K + K + c] = lo;
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(DMTS_FULL, v, o);

@@ -20,7 +20,8 @@ struct Buf {
 struct DevModel {
     int L = 0, C = 0, lmax = 0, K = 0, S = 0, nc = 0, nl = 0, p = 0;
     float rc = 0.f, nu = 0.f, scale = 0.f;
-    bool bf16 = false;
+    bool bf16 = false;                    // MLP contractions on the tensor cores
+    int nseg = 1;                         // 3: split-bf16 products (hi*hi + lo*hi + hi*lo); 1: hi*hi only
     float *dev = nullptr;                 // one allocation holding every tensor (the blob's order)
     size_t n_weights = 0;                 // floats in that allocation
     float *emb = nullptr;
@@ -28,8 +29,9 @@ struct DevModel {
           *w2[DMTS_MAX_LAYERS] = {}, *b2[DMTS_MAX_LAYERS] = {};
     float *wr = nullptr, *br = nullptr, *wo = nullptr;
     float *U = nullptr, *Wqk = nullptr;
-    // bf16 copies for the tensor-core contractions, every one K-major
-    // ([out][in]): W1, W2, Wr (forward), their transposes (adjoint), Wqk.
+    // split-bf16 copies for the tensor-core contractions, every one K-major
+    // ([out][2 in]: hi | lo): W1, W2, Wr (forward), their transposes
+    // (adjoint), Wqk.
     __nv_bfloat16 *dev_bf = nullptr;
     __nv_bfloat16 *w1_bf[DMTS_MAX_LAYERS] = {}, *w2_bf[DMTS_MAX_LAYERS] = {}, *w1t_bf[DMTS_MAX_LAYERS] = {},
                   *w2t_bf[DMTS_MAX_LAYERS] = {};
@@ -51,7 +53,7 @@ struct NbrScratch {
 struct Workspace {
     Buf s, A, q, h, act, u, gz, gs0, gs1, gA, e_atom, ftmp, atom_rep;
     Buf nc_s, nc_q, nc_act, nc_qk, nc_v, nc_f;
-    // bf16 operands of the tensor-core contractions
+    // split-bf16 operands of the tensor-core contractions ([rows][2K])
     Buf q_bf, act_bf, s_bf, gz_bf, gs0_bf, gs1_bf, nc_q_bf, nc_act_bf, nc_s_bf;
     Buf ms_scratch;   // per-part sums of the mean subtraction
     Buf nc_w;         // per-atom virial proxy of the fast force

@@ -9,8 +9,16 @@
 // K = 16 per instruction) into a TMEM accumulator, warp 2 owns the TMEM
 // allocation; warps 0-3 read the accumulator back with tcgen05.ld (warp w
 // reads rows 32w..32w+31) into shared memory and all eight warps apply the
-// epilogue with coalesced accesses. Every wait on an mbarrier is bounded: on
-// timeout the CTA records DMTS_E_TIMEOUT, frees its tensor memory and returns.
+// epilogue with coalesced accesses.
+//
+// Split-bf16 operands (common.cuh: rows of 2K holding hi | lo) are
+// contracted in three segments of K-chunks into the same accumulator,
+// hi*hi + lo*hi + hi*lo, which keeps about 16 significant bits of each
+// operand while every MMA is a plain bf16 x bf16 -> fp32 instruction.
+//
+// Every wait on an mbarrier is bounded: on timeout the CTA records
+// DMTS_E_TIMEOUT, waits (bounded) for the loads and MMAs it has issued,
+// frees its tensor memory and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -93,7 +101,7 @@ __device__ __forceinline__ void epilogue_tile(const Epi &e, int N, int rows, int
     for (int base = threadIdx.x; base < total; base += EU * step) {
         float v[EU];
         size_t o[EU];
-        int n[EU];
+        int n[EU], r_[EU];
         bool ok[EU];
 #pragma unroll
         for (int u = 0; u < EU; ++u) {
@@ -102,6 +110,7 @@ __device__ __forceinline__ void epilogue_tile(const Epi &e, int N, int rows, int
             const int r = ok[u] ? idx / BN : 0, c = ok[u] ? idx - r * BN : 0;
             v[u] = ok[u] ? tile[r * ld + c] : 0.f;
             n[u] = n0 + c;
+            r_[u] = r;
             o[u] = (size_t)(m0 + r) * N + n[u];
         }
         switch (e.mode) {
@@ -110,7 +119,7 @@ __device__ __forceinline__ void epilogue_tile(const Epi &e, int N, int rows, int
             for (int u = 0; u < EU; ++u)
                 if (ok[u]) {
                     e.out[o[u]] = v[u];
-                    if (e.out_bf16) e.out_bf16[o[u]] = __float2bfloat16_rn(v[u]);
+                    if (e.out_bf16) st_split(e.out_bf16, (size_t)(m0 + r_[u]), N, n[u], v[u]);
                 }
             break;
         case EPI_BIAS_SILU: {
@@ -124,7 +133,7 @@ __device__ __forceinline__ void epilogue_tile(const Epi &e, int N, int rows, int
                     const float sv = silu_d(h);
                     if (e.H) e.H[o[u]] = h;
                     e.out[o[u]] = sv;
-                    if (e.out_bf16) e.out_bf16[o[u]] = __float2bfloat16_rn(sv);
+                    if (e.out_bf16) st_split(e.out_bf16, (size_t)(m0 + r_[u]), N, n[u], sv);
                 }
             break;
         }
@@ -140,7 +149,7 @@ __device__ __forceinline__ void epilogue_tile(const Epi &e, int N, int rows, int
                 if (ok[u]) {
                     const float rr = rs[u] + v[u] + b[u];
                     e.out[o[u]] = rr;
-                    if (e.out_bf16) e.out_bf16[o[u]] = __float2bfloat16_rn(rr);
+                    if (e.out_bf16) st_split(e.out_bf16, (size_t)(m0 + r_[u]), N, n[u], rr);
                 }
             break;
         }
@@ -153,7 +162,7 @@ __device__ __forceinline__ void epilogue_tile(const Epi &e, int N, int rows, int
                 if (ok[u]) {
                     const float rr = v[u] * dsilu_d(h[u]);
                     e.out[o[u]] = rr;
-                    if (e.out_bf16) e.out_bf16[o[u]] = __float2bfloat16_rn(rr);
+                    if (e.out_bf16) st_split(e.out_bf16, (size_t)(m0 + r_[u]), N, n[u], rr);
                 }
             break;
         }
@@ -193,7 +202,7 @@ __device__ __forceinline__ void epilogue_tile(const Epi &e, int N, int rows, int
                     e.out[o[u]] = w[u] * silu_d(z);
                     const float gz = e.scale * w[u] * dsilu_d(z);
                     e.out2[o[u]] = gz;
-                    if (e.out_bf16) e.out_bf16[o[u]] = __float2bfloat16_rn(gz);
+                    if (e.out_bf16) st_split(e.out_bf16, (size_t)(m0 + r_[u]), N, n[u], gz);
                 }
             break;
         }
@@ -207,12 +216,21 @@ __device__ __forceinline__ void epilogue_tile(const Epi &e, int N, int rows, int
 // vectors, and the row / column of its next group follow by additions.
 __device__ __forceinline__ float4 ld4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
 __device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
-__device__ __forceinline__ void st4_bf16(__nv_bfloat16 *p, float4 v) {
-    const __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
-    uint2 u;
-    u.x = *reinterpret_cast<const uint32_t *>(&lo);
-    u.y = *reinterpret_cast<const uint32_t *>(&hi);
-    *reinterpret_cast<uint2 *>(p) = u;
+// Four consecutive columns of a split-bf16 copy (common.cuh): the hi parts
+// at p, the lo parts at p + N (N = the logical row length).
+__device__ __forceinline__ void st4_split(__nv_bfloat16 *p, int N, float4 v) {
+    __nv_bfloat16 h[4], l[4];
+    split_bf16(v.x, h[0], l[0]);
+    split_bf16(v.y, h[1], l[1]);
+    split_bf16(v.z, h[2], l[2]);
+    split_bf16(v.w, h[3], l[3]);
+    uint2 uh, ul;
+    uh.x = (uint32_t)__bfloat16_as_ushort(h[0]) | ((uint32_t)__bfloat16_as_ushort(h[1]) << 16);
+    uh.y = (uint32_t)__bfloat16_as_ushort(h[2]) | ((uint32_t)__bfloat16_as_ushort(h[3]) << 16);
+    ul.x = (uint32_t)__bfloat16_as_ushort(l[0]) | ((uint32_t)__bfloat16_as_ushort(l[1]) << 16);
+    ul.y = (uint32_t)__bfloat16_as_ushort(l[2]) | ((uint32_t)__bfloat16_as_ushort(l[3]) << 16);
+    *reinterpret_cast<uint2 *>(p) = uh;
+    *reinterpret_cast<uint2 *>(p + N) = ul;
 }
 __device__ __forceinline__ float4 bias4(const float *b, int n) {
     return make_float4(__ldg(b + n), __ldg(b + n + 1), __ldg(b + n + 2), __ldg(b + n + 3));
@@ -249,7 +267,7 @@ __device__ __forceinline__ void epilogue_tile_v4(const Epi &e, int N, int rows, 
                 if (ok[u]) {
                     const size_t o = (size_t)(m0 + rr[u]) * N + n0 + 4 * cc[u];
                     st4(e.out + o, v[u]);
-                    if (e.out_bf16) st4_bf16(e.out_bf16 + o, v[u]);
+                    if (e.out_bf16) st4_split(e.out_bf16 + (size_t)(m0 + rr[u]) * 2 * N + n0 + 4 * cc[u], N, v[u]);
                 }
             break;
         case EPI_BIAS_SILU:
@@ -263,7 +281,7 @@ __device__ __forceinline__ void epilogue_tile_v4(const Epi &e, int N, int rows, 
                     const float4 sv = silu4(h);
                     if (e.H) st4(e.H + o, h);
                     st4(e.out + o, sv);
-                    if (e.out_bf16) st4_bf16(e.out_bf16 + o, sv);
+                    if (e.out_bf16) st4_split(e.out_bf16 + (size_t)(m0 + rr[u]) * 2 * N + n0 + 4 * cc[u], N, sv);
                 }
             break;
         case EPI_RESID: {
@@ -280,7 +298,7 @@ __device__ __forceinline__ void epilogue_tile_v4(const Epi &e, int N, int rows, 
                     const float4 o4 = make_float4(rs[u].x + v[u].x + b.x, rs[u].y + v[u].y + b.y,
                                                   rs[u].z + v[u].z + b.z, rs[u].w + v[u].w + b.w);
                     st4(e.out + o, o4);
-                    if (e.out_bf16) st4_bf16(e.out_bf16 + o, o4);
+                    if (e.out_bf16) st4_split(e.out_bf16 + (size_t)(m0 + rr[u]) * 2 * N + n0 + 4 * cc[u], N, o4);
                 }
             break;
         }
@@ -296,7 +314,7 @@ __device__ __forceinline__ void epilogue_tile_v4(const Epi &e, int N, int rows, 
                     const float4 o4 = make_float4(v[u].x * dsilu_d(h[u].x), v[u].y * dsilu_d(h[u].y),
                                                   v[u].z * dsilu_d(h[u].z), v[u].w * dsilu_d(h[u].w));
                     st4(e.out + o, o4);
-                    if (e.out_bf16) st4_bf16(e.out_bf16 + o, o4);
+                    if (e.out_bf16) st4_split(e.out_bf16 + (size_t)(m0 + rr[u]) * 2 * N + n0 + 4 * cc[u], N, o4);
                 }
             break;
         }
@@ -337,25 +355,36 @@ __device__ __forceinline__ void epilogue_tile_v4(const Epi &e, int N, int rows, 
                     const float4 gz = make_float4(e.scale * w.x * dsilu_d(z.x), e.scale * w.y * dsilu_d(z.y),
                                                   e.scale * w.z * dsilu_d(z.z), e.scale * w.w * dsilu_d(z.w));
                     st4(e.out2 + o, gz);
-                    if (e.out_bf16) st4_bf16(e.out_bf16 + o, gz);
+                    if (e.out_bf16) st4_split(e.out_bf16 + (size_t)(m0 + rr[u]) * 2 * N + n0 + 4 * cc[u], N, gz);
                 }
             break;
         }
     }
 }
 
+// K-chunk k of a contraction over nseg segments (nk chunks each): segment 0
+// multiplies the hi parts of both operands, segment 1 the activation's lo
+// part with the weight's hi part, segment 2 the activation's hi part with
+// the weight's lo part; kofs is the column where the lo parts start.
+__device__ __forceinline__ void chunk_coords(int k, int nk, int kofs, int &xa, int &xb) {
+    const int seg = k / nk, kc = k - seg * nk;
+    xa = kc * TC_K + (seg == 1 ? kofs : 0);
+    xb = kc * TC_K + (seg == 2 ? kofs : 0);
+}
+
 __global__ void __launch_bounds__(256) k_gemm_tc(const __grid_constant__ CUtensorMap tmA,
                                                  const __grid_constant__ CUtensorMap tmB, int M, int N, int K,
-                                                 int BN, int tmem_cols, int n_stages, int vec, Epi e, int *err) {
+                                                 int BN, int tmem_cols, int n_stages, int vec, int nseg, int kofs,
+                                                 Epi e, int *err) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t bar_full[TC_STAGES], bar_empty[TC_STAGES], bar_done;
     __shared__ uint32_t tmem_base_sh;
-    __shared__ int abort_sh;
+    __shared__ int abort_sh, issued_sh, consumed_sh;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // column tiles in reverse order: the gA epilogue's highest-degree tiles
     // (5 loads and stores per element for l = 2) are scheduled first
     const int m0 = blockIdx.x * TC_M, n0 = (gridDim.y - 1 - blockIdx.y) * BN;
-    const int nk = K / TC_K;
+    const int nk = K / TC_K, nkt = nk * nseg;
     const uint32_t a_bytes = TC_M * TC_K * 2, b_bytes = (uint32_t)BN * TC_K * 2;
     const uint32_t stage_bytes = a_bytes + ((b_bytes + 1023u) & ~1023u);
     const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;   // 1024-byte aligned tiles
@@ -367,6 +396,8 @@ __global__ void __launch_bounds__(256) k_gemm_tc(const __grid_constant__ CUtenso
         }
         mbar_init(smem_u32(&bar_done), 1);
         abort_sh = 0;
+        issued_sh = 0;
+        consumed_sh = 0;
         mbar_init_fence();
     }
     if (warp == 2) {
@@ -381,27 +412,30 @@ __global__ void __launch_bounds__(256) k_gemm_tc(const __grid_constant__ CUtenso
 
     if (warp == 0 && lane == 0) {
         // ---- TMA producer
-        for (int k = 0; k < nk; ++k) {
+        int k = 0;
+        for (; k < nkt; ++k) {
             const int s = k % n_stages;
             if (k >= n_stages && !mbar_wait(smem_u32(&bar_empty[s]), ((k / n_stages) - 1) & 1)) {
                 atomicExch(&abort_sh, 1);
                 break;
             }
+            int xa, xb;
+            chunk_coords(k, nk, kofs, xa, xb);
             const uint32_t sa = base + s * stage_bytes, sb = sa + a_bytes;
             mbar_expect_tx(smem_u32(&bar_full[s]), a_bytes + b_bytes);
-            tma_load_2d(sa, &tmA, k * TC_K, m0, smem_u32(&bar_full[s]));
-            tma_load_2d(sb, &tmB, k * TC_K, n0, smem_u32(&bar_full[s]));
+            tma_load_2d(sa, &tmA, xa, m0, smem_u32(&bar_full[s]));
+            tma_load_2d(sb, &tmB, xb, n0, smem_u32(&bar_full[s]));
         }
+        issued_sh = k;   // loads issued; read after the block-wide barrier below
     } else if (warp == 1 && lane == 0) {
         // ---- MMA issuer
         const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                                ((uint32_t)(TC_M >> 4) << 24);
-        bool ok = true;
-        for (int k = 0; k < nk && ok; ++k) {
+        int k = 0;
+        for (; k < nkt; ++k) {
             const int s = k % n_stages;
             if (!mbar_wait(smem_u32(&bar_full[s]), (k / n_stages) & 1)) {
                 atomicExch(&abort_sh, 1);
-                ok = false;
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -411,6 +445,8 @@ __global__ void __launch_bounds__(256) k_gemm_tc(const __grid_constant__ CUtenso
                 mma_bf16(tmem, smem_desc(sa + kk * 32), smem_desc(sb + kk * 32), idesc, (k > 0 || kk > 0) ? 1u : 0u);
             mma_commit(smem_u32(&bar_empty[s]));
         }
+        consumed_sh = k;   // stages whose loads landed
+        // arrives once every MMA issued above has completed
         mma_commit(smem_u32(&bar_done));
     }
     __syncwarp();
@@ -419,7 +455,16 @@ __global__ void __launch_bounds__(256) k_gemm_tc(const __grid_constant__ CUtenso
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!__syncthreads_and(done ? 1 : 0) || abort_sh) {
-        if (threadIdx.x == 0) atomicCAS(err, 0, (int)DMTS_E_TIMEOUT);
+        if (threadIdx.x == 0) {
+            atomicCAS(err, 0, (int)DMTS_E_TIMEOUT);
+            // Drain before tensor and shared memory are released: every load
+            // issued but not consumed (at most one per stage, the producer
+            // refills a stage only after its MMAs completed) must land, and
+            // the MMAs issued must complete; each wait again bounded.
+            for (int k = consumed_sh; k < issued_sh; ++k)
+                mbar_wait(smem_u32(&bar_full[k % n_stages]), (k / n_stages) & 1);
+            if (!done) mbar_wait(smem_u32(&bar_done), 0);
+        }
     } else {
         // TMEM -> shared memory (the drained pipeline buffers): warps 0-3
         // each move their 32-lane quarter, one row per lane. Then all eight
@@ -485,9 +530,11 @@ bool make_map(CUtensorMap *map, const void *ptr, int rows, int cols, int box_row
 bool gemm_tc_supported(int N, int K) { return K % TC_K == 0 && K > 0 && N % 16 == 0 && N > 0; }
 
 int launch_gemm_tc(int M, int N, int K, const __nv_bfloat16 *Act, const __nv_bfloat16 *Wt, const Epi &e, int *err,
-                   cudaStream_t st) {
+                   cudaStream_t st, int split, int nseg) {
     if (M == 0) return 0;
     if (!gemm_tc_supported(N, K)) return -1;
+    if (!(nseg == 1 || (split && nseg == 3))) return -1;
+    const int width = split ? 2 * K : K;   // physical row length of both operands
     if (((uintptr_t)Act & 15) || ((uintptr_t)Wt & 15)) return -2;
     // column tile: the multiple of 16 dividing N closest to kBNTarget (the
     // smaller on a tie). Narrow tiles give more CTAs per SM (a smaller
@@ -500,9 +547,9 @@ int launch_gemm_tc(int M, int N, int K, const __nv_bfloat16 *Act, const __nv_bfl
     int tmem_cols = 32;
     while (tmem_cols < BN) tmem_cols <<= 1;
     CUtensorMap ma, mb;
-    if (!make_map(&ma, Act, M, K, TC_M) || !make_map(&mb, Wt, N, K, BN)) return -3;
+    if (!make_map(&ma, Act, M, width, TC_M) || !make_map(&mb, Wt, N, width, BN)) return -3;
     const uint32_t stage = TC_M * TC_K * 2 + ((BN * TC_K * 2 + 1023) & ~1023);
-    const int n_stages = std::min(3, K / TC_K);
+    const int n_stages = std::min(3, nseg * K / TC_K);
     const size_t tile = (size_t)TC_M * (BN + 1) * sizeof(float);   // epilogue staging
     const size_t smem = std::max((size_t)stage * n_stages, tile) + 1024;
     // per launch: the attribute belongs to the current device's context
@@ -511,7 +558,7 @@ int launch_gemm_tc(int M, int N, int K, const __nv_bfloat16 *Act, const __nv_bfl
     const int vec = al(e.out, 16) && al(e.out2, 16) && al(e.H, 16) && al(e.res, 16) && al(e.A, 16) &&
                     al(e.out_bf16, 8) && (e.mode != EPI_GA || e.C % 4 == 0);
     dim3 grid((M + TC_M - 1) / TC_M, N / BN);
-    k_gemm_tc<<<grid, 256, smem, st>>>(ma, mb, M, N, K, BN, tmem_cols, n_stages, vec, e, err);
+    k_gemm_tc<<<grid, 256, smem, st>>>(ma, mb, M, N, K, BN, tmem_cols, n_stages, vec, nseg, K, e, err);
     count_launch();
     return 0;
 }

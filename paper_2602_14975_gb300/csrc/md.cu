@@ -681,7 +681,7 @@ void launch_distill_residual(int n, const float *F, const float *T, float *g, fl
 
 // Adam (Kingma & Ba), beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected.
 __global__ void k_adam(int n, float *w, const float *grad, float *m, float *v, float lr, float c1, float c2,
-                       __nv_bfloat16 *w_bf) {
+                       __nv_bfloat16 *w_bf, int kd) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float gr = grad[i];
@@ -690,14 +690,14 @@ __global__ void k_adam(int n, float *w, const float *grad, float *m, float *v, f
     v[i] = vi;
     const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
     w[i] = wi;
-    if (w_bf) w_bf[i] = __float2bfloat16_rn(wi);
+    if (w_bf) st_split(w_bf, (size_t)(i / kd), kd, i % kd, wi);
 }
 
 void launch_adam(int n, float *w, const float *grad, float *m, float *v, float lr, int step, __nv_bfloat16 *w_bf,
-                 cudaStream_t st) {
+                 int kd, cudaStream_t st) {
     if (n == 0) return;
     const float c1 = 1.f - powf(0.9f, (float)step), c2 = 1.f - powf(0.999f, (float)step);
-    k_adam<<<(n + 255) / 256, 256, 0, st>>>(n, w, grad, m, v, lr, c1, c2, w_bf);
+    k_adam<<<(n + 255) / 256, 256, 0, st>>>(n, w, grad, m, v, lr, c1, c2, w_bf, kd);
     count_launch();
 }
 

@@ -81,9 +81,10 @@ void launch_atb(int N, int O, int I, const float *G, const float *X, float *out,
                 cudaStream_t st);
 // g = 2 (F - T), sq = |F - T|^2 per atom.
 void launch_distill_residual(int n, const float *F, const float *T, float *g, float *sq, cudaStream_t st);
-// Adam on n parameters (fp32, moments m, v), then the bf16 copy (nullable).
+// Adam on n parameters (fp32, moments m, v), then the split-bf16 copy
+// (nullable; K-major with logical row length kd).
 void launch_adam(int n, float *w, const float *grad, float *m, float *v, float lr, int step, __nv_bfloat16 *w_bf,
-                 cudaStream_t st);
+                 int kd, cudaStream_t st);
 // v[i] *= f, i < n.
 void launch_scale_d(double *v, int n, double f, cudaStream_t st);
 // est[r] = cons[r] - last[r] + avg[r]

@@ -208,8 +208,7 @@ __global__ void __launch_bounds__(MP_WARPS * 32) k_mp_fwd(EdgeGeom g, LayerIO io
             for (int p = 0; p < NP; ++p)
 #pragma unroll
                 for (int hh = 0; hh < PW; ++hh)
-                    io.q_bf16[(size_t)i * NL * C + l * C + co + lane * CPW + p * PW + hh] =
-                        __float2bfloat16_rn(vget(qv[l][p], hh));
+                    st_split(io.q_bf16, i, NL * C, l * C + co + lane * CPW + p * PW + hh, vget(qv[l][p], hh));
         }
     }
 }
@@ -422,7 +421,7 @@ __global__ void __launch_bounds__(MP_WARPS * 32) k_mp_bwd(EdgeGeom g, LayerIO io
         for (int p = 0; p < NP; ++p)
 #pragma unroll
             for (int hh = 0; hh < PW; ++hh)
-                io.gs_out_bf16[(size_t)a * C + lane * CPW + p * PW + hh] = __float2bfloat16_rn(vget(gout[p], hh));
+                st_split(io.gs_out_bf16, a, C, lane * CPW + p * PW + hh, vget(gout[p], hh));
     }
 }
 
@@ -491,29 +490,30 @@ constexpr int GM = 64, GN = 64, GK = 16;
 
 __device__ __forceinline__ void epilogue(const Epi &e, int N, int m, int n, float v) {
     const size_t o = (size_t)m * N + n;
+    // bf16 copies are split hi/lo rows of width 2N (common.cuh)
     switch (e.mode) {
     case EPI_STORE:
         e.out[o] = v;
-        if (e.out_bf16) e.out_bf16[o] = __float2bfloat16_rn(v);
+        if (e.out_bf16) st_split(e.out_bf16, m, N, n, v);
         break;
     case EPI_BIAS_SILU: {
         const float h = v + e.bias[n];
         if (e.H) e.H[o] = h;
         const float s = silu_f(h);
         e.out[o] = s;
-        if (e.out_bf16) e.out_bf16[o] = __float2bfloat16_rn(s);
+        if (e.out_bf16) st_split(e.out_bf16, m, N, n, s);
         break;
     }
     case EPI_RESID: {
         const float r = e.res[o] + v + e.bias[n];
         e.out[o] = r;
-        if (e.out_bf16) e.out_bf16[o] = __float2bfloat16_rn(r);
+        if (e.out_bf16) st_split(e.out_bf16, m, N, n, r);
         break;
     }
     case EPI_DSILU: {
         const float r = v * dsilu_f(e.H[o]);
         e.out[o] = r;
-        if (e.out_bf16) e.out_bf16[o] = __float2bfloat16_rn(r);
+        if (e.out_bf16) st_split(e.out_bf16, m, N, n, r);
         break;
     }
     case EPI_GA: {
@@ -530,7 +530,7 @@ __device__ __forceinline__ void epilogue(const Epi &e, int N, int m, int n, floa
         e.out[o] = e.wo[n] * silu_f(z);
         const float gz = e.scale * e.wo[n] * dsilu_f(z);
         e.out2[o] = gz;
-        if (e.out_bf16) e.out_bf16[o] = __float2bfloat16_rn(gz);
+        if (e.out_bf16) st_split(e.out_bf16, m, N, n, gz);
         break;
     }
     }

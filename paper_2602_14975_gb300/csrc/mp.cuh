@@ -25,14 +25,14 @@ struct LayerIO {
     float nu;
     float *A;                // [N][NLM][C]  (forward out; nullable: not stored)
     float *q;                // [N][(LMAX+1)C] (forward out, fp32)
-    __nv_bfloat16 *q_bf16;   // optional bf16 copy of q (forward out)
+    __nv_bfloat16 *q_bf16;   // optional split-bf16 copy of q, [N][2(LMAX+1)C] (forward out)
     const float *U;          // optional: tensor-head mix U[n_l][C] (NC embedding)
     float *V;                // optional: V[N][n_l][3] = sum_c U[h][c] A[1+a][c]
     int n_l;
     const float *gA;         // [N][NLM][C]  (backward in)
     const float *gs_in;      // [N][C]       (backward in)
     float *gs_out;           // [N][C]       (backward out; nullable: not computed)
-    __nv_bfloat16 *gs_out_bf16;  // optional bf16 copy of gs_out
+    __nv_bfloat16 *gs_out_bf16;  // optional split-bf16 copy of gs_out, [N][2C]
     float *F;                // [N][3]       (backward: accumulated forces)
     int accumulate;          // backward: 0 write F, 1 add to F (and W)
     float *W;                // [N] (backward, nullable): per-atom virial proxy, pair form
@@ -85,7 +85,7 @@ enum EpiMode {
 struct Epi {
     int mode;
     float *out;
-    __nv_bfloat16 *out_bf16;   // optional bf16 copy of out
+    __nv_bfloat16 *out_bf16;   // optional split-bf16 copy of out, [M][2N] (hi | lo)
     float *out2;
     const float *bias;
     const float *res;          // residual input [M][N]
@@ -101,11 +101,15 @@ struct Epi {
 void launch_gemm_f32(int M, int N, int K, const float *Act, const float *W, int trans, const Epi &e,
                      cudaStream_t st);
 // Out[M][N] = Act[M][K] x Wt^T on the tensor cores (tcgen05, bf16 operands,
-// fp32 accumulator in tensor memory), Wt K-major [N][K]. Needs K % 64 == 0,
-// N % 16 == 0, M >= 128 and 16-byte aligned operands; returns 0 when
-// launched, < 0 when the shape is not supported.
+// fp32 accumulator in tensor memory), Wt K-major [N][K]. With split = 1 both
+// operands are split-bf16 copies (rows of 2K: hi | lo, common.cuh) and
+// nseg = 3 accumulates hi*hi + lo*hi + hi*lo (nseg = 1: hi*hi only); with
+// split = 0 they are plain bf16 [M][K] / [N][K] and nseg must be 1. Needs
+// K % 64 == 0, N % 16 == 0, M >= 1 (rows past M of the last 128-row tile
+// read as zeros and are not stored) and 16-byte aligned operands; returns 0
+// when launched, < 0 when the shape is not supported.
 int launch_gemm_tc(int M, int N, int K, const __nv_bfloat16 *Act, const __nv_bfloat16 *Wt, const Epi &e, int *err,
-                   cudaStream_t st);
+                   cudaStream_t st, int split, int nseg);
 bool gemm_tc_supported(int N, int K);
 
 // Per-replica FP64 sums of per-atom values: out[r] = sum_{i in r} v[i].

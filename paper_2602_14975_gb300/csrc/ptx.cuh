@@ -6,7 +6,17 @@
 
 namespace dmts {
 
+// Every mbarrier wait gives up after kWaitLimitNs of wall time on the GPU's
+// global timer (1 s, far above any legitimate wait of these kernels), with a
+// poll count as a second bound should the timer not advance.
 constexpr uint32_t kSpinLimit = 1u << 26;
+constexpr uint64_t kWaitLimitNs = 1000000000ull;
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -26,8 +36,10 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
-// Bounded wait for the phase with the given parity; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Bounded wait for the phase with the given parity; false once limit_ns
+// have passed (or kSpinLimit polls) without that phase completing.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns = kWaitLimitNs) {
+    uint64_t t0 = 0;
     for (uint32_t it = 0; it < kSpinLimit; ++it) {
         uint32_t ok;
         asm volatile(
@@ -38,6 +50,11 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
             : "r"(bar), "r"(parity)
             : "memory");
         if (ok) return true;
+        if ((it & 15u) == 0) {
+            const uint64_t t = globaltimer_ns();
+            if (it == 0) t0 = t;
+            else if (t - t0 > limit_ns) return false;
+        }
     }
     return false;
 }

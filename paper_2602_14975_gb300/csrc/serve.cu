@@ -154,6 +154,9 @@ long long dmts_replica_footprint(const dmts_ctx *ctx, int n_atoms) {
     const DevModel &m = ctx->cons;
     const int nlm = (m.lmax + 1) * (m.lmax + 1);
     b += (long long)n_atoms * m.C * 4 * (m.L + 1 + m.L * nlm + (m.lmax + 1) + m.L + 6 + nlm);
+    // split-bf16 operand copies (hi and lo: 4 bytes per element) of q and of
+    // the five [N][C] contraction inputs
+    if (m.bf16) b += (long long)n_atoms * m.C * 4 * ((m.lmax + 1) + 5);
     return b;
 }
 

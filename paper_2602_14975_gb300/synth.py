@@ -369,17 +369,18 @@ class ModelSpec:
     n_c: int = 0           # NC: attention dimension
     n_l: int = 0           # NC: tensor heads
     n_species: int = N_SPECIES
-    bf16: bool = False     # MLP contractions in bf16 (fp32 accumulate)
+    bf16: bool = False     # MLP contractions in bf16 on the tensor cores (fp32 accumulate)
+    bf16_plain: bool = False   # with bf16: one bf16 rounding per operand instead of hi + lo pairs
 
 
-def cons_spec(L, C, lmax, K=8, rc=5.0, p=6, scale=1e-2, bf16=False) -> ModelSpec:
+def cons_spec(L, C, lmax, K=8, rc=5.0, p=6, scale=1e-2, bf16=False, bf16_plain=False) -> ModelSpec:
     return ModelSpec(L, C, lmax, K, rc, p, 1.0 / math.sqrt(expected_neighbours(rc)), scale,
-                     bf16=bf16)
+                     bf16=bf16, bf16_plain=bf16_plain)
 
 
-def nc_spec(C, K=8, rc=4.0, p=5, n_c=8, n_l=2, scale=1e-2, bf16=False) -> ModelSpec:
+def nc_spec(C, K=8, rc=4.0, p=5, n_c=8, n_l=2, scale=1e-2, bf16=False, bf16_plain=False) -> ModelSpec:
     return ModelSpec(1, C, 1, K, rc, p, 1.0 / math.sqrt(expected_neighbours(rc)), scale,
-                     n_c=n_c, n_l=n_l, bf16=bf16)
+                     n_c=n_c, n_l=n_l, bf16=bf16, bf16_plain=bf16_plain)
 
 
 def _xavier(rng, fan_out, fan_in, shape=None, gain=1.0):

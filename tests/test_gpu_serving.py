@@ -95,3 +95,23 @@ def test_zero_step_request_returns_its_input(ctx):
     r = _request(30, 20, 0)
     out, _ = core.run_replicas(ctx, [r], _integ())
     assert np.array_equal(out[0]["x"], r.x)
+
+
+def test_alone_and_in_the_mix_at_serving_sizes():
+    """The serving workload's model sizes (conservative L = 3, C = 128,
+    l_max = 2, NC C = 64 at 4 Å, split-bf16 tensor-core contractions):
+    packed batches whose 128-row contraction tiles span replica boundaries
+    give each replica the same bits as a run alone."""
+    cs, ns = S.cons_spec(3, 128, 2, bf16=True), S.nc_spec(64, rc=4.0, bf16=True)
+    cx = core.Context(cons=(cs, S.cons_weights(cs, 402)), nc=(ns, S.nc_weights(ns, 402)))
+    sizes = [(37, 4), (90, 3), (23, 6), (61, 2), (44, 5)]   # 148..360 atoms per replica
+    reqs = [_request(40 + k, n, st) for k, (n, st) in enumerate(sizes)]
+    assert any((sum(r.x.shape[0] for r in reqs[:j]) % 128) != 0 for j in range(1, 3))
+    mix, stats = core.run_replicas(cx, reqs, _integ(), max_slots=3)
+    assert stats["max_resident"] == 3
+    for k, r in enumerate(reqs):
+        alone, _ = core.run_replicas(cx, [r], _integ())
+        assert mix[k]["status"] == 0 and alone[0]["status"] == 0
+        assert np.array_equal(mix[k]["x"], alone[0]["x"])
+        assert np.array_equal(mix[k]["v"], alone[0]["v"])
+        assert mix[k]["energy"] == alone[0]["energy"]
