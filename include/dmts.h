@@ -322,6 +322,16 @@ typedef struct {
     double *baro;              /* device double [n_replicas][3] (may be NULL unless the barostat is on):
                                   p_eps (kcal/mol fs), the piston force G at the last step end, and a
                                   flag (1 once G is set; start from zeros) */
+    double *thermo;            /* device double [n_replicas][3] (may be NULL; needs energy): at the end of each
+                                  call, for the end of its last outer step (velocities after the closing
+                                  kicks): the kinetic energy K = sum_i m_i |v_i|^2 / 2 (kcal/mol), the total
+                                  energy U + K with U as in `energy`, and the kinetic temperature
+                                  2K / (3 n_r kB) (K) of Sec. 3's temperature checks; every per-atom term is
+                                  formed in FP64 from the fp32 state and summed in FP64, in an order that
+                                  does not depend on the other replicas of the batch */
+    double *thermo_trace;      /* device double [thermo_trace_rows][n_replicas][3] (may be NULL; needs thermo):
+                                  row o receives the same three values after outer step o of each call */
+    int thermo_trace_rows;     /* rows of thermo_trace; a call with more outer steps is rejected */
 } dmts_state;
 
 /*
@@ -507,6 +517,16 @@ dmts_status dmts_gaussians(dmts_ctx *ctx, uint64_t seed, uint32_t replica, uint6
  * multiple of 16, M >= 1, else DMTS_E_INVALID. */
 dmts_status dmts_contract_bf16(dmts_ctx *ctx, int M, int N, int K, const void *act_bf16, const void *wt_bf16,
                                float *out, int split, void *stream);
+
+/* (No counterpart in the paper: failure detection.) Exercises the bounded
+ * waits every kernel of this library uses on its mbarriers: launches one
+ * block that waits, with that same wait but a limit of limit_us
+ * microseconds, on an mbarrier of its own shared memory on which nothing
+ * ever arrives and which no copy targets. The wait runs out, the block
+ * records DMTS_E_TIMEOUT in the context's sticky error word and returns; the
+ * next dmts_sync() returns DMTS_E_TIMEOUT (and clears it) and the context
+ * stays usable. limit_us in [1, 1000000], else DMTS_E_INVALID. */
+dmts_status dmts_check_bounded_wait(dmts_ctx *ctx, int limit_us, void *stream);
 
 /* Bytes of device workspace a replica of n_atoms needs in the serving loop
  * (admission accounting). */

@@ -72,7 +72,8 @@ class State(ct.Structure):
                 ("masses", ct.c_void_p), ("energy", ct.c_void_p), ("step", ct.c_void_p),
                 ("seed", ct.c_void_p), ("replica_id", ct.c_void_p), ("first_step", ct.c_int),
                 ("internal", ct.c_void_p), ("virial_nc", ct.c_void_p), ("virial_cons", ct.c_void_p),
-                ("virial_est", ct.c_void_p), ("baro", ct.c_void_p)]
+                ("virial_est", ct.c_void_p), ("baro", ct.c_void_p), ("thermo", ct.c_void_p),
+                ("thermo_trace", ct.c_void_p), ("thermo_trace_rows", ct.c_int)]
 
 
 class Request(ct.Structure):
@@ -103,7 +104,7 @@ EXPORTS = ("dmts_create", "dmts_destroy", "dmts_last_error", "dmts_sync", "nbr_b
            "energy_forces_cons", "forces_nc", "respa_step", "dmts_state_release", "dmts_state_lists", "nc_distill_step", "run_replicas",
            "dmts_masses_hmr", "dmts_bond_table", "dmts_philox_words", "dmts_gaussians",
            "dmts_replica_footprint", "dmts_profile_enable", "dmts_profile_read", "nbr_build_noalloc",
-           "dmts_contract_bf16", "dmts_kernel_launches", "respa_guarded")
+           "dmts_contract_bf16", "dmts_kernel_launches", "respa_guarded", "dmts_check_bounded_wait")
 
 
 def lib_path() -> str:
@@ -155,6 +156,8 @@ def _declare(L):
     L.dmts_replica_footprint.argtypes = [vp, i]
     L.dmts_contract_bf16.restype = i
     L.dmts_contract_bf16.argtypes = [vp, i, i, i, vp, vp, vp, i, vp]
+    L.dmts_check_bounded_wait.restype = i
+    L.dmts_check_bounded_wait.argtypes = [vp, i, vp]
     L.nbr_build_noalloc.restype = i
     L.nbr_build_noalloc.argtypes = [ct.POINTER(System), ct.POINTER(Nbr), ct.POINTER(ct.c_longlong), vp]
     L.dmts_profile_enable.restype = i

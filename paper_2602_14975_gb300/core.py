@@ -244,7 +244,7 @@ class MDState:
     """Device-resident dynamic state of a batch (positions live in dsys.x)."""
 
     def __init__(self, dsys: DeviceSystem, v, masses, seeds, replica_ids=None, steps=None, virial=False,
-                 barostat=False):
+                 barostat=False, thermo=False, trace_rows=0):
         dev = dsys.x.device
         self.dsys = dsys
         self.v = torch.as_tensor(np.asarray(v, np.float32)).to(dev).contiguous()
@@ -268,9 +268,16 @@ class MDState:
         self.virial_est = torch.zeros(R, dtype=torch.float64, device=dev) if virial else None
         # with barostat=True: per replica the piston momentum, its last force and a set flag
         self.baro = torch.zeros(R, 3, dtype=torch.float64, device=dev) if barostat else None
+        # with thermo=True: per replica (K, U + K, T) at the end of each call,
+        # FP64 on the device; with trace_rows > 0 also after every outer step
+        # of a call (rows = outer steps, at most trace_rows per call)
+        self.thermo = torch.zeros(R, 3, dtype=torch.float64, device=dev) if (thermo or trace_rows) else None
+        self.thermo_trace = (torch.zeros(trace_rows, R, 3, dtype=torch.float64, device=dev)
+                             if trace_rows else None)
         self.c = L.State(dsys.struct(), _ptr(self.v), _ptr(self.f_nc), _ptr(self.f_cons), _ptr(self.masses),
                          _ptr(self.energy), _ptr(self.step), _ptr(self.seed), _ptr(self.replica_id), 1, None,
-                         _ptr(self.virial_nc), _ptr(self.virial_cons), _ptr(self.virial_est), _ptr(self.baro))
+                         _ptr(self.virial_nc), _ptr(self.virial_cons), _ptr(self.virial_est), _ptr(self.baro),
+                         _ptr(self.thermo), _ptr(self.thermo_trace), int(trace_rows))
         self.ctx = None
 
     def lists(self, which: int) -> NbrList:
@@ -452,3 +459,11 @@ def contract_bf16(ctx: Context, act: torch.Tensor, wt: torch.Tensor, split: bool
     L.check(ctx.lib.dmts_contract_bf16(ctx.handle, M, N, K, _ptr(act), _ptr(wt), _ptr(out), int(split),
                                        _stream(act.device)), ctx.handle)
     return out
+
+
+def check_bounded_wait(ctx: Context, limit_us: int) -> int:
+    """Runs the library's bounded mbarrier wait on a barrier nothing arrives
+    on (limit_us microseconds) and returns the status dmts_sync then reports
+    (DMTS_E_TIMEOUT expected); the sticky error word is cleared."""
+    L.check(ctx.lib.dmts_check_bounded_wait(ctx.handle, int(limit_us), _stream()), ctx.handle)
+    return int(ctx.lib.dmts_sync(ctx.handle, _stream()))

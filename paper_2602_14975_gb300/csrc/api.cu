@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "engine.cuh"
+#include "ptx.cuh"
 
 using namespace dmts;
 
@@ -1095,6 +1096,10 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
     const bool npt = !sts && p->barostat;
     if (npt && (!stt->baro || !stt->virial_est || !(p->tau_p_ps > 0.f)))
         return fail(ctx, DMTS_E_INVALID, "the barostat needs st->baro, the virial arrays and tau_p_ps > 0");
+    if ((stt->thermo || stt->thermo_trace) && !stt->energy)
+        return fail(ctx, DMTS_E_INVALID, "thermo needs the energy array");
+    if (stt->thermo_trace && (!stt->thermo || n_outer > stt->thermo_trace_rows))
+        return fail(ctx, DMTS_E_INVALID, "thermo_trace needs thermo and at least n_outer rows");
     cudaSetDevice(ctx->device);
     if (stt->virial_est && !sts && !ctx->ws.nc_w_last.ensure(sizeof(double) * stt->sys.n_replicas))
         return fail(ctx, DMTS_E_OOM, "workspace allocation failed");
@@ -1171,6 +1176,26 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
     ia.h_in = (float)(0.5 * delta);
     ia.h_out = 0.5f * p->dt_outer;
     if (n_outer == 0) return DMTS_OK;
+    // FP64 K, U + K and T per replica (pending closing kicks selected per call site)
+    ThermoArgs ta;
+    memset(&ta, 0, sizeof ta);
+    ta.rep_off = v.rep_off;
+    ta.v = stt->v;
+    ta.f_fast = ia.f_fast;
+    ta.f_slow = stt->f_cons;
+    ta.masses = stt->masses;
+    ta.h_in = ia.h_in;
+    ta.h_out = ia.h_out;
+    ta.energy = stt->energy;
+    ta.out = stt->thermo;
+    auto thermo = [&](bool pending, double *trace_row) {
+        ThermoArgs t = ta;
+        t.close_b = pending;
+        t.kick_l = pending && !sts;
+        t.trace = trace_row;
+        ProfScope ps(ctx, "thermo", st);
+        launch_thermo(t, v.n_rep, st);
+    };
     BaroArgs ba;
     memset(&ba, 0, sizeof ba);
     if (npt) {
@@ -1257,11 +1282,15 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
             ba.wvir = stt->virial_est;
             { ProfScope ps(ctx, "barostat", st); launch_baro_end(ba, st); }
         }
+        // the end of outer step o: under the barostat the step closed itself
+        // above; otherwise its closing kicks are still pending
+        if (stt->thermo_trace) thermo(!npt, stt->thermo_trace + (size_t)o * v.n_rep * 3);
     }
     if (!npt) {
         ia.ops = sts ? OP_CLOSE_B : (OP_CLOSE_B | OP_KICK_L);
         { ProfScope ps(ctx, "integrate", st); launch_integrate(ia, st); }
     }
+    if (stt->thermo && !stt->thermo_trace) thermo(false, nullptr);
     launch_advance_step(stt->step, v.n_rep, (uint64_t)n_outer * n_in, ctx->d_err, st);
     return ck(ctx, cudaGetLastError(), "respa_step launch") ? DMTS_OK : DMTS_E_CUDA;
 }
@@ -1323,6 +1352,26 @@ dmts_status dmts_contract_bf16(dmts_ctx *ctx, int M, int N, int K, const void *a
                                  (cudaStream_t)stream, split, split ? 3 : 1);
     if (r != 0) return fail(ctx, DMTS_E_INVALID, "dmts_contract_bf16: unaligned operand or tensor map failure");
     return ck(ctx, cudaGetLastError(), "dmts_contract_bf16 launch") ? DMTS_OK : DMTS_E_CUDA;
+}
+
+// A wait that runs out: nothing arrives on this block's mbarrier.
+__global__ void k_bounded_wait(uint64_t limit_ns, int *err) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&bar), 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait(smem_u32(&bar), 0, limit_ns)) set_error(err, DMTS_E_TIMEOUT);
+}
+
+dmts_status dmts_check_bounded_wait(dmts_ctx *ctx, int limit_us, void *stream) {
+    if (!ctx || limit_us < 1 || limit_us > 1000000)
+        return fail(ctx, DMTS_E_INVALID, "dmts_check_bounded_wait: limit_us must be in [1, 1000000]");
+    cudaSetDevice(ctx->device);
+    k_bounded_wait<<<1, 32, 0, (cudaStream_t)stream>>>((uint64_t)limit_us * 1000ull, ctx->d_err);
+    count_launch();
+    return ck(ctx, cudaGetLastError(), "dmts_check_bounded_wait launch") ? DMTS_OK : DMTS_E_CUDA;
 }
 
 __global__ void k_philox_words(uint64_t seed, uint32_t rep, uint64_t step, uint32_t atom0, int count, uint32_t *out) {

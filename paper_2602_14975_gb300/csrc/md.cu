@@ -953,6 +953,16 @@ void launch_prior(const PriorArgs &a, cudaStream_t st) {
 }
 
 // ----------------------------------------------------------- integrator
+// The closing kicks of a step, shared by the integrator and the FP64
+// kinetic-energy reduction so that both form the same closed velocity:
+// v += h_in a F_fast (B), then v += h_out a (F_slow - F_fast) (outer kick).
+__device__ __forceinline__ void closing_b(float h, float sfx, float sfy, float sfz, float &vx, float &vy, float &vz) {
+    vx = fmaf(h, sfx, vx); vy = fmaf(h, sfy, vy); vz = fmaf(h, sfz, vz);
+}
+__device__ __forceinline__ void outer_kick(float h, float lx, float ly, float lz, float &vx, float &vy, float &vz) {
+    vx = fmaf(h, lx, vx); vy = fmaf(h, ly, vy); vz = fmaf(h, lz, vz);
+}
+
 // One thread per atom; the operations selected by `ops` run in this order:
 // closing B, closing outer kick, opening outer kick, then B-A-O-A.
 __global__ void k_integrate(IntegArgs g) {
@@ -962,14 +972,11 @@ __global__ void k_integrate(IntegArgs g) {
     const float am = kAccConv / g.masses[i];
     float vx = g.v[3 * i], vy = g.v[3 * i + 1], vz = g.v[3 * i + 2];
     const float sfx = g.f_fast[3 * i], sfy = g.f_fast[3 * i + 1], sfz = g.f_fast[3 * i + 2];
-    if (g.ops & OP_CLOSE_B) {
-        const float h = g.h_in * am;
-        vx = fmaf(h, sfx, vx); vy = fmaf(h, sfy, vy); vz = fmaf(h, sfz, vz);
-    }
+    if (g.ops & OP_CLOSE_B) closing_b(g.h_in * am, sfx, sfy, sfz, vx, vy, vz);
     if (g.ops & (OP_KICK_L | OP_KICK_L2)) {
         const float h = g.h_out * am;
         const float lx = g.f_slow[3 * i] - sfx, ly = g.f_slow[3 * i + 1] - sfy, lz = g.f_slow[3 * i + 2] - sfz;
-        if (g.ops & OP_KICK_L) { vx = fmaf(h, lx, vx); vy = fmaf(h, ly, vy); vz = fmaf(h, lz, vz); }
+        if (g.ops & OP_KICK_L) outer_kick(h, lx, ly, lz, vx, vy, vz);
         if (g.ops & OP_KICK_L2) { vx = fmaf(h, lx, vx); vy = fmaf(h, ly, vy); vz = fmaf(h, lz, vz); }
         if (g.fl_max) {
             // disagreement monitor of the rewind procedure: max |F_L| per replica
@@ -1032,6 +1039,60 @@ __global__ void k_integrate(IntegArgs g) {
 void launch_integrate(const IntegArgs &a, cudaStream_t st) {
     if (a.n_atoms == 0) return;
     k_integrate<<<(a.n_atoms + 255) / 256, 256, 0, st>>>(a);
+    count_launch();
+}
+
+// ------------------------------------------------------- thermodynamics
+// One block per replica: K = sum_i m_i |v_i|^2 / 2 with every per-atom term
+// formed in FP64 from the fp32 state and summed in FP64 in a fixed order
+// (a strided partial per thread, then a fixed tree), so the result does not
+// depend on the batch the replica is in. The velocities are first closed
+// with the step's pending kicks (ThermoArgs), in the integrator's own
+// arithmetic. Writes (K, U + K, 2K / (3 n_r kB)) per replica.
+constexpr int kThermoThreads = 512;
+
+__global__ void __launch_bounds__(kThermoThreads) k_thermo(ThermoArgs g) {
+    __shared__ double red[kThermoThreads / 32];
+    const int r = blockIdx.x;
+    const int beg = g.rep_off[r], end = g.rep_off[r + 1];
+    double acc = 0.0;
+    for (int i = beg + threadIdx.x; i < end; i += kThermoThreads) {
+        const float am = kAccConv / g.masses[i];
+        float vx = g.v[3 * i], vy = g.v[3 * i + 1], vz = g.v[3 * i + 2];
+        if (g.close_b || g.kick_l) {
+            const float sfx = g.f_fast[3 * i], sfy = g.f_fast[3 * i + 1], sfz = g.f_fast[3 * i + 2];
+            if (g.close_b) closing_b(g.h_in * am, sfx, sfy, sfz, vx, vy, vz);
+            if (g.kick_l)
+                outer_kick(g.h_out * am, g.f_slow[3 * i] - sfx, g.f_slow[3 * i + 1] - sfy, g.f_slow[3 * i + 2] - sfz,
+                           vx, vy, vz);
+        }
+        const double dx = vx, dy = vy, dz = vz;
+        acc += 0.5 * (double)g.masses[i] * (dx * dx + dy * dy + dz * dz);
+    }
+    acc = warp_sum_d(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double t = threadIdx.x < kThermoThreads / 32 ? red[threadIdx.x] : 0.0;
+        t = warp_sum_d(t);
+        if (threadIdx.x == 0) {
+            const double K = t / kAccConvD;   // amu A^2/fs^2 -> kcal/mol
+            const int n = end - beg;
+            const double T = n > 0 ? 2.0 * K / (3.0 * n * kBoltzmann) : 0.0;
+            const double U = g.energy[r];
+            double *o = g.out + 3 * (size_t)r;
+            o[0] = K; o[1] = U + K; o[2] = T;
+            if (g.trace) {
+                double *q = g.trace + 3 * (size_t)r;
+                q[0] = K; q[1] = U + K; q[2] = T;
+            }
+        }
+    }
+}
+
+void launch_thermo(const ThermoArgs &a, int n_rep, cudaStream_t st) {
+    if (n_rep == 0) return;
+    k_thermo<<<n_rep, kThermoThreads, 0, st>>>(a);
     count_launch();
 }
 

@@ -153,6 +153,19 @@ struct IntegArgs {
 };
 void launch_integrate(const IntegArgs &a, cudaStream_t st);
 
+// Per-replica FP64 kinetic energy, total energy and kinetic temperature of a
+// state whose velocities still lack the closing kicks selected here.
+struct ThermoArgs {
+    const int *rep_off;
+    const float *v, *f_fast, *f_slow, *masses;
+    float h_in, h_out;
+    int close_b, kick_l;           // apply v += h_in a F_fast, then v += h_out a (F_slow - F_fast)
+    const double *energy;          // [R] potential energy U at the same configuration
+    double *out;                   // [R][3]: K, U + K, T
+    double *trace;                 // nullable: [R][3] copy (one row of a per-outer-step trace)
+};
+void launch_thermo(const ThermoArgs &a, int n_rep, cudaStream_t st);
+
 // Barostat of the outer step (piston on epsilon = ln(V)/3; see dmts_integrator).
 struct BaroArgs {
     int n_rep;
