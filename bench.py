@@ -5,12 +5,16 @@ its adjoint forces, n = 5 NC evaluations, the fused integrator, neighbour
 rebuilds) on the 23,558-atom solvated bead chain in water. The same GPU also
 runs single-time-step BAOAB (1 fs, no HMR) for the ns/day ratio.
 
-Prints one JSON line (rank 0). `--impl reference` times the FP64 CPU oracle
-instead, on a bounded cut-out of the same workload.
+Prints one JSON line (rank 0), the headline first; `--detail PATH` also
+writes every leg's figures (per-kernel shares and rooflines, the other
+configurations, serving latencies, rewind guard, FFL, NPT, distillation) to
+a JSON file. `--impl reference` times the FP64 CPU oracle instead, on
+periodic samples of the same workload.
 """
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -103,6 +107,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--detail", default="", help="also write every leg's figures to this JSON file")
     return ap.parse_args()
 
 
@@ -160,41 +165,76 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------- CPU oracle --
+def host_cpu():
+    """(logical CPUs, CPU model) of the host the oracle runs on."""
+    n = os.cpu_count() or 1
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            k, _, v = line.partition(":")
+            if k.strip() == "Model name" and v.strip():
+                model = v.strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                k, _, v = line.partition(":")
+                if k.strip() == "model name":
+                    model = v.strip()
+                    break
+        except OSError:
+            pass
+    import platform
+    return n, model or platform.machine()
+
+
 def cutout(sy, frac_edge):
-    """Atoms of whole molecules whose first atom lies in [0, frac_edge*L)^3
-    (wrapped); bonds re-indexed; same box."""
+    """A periodic sample of the system at its own density: the molecules
+    whose first atom lies in [0, f L)^3 (wrapped), each kept whole next to
+    that atom, in a periodic box of edge f L, so that every atom has about
+    as many neighbours as in the full system (an open cut-out would lose
+    those beyond its faces and look cheaper per atom). Chain beads inside
+    the region are kept with the bonds between them."""
     from paper_2602_14975_gb300 import synth as S
     xw = np.mod(sy.x, sy.box)
     lim = frac_edge * sy.box
-    keep_mol = set()
-    seen = set()
+    first = {}
+    for i in range(sy.n_atoms):
+        first.setdefault(int(sy.mol_id[i]), i)
+    keep = np.zeros(sy.n_atoms, bool)
+    xk = np.array(sy.x, np.float64)
+    chain = set(int(m) for m, c in zip(*np.unique(sy.mol_id, return_counts=True)) if c > 3)
     for i in range(sy.n_atoms):
         m = int(sy.mol_id[i])
-        if m in seen:
-            continue
-        seen.add(m)
-        if np.all(xw[i] < lim):
-            keep_mol.add(m)
-    keep = np.array([int(sy.mol_id[i]) in keep_mol for i in range(sy.n_atoms)])
-    if sy.mol_id[0] == 0 and 0 not in keep_mol:
-        # the chain is one molecule: keep its beads inside the cut-out region
-        keep |= (sy.mol_id == 0) & np.all(xw < lim, axis=1)
+        if m in chain:
+            keep[i] = bool(np.all(xw[i] < lim))
+            xk[i] = xw[i]
+        else:
+            f = first[m]
+            if np.all(xw[f] < lim):
+                keep[i] = True
+                d = sy.x[i] - sy.x[f]
+                xk[i] = xw[f] + d - sy.box * np.rint(d / sy.box)
     idx = np.nonzero(keep)[0]
     remap = -np.ones(sy.n_atoms, np.int64)
     remap[idx] = np.arange(idx.size)
     b = sy.bonds
     bm = keep[b[:, 0]] & keep[b[:, 1]]
-    return S.System(sy.name + "_cutout", sy.x[idx], sy.species[idx], sy.mol_id[idx],
-                    remap[b[bm]].astype(np.int32), sy.bond_r0[bm], sy.box)
+    return S.System(sy.name + "_cutout", xk[idx], sy.species[idx], sy.mol_id[idx],
+                    remap[b[bm]].astype(np.int32), sy.bond_r0[bm], np.array(sy.box) * frac_edge)
 
 
 def oracle_outer_step_seconds(sy, W, frac_edge):
     """Times the oracle's force evaluations of one DMTS-NC outer step (one
-    conservative energy+forces, n NC evaluations) on a cut-out; returns
-    (seconds per outer step scaled to the full system, sample description)."""
+    conservative energy + forces with the prior, n NC evaluations) on a
+    periodic sample; returns (seconds per outer step scaled to the full
+    system, seconds the sample took, sample description)."""
     import oracle as O
     from paper_2602_14975_gb300 import synth as S
-    sub = cutout(sy, frac_edge)
+    sub = cutout(sy, frac_edge) if frac_edge < 1.0 else sy
     cs, ns = W["cons"](), W["nc"]()
     cb, nb = S.cons_weights(cs, W["w_seed"]), S.nc_weights(ns, W["w_seed"])
     n_in = W["dmts"].n_inner
@@ -206,10 +246,11 @@ def oracle_outer_step_seconds(sy, W, frac_edge):
     t2 = time.perf_counter()
     per_outer = (t1 - t0) + n_in * (t2 - t1)
     scale = sy.n_atoms / sub.n_atoms
-    desc = (f"oracle (FP64 C, 1 thread): 1 conservative E+F + 1 NC evaluation timed on a "
-            f"{sub.n_atoms}-atom cut-out ({frac_edge:.3f} of the box edge) of {sy.name}; "
-            f"outer step = t_cons + {n_in} t_nc, scaled x{scale:.2f} to {sy.n_atoms} atoms")
-    return per_outer * scale, desc
+    what = (f"a periodic {sub.n_atoms}-atom sample ({frac_edge:.3f} of the box edge, same density) of {sy.name}, "
+            f"scaled x{scale:.2f}") if sub is not sy else f"the whole {sy.name}"
+    desc = (f"oracle (FP64 C, as it stands, 1 thread): 1 conservative E+F + 1 NC evaluation timed on {what}; "
+            f"outer step = t_cons + {n_in} t_nc")
+    return per_outer * scale, t2 - t0, desc
 
 
 def workload_config(sy, I, cs, ns):
@@ -264,7 +305,74 @@ def serving_roofline(prof, atom_outer_steps, n_inner, cs):
     return out
 
 
+def serving_tail(tick_ms, tick_atoms):
+    """What sets the per-tick latency percentiles: a least-squares fit
+    ms = a + b * atoms over all ticks, and the batch sizes of the p50 and p99
+    ticks (a tick's cost follows the atoms resident in it)."""
+    t = np.asarray(tick_ms, np.float64)
+    n = np.asarray(tick_atoms, np.float64)
+    if t.size < 2 or np.ptp(n) == 0:
+        return None
+    b, a = np.polyfit(n, t, 1)
+    resid = t - (a + b * n)
+    p50, p99 = np.percentile(t, 50), np.percentile(t, 99)
+    near = lambda p: float(np.median(n[np.abs(t - p) <= 0.05 * p])) if np.any(np.abs(t - p) <= 0.05 * p) else None  # noqa: E731
+    return {"fit_ms": {"intercept": float(a), "per_1000_atoms": float(b * 1e3)},
+            "fit_residual_ms_p99_abs": float(np.percentile(np.abs(resid), 99)),
+            "atoms_at_p50_tick": near(p50), "atoms_at_p99_tick": near(p99),
+            "atoms_p50": float(np.percentile(n, 50)), "atoms_max": float(n.max())}
+
+
 # ------------------------------------------------------------------ main --
+def reference_arm(args, W, I):
+    """The FP64 oracle, as it stands, on the host cores: every step times one
+    outer step's force evaluations on a periodic sample of the workload sized
+    so that warm-up and timed steps take about two minutes together."""
+    sy = W["system"]()
+    t_full, t_cal, _ = oracle_outer_step_seconds(sy, W, 0.25)
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    frac = min(0.6, 0.25 * (budget / max(t_cal, 1e-3)) ** (1.0 / 3.0))
+    frac = max(frac, 0.2)
+    for _ in range(args.warmup):
+        oracle_outer_step_seconds(sy, W, frac)
+    t0 = time.perf_counter()
+    per, wall_each = [], []
+    for _ in range(args.steps):
+        s_full, s_sample, desc = oracle_outer_step_seconds(sy, W, frac)
+        per.append(s_full)
+        wall_each.append(s_sample)
+    wall = time.perf_counter() - t0
+    t_outer = float(np.mean(per))
+    val = ns_per_day(I.dt_outer, 1.0 / t_outer)
+    ncpu, model = host_cpu()
+    return {"impl": "reference", "metric": "ns/day (DMTS-NC)", "value": val, "unit": "ns/day",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": float(np.mean(wall_each)) * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(sy, I, W["cons"](), W["nc"]()),
+            "cpu_baseline": {"value": val, "unit": "ns/day", "cores": 1, "kind": "oracle", "sample": desc,
+                             "host_cpus": ncpu, "cpu_model": model,
+                             "full_system_s_per_outer_step": t_outer},
+            "e2e": {"value": val, "unit": "ns/day", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": wall}
+
+
+def fp32_peak_tflops(props, peaks):
+    """FP32 FMA peak: SMs (from the device) x 128 FP32 lanes per SM x 2 FLOP
+    x the maximum SM clock (the measured-peaks file, else nvidia-smi)."""
+    mhz = peaks.get("sm_max_mhz")
+    src = "measured-peaks file"
+    if not mhz:
+        try:
+            out = subprocess.run(["nvidia-smi", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits"],
+                                 capture_output=True, text=True, timeout=20).stdout.split()
+            mhz, src = float(out[0]), "nvidia-smi"
+        except (OSError, subprocess.SubprocessError, ValueError, IndexError):
+            mhz, src = 2070.0, "nominal"
+    sms = props.multi_processor_count
+    return sms * 128 * 2 * mhz * 1e6 / 1e12, f"{sms} SMs x 128 FP32 lanes x 2 FLOP x {mhz:.0f} MHz ({src} clock)"
+
+
 def main():
     args = parse()
     from paper_2602_14975_gb300 import dist as D
@@ -276,33 +384,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return 0
-        sy = W["system"]()
-        # size the per-step cut-out so that warm-up + timed steps take about
-        # two minutes (cost grows linearly with the cut-out's atom count)
-        t_cal, _ = oracle_outer_step_seconds(sy, W, 0.25)
-        n_cal = cutout(sy, 0.25).n_atoms
-        t_cal_sample = t_cal * n_cal / sy.n_atoms
-        budget = 120.0 / max(1, args.steps + args.warmup)
-        frac = min(1.0 / 3.0, 0.25 * (budget / max(t_cal_sample, 1e-3)) ** (1.0 / 3.0))
-        for _ in range(args.warmup):
-            oracle_outer_step_seconds(sy, W, frac)
-        t0 = time.perf_counter()
-        per = []
-        for _ in range(args.steps):
-            s, desc = oracle_outer_step_seconds(sy, W, frac)
-            per.append(s)
-        wall = time.perf_counter() - t0
-        t_outer = float(np.mean(per))
-        val = ns_per_day(I.dt_outer, 1.0 / t_outer)
-        line = {"impl": "reference", "metric": "ns/day (DMTS-NC)", "value": val, "unit": "ns/day",
-                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": t_outer * 1e3, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": workload_config(sy, I, W["cons"](), W["nc"]()),
-                "cpu_baseline": {"value": val, "unit": "ns/day", "cores": 1, "kind": "oracle", "sample": desc},
-                "e2e": {"value": val, "unit": "ns/day", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-                "wall_s": wall}
-        print(json.dumps(line), flush=True)
+        print(json.dumps(reference_arm(args, W, I)), flush=True)
         return 0
 
     import torch
@@ -310,18 +392,50 @@ def main():
     D.init("nccl", torch.device(f"cuda:{local}"))
     from paper_2602_14975_gb300 import core
 
-    sy = W["system"]()
-    cs, ns = W["cons"](), W["nc"]()    # bf16 MLP contractions on the tensor cores
-    cb, nb = S.cons_weights(cs, W["w_seed"]), S.nc_weights(ns, W["w_seed"])
-    ctx = core.Context(cons=(cs, cb), nc=(ns, nb), device=local)
-
     dev = torch.device(f"cuda:{local}")
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    skin = 0.5    # Verlet skin (A); rebuilds are gated on half-skin displacement
 
     def barrier():
         D.barrier(dev)
 
     def max_over_ranks(v):
         return D.max_over_ranks(v, dev)
+
+    def timed(ctx_, st_, integ_, n):
+        """ms per step of n steps through respa_step (max over ranks)."""
+        barrier()
+        e0.record(stream)
+        core.respa_step(ctx_, st_, integ_, n)
+        e1.record(stream)
+        barrier()
+        ctx_.sync()
+        return max_over_ranks(e0.elapsed_time(e1)) / n
+
+    def integ_of(spec, **kw):
+        return core.integrator(spec.dt_outer, spec.n_inner, spec.temperature, spec.gamma_ps, skin=skin, **kw)
+
+    def run_leg(ctx_, sy_, spec, v_seed, n, warm=3, sts=False):
+        """ms per step of `n` steps of one system (HMR masses per `spec`)."""
+        m_ = (core.masses_hmr(sy_.species, sy_.mol_id, sy_.element_masses(), spec.hmr_delta)
+              if spec.hmr_delta else sy_.element_masses())
+        d_ = core.DeviceSystem(sy_)
+        st_ = core.MDState(d_, S.maxwell_boltzmann(m_, spec.temperature, v_seed), m_.astype(np.float32),
+                           seeds=spec.seed, replica_ids=[D.replica_id(rank, 0)])
+        ig = integ_of(spec, mode=core.L.MODE_STS if sts else core.L.MODE_RESPA)
+        core.respa_step(ctx_, st_, ig, warm)
+        ctx_.sync()
+        ms = timed(ctx_, st_, ig, n)
+        st_.release()
+        return ms
+
+    sy = W["system"]()
+    cs, ns = W["cons"](), W["nc"]()    # split-bf16 MLP contractions on the tensor cores
+    cb, nb = S.cons_weights(cs, W["w_seed"]), S.nc_weights(ns, W["w_seed"])
+    ctx = core.Context(cons=(cs, cb), nc=(ns, nb), device=local)
+    cs32 = dataclasses.replace(cs, bf16=False)
+    ctx32 = core.Context(cons=(cs32, cb), device=local)     # plain FP32 single-time-step baseline
 
     # algorithmic work of the dominant kernels (active edges within the cutoffs)
     d0 = core.DeviceSystem(sy)
@@ -333,14 +447,12 @@ def main():
     m_hmr = core.masses_hmr(sy.species, sy.mol_id, sy.element_masses(), I.hmr_delta)
     v0 = S.maxwell_boltzmann(m_hmr, I.temperature, W["rng_seed"])
     dsys = core.DeviceSystem(sy)
-    st = core.MDState(dsys, v0, m_hmr.astype(np.float32), seeds=I.seed, replica_ids=[D.replica_id(rank, 0)])
-    skin = 0.5    # Verlet skin (A); rebuilds are gated on half-skin displacement
-    integ = core.integrator(I.dt_outer, I.n_inner, I.temperature, I.gamma_ps, skin=skin)
+    st = core.MDState(dsys, v0, m_hmr.astype(np.float32), seeds=I.seed, replica_ids=[D.replica_id(rank, 0)],
+                      thermo=True)
+    integ = integ_of(I)
     core.respa_step(ctx, st, integ, args.warmup)
     ctx.sync()
     clocks = ClockSampler(local)
-    stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     # per-kernel events on every PROF_EVERY-th outer step of the timed
     # region (events on every step cost about 4 % of the step time)
     core.profile_enable(ctx, True, every=PROF_EVERY)
@@ -360,6 +472,7 @@ def main():
     prof = core.profile_read(ctx)
     core.profile_enable(ctx, False)
     ms_dmts = max_over_ranks(e0.elapsed_time(e1)) / args.steps
+    thermo_end = st.thermo.cpu().numpy()[0].tolist()
     st.release()
 
     # ------------------------------------- rewind guard, FFL thermostat
@@ -371,8 +484,7 @@ def main():
     for label, th in (("guarded", 0), ("ffl", 1)):
         dg = core.DeviceSystem(W["system"]())
         sg = core.MDState(dg, v0, m_hmr.astype(np.float32), seeds=I.seed, replica_ids=[D.replica_id(rank, 0)])
-        ig = core.integrator(I.dt_outer, I.n_inner, I.temperature, I.gamma_ps, skin=skin,
-                             thermostat=core.L.FFL if th else core.L.LANGEVIN)
+        ig = integ_of(I, thermostat=core.L.FFL if th else core.L.LANGEVIN)
         core.respa_step(ctx, sg, ig, 2)
         ctx.sync()
         barrier()
@@ -400,22 +512,14 @@ def main():
     dn = core.DeviceSystem(W["system"]())
     sn = core.MDState(dn, v0, m_hmr.astype(np.float32), seeds=I.seed, replica_ids=[D.replica_id(rank, 0)],
                       virial=True, barostat=True)
-    i_init = core.integrator(I.dt_outer, I.n_inner, I.temperature, I.gamma_ps, skin=skin, barostat=True)
-    core.respa_step(ctx, sn, i_init, 0)      # lists (with the piston's cell margin) and first forces
+    core.respa_step(ctx, sn, integ_of(I, barostat=True), 0)   # lists (with the piston's cell margin), forces
     ctx.sync()
     k_start = 0.5 * float((m_hmr[:, None] * v0 ** 2).sum()) / 4.184e-4
     p_start = (2 * k_start - float(sn.virial_cons[0].item())) / (3 * float(np.prod(sy.box))) / KCAL_A3_PER_ATM
-    i_npt = core.integrator(I.dt_outer, I.n_inner, I.temperature, I.gamma_ps, skin=skin, barostat=True,
-                            pressure_atm=p_start, tau_p_ps=2.0)
+    i_npt = integ_of(I, barostat=True, pressure_atm=p_start, tau_p_ps=2.0)
     core.respa_step(ctx, sn, i_npt, 2)
     ctx.sync()
-    barrier()
-    e0.record(stream)
-    core.respa_step(ctx, sn, i_npt, n_side)
-    e1.record(stream)
-    barrier()
-    ctx.sync()
-    ms = max_over_ranks(e0.elapsed_time(e1)) / n_side
+    ms = timed(ctx, sn, i_npt, n_side)
     box_end = dn.box.cpu().numpy().reshape(-1)
     side["npt"] = {"ns_per_day": ns_per_day(I.dt_outer, 1e3 / ms) * world, "ms_per_step": ms, "steps": n_side,
                    "pressure_atm": p_start, "tau_p_ps": 2.0,
@@ -466,24 +570,13 @@ def main():
     del frames, ctxD
 
     # --------------------------------------------------------------- STS
+    # single-time-step BAOAB at 1 fs, no HMR: with plain FP32 models (the
+    # baseline the target is stated against) and with the same split-bf16
+    # contractions as DMTS-NC (to separate precision from multiple time steps)
     sts = W["sts"]
-    m_el = sy.element_masses()
-    sy2 = W["system"]()
-    d2 = core.DeviceSystem(sy2)
-    st2 = core.MDState(d2, S.maxwell_boltzmann(m_el, sts.temperature, W["rng_seed"]),
-                       m_el.astype(np.float32), seeds=sts.seed, replica_ids=[D.replica_id(rank, 0)])
-    integ2 = core.integrator(sts.dt_outer, 1, sts.temperature, sts.gamma_ps, mode=1, skin=skin)
-    n_sts = max(10, args.steps)
-    core.respa_step(ctx, st2, integ2, args.warmup)
-    ctx.sync()
-    barrier()
-    e0.record(stream)
-    core.respa_step(ctx, st2, integ2, n_sts)
-    e1.record(stream)
-    barrier()
-    ctx.sync()
-    ms_sts = max_over_ranks(e0.elapsed_time(e1)) / n_sts
-    st2.release()
+    n_sts = max(10, args.steps // 2)
+    ms_sts = run_leg(ctx32, W["system"](), sts, W["rng_seed"], n_sts, warm=args.warmup, sts=True)
+    ms_sts_bf = run_leg(ctx, W["system"](), sts, W["rng_seed"], n_sts, warm=3, sts=True)
 
     # --------------------------------------------------------------- e2e
     # state held on the host (pinned): every step copies x, v in, runs one
@@ -497,7 +590,6 @@ def main():
     ctx.sync()
     n_e2e = max(5, args.steps // 4)
     barrier()
-    t0 = time.perf_counter()
     e0.record(stream)
     for _ in range(n_e2e):
         d3.x.copy_(hx, non_blocking=True)
@@ -514,51 +606,42 @@ def main():
     bytes_in = 2 * sy.n_atoms * 12
     bytes_out = 2 * sy.n_atoms * 12 + 8
 
-    # ------------------------------------------------ 100,000-atom box
-    # the largest synthetic system: same models, the integrator and list
-    # kernels at a size where they stream enough bytes to be HBM-bound
-    WL = S.WORKLOADS[LARGE_WORKLOAD]
-    syL = WL["system"]()
-    csL, nsL = WL["cons"](), WL["nc"]()
-    ctxL = core.Context(cons=(csL, S.cons_weights(csL, WL["w_seed"])), nc=(nsL, S.nc_weights(nsL, WL["w_seed"])),
-                        device=local)
-    IL = WL["dmts"]
-    mL = core.masses_hmr(syL.species, syL.mol_id, syL.element_masses(), IL.hmr_delta)
-    dL = core.DeviceSystem(syL)
-    stL = core.MDState(dL, S.maxwell_boltzmann(mL, IL.temperature, WL["rng_seed"]), mL.astype(np.float32),
-                       seeds=IL.seed, replica_ids=[D.replica_id(rank, 0)])
-    integL = core.integrator(IL.dt_outer, IL.n_inner, IL.temperature, IL.gamma_ps, skin=skin)
-    n_large = max(5, min(20, args.steps // 10))
-    core.respa_step(ctxL, stL, integL, 3)
-    ctxL.sync()
-    core.profile_enable(ctxL, True)
-    barrier()
-    e0.record(stream)
-    core.respa_step(ctxL, stL, integL, n_large)
-    e1.record(stream)
-    barrier()
-    ctxL.sync()
-    profL = core.profile_read(ctxL)
-    core.profile_enable(ctxL, False)
-    ms_large = max_over_ranks(e0.elapsed_time(e1)) / n_large
-    stL.release()
-    stsL = WL["sts"]
-    mLe = syL.element_masses()
-    dL2 = core.DeviceSystem(syL)
-    stL2 = core.MDState(dL2, S.maxwell_boltzmann(mLe, stsL.temperature, WL["rng_seed"]), mLe.astype(np.float32),
-                        seeds=stsL.seed, replica_ids=[D.replica_id(rank, 0)])
-    integL2 = core.integrator(stsL.dt_outer, 1, stsL.temperature, stsL.gamma_ps, mode=1, skin=skin)
-    core.respa_step(ctxL, stL2, integL2, 3)
-    ctxL.sync()
-    barrier()
-    e0.record(stream)
-    core.respa_step(ctxL, stL2, integL2, 2 * n_large)
-    e1.record(stream)
-    barrier()
-    ctxL.sync()
-    ms_large_sts = max_over_ranks(e0.elapsed_time(e1)) / (2 * n_large)
-    stL2.release()
-    del ctxL
+    # ---------------------------------- the other configurations (1, 2, 5)
+    # each: DMTS-NC with its own models and the single-time-step baseline in
+    # plain FP32; the 100,000-atom box also with FP32 DMTS-NC and bf16 STS
+    others = {}
+    for name in ("water_192", "water_12288", LARGE_WORKLOAD):
+        Wo = S.WORKLOADS[name]
+        syo = Wo["system"]()
+        cso, nso = Wo["cons"](), Wo["nc"]()
+        cbo, nbo = S.cons_weights(cso, Wo["w_seed"]), S.nc_weights(nso, Wo["w_seed"])
+        ctxo = core.Context(cons=(cso, cbo), nc=(nso, nbo), device=local)
+        ctxo32 = core.Context(cons=(dataclasses.replace(cso, bf16=False), cbo),
+                              nc=(dataclasses.replace(nso, bf16=False), nbo), device=local)
+        n_o = max(5, min(50, args.steps // 4)) if syo.n_atoms > 50000 else max(10, args.steps // 2)
+        big = name == LARGE_WORKLOAD
+        if big:
+            core.profile_enable(ctxo, True)
+        ms_d = run_leg(ctxo, syo, Wo["dmts"], Wo["rng_seed"], n_o)
+        prof_o = core.profile_read(ctxo) if big else None
+        if big:
+            core.profile_enable(ctxo, False)
+        ms_s = run_leg(ctxo32, syo, Wo["sts"], Wo["rng_seed"], 2 * n_o, sts=True)
+        rec = {"n_atoms": syo.n_atoms, "precision": "split-bf16" if cso.bf16 else "fp32",
+               "ns_per_day": ns_per_day(Wo["dmts"].dt_outer, 1e3 / ms_d) * world, "ms_per_step": ms_d,
+               "sts_fp32_ns_per_day": ns_per_day(Wo["sts"].dt_outer, 1e3 / ms_s) * world,
+               "sts_fp32_ms_per_step": ms_s, "steps": n_o}
+        rec["speedup_vs_sts"] = rec["ns_per_day"] / rec["sts_fp32_ns_per_day"]
+        if cso.bf16:
+            ms_d32 = run_leg(ctxo32, syo, Wo["dmts"], Wo["rng_seed"], n_o)
+            ms_sbf = run_leg(ctxo, syo, Wo["sts"], Wo["rng_seed"], 2 * n_o, sts=True)
+            rec["fp32_ns_per_day"] = ns_per_day(Wo["dmts"].dt_outer, 1e3 / ms_d32) * world
+            rec["sts_bf16_ns_per_day"] = ns_per_day(Wo["sts"].dt_outer, 1e3 / ms_sbf) * world
+        if big:
+            rec["kernels_ms_per_step"] = {k: v[1] / n_o for k, v in prof_o.items()}
+            prof_large, n_large, n_at_large = prof_o, n_o, syo.n_atoms
+        others[name] = rec
+        del ctxo, ctxo32
 
     # ----------------------------------------------------------- serving
     # (1) the 23,558-atom system as a request of the serving loop
@@ -584,6 +667,7 @@ def main():
     barrier()
     tk = sst["tick_ms"]
     lat = np.array([o["t_done_s"] - o["t_arrival_s"] for o in outs])
+    ms_sts_ns = ns_per_day(sts.dt_outer, 1e3 / ms_sts)
     serving = {
         "workload": f"{n_req} Poisson requests (200/s), 80-1600 atoms each, 50-2000 outer steps, open droplets",
         "p50_ms_per_outer_step": float(np.percentile(tk, 50)), "p99_ms_per_outer_step": float(np.percentile(tk, 99)),
@@ -592,9 +676,12 @@ def main():
         "request_latency_s_p50": float(np.percentile(lat, 50)), "request_latency_s_p99": float(np.percentile(lat, 99)),
         "failed": int(sum(o["status"] != 0 for o in outs)),
         "kernel_roofline": serving_roofline(prof_serve, sst["atom_outer_steps"], I.n_inner, cs),
+        "tick_ms_all": [round(float(t), 4) for t in tk],
+        "tick_atoms_all": [int(a) for a in sst["tick_atoms"]],
+        "tail": serving_tail(tk, sst["tick_atoms"]),
         "solvated_chain_23558_in_loop": {"ns_per_day": ns_per_day(I.dt_outer, 1e3 / ms_serve) * world,
                                          "ms_per_outer_step": ms_serve,
-                                         "vs_sts": ns_per_day(I.dt_outer, 1e3 / ms_serve) / ns_per_day(sts.dt_outer, 1e3 / ms_sts)},
+                                         "vs_sts": ns_per_day(I.dt_outer, 1e3 / ms_serve) / ms_sts_ns},
     }
 
     # ---------------------------------------------------------- roofline
@@ -602,42 +689,44 @@ def main():
     pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pk_path):
         peaks = json.load(open(pk_path))
+    fp32_pk, fp32_src = fp32_peak_tflops(torch.cuda.get_device_properties(local), peaks)
     C = cs.C
-    # algorithmic FLOP per active edge (one layer), counted as 2 per FMA:
-    # forward: radial 3*8 FMA + 3 mul + 9 FMA per channel;
-    # adjoint: radial and derivative 48 FMA + 18 + 9 + 3 + 9 + 9 + 3 per
-    # channel, plus 30 FMA per lane for the direction derivatives; layer 0
-    # has no sender-role gradient (its inputs are the species embedding), so
-    # 87 FMA per channel there. mp_bwd is the average over the L launches of
-    # one evaluation, as the per-launch time is.
     Lc = cs.L
-    flop_edge = {"mp_fwd": 2 * 36 * C,
-                 "mp_bwd": (2 * 99 * C * (Lc - 1) + 2 * 87 * C) / Lc + 2 * 30 * 32}
-    fp32_peak_tflops = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
-    fp32_src = "152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz (nominal unit counts and max clock)"
+    nl1 = cs.lmax + 1
+    nlm = nl1 * nl1
+    # the method's work per active edge and layer (each FMA 2 FLOP): the
+    # radial contraction R_lc = sum_k W B_k (K (l_max+1) FMA per channel) and
+    # the message into A_lm (one FMA per (l, m) and channel); the adjoint
+    # with per-layer recomputation counts twice the forward
+    flop_method = {"mp_fwd": 2 * (cs.K * nl1 + nlm) * C}
+    flop_method["mp_bwd"] = 2 * flop_method["mp_fwd"]
+    # what the kernels execute per active edge (each FMA 2 FLOP): forward
+    # 36 FMA per channel; adjoint 99 per channel (87 in layer 0, which has no
+    # sender-role gradient) plus 30 per lane for the direction derivatives,
+    # averaged over the L launches of one evaluation
+    flop_kernel = {"mp_fwd": 2 * 36 * C,
+                   "mp_bwd": (2 * 99 * C * (Lc - 1) + 2 * 87 * C) / Lc + 2 * 30 * 32}
 
     def per_launch_s(pr, k):
         v = pr.get(k)
         return v[1] / v[0] * 1e-3 if v and v[0] else None
 
-    ranked = sorted(((k, v) for k, v in prof.items() if k in flop_edge), key=lambda kv: -kv[1][1])
+    ranked = sorted(((k, v) for k, v in prof.items() if k in flop_method), key=lambda kv: -kv[1][1])
     name = ranked[0][0] if ranked else "mp_bwd"
     pl = per_launch_s(prof, name)
-    achieved = flop_edge[name] * e_cons / pl / 1e12 if pl else None
-    roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
-            "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops if achieved else None,
-            "traffic": ncu_traffic(name), "peak_source": fp32_src,
-            "work_per_launch": f"{flop_edge[name]} FLOP x {e_cons} active edges",
-            "algorithmic_bytes_per_launch": None}
-    # node arrays once (fp32 unless noted) and the active-edge stream (4 B of
-    # column index per active entry): forward reads s, x and writes A, q
-    # (+ its bf16 copy); the adjoint reads s, gA, g_s and x and writes g_s
-    # (+ bf16 copy) and F
-    nlm = (cs.lmax + 1) ** 2
+    achieved = flop_method[name] * e_cons / pl / 1e12 if pl else None
+    # node arrays once and the active-edge stream (4 B of column index per
+    # active entry): forward reads s, x and writes A, q (+ its split-bf16
+    # copy); the adjoint reads s, gA, g_s and x and writes g_s (+ copy) and F
     n_at = sy.n_atoms
-    alg_bytes = {"mp_fwd": n_at * (4 * C + 12 + 4 * nlm * C + 6 * (cs.lmax + 1) * C) + 4 * e_cons,
-                 "mp_bwd": n_at * (4 * C + 4 * nlm * C + 12 + 12 + (Lc - 1) / Lc * (4 * C + 6 * C)) + 4 * e_cons}
-    roof["algorithmic_bytes_per_launch"] = alg_bytes[name]
+    alg_bytes = {"mp_fwd": n_at * (4 * C + 12 + 4 * nlm * C + 8 * nl1 * C) + 4 * e_cons,
+                 "mp_bwd": n_at * (4 * C + 4 * nlm * C + 12 + 12 + (Lc - 1) / Lc * (4 * C + 8 * C)) + 4 * e_cons}
+    roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fp32_pk, "unit": "TFLOP/s",
+            "frac": achieved / fp32_pk if achieved else None, "traffic": ncu_traffic(name),
+            "work": f"{flop_method[name]} FLOP per active edge (the method's count) x {e_cons} edges per launch",
+            "peak_source": fp32_src,
+            "kernel_executed_tflops": flop_kernel[name] * e_cons / pl / 1e12 if pl else None,
+            "algorithmic_bytes_per_launch": alg_bytes[name]}
 
     # every hot kernel against its own bound (per-launch averages over the
     # timed region; algorithmic work counts each node array once and each
@@ -657,22 +746,22 @@ def main():
     nc_bytes = N * (qkw * 4 + ns.n_l * 12 + 12 + 12) + 4 * e_nc
     kr = {}
     for k in ("mp_fwd", "mp_bwd"):
-        a = rate(flop_edge[k] * e_cons, per_launch_s(prof, k), 1e12)
+        a = rate(flop_method[k] * e_cons, per_launch_s(prof, k), 1e12)
         kr[k] = {"row": "a2+a3" if k == "mp_fwd" else "a5", "bound": "alu", "tflops": a,
-                 "frac_fp32_peak": a / fp32_peak_tflops if a else None}
+                 "frac_fp32_peak": a / fp32_pk if a else None,
+                 "kernel_executed_tflops": rate(flop_kernel[k] * e_cons, per_launch_s(prof, k), 1e12)}
     g = rate(gemm_flop_cons, t_gemm, 1e12)
     kr["gemm_tc"] = {"row": "a4", "bound": "tensor", "tflops": g, "frac_bf16_sustained": g / bf16_pk if g and bf16_pk else None,
-                     "flop_per_step": gemm_flop_cons}
+                     "flop_per_step": gemm_flop_cons,
+                     "note": "the model's FLOP; split-bf16 issues three bf16 MMAs per product"}
     g = rate(gemm_flop_nc * I.n_inner, t_ncg, 1e12)
     kr["nc_gemm_tc"] = {"row": "a4 (NC)", "bound": "tensor", "tflops": g,
                         "frac_bf16_sustained": g / bf16_pk if g and bf16_pk else None}
-    # the NC layer's forward: radial K(l_max+1) FMA + (l_max+1) mul +
-    # (l_max+1)^2 FMA per (edge, channel), as for the conservative layer
     nnl = ns.lmax + 1
     flop_nc_edge = 2 * (ns.K * nnl + nnl + nnl * nnl) * Cn
     a = rate(flop_nc_edge * e_nc, per_launch_s(prof, "nc_mp_fwd"), 1e12)
     kr["nc_mp_fwd"] = {"row": "a7 (NC layer: a2+a3 at NC sizes)", "bound": "alu", "tflops": a,
-                       "frac_fp32_peak": a / fp32_peak_tflops if a else None, "flop_per_edge": flop_nc_edge}
+                       "frac_fp32_peak": a / fp32_pk if a else None, "flop_per_edge": flop_nc_edge}
     b = rate(nc_bytes, per_launch_s(prof, "nc_head"), 1e9)
     kr["nc_head"] = {"row": "a7", "bound": "hbm", "gbs": b, "frac_hbm": b / hbm if b and hbm else None,
                      "bytes_per_launch": nc_bytes}
@@ -682,48 +771,62 @@ def main():
     b = rate(ib * N, per_launch_s(prof, "integrate"), 1e9)
     kr["integrate"] = {"row": "a8", "bound": "hbm", "gbs": b, "frac_hbm": b / hbm if b and hbm else None,
                        "bytes_per_launch": ib * N}
-    b = rate(ib * syL.n_atoms, per_launch_s(profL, "integrate"), 1e9)
+    b = rate(ib * n_at_large, per_launch_s(prof_large, "integrate"), 1e9)
     kr["integrate_100k"] = {"row": "a8", "bound": "hbm", "gbs": b, "frac_hbm": b / hbm if b and hbm else None,
-                            "bytes_per_launch": ib * syL.n_atoms}
+                            "bytes_per_launch": ib * n_at_large}
     shares = {k: {"launches": v[0], "ms_per_step": v[1] / n_prof,
                   "share": v[1] / max(sum(x[1] for x in prof.values()), 1e-9)} for k, v in prof.items()}
 
     val = ns_per_day(I.dt_outer, 1e3 / ms_dmts) * world
     sts_val = ns_per_day(sts.dt_outer, 1e3 / ms_sts) * world
+    sts_bf_val = ns_per_day(sts.dt_outer, 1e3 / ms_sts_bf) * world
+    e2e_val = ns_per_day(I.dt_outer, 1e3 / ms_e2e) * world
+    cpu = None
+    if rank == 0 and not args.no_cpu and world == 1:
+        t_outer, _, desc = oracle_outer_step_seconds(sy, W, 0.6)
+        ncpu, model = host_cpu()
+        cpu = {"value": ns_per_day(I.dt_outer, 1.0 / t_outer), "unit": "ns/day", "cores": 1, "kind": "oracle",
+               "sample": desc, "host_cpus": ncpu, "cpu_model": model}
+    pick = lambda d, *ks: {k: d[k] for k in ks}   # noqa: E731
+    # the contract line: headline first, short; everything else in the detail file
     line = {
         "metric": "ns/day (DMTS-NC)", "value": val, "unit": "ns/day", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_dmts, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16" if cs.bf16 else "f32", "data": "synthetic",
-        "config": workload_config(sy, I, cs, ns),
-        "atom_steps_per_s": sy.n_atoms * 1e3 / ms_dmts * world,
-        "sts": {"ns_per_day": sts_val, "ms_per_step": ms_sts, "dt_fs": sts.dt_outer,
-                "atom_steps_per_s": sy.n_atoms * 1e3 / ms_sts * world},
+        "config": {"workload": sy.name, "n_atoms": sy.n_atoms,
+                   "integrator": f"DMTS-NC {I.dt_outer} fs / {I.n_inner} inner, HMR, HHF",
+                   "precision": "split-bf16 tcgen05 MLPs, fp32 elsewhere, fp64 sums" if cs.bf16 else "fp32",
+                   "l2": "inputs larger than L2", "parallelism": "replicas only"},
         "speedup_vs_sts": val / sts_val,
-        "e2e": {"value": ns_per_day(I.dt_outer, 1e3 / ms_e2e) * world, "unit": "ns/day",
-                "h2d_bytes_per_step": bytes_in, "d2h_bytes_per_step": bytes_out, "steps": n_e2e},
-        "serving": serving,
+        "sts": {"fp32_ns_per_day": sts_val, "bf16_ns_per_day": sts_bf_val, "ms_per_step": ms_sts},
+        "serving": {**pick(serving, "p50_ms_per_outer_step", "p99_ms_per_outer_step", "atom_outer_steps_per_s",
+                           "failed"),
+                    "atoms_at_p50_p99_tick": [serving["tail"]["atoms_at_p50_tick"], serving["tail"]["atoms_at_p99_tick"]]
+                    if serving["tail"] else None,
+                    "chain_in_loop_ns_per_day": serving["solvated_chain_23558_in_loop"]["ns_per_day"],
+                    "chain_in_loop_vs_sts": serving["solvated_chain_23558_in_loop"]["vs_sts"]},
+        "e2e": {"value": e2e_val, "unit": "ns/day", "h2d_bytes_per_step": bytes_in, "d2h_bytes_per_step": bytes_out},
+        "atom_steps_per_s": sy.n_atoms * 1e3 / ms_dmts * world,
         "gpu_launches": n_launches,
         "clocks": ck,
-        "roofline": roof,
-        "kernels": shares,
-        "kernel_roofline": kr,
-        "rewind_guard": side["guarded"],
-        "ffl": side["ffl"],
-        "npt": side["npt"],
-        "distill": side["distill"],
-        "large_system": {"workload": syL.name, "n_atoms": syL.n_atoms, "steps": n_large,
-                         "ns_per_day": ns_per_day(IL.dt_outer, 1e3 / ms_large) * world, "ms_per_step": ms_large,
-                         "sts_ns_per_day": ns_per_day(stsL.dt_outer, 1e3 / ms_large_sts) * world,
-                         "sts_ms_per_step": ms_large_sts,
-                         "speedup_vs_sts": ns_per_day(IL.dt_outer, 1e3 / ms_large) / ns_per_day(stsL.dt_outer, 1e3 / ms_large_sts),
-                         "kernels_ms_per_step": {k: v[1] / n_large for k, v in profL.items()}},
-        "active_edges": {"cons": e_cons, "nc": e_nc},
+        "roofline": pick(roof, "kernel", "bound", "achieved", "peak", "unit", "frac", "traffic"),
+        "configs": {k: {"ns_per_day": round(v["ns_per_day"], 2), "vs_sts": round(v["speedup_vs_sts"], 2)}
+                    for k, v in others.items()},
+        "cpu_baseline": pick(cpu, "value", "unit", "cores", "kind", "sample") if cpu else None,
     }
-    if rank == 0 and not args.no_cpu and world == 1:
-        t_outer, desc = oracle_outer_step_seconds(sy, W, 0.6)
-        line["cpu_baseline"] = {"value": ns_per_day(I.dt_outer, 1.0 / t_outer), "unit": "ns/day",
-                                "cores": 1, "kind": "oracle", "sample": desc}
+    detail = dict(line, roofline=roof, cpu_baseline=cpu, thermo_end={"K": thermo_end[0], "U_plus_K": thermo_end[1],
+                                                                     "T": thermo_end[2]},
+                  sts={"fp32": {"ns_per_day": sts_val, "ms_per_step": ms_sts},
+                       "bf16": {"ns_per_day": sts_bf_val, "ms_per_step": ms_sts_bf},
+                       "dt_fs": sts.dt_outer, "atom_steps_per_s": sy.n_atoms * 1e3 / ms_sts * world},
+                  speedup_vs_sts_bf16=val / sts_bf_val, serving=serving, kernels=shares, kernel_roofline=kr,
+                  rewind_guard=side["guarded"], ffl=side["ffl"], npt=side["npt"], distill=side["distill"],
+                  configs=others, active_edges={"cons": e_cons, "nc": e_nc})
     if rank == 0:
+        if args.detail:
+            os.makedirs(os.path.dirname(os.path.abspath(args.detail)), exist_ok=True)
+            with open(args.detail, "w") as f:
+                json.dump(detail, f, indent=1)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

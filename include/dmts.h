@@ -189,9 +189,9 @@ dmts_status nbr_build(dmts_ctx *ctx, const dmts_system *sys, dmts_nbr *nbr,
 /*
  * nbr_build for callers that cannot allocate device memory -- code running
  * where cudaMalloc is unavailable or forbidden (inside a memory-pool-managed
- * framework that owns every device allocation, during stream capture, or in
- * a plug-in that may only touch buffers its host hands it), and callers that
- * have no dmts_ctx because creating one allocates. The paper has no
+ * framework that owns every device allocation, or in a plug-in that may only
+ * touch buffers its host hands it), and callers that have no dmts_ctx
+ * because creating one allocates. The paper has no
  * counterpart; this is the same cell-list neighbour build as nbr_build, with
  * identical output.
  *
@@ -469,6 +469,9 @@ typedef struct {
     double wall_s;             /* out: duration of the whole run */
     double atom_outer_steps;   /* out: sum over ticks of resident atoms */
     int max_resident;          /* out */
+    int *tick_atoms;           /* host array of capacity tick_cap (may be NULL): atoms in the packed batch
+                                  each tick integrated (resident replicas, and retired ones not yet
+                                  removed by a re-pack) */
 } dmts_serve_stats;
 
 /*

@@ -96,7 +96,8 @@ class Result(ct.Structure):
 
 class ServeStats(ct.Structure):
     _fields_ = [("tick_ms", ct.c_void_p), ("tick_cap", ct.c_int), ("n_ticks", ct.c_int),
-                ("wall_s", ct.c_double), ("atom_outer_steps", ct.c_double), ("max_resident", ct.c_int)]
+                ("wall_s", ct.c_double), ("atom_outer_steps", ct.c_double), ("max_resident", ct.c_int),
+                ("tick_atoms", ct.c_void_p)]
 
 
 # every entry point declared in include/dmts.h

@@ -419,7 +419,8 @@ def run_replicas(ctx: Context, requests, integ: L.Integrator, hbm_budget_bytes: 
                  max_slots: int = 512, realtime: bool = False, tick_cap: int = 1 << 20):
     """Continuous-batching serving loop. Returns (results, stats): results[k]
     = dict(x, v, energy, t_arrival_s, t_admit_s, t_done_s, status); stats =
-    dict(tick_ms, n_ticks, wall_s, atom_outer_steps, max_resident)."""
+    dict(tick_ms, tick_atoms, n_ticks, wall_s, atom_outer_steps, max_resident),
+    tick_atoms being the atoms of the packed batch each tick integrated."""
     n = len(requests)
     reqs = (L.Request * max(1, n))(*[r.struct() for r in requests])
     xs = [np.zeros_like(r.x) for r in requests]
@@ -429,14 +430,16 @@ def run_replicas(ctx: Context, requests, integ: L.Integrator, hbm_budget_bytes: 
         res[k].x = xs[k].ctypes.data
         res[k].v = vs[k].ctypes.data
     ticks = np.zeros(tick_cap, np.float64)
-    stats = L.ServeStats(ticks.ctypes.data, tick_cap, 0, 0.0, 0.0, 0)
+    tick_atoms = np.zeros(tick_cap, np.int32)
+    stats = L.ServeStats(ticks.ctypes.data, tick_cap, 0, 0.0, 0.0, 0, tick_atoms.ctypes.data)
     cfg = L.ServeCfg(int(hbm_budget_bytes), int(max_slots), 1 if realtime else 0)
     st = ctx.lib.run_replicas(ctx.handle, reqs, n, ct.byref(integ), ct.byref(cfg), res, ct.byref(stats))
     L.check(st, ctx.handle)
     out = [dict(x=xs[k], v=vs[k], energy=res[k].energy, t_arrival_s=res[k].t_arrival_s,
                 t_admit_s=res[k].t_admit_s, t_done_s=res[k].t_done_s, status=res[k].status) for k in range(n)]
     nt = min(stats.n_ticks, tick_cap)
-    return out, dict(tick_ms=ticks[:nt].copy(), n_ticks=stats.n_ticks, wall_s=stats.wall_s,
+    return out, dict(tick_ms=ticks[:nt].copy(), tick_atoms=tick_atoms[:nt].copy(), n_ticks=stats.n_ticks,
+                     wall_s=stats.wall_s,
                      atom_outer_steps=stats.atom_outer_steps, max_resident=stats.max_resident)
 
 

@@ -839,6 +839,14 @@ dmts_status nbr_build(dmts_ctx *ctx, const dmts_system *sys, dmts_nbr *nbr, long
     NbrWork nw;
     s = prepare_nbr_work(ctx, ctx->nbr_scratch, v, grids, n_cells, nullptr, nw, st);
     if (s != DMTS_OK) return s;
+    if (sys->n_atoms == 0) {
+        // nothing to launch: the one row offset is 0 and there are no pairs
+        if (!ck(ctx, cudaMemsetAsync(nbr->row_ptr, 0, sizeof(int), st), "row_ptr") ||
+            !ck(ctx, cudaStreamSynchronize(st), "nbr_build"))
+            return DMTS_E_CUDA;
+        if (n_pairs) *n_pairs = 0;
+        return DMTS_OK;
+    }
     nbr_cells(nw, nbr->r_list, st);
     nbr_fill(nw, nbr->r_list, nbr->row_ptr, nbr->col, nbr->capacity, nullptr, st);
     long long tot = 0;

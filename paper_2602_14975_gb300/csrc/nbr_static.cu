@@ -137,6 +137,9 @@ extern "C" dmts_status nbr_build_noalloc(const dmts_system *sys, dmts_nbr *nbr, 
         !ck(nullptr, cudaMemcpyAsync(w.grid, h_grid, sizeof(CellGrid) * R, cudaMemcpyHostToDevice, st),
             "nbr_build_noalloc: grid"))
         return DMTS_E_CUDA;
+    // an empty system launches nothing: its one row offset is written here
+    if (N == 0 && !ck(nullptr, cudaMemsetAsync(nbr->row_ptr, 0, sizeof(int), st), "nbr_build_noalloc: row_ptr"))
+        return DMTS_E_CUDA;
     atom_rep_map(sys->rep_off, R, N, atom_rep, st);
     nbr_cells(w, nbr->r_list, st);
     nbr_fill(w, nbr->r_list, nbr->row_ptr, nbr->col, nbr->capacity, nullptr, st);

@@ -368,6 +368,7 @@ dmts_status run_replicas(dmts_ctx *ctx, const dmts_request *reqs, int n_req, con
         float ms = 0.f;
         cudaEventElapsedTime(&ms, ev0, ev1);
         if (stats && stats->tick_ms && n_ticks < stats->tick_cap) stats->tick_ms[n_ticks] = ms;
+        if (stats && stats->tick_atoms && n_ticks < stats->tick_cap) stats->tick_atoms[n_ticks] = state.sys.n_atoms;
         ++n_ticks;
         ++ticks_since_repack;
         int off = 0, r = 0, resident = 0;

@@ -101,6 +101,13 @@ def test_nbr_empty_replica_and_single_atom(ctx1):
     nb = core.nbr_build(ctx1, d, 5.5)
     rp = nb.row_ptr.cpu().numpy()
     assert rp[1] - rp[0] == 0
+    # a system without atoms: no kernel runs, and its one row offset is 0
+    none = S.System("none", np.zeros((0, 3)), np.zeros(0, np.uint8), np.zeros(0, np.int32),
+                    np.zeros((0, 2), np.int32), np.zeros(0), np.zeros(3))
+    d0 = core.DeviceSystem(none)
+    for _ in range(2):
+        nb0 = core.nbr_build(ctx1, d0, 5.5)
+        assert nb0.n_pairs == 0 and nb0.row_ptr.cpu().tolist() == [0]
 
 
 def _state_system(systems, x):

@@ -1,7 +1,6 @@
 """GPU test of nbr_build_noalloc, the neighbour build for callers that cannot
 allocate device memory (a host framework that owns every device allocation,
-code running under stream capture, a plug-in limited to the buffers it is
-given). Its scratch is a fixed static device array; these checks call it
+a plug-in limited to the buffers it is given). Its scratch is a fixed static device array; these checks call it
 through the C ABI and compare its lists with nbr_build's, bit for bit, on
 consecutive calls that reuse that array."""
 import ctypes as ct
@@ -64,3 +63,14 @@ def test_noalloc_overflow_then_recovers_and_rejects_oversize():
     nn = ct.c_longlong(0)
     assert L.lib().nbr_build_noalloc(ct.byref(big), ct.byref(nb), ct.byref(nn), None) == L.E_INVALID
     assert b"DMTS_STATIC_MAX_ATOMS" in L.lib().dmts_last_error(None)
+
+
+def test_noalloc_empty_system_writes_its_row_offset():
+    """A system without atoms launches nothing; the call still sets the one
+    row offset it owns to 0 (the buffer held -7)."""
+    none = S.System("none", np.zeros((0, 3)), np.zeros(0, np.uint8), np.zeros(0, np.int32),
+                    np.zeros((0, 2), np.int32), np.zeros(0), np.zeros(3))
+    d0 = core.DeviceSystem(none)
+    st, row, _, n = _noalloc(d0, 5.5, 16)
+    assert st == L.OK, L.lib().dmts_last_error(None)
+    assert n == 0 and row.cpu().tolist() == [0]
