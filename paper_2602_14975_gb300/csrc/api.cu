@@ -461,7 +461,11 @@ dmts_status nc_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const i
     a.order = s.order;
     a.err = ctx->d_err;
     { ProfScope ps(ctx, "nc_head", st); launch_nc_head(m.K, m.nc, m.nl, a, st); }
-    {
+    if (flags & kFlagDeferMean) {
+        ProfScope ps(ctx, "mean_sub", st);
+        launch_mean_only((float *)w.nc_f.p, s.rep_off, s.n_rep, N, net, w.ms_scratch.p, s.ms_part_off, s.ms_cnt,
+                         s.ms_mean, ctx->d_err, st);
+    } else {
         ProfScope ps(ctx, "mean_sub", st);
         launch_mean_sub((float *)w.nc_f.p, forces, s.rep_off, s.n_rep, N, net, w.ms_scratch.p, ctx->d_err, st,
                         s.ms_part_off);
@@ -535,6 +539,8 @@ SysView state_view(dmts_state *stt) {
     v.atom_rep = (int *)si->atom_rep.p;
     v.order = (const int *)si->scratch.cell_atoms.p;   // atoms sorted by cell at the last rebuild
     v.ms_part_off = (const int *)si->ms_part.p;
+    v.ms_cnt = (int *)si->ms_cnt.p;
+    v.ms_mean = (float *)si->ms_mean.p;
     return v;
 }
 
@@ -639,6 +645,8 @@ void free_state_internal(StateInternal *si) {
     si->gate.release();
     si->atom_rep.release();
     si->ms_part.release();
+    si->ms_cnt.release();
+    si->ms_mean.release();
     si->baro_ke.release();
     si->baro_K.release();
     si->baro_f.release();
@@ -670,8 +678,11 @@ dmts_status init_state(dmts_ctx *ctx, dmts_state *stt, float skin, cudaStream_t 
     const int N = si->n;
     if (!si->atom_rep.ensure(sizeof(int) * (N + 1)) || !si->x_ref.ensure(sizeof(float) * 3 * (N + 1)) ||
         !si->gate.ensure(sizeof(int)) || !si->cons_row.ensure(sizeof(int) * (N + 1)) ||
-        !si->nc_row.ensure(sizeof(int) * (N + 1)) || !si->ms_part.ensure(sizeof(int) * (sys->n_replicas + 1)))
+        !si->nc_row.ensure(sizeof(int) * (N + 1)) || !si->ms_part.ensure(sizeof(int) * (sys->n_replicas + 1)) ||
+        !si->ms_cnt.ensure(sizeof(int) * sys->n_replicas) || !si->ms_mean.ensure(sizeof(float) * 3 * sys->n_replicas))
         return fail(ctx, DMTS_E_OOM, "state allocation failed");
+    if (!ck(ctx, cudaMemsetAsync(si->ms_cnt.p, 0, sizeof(int) * sys->n_replicas, st), "state counters"))
+        return DMTS_E_CUDA;
     atom_rep_map(sys->rep_off, sys->n_replicas, N, (int *)si->atom_rep.p, st);
     launch_mean_part_off(sys->rep_off, sys->n_replicas, (int *)si->ms_part.p, st);
     k_set_int<<<1, 1, 0, st>>>((int *)si->gate.p, 1);
@@ -1142,11 +1153,26 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
     };
     // fast force; inside the inner loop it also adds its virial proxy to the
     // per-replica average of the outer step (Sec. 2, virial term in NPT)
+    // The fast force's mean subtraction is left to the next integrator launch
+    // (or the kinetic-energy reduction before it), which reads the head's
+    // force and the replica means and stores the subtracted force in
+    // stt->f_nc: one launch and one pass over the forces less per inner step.
+    bool mean_pending = false;
     auto nc_fast = [&](bool with_virial) {
-        const dmts_status r = nc_eval(ctx, v, nrow, ncol, stt->f_nc, nullptr, DMTS_WITH_BONDS | nc_emb, st,
-                                      with_virial ? stt->virial_nc : nullptr, 1);
+        const dmts_status r = nc_eval(ctx, v, nrow, ncol, stt->f_nc, nullptr, DMTS_WITH_BONDS | nc_emb | kFlagDeferMean,
+                                      st, with_virial ? stt->virial_nc : nullptr, 1);
         nc_emb = kFlagEmbedded;
+        mean_pending = true;
         return r;
+    };
+    auto integrate = [&](IntegArgs a) {
+        if (mean_pending) {
+            a.fast_pre = (const float *)ctx->ws.nc_f.p;
+            a.fast_mean = v.ms_mean;
+            a.fast_out = stt->f_nc;
+            mean_pending = false;
+        }
+        launch_integrate(a, st);
     };
 
     if (stt->first_step) {
@@ -1183,7 +1209,14 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
     gamma_consts(p, delta, ia.c1, ia.c2);
     ia.h_in = (float)(0.5 * delta);
     ia.h_out = 0.5f * p->dt_outer;
-    if (n_outer == 0) return DMTS_OK;
+    if (n_outer == 0) {
+        if (mean_pending) {   // first forces only: store the subtracted fast force
+            IntegArgs a0 = ia;
+            a0.ops = 0;
+            integrate(a0);
+        }
+        return ck(ctx, cudaGetLastError(), "respa_step launch") ? DMTS_OK : DMTS_E_CUDA;
+    }
     // FP64 K, U + K and T per replica (pending closing kicks selected per call site)
     ThermoArgs ta;
     memset(&ta, 0, sizeof ta);
@@ -1201,6 +1234,10 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
         t.close_b = pending;
         t.kick_l = pending && !sts;
         t.trace = trace_row;
+        if (pending && mean_pending) {
+            t.f_fast = (const float *)ctx->ws.nc_f.p;
+            t.fast_mean = v.ms_mean;
+        }
         ProfScope ps(ctx, "thermo", st);
         launch_thermo(t, v.n_rep, st);
     };
@@ -1229,7 +1266,7 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
         ik.ops = 0;
         ik.baro_f = nullptr;
         ik.ke = (float *)si->baro_ke.p;
-        launch_integrate(ik, st);
+        integrate(ik);
         launch_replica_sum((const float *)si->baro_ke.p, v.rep_off, v.n_rep, (double *)si->baro_K.p, 0, st);
     }
     // outer steps not timed under a sampling profiler; calls outside the loop are
@@ -1256,7 +1293,7 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
             else if (k == 0) ia.ops = (o == 0 ? OP_KICK_L2 : (OP_CLOSE_B | OP_KICK_L | OP_KICK_L2)) | OP_BAOA;
             else ia.ops = OP_CLOSE_B | OP_BAOA;
             ia.step_add = (uint64_t)o * n_in + k;
-            { ProfScope ps(ctx, "integrate", st); launch_integrate(ia, st); }
+            { ProfScope ps(ctx, "integrate", st); integrate(ia); }
             rebuild_lists(ctx, si, v, st);
             if (!sts) {
                 s = nc_fast(stt->virial_nc != nullptr);
@@ -1284,7 +1321,7 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
             // close the outer step, then the piston's half kick with the estimator
             ia.ops = OP_CLOSE_B | OP_KICK_L;
             ia.ke = (float *)si->baro_ke.p;
-            { ProfScope ps(ctx, "integrate", st); launch_integrate(ia, st); }
+            { ProfScope ps(ctx, "integrate", st); integrate(ia); }
             ia.ke = nullptr;
             launch_replica_sum((const float *)si->baro_ke.p, v.rep_off, v.n_rep, (double *)si->baro_K.p, 0, st);
             ba.wvir = stt->virial_est;
@@ -1296,7 +1333,7 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
     }
     if (!npt) {
         ia.ops = sts ? OP_CLOSE_B : (OP_CLOSE_B | OP_KICK_L);
-        { ProfScope ps(ctx, "integrate", st); launch_integrate(ia, st); }
+        { ProfScope ps(ctx, "integrate", st); integrate(ia); }
     }
     if (stt->thermo && !stt->thermo_trace) thermo(false, nullptr);
     launch_advance_step(stt->step, v.n_rep, (uint64_t)n_outer * n_in, ctx->d_err, st);

@@ -87,13 +87,15 @@ struct SysView {
     const int *atom_rep;
     const int *order = nullptr;   // processing order of the per-atom kernels (nullable)
     const int *ms_part_off = nullptr;   // mean-subtraction part offsets of this batch (nullable)
+    int *ms_cnt = nullptr;              // per-replica part counters of the deferred mean (zero between uses)
+    float *ms_mean = nullptr;           // per-replica fast-force means of the deferred mean [R][3]
 };
 
 struct StateInternal {
     int n = 0, n_rep = 0, n_cells = 0;
     float skin = 0.f, r_cons = 0.f, r_nc = 0.f, grid_margin = 0.f;
     std::vector<CellGrid> grids;
-    Buf cons_row, cons_col, nc_row, nc_col, x_ref, gate, atom_rep, ms_part;
+    Buf cons_row, cons_col, nc_row, nc_col, x_ref, gate, atom_rep, ms_part, ms_cnt, ms_mean;
     Buf baro_ke, baro_K, baro_f;   // barostat: per-atom kinetic energy, per-replica sum, drift factors
     long long cons_cap = 0, nc_cap = 0;
     NbrScratch scratch;
@@ -160,6 +162,10 @@ constexpr int kFlagEmbedded = 1 << 30;
 // Internal flag of nc_eval: keep the layer output A (ws.dist_A) and the MLP
 // pre-activation (ws.dist_h) for the distillation's backward pass.
 constexpr int kFlagKeepPre = 1 << 29;
+// Internal flag of nc_eval (respa_step): leave the mean subtraction to the
+// integrator; the head's force stays in ws.nc_f and the replica means go to
+// the state's ms_mean (forces is not written).
+constexpr int kFlagDeferMean = 1 << 28;
 dmts_status cons_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const int *col, double *energy,
                       float *forces, int flags, cudaStream_t st, double *virial = nullptr);
 dmts_status nc_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const int *col, float *forces,

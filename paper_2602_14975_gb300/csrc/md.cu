@@ -789,10 +789,15 @@ __device__ __forceinline__ bool mean_part_of(const int *part_off, int n_rep, int
     return true;
 }
 
+// Per-part FP64 sums of F_in. With cnt (zero on entry, left zero), the block
+// that completes the last part of a replica also adds that replica's part
+// sums in part order and writes the mean (float, as the subtraction uses
+// it) and, with net, the net force (the same sums k_mean_apply forms).
 __global__ void __launch_bounds__(MS_THREADS) k_mean_partial(const float *__restrict__ F_in,
                                                              const int *__restrict__ rep_off,
                                                              const int *__restrict__ part_off, int n_rep,
-                                                             double *__restrict__ partial, const int *__restrict__ err) {
+                                                             double *__restrict__ partial, const int *__restrict__ err,
+                                                             int *cnt, float *mean, double *net) {
     if (*err) return;
     int r, p;
     if (!mean_part_of(part_off, n_rep, blockIdx.x, r, p)) return;
@@ -817,6 +822,20 @@ __global__ void __launch_bounds__(MS_THREADS) k_mean_partial(const float *__rest
         double t = 0.0;
         for (int w = 0; w < MS_THREADS / 32; ++w) t += red[threadIdx.x][w];
         partial[3 * (size_t)blockIdx.x + threadIdx.x] = t;
+    }
+    if (!cnt) return;
+    __shared__ int last;
+    __threadfence();            // this block's part sums visible before its ticket
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(cnt + r, 1) == part_off[r + 1] - part_off[r] - 1;
+    __syncthreads();
+    if (last && threadIdx.x < 3) {
+        __threadfence();
+        double t = 0.0;
+        for (int q = part_off[r]; q < part_off[r + 1]; ++q) t += __ldcg(partial + 3 * (size_t)q + threadIdx.x);
+        if (net) net[3 * r + threadIdx.x] = t;
+        mean[3 * r + threadIdx.x] = (float)(t / (double)(rep_off[r + 1] - rep_off[r]));
+        if (threadIdx.x == 0) cnt[r] = 0;
     }
 }
 
@@ -873,9 +892,19 @@ void launch_mean_sub(const float *F_in, float *F_out, const int *rep_off, int n_
         k_mean_part_off<<<1, 1024, 0, st>>>(rep_off, n_rep, part_off, net);
         count_launch();
     }
-    k_mean_partial<<<parts, MS_THREADS, 0, st>>>(F_in, rep_off, part_off, n_rep, partial, err);
+    k_mean_partial<<<parts, MS_THREADS, 0, st>>>(F_in, rep_off, part_off, n_rep, partial, err, nullptr, nullptr,
+                                                 nullptr);
     count_launch();
     k_mean_apply<<<parts, MS_THREADS, 0, st>>>(F_in, F_out, rep_off, part_off, n_rep, partial, net, err);
+    count_launch();
+}
+
+void launch_mean_only(const float *F_in, const int *rep_off, int n_rep, int n_atoms, double *net, void *scratch,
+                      const int *part_off, int *cnt, float *mean, const int *err, cudaStream_t st) {
+    if (n_rep == 0) return;
+    const int parts = (n_atoms + MS_PART - 1) / MS_PART + n_rep;
+    double *partial = static_cast<double *>(scratch);
+    k_mean_partial<<<parts, MS_THREADS, 0, st>>>(F_in, rep_off, part_off, n_rep, partial, err, cnt, mean, net);
     count_launch();
 }
 
@@ -971,7 +1000,17 @@ __global__ void k_integrate(IntegArgs g) {
     if (i >= g.n_atoms) return;
     const float am = kAccConv / g.masses[i];
     float vx = g.v[3 * i], vy = g.v[3 * i + 1], vz = g.v[3 * i + 2];
-    const float sfx = g.f_fast[3 * i], sfy = g.f_fast[3 * i + 1], sfz = g.f_fast[3 * i + 2];
+    float sfx, sfy, sfz;
+    if (g.fast_pre) {
+        // the fast force's pending mean subtraction, stored as the cached force
+        const int r = g.atom_rep[i];
+        sfx = g.fast_pre[3 * i] - g.fast_mean[3 * r];
+        sfy = g.fast_pre[3 * i + 1] - g.fast_mean[3 * r + 1];
+        sfz = g.fast_pre[3 * i + 2] - g.fast_mean[3 * r + 2];
+        g.fast_out[3 * i] = sfx; g.fast_out[3 * i + 1] = sfy; g.fast_out[3 * i + 2] = sfz;
+    } else {
+        sfx = g.f_fast[3 * i]; sfy = g.f_fast[3 * i + 1]; sfz = g.f_fast[3 * i + 2];
+    }
     if (g.ops & OP_CLOSE_B) closing_b(g.h_in * am, sfx, sfy, sfz, vx, vy, vz);
     if (g.ops & (OP_KICK_L | OP_KICK_L2)) {
         const float h = g.h_out * am;
@@ -1060,7 +1099,10 @@ __global__ void __launch_bounds__(kThermoThreads) k_thermo(ThermoArgs g) {
         const float am = kAccConv / g.masses[i];
         float vx = g.v[3 * i], vy = g.v[3 * i + 1], vz = g.v[3 * i + 2];
         if (g.close_b || g.kick_l) {
-            const float sfx = g.f_fast[3 * i], sfy = g.f_fast[3 * i + 1], sfz = g.f_fast[3 * i + 2];
+            float sfx = g.f_fast[3 * i], sfy = g.f_fast[3 * i + 1], sfz = g.f_fast[3 * i + 2];
+            if (g.fast_mean) {
+                sfx -= g.fast_mean[3 * r]; sfy -= g.fast_mean[3 * r + 1]; sfz -= g.fast_mean[3 * r + 2];
+            }
             if (g.close_b) closing_b(g.h_in * am, sfx, sfy, sfz, vx, vy, vz);
             if (g.kick_l)
                 outer_kick(g.h_out * am, g.f_slow[3 * i] - sfx, g.f_slow[3 * i + 1] - sfy, g.f_slow[3 * i + 2] - sfz,

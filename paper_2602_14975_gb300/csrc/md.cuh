@@ -99,6 +99,12 @@ void launch_mean_sub(const float *F_in, float *F_out, const int *rep_off, int n_
                      void *scratch, const int *err, cudaStream_t st, const int *part_off = nullptr);
 // part_off: device int [n_rep + 1]
 void launch_mean_part_off(const int *rep_off, int n_rep, int *part_off, cudaStream_t st);
+// The first half of launch_mean_sub for a consumer that subtracts the mean
+// itself (the integrator): per-replica mean (float [R][3]) and net force
+// (double [R][3], nullable) of F_in; cnt: device int [n_rep], zero on entry
+// and left zero.
+void launch_mean_only(const float *F_in, const int *rep_off, int n_rep, int n_atoms, double *net, void *scratch,
+                      const int *part_off, int *cnt, float *mean, const int *err, cudaStream_t st);
 
 struct PriorArgs {
     const float *x;
@@ -150,6 +156,11 @@ struct IntegArgs {
     const float *baro_f;           // nullable: per replica [3] = e^(b h), h (e^(b h) - 1)/(b h), e^(-a h)
     float *box;                    // with baro_f: per-replica box, scaled by e^(2 b h) per BAOA
     float *ke;                     // nullable: per-atom kinetic energy m v^2 / 2 (kcal/mol) after the update
+    // nullable: the fast force before its mean subtraction; when set, the
+    // force used is fast_pre - fast_mean[replica] (float [R][3]) and it is
+    // written to fast_out (f_fast is then not read)
+    const float *fast_pre, *fast_mean;
+    float *fast_out;
 };
 void launch_integrate(const IntegArgs &a, cudaStream_t st);
 
@@ -160,6 +171,7 @@ struct ThermoArgs {
     const float *v, *f_fast, *f_slow, *masses;
     float h_in, h_out;
     int close_b, kick_l;           // apply v += h_in a F_fast, then v += h_out a (F_slow - F_fast)
+    const float *fast_mean;        // nullable: [R][3] mean still to be subtracted from f_fast
     const double *energy;          // [R] potential energy U at the same configuration
     double *out;                   // [R][3]: K, U + K, T
     double *trace;                 // nullable: [R][3] copy (one row of a per-outer-step trace)
