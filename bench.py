@@ -108,6 +108,8 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--detail", default="", help="also write every leg's figures to this JSON file")
+    ap.add_argument("--main-only", action="store_true",
+                    help="only the timed DMTS-NC leg (for profiler captures); prints its time and kernel shares")
     return ap.parse_args()
 
 
@@ -474,6 +476,12 @@ def main():
     ms_dmts = max_over_ranks(e0.elapsed_time(e1)) / args.steps
     thermo_end = st.thermo.cpu().numpy()[0].tolist()
     st.release()
+    if args.main_only:
+        if rank == 0:
+            print(json.dumps({"workload": sy.name, "ms_per_step": ms_dmts,
+                              "ns_per_day": ns_per_day(I.dt_outer, 1e3 / ms_dmts) * world, "gpu_launches": n_launches,
+                              "kernels_ms_per_step": {k: v[1] / n_prof for k, v in prof.items()}}), flush=True)
+        return 0
 
     # ------------------------------------- rewind guard, FFL thermostat
     # the same outer step under the rewind guard (saved frame and monitor

@@ -46,6 +46,14 @@ bool Buf::ensure(size_t bytes) {
     return true;
 }
 
+// ensure() for a buffer that must hold zeros whenever it is not in use: a
+// new allocation is cleared on the stream.
+static bool ensure_zeroed(dmts_ctx *ctx, Buf &b, size_t bytes, cudaStream_t st) {
+    if (bytes <= b.cap) return true;
+    if (!b.ensure(bytes)) return false;
+    return ck(ctx, cudaMemsetAsync(b.p, 0, b.cap, st), "workspace clear");
+}
+
 void Buf::release() {
     if (p) cudaFree(p);
     p = nullptr;
@@ -395,7 +403,9 @@ dmts_status nc_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const i
     if (!w.nc_s.ensure(sizeof(float) * nc_ * 2) ||
         !w.nc_q.ensure(sizeof(float) * nc_ * 2) ||
         !w.nc_act.ensure(sizeof(float) * nc_) || !w.nc_qk.ensure(sizeof(float) * (size_t)N * QKW) ||
-        !w.nc_v.ensure(sizeof(float) * (size_t)N * m.nl * 3) || !w.nc_f.ensure(sizeof(float) * 3 * (N + 1)) ||
+        !w.nc_v.ensure(sizeof(float) * (size_t)N * nc_v_stride(m.nl)) || !w.nc_f.ensure(sizeof(float) * 3 * (N + 1)) ||
+        !ensure_zeroed(ctx, w.nc_ffix, sizeof(unsigned long long) * 3 * (N + 1), st) ||
+        !w.nc_sum.ensure(sizeof(unsigned long long) * 3 * (s.n_rep + 1)) ||
         !w.ms_scratch.ensure(mean_sub_scratch_bytes(N, s.n_rep)) ||
         (virial && !w.nc_w.ensure(sizeof(float) * (N + 1))))
         return fail(ctx, DMTS_E_OOM, "workspace allocation failed");
@@ -456,19 +466,22 @@ dmts_status nc_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const i
     if (flags & DMTS_WITH_BONDS) a.bonds = {s.bond_ptr, s.bond_idx, s.bond_r0, ctx->prior.k_bond};
     a.rep = rep_table(ctx);
     a.species = s.species;
-    a.F = (float *)w.nc_f.p;
+    a.Ffix = (unsigned long long *)w.nc_ffix.p;
+    a.sum = (unsigned long long *)w.nc_sum.p;
+    a.n_rep = s.n_rep;
     a.W = virial ? (float *)w.nc_w.p : nullptr;
     a.order = s.order;
     a.err = ctx->d_err;
     { ProfScope ps(ctx, "nc_head", st); launch_nc_head(m.K, m.nc, m.nl, a, st); }
-    if (flags & kFlagDeferMean) {
+    if (N == 0 && !ck(ctx, cudaMemsetAsync(w.nc_sum.p, 0, sizeof(unsigned long long) * 3 * s.n_rep, st), "sums"))
+        return DMTS_E_CUDA;   // no head launch clears them
+    {
+        // fp32 forces and the replicas' exact sums; the mean subtraction here
+        // or, inside respa_step, in the next integrator launch
         ProfScope ps(ctx, "mean_sub", st);
-        launch_mean_only((float *)w.nc_f.p, s.rep_off, s.n_rep, N, net, w.ms_scratch.p, s.ms_part_off, s.ms_cnt,
-                         s.ms_mean, ctx->d_err, st);
-    } else {
-        ProfScope ps(ctx, "mean_sub", st);
-        launch_mean_sub((float *)w.nc_f.p, forces, s.rep_off, s.n_rep, N, net, w.ms_scratch.p, ctx->d_err, st,
-                        s.ms_part_off);
+        launch_nc_convert(N, s.atom_rep, a.Ffix, (float *)w.nc_f.p, a.sum, st);
+        if (!(flags & kFlagDeferMean))
+            launch_nc_apply(N, s.atom_rep, s.rep_off, s.n_rep, (float *)w.nc_f.p, forces, a.sum, net, ctx->d_err, st);
     }
     if (virial) {
         ProfScope ps(ctx, "replica_sum", st);
@@ -539,8 +552,6 @@ SysView state_view(dmts_state *stt) {
     v.atom_rep = (int *)si->atom_rep.p;
     v.order = (const int *)si->scratch.cell_atoms.p;   // atoms sorted by cell at the last rebuild
     v.ms_part_off = (const int *)si->ms_part.p;
-    v.ms_cnt = (int *)si->ms_cnt.p;
-    v.ms_mean = (float *)si->ms_mean.p;
     return v;
 }
 
@@ -645,8 +656,6 @@ void free_state_internal(StateInternal *si) {
     si->gate.release();
     si->atom_rep.release();
     si->ms_part.release();
-    si->ms_cnt.release();
-    si->ms_mean.release();
     si->baro_ke.release();
     si->baro_K.release();
     si->baro_f.release();
@@ -678,11 +687,8 @@ dmts_status init_state(dmts_ctx *ctx, dmts_state *stt, float skin, cudaStream_t 
     const int N = si->n;
     if (!si->atom_rep.ensure(sizeof(int) * (N + 1)) || !si->x_ref.ensure(sizeof(float) * 3 * (N + 1)) ||
         !si->gate.ensure(sizeof(int)) || !si->cons_row.ensure(sizeof(int) * (N + 1)) ||
-        !si->nc_row.ensure(sizeof(int) * (N + 1)) || !si->ms_part.ensure(sizeof(int) * (sys->n_replicas + 1)) ||
-        !si->ms_cnt.ensure(sizeof(int) * sys->n_replicas) || !si->ms_mean.ensure(sizeof(float) * 3 * sys->n_replicas))
+        !si->nc_row.ensure(sizeof(int) * (N + 1)) || !si->ms_part.ensure(sizeof(int) * (sys->n_replicas + 1)))
         return fail(ctx, DMTS_E_OOM, "state allocation failed");
-    if (!ck(ctx, cudaMemsetAsync(si->ms_cnt.p, 0, sizeof(int) * sys->n_replicas, st), "state counters"))
-        return DMTS_E_CUDA;
     atom_rep_map(sys->rep_off, sys->n_replicas, N, (int *)si->atom_rep.p, st);
     launch_mean_part_off(sys->rep_off, sys->n_replicas, (int *)si->ms_part.p, st);
     k_set_int<<<1, 1, 0, st>>>((int *)si->gate.p, 1);
@@ -1168,7 +1174,7 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
     auto integrate = [&](IntegArgs a) {
         if (mean_pending) {
             a.fast_pre = (const float *)ctx->ws.nc_f.p;
-            a.fast_mean = v.ms_mean;
+            a.fast_sum = (const unsigned long long *)ctx->ws.nc_sum.p;
             a.fast_out = stt->f_nc;
             mean_pending = false;
         }
@@ -1236,7 +1242,7 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
         t.trace = trace_row;
         if (pending && mean_pending) {
             t.f_fast = (const float *)ctx->ws.nc_f.p;
-            t.fast_mean = v.ms_mean;
+            t.fast_sum = (const unsigned long long *)ctx->ws.nc_sum.p;
         }
         ProfScope ps(ctx, "thermo", st);
         launch_thermo(t, v.n_rep, st);

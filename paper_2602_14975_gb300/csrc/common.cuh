@@ -22,6 +22,11 @@ void count_launch();
 
 __device__ __forceinline__ void set_error(int *err, int code) { atomicCAS(err, 0, code); }
 
+// Row stride (floats) of the NC model's tensor-head vectors V [N][stride]:
+// n_l 3-vectors padded to a multiple of four floats, so that a row is a
+// whole number of 16-byte units (bulk copies).
+__host__ __device__ constexpr int nc_v_stride(int n_l) { return 4 * ((3 * n_l + 3) / 4); }
+
 // Split-bf16 operand copies of the tensor-core contractions. A logical
 // [rows][K] fp32 operand is stored as bf16 [rows][2K]: column c holds
 // hi = rn(v) and column K + c holds lo = rn(v - hi), so hi + lo carries

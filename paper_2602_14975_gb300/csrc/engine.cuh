@@ -53,6 +53,8 @@ struct NbrScratch {
 struct Workspace {
     Buf s, A, q, h, act, u, gz, gs0, gs1, gA, e_atom, ftmp, atom_rep;
     Buf nc_s, nc_q, nc_act, nc_qk, nc_v, nc_f;
+    Buf nc_ffix;      // NC head forces in 32.32 fixed point, zero between evaluations
+    Buf nc_sum;       // per-replica exact sums of the NC forces (fixed point) of the last evaluation
     // split-bf16 operands of the tensor-core contractions ([rows][2K])
     Buf q_bf, act_bf, s_bf, gz_bf, gs0_bf, gs1_bf, nc_q_bf, nc_act_bf, nc_s_bf;
     Buf ms_scratch;   // per-part sums of the mean subtraction
@@ -65,7 +67,7 @@ struct Workspace {
     Buf dist_A, dist_gq, dist_gv;
     void release_all() {
         Buf *all[] = {&s, &A, &q, &h, &act, &u, &gz, &gs0, &gs1, &gA, &e_atom, &ftmp, &atom_rep,
-                      &nc_s, &nc_q, &nc_act, &nc_qk, &nc_v, &nc_f,
+                      &nc_s, &nc_q, &nc_act, &nc_qk, &nc_v, &nc_f, &nc_ffix, &nc_sum,
                       &q_bf, &act_bf, &s_bf, &gz_bf, &gs0_bf, &gs1_bf, &nc_q_bf, &nc_act_bf, &nc_s_bf,
                       &ms_scratch, &nc_w, &cons_w, &nc_w_last,
                       &dist_F, &dist_g, &dist_sq, &dist_gqk, &dist_gs1, &dist_gh, &dist_h, &dist_dw,
@@ -87,15 +89,13 @@ struct SysView {
     const int *atom_rep;
     const int *order = nullptr;   // processing order of the per-atom kernels (nullable)
     const int *ms_part_off = nullptr;   // mean-subtraction part offsets of this batch (nullable)
-    int *ms_cnt = nullptr;              // per-replica part counters of the deferred mean (zero between uses)
-    float *ms_mean = nullptr;           // per-replica fast-force means of the deferred mean [R][3]
 };
 
 struct StateInternal {
     int n = 0, n_rep = 0, n_cells = 0;
     float skin = 0.f, r_cons = 0.f, r_nc = 0.f, grid_margin = 0.f;
     std::vector<CellGrid> grids;
-    Buf cons_row, cons_col, nc_row, nc_col, x_ref, gate, atom_rep, ms_part, ms_cnt, ms_mean;
+    Buf cons_row, cons_col, nc_row, nc_col, x_ref, gate, atom_rep, ms_part;
     Buf baro_ke, baro_K, baro_f;   // barostat: per-atom kinetic energy, per-replica sum, drift factors
     long long cons_cap = 0, nc_cap = 0;
     NbrScratch scratch;
@@ -163,8 +163,8 @@ constexpr int kFlagEmbedded = 1 << 30;
 // pre-activation (ws.dist_h) for the distillation's backward pass.
 constexpr int kFlagKeepPre = 1 << 29;
 // Internal flag of nc_eval (respa_step): leave the mean subtraction to the
-// integrator; the head's force stays in ws.nc_f and the replica means go to
-// the state's ms_mean (forces is not written).
+// integrator; the force before it stays in ws.nc_f and the replicas' exact
+// sums in ws.nc_sum (forces is not written).
 constexpr int kFlagDeferMean = 1 << 28;
 dmts_status cons_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const int *col, double *energy,
                       float *forces, int flags, cudaStream_t st, double *virial = nullptr);

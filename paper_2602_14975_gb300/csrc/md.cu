@@ -42,21 +42,34 @@ void launch_rowsum(int n, int C, const float *u, float scale, float *e_atom, cud
     count_launch();
 }
 
+// Bond entry q of atom a (d = x_j - x_a): the force on a, k (r - r0) d / r,
+// its energy and pair-form virial. The same bond seen from j gives exactly
+// the opposite force (d exactly negated, the same r and factor).
+__device__ __forceinline__ void bond_term(const BondTable &b, const float *x, int q, float xa, float ya, float za,
+                                          float bx, float by, float bz, float ibx, float iby, float ibz, float &gx,
+                                          float &gy, float &gz, float &e, float &w) {
+    const int j = b.idx[q];
+    const float dx = min_img(x[3 * j] - xa, bx, ibx);
+    const float dy = min_img(x[3 * j + 1] - ya, by, iby);
+    const float dz = min_img(x[3 * j + 2] - za, bz, ibz);
+    const float r = sqrtf(dx * dx + dy * dy + dz * dz);
+    const float dr = r - b.r0[q];
+    const float g = b.k * dr / r;
+    gx = g * dx; gy = g * dy; gz = g * dz;
+    e = 0.25f * b.k * dr * dr;            // each bond is listed by both atoms
+    w = 0.5f * g * r * r;                 // pair-form virial, half per listed direction
+}
+
 __device__ __forceinline__ void bond_force(const BondTable &b, const float *x, int a, float bx, float by,
                                            float bz, float ibx, float iby, float ibz, int lane, float &fx,
                                            float &fy, float &fz, float &e, float *w = nullptr) {
     const float xa = x[3 * a], ya = x[3 * a + 1], za = x[3 * a + 2];
     for (int q = b.ptr[a] + lane; q < b.ptr[a + 1]; q += 32) {
-        const int j = b.idx[q];
-        const float dx = min_img(x[3 * j] - xa, bx, ibx);
-        const float dy = min_img(x[3 * j + 1] - ya, by, iby);
-        const float dz = min_img(x[3 * j + 2] - za, bz, ibz);
-        const float r = sqrtf(dx * dx + dy * dy + dz * dz);
-        const float dr = r - b.r0[q];
-        const float g = b.k * dr / r;     // F_a = k (r - r0) d / r, d = x_j - x_a
-        fx += g * dx; fy += g * dy; fz += g * dz;
-        e += 0.25f * b.k * dr * dr;       // each bond is listed by both atoms
-        if (w) *w += 0.5f * g * r * r;    // pair-form virial, half per listed direction
+        float gx, gy, gz, eq, wq;
+        bond_term(b, x, q, xa, ya, za, bx, by, bz, ibx, iby, ibz, gx, gy, gz, eq, wq);
+        fx += gx; fy += gy; fz += gz;
+        e += eq;
+        if (w) *w += wq;
     }
 }
 
@@ -113,19 +126,61 @@ __device__ __forceinline__ float rep_pair(const RepTable &t, int si, int sj, flo
 }
 
 // ------------------------------------------------------------- NC head
-// Warp per atom a; lane per neighbour j. For each head h:
+// Each pair (a, j), a < j, within r_c is evaluated once, by atom a's warp:
 //   c_ajh = q_ah . k_jh / sqrt(n_c),  c_jah = q_jh . k_ah / sqrt(n_c)
 //   F_aj = (sum_{h<K} c_ajh B_h) (n + sum_{h<n_l} c_aj(K+h) V_ah) f_c
 //   F_ja = (sum_{h<K} c_jah B_h) (-n + sum_{h<n_l} c_ja(K+h) V_jh) f_c
-//   F_a = scale sum_j (F_aj - F_ja) (+ bonds)
-// Active neighbours are taken 16 at a time (the g-th active entry of the row
-// in batch g / 16 on lanes g % 16 and g % 16 + 16). The first lane of each
-// pair starts one bulk copy of its neighbour's q/k row into shared memory;
-// both evaluate the radial part of the edge while the rows arrive, then each
-// forms the dot products of half of the heads from shared memory and the two
-// halves are added with one shuffle. No load instruction gathers scattered
-// rows, and 16-row staging keeps enough warps resident to hide the latency.
+//   P_aj = scale (F_aj - F_ja) (+ the screened repulsion of the pair)
+// which enters F_a with + and F_j with - (the antisymmetric sum), so every
+// pair costs one evaluation instead of one from each end. Forces are summed
+// in 32.32 fixed point with 64-bit integer atomics: integer addition is
+// exact and associative, so F does not depend on the order in which warps
+// add their terms, nor on the skin entries of the list (bit-reproducible
+// alone or batched). k_mean_partial converts F to fp32 and clears it.
+// Upper active neighbours (j > a) are taken 16 at a time (the g-th in
+// batch g / 16 on lanes g % 16 and g % 16 + 16): the first lane of each pair
+// bulk-copies the neighbour's q/k row into shared memory while both evaluate
+// the radial part, each forms the dot products of half of the heads.
 constexpr int NCH_WARPS = 2;
+constexpr float kFixScale = 4294967296.f;     // 2^32 per unit force (kcal/mol/A)
+constexpr float kFixMax = 16777216.f;         // |term| bound (2^24): up to 128 terms fit the 64-bit sums
+
+__device__ __forceinline__ long long to_fix(float v) { return __float2ll_rn(v * kFixScale); }
+__device__ __forceinline__ void fix_add(unsigned long long *dst, long long q) {
+    atomicAdd(dst, (unsigned long long)q);
+}
+__device__ __forceinline__ double fix_sum_to_double(unsigned long long s) {
+    return (double)(long long)s * (1.0 / 4294967296.0);   // exact for |s| < 2^53
+}
+__device__ __forceinline__ float fix_to_float(long long q) { return (float)((double)q * (1.0 / 4294967296.0)); }
+// Mean force of replica r from its exact fixed-point sum (FP64, as used by
+// the subtraction).
+// The sums of the head's forces cancel exactly (every term enters two atoms
+// with opposite signs), so a zero sum is the rule and skips the division.
+__device__ __forceinline__ float fix_mean1(unsigned long long s, double n) {
+    return s == 0ull ? 0.f : (float)(fix_sum_to_double(s) / n);
+}
+__device__ __forceinline__ float3 fix_mean(const unsigned long long *sum, const int *rep_off, int r) {
+    const double n = (double)(rep_off[r + 1] - rep_off[r]);
+    return make_float3(fix_mean1(sum[3 * r], n), fix_mean1(sum[3 * r + 1], n), fix_mean1(sum[3 * r + 2], n));
+}
+// Sum of a 64-bit integer over the lanes whose key equals this lane's (the
+// lanes of one replica); every lane takes part.
+__device__ __forceinline__ long long seg_sum_ll(long long v, int key) {
+    const int k0 = __shfl_sync(DMTS_FULL, key, 0);
+    if (__all_sync(DMTS_FULL, key == k0)) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(DMTS_FULL, v, o);
+        return v;
+    }
+    const unsigned peers = __match_any_sync(DMTS_FULL, key);
+    long long t = 0;
+    for (int src = 0; src < 32; ++src) {
+        const long long u = __shfl_sync(DMTS_FULL, v, src);
+        if ((peers >> src) & 1u) t += u;
+    }
+    return t;
+}
 
 template <int K, int NC, int NL>
 struct NCHeadSmem {
@@ -134,12 +189,14 @@ struct NCHeadSmem {
     static constexpr int ROWB = QKW * 4;    // bytes copied per row
     static constexpr int BATCH = 16;        // neighbours per staged batch
     static constexpr int HH = (H + 1) / 2;  // heads per lane of a pair
+    static constexpr int VS = nc_v_stride(NL);   // staged V row (floats), a multiple of 16 bytes
     static constexpr size_t rows = (size_t)NCH_WARPS * BATCH * RSTR * 4;
+    static constexpr size_t vrows = (size_t)NCH_WARPS * BATCH * VS * 4;
     static constexpr size_t qk = (size_t)NCH_WARPS * QKW * 4;
     static constexpr size_t vv = (size_t)NCH_WARPS * 4 * NL * 4;
     static constexpr size_t queue = (size_t)NCH_WARPS * 64 * 4;
     static constexpr size_t qdisp = (size_t)NCH_WARPS * 64 * 3 * 4;   // displacement of each queued edge
-    static constexpr size_t bytes = rows + qk + vv + queue + qdisp + NCH_WARPS * 8;
+    static constexpr size_t bytes = rows + vrows + qk + vv + queue + qdisp + NCH_WARPS * 8;
     static_assert(QKW % 16 == 0, "row stride");
     static_assert(HH <= K, "each lane's first heads are Bessel heads");
 };
@@ -152,12 +209,18 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int BATCH = SM::BATCH, HH = SM::HH;
     float *rows = reinterpret_cast<float *>(nch_smem) + (size_t)warp * BATCH * RSTR;
-    float *qa = reinterpret_cast<float *>(nch_smem + SM::rows) + warp * QKW;
-    float *va = reinterpret_cast<float *>(nch_smem + SM::rows + SM::qk) + warp * 4 * NL;
-    int *queue = reinterpret_cast<int *>(nch_smem + SM::rows + SM::qk + SM::vv) + warp * 64;
-    float *qd = reinterpret_cast<float *>(nch_smem + SM::rows + SM::qk + SM::vv + SM::queue) + warp * 64 * 3;
-    uint64_t *bar_p = reinterpret_cast<uint64_t *>(nch_smem + SM::rows + SM::qk + SM::vv + SM::queue + SM::qdisp) + warp;
+    float *vrows = reinterpret_cast<float *>(nch_smem + SM::rows) + (size_t)warp * BATCH * SM::VS;
+    unsigned char *rest = nch_smem + SM::rows + SM::vrows;
+    float *qa = reinterpret_cast<float *>(rest) + warp * QKW;
+    float *va = reinterpret_cast<float *>(rest + SM::qk) + warp * 4 * NL;
+    int *queue = reinterpret_cast<int *>(rest + SM::qk + SM::vv) + warp * 64;
+    float *qd = reinterpret_cast<float *>(rest + SM::qk + SM::vv + SM::queue) + warp * 64 * 3;
+    uint64_t *bar_p = reinterpret_cast<uint64_t *>(rest + SM::qk + SM::vv + SM::queue + SM::qdisp) + warp;
     const uint32_t bar = smem_u32(bar_p);
+    // the per-replica sums of the last evaluation have been consumed: clear
+    // them for this one's conversion
+    if (blockIdx.x == 0 && g.sum)
+        for (int t = threadIdx.x; t < 3 * g.n_rep; t += blockDim.x) g.sum[t] = 0ull;
     const int wa = blockIdx.x * NCH_WARPS + warp;
     if (wa >= g.n_atoms || *g.err) return;
     const int a = g.order ? __ldg(g.order + wa) : wa;
@@ -166,7 +229,7 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
         mbar_init_fence();
     }
     for (int t = lane; t < QKW; t += 32) qa[t] = g.QK[(size_t)a * QKW + t];
-    for (int t = lane; t < NL * 3; t += 32) va[t] = g.V[(size_t)a * NL * 3 + t];
+    for (int t = lane; t < NL * 3; t += 32) va[t] = g.V[(size_t)a * SM::VS + t];
     __syncwarp();
     const float *ka = qa + H * NC;
     const int rep = g.atom_rep[a];
@@ -190,8 +253,9 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
         if (nbp > 4) return is_bonded(g.bonds, a, j);
         return j == bp[0] || j == bp[1] || j == bp[2] || j == bp[3];
     };
-    float fx = 0.f, fy = 0.f, fz = 0.f, rx = 0.f, ry = 0.f, rz = 0.f;
-    float wv = 0.f, wr = 0.f;   // virial proxy: sum_j F_aj . d_aj, and the repulsion's half pair terms
+    long long ox = 0, oy = 0, oz = 0;     // this lane's share of a's side of its pairs, fixed point
+    float wv = 0.f;                       // virial proxy: (F_aj - F_ja) . d_aj (+ repulsion) over a's pairs
+    bool bad = false;                     // a pair term outside the fixed-point range (or not finite)
     uint32_t phase = 0;
     bool alive = true;
 
@@ -202,24 +266,25 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
         const int qs = (taken + slot) & 63;
         const int j = slot < nb ? queue[qs] : -1;
         fence_proxy_async_smem();      // earlier reads of the rows before the copies overwrite them
-        if (lane == 0) mbar_expect_tx(bar, (uint32_t)nb * SM::ROWB);
+        if (lane == 0) mbar_expect_tx(bar, (uint32_t)nb * (SM::ROWB + SM::VS * 4));
         __syncwarp();
-        if (j >= 0 && half == 0) bulk_g2s(smem_u32(rows + slot * RSTR), g.QK + (size_t)j * QKW, SM::ROWB, bar);
+        if (j >= 0 && half == 0) {
+            bulk_g2s(smem_u32(rows + slot * RSTR), g.QK + (size_t)j * QKW, SM::ROWB, bar);
+            bulk_g2s(smem_u32(vrows + slot * SM::VS), g.V + (size_t)j * SM::VS, SM::VS * 4, bar);
+        }
         // radial part of the edge while the rows arrive
-        float dx = 0.f, dy = 0.f, dz = 0.f, inv = 1.f, fc = 0.f, Bh[HH];
+        float dx = 0.f, dy = 0.f, dz = 0.f, inv = 1.f, fc = 0.f, Bh[HH], crep = 0.f, r2 = 0.f;
         if (j >= 0) {
             dx = qd[3 * qs];
             dy = qd[3 * qs + 1];
             dz = qd[3 * qs + 2];
-            const float r2 = dx * dx + dy * dy + dz * dz;
+            r2 = dx * dx + dy * dy + dz * dz;
             const float r = sqrtf(r2);
             inv = 1.f / r;
             if (half == 0 && with_rep && r2 < rep2 && !bonded(j)) {
                 float dE;
                 rep_pair(g.rep, sa, g.species[j], r, &dE);
-                const float c = dE * inv;              // F_a = E'(r) d / r
-                rx += c * dx; ry += c * dy; rz += c * dz;
-                wr += 0.5f * c * r2;
+                crep = dE * inv;               // F_a = E'(r) d / r, F_j = -F_a
             }
             float du;
             fc = envelope(r * g.inv_rc, g.p, &du);
@@ -266,11 +331,11 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
                         part[1] = fmaf(cja, Bh[hl], part[1]);
                     } else {
                         const int t = h - K;
-                        const float *vjt = g.V + ((size_t)j * NL + t) * 3;
+                        const float *vjt = vrows + slot * SM::VS + 3 * t;
 #pragma unroll
                         for (int cmp = 0; cmp < 3; ++cmp) {
                             part[2 + cmp] = fmaf(caj, va[3 * t + cmp], part[2 + cmp]);
-                            part[5 + cmp] = fmaf(cja, __ldg(vjt + cmp), part[5 + cmp]);
+                            part[5 + cmp] = fmaf(cja, vjt[cmp], part[5 + cmp]);
                         }
                     }
                 }
@@ -281,10 +346,20 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
         if (j >= 0 && half == 0) {
             const float nx = dx * inv, ny = dy * inv, nz = dz * inv;
             const float pa = part[0] * fc, pj = part[1] * fc;
-            fx += pa * (nx + part[2]) - pj * (-nx + part[5]);
-            fy += pa * (ny + part[3]) - pj * (-ny + part[6]);
-            fz += pa * (nz + part[4]) - pj * (-nz + part[7]);
-            wv += pa * ((nx + part[2]) * dx + (ny + part[3]) * dy + (nz + part[4]) * dz);
+            const float ux = pa * (nx + part[2]) - pj * (-nx + part[5]);
+            const float uy = pa * (ny + part[3]) - pj * (-ny + part[6]);
+            const float uz = pa * (nz + part[4]) - pj * (-nz + part[7]);
+            const float px = fmaf(g.scale, ux, crep * dx), py = fmaf(g.scale, uy, crep * dy),
+                        pz = fmaf(g.scale, uz, crep * dz);
+            wv += fmaf(g.scale, ux * dx + uy * dy + uz * dz, crep * r2);
+            if (fabsf(px) < kFixMax && fabsf(py) < kFixMax && fabsf(pz) < kFixMax) {
+                const long long qx = to_fix(px), qy = to_fix(py), qz = to_fix(pz);
+                ox += qx; oy += qy; oz += qz;
+                unsigned long long *fj = g.Ffix + 3 * (size_t)j;
+                fix_add(fj, -qx); fix_add(fj + 1, -qy); fix_add(fj + 2, -qz);
+            } else {
+                bad = true;   // not finite, or a blow-up beyond the fixed-point range
+            }
         }
         __syncwarp();
     };
@@ -296,7 +371,7 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
         const int j = e < end ? __ldg(g.col + e) : -1;
         bool act = false;
         float dx = 0.f, dy = 0.f, dz = 0.f;
-        if (j >= 0) {
+        if (j > a) {
             dx = min_img(__ldg(g.x + 3 * j) - xa, bx, ibx);
             dy = min_img(__ldg(g.x + 3 * j + 1) - ya, by, iby);
             dz = min_img(__ldg(g.x + 3 * j + 2) - za, bz, ibz);
@@ -319,16 +394,29 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
     }
     if (alive && queued > taken) batch(taken, queued - taken);
     if (!alive) return;
-    fx = fmaf(g.scale, fx, rx); fy = fmaf(g.scale, fy, ry); fz = fmaf(g.scale, fz, rz);
-    float w = fmaf(g.scale, wv, wr);
+    float w = wv;
     if (g.bonds.ptr) {
-        float e = 0.f;
-        bond_force(g.bonds, g.x, a, bx, by, bz, ibx, iby, ibz, lane, fx, fy, fz, e, &w);
+        // bonds in fixed point too: the two ends' terms cancel exactly
+        for (int q = g.bonds.ptr[a] + lane; q < g.bonds.ptr[a + 1]; q += 32) {
+            float gx, gy, gz, eq, wq;
+            bond_term(g.bonds, g.x, q, xa, ya, za, bx, by, bz, ibx, iby, ibz, gx, gy, gz, eq, wq);
+            if (fabsf(gx) < kFixMax && fabsf(gy) < kFixMax && fabsf(gz) < kFixMax) {
+                ox += to_fix(gx); oy += to_fix(gy); oz += to_fix(gz);
+            } else {
+                bad = true;
+            }
+            w += wq;
+        }
     }
-    fx = warp_sum(fx); fy = warp_sum(fy); fz = warp_sum(fz);
+    if (__any_sync(DMTS_FULL, bad)) {
+        if (lane == 0) set_error(g.err, DMTS_E_NONFINITE);
+        return;
+    }
+    ox = seg_sum_ll(ox, 0); oy = seg_sum_ll(oy, 0); oz = seg_sum_ll(oz, 0);
     if (g.W) w = warp_sum(w);
     if (lane == 0) {
-        g.F[3 * a] = fx; g.F[3 * a + 1] = fy; g.F[3 * a + 2] = fz;
+        unsigned long long *fa = g.Ffix + 3 * (size_t)a;
+        fix_add(fa, ox); fix_add(fa + 1, oy); fix_add(fa + 2, oz);
         if (g.W) g.W[a] = w;
     }
 }
@@ -384,7 +472,7 @@ __global__ void __launch_bounds__(128) k_nc_head_bwd(NCHeadArgs g, const float *
     }
     float va[3 * NL];
 #pragma unroll
-    for (int t = 0; t < 3 * NL; ++t) va[t] = g.V[(size_t)a * NL * 3 + t];
+    for (int t = 0; t < 3 * NL; ++t) va[t] = g.V[(size_t)a * nc_v_stride(NL) + t];
     const float gax = gF[3 * a], gay = gF[3 * a + 1], gaz = gF[3 * a + 2];
     const int rep = g.atom_rep[a];
     const float bx = g.box[3 * rep], by = g.box[3 * rep + 1], bz = g.box[3 * rep + 2];
@@ -423,7 +511,8 @@ __global__ void __launch_bounds__(128) k_nc_head_bwd(NCHeadArgs g, const float *
         if (live && h >= K) {
 #pragma unroll
             for (int q = 0; q < 3; ++q)
-                vt[q] = role_aj ? va[3 * (t < NL ? t : 0) + q] : __ldg(g.V + ((size_t)j * NL + (t < NL ? t : 0)) * 3 + q);
+                vt[q] = role_aj ? va[3 * (t < NL ? t : 0) + q]
+                                : __ldg(g.V + (size_t)j * nc_v_stride(NL) + 3 * (t < NL ? t : 0) + q);
         }
         const float sB = bes ? c * Bh : 0.f;
         const float S_aj = warp_sum(role_aj ? sB : 0.f), S_ja = warp_sum(role_aj ? 0.f : sB);
@@ -789,15 +878,10 @@ __device__ __forceinline__ bool mean_part_of(const int *part_off, int n_rep, int
     return true;
 }
 
-// Per-part FP64 sums of F_in. With cnt (zero on entry, left zero), the block
-// that completes the last part of a replica also adds that replica's part
-// sums in part order and writes the mean (float, as the subtraction uses
-// it) and, with net, the net force (the same sums k_mean_apply forms).
 __global__ void __launch_bounds__(MS_THREADS) k_mean_partial(const float *__restrict__ F_in,
                                                              const int *__restrict__ rep_off,
                                                              const int *__restrict__ part_off, int n_rep,
-                                                             double *__restrict__ partial, const int *__restrict__ err,
-                                                             int *cnt, float *mean, double *net) {
+                                                             double *__restrict__ partial, const int *__restrict__ err) {
     if (*err) return;
     int r, p;
     if (!mean_part_of(part_off, n_rep, blockIdx.x, r, p)) return;
@@ -822,20 +906,6 @@ __global__ void __launch_bounds__(MS_THREADS) k_mean_partial(const float *__rest
         double t = 0.0;
         for (int w = 0; w < MS_THREADS / 32; ++w) t += red[threadIdx.x][w];
         partial[3 * (size_t)blockIdx.x + threadIdx.x] = t;
-    }
-    if (!cnt) return;
-    __shared__ int last;
-    __threadfence();            // this block's part sums visible before its ticket
-    __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(cnt + r, 1) == part_off[r + 1] - part_off[r] - 1;
-    __syncthreads();
-    if (last && threadIdx.x < 3) {
-        __threadfence();
-        double t = 0.0;
-        for (int q = part_off[r]; q < part_off[r + 1]; ++q) t += __ldcg(partial + 3 * (size_t)q + threadIdx.x);
-        if (net) net[3 * r + threadIdx.x] = t;
-        mean[3 * r + threadIdx.x] = (float)(t / (double)(rep_off[r + 1] - rep_off[r]));
-        if (threadIdx.x == 0) cnt[r] = 0;
     }
 }
 
@@ -892,19 +962,65 @@ void launch_mean_sub(const float *F_in, float *F_out, const int *rep_off, int n_
         k_mean_part_off<<<1, 1024, 0, st>>>(rep_off, n_rep, part_off, net);
         count_launch();
     }
-    k_mean_partial<<<parts, MS_THREADS, 0, st>>>(F_in, rep_off, part_off, n_rep, partial, err, nullptr, nullptr,
-                                                 nullptr);
+    k_mean_partial<<<parts, MS_THREADS, 0, st>>>(F_in, rep_off, part_off, n_rep, partial, err);
     count_launch();
     k_mean_apply<<<parts, MS_THREADS, 0, st>>>(F_in, F_out, rep_off, part_off, n_rep, partial, net, err);
     count_launch();
 }
 
-void launch_mean_only(const float *F_in, const int *rep_off, int n_rep, int n_atoms, double *net, void *scratch,
-                      const int *part_off, int *cnt, float *mean, const int *err, cudaStream_t st) {
-    if (n_rep == 0) return;
-    const int parts = (n_atoms + MS_PART - 1) / MS_PART + n_rep;
-    double *partial = static_cast<double *>(scratch);
-    k_mean_partial<<<parts, MS_THREADS, 0, st>>>(F_in, rep_off, part_off, n_rep, partial, err, cnt, mean, net);
+// ------------------------------------------------ NC forces: fixed point
+// One thread per atom: the head's 32.32 fixed-point force -> fp32 (F), the
+// fixed-point words cleared for the next evaluation (also when the error
+// word is set, so an aborted evaluation leaves nothing behind), and the
+// replica's exact integer sum of the forces added to sum[r] (warp-aggregated
+// 64-bit atomics; integer sums do not depend on their order).
+__global__ void k_nc_convert(int n, const int *__restrict__ atom_rep, unsigned long long *__restrict__ Ffix,
+                             float *__restrict__ F, unsigned long long *__restrict__ sum) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = i < n;
+    const int r = live ? atom_rep[i] : -1;
+    long long q[3] = {0, 0, 0};
+    if (live) {
+        for (int c = 0; c < 3; ++c) {
+            q[c] = (long long)Ffix[3 * i + c];
+            Ffix[3 * i + c] = 0ull;
+            F[3 * i + c] = fix_to_float(q[c]);
+        }
+    }
+    const int leader = __ffs(__match_any_sync(DMTS_FULL, r)) - 1;
+    for (int c = 0; c < 3; ++c) {
+        const long long t = seg_sum_ll(q[c], r);
+        if (live && (int)(threadIdx.x & 31) == leader) fix_add(sum + 3 * (size_t)r + c, t);
+    }
+}
+
+void launch_nc_convert(int n, const int *atom_rep, unsigned long long *Ffix, float *F, unsigned long long *sum,
+                       cudaStream_t st) {
+    if (n == 0) return;
+    k_nc_convert<<<(n + 255) / 256, 256, 0, st>>>(n, atom_rep, Ffix, F, sum);
+    count_launch();
+}
+
+// F_out = F - the replica's mean (from the exact sums); net (nullable) [R][3].
+__global__ void k_nc_apply(int n, const int *__restrict__ atom_rep, const int *__restrict__ rep_off, int n_rep,
+                           const float *__restrict__ F, float *__restrict__ F_out,
+                           const unsigned long long *__restrict__ sum, double *__restrict__ net,
+                           const int *__restrict__ err) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (net && i < 3 * n_rep) net[i] = fix_sum_to_double(sum[i]);
+    if (i >= n || *err) return;
+    const int r = atom_rep[i];
+    const float3 m = fix_mean(sum, rep_off, r);
+    F_out[3 * i] = F[3 * i] - m.x;
+    F_out[3 * i + 1] = F[3 * i + 1] - m.y;
+    F_out[3 * i + 2] = F[3 * i + 2] - m.z;
+}
+
+void launch_nc_apply(int n, const int *atom_rep, const int *rep_off, int n_rep, const float *F, float *F_out,
+                     const unsigned long long *sum, double *net, const int *err, cudaStream_t st) {
+    const int work = n > 3 * n_rep ? n : 3 * n_rep;
+    if (work == 0) return;
+    k_nc_apply<<<(work + 255) / 256, 256, 0, st>>>(n, atom_rep, rep_off, n_rep, F, F_out, sum, net, err);
     count_launch();
 }
 
@@ -1003,10 +1119,10 @@ __global__ void k_integrate(IntegArgs g) {
     float sfx, sfy, sfz;
     if (g.fast_pre) {
         // the fast force's pending mean subtraction, stored as the cached force
-        const int r = g.atom_rep[i];
-        sfx = g.fast_pre[3 * i] - g.fast_mean[3 * r];
-        sfy = g.fast_pre[3 * i + 1] - g.fast_mean[3 * r + 1];
-        sfz = g.fast_pre[3 * i + 2] - g.fast_mean[3 * r + 2];
+        const float3 m = fix_mean(g.fast_sum, g.rep_off, g.atom_rep[i]);
+        sfx = g.fast_pre[3 * i] - m.x;
+        sfy = g.fast_pre[3 * i + 1] - m.y;
+        sfz = g.fast_pre[3 * i + 2] - m.z;
         g.fast_out[3 * i] = sfx; g.fast_out[3 * i + 1] = sfy; g.fast_out[3 * i + 2] = sfz;
     } else {
         sfx = g.f_fast[3 * i]; sfy = g.f_fast[3 * i + 1]; sfz = g.f_fast[3 * i + 2];
@@ -1100,8 +1216,9 @@ __global__ void __launch_bounds__(kThermoThreads) k_thermo(ThermoArgs g) {
         float vx = g.v[3 * i], vy = g.v[3 * i + 1], vz = g.v[3 * i + 2];
         if (g.close_b || g.kick_l) {
             float sfx = g.f_fast[3 * i], sfy = g.f_fast[3 * i + 1], sfz = g.f_fast[3 * i + 2];
-            if (g.fast_mean) {
-                sfx -= g.fast_mean[3 * r]; sfy -= g.fast_mean[3 * r + 1]; sfz -= g.fast_mean[3 * r + 2];
+            if (g.fast_sum) {
+                const float3 m = fix_mean(g.fast_sum, g.rep_off, r);
+                sfx -= m.x; sfy -= m.y; sfz -= m.z;
             }
             if (g.close_b) closing_b(g.h_in * am, sfx, sfy, sfz, vx, vy, vz);
             if (g.kick_l)

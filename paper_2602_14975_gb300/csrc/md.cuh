@@ -30,13 +30,17 @@ struct NCHeadArgs {
     float rc, inv_rc, bnorm;
     int p;
     const float *QK;               // [N][2][H][nc]
-    const float *V;                // [N][n_l][3]
+    const float *V;                // [N][nc_v_stride(n_l)]: the n_l 3-vectors of each atom, padded
     float scale;
     BondTable bonds;               // bonds.ptr null: no bond force, no F_rep
     RepTable rep;
     const uint8_t *species;
-    float *F;                      // [N][3] before mean subtraction
-    float *W;                      // nullable [N]: per-atom virial proxy (pair form)
+    unsigned long long *Ffix;      // [N][3] forces before mean subtraction, 32.32 fixed point, added to
+                                   // (zero on entry; launch_nc_convert converts and clears them)
+    unsigned long long *sum;       // [R][3] per-replica exact sums, cleared by the head for launch_nc_convert
+    int n_rep;
+    float *W;                      // nullable [N]: per-atom virial proxy (pair form; each NC pair on its
+                                   // lower-index atom)
     const int *order;              // nullable processing order
     int *err;                      // sticky device error word (read, and set on a timeout)
 };
@@ -99,12 +103,14 @@ void launch_mean_sub(const float *F_in, float *F_out, const int *rep_off, int n_
                      void *scratch, const int *err, cudaStream_t st, const int *part_off = nullptr);
 // part_off: device int [n_rep + 1]
 void launch_mean_part_off(const int *rep_off, int n_rep, int *part_off, cudaStream_t st);
-// The first half of launch_mean_sub for a consumer that subtracts the mean
-// itself (the integrator): per-replica mean (float [R][3]) and net force
-// (double [R][3], nullable) of F_in; cnt: device int [n_rep], zero on entry
-// and left zero.
-void launch_mean_only(const float *F_in, const int *rep_off, int n_rep, int n_atoms, double *net, void *scratch,
-                      const int *part_off, int *cnt, float *mean, const int *err, cudaStream_t st);
+// The NC head's fixed-point forces -> fp32 F, cleared; sum[r] += the
+// replica's exact integer force sum (sum cleared by the head beforehand).
+void launch_nc_convert(int n, const int *atom_rep, unsigned long long *Ffix, float *F, unsigned long long *sum,
+                       cudaStream_t st);
+// F_out = F - mean (replica means from the exact sums: sum / 2^32 / n_r in
+// FP64); net (nullable) [R][3] = the sums in FP64.
+void launch_nc_apply(int n, const int *atom_rep, const int *rep_off, int n_rep, const float *F, float *F_out,
+                     const unsigned long long *sum, double *net, const int *err, cudaStream_t st);
 
 struct PriorArgs {
     const float *x;
@@ -157,9 +163,11 @@ struct IntegArgs {
     float *box;                    // with baro_f: per-replica box, scaled by e^(2 b h) per BAOA
     float *ke;                     // nullable: per-atom kinetic energy m v^2 / 2 (kcal/mol) after the update
     // nullable: the fast force before its mean subtraction; when set, the
-    // force used is fast_pre - fast_mean[replica] (float [R][3]) and it is
-    // written to fast_out (f_fast is then not read)
-    const float *fast_pre, *fast_mean;
+    // force used is fast_pre minus the replica mean formed from fast_sum (the
+    // exact fixed-point sums of launch_nc_convert) and it is written to
+    // fast_out (f_fast is then not read)
+    const float *fast_pre;
+    const unsigned long long *fast_sum;
     float *fast_out;
 };
 void launch_integrate(const IntegArgs &a, cudaStream_t st);
@@ -171,7 +179,8 @@ struct ThermoArgs {
     const float *v, *f_fast, *f_slow, *masses;
     float h_in, h_out;
     int close_b, kick_l;           // apply v += h_in a F_fast, then v += h_out a (F_slow - F_fast)
-    const float *fast_mean;        // nullable: [R][3] mean still to be subtracted from f_fast
+    const unsigned long long *fast_sum;   // nullable: [R][3] fixed-point sums whose mean is still to be
+                                          // subtracted from f_fast
     const double *energy;          // [R] potential energy U at the same configuration
     double *out;                   // [R][3]: K, U + K, T
     double *trace;                 // nullable: [R][3] copy (one row of a per-outer-step trace)

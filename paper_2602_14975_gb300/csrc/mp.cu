@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(MP_WARPS * 32) k_mp_fwd(EdgeGeom g, LayerIO io
                     for (int hh = 0; hh < PW; ++hh)
                         part = fmaf(vget(u4[p], hh), io.nu * vget(acc[1 + cmp][p], hh), part);
                 part = warp_sum(part);
-                if (lane == 0) io.V[((size_t)i * io.n_l + h) * 3 + cmp] = part;
+                if (lane == 0) io.V[(size_t)i * nc_v_stride(io.n_l) + h * 3 + cmp] = part;
             }
         }
     }

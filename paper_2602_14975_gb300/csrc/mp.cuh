@@ -27,7 +27,7 @@ struct LayerIO {
     float *q;                // [N][(LMAX+1)C] (forward out, fp32)
     __nv_bfloat16 *q_bf16;   // optional split-bf16 copy of q, [N][2(LMAX+1)C] (forward out)
     const float *U;          // optional: tensor-head mix U[n_l][C] (NC embedding)
-    float *V;                // optional: V[N][n_l][3] = sum_c U[h][c] A[1+a][c]
+    float *V;                // optional: V[N][nc_v_stride(n_l)], V[i][3h + a] = sum_c U[h][c] A[1+a][c]
     int n_l;
     const float *gA;         // [N][NLM][C]  (backward in)
     const float *gs_in;      // [N][C]       (backward in)

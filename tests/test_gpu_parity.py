@@ -232,8 +232,10 @@ def test_nc_forces_fp32(ctx1, models1, water):
         Fo, neto = O.nc_forces(water, ns, nb_, with_bonds=with_bonds)
         assert rel_maxabs(F, Fo) <= TOL_F32
         assert np.abs(F.astype(np.float64).sum(0)).max() <= 1e-5 * np.abs(Fo).max()
-        # antisymmetric sum: the pre-subtraction net force is only rounding
-        assert np.abs(net.cpu().numpy()).max() <= 1e-4 * np.abs(Fo).max()
+        # antisymmetric sum (Sec. 2, the NC force sums to zero): each pair term,
+        # bond and repulsion enters its two atoms with opposite signs in exact
+        # fixed-point sums, so the pre-subtraction net force is exactly zero
+        assert np.array_equal(net.cpu().numpy(), np.zeros_like(net.cpu().numpy()))
 
 
 def test_nc_open_boundary_batch(ctx1, models1):
