@@ -597,6 +597,11 @@ void prepare_nbr_work_async(dmts_ctx *ctx, StateInternal *si, const SysView &v, 
     nw.gate = (int *)si->gate.p;
     nw.err = ctx->d_err;
     nw.box = v.box;
+    // sized when the state was set up (prepare_nbr_work)
+    nw.scan_status = (unsigned long long *)b.scan.p;
+    nw.scan_counter = (int *)(nw.scan_status + 2 * (size_t)b.scan_tiles);
+    nw.scan_tiles = b.scan_tiles;
+    nw.scan_epoch = &b.scan_epoch;
 }
 
 }  // namespace dmts
@@ -611,6 +616,23 @@ static bool host_copy_offsets(dmts_ctx *ctx, const dmts_system *sys, std::vector
            ck(ctx, cudaMemcpyAsync(box.data(), sys->box, sizeof(float) * box.size(), cudaMemcpyDeviceToHost, st),
               "box copy") &&
            ck(ctx, cudaStreamSynchronize(st), "offsets");
+}
+
+// Prefix-scan scratch for scans of up to n elements (status words and tile
+// counters, zero on allocation) and its fields of `nw`.
+static bool scan_scratch(dmts_ctx *ctx, NbrScratch &b, int n, NbrWork &nw, cudaStream_t st) {
+    const int tiles = scan_tiles_for(n);
+    if (tiles > b.scan_tiles) {
+        b.scan.release();
+        const size_t bytes = sizeof(unsigned long long) * 2 * (size_t)tiles + 2 * sizeof(int);
+        if (!b.scan.ensure(bytes) || !ck(ctx, cudaMemsetAsync(b.scan.p, 0, bytes, st), "scan scratch")) return false;
+        b.scan_tiles = tiles;
+    }
+    nw.scan_status = (unsigned long long *)b.scan.p;
+    nw.scan_counter = (int *)(nw.scan_status + 2 * (size_t)b.scan_tiles);
+    nw.scan_tiles = b.scan_tiles;
+    nw.scan_epoch = &b.scan_epoch;
+    return true;
 }
 
 // Builds the cell structure for `grids` into `nw` scratch owned by `bufs`.
@@ -643,6 +665,7 @@ static dmts_status prepare_nbr_work(dmts_ctx *ctx, NbrScratch &b, const SysView 
     nw.total = (long long *)b.total.p;
     nw.gate = gate;
     nw.err = ctx->d_err;
+    if (!scan_scratch(ctx, b, std::max(N, n_cells), nw, st)) return fail(ctx, DMTS_E_OOM, "scan scratch allocation failed");
     return DMTS_OK;
 }
 

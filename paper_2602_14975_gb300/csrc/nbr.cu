@@ -3,6 +3,7 @@
 // fewer, de-duplicated) neighbouring cells. Rows are sorted by neighbour
 // index, so their order is canonical and independent of scheduling.
 #include "nbr.cuh"
+#include "ptx.cuh"
 
 namespace dmts {
 
@@ -419,43 +420,122 @@ __global__ void __launch_bounds__(NB_WARPS * 32) k_nbr_fill_warp(NbrWork w, floa
     }
 }
 
-// Single-block exclusive scan (n up to a few million).
-__global__ void __launch_bounds__(1024) k_scan(const int *in, int n, int *out, long long capacity,
-                                               long long *total, int *err, const int *gate) {
+// ------------------------------------------------------------ prefix scan
+// Decoupled look-back: each block takes the next tile in order (a counter,
+// so that every tile's predecessors have started), sums its kScanTile
+// elements, publishes that sum, and walks back over its predecessors'
+// published words until one carries a full prefix; then it publishes its
+// own prefix and writes its outputs. A status word packs (launch tag, flag,
+// value): 28 bits of tag, 2 of flag (1 = tile sum, 2 = prefix), 34 of value,
+// so words left by earlier scans never look valid.
+constexpr int SCAN_THREADS = 256, SCAN_ITEMS = kScanTile / SCAN_THREADS;
+constexpr int kFlagSum = 1, kFlagPrefix = 2;
+
+__device__ __forceinline__ unsigned long long scan_word(unsigned tag, int flag, long long v) {
+    return ((unsigned long long)(tag & 0x0fffffffu) << 36) | ((unsigned long long)flag << 34) |
+           ((unsigned long long)v & 0x3ffffffffull);
+}
+
+struct ScanJob {
+    const int *in;
+    int *out;
+    long long cap;
+    long long *total;
+};
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan(ScanJob j0, ScanJob j1, int n, int n_tiles,
+                                                       unsigned long long *status_all, int *counters, int tiles_cap,
+                                                       unsigned tag, int *err, const int *gate) {
     if (gated_off(gate, err)) return;
-    __shared__ long long part[1024];
-    const int t = threadIdx.x;
-    const int chunk = (n + 1023) / 1024;
-    const int beg = min(t * chunk, n), end = min(beg + chunk, n);
-    long long s = 0;
-    for (int k = beg; k < end; ++k) s += in[k];
-    part[t] = s;
+    const ScanJob J = blockIdx.y ? j1 : j0;
+    unsigned long long *status = status_all + (size_t)blockIdx.y * tiles_cap;
+    int *counter = counters + blockIdx.y;
+    __shared__ int tile_sh;
+    __shared__ long long warp_tot[SCAN_THREADS / 32], excl_sh;
+    if (threadIdx.x == 0) {
+        const int t = atomicAdd(counter, 1);
+        if (t == n_tiles - 1) *counter = 0;   // every block has taken its tile: ready for the next scan
+        tile_sh = t;
+    }
     __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        long long v = t >= off ? part[t - off] : 0;
-        __syncthreads();
-        part[t] += v;
-        __syncthreads();
+    const int tile = tile_sh, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int first = tile * kScanTile + threadIdx.x * SCAN_ITEMS;
+    int v[SCAN_ITEMS];
+    long long s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        v[k] = first + k < n ? J.in[first + k] : 0;
+        s += v[k];
     }
-    long long run = part[t] - s;
-    const long long tot = part[1023];
-    const bool over = capacity >= 0 && tot > capacity;
-    if (!over) {
-        for (int k = beg; k < end; ++k) {
-            out[k] = (int)run;
-            run += in[k];
+    // block-wide inclusive scan of the per-thread sums
+    long long inc = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long t = __shfl_up_sync(DMTS_FULL, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) warp_tot[wid] = inc;
+    __syncthreads();
+    long long wbase = 0, agg = 0;
+#pragma unroll
+    for (int w = 0; w < SCAN_THREADS / 32; ++w) {
+        if (w < wid) wbase += warp_tot[w];
+        agg += warp_tot[w];
+    }
+    const long long mine = wbase + inc - s;   // exclusive prefix of this thread inside the tile
+    if (threadIdx.x == 0) {
+        long long excl = 0;
+        volatile unsigned long long *vs = status;
+        if (tile == 0) {
+            vs[0] = scan_word(tag, kFlagPrefix, agg);
+        } else {
+            vs[tile] = scan_word(tag, kFlagSum, agg);
+            const uint64_t t0 = globaltimer_ns();
+            for (int p = tile - 1; p >= 0;) {
+                const unsigned long long wd = vs[p];
+                const int flag = (int)((wd >> 34) & 3ull);
+                if ((unsigned)(wd >> 36) != (tag & 0x0fffffffu) || flag == 0) {
+                    if (globaltimer_ns() - t0 > kWaitLimitNs) {   // a predecessor never published
+                        set_error(err, DMTS_E_TIMEOUT);
+                        excl = -1;
+                        break;
+                    }
+                    continue;
+                }
+                excl += (long long)(wd & 0x3ffffffffull);
+                if (flag == kFlagPrefix) break;
+                --p;
+            }
+            if (excl >= 0) vs[tile] = scan_word(tag, kFlagPrefix, excl + agg);
         }
-        if (t == 1023) out[n] = (int)tot;
+        excl_sh = excl;
     }
-    if (t == 0) {
-        if (total) *total = tot;
-        if (over) set_error(err, DMTS_E_NBR_OVERFLOW);
+    __syncthreads();
+    const long long excl = excl_sh;
+    if (excl < 0) return;
+    long long run = excl + mine;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        if (first + k < n) J.out[first + k] = (int)run;
+        run += v[k];
+    }
+    if (tile == n_tiles - 1 && threadIdx.x == 0) {
+        const long long tot = excl + agg;
+        J.out[n] = (int)tot;
+        if (J.total) *J.total = tot;
+        if ((J.cap >= 0 && tot > J.cap) || tot > 0x7fffffffLL) set_error(err, DMTS_E_NBR_OVERFLOW);
     }
 }
 
-void scan_ints(const int *in, int n, int *out, long long capacity, long long *total, int *err,
-               const int *gate, cudaStream_t st) {
-    k_scan<<<1, 1024, 0, st>>>(in, n, out, capacity, total, err, gate);
+void scan_ints(const NbrWork &w, const int *in0, int *out0, long long cap0, long long *total0, const int *in1,
+               int *out1, long long cap1, long long *total1, int n, cudaStream_t st) {
+    const int tiles = (n + kScanTile - 1) / kScanTile;
+    const int n_tiles = tiles > 0 ? tiles : 1;
+    unsigned tag = ++*w.scan_epoch & 0x0fffffffu;
+    if (tag == 0) tag = *w.scan_epoch = 1;   // zeroed words carry tag 0
+    dim3 grid(n_tiles, in1 ? 2 : 1);
+    k_scan<<<grid, SCAN_THREADS, 0, st>>>(ScanJob{in0, out0, cap0, total0}, ScanJob{in1, out1, cap1, total1}, n,
+                                          n_tiles, w.scan_status, w.scan_counter, w.scan_tiles, tag, w.err, w.gate);
     count_launch();
 }
 
@@ -466,7 +546,7 @@ void nbr_cells(const NbrWork &w, float r_list, cudaStream_t st) {
     const int nb = (w.n_atoms + 255) / 256;
     k_cell_assign<<<nb, 256, 0, st>>>(w);
     count_launch();
-    scan_ints(w.cell_cnt, w.n_cells, w.cell_start, -1, nullptr, w.err, w.gate, st);
+    scan_ints(w, w.cell_cnt, w.cell_start, -1, nullptr, nullptr, nullptr, -1, nullptr, w.n_cells, st);
     k_cell_scatter<<<nb, 256, 0, st>>>(w);
     count_launch();
 }
@@ -479,8 +559,9 @@ void nbr_fill(const NbrWork &w, float r_list, int *row_ptr, int *col, long long 
     if (!sub_row) wc.counts_sub = nullptr;
     k_nbr_count_warp<<<nb, NB_WARPS * 32, 0, st>>>(wc, r_list * r_list, r_sub * r_sub);
     count_launch();
-    scan_ints(wc.counts, wc.n_atoms, row_ptr, capacity, wc.total, wc.err, wc.gate, st);
-    if (wc.counts_sub) scan_ints(wc.counts_sub, wc.n_atoms, sub_row, sub_capacity, wc.total, wc.err, wc.gate, st);
+    // the full list's and the sub-list's row offsets in one launch
+    scan_ints(wc, wc.counts, row_ptr, capacity, wc.total, wc.counts_sub, wc.counts_sub ? sub_row : nullptr,
+              sub_capacity, nullptr, wc.n_atoms, st);
     if (col) {
         k_nbr_fill_warp<<<nb, NB_WARPS * 32, 0, st>>>(wc, r_list * r_list, row_ptr, col, x_ref, r_sub * r_sub,
                                                       wc.counts_sub ? sub_row : nullptr,

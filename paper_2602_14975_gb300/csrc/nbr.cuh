@@ -38,7 +38,19 @@ struct NbrWork {
     int slot_cap = 0;
     const float *box = nullptr;  // [n_rep][3] (nullable): current boxes; periodic grids follow them at each
                                  // rebuild (a barostat moves the box)
+    // prefix-scan state: per job [scan_tiles] tile status words and a tile
+    // counter (zero between scans), and the host-side launch counter whose
+    // value tags this scan's status words
+    unsigned long long *scan_status = nullptr;   // [2][scan_tiles]
+    int *scan_counter = nullptr;                 // [2]
+    int scan_tiles = 0;
+    unsigned *scan_epoch = nullptr;              // host
 };
+
+// Tiles of the prefix scan (elements per tile) and the tiles a scan of n
+// elements needs.
+constexpr int kScanTile = 2048;
+inline int scan_tiles_for(int n) { return (n + kScanTile - 1) / kScanTile + 1; }
 
 // Builds the cell structure (assign, count, scan, scatter, sort).
 void nbr_cells(const NbrWork &w, float r_list, cudaStream_t st);
@@ -51,9 +63,12 @@ void nbr_fill(const NbrWork &w, float r_list, int *row_ptr, int *col, long long 
               long long sub_capacity = -1);
 // Atom -> replica map.
 void atom_rep_map(const int *rep_off, int n_rep, int n_atoms, int *atom_rep, cudaStream_t st);
-// Exclusive scan of n ints into out[n+1]; if capacity >= 0 and the total
-// exceeds it, set the overflow error. total (nullable) receives the sum.
-void scan_ints(const int *in, int n, int *out, long long capacity, long long *total, int *err,
-               const int *gate, cudaStream_t st);
+// Exclusive scans of n ints into out[n+1], one or two arrays in one launch
+// (in1 nullable); if capacity >= 0 and a total exceeds it, set the overflow
+// error; total (nullable) receives the sum. Single pass over the whole grid:
+// tiles of kScanTile elements publish their sums and look back at their
+// predecessors' (decoupled look-back), every wait bounded.
+void scan_ints(const NbrWork &w, const int *in0, int *out0, long long cap0, long long *total0, const int *in1,
+               int *out1, long long cap1, long long *total1, int n, cudaStream_t st);
 
 }  // namespace dmts
