@@ -680,6 +680,7 @@ void free_state_internal(StateInternal *si) {
     si->atom_rep.release();
     si->ms_part.release();
     si->baro_ke.release();
+    si->thermo_part.release();
     si->baro_K.release();
     si->baro_f.release();
     si->scratch.release_all();
@@ -1164,6 +1165,9 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
         return fail(ctx, DMTS_E_INVALID, "state shape changed; release the state first");
     if (npt && si->grid_margin < kBaroGridMargin)
         return fail(ctx, DMTS_E_INVALID, "state built without the barostat's cell margin; release it first");
+    if ((stt->thermo || stt->thermo_trace) &&
+        !si->thermo_part.ensure(thermo_scratch_bytes(stt->sys.n_atoms, stt->sys.n_replicas)))
+        return fail(ctx, DMTS_E_OOM, "thermo workspace allocation failed");
     if (npt && (!si->baro_ke.ensure(sizeof(float) * (stt->sys.n_atoms + 1)) ||
                 !si->baro_K.ensure(sizeof(double) * stt->sys.n_replicas) ||
                 !si->baro_f.ensure(sizeof(float) * 3 * stt->sys.n_replicas)))
@@ -1258,6 +1262,9 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
     ta.h_out = ia.h_out;
     ta.energy = stt->energy;
     ta.out = stt->thermo;
+    ta.part_off = v.ms_part_off;
+    ta.partial = (double *)si->thermo_part.p;
+    ta.n_rep = v.n_rep;
     auto thermo = [&](bool pending, double *trace_row) {
         ThermoArgs t = ta;
         t.close_b = pending;
@@ -1268,7 +1275,7 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
             t.fast_sum = (const unsigned long long *)ctx->ws.nc_sum.p;
         }
         ProfScope ps(ctx, "thermo", st);
-        launch_thermo(t, v.n_rep, st);
+        launch_thermo(t, v.n, v.n_rep, st);
     };
     BaroArgs ba;
     memset(&ba, 0, sizeof ba);

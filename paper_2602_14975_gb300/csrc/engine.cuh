@@ -101,6 +101,7 @@ struct StateInternal {
     std::vector<CellGrid> grids;
     Buf cons_row, cons_col, nc_row, nc_col, x_ref, gate, atom_rep, ms_part;
     Buf baro_ke, baro_K, baro_f;   // barostat: per-atom kinetic energy, per-replica sum, drift factors
+    Buf thermo_part;               // per-part FP64 kinetic-energy sums
     long long cons_cap = 0, nc_cap = 0;
     NbrScratch scratch;
 };

@@ -1198,20 +1198,20 @@ void launch_integrate(const IntegArgs &a, cudaStream_t st) {
 }
 
 // ------------------------------------------------------- thermodynamics
-// One block per replica: K = sum_i m_i |v_i|^2 / 2 with every per-atom term
-// formed in FP64 from the fp32 state and summed in FP64 in a fixed order
-// (a strided partial per thread, then a fixed tree), so the result does not
-// depend on the batch the replica is in. The velocities are first closed
-// with the step's pending kicks (ThermoArgs), in the integrator's own
-// arithmetic. Writes (K, U + K, 2K / (3 n_r kB)) per replica.
-constexpr int kThermoThreads = 512;
-
-__global__ void __launch_bounds__(kThermoThreads) k_thermo(ThermoArgs g) {
-    __shared__ double red[kThermoThreads / 32];
-    const int r = blockIdx.x;
-    const int beg = g.rep_off[r], end = g.rep_off[r + 1];
+// K = sum_i m_i |v_i|^2 / 2 per replica with every per-atom term formed in
+// FP64 from the fp32 state, summed in FP64 in a fixed order over the
+// replica-local parts of MS_PART atoms (the same parts as the mean
+// subtraction), so the result does not depend on the batch the replica is
+// in; the velocities are first closed with the step's pending kicks
+// (ThermoArgs), in the integrator's own arithmetic. One block per part, then
+// one thread per replica adds its parts in order and writes
+// (K, U + K, 2K / (3 n_r kB)).
+__global__ void __launch_bounds__(MS_THREADS) k_thermo_part(ThermoArgs g) {
+    int r, p;
+    if (!mean_part_of(g.part_off, g.n_rep, blockIdx.x, r, p)) return;
+    const int lo = g.rep_off[r] + p * MS_PART, hi = min(g.rep_off[r + 1], lo + MS_PART);
     double acc = 0.0;
-    for (int i = beg + threadIdx.x; i < end; i += kThermoThreads) {
+    for (int i = lo + threadIdx.x; i < hi; i += MS_THREADS) {
         const float am = kAccConv / g.masses[i];
         float vx = g.v[3 * i], vy = g.v[3 * i + 1], vz = g.v[3 * i + 2];
         if (g.close_b || g.kick_l) {
@@ -1228,30 +1228,44 @@ __global__ void __launch_bounds__(kThermoThreads) k_thermo(ThermoArgs g) {
         const double dx = vx, dy = vy, dz = vz;
         acc += 0.5 * (double)g.masses[i] * (dx * dx + dy * dy + dz * dz);
     }
+    __shared__ double red[MS_THREADS / 32];
     acc = warp_sum_d(acc);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
-    if (threadIdx.x < 32) {
-        double t = threadIdx.x < kThermoThreads / 32 ? red[threadIdx.x] : 0.0;
-        t = warp_sum_d(t);
-        if (threadIdx.x == 0) {
-            const double K = t / kAccConvD;   // amu A^2/fs^2 -> kcal/mol
-            const int n = end - beg;
-            const double T = n > 0 ? 2.0 * K / (3.0 * n * kBoltzmann) : 0.0;
-            const double U = g.energy[r];
-            double *o = g.out + 3 * (size_t)r;
-            o[0] = K; o[1] = U + K; o[2] = T;
-            if (g.trace) {
-                double *q = g.trace + 3 * (size_t)r;
-                q[0] = K; q[1] = U + K; q[2] = T;
-            }
-        }
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < MS_THREADS / 32; ++w) t += red[w];
+        g.partial[blockIdx.x] = t;
     }
 }
 
-void launch_thermo(const ThermoArgs &a, int n_rep, cudaStream_t st) {
+__global__ void k_thermo_final(ThermoArgs g) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= g.n_rep) return;
+    double t = 0.0;
+    for (int q = g.part_off[r]; q < g.part_off[r + 1]; ++q) t += g.partial[q];
+    const double K = t / kAccConvD;   // amu A^2/fs^2 -> kcal/mol
+    const int n = g.rep_off[r + 1] - g.rep_off[r];
+    const double T = n > 0 ? 2.0 * K / (3.0 * n * kBoltzmann) : 0.0;
+    const double U = g.energy[r];
+    double *o = g.out + 3 * (size_t)r;
+    o[0] = K; o[1] = U + K; o[2] = T;
+    if (g.trace) {
+        double *q = g.trace + 3 * (size_t)r;
+        q[0] = K; q[1] = U + K; q[2] = T;
+    }
+}
+
+size_t thermo_scratch_bytes(int n_atoms, int n_rep) {
+    return sizeof(double) * ((size_t)(n_atoms + MS_PART - 1) / MS_PART + (size_t)n_rep);
+}
+
+void launch_thermo(const ThermoArgs &a, int n_atoms, int n_rep, cudaStream_t st) {
     if (n_rep == 0) return;
-    k_thermo<<<n_rep, kThermoThreads, 0, st>>>(a);
+    const int parts = (n_atoms + MS_PART - 1) / MS_PART + n_rep;   // bound on the parts of all replicas
+    k_thermo_part<<<parts, MS_THREADS, 0, st>>>(a);
+    count_launch();
+    k_thermo_final<<<(n_rep + 127) / 128, 128, 0, st>>>(a);
     count_launch();
 }
 

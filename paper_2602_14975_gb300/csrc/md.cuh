@@ -184,8 +184,12 @@ struct ThermoArgs {
     const double *energy;          // [R] potential energy U at the same configuration
     double *out;                   // [R][3]: K, U + K, T
     double *trace;                 // nullable: [R][3] copy (one row of a per-outer-step trace)
+    const int *part_off;           // [R+1] replica-local parts (launch_mean_part_off)
+    double *partial;               // scratch of thermo_scratch_bytes(n_atoms, n_rep) bytes
+    int n_rep;
 };
-void launch_thermo(const ThermoArgs &a, int n_rep, cudaStream_t st);
+size_t thermo_scratch_bytes(int n_atoms, int n_rep);
+void launch_thermo(const ThermoArgs &a, int n_atoms, int n_rep, cudaStream_t st);
 
 // Barostat of the outer step (piston on epsilon = ln(V)/3; see dmts_integrator).
 struct BaroArgs {
