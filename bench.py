@@ -108,6 +108,9 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--detail", default="", help="also write every leg's figures to this JSON file")
+    ap.add_argument("--next3", action="store_true",
+                    help="the distillation study on the 12,288-atom water box instead (NEXT-3): held-out |F_L| "
+                         "before and after, and DMTS-NC kinetic temperatures against (T/d) chi^2(d)")
     ap.add_argument("--main-only", action="store_true",
                     help="only the timed DMTS-NC leg (for profiler captures); prints its time and kernel shares")
     return ap.parse_args()
@@ -325,6 +328,87 @@ def serving_tail(tick_ms, tick_atoms):
             "atoms_p50": float(np.percentile(n, 50)), "atoms_max": float(n.max())}
 
 
+# ----------------------------------------------------------------- NEXT-3 --
+def next3_study(core, S, D, rank):
+    """Distillation of the NC model (Sec. 2, "Model training") on frames of a
+    single-time-step run of the 12,288-atom water box with the conservative
+    model (20 training frames and 4 held out, 50 fs apart), 2,000 Adam steps
+    on all frames at once with a cosine learning rate from 2e-3; then
+    DMTS-NC at Delta = 10 fs with the distilled model for n = 5, 10, 20 inner
+    steps: kinetic temperatures every 0.5 ps after 5 ps against
+    (T/d) chi^2(d), d = 3N (Sec. 3), and the largest |F - F_S| the rewind
+    guard sees with the random and the distilled NC model."""
+    from scipy import stats
+    import torch
+    W = S.WORKLOADS["water_12288"]
+    sy = W["system"]()
+    cs, ns = W["cons"](), W["nc"]()
+    cb, nb = S.cons_weights(cs, W["w_seed"]), S.nc_weights(ns, W["w_seed"])
+    ctx = core.Context(cons=(cs, cb), nc=(ns, nb))
+    ctx0 = core.Context(cons=(cs, cb), nc=(ns, nb))
+    I = W["dmts"]
+    m_el = sy.element_masses()
+    d = core.DeviceSystem(sy)
+    st = core.MDState(d, S.maxwell_boltzmann(m_el, 300.0, 7), m_el.astype(np.float32), seeds=11)
+    ig = core.integrator(1.0, 1, 300.0, (1.0,) * 5, mode=core.L.MODE_STS, skin=0.5)
+    core.respa_step(ctx, st, ig, 200)
+    frames = []
+    for _ in range(24):
+        core.respa_step(ctx, st, ig, 50)
+        frames.append(d.x.cpu().numpy().astype(np.float64))
+    st.release()
+
+    def batch(xs):
+        db = core.DeviceSystem([S.System(sy.name, x, sy.species, sy.mol_id, sy.bonds, sy.bond_r0, sy.box)
+                                for x in xs])
+        _, T = core.energy_forces_cons(ctx, db, core.nbr_build(ctx, db, cs.rc + 0.5), with_prior=True)
+        return db, core.nbr_build(ctx, db, ns.rc + 0.5), T
+
+    train, hold = batch(frames[:20]), batch(frames[20:])
+
+    def rms(b):
+        loss, _ = core.nc_distill_step(ctx, b[0], b[1], b[2], lr=0.0)
+        return math.sqrt(loss.sum().item() / (3 * b[0].n_atoms))
+
+    r0 = (rms(train), rms(hold))
+    n_steps = 2000
+    t0 = time.perf_counter()
+    for k in range(n_steps):
+        lr = 2e-3 * 0.5 * (1.0 + math.cos(math.pi * k / n_steps))
+        core.nc_distill_step(ctx, train[0], train[1], train[2], lr=lr, step=k + 1)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    r1 = (rms(train), rms(hold))
+    m = core.masses_hmr(sy.species, sy.mol_id, sy.element_masses(), I.hmr_delta)
+    dof = 3 * sy.n_atoms
+    runs = []
+    for n_in in (5, 10, 20):
+        dd = core.DeviceSystem(sy)
+        s2 = core.MDState(dd, S.maxwell_boltzmann(m, 300.0, 9), m.astype(np.float32), seeds=13, thermo=True)
+        ii = core.integrator(I.dt_outer, n_in, I.temperature, I.gamma_ps, skin=0.5)
+        Ts = []
+        for _ in range(60):
+            core.respa_step(ctx, s2, ii, 50)
+            Ts.append(float(s2.thermo.cpu().numpy()[0, 2]))
+        s2.release()
+        T = np.array(Ts[10:])
+        runs.append({"n_inner": n_in, "delta_fs": I.dt_outer / n_in, "T_mean": float(T.mean()),
+                     "T_std": float(T.std()), "T_std_chi2": 300.0 * math.sqrt(2.0 / dof), "samples": int(T.size),
+                     "ks_p": float(stats.kstest(T * dof / 300.0, stats.chi2(dof).cdf).pvalue)})
+    guard = {}
+    for label, cx in (("random", ctx0), ("distilled", ctx)):
+        dg = core.DeviceSystem(sy)
+        sg = core.MDState(dg, S.maxwell_boltzmann(m, 300.0, 9), m.astype(np.float32), seeds=13)
+        gs = core.respa_guarded(cx, sg, core.integrator(I.dt_outer, I.n_inner, I.temperature, I.gamma_ps, skin=0.5),
+                                200, math.inf, 50, 4 * I.n_inner, I.dt_outer / I.n_inner)
+        guard[label] = float(np.max(gs["chunk_max"]))
+        sg.release()
+    return {"study": "NEXT-3 distillation", "workload": sy.name, "train_frames": 20, "held_out_frames": 4,
+            "adam_steps": n_steps, "train_s": t_train, "f_l_rms_train": [r0[0], r1[0]],
+            "f_l_rms_held_out": [r0[1], r1[1]], "unit": "kcal/mol/A", "temperatures": runs,
+            "max_force_disagreement_200_outer_steps": guard}
+
+
 # ------------------------------------------------------------------ main --
 def reference_arm(args, W, I):
     """The FP64 oracle, as it stands, on the host cores: every step times one
@@ -394,6 +478,11 @@ def main():
     D.init("nccl", torch.device(f"cuda:{local}"))
     from paper_2602_14975_gb300 import core
 
+    if args.next3:
+        out = next3_study(core, S, D, rank)
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        return 0
     dev = torch.device(f"cuda:{local}")
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
