@@ -808,6 +808,9 @@ void dmts_destroy(dmts_ctx *ctx) {
     if (ctx->cons.dev_bf) cudaFree(ctx->cons.dev_bf);
     if (ctx->nc.dev_bf) cudaFree(ctx->nc.dev_bf);
     if (ctx->d_err) cudaFree(ctx->d_err);
+    if (ctx->aux) cudaStreamDestroy(ctx->aux);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     ctx->ws.release_all();
     ctx->nbr_scratch.release_all();
     ctx->prof.release();
@@ -1191,13 +1194,24 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
     // force and the replica means and stores the subtracted force in
     // stt->f_nc: one launch and one pass over the forces less per inner step.
     bool mean_pending = false;
-    auto nc_fast = [&](bool with_virial) {
+    auto nc_fast_on = [&](bool with_virial, cudaStream_t s_nc) {
         const dmts_status r = nc_eval(ctx, v, nrow, ncol, stt->f_nc, nullptr, DMTS_WITH_BONDS | nc_emb | kFlagDeferMean,
-                                      st, with_virial ? stt->virial_nc : nullptr, 1);
+                                      s_nc, with_virial ? stt->virial_nc : nullptr, 1);
         nc_emb = kFlagEmbedded;
         mean_pending = true;
         return r;
     };
+    auto nc_fast = [&](bool with_virial) { return nc_fast_on(with_virial, st); };
+    // the last NC evaluation of an outer step and the conservative one are
+    // both at the step's final positions and share no buffer: the first runs
+    // on the context's second stream, forked after the list rebuild and
+    // joined before the next integrator launch
+    const bool overlap = !sts;
+    if (overlap && !ctx->aux &&
+        (!ck(ctx, cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking), "second stream") ||
+         !ck(ctx, cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming), "fork event") ||
+         !ck(ctx, cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming), "join event")))
+        return DMTS_E_CUDA;
     auto integrate = [&](IntegArgs a) {
         if (mean_pending) {
             a.fast_pre = (const float *)ctx->ws.nc_f.p;
@@ -1332,17 +1346,30 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
             { ProfScope ps(ctx, "integrate", st); integrate(ia); }
             rebuild_lists(ctx, si, v, st);
             if (!sts) {
-                s = nc_fast(stt->virial_nc != nullptr);
+                const bool last = k == n_in - 1;
+                cudaStream_t s_nc = st;
+                if (last && overlap) {
+                    s_nc = ctx->aux;
+                    if (!ck(ctx, cudaEventRecord(ctx->ev_fork, st), "fork") ||
+                        !ck(ctx, cudaStreamWaitEvent(s_nc, ctx->ev_fork, 0), "fork"))
+                        return DMTS_E_CUDA;
+                }
+                s = nc_fast_on(stt->virial_nc != nullptr, s_nc);
                 if (s != DMTS_OK) return s;
-                // the fast force's virial at the end of the outer step, for the estimator
-                if (stt->virial_est && k == n_in - 1)
-                    launch_replica_sum((const float *)ctx->ws.nc_w.p, v.rep_off, v.n_rep, (double *)ctx->ws.nc_w_last.p,
-                                       0, st);
+                if (last) {
+                    // the fast force's virial at the end of the outer step, for
+                    // the estimator, and its average over the inner steps
+                    if (stt->virial_est)
+                        launch_replica_sum((const float *)ctx->ws.nc_w.p, v.rep_off, v.n_rep,
+                                           (double *)ctx->ws.nc_w_last.p, 0, s_nc);
+                    if (stt->virial_nc) launch_scale_d(stt->virial_nc, v.n_rep, 1.0 / n_in, s_nc);
+                    if (overlap && !ck(ctx, cudaEventRecord(ctx->ev_join, s_nc), "join")) return DMTS_E_CUDA;
+                }
             }
         }
-        if (!sts && stt->virial_nc) launch_scale_d(stt->virial_nc, v.n_rep, 1.0 / n_in, st);
         s = cons_full();
         if (s != DMTS_OK) return s;
+        if (overlap && !ck(ctx, cudaStreamWaitEvent(st, ctx->ev_join, 0), "join")) return DMTS_E_CUDA;
         if (stt->virial_est) {
             if (sts) {
                 if (!ck(ctx, cudaMemcpyAsync(stt->virial_est, stt->virial_cons, sizeof(double) * v.n_rep,

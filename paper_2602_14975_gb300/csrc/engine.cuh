@@ -154,6 +154,11 @@ struct dmts_ctx {
     dmts::Workspace ws;
     dmts::NbrScratch nbr_scratch;
     dmts::Profiler prof;
+    // second stream of respa_step: the NC evaluation at the end of an outer
+    // step runs on it, concurrently with the conservative evaluation at the
+    // same positions (created on first use)
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace dmts {
