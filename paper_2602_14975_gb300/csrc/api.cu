@@ -297,7 +297,7 @@ dmts_status cons_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const
         Epi e1 = epi(EPI_BIAS_SILU);
         e1.bias = m.b1[t];
         e1.H = H + nc_ * t;
-        e1.out = act;
+        e1.out = bf ? nullptr : act;            // the tensor-core path reads only the split-bf16 copy
         e1.out_bf16 = act_bf;
         if (!contract(ctx, m, N, C, NL * C, q, q_bf, m.w1[t], 1, m.w1_bf[t], e1, st, "gemm_tc", "gemm"))
             return DMTS_E_CUDA;
@@ -433,7 +433,9 @@ dmts_status nc_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const i
     Epi e1 = epi(EPI_BIAS_SILU);
     e1.bias = m.b1[0];
     e1.H = (flags & kFlagKeepPre) ? (float *)w.dist_h.p : nullptr;   // kept only for the distillation
-    e1.out = (float *)w.nc_act.p;
+    // the tensor-core path reads only the split-bf16 copy; the distillation's
+    // weight gradient reads the fp32 activation
+    e1.out = (bf && !(flags & kFlagKeepPre)) ? nullptr : (float *)w.nc_act.p;
     e1.out_bf16 = act_bf;
     if (!contract(ctx, m, N, C, 2 * C, io.q, q_bf, m.w1[0], 1, m.w1_bf[0], e1, st, "nc_gemm_tc", "nc_gemm"))
         return DMTS_E_CUDA;

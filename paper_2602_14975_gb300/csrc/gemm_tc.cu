@@ -132,7 +132,7 @@ __device__ __forceinline__ void epilogue_tile(const Epi &e, int N, int rows, int
                     const float h = v[u] + b[u];
                     const float sv = silu_d(h);
                     if (e.H) e.H[o[u]] = h;
-                    e.out[o[u]] = sv;
+                    if (e.out) e.out[o[u]] = sv;
                     if (e.out_bf16) st_split(e.out_bf16, (size_t)(m0 + r_[u]), N, n[u], sv);
                 }
             break;
@@ -280,7 +280,7 @@ __device__ __forceinline__ void epilogue_tile_v4(const Epi &e, int N, int rows, 
                     const float4 h = make_float4(v[u].x + b.x, v[u].y + b.y, v[u].z + b.z, v[u].w + b.w);
                     const float4 sv = silu4(h);
                     if (e.H) st4(e.H + o, h);
-                    st4(e.out + o, sv);
+                    if (e.out) st4(e.out + o, sv);
                     if (e.out_bf16) st4_split(e.out_bf16 + (size_t)(m0 + rr[u]) * 2 * N + n0 + 4 * cc[u], N, sv);
                 }
             break;

@@ -314,15 +314,14 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
                 if (h < H) {
                     const float4 *qj4 = reinterpret_cast<const float4 *>(row + h * NC);
                     const float4 *kj4 = reinterpret_cast<const float4 *>(row + (H + h) * NC);
-                    const float *qah = qa + h * NC, *kah = ka + h * NC;
+                    const float4 *qa4 = reinterpret_cast<const float4 *>(qa + h * NC);
+                    const float4 *ka4 = reinterpret_cast<const float4 *>(ka + h * NC);
                     float caj = 0.f, cja = 0.f;
 #pragma unroll
                     for (int q = 0; q < NC / 4; ++q) {
-                        const float4 kj = kj4[q], qj = qj4[q];
-                        caj = fmaf(qah[4 * q], kj.x, fmaf(qah[4 * q + 1], kj.y,
-                                   fmaf(qah[4 * q + 2], kj.z, fmaf(qah[4 * q + 3], kj.w, caj))));
-                        cja = fmaf(qj.x, kah[4 * q], fmaf(qj.y, kah[4 * q + 1],
-                                   fmaf(qj.z, kah[4 * q + 2], fmaf(qj.w, kah[4 * q + 3], cja))));
+                        const float4 kj = kj4[q], qj = qj4[q], qi = qa4[q], ki = ka4[q];
+                        caj = fmaf(qi.x, kj.x, fmaf(qi.y, kj.y, fmaf(qi.z, kj.z, fmaf(qi.w, kj.w, caj))));
+                        cja = fmaf(qj.x, ki.x, fmaf(qj.y, ki.y, fmaf(qj.z, ki.z, fmaf(qj.w, ki.w, cja))));
                     }
                     caj *= isnc;
                     cja *= isnc;

@@ -500,7 +500,7 @@ __device__ __forceinline__ void epilogue(const Epi &e, int N, int m, int n, floa
         const float h = v + e.bias[n];
         if (e.H) e.H[o] = h;
         const float s = silu_f(h);
-        e.out[o] = s;
+        if (e.out) e.out[o] = s;
         if (e.out_bf16) st_split(e.out_bf16, m, N, n, s);
         break;
     }

@@ -75,7 +75,7 @@ void launch_mp_bwd(int C, int lmax, int K, const EdgeGeom &g, const LayerIO &io,
 // ---------------------------------------------------------------- GEMM ----
 enum EpiMode {
     EPI_STORE = 0,           // out = v
-    EPI_BIAS_SILU = 1,       // H = v + bias; out = silu(H) (and H stored)
+    EPI_BIAS_SILU = 1,       // H = v + bias; out = silu(H) (out, H and the bf16 copy each nullable)
     EPI_RESID = 2,           // out = res + v + bias
     EPI_DSILU = 3,           // out = v * dsilu(H)
     EPI_GA = 4,              // gA[m][lm][c] = 2 A[m][lm][c] v,  n = l*C + c
