@@ -41,7 +41,7 @@ PROF_EVERY = 4   # time every 4th outer step of the timed region per kernel
 KCAL_A3_PER_ATM = 101325.0 * 6.02214076e23 * 1e-30 / 4184.0   # 1 atm in kcal/mol/A^3
 
 NCU_TRAFFIC = {
-    "mp_bwd": {"bytes_per_launch": (153792768 + 14773248 + 154217472 + 12226560 + 141881088 + 280320) / 3,
+    "mp_bwd": {"bytes_per_launch": (153862400 + 19086848 + 154141440 + 16657920 + 141894656 + 361984) / 3,
                # the adjoint's code: channel-pack helpers, kernel and launch, the
                # argument structs, the device helpers
                "sources": [("paper_2602_14975_gb300/csrc/mp.cu", ("// ---- channel packs", "// ---- forward")),
@@ -50,7 +50,7 @@ NCU_TRAFFIC = {
                                                                   "#define DMTS_DISPATCH")),
                            ("paper_2602_14975_gb300/csrc/mp.cuh", ("struct EdgeGeom {", "template <int CPW>")),
                            ("paper_2602_14975_gb300/csrc/common.cuh", None)],
-               "sha256": "3796c7e6556c549033dba13f00650618a0defe87a98c4c586074b1306b886a7e"},
+               "sha256": "c0cc6635d43ad41fdb3a0c50bb9e55ecb557943723cd345cb8c5ea0fd0554de2"},
 }
 
 
