@@ -261,7 +261,8 @@ def oracle_outer_step_seconds(sy, W, frac_edge):
 def workload_config(sy, I, cs, ns):
     """The `config` of the JSON line (the same for both arms)."""
     return {"workload": sy.name, "n_atoms": sy.n_atoms,
-            "integrator": f"DMTS-NC outer {I.dt_outer} fs / {I.n_inner} inner, HMR +{I.hmr_delta} amu on H, "
+            "integrator": f"DMTS-NC outer {I.dt_outer} fs / {I.n_inner} inner, HMR +{I.hmr_delta} Da on H "
+                          f"(the paper's HMR; the configurations' 'H mass 3 amu' read as this), "
                           f"gamma_H {I.gamma_ps[0]}/ps, gamma_heavy {I.gamma_ps[1]}/ps",
             "cons_model": f"L={cs.L} C={cs.C} lmax={cs.lmax} K={cs.K} rc={cs.rc}",
             "nc_model": f"C={ns.C} lmax=1 rc={ns.rc} n_c={ns.n_c} n_l={ns.n_l}",
@@ -891,7 +892,8 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_dmts, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16" if cs.bf16 else "f32", "data": "synthetic",
         "config": {"workload": sy.name, "n_atoms": sy.n_atoms,
-                   "integrator": f"DMTS-NC {I.dt_outer} fs / {I.n_inner} inner, HMR, HHF",
+                   "integrator": f"DMTS-NC {I.dt_outer} fs / {I.n_inner} inner, HMR +{I.hmr_delta} Da on H "
+                                 f"(the paper's HMR), HHF",
                    "precision": "split-bf16 tcgen05 MLPs, fp32 elsewhere, fp64 sums" if cs.bf16 else "fp32",
                    "l2": "inputs larger than L2", "parallelism": "replicas only"},
         "speedup_vs_sts": val / sts_val,
