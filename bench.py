@@ -266,7 +266,7 @@ def workload_config(sy, I, cs, ns):
                           f"gamma_H {I.gamma_ps[0]}/ps, gamma_heavy {I.gamma_ps[1]}/ps",
             "cons_model": f"L={cs.L} C={cs.C} lmax={cs.lmax} K={cs.K} rc={cs.rc}",
             "nc_model": f"C={ns.C} lmax=1 rc={ns.rc} n_c={ns.n_c} n_l={ns.n_l}",
-            "precision": ("bf16 MLP contractions on the tensor cores (tcgen05, fp32 accumulate), "
+            "precision": ("split-bf16 MLP contractions on the tensor cores (tcgen05, fp32 accumulate), "
                           "fp32 everywhere else, fp64 per-replica sums") if cs.bf16 else "fp32",
             "l2": "inputs larger than L2: about 0.5 GB of node and edge data per outer step",
             "parallelism": "replicas only (one replica per GPU)"}
