@@ -298,16 +298,13 @@ __device__ __forceinline__ void rank_scatter(const int *sb, int cnt, int *dst, i
 
 // Row lengths (and sub-list row lengths). With w.slots the sorted row, sub
 // entries flagged, is also kept for the fill, which then only copies it.
-__global__ void __launch_bounds__(NB_WARPS * 32) k_nbr_count_warp(NbrWork w, float rc2, float rc2_sub) {
-    if (gated_off(w.gate, w.err)) return;
-    __shared__ int buf[NB_WARPS][NB_MAXROW];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int i = blockIdx.x * NB_WARPS + warp;
-    if (i >= w.n_atoms) return;
-    int *sb = buf[warp];
-    const bool keep = w.slots != nullptr;
+// RowAcc collects one atom's hits (warp-cooperative) and writes its counts
+// and kept row.
+struct RowAcc {
+    int *sb;
     int cnt = 0, cnt_sub = 0;
-    for_candidates_warp(w, i, rc2, lane, [&](bool hit, int j, float r2) {
+    __device__ __forceinline__ void add(const NbrWork &w, bool keep, bool hit, int j, float r2, float rc2_sub,
+                                        int lane) {
         const bool sub = hit && r2 < rc2_sub;
         const unsigned m = __ballot_sync(DMTS_FULL, hit);
         if (keep && hit) {
@@ -316,20 +313,144 @@ __global__ void __launch_bounds__(NB_WARPS * 32) k_nbr_count_warp(NbrWork w, flo
         }
         cnt += __popc(m);
         if (w.counts_sub) cnt_sub += __popc(__ballot_sync(DMTS_FULL, sub));
-    });
-    if (lane == 0) {
-        w.counts[i] = cnt;
-        if (w.counts_sub) w.counts_sub[i] = cnt_sub;
     }
-    if (keep && cnt <= w.slot_cap && cnt <= NB_MAXROW) {
-        __syncwarp();
-        int *dst = w.slots + (size_t)i * w.slot_cap;
-        if (cnt <= 128) {
-            rank_scatter(sb, cnt, dst, lane);
-        } else {
-            sort_row(sb, cnt, lane);
-            for (int t = lane; t < cnt; t += 32) dst[t] = sb[t];
+    __device__ __forceinline__ void finish(const NbrWork &w, bool keep, int i, int lane) {
+        if (lane == 0) {
+            w.counts[i] = cnt;
+            if (w.counts_sub) w.counts_sub[i] = cnt_sub;
         }
+        if (keep && cnt <= w.slot_cap && cnt <= NB_MAXROW) {
+            __syncwarp();
+            int *dst = w.slots + (size_t)i * w.slot_cap;
+            if (cnt <= 128) {
+                rank_scatter(sb, cnt, dst, lane);
+            } else {
+                sort_row(sb, cnt, lane);
+                for (int t = lane; t < cnt; t += 32) dst[t] = sb[t];
+            }
+        }
+        __syncwarp();
+    }
+};
+
+__global__ void __launch_bounds__(NB_WARPS * 32) k_nbr_count_warp(NbrWork w, float rc2, float rc2_sub) {
+    if (gated_off(w.gate, w.err)) return;
+    __shared__ int buf[NB_WARPS][NB_MAXROW];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * NB_WARPS + warp;
+    if (i >= w.n_atoms) return;
+    const bool keep = w.slots != nullptr;
+    RowAcc acc{buf[warp]};
+    for_candidates_warp(w, i, rc2, lane, [&](bool hit, int j, float r2) { acc.add(w, keep, hit, j, r2, rc2_sub, lane); });
+    acc.finish(w, keep, i, lane);
+}
+
+// The same count by cells: one block per cell stages the indices and
+// positions of every candidate of its neighbouring cells in shared memory
+// once (in the order for_candidates_warp visits them), then each warp
+// sweeps them for one atom of the cell at a time. The candidates' positions
+// are exact copies, so every distance and decision is the same as in the
+// per-atom sweep; a cell with more candidates than fit falls back to it.
+constexpr int NBC_WARPS = 8, NBC_CAP = 2048;
+
+__global__ void __launch_bounds__(NBC_WARPS * 32) k_nbr_count_cell(NbrWork w, float rc2, float rc2_sub) {
+    if (gated_off(w.gate, w.err)) return;
+    __shared__ int cj[NBC_CAP];
+    __shared__ float cx[NBC_CAP], cy[NBC_CAP], cz[NBC_CAP];
+    __shared__ int buf[NBC_WARPS][NB_MAXROW];
+    __shared__ int seg_beg[18], seg_excl[19];
+    const int c = blockIdx.x;
+    const int a_beg = w.cell_start[c], a_end = w.cell_start[c + 1];
+    if (a_beg == a_end) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const CellGrid g = w.grid[w.atom_rep[w.cell_atoms[a_beg]]];
+    if (threadIdx.x == 0) {
+        // the neighbouring cells' x-runs, as for_candidates_warp forms them
+        const int own = c - g.cell_off;
+        const int ccx = own % g.dim[0], ccy = (own / g.dim[0]) % g.dim[1], ccz = own / (g.dim[0] * g.dim[1]);
+        int lo[3], hi[3];
+        const int c3[3] = {ccx, ccy, ccz};
+        for (int a = 0; a < 3; ++a) {
+            if (g.box[a] > 0.f) {
+                if (g.dim[a] >= 3) { lo[a] = -1; hi[a] = 1; }
+                else if (g.dim[a] == 2) { lo[a] = 0; hi[a] = 1; }
+                else { lo[a] = 0; hi[a] = 0; }
+            } else {
+                lo[a] = c3[a] > 0 ? -1 : 0;
+                hi[a] = c3[a] < g.dim[a] - 1 ? 1 : 0;
+            }
+        }
+        int a0 = ccx + lo[0], b0 = ccx + hi[0], a1 = 0, b1 = -1;
+        if (a0 < 0) { a1 = a0 + g.dim[0]; b1 = g.dim[0] - 1; a0 = 0; }
+        else if (b0 >= g.dim[0]) { a1 = 0; b1 = b0 - g.dim[0]; b0 = g.dim[0] - 1; }
+        int ns = 0, tot = 0;
+        for (int oz = lo[2]; oz <= hi[2]; ++oz) {
+            int z = ccz + oz;
+            if (g.box[2] > 0.f) z = (z + g.dim[2]) % g.dim[2];
+            for (int oy = lo[1]; oy <= hi[1]; ++oy) {
+                int y = ccy + oy;
+                if (g.box[1] > 0.f) y = (y + g.dim[1]) % g.dim[1];
+                const int row = g.cell_off + (z * g.dim[1] + y) * g.dim[0];
+                seg_beg[ns] = w.cell_start[row + a0];
+                seg_excl[ns] = tot;
+                tot += w.cell_start[row + b0 + 1] - seg_beg[ns];
+                ++ns;
+                if (b1 >= a1) {
+                    seg_beg[ns] = w.cell_start[row + a1];
+                    seg_excl[ns] = tot;
+                    tot += w.cell_start[row + b1 + 1] - seg_beg[ns];
+                    ++ns;
+                }
+            }
+        }
+        for (int k = ns; k < 19; ++k) seg_excl[k] = tot;
+    }
+    __syncthreads();
+    const int total = seg_excl[18];
+    const bool staged = total <= NBC_CAP;
+    if (staged) {
+        for (int q = threadIdx.x; q < total; q += blockDim.x) {
+            int sl = 0;
+            while (seg_excl[sl + 1] <= q) ++sl;
+            const int j = w.cell_atoms[seg_beg[sl] + (q - seg_excl[sl])];
+            cj[q] = j;
+            cx[q] = w.x[3 * j];
+            cy[q] = w.x[3 * j + 1];
+            cz[q] = w.x[3 * j + 2];
+        }
+    }
+    __syncthreads();
+    const bool keep = w.slots != nullptr;
+    const float ibx = g.box[0] > 0.f ? 1.f / g.box[0] : 0.f;
+    const float iby = g.box[1] > 0.f ? 1.f / g.box[1] : 0.f;
+    const float ibz = g.box[2] > 0.f ? 1.f / g.box[2] : 0.f;
+    for (int k = a_beg + warp; k < a_end; k += NBC_WARPS) {
+        const int i = w.cell_atoms[k];
+        RowAcc acc{buf[warp]};
+        if (staged) {
+            const float xi = w.x[3 * i], yi = w.x[3 * i + 1], zi = w.x[3 * i + 2];
+            for (int q0 = 0; q0 < total; q0 += 32) {
+                const int q = q0 + lane;
+                bool hit = false;
+                int j = -1;
+                float r2 = 0.f;
+                if (q < total) {
+                    j = cj[q];
+                    if (j != i) {
+                        const float dx = min_img(cx[q] - xi, g.box[0], ibx);
+                        const float dy = min_img(cy[q] - yi, g.box[1], iby);
+                        const float dz = min_img(cz[q] - zi, g.box[2], ibz);
+                        r2 = dx * dx + dy * dy + dz * dz;
+                        hit = r2 < rc2;
+                    }
+                }
+                acc.add(w, keep, hit, j, r2, rc2_sub, lane);
+            }
+        } else {
+            for_candidates_warp(w, i, rc2, lane,
+                                [&](bool hit, int j, float r2) { acc.add(w, keep, hit, j, r2, rc2_sub, lane); });
+        }
+        acc.finish(w, keep, i, lane);
     }
 }
 
@@ -557,7 +678,7 @@ void nbr_fill(const NbrWork &w, float r_list, int *row_ptr, int *col, long long 
     const int nb = (w.n_atoms + NB_WARPS - 1) / NB_WARPS;
     NbrWork wc = w;
     if (!sub_row) wc.counts_sub = nullptr;
-    k_nbr_count_warp<<<nb, NB_WARPS * 32, 0, st>>>(wc, r_list * r_list, r_sub * r_sub);
+    k_nbr_count_cell<<<wc.n_cells, NBC_WARPS * 32, 0, st>>>(wc, r_list * r_list, r_sub * r_sub);
     count_launch();
     // the full list's and the sub-list's row offsets in one launch
     scan_ints(wc, wc.counts, row_ptr, capacity, wc.total, wc.counts_sub, wc.counts_sub ? sub_row : nullptr,
