@@ -77,10 +77,14 @@ def test_nbr_batched_open_and_ragged(ctx1):
     _check_pairs(systems, nb, 5.5)
 
 
-def test_nbr_large_periodic_and_overflow_retry(ctx1):
+@pytest.mark.parametrize("rcut", [5.5, 9.0])
+def test_nbr_large_periodic_and_overflow_retry(ctx1, rcut):
+    """rcut 5.5: each cell's ~450 candidates are staged in shared memory;
+    rcut 9.0: ~2,600 candidates do not fit and the per-atom sweep takes
+    over. Both start from a pair capacity of 1,000 (overflow, grow, retry)."""
     sy = S.water_12288()
     d = core.DeviceSystem(sy)
-    nb = core.nbr_build(ctx1, d, 5.5, capacity=1000)   # overflow -> grow -> retry
+    nb = core.nbr_build(ctx1, d, rcut, capacity=1000)
     rp = nb.row_ptr.cpu().numpy()
     col = nb.col.cpu().numpy()
     rng = np.random.default_rng(0)
@@ -88,10 +92,12 @@ def test_nbr_large_periodic_and_overflow_retry(ctx1):
         dd = sy.x - sy.x[i]
         dd -= sy.box * np.rint(dd / sy.box)
         r2 = (dd ** 2).sum(1)
-        ref = set(np.nonzero(r2 < 5.5 ** 2)[0]) - {i}
-        got = set(col[rp[i]:rp[i + 1]].tolist())
-        amb = set(np.nonzero(np.abs(r2 - 5.5 ** 2) < 1e-4)[0])
+        ref = set(np.nonzero(r2 < rcut ** 2)[0]) - {i}
+        row = col[rp[i]:rp[i + 1]]
+        got = set(row.tolist())
+        amb = set(np.nonzero(np.abs(r2 - rcut ** 2) < 1e-4)[0])
         assert (ref ^ got) <= amb
+        assert np.all(np.diff(row) > 0)
 
 
 def test_nbr_empty_replica_and_single_atom(ctx1):
