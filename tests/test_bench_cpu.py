@@ -1,8 +1,8 @@
 """Host-side parts of bench.py that need no GPU: the reference arm's JSON
-line (the oracle timed on the host cores), the unit conversion of the
-metric, the per-launch byte counts of the integrator and the guard that
-reports the adjoint's DRAM traffic only while its sources are the captured
-ones."""
+line (the oracle timed on the host cores), the all-cores CPU leg (one
+oracle copy per core), the unit conversion of the metric, the per-launch
+byte counts of the integrator and the guard that reports the adjoint's DRAM
+traffic only while its sources are the captured ones."""
 import json
 import os
 import subprocess
@@ -70,3 +70,16 @@ def test_reference_arm_prints_the_contract_line():
     assert line["config"]["workload"] == "solvated_chain_23558"
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+
+
+def test_all_cores_leg_runs_one_oracle_copy_per_usable_cpu():
+    """The all-cores CPU figure: the unmodified oracle in one spawned process
+    per CPU this process may use, on the same periodic sample; its rate is
+    the sum of the copies' rates (each scaled to the full system)."""
+    from paper_2602_14975_gb300 import synth as S
+    W = S.WORKLOADS["solvated_chain_23558"]
+    sy = S.WORKLOADS["water_12288"]["system"]()
+    rate, p, wall, desc = bench.oracle_all_cores(sy, W, 0.3)
+    assert p == bench.usable_cpus() >= 1
+    assert rate > 0.0 and wall > 0.0
+    assert f"{p} concurrent copies" in desc
