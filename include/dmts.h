@@ -56,8 +56,10 @@ typedef enum {
 } dmts_status;
 
 /*
- * Arithmetic of the MLP contractions (the paper states none; the stand-in
- * models run them as follows). DMTS_FP32: fp32 SIMT products. DMTS_BF16:
+ * Arithmetic of the MLP contractions, and of the per-edge radial
+ * contraction R_lc = sum_k W_lkc f_c B_k of a conservative model with
+ * C = 128 (the paper states none; the stand-in models run them as
+ * follows). DMTS_FP32: fp32 SIMT products. DMTS_BF16:
  * tensor cores, bf16 x bf16 products accumulated in fp32, each operand held
  * as a split pair hi = rn_bf16(v), lo = rn_bf16(v - hi) and the products
  * hi*hi + lo*hi + hi*lo accumulated (about 16 significant bits per operand;

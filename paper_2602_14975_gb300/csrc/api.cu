@@ -293,7 +293,11 @@ dmts_status cons_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const
         io.q = q;
         io.q_bf16 = q_bf;
         io.err = ctx->d_err;
-        { ProfScope ps(ctx, "mp_fwd", st); launch_mp_fwd(C, m.lmax, m.K, g, io, st); }
+        {
+            ProfScope ps(ctx, "mp_fwd", st);
+            if (bf && mp_fwd_tc_supported(C, m.K, io)) launch_mp_fwd_tc(m.lmax, g, io, m.nseg, ctx->d_err, st);
+            else launch_mp_fwd(C, m.lmax, m.K, g, io, st);
+        }
         Epi e1 = epi(EPI_BIAS_SILU);
         e1.bias = m.b1[t];
         e1.H = H + nc_ * t;

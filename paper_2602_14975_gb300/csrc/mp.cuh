@@ -70,6 +70,12 @@ __device__ __forceinline__ void stv(float *p, const float *v) {
 }
 
 void launch_mp_fwd(int C, int lmax, int K, const EdgeGeom &g, const LayerIO &io, cudaStream_t st);
+// The forward layer with the radial contraction R = W B on the tensor cores
+// (split-bf16 operands, nseg as for launch_gemm_tc): C = 128, K = 8 and no
+// tensor-head output (io.V null) only; err receives DMTS_E_TIMEOUT if a
+// bounded wait on the tensor cores runs out.
+bool mp_fwd_tc_supported(int C, int K, const LayerIO &io);
+void launch_mp_fwd_tc(int lmax, const EdgeGeom &g, const LayerIO &io, int nseg, int *err, cudaStream_t st);
 void launch_mp_bwd(int C, int lmax, int K, const EdgeGeom &g, const LayerIO &io, cudaStream_t st);
 
 // ---------------------------------------------------------------- GEMM ----
