@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -605,9 +606,8 @@ void prepare_nbr_work_async(dmts_ctx *ctx, StateInternal *si, const SysView &v, 
     nw.box = v.box;
     // sized when the state was set up (prepare_nbr_work)
     nw.scan_status = (unsigned long long *)b.scan.p;
-    nw.scan_counter = (int *)(nw.scan_status + 2 * (size_t)b.scan_tiles);
+    nw.scan_counter = nw.scan_status + 2 * (size_t)b.scan_tiles;
     nw.scan_tiles = b.scan_tiles;
-    nw.scan_epoch = &b.scan_epoch;
 }
 
 }  // namespace dmts
@@ -630,14 +630,13 @@ static bool scan_scratch(dmts_ctx *ctx, NbrScratch &b, int n, NbrWork &nw, cudaS
     const int tiles = scan_tiles_for(n);
     if (tiles > b.scan_tiles) {
         b.scan.release();
-        const size_t bytes = sizeof(unsigned long long) * 2 * (size_t)tiles + 2 * sizeof(int);
+        const size_t bytes = sizeof(unsigned long long) * (2 * (size_t)tiles + 2);
         if (!b.scan.ensure(bytes) || !ck(ctx, cudaMemsetAsync(b.scan.p, 0, bytes, st), "scan scratch")) return false;
         b.scan_tiles = tiles;
     }
     nw.scan_status = (unsigned long long *)b.scan.p;
-    nw.scan_counter = (int *)(nw.scan_status + 2 * (size_t)b.scan_tiles);
+    nw.scan_counter = nw.scan_status + 2 * (size_t)b.scan_tiles;
     nw.scan_tiles = b.scan_tiles;
-    nw.scan_epoch = &b.scan_epoch;
     return true;
 }
 
@@ -814,6 +813,9 @@ void dmts_destroy(dmts_ctx *ctx) {
     if (ctx->cons.dev_bf) cudaFree(ctx->cons.dev_bf);
     if (ctx->nc.dev_bf) cudaFree(ctx->nc.dev_bf);
     if (ctx->d_err) cudaFree(ctx->d_err);
+    if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
+    if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
+    if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
     if (ctx->aux) cudaStreamDestroy(ctx->aux);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
@@ -1134,6 +1136,16 @@ dmts_status respa_step(dmts_ctx *ctx, dmts_state *stt, const dmts_integrator *p,
 // Algorithm 1 (or STS) for n_outer outer steps; fl_max (nullable, device,
 // one per replica) receives the running maximum of |F - F_S| (float bits) at
 // every outer kick.
+// Outer steps replayed from a CUDA graph unless DMTS_CUDA_GRAPHS=0 (the
+// launches are the same either way; the variable exists to compare them).
+static bool graphs_enabled() {
+    static const bool on = [] {
+        const char *e = std::getenv("DMTS_CUDA_GRAPHS");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
+
 dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrator *p, int n_outer, cudaStream_t st,
                             unsigned *fl_max) {
     if (!stt || !p) return fail(ctx, DMTS_E_INVALID, "NULL argument");
@@ -1330,17 +1342,16 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
         dmts_ctx *c;
         ~ActiveReset() { c->prof.active = true; }
     } active_reset{ctx};
-    for (int o = 0; o < n_outer; ++o) {
-        if (ctx->prof.on) {
-            ctx->prof.active = ctx->prof.every <= 1 || ctx->prof.outer % ctx->prof.every == 0;
-            ctx->prof.outer++;
-        }
+    // one outer step; its launches depend on o only through o == 0 (the
+    // first inner step's kicks) and the trace row, so every later step is
+    // the same sequence of launches with the same arguments
+    auto outer_step = [&](int o) -> dmts_status {
+        dmts_status r;
         if (!sts && stt->virial_nc &&
             !ck(ctx, cudaMemsetAsync(stt->virial_nc, 0, sizeof(double) * v.n_rep, st), "virial reset"))
             return DMTS_E_CUDA;
         if (npt) {
             ba.wvir = stt->virial_cons;
-            ba.step_add = (uint64_t)o * n_in;
             launch_baro_start(ba, st);
         }
         for (int k = 0; k < n_in; ++k) {
@@ -1348,7 +1359,7 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
             else if (k == 0 && npt) ia.ops = OP_KICK_L2 | OP_BAOA;   // the previous step closed itself
             else if (k == 0) ia.ops = (o == 0 ? OP_KICK_L2 : (OP_CLOSE_B | OP_KICK_L | OP_KICK_L2)) | OP_BAOA;
             else ia.ops = OP_CLOSE_B | OP_BAOA;
-            ia.step_add = (uint64_t)o * n_in + k;
+            ia.step_add = (uint64_t)k;   // the replicas' step counters advance at the end of each outer step
             { ProfScope ps(ctx, "integrate", st); integrate(ia); }
             rebuild_lists(ctx, si, v, st);
             if (!sts) {
@@ -1360,8 +1371,8 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
                         !ck(ctx, cudaStreamWaitEvent(s_nc, ctx->ev_fork, 0), "fork"))
                         return DMTS_E_CUDA;
                 }
-                s = nc_fast_on(stt->virial_nc != nullptr, s_nc);
-                if (s != DMTS_OK) return s;
+                r = nc_fast_on(stt->virial_nc != nullptr, s_nc);
+                if (r != DMTS_OK) return r;
                 if (last) {
                     // the fast force's virial at the end of the outer step, for
                     // the estimator, and its average over the inner steps
@@ -1373,8 +1384,8 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
                 }
             }
         }
-        s = cons_full();
-        if (s != DMTS_OK) return s;
+        r = cons_full();
+        if (r != DMTS_OK) return r;
         if (overlap && !ck(ctx, cudaStreamWaitEvent(st, ctx->ev_join, 0), "join")) return DMTS_E_CUDA;
         if (stt->virial_est) {
             if (sts) {
@@ -1399,13 +1410,88 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
         // the end of outer step o: under the barostat the step closed itself
         // above; otherwise its closing kicks are still pending
         if (stt->thermo_trace) thermo(!npt, stt->thermo_trace + (size_t)o * v.n_rep * 3);
+        launch_advance_step(stt->step, v.n_rep, (uint64_t)n_in, ctx->d_err, st);
+        return DMTS_OK;
+    };
+    // Outer steps after the first are replayed from a CUDA graph captured
+    // from the second (calls of three or more steps; not with a per-step
+    // trace, whose row changes, nor on the steps a sampling profiler times).
+    const bool graphs = n_outer >= 3 && !stt->thermo_trace && graphs_enabled();
+    if (graphs && !ctx->gstream &&
+        (!ck(ctx, cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking), "graph stream") ||
+         !ck(ctx, cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming), "graph event") ||
+         !ck(ctx, cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming), "graph event")))
+        return DMTS_E_CUDA;
+    // the outer steps run on the context's graph stream, after everything
+    // the caller's stream holds; on every way out, the caller's stream waits
+    // for them and the rest of the call runs on it again
+    struct StreamJoin {
+        dmts_ctx *c;
+        cudaStream_t *cur, user;
+        bool on;
+        void join() {
+            if (!on) return;
+            cudaEventRecord(c->ev_out, *cur);
+            cudaStreamWaitEvent(user, c->ev_out, 0);
+            *cur = user;
+            on = false;
+        }
+        ~StreamJoin() { join(); }
+    } sj{ctx, &st, st, false};
+    cudaGraphExec_t gx = nullptr;
+    unsigned long long gx_launches = 0;
+    struct GraphExecReset {
+        cudaGraphExec_t *g;
+        ~GraphExecReset() { if (*g) cudaGraphExecDestroy(*g); }
+    } gx_reset{&gx};
+    if (graphs) {
+        if (!ck(ctx, cudaEventRecord(ctx->ev_in, st), "graph stream") ||
+            !ck(ctx, cudaStreamWaitEvent(ctx->gstream, ctx->ev_in, 0), "graph stream"))
+            return DMTS_E_CUDA;
+        st = ctx->gstream;
+        sj.on = true;
     }
+    for (int o = 0; o < n_outer; ++o) {
+        if (ctx->prof.on) {
+            ctx->prof.active = ctx->prof.every <= 1 || ctx->prof.outer % ctx->prof.every == 0;
+            ctx->prof.outer++;
+        }
+        const bool replayable = graphs && o > 0 && !(ctx->prof.on && ctx->prof.active);
+        if (replayable && gx) {
+            if (!ck(ctx, cudaGraphLaunch(gx, st), "graph launch")) return DMTS_E_CUDA;
+            count_launches(gx_launches);
+            continue;
+        }
+        if (replayable) {
+            // capture this step (nothing runs while capturing), then launch it
+            const unsigned long long l0 = launch_count();
+            if (!ck(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed), "graph capture")) return DMTS_E_CUDA;
+            s = outer_step(o);
+            cudaGraph_t gr = nullptr;
+            const cudaError_t ce = cudaStreamEndCapture(st, &gr);
+            if (s != DMTS_OK) {
+                if (gr) cudaGraphDestroy(gr);
+                return s;
+            }
+            const bool inst = ce == cudaSuccess && gr && cudaGraphInstantiate(&gx, gr, 0) == cudaSuccess;
+            if (gr) cudaGraphDestroy(gr);
+            if (!inst) {
+                gx = nullptr;
+                return fail(ctx, DMTS_E_CUDA, "respa_step: graph capture of an outer step failed");
+            }
+            gx_launches = launch_count() - l0;
+            if (!ck(ctx, cudaGraphLaunch(gx, st), "graph launch")) return DMTS_E_CUDA;
+            continue;
+        }
+        s = outer_step(o);
+        if (s != DMTS_OK) return s;
+    }
+    sj.join();
     if (!npt) {
         ia.ops = sts ? OP_CLOSE_B : (OP_CLOSE_B | OP_KICK_L);
         { ProfScope ps(ctx, "integrate", st); integrate(ia); }
     }
     if (stt->thermo && !stt->thermo_trace) thermo(false, nullptr);
-    launch_advance_step(stt->step, v.n_rep, (uint64_t)n_outer * n_in, ctx->d_err, st);
     return ck(ctx, cudaGetLastError(), "respa_step launch") ? DMTS_OK : DMTS_E_CUDA;
 }
 

@@ -19,6 +19,8 @@ constexpr double kKcalPerA3PerAtm = 101325.0 * 6.02214076e23 * 1e-30 / 4184.0;  
 // Host-side count of this library's kernel launches (every launch site calls
 // it right after the launch); read through dmts_kernel_launches().
 void count_launch();
+void count_launches(unsigned long long n);   // a graph replay: the kernels its capture counted
+unsigned long long launch_count();
 
 __device__ __forceinline__ void set_error(int *err, int code) { atomicCAS(err, 0, code); }
 

@@ -43,9 +43,8 @@ constexpr int kNbrSlots = 128;   // longest row kept by the count pass of a stat
 struct NbrScratch {
     Buf grid, cell_cnt, cell_start, cell_atoms, atom_cell, atom_slot, counts, total, counts_sub;
     Buf slots;    // [n_atoms][kNbrSlots] sorted rows kept between the count and the fill of a rebuild
-    Buf scan;     // prefix-scan status words [2][scan_tiles] and tile counters [2] (zero-initialised)
+    Buf scan;     // prefix-scan status words [2][scan_tiles] and epoch/tile counters [2] (zero-initialised)
     int scan_tiles = 0;
-    unsigned scan_epoch = 0;
     void release_all() {
         grid.release(); cell_cnt.release(); cell_start.release(); cell_atoms.release();
         atom_cell.release(); atom_slot.release(); counts.release(); total.release(); counts_sub.release();
@@ -159,6 +158,10 @@ struct dmts_ctx {
     // same positions (created on first use)
     cudaStream_t aux = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // stream of respa_step's graph-replayed outer steps (a capturable stream
+    // whatever the caller's), joined to the caller's stream by two events
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 };
 
 namespace dmts {

@@ -565,20 +565,27 @@ struct ScanJob {
 };
 
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan(ScanJob j0, ScanJob j1, int n, int n_tiles,
-                                                       unsigned long long *status_all, int *counters, int tiles_cap,
-                                                       unsigned tag, int *err, const int *gate) {
+                                                       unsigned long long *status_all, unsigned long long *counters,
+                                                       int tiles_cap, int *err, const int *gate) {
     if (gated_off(gate, err)) return;
     const ScanJob J = blockIdx.y ? j1 : j0;
     unsigned long long *status = status_all + (size_t)blockIdx.y * tiles_cap;
-    int *counter = counters + blockIdx.y;
+    unsigned long long *counter = counters + blockIdx.y;
     __shared__ int tile_sh;
+    __shared__ unsigned tag_sh;
     __shared__ long long warp_tot[SCAN_THREADS / 32], excl_sh;
     if (threadIdx.x == 0) {
-        const int t = atomicAdd(counter, 1);
-        if (t == n_tiles - 1) *counter = 0;   // every block has taken its tile: ready for the next scan
+        // every block of this launch takes one tile and reads the same epoch;
+        // the block that takes the last one opens the next epoch
+        const unsigned long long old = atomicAdd(counter, 1ull);
+        const int t = (int)(old & 0xffffffffull);
+        const unsigned epoch = (unsigned)(old >> 32);
+        if (t == n_tiles - 1) atomicExch(counter, (unsigned long long)(epoch + 1u) << 32);
         tile_sh = t;
+        tag_sh = epoch % 0x0ffffffeu + 1u;   // 1 .. 2^28 - 2: zeroed words carry tag 0
     }
     __syncthreads();
+    const unsigned tag = tag_sh;
     const int tile = tile_sh, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int first = tile * kScanTile + threadIdx.x * SCAN_ITEMS;
     int v[SCAN_ITEMS];
@@ -652,11 +659,9 @@ void scan_ints(const NbrWork &w, const int *in0, int *out0, long long cap0, long
                int *out1, long long cap1, long long *total1, int n, cudaStream_t st) {
     const int tiles = (n + kScanTile - 1) / kScanTile;
     const int n_tiles = tiles > 0 ? tiles : 1;
-    unsigned tag = ++*w.scan_epoch & 0x0fffffffu;
-    if (tag == 0) tag = *w.scan_epoch = 1;   // zeroed words carry tag 0
     dim3 grid(n_tiles, in1 ? 2 : 1);
     k_scan<<<grid, SCAN_THREADS, 0, st>>>(ScanJob{in0, out0, cap0, total0}, ScanJob{in1, out1, cap1, total1}, n,
-                                          n_tiles, w.scan_status, w.scan_counter, w.scan_tiles, tag, w.err, w.gate);
+                                          n_tiles, w.scan_status, w.scan_counter, w.scan_tiles, w.err, w.gate);
     count_launch();
 }
 

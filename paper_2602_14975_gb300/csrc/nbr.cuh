@@ -38,13 +38,14 @@ struct NbrWork {
     int slot_cap = 0;
     const float *box = nullptr;  // [n_rep][3] (nullable): current boxes; periodic grids follow them at each
                                  // rebuild (a barostat moves the box)
-    // prefix-scan state: per job [scan_tiles] tile status words and a tile
-    // counter (zero between scans), and the host-side launch counter whose
-    // value tags this scan's status words
+    // prefix-scan state: per job [scan_tiles] tile status words and a word
+    // holding the scan's epoch (upper 32 bits) and the tiles taken so far
+    // (lower 32, zero between scans); the epoch tags the status words, so a
+    // scan never reads an earlier scan's words and no launch argument
+    // changes from one scan to the next (graph replays)
     unsigned long long *scan_status = nullptr;   // [2][scan_tiles]
-    int *scan_counter = nullptr;                 // [2]
+    unsigned long long *scan_counter = nullptr;  // [2]
     int scan_tiles = 0;
-    unsigned *scan_epoch = nullptr;              // host
 };
 
 // Tiles of the prefix scan (elements per tile) and the tiles a scan of n

@@ -31,7 +31,7 @@ constexpr size_t kOffTotal = kOffAtomRep + align256(sizeof(int) * kMaxAtoms);
 constexpr size_t kOffErr = kOffTotal + align256(sizeof(long long));
 constexpr int kScanTiles = (std::max(kMaxAtoms, kMaxCells) + kScanTile - 1) / kScanTile + 1;
 constexpr size_t kOffScan = kOffErr + align256(sizeof(int));   // prefix-scan status words and tile counters
-constexpr size_t kScratchBytes = kOffScan + align256(sizeof(unsigned long long) * 2 * kScanTiles + 2 * sizeof(int));
+constexpr size_t kScratchBytes = kOffScan + align256(sizeof(unsigned long long) * (2 * kScanTiles + 2));
 
 }  // namespace
 
@@ -133,11 +133,9 @@ extern "C" dmts_status nbr_build_noalloc(const dmts_system *sys, dmts_nbr *nbr, 
     w.total = (long long *)(base + kOffTotal);
     w.gate = nullptr;
     w.err = (int *)(base + kOffErr);
-    static unsigned scan_epoch = 0;   // calls are serialised by the caller (see the header)
     w.scan_status = (unsigned long long *)(base + kOffScan);
-    w.scan_counter = (int *)(w.scan_status + 2 * (size_t)kScanTiles);
+    w.scan_counter = w.scan_status + 2 * (size_t)kScanTiles;
     w.scan_tiles = kScanTiles;
-    w.scan_epoch = &scan_epoch;
     // the previous call's contents are still there: clear the words that
     // must start at zero (error word, total; nbr_cells clears the counts)
     if (!ck(nullptr, cudaMemsetAsync(base + kOffTotal, 0, kScratchBytes - kOffTotal, st), "nbr_build_noalloc: clear") ||

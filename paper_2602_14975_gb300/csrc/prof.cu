@@ -10,6 +10,8 @@ namespace dmts {
 static std::atomic<unsigned long long> g_kernel_launches{0};
 
 void count_launch() { g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(unsigned long long n) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }
+unsigned long long launch_count() { return g_kernel_launches.load(std::memory_order_relaxed); }
 
 int Profiler::slot(const char *name) {
     for (size_t k = 0; k < slots.size(); ++k)

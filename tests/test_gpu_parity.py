@@ -617,20 +617,28 @@ def test_bad_thermostat_is_rejected(ctx1, water):
     st.release()
 
 
-def test_respa_split_calls_equal_single_call(ctx1, water):
+@pytest.mark.parametrize("mode", ["respa", "sts"])
+def test_respa_split_calls_equal_single_call(ctx1, water, mode):
+    """A call of three or more outer steps replays the second one's CUDA
+    graph for the rest; calls of one or two run every launch directly. The
+    trajectories agree bit for bit, with and without the graph, and with the
+    step counters (Philox keys) advanced inside the graph."""
     m, v = _md_setup(water)
     out = []
-    for split in ((6,), (2, 3, 1)):
+    for split in ((6,), (2, 3, 1), (1,) * 6):
         d = core.DeviceSystem(water)
         st = core.MDState(d, v, m.astype(np.float32), seeds=7)
-        integ = core.integrator(4.0, 4, 300.0, [1.0] * 5, skin=0.5)
+        integ = core.integrator(4.0 if mode == "respa" else 1.0, 4, 300.0, [1.0] * 5, skin=0.5,
+                                mode=core.L.MODE_RESPA if mode == "respa" else core.L.MODE_STS)
         for k in split:
             core.respa_step(ctx1, st, integ, k)
         ctx1.sync()
-        out.append((d.x.cpu().numpy(), st.v.cpu().numpy()))
+        out.append((d.x.cpu().numpy(), st.v.cpu().numpy(), st.step.cpu().numpy()))
         st.release()
-    assert np.array_equal(out[0][0], out[1][0])
-    assert np.array_equal(out[0][1], out[1][1])
+    for o in out[1:]:
+        assert np.array_equal(out[0][0], o[0])
+        assert np.array_equal(out[0][1], o[1])
+        assert np.array_equal(out[0][2], o[2])
 
 
 def test_sts_positions_after_10_steps(ctx1, models1, water):
