@@ -1,6 +1,7 @@
 // Host side of the C ABI: context, device models, workspace, force
 // evaluations, the Algorithm-1 driver (respa_step) and host helpers.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -33,8 +34,13 @@ dmts_status fail(dmts_ctx *ctx, dmts_status s, const std::string &msg) {
     return s;
 }
 
+static std::atomic<unsigned long long> g_alloc_gen{0};
+unsigned long long alloc_generation() { return g_alloc_gen.load(std::memory_order_relaxed); }
+void bump_alloc_generation() { g_alloc_gen.fetch_add(1, std::memory_order_relaxed); }
+
 bool Buf::ensure(size_t bytes) {
     if (bytes <= cap) return true;
+    bump_alloc_generation();
     if (p) cudaFree(p);
     p = nullptr;
     cap = 0;
@@ -56,7 +62,10 @@ static bool ensure_zeroed(dmts_ctx *ctx, Buf &b, size_t bytes, cudaStream_t st) 
 }
 
 void Buf::release() {
-    if (p) cudaFree(p);
+    if (p) {
+        bump_alloc_generation();
+        cudaFree(p);
+    }
     p = nullptr;
     cap = 0;
 }
@@ -71,6 +80,7 @@ static uint16_t bf16_bits(float f) {
 }
 
 static bool upload(DevModel &m, const std::vector<float> &h) {
+    bump_alloc_generation();
     if (cudaMalloc(&m.dev, h.size() * sizeof(float)) != cudaSuccess) return false;
     return cudaMemcpy(m.dev, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess;
 }
@@ -175,6 +185,7 @@ static dmts_status load_model(dmts_ctx *ctx, const dmts_model *in, bool is_nc, D
         } else {
             o_qk = push(m.Wqk, 2 * (K + m.nl) * m.nc, C, false);
         }
+        bump_alloc_generation();
         if (cudaMalloc(&m.dev_bf, hb.size() * 2) != cudaSuccess ||
             cudaMemcpy(m.dev_bf, hb.data(), hb.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess)
             return fail(ctx, DMTS_E_OOM, "bf16 weight upload failed");
@@ -676,6 +687,7 @@ static dmts_status prepare_nbr_work(dmts_ctx *ctx, NbrScratch &b, const SysView 
 
 void free_state_internal(StateInternal *si) {
     if (!si) return;
+    if (si->call_graph) cudaGraphExecDestroy(si->call_graph);
     si->cons_row.release();
     si->cons_col.release();
     si->nc_row.release();
@@ -1128,7 +1140,7 @@ static void gamma_consts(const dmts_integrator *p, double dt, float *c1, float *
 }
 
 dmts_status respa_step(dmts_ctx *ctx, dmts_state *stt, const dmts_integrator *p, int n_outer, void *stream) {
-    return dmts::respa_run(ctx, stt, p, n_outer, (cudaStream_t)stream, nullptr);
+    return dmts::respa_run(ctx, stt, p, n_outer, (cudaStream_t)stream, nullptr, true);
 }
 
 }  // extern "C"
@@ -1146,8 +1158,47 @@ static bool graphs_enabled() {
     return on;
 }
 
+// The context's graph stream and its two join events (created on first use).
+static bool ensure_graph_stream(dmts_ctx *ctx) {
+    if (ctx->gstream) return true;
+    return ck(ctx, cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking), "graph stream") &&
+           ck(ctx, cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming), "graph event") &&
+           ck(ctx, cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming), "graph event");
+}
+
+// What a captured call depends on besides the device contents: the
+// integrator's parameters, the number of outer steps, the state's arrays and
+// the generation of the library's device allocations.
+static std::vector<uint64_t> call_key(const dmts_integrator *p, int n_outer, const dmts_state *stt) {
+    std::vector<uint64_t> k;
+    auto f32 = [&](float v) { uint32_t u; memcpy(&u, &v, 4); k.push_back(u); };
+    auto f64 = [&](double v) { uint64_t u; memcpy(&u, &v, 8); k.push_back(u); };
+    auto ptr = [&](const void *q) { k.push_back((uint64_t)(uintptr_t)q); };
+    f32(p->dt_outer);
+    k.push_back((uint64_t)(uint32_t)p->n_inner);
+    f32(p->temperature);
+    for (int i = 0; i < DMTS_MAX_SPECIES; ++i) f64(p->gamma_ps[i]);
+    k.push_back((uint64_t)(uint32_t)p->mode);
+    f32(p->skin);
+    k.push_back((uint64_t)(uint32_t)p->thermostat);
+    k.push_back((uint64_t)(uint32_t)p->barostat);
+    f32(p->pressure_atm);
+    f32(p->tau_p_ps);
+    k.push_back((uint64_t)(uint32_t)n_outer);
+    const dmts_system &y = stt->sys;
+    k.push_back((uint64_t)(uint32_t)y.n_atoms);
+    k.push_back((uint64_t)(uint32_t)y.n_replicas);
+    const void *arrays[] = {y.rep_off, y.box, y.x, y.species, y.mol_id, y.bond_ptr, y.bond_idx, y.bond_r0,
+                            stt->v, stt->f_nc, stt->f_cons, stt->masses, stt->energy, stt->step, stt->seed,
+                            stt->replica_id, stt->virial_nc, stt->virial_cons, stt->virial_est, stt->baro,
+                            stt->thermo, stt->internal};
+    for (const void *q : arrays) ptr(q);
+    k.push_back(alloc_generation());
+    return k;
+}
+
 dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrator *p, int n_outer, cudaStream_t st,
-                            unsigned *fl_max) {
+                            unsigned *fl_max, bool cache_short_calls) {
     if (!stt || !p) return fail(ctx, DMTS_E_INVALID, "NULL argument");
     dmts_status s = check_sys(ctx, &stt->sys);
     if (s != DMTS_OK) return s;
@@ -1282,217 +1333,268 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
         }
         return ck(ctx, cudaGetLastError(), "respa_step launch") ? DMTS_OK : DMTS_E_CUDA;
     }
-    // FP64 K, U + K and T per replica (pending closing kicks selected per call site)
-    ThermoArgs ta;
-    memset(&ta, 0, sizeof ta);
-    ta.rep_off = v.rep_off;
-    ta.v = stt->v;
-    ta.f_fast = ia.f_fast;
-    ta.f_slow = stt->f_cons;
-    ta.masses = stt->masses;
-    ta.h_in = ia.h_in;
-    ta.h_out = ia.h_out;
-    ta.energy = stt->energy;
-    ta.out = stt->thermo;
-    ta.part_off = v.ms_part_off;
-    ta.partial = (double *)si->thermo_part.p;
-    ta.n_rep = v.n_rep;
-    auto thermo = [&](bool pending, double *trace_row) {
-        ThermoArgs t = ta;
-        t.close_b = pending;
-        t.kick_l = pending && !sts;
-        t.trace = trace_row;
-        if (pending && mean_pending) {
-            t.f_fast = (const float *)ctx->ws.nc_f.p;
-            t.fast_sum = (const unsigned long long *)ctx->ws.nc_sum.p;
-        }
-        ProfScope ps(ctx, "thermo", st);
-        launch_thermo(t, v.n, v.n_rep, st);
-    };
-    BaroArgs ba;
-    memset(&ba, 0, sizeof ba);
-    if (npt) {
-        ba.n_rep = v.n_rep;
-        ba.rep_off = v.rep_off;
-        ba.baro = stt->baro;
-        ba.box = const_cast<float *>(stt->sys.box);
-        ba.K = (const double *)si->baro_K.p;
-        ba.baro_f = (float *)si->baro_f.p;
-        ba.seed = stt->seed;
-        ba.rep_id = stt->replica_id;
-        ba.step = stt->step;
-        ba.delta_outer = p->dt_outer;
-        ba.h = 0.5 * delta;
-        ba.p_kcal = (double)p->pressure_atm * kKcalPerA3PerAtm;
-        ba.tau_fs = (double)p->tau_p_ps * 1e3;
-        ba.kT = kBoltzmann * p->temperature;
-        ba.err = ctx->d_err;
-        ia.baro_f = (const float *)si->baro_f.p;
-        ia.box = ba.box;
-        // kinetic energy now, for a piston force not yet set (the full force's virial)
-        IntegArgs ik = ia;
-        ik.ops = 0;
-        ik.baro_f = nullptr;
-        ik.ke = (float *)si->baro_ke.p;
-        integrate(ik);
-        launch_replica_sum((const float *)si->baro_ke.p, v.rep_off, v.n_rep, (double *)si->baro_K.p, 0, st);
-    }
-    // outer steps not timed under a sampling profiler; calls outside the loop are
-    struct ActiveReset {
-        dmts_ctx *c;
-        ~ActiveReset() { c->prof.active = true; }
-    } active_reset{ctx};
-    // one outer step; its launches depend on o only through o == 0 (the
-    // first inner step's kicks) and the trace row, so every later step is
-    // the same sequence of launches with the same arguments
-    auto outer_step = [&](int o) -> dmts_status {
-        dmts_status r;
-        if (!sts && stt->virial_nc &&
-            !ck(ctx, cudaMemsetAsync(stt->virial_nc, 0, sizeof(double) * v.n_rep, st), "virial reset"))
+    // A call of one or two outer steps (the loop of a caller that copies
+    // the state in and out between calls) is replayed whole from a graph the
+    // state keeps, captured from its first such call: the key holds the
+    // integrator's parameters, the number of steps, every array of the state
+    // and the generation of the library's device allocations, so a graph is
+    // never replayed on arrays that moved or were freed.
+    const bool cache_call =
+        cache_short_calls && n_outer <= 2 && !ctx->prof.on && !stt->thermo_trace && !fl_max && graphs_enabled();
+    if (cache_call && si->call_graph && si->call_key == call_key(p, n_outer, stt)) {
+        if (!ensure_graph_stream(ctx) || !ck(ctx, cudaEventRecord(ctx->ev_in, st), "graph stream") ||
+            !ck(ctx, cudaStreamWaitEvent(ctx->gstream, ctx->ev_in, 0), "graph stream") ||
+            !ck(ctx, cudaGraphLaunch(si->call_graph, ctx->gstream), "graph launch") ||
+            !ck(ctx, cudaEventRecord(ctx->ev_out, ctx->gstream), "graph stream") ||
+            !ck(ctx, cudaStreamWaitEvent(st, ctx->ev_out, 0), "graph stream"))
             return DMTS_E_CUDA;
-        if (npt) {
-            ba.wvir = stt->virial_cons;
-            launch_baro_start(ba, st);
-        }
-        for (int k = 0; k < n_in; ++k) {
-            if (sts) ia.ops = (o == 0 ? 0 : OP_CLOSE_B) | OP_BAOA;
-            else if (k == 0 && npt) ia.ops = OP_KICK_L2 | OP_BAOA;   // the previous step closed itself
-            else if (k == 0) ia.ops = (o == 0 ? OP_KICK_L2 : (OP_CLOSE_B | OP_KICK_L | OP_KICK_L2)) | OP_BAOA;
-            else ia.ops = OP_CLOSE_B | OP_BAOA;
-            ia.step_add = (uint64_t)k;   // the replicas' step counters advance at the end of each outer step
-            { ProfScope ps(ctx, "integrate", st); integrate(ia); }
-            rebuild_lists(ctx, si, v, st);
-            if (!sts) {
-                const bool last = k == n_in - 1;
-                cudaStream_t s_nc = st;
-                if (last && overlap) {
-                    s_nc = ctx->aux;
-                    if (!ck(ctx, cudaEventRecord(ctx->ev_fork, st), "fork") ||
-                        !ck(ctx, cudaStreamWaitEvent(s_nc, ctx->ev_fork, 0), "fork"))
-                        return DMTS_E_CUDA;
-                }
-                r = nc_fast_on(stt->virial_nc != nullptr, s_nc);
-                if (r != DMTS_OK) return r;
-                if (last) {
-                    // the fast force's virial at the end of the outer step, for
-                    // the estimator, and its average over the inner steps
-                    if (stt->virial_est)
-                        launch_replica_sum((const float *)ctx->ws.nc_w.p, v.rep_off, v.n_rep,
-                                           (double *)ctx->ws.nc_w_last.p, 0, s_nc);
-                    if (stt->virial_nc) launch_scale_d(stt->virial_nc, v.n_rep, 1.0 / n_in, s_nc);
-                    if (overlap && !ck(ctx, cudaEventRecord(ctx->ev_join, s_nc), "join")) return DMTS_E_CUDA;
-                }
-            }
-        }
-        r = cons_full();
-        if (r != DMTS_OK) return r;
-        if (overlap && !ck(ctx, cudaStreamWaitEvent(st, ctx->ev_join, 0), "join")) return DMTS_E_CUDA;
-        if (stt->virial_est) {
-            if (sts) {
-                if (!ck(ctx, cudaMemcpyAsync(stt->virial_est, stt->virial_cons, sizeof(double) * v.n_rep,
-                                             cudaMemcpyDeviceToDevice, st), "virial copy"))
-                    return DMTS_E_CUDA;
-            } else {
-                launch_virial_estimate(stt->virial_est, stt->virial_cons, (const double *)ctx->ws.nc_w_last.p,
-                                       stt->virial_nc, v.n_rep, st);
-            }
-        }
-        if (npt) {
-            // close the outer step, then the piston's half kick with the estimator
-            ia.ops = OP_CLOSE_B | OP_KICK_L;
-            ia.ke = (float *)si->baro_ke.p;
-            { ProfScope ps(ctx, "integrate", st); integrate(ia); }
-            ia.ke = nullptr;
-            launch_replica_sum((const float *)si->baro_ke.p, v.rep_off, v.n_rep, (double *)si->baro_K.p, 0, st);
-            ba.wvir = stt->virial_est;
-            { ProfScope ps(ctx, "barostat", st); launch_baro_end(ba, st); }
-        }
-        // the end of outer step o: under the barostat the step closed itself
-        // above; otherwise its closing kicks are still pending
-        if (stt->thermo_trace) thermo(!npt, stt->thermo_trace + (size_t)o * v.n_rep * 3);
-        launch_advance_step(stt->step, v.n_rep, (uint64_t)n_in, ctx->d_err, st);
+        count_launches(si->call_launches);
         return DMTS_OK;
-    };
-    // Outer steps after the first are replayed from a CUDA graph captured
-    // from the second (calls of three or more steps; not with a per-step
-    // trace, whose row changes, nor on the steps a sampling profiler times).
-    const bool graphs = n_outer >= 3 && !stt->thermo_trace && graphs_enabled();
-    if (graphs && !ctx->gstream &&
-        (!ck(ctx, cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking), "graph stream") ||
-         !ck(ctx, cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming), "graph event") ||
-         !ck(ctx, cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming), "graph event")))
-        return DMTS_E_CUDA;
-    // the outer steps run on the context's graph stream, after everything
-    // the caller's stream holds; on every way out, the caller's stream waits
-    // for them and the rest of the call runs on it again
-    struct StreamJoin {
-        dmts_ctx *c;
-        cudaStream_t *cur, user;
-        bool on;
-        void join() {
-            if (!on) return;
-            cudaEventRecord(c->ev_out, *cur);
-            cudaStreamWaitEvent(user, c->ev_out, 0);
-            *cur = user;
-            on = false;
-        }
-        ~StreamJoin() { join(); }
-    } sj{ctx, &st, st, false};
-    cudaGraphExec_t gx = nullptr;
-    unsigned long long gx_launches = 0;
-    struct GraphExecReset {
-        cudaGraphExec_t *g;
-        ~GraphExecReset() { if (*g) cudaGraphExecDestroy(*g); }
-    } gx_reset{&gx};
-    if (graphs) {
-        if (!ck(ctx, cudaEventRecord(ctx->ev_in, st), "graph stream") ||
-            !ck(ctx, cudaStreamWaitEvent(ctx->gstream, ctx->ev_in, 0), "graph stream"))
-            return DMTS_E_CUDA;
-        st = ctx->gstream;
-        sj.on = true;
     }
-    for (int o = 0; o < n_outer; ++o) {
-        if (ctx->prof.on) {
-            ctx->prof.active = ctx->prof.every <= 1 || ctx->prof.outer % ctx->prof.every == 0;
-            ctx->prof.outer++;
+    auto rest_of_call = [&](bool step_graphs) -> dmts_status {
+        // FP64 K, U + K and T per replica (pending closing kicks selected per call site)
+        ThermoArgs ta;
+        memset(&ta, 0, sizeof ta);
+        ta.rep_off = v.rep_off;
+        ta.v = stt->v;
+        ta.f_fast = ia.f_fast;
+        ta.f_slow = stt->f_cons;
+        ta.masses = stt->masses;
+        ta.h_in = ia.h_in;
+        ta.h_out = ia.h_out;
+        ta.energy = stt->energy;
+        ta.out = stt->thermo;
+        ta.part_off = v.ms_part_off;
+        ta.partial = (double *)si->thermo_part.p;
+        ta.n_rep = v.n_rep;
+        auto thermo = [&](bool pending, double *trace_row) {
+            ThermoArgs t = ta;
+            t.close_b = pending;
+            t.kick_l = pending && !sts;
+            t.trace = trace_row;
+            if (pending && mean_pending) {
+                t.f_fast = (const float *)ctx->ws.nc_f.p;
+                t.fast_sum = (const unsigned long long *)ctx->ws.nc_sum.p;
+            }
+            ProfScope ps(ctx, "thermo", st);
+            launch_thermo(t, v.n, v.n_rep, st);
+        };
+        BaroArgs ba;
+        memset(&ba, 0, sizeof ba);
+        if (npt) {
+            ba.n_rep = v.n_rep;
+            ba.rep_off = v.rep_off;
+            ba.baro = stt->baro;
+            ba.box = const_cast<float *>(stt->sys.box);
+            ba.K = (const double *)si->baro_K.p;
+            ba.baro_f = (float *)si->baro_f.p;
+            ba.seed = stt->seed;
+            ba.rep_id = stt->replica_id;
+            ba.step = stt->step;
+            ba.delta_outer = p->dt_outer;
+            ba.h = 0.5 * delta;
+            ba.p_kcal = (double)p->pressure_atm * kKcalPerA3PerAtm;
+            ba.tau_fs = (double)p->tau_p_ps * 1e3;
+            ba.kT = kBoltzmann * p->temperature;
+            ba.err = ctx->d_err;
+            ia.baro_f = (const float *)si->baro_f.p;
+            ia.box = ba.box;
+            // kinetic energy now, for a piston force not yet set (the full force's virial)
+            IntegArgs ik = ia;
+            ik.ops = 0;
+            ik.baro_f = nullptr;
+            ik.ke = (float *)si->baro_ke.p;
+            integrate(ik);
+            launch_replica_sum((const float *)si->baro_ke.p, v.rep_off, v.n_rep, (double *)si->baro_K.p, 0, st);
         }
-        const bool replayable = graphs && o > 0 && !(ctx->prof.on && ctx->prof.active);
-        if (replayable && gx) {
-            if (!ck(ctx, cudaGraphLaunch(gx, st), "graph launch")) return DMTS_E_CUDA;
-            count_launches(gx_launches);
-            continue;
+        // outer steps not timed under a sampling profiler; calls outside the loop are
+        struct ActiveReset {
+            dmts_ctx *c;
+            ~ActiveReset() { c->prof.active = true; }
+        } active_reset{ctx};
+        // one outer step; its launches depend on o only through o == 0 (the
+        // first inner step's kicks) and the trace row, so every later step is
+        // the same sequence of launches with the same arguments
+        auto outer_step = [&](int o) -> dmts_status {
+            dmts_status r;
+            if (!sts && stt->virial_nc &&
+                !ck(ctx, cudaMemsetAsync(stt->virial_nc, 0, sizeof(double) * v.n_rep, st), "virial reset"))
+                return DMTS_E_CUDA;
+            if (npt) {
+                ba.wvir = stt->virial_cons;
+                launch_baro_start(ba, st);
+            }
+            for (int k = 0; k < n_in; ++k) {
+                if (sts) ia.ops = (o == 0 ? 0 : OP_CLOSE_B) | OP_BAOA;
+                else if (k == 0 && npt) ia.ops = OP_KICK_L2 | OP_BAOA;   // the previous step closed itself
+                else if (k == 0) ia.ops = (o == 0 ? OP_KICK_L2 : (OP_CLOSE_B | OP_KICK_L | OP_KICK_L2)) | OP_BAOA;
+                else ia.ops = OP_CLOSE_B | OP_BAOA;
+                ia.step_add = (uint64_t)k;   // the replicas' step counters advance at the end of each outer step
+                { ProfScope ps(ctx, "integrate", st); integrate(ia); }
+                rebuild_lists(ctx, si, v, st);
+                if (!sts) {
+                    const bool last = k == n_in - 1;
+                    cudaStream_t s_nc = st;
+                    if (last && overlap) {
+                        s_nc = ctx->aux;
+                        if (!ck(ctx, cudaEventRecord(ctx->ev_fork, st), "fork") ||
+                            !ck(ctx, cudaStreamWaitEvent(s_nc, ctx->ev_fork, 0), "fork"))
+                            return DMTS_E_CUDA;
+                    }
+                    r = nc_fast_on(stt->virial_nc != nullptr, s_nc);
+                    if (r != DMTS_OK) return r;
+                    if (last) {
+                        // the fast force's virial at the end of the outer step, for
+                        // the estimator, and its average over the inner steps
+                        if (stt->virial_est)
+                            launch_replica_sum((const float *)ctx->ws.nc_w.p, v.rep_off, v.n_rep,
+                                               (double *)ctx->ws.nc_w_last.p, 0, s_nc);
+                        if (stt->virial_nc) launch_scale_d(stt->virial_nc, v.n_rep, 1.0 / n_in, s_nc);
+                        if (overlap && !ck(ctx, cudaEventRecord(ctx->ev_join, s_nc), "join")) return DMTS_E_CUDA;
+                    }
+                }
+            }
+            r = cons_full();
+            if (r != DMTS_OK) return r;
+            if (overlap && !ck(ctx, cudaStreamWaitEvent(st, ctx->ev_join, 0), "join")) return DMTS_E_CUDA;
+            if (stt->virial_est) {
+                if (sts) {
+                    if (!ck(ctx, cudaMemcpyAsync(stt->virial_est, stt->virial_cons, sizeof(double) * v.n_rep,
+                                                 cudaMemcpyDeviceToDevice, st), "virial copy"))
+                        return DMTS_E_CUDA;
+                } else {
+                    launch_virial_estimate(stt->virial_est, stt->virial_cons, (const double *)ctx->ws.nc_w_last.p,
+                                           stt->virial_nc, v.n_rep, st);
+                }
+            }
+            if (npt) {
+                // close the outer step, then the piston's half kick with the estimator
+                ia.ops = OP_CLOSE_B | OP_KICK_L;
+                ia.ke = (float *)si->baro_ke.p;
+                { ProfScope ps(ctx, "integrate", st); integrate(ia); }
+                ia.ke = nullptr;
+                launch_replica_sum((const float *)si->baro_ke.p, v.rep_off, v.n_rep, (double *)si->baro_K.p, 0, st);
+                ba.wvir = stt->virial_est;
+                { ProfScope ps(ctx, "barostat", st); launch_baro_end(ba, st); }
+            }
+            // the end of outer step o: under the barostat the step closed itself
+            // above; otherwise its closing kicks are still pending
+            if (stt->thermo_trace) thermo(!npt, stt->thermo_trace + (size_t)o * v.n_rep * 3);
+            launch_advance_step(stt->step, v.n_rep, (uint64_t)n_in, ctx->d_err, st);
+            return DMTS_OK;
+        };
+        // Outer steps after the first are replayed from a CUDA graph captured
+        // from the second (calls of three or more steps; not with a per-step
+        // trace, whose row changes, nor on the steps a sampling profiler times).
+        const bool graphs = step_graphs && n_outer >= 3 && !stt->thermo_trace && graphs_enabled();
+        if (graphs && !ensure_graph_stream(ctx)) return DMTS_E_CUDA;
+        // the outer steps run on the context's graph stream, after everything
+        // the caller's stream holds; on every way out, the caller's stream waits
+        // for them and the rest of the call runs on it again
+        struct StreamJoin {
+            dmts_ctx *c;
+            cudaStream_t *cur, user;
+            bool on;
+            void join() {
+                if (!on) return;
+                cudaEventRecord(c->ev_out, *cur);
+                cudaStreamWaitEvent(user, c->ev_out, 0);
+                *cur = user;
+                on = false;
+            }
+            ~StreamJoin() { join(); }
+        } sj{ctx, &st, st, false};
+        cudaGraphExec_t gx = nullptr;
+        unsigned long long gx_launches = 0;
+        struct GraphExecReset {
+            cudaGraphExec_t *g;
+            ~GraphExecReset() { if (*g) cudaGraphExecDestroy(*g); }
+        } gx_reset{&gx};
+        if (graphs) {
+            if (!ck(ctx, cudaEventRecord(ctx->ev_in, st), "graph stream") ||
+                !ck(ctx, cudaStreamWaitEvent(ctx->gstream, ctx->ev_in, 0), "graph stream"))
+                return DMTS_E_CUDA;
+            st = ctx->gstream;
+            sj.on = true;
         }
-        if (replayable) {
-            // capture this step (nothing runs while capturing), then launch it
-            const unsigned long long l0 = launch_count();
-            if (!ck(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed), "graph capture")) return DMTS_E_CUDA;
-            s = outer_step(o);
-            cudaGraph_t gr = nullptr;
-            const cudaError_t ce = cudaStreamEndCapture(st, &gr);
-            if (s != DMTS_OK) {
+        for (int o = 0; o < n_outer; ++o) {
+            if (ctx->prof.on) {
+                ctx->prof.active = ctx->prof.every <= 1 || ctx->prof.outer % ctx->prof.every == 0;
+                ctx->prof.outer++;
+            }
+            const bool replayable = graphs && o > 0 && !(ctx->prof.on && ctx->prof.active);
+            if (replayable && gx) {
+                if (!ck(ctx, cudaGraphLaunch(gx, st), "graph launch")) return DMTS_E_CUDA;
+                count_launches(gx_launches);
+                continue;
+            }
+            if (replayable) {
+                // capture this step (nothing runs while capturing), then launch it
+                const unsigned long long l0 = launch_count();
+                if (!ck(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed), "graph capture")) return DMTS_E_CUDA;
+                s = outer_step(o);
+                cudaGraph_t gr = nullptr;
+                const cudaError_t ce = cudaStreamEndCapture(st, &gr);
+                if (s != DMTS_OK) {
+                    if (gr) cudaGraphDestroy(gr);
+                    return s;
+                }
+                const bool inst = ce == cudaSuccess && gr && cudaGraphInstantiate(&gx, gr, 0) == cudaSuccess;
                 if (gr) cudaGraphDestroy(gr);
-                return s;
+                if (!inst) {
+                    gx = nullptr;
+                    return fail(ctx, DMTS_E_CUDA, "respa_step: graph capture of an outer step failed");
+                }
+                gx_launches = launch_count() - l0;
+                if (!ck(ctx, cudaGraphLaunch(gx, st), "graph launch")) return DMTS_E_CUDA;
+                continue;
             }
-            const bool inst = ce == cudaSuccess && gr && cudaGraphInstantiate(&gx, gr, 0) == cudaSuccess;
-            if (gr) cudaGraphDestroy(gr);
-            if (!inst) {
-                gx = nullptr;
-                return fail(ctx, DMTS_E_CUDA, "respa_step: graph capture of an outer step failed");
-            }
-            gx_launches = launch_count() - l0;
-            if (!ck(ctx, cudaGraphLaunch(gx, st), "graph launch")) return DMTS_E_CUDA;
-            continue;
+            s = outer_step(o);
+            if (s != DMTS_OK) return s;
         }
-        s = outer_step(o);
-        if (s != DMTS_OK) return s;
-    }
-    sj.join();
-    if (!npt) {
-        ia.ops = sts ? OP_CLOSE_B : (OP_CLOSE_B | OP_KICK_L);
-        { ProfScope ps(ctx, "integrate", st); integrate(ia); }
-    }
+        sj.join();
+        if (!npt) {
+            ia.ops = sts ? OP_CLOSE_B : (OP_CLOSE_B | OP_KICK_L);
+            { ProfScope ps(ctx, "integrate", st); integrate(ia); }
+        }
     if (stt->thermo && !stt->thermo_trace) thermo(false, nullptr);
-    return ck(ctx, cudaGetLastError(), "respa_step launch") ? DMTS_OK : DMTS_E_CUDA;
+        return ck(ctx, cudaGetLastError(), "respa_step launch") ? DMTS_OK : DMTS_E_CUDA;
+    };
+    if (!cache_call) return rest_of_call(true);
+    if (si->call_graph) {
+        cudaGraphExecDestroy(si->call_graph);
+        si->call_graph = nullptr;
+    }
+    if (!ensure_graph_stream(ctx) || !ck(ctx, cudaEventRecord(ctx->ev_in, st), "graph stream") ||
+        !ck(ctx, cudaStreamWaitEvent(ctx->gstream, ctx->ev_in, 0), "graph stream"))
+        return DMTS_E_CUDA;
+    const cudaStream_t user_st = st;
+    st = ctx->gstream;
+    const unsigned long long l0 = launch_count();
+    if (!ck(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed), "graph capture")) {
+        st = user_st;
+        return DMTS_E_CUDA;
+    }
+    s = rest_of_call(false);
+    cudaGraph_t gr = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(st, &gr);
+    st = user_st;
+    if (s != DMTS_OK) {
+        if (gr) cudaGraphDestroy(gr);
+        return s;
+    }
+    cudaGraphExec_t gx = nullptr;
+    const bool inst = ce == cudaSuccess && gr && cudaGraphInstantiate(&gx, gr, 0) == cudaSuccess;
+    if (gr) cudaGraphDestroy(gr);
+    if (!inst) return fail(ctx, DMTS_E_CUDA, "respa_step: graph capture of the call failed");
+    si->call_graph = gx;
+    si->call_key = call_key(p, n_outer, stt);   // after the capture: buffers it allocated are in the key
+    si->call_launches = launch_count() - l0;
+    if (!ck(ctx, cudaGraphLaunch(gx, ctx->gstream), "graph launch") ||
+        !ck(ctx, cudaEventRecord(ctx->ev_out, ctx->gstream), "graph stream") ||
+        !ck(ctx, cudaStreamWaitEvent(st, ctx->ev_out, 0), "graph stream"))
+        return DMTS_E_CUDA;
+    return DMTS_OK;
 }
 
 extern "C" {

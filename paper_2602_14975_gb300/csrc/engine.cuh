@@ -16,6 +16,10 @@ struct Buf {
     bool ensure(size_t bytes);
     void release();
 };
+// Counts the library's device (re)allocations and frees: a captured graph
+// recorded with an older value may hold pointers that are no longer valid.
+unsigned long long alloc_generation();
+void bump_alloc_generation();
 
 struct DevModel {
     int L = 0, C = 0, lmax = 0, K = 0, S = 0, nc = 0, nl = 0, p = 0;
@@ -103,6 +107,10 @@ struct StateInternal {
     Buf thermo_part;               // per-part FP64 kinetic-energy sums
     long long cons_cap = 0, nc_cap = 0;
     NbrScratch scratch;
+    // respa_step's cached graph of a short call and what it depends on
+    cudaGraphExec_t call_graph = nullptr;
+    std::vector<uint64_t> call_key;
+    unsigned long long call_launches = 0;
 };
 
 struct ProfSlot {
@@ -191,8 +199,11 @@ SysView state_view(dmts_state *stt);
 RepTable rep_table(const dmts_ctx *ctx);
 void rebuild_lists(dmts_ctx *ctx, StateInternal *si, const SysView &v, cudaStream_t st);
 void state_force_rebuild(dmts_ctx *ctx, dmts_state *stt, cudaStream_t st);
+// cache_short_calls: a call of one or two outer steps may be replayed from
+// the state's cached graph (respa_step; not the serving loop, whose packed
+// batch changes from tick to tick)
 dmts_status respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrator *p, int n_outer, cudaStream_t st,
-                      unsigned *fl_max);
+                      unsigned *fl_max, bool cache_short_calls = false);
 void prepare_nbr_work_async(dmts_ctx *ctx, StateInternal *si, const SysView &v, NbrWork &nw);
 }  // namespace dmts
 

@@ -355,7 +355,7 @@ dmts_status run_replicas(dmts_ctx *ctx, const dmts_request *reqs, int n_req, con
         }
         // ---- one batched outer step for every resident replica
         cudaEventRecord(ev0, st);
-        if ((status = respa_step(ctx, &state, p, 1, st)) != DMTS_OK) break;
+        if ((status = respa_run(ctx, &state, p, 1, st, nullptr)) != DMTS_OK) break;
         cudaEventRecord(ev1, st);
         if (!ck(ctx, cudaEventSynchronize(ev1), "run_replicas: tick")) { status = DMTS_E_CUDA; break; }
         int err = 0;

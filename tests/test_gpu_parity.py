@@ -641,6 +641,30 @@ def test_respa_split_calls_equal_single_call(ctx1, water, mode):
         assert np.array_equal(out[0][2], o[2])
 
 
+def test_cached_call_graph_follows_parameter_changes(ctx1, water):
+    """Calls of one outer step replay a graph the state keeps; a call with
+    other integrator parameters (here the temperature) is captured anew.
+    The trajectory equals the same calls run without any graph (the
+    profiler, when on, keeps every launch direct)."""
+    m, v = _md_setup(water)
+    temps = (300.0, 300.0, 310.0, 310.0, 300.0, 300.0)
+    out = []
+    for direct in (False, True):
+        d = core.DeviceSystem(water)
+        st = core.MDState(d, v, m.astype(np.float32), seeds=5)
+        if direct:
+            core.profile_enable(ctx1, True)
+        for T in temps:
+            core.respa_step(ctx1, st, core.integrator(4.0, 4, T, [1.0] * 5, skin=0.5), 1)
+        ctx1.sync()
+        if direct:
+            core.profile_enable(ctx1, False)
+        out.append((d.x.cpu().numpy(), st.v.cpu().numpy()))
+        st.release()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+
+
 def test_sts_positions_after_10_steps(ctx1, models1, water):
     (cs, cb), _ = models1
     m, v = _md_setup(water)
