@@ -15,7 +15,9 @@
 //   A row c (weights): W_hi[0..7] | W_lo[0..7] | W_hi[0..7] | 0
 //   B row e (edge):    b_hi[0..7] | b_hi[0..7] | b_lo[0..7] | 0
 // (nseg = 1 keeps W_hi alone: hi*hi only). Rows are 128-byte-swizzled
-// K-major tiles, of which the first 64 bytes (two K = 16 steps) are used.
+// K-major tiles: l = 0 and 1 share a weight tile (bytes 0-63 and 64-127 of
+// each row, two K = 16 steps each), and every basis row holds the edge's
+// 64 bytes twice, so that each l's MMA starts at its own half.
 //
 // One CTA of 128 threads owns a TMEM accumulator of 128 columns and
 // processes receivers in cell order (grid-stride). Per receiver, 128
@@ -36,14 +38,15 @@ namespace {
 
 constexpr int TF_C = 128;        // channels = TMEM lanes = threads per CTA
 constexpr int TF_K = 8;          // radial basis functions
-constexpr int TF_PASS = 128;     // candidates tested per pass (one per thread)
+constexpr int TF_PASS = 96;      // candidates tested per pass (one per thread of the first three warps)
 constexpr int TF_CHUNK = 32;     // edges per MMA (N)
 constexpr int TF_TMEM = 128;     // TMEM columns: (l_max + 1) x 32 <= 96
 
 template <int LMAX>
 struct FwdTcSmem {
     static constexpr int NL = LMAX + 1;
-    static constexpr uint32_t a_bytes = NL * TF_C * 128;      // weights, one swizzled tile per l
+    // weights: l = 2j and 2j + 1 share tile j (K-chunks 0-3 and 4-7 of its 128-byte rows)
+    static constexpr uint32_t a_bytes = ((NL + 1) / 2) * TF_C * 128;
     static constexpr uint32_t b_bytes = TF_PASS * 128;        // basis rows of one pass
     static constexpr size_t bytes = a_bytes + b_bytes + 1024;  // + alignment slack
 };
@@ -63,7 +66,7 @@ __device__ __forceinline__ uint4 pack8(const __nv_bfloat16 *v) {
 }
 
 template <int LMAX>
-__global__ void __launch_bounds__(TF_C, 3) k_mp_fwd_tc(EdgeGeom g, LayerIO io, int nseg, int *err) {
+__global__ void __launch_bounds__(TF_C, 4) k_mp_fwd_tc(EdgeGeom g, LayerIO io, int nseg, int *err) {
     using SM = FwdTcSmem<LMAX>;
     constexpr int NL = LMAX + 1, NLM = NL * NL, C = TF_C, K = TF_K;
     extern __shared__ uint8_t tf_smem[];
@@ -95,11 +98,12 @@ __global__ void __launch_bounds__(TF_C, 3) k_mp_fwd_tc(EdgeGeom g, LayerIO io, i
             __nv_bfloat16 hi[K], lo[K];
 #pragma unroll
             for (int k = 0; k < K; ++k) split_bf16(__ldg(io.wrad + (l * K + k) * C + tid), hi[k], lo[k]);
-            uint8_t *t = pA + l * TF_C * 128;
-            st_chunk(t, tid, 0, pack8(hi));
-            st_chunk(t, tid, 1, nseg == 3 ? pack8(lo) : z);
-            st_chunk(t, tid, 2, nseg == 3 ? pack8(hi) : z);
-            st_chunk(t, tid, 3, z);
+            uint8_t *t = pA + (l >> 1) * TF_C * 128;
+            const int c0 = 4 * (l & 1);
+            st_chunk(t, tid, c0, pack8(hi));
+            st_chunk(t, tid, c0 + 1, nseg == 3 ? pack8(lo) : z);
+            st_chunk(t, tid, c0 + 2, nseg == 3 ? pack8(hi) : z);
+            st_chunk(t, tid, c0 + 3, z);
         }
     }
     fence_proxy_async_smem();
@@ -128,7 +132,7 @@ __global__ void __launch_bounds__(TF_C, 3) k_mp_fwd_tc(EdgeGeom g, LayerIO io, i
             // ---- test one candidate per thread, compact the active ones
             const int e = pbeg + tid;
             bool act = false;
-            if (e < end) {
+            if (tid < TF_PASS && e < end) {
                 const int j = __ldg(g.col + e);
                 const float dx = min_img(__ldg(g.x + 3 * j) - xi, bx, ibx);
                 const float dy = min_img(__ldg(g.x + 3 * j + 1) - yi, by, iby);
@@ -166,10 +170,14 @@ __global__ void __launch_bounds__(TF_C, 3) k_mp_fwd_tc(EdgeGeom g, LayerIO io, i
 #pragma unroll
                 for (int k = 0; k < K; ++k) split_bf16(fc * B[k], hi[k], lo[k]);
                 const uint4 h8 = pack8(hi);
-                st_chunk(pB, tid, 0, h8);
-                st_chunk(pB, tid, 1, h8);
-                st_chunk(pB, tid, 2, pack8(lo));
-                st_chunk(pB, tid, 3, make_uint4(0u, 0u, 0u, 0u));
+                const uint4 l8 = pack8(lo), z4 = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+                for (int hh = 0; hh < (NL > 1 ? 2 : 1); ++hh) {   // the basis in both halves of the row
+                    st_chunk(pB, tid, 4 * hh, h8);
+                    st_chunk(pB, tid, 4 * hh + 1, h8);
+                    st_chunk(pB, tid, 4 * hh + 2, l8);
+                    st_chunk(pB, tid, 4 * hh + 3, z4);
+                }
                 float Y[NLM];
                 sph<LMAX>(d.x * inv, d.y * inv, d.z * inv, Y);
 #pragma unroll
@@ -180,7 +188,7 @@ __global__ void __launch_bounds__(TF_C, 3) k_mp_fwd_tc(EdgeGeom g, LayerIO io, i
                 // harmonics, and the receiver's own (finite) features
                 const uint4 z = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) st_chunk(pB, tid, q, z);
+                for (int q = 0; q < 8; ++q) st_chunk(pB, tid, q, z);
 #pragma unroll
                 for (int lm = 0; lm < NLM; ++lm) sY[lm][tid] = 0.f;
                 sJ[tid] = i;
@@ -195,8 +203,8 @@ __global__ void __launch_bounds__(TF_C, 3) k_mp_fwd_tc(EdgeGeom g, LayerIO io, i
                     for (int l = 0; l < NL; ++l)
 #pragma unroll
                         for (int kk = 0; kk < 2; ++kk)
-                            mma_bf16(tmem + l * TF_CHUNK, smem_desc(sA + l * TF_C * 128 + kk * 32),
-                                     smem_desc(sB + q0 * 128 + kk * 32), idesc, kk);
+                            mma_bf16(tmem + l * TF_CHUNK, smem_desc(sA + (l >> 1) * TF_C * 128 + (l & 1) * 64 + kk * 32),
+                                     smem_desc(sB + q0 * 128 + (l & 1) * 64 + kk * 32), idesc, kk);
                     mma_commit(smem_u32(&bar));
                 }
                 // neighbour features of this chunk (padding slots read the
