@@ -136,11 +136,13 @@ __device__ __forceinline__ float rep_pair(const RepTable &t, int si, int sj, flo
 // in 32.32 fixed point with 64-bit integer atomics: integer addition is
 // exact and associative, so F does not depend on the order in which warps
 // add their terms, nor on the skin entries of the list (bit-reproducible
-// alone or batched). k_mean_partial converts F to fp32 and clears it.
+// alone or batched). k_nc_convert converts F to fp32 and clears it.
 // Upper active neighbours (j > a) are taken 16 at a time (the g-th in
 // batch g / 16 on lanes g % 16 and g % 16 + 16): the first lane of each pair
-// bulk-copies the neighbour's q/k row into shared memory while both evaluate
-// the radial part, each forms the dot products of half of the heads.
+// bulk-copies the neighbour's q/k row into shared memory, the second loads
+// the neighbour's tensor-head vectors (its heads), both evaluate the radial
+// part while the row arrives, and each forms the dot products of half of
+// the heads.
 constexpr int NCH_WARPS = 2;
 constexpr float kFixScale = 4294967296.f;     // 2^32 per unit force (kcal/mol/A)
 constexpr float kFixMax = 16777216.f;         // |term| bound (2^24): up to 128 terms fit the 64-bit sums
@@ -189,14 +191,13 @@ struct NCHeadSmem {
     static constexpr int ROWB = QKW * 4;    // bytes copied per row
     static constexpr int BATCH = 16;        // neighbours per staged batch
     static constexpr int HH = (H + 1) / 2;  // heads per lane of a pair
-    static constexpr int VS = nc_v_stride(NL);   // staged V row (floats), a multiple of 16 bytes
+    static constexpr int VS = nc_v_stride(NL);   // V row stride (floats)
     static constexpr size_t rows = (size_t)NCH_WARPS * BATCH * RSTR * 4;
-    static constexpr size_t vrows = (size_t)NCH_WARPS * BATCH * VS * 4;
     static constexpr size_t qk = (size_t)NCH_WARPS * QKW * 4;
     static constexpr size_t vv = (size_t)NCH_WARPS * 4 * NL * 4;
     static constexpr size_t queue = (size_t)NCH_WARPS * 64 * 4;
     static constexpr size_t qdisp = (size_t)NCH_WARPS * 64 * 3 * 4;   // displacement of each queued edge
-    static constexpr size_t bytes = rows + vrows + qk + vv + queue + qdisp + NCH_WARPS * 8;
+    static constexpr size_t bytes = rows + qk + vv + queue + qdisp + NCH_WARPS * 8;
     static_assert(QKW % 16 == 0, "row stride");
     static_assert(HH <= K, "each lane's first heads are Bessel heads");
 };
@@ -209,8 +210,7 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int BATCH = SM::BATCH, HH = SM::HH;
     float *rows = reinterpret_cast<float *>(nch_smem) + (size_t)warp * BATCH * RSTR;
-    float *vrows = reinterpret_cast<float *>(nch_smem + SM::rows) + (size_t)warp * BATCH * SM::VS;
-    unsigned char *rest = nch_smem + SM::rows + SM::vrows;
+    unsigned char *rest = nch_smem + SM::rows;
     float *qa = reinterpret_cast<float *>(rest) + warp * QKW;
     float *va = reinterpret_cast<float *>(rest + SM::qk) + warp * 4 * NL;
     int *queue = reinterpret_cast<int *>(rest + SM::qk + SM::vv) + warp * 64;
@@ -266,12 +266,14 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
         const int qs = (taken + slot) & 63;
         const int j = slot < nb ? queue[qs] : -1;
         fence_proxy_async_smem();      // earlier reads of the rows before the copies overwrite them
-        if (lane == 0) mbar_expect_tx(bar, (uint32_t)nb * (SM::ROWB + SM::VS * 4));
+        if (lane == 0) mbar_expect_tx(bar, (uint32_t)nb * SM::ROWB);
         __syncwarp();
-        if (j >= 0 && half == 0) {
-            bulk_g2s(smem_u32(rows + slot * RSTR), g.QK + (size_t)j * QKW, SM::ROWB, bar);
-            bulk_g2s(smem_u32(vrows + slot * SM::VS), g.V + (size_t)j * SM::VS, SM::VS * 4, bar);
-        }
+        if (j >= 0 && half == 0) bulk_g2s(smem_u32(rows + slot * RSTR), g.QK + (size_t)j * QKW, SM::ROWB, bar);
+        // the neighbour's tensor-head vectors, for the lane of the pair that
+        // owns the tensor heads (plain loads: 12 bytes per head)
+        float vj[3 * NL];
+#pragma unroll
+        for (int q = 0; q < 3 * NL; ++q) vj[q] = (j >= 0 && half == 1) ? __ldg(g.V + (size_t)j * SM::VS + q) : 0.f;
         // radial part of the edge while the rows arrive
         float dx = 0.f, dy = 0.f, dz = 0.f, inv = 1.f, fc = 0.f, Bh[HH], crep = 0.f, r2 = 0.f;
         if (j >= 0) {
@@ -329,12 +331,12 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
                         part[0] = fmaf(caj, Bh[hl], part[0]);
                         part[1] = fmaf(cja, Bh[hl], part[1]);
                     } else {
-                        const int t = h - K;
-                        const float *vjt = vrows + slot * SM::VS + 3 * t;
+                        // tensor heads lie in the second lane's half (HH <= K): t is static
+                        const int t = HH + hl - K;
 #pragma unroll
                         for (int cmp = 0; cmp < 3; ++cmp) {
                             part[2 + cmp] = fmaf(caj, va[3 * t + cmp], part[2 + cmp]);
-                            part[5 + cmp] = fmaf(cja, vjt[cmp], part[5 + cmp]);
+                            part[5 + cmp] = fmaf(cja, vj[3 * t + cmp], part[5 + cmp]);
                         }
                     }
                 }
