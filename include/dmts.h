@@ -341,7 +341,17 @@ typedef struct {
  * (RESPA mode) or n_outer single time steps (STS mode). Forces are cached
  * across calls (first_step). Neighbour lists live in st->internal and are
  * rebuilt on the device when needed. Asynchronous: errors detected on the
- * device surface in dmts_sync().
+ * device surface in dmts_sync(). Ordered after everything already queued on
+ * `stream`, and work queued on `stream` afterwards waits for it. In a call
+ * of three or more outer steps the second is captured into a CUDA graph and
+ * the later ones replay it; a call of one or two outer steps is replayed
+ * from a graph kept in st->internal, recaptured whenever the integrator's
+ * parameters, the number of steps, an array pointer of `st` or any of the
+ * library's device buffers changed (graphs run on a stream of the context,
+ * joined to `stream` by events). The step counters st->step advance by
+ * n_inner (1 in STS mode) at the end of every outer step. The environment
+ * variable DMTS_CUDA_GRAPHS=0 launches every kernel directly instead (the
+ * same kernels and results).
  */
 dmts_status respa_step(dmts_ctx *ctx, dmts_state *st, const dmts_integrator *p, int n_outer,
                        void *stream);
