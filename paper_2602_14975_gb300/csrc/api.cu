@@ -1565,11 +1565,23 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
         cudaGraphExecDestroy(si->call_graph);
         si->call_graph = nullptr;
     }
+    // the captured call must read only the state's own arrays at entry: a
+    // fast force whose mean subtraction is still pending (the first call's
+    // initial forces, in the context's workspace) is stored in st->f_nc now
+    if (mean_pending) {
+        IntegArgs a0 = ia;
+        a0.ops = 0;
+        integrate(a0);
+    }
     if (!ensure_graph_stream(ctx) || !ck(ctx, cudaEventRecord(ctx->ev_in, st), "graph stream") ||
         !ck(ctx, cudaStreamWaitEvent(ctx->gstream, ctx->ev_in, 0), "graph stream"))
         return DMTS_E_CUDA;
     const cudaStream_t user_st = st;
     st = ctx->gstream;
+    // the workspace's species embedding may be another state's by the time
+    // the graph is replayed: the captured call computes its own
+    cons_emb = 0;
+    nc_emb = 0;
     const unsigned long long l0 = launch_count();
     if (!ck(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed), "graph capture")) {
         st = user_st;

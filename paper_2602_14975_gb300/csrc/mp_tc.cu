@@ -19,11 +19,11 @@
 // each row, two K = 16 steps each), and every basis row holds the edge's
 // 64 bytes twice, so that each l's MMA starts at its own half.
 //
-// One CTA of 128 threads owns a TMEM accumulator of 128 columns and
-// processes receivers in cell order (grid-stride). Per receiver, 128
-// candidates of its row at a time are tested; the active ones are compacted
-// into shared memory (basis row for the MMA, Y_lm, neighbour index), then
-// each chunk of 32 is contracted and consumed. Every mbarrier wait is
+// One CTA of 128 threads (four per SM) owns a TMEM accumulator of 128
+// columns and processes receivers in cell order (grid-stride). Per
+// receiver, 96 candidates of its row at a time are tested; the active ones
+// are compacted into shared memory (basis row for the MMA, Y_lm, neighbour
+// index), then each chunk of 32 is contracted and consumed. Every mbarrier wait is
 // bounded: on timeout the CTA records DMTS_E_TIMEOUT, waits (bounded) for
 // the MMAs it issued, frees its tensor memory and returns.
 #include <algorithm>

@@ -665,6 +665,39 @@ def test_cached_call_graph_follows_parameter_changes(ctx1, water):
     assert np.array_equal(out[0][1], out[1][1])
 
 
+def test_cached_call_graphs_of_two_states_sharing_a_context(ctx1, water):
+    """Two states of the same size but different species order (the water
+    box and its atoms in reverse order) alternate one-step calls on one
+    context: each replays its own cached graph, which computes its own
+    species embedding (the context's workspace holds the other state's by
+    then). Positions equal those of the same calls without graphs."""
+    n = water.n_atoms
+    rev = S.System(water.name + "_rev", water.x[::-1].copy(), water.species[::-1].copy(),
+                   water.mol_id[::-1].copy(), (n - 1 - water.bonds).astype(np.int32), water.bond_r0.copy(),
+                   water.box)
+    out = []
+    for direct in (False, True):
+        states = []
+        for sy in (water, rev):
+            m, v = _md_setup(sy)
+            d = core.DeviceSystem(sy)
+            states.append((d, core.MDState(d, v, m.astype(np.float32), seeds=3)))
+        if direct:
+            core.profile_enable(ctx1, True)
+        integ = core.integrator(4.0, 4, 300.0, [1.0] * 5, skin=0.5)
+        for _ in range(3):
+            for _, st in states:
+                core.respa_step(ctx1, st, integ, 1)
+        ctx1.sync()
+        if direct:
+            core.profile_enable(ctx1, False)
+        out.append([d.x.cpu().numpy() for d, _ in states])
+        for _, st in states:
+            st.release()
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
+
+
 def test_sts_positions_after_10_steps(ctx1, models1, water):
     (cs, cb), _ = models1
     m, v = _md_setup(water)
