@@ -797,6 +797,33 @@ def test_bf16_tensor_core_path(which):
     assert np.abs(F32.cpu().numpy() - Fo).max() <= TOL_F32 * np.abs(Fo).max()
 
 
+def test_tensor_core_forward_layer_over_several_passes():
+    """The forward layer's tensor-core kernel tests a row's candidates 96 at
+    a time and contracts the active ones 32 at a time: with a 7.5 A list
+    (about 180 candidates per row, two passes, chunks cut at pass
+    boundaries) the message-passing force meets the split-bf16 bar against
+    the oracle, and differs from the 5.5 A list's only by the order of the
+    forward's fp32 sums (relative 1e-7) carried through the split-bf16
+    contractions, whose lo parts resolve 2^-16: within 2e-4 of the RMS."""
+    sy = S.solvated_chain(n_chain=300, n_water=900, box_len=31.0, seed=9)
+    cs = S.cons_spec(3, 128, 2, bf16=True)
+    cb = S.cons_weights(cs, 302)
+    ctx = core.Context(cons=(cs, cb))
+    d = core.DeviceSystem(sy)
+    _, Fo = O.cons_energy_forces(sy, cs, cb)
+    out = []
+    for r_list in (5.5, 7.5):
+        nb = core.nbr_build(ctx, d, r_list)
+        if r_list == 7.5:
+            rp = nb.row_ptr.cpu().numpy()
+            assert np.diff(rp).max() > 96   # rows of two or more passes
+        _, F = core.energy_forces_cons(ctx, d, nb, with_prior=False)
+        out.append(F.cpu().numpy())
+    for F in out:
+        assert np.abs(F - Fo).max() <= TOL_BF16_RMS * _rms(Fo), (np.abs(F - Fo).max() / _rms(Fo))
+    assert np.abs(out[0] - out[1]).max() <= 2e-4 * _rms(Fo), np.abs(out[0] - out[1]).max() / _rms(Fo)
+
+
 def test_bf16_plain_is_coarser():
     """DMTS_BF16_PLAIN (one bf16 rounding per operand, hi*hi products only)
     runs the same kernels with a third of the tensor-core work: its
