@@ -45,19 +45,27 @@ void launch_rowsum(int n, int C, const float *u, float scale, float *e_atom, cud
 // Bond entry q of atom a (d = x_j - x_a): the force on a, k (r - r0) d / r,
 // its energy and pair-form virial. The same bond seen from j gives exactly
 // the opposite force (d exactly negated, the same r and factor).
+// Harmonic bond term of atom a with its partner at (xj, yj, zj), rest length r0.
+__device__ __forceinline__ void bond_term_at(float k, float xj, float yj, float zj, float r0, float xa, float ya,
+                                             float za, float bx, float by, float bz, float ibx, float iby, float ibz,
+                                             float &gx, float &gy, float &gz, float &e, float &w) {
+    const float dx = min_img(xj - xa, bx, ibx);
+    const float dy = min_img(yj - ya, by, iby);
+    const float dz = min_img(zj - za, bz, ibz);
+    const float r = sqrtf(dx * dx + dy * dy + dz * dz);
+    const float dr = r - r0;
+    const float g = k * dr / r;
+    gx = g * dx; gy = g * dy; gz = g * dz;
+    e = 0.25f * k * dr * dr;              // each bond is listed by both atoms
+    w = 0.5f * g * r * r;                 // pair-form virial, half per listed direction
+}
+
 __device__ __forceinline__ void bond_term(const BondTable &b, const float *x, int q, float xa, float ya, float za,
                                           float bx, float by, float bz, float ibx, float iby, float ibz, float &gx,
                                           float &gy, float &gz, float &e, float &w) {
     const int j = b.idx[q];
-    const float dx = min_img(x[3 * j] - xa, bx, ibx);
-    const float dy = min_img(x[3 * j + 1] - ya, by, iby);
-    const float dz = min_img(x[3 * j + 2] - za, bz, ibz);
-    const float r = sqrtf(dx * dx + dy * dy + dz * dz);
-    const float dr = r - b.r0[q];
-    const float g = b.k * dr / r;
-    gx = g * dx; gy = g * dy; gz = g * dz;
-    e = 0.25f * b.k * dr * dr;            // each bond is listed by both atoms
-    w = 0.5f * g * r * r;                 // pair-form virial, half per listed direction
+    bond_term_at(b.k, x[3 * j], x[3 * j + 1], x[3 * j + 2], b.r0[q], xa, ya, za, bx, by, bz, ibx, iby, ibz, gx, gy, gz,
+                 e, w);
 }
 
 __device__ __forceinline__ void bond_force(const BondTable &b, const float *x, int a, float bx, float by,
@@ -253,6 +261,21 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
         if (nbp > 4) return is_bonded(g.bonds, a, j);
         return j == bp[0] || j == bp[1] || j == bp[2] || j == bp[3];
     };
+    // a's bonds (one per lane): partner position and rest length, loaded now
+    // so that their latency overlaps the pairs' work
+    int nbond = 0;
+    float bjx = 0.f, bjy = 0.f, bjz = 0.f, br0 = 0.f;
+    if (g.bonds.ptr) {
+        const int q0 = g.bonds.ptr[a];
+        nbond = g.bonds.ptr[a + 1] - q0;
+        if (lane < nbond) {
+            const int jb = __ldg(g.bonds.idx + q0 + lane);
+            bjx = __ldg(g.x + 3 * jb);
+            bjy = __ldg(g.x + 3 * jb + 1);
+            bjz = __ldg(g.x + 3 * jb + 2);
+            br0 = __ldg(g.bonds.r0 + q0 + lane);
+        }
+    }
     long long ox = 0, oy = 0, oz = 0;     // this lane's share of a's side of its pairs, fixed point
     float wv = 0.f;                       // virial proxy: (F_aj - F_ja) . d_aj (+ repulsion) over a's pairs
     bool bad = false;                     // a pair term outside the fixed-point range (or not finite)
@@ -398,9 +421,12 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
     float w = wv;
     if (g.bonds.ptr) {
         // bonds in fixed point too: the two ends' terms cancel exactly
-        for (int q = g.bonds.ptr[a] + lane; q < g.bonds.ptr[a + 1]; q += 32) {
+        for (int q = lane; q < nbond; q += 32) {
             float gx, gy, gz, eq, wq;
-            bond_term(g.bonds, g.x, q, xa, ya, za, bx, by, bz, ibx, iby, ibz, gx, gy, gz, eq, wq);
+            if (q < 32)   // the prefetched bond of this lane
+                bond_term_at(g.bonds.k, bjx, bjy, bjz, br0, xa, ya, za, bx, by, bz, ibx, iby, ibz, gx, gy, gz, eq, wq);
+            else
+                bond_term(g.bonds, g.x, g.bonds.ptr[a] + q, xa, ya, za, bx, by, bz, ibx, iby, ibz, gx, gy, gz, eq, wq);
             if (fabsf(gx) < kFixMax && fabsf(gy) < kFixMax && fabsf(gz) < kFixMax) {
                 ox += to_fix(gx); oy += to_fix(gy); oz += to_fix(gz);
             } else {
