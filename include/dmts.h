@@ -348,10 +348,11 @@ typedef struct {
  * from a graph kept in st->internal, recaptured whenever the integrator's
  * parameters, the number of steps, an array pointer of `st` or any of the
  * library's device buffers changed (graphs run on a stream of the context,
- * joined to `stream` by events). The step counters st->step advance by
- * n_inner (1 in STS mode) at the end of every outer step. The environment
- * variable DMTS_CUDA_GRAPHS=0 launches every kernel directly instead (the
- * same kernels and results).
+ * joined to `stream` by events). Should a capture or its instantiation
+ * fail, the call runs its launches directly and the context does so from
+ * then on. The step counters st->step advance by n_inner (1 in STS mode) at
+ * the end of every outer step. The environment variable DMTS_CUDA_GRAPHS=0
+ * launches every kernel directly instead (the same kernels and results).
  */
 dmts_status respa_step(dmts_ctx *ctx, dmts_state *st, const dmts_integrator *p, int n_outer,
                        void *stream);

@@ -1339,8 +1339,8 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
     // integrator's parameters, the number of steps, every array of the state
     // and the generation of the library's device allocations, so a graph is
     // never replayed on arrays that moved or were freed.
-    const bool cache_call =
-        cache_short_calls && n_outer <= 2 && !ctx->prof.on && !stt->thermo_trace && !fl_max && graphs_enabled();
+    const bool cache_call = cache_short_calls && n_outer <= 2 && !ctx->prof.on && !stt->thermo_trace && !fl_max &&
+                            graphs_enabled() && !ctx->graphs_off;
     if (cache_call && si->call_graph && si->call_key == call_key(p, n_outer, stt)) {
         if (!ensure_graph_stream(ctx) || !ck(ctx, cudaEventRecord(ctx->ev_in, st), "graph stream") ||
             !ck(ctx, cudaStreamWaitEvent(ctx->gstream, ctx->ev_in, 0), "graph stream") ||
@@ -1486,7 +1486,7 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
         // Outer steps after the first are replayed from a CUDA graph captured
         // from the second (calls of three or more steps; not with a per-step
         // trace, whose row changes, nor on the steps a sampling profiler times).
-        const bool graphs = step_graphs && n_outer >= 3 && !stt->thermo_trace && graphs_enabled();
+        const bool graphs = step_graphs && n_outer >= 3 && !stt->thermo_trace && graphs_enabled() && !ctx->graphs_off;
         if (graphs && !ensure_graph_stream(ctx)) return DMTS_E_CUDA;
         // the outer steps run on the context's graph stream, after everything
         // the caller's stream holds; on every way out, the caller's stream waits
@@ -1517,12 +1517,13 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
             st = ctx->gstream;
             sj.on = true;
         }
+        bool graphs_now = graphs;
         for (int o = 0; o < n_outer; ++o) {
             if (ctx->prof.on) {
                 ctx->prof.active = ctx->prof.every <= 1 || ctx->prof.outer % ctx->prof.every == 0;
                 ctx->prof.outer++;
             }
-            const bool replayable = graphs && o > 0 && !(ctx->prof.on && ctx->prof.active);
+            const bool replayable = graphs_now && o > 0 && !(ctx->prof.on && ctx->prof.active);
             if (replayable && gx) {
                 if (!ck(ctx, cudaGraphLaunch(gx, st), "graph launch")) return DMTS_E_CUDA;
                 count_launches(gx_launches);
@@ -1542,8 +1543,14 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
                 const bool inst = ce == cudaSuccess && gr && cudaGraphInstantiate(&gx, gr, 0) == cudaSuccess;
                 if (gr) cudaGraphDestroy(gr);
                 if (!inst) {
+                    // nothing ran while capturing: this context launches directly from now on
                     gx = nullptr;
-                    return fail(ctx, DMTS_E_CUDA, "respa_step: graph capture of an outer step failed");
+                    cudaGetLastError();
+                    ctx->graphs_off = true;
+                    graphs_now = false;
+                    s = outer_step(o);
+                    if (s != DMTS_OK) return s;
+                    continue;
                 }
                 gx_launches = launch_count() - l0;
                 if (!ck(ctx, cudaGraphLaunch(gx, st), "graph launch")) return DMTS_E_CUDA;
@@ -1598,7 +1605,13 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
     cudaGraphExec_t gx = nullptr;
     const bool inst = ce == cudaSuccess && gr && cudaGraphInstantiate(&gx, gr, 0) == cudaSuccess;
     if (gr) cudaGraphDestroy(gr);
-    if (!inst) return fail(ctx, DMTS_E_CUDA, "respa_step: graph capture of the call failed");
+    if (!inst) {
+        // nothing ran while capturing: run the call directly, and launch
+        // directly in this context from now on
+        cudaGetLastError();
+        ctx->graphs_off = true;
+        return rest_of_call(false);
+    }
     si->call_graph = gx;
     si->call_key = call_key(p, n_outer, stt);   // after the capture: buffers it allocated are in the key
     si->call_launches = launch_count() - l0;

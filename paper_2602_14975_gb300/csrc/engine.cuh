@@ -170,6 +170,7 @@ struct dmts_ctx {
     // whatever the caller's), joined to the caller's stream by two events
     cudaStream_t gstream = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    bool graphs_off = false;   // a capture or instantiation failed once: launch directly
 };
 
 namespace dmts {
