@@ -1564,7 +1564,7 @@ dmts_status dmts::respa_run(dmts_ctx *ctx, dmts_state *stt, const dmts_integrato
             ia.ops = sts ? OP_CLOSE_B : (OP_CLOSE_B | OP_KICK_L);
             { ProfScope ps(ctx, "integrate", st); integrate(ia); }
         }
-    if (stt->thermo && !stt->thermo_trace) thermo(false, nullptr);
+        if (stt->thermo && !stt->thermo_trace) thermo(false, nullptr);
         return ck(ctx, cudaGetLastError(), "respa_step launch") ? DMTS_OK : DMTS_E_CUDA;
     };
     if (!cache_call) return rest_of_call(true);
