@@ -847,11 +847,15 @@ def main():
     flop_method = {"mp_fwd": 2 * (cs.K * nl1 + nlm) * C}
     flop_method["mp_bwd"] = 2 * flop_method["mp_fwd"]
     # what the kernels execute per active edge (each FMA 2 FLOP): forward
-    # 36 FMA per channel; adjoint 99 per channel (87 in layer 0, which has no
-    # sender-role gradient) plus 30 per lane for the direction derivatives,
-    # averaged over the L launches of one evaluation
+    # 36 FMA per channel; the adjoint forms each pair once, from its lower
+    # atom: 99 FMA per channel (87 in layer 0, which has no sender-role
+    # gradient), 30 per lane for the direction derivatives and 93 adds for
+    # the lanes' sum of the pair force, and the lower atom's sender-role
+    # term of the reverse edge takes 36 per channel (none in layer 0), so a
+    # directed edge averages half of a pair; averaged over the L launches of
+    # one evaluation
     flop_kernel = {"mp_fwd": 2 * 36 * C,
-                   "mp_bwd": (2 * 99 * C * (Lc - 1) + 2 * 87 * C) / Lc + 2 * 30 * 32}
+                   "mp_bwd": ((99 + 36) * C * (Lc - 1) + 87 * C) / Lc + 30 * 32 + 93 / 2}
     # a split-bf16 model with C = 128 runs the forward's radial contraction
     # on the tensor cores (three bf16 MMAs per product, K = 8): 12 FMA per
     # channel stay on the CUDA cores

@@ -280,7 +280,9 @@ dmts_status cons_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const
         !w.act.ensure(sizeof(float) * nc_) || !w.u.ensure(sizeof(float) * nc_) || !w.gz.ensure(sizeof(float) * nc_) ||
         !w.gs0.ensure(sizeof(float) * nc_) || !w.gs1.ensure(sizeof(float) * nc_) ||
         !w.gA.ensure(sizeof(float) * nc_ * NLM) || !w.e_atom.ensure(sizeof(float) * (N + 1)) ||
-        !w.ftmp.ensure(sizeof(float) * 3 * (N + 1)) || (virial && !w.cons_w.ensure(sizeof(float) * (N + 1))))
+        !w.ftmp.ensure(sizeof(float) * 3 * (N + 1)) || (virial && !w.cons_w.ensure(sizeof(float) * (N + 1))) ||
+        (forces && !ensure_zeroed(ctx, w.cons_ffix, sizeof(unsigned long long) * 3 * (N + 1), st)) ||
+        (forces && virial && !ensure_zeroed(ctx, w.cons_wfix, sizeof(unsigned long long) * (N + 1), st)))
         return fail(ctx, DMTS_E_OOM, "workspace allocation failed");
     // split-bf16 copies: 4 bytes per logical element (hi and lo)
     if (bf && (!w.q_bf.ensure(4 * nc_ * NL + 16) || !w.act_bf.ensure(4 * nc_ + 16) || !w.s_bf.ensure(4 * nc_ + 16) ||
@@ -367,14 +369,18 @@ dmts_status cons_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const
             io.gs_in = gin;
             io.gs_out = t > 0 ? gout : nullptr;   // layer 0's inputs are the species embedding
             io.gs_out_bf16 = t > 0 ? gout_bf : nullptr;
-            io.F = forces;
-            io.accumulate = t != L - 1;
-            io.W = virial ? (float *)w.cons_w.p : nullptr;
+            io.Ffix = (unsigned long long *)w.cons_ffix.p;
+            io.Wfix = virial ? (unsigned long long *)w.cons_wfix.p : nullptr;
             io.err = ctx->d_err;
             { ProfScope ps(ctx, "mp_bwd", st); launch_mp_bwd(C, m.lmax, m.K, g, io, st); }
             std::swap(gin, gout);
             std::swap(gin_bf, gout_bf);
         }
+        // the layers' fixed-point sums -> F (and the virial), cleared
+        ProfScope ps(ctx, "fix_convert", st);
+        launch_fix_convert(N, (unsigned long long *)w.cons_ffix.p, forces,
+                           virial ? (unsigned long long *)w.cons_wfix.p : nullptr,
+                           virial ? (float *)w.cons_w.p : nullptr, st);
     }
     if (flags & DMTS_WITH_PRIOR) {
         PriorArgs pa;

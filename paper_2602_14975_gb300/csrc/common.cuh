@@ -47,6 +47,19 @@ __device__ __forceinline__ void st_split(__nv_bfloat16 *base, size_t r, int K, i
     base[r * 2 * K + K + c] = lo;
 }
 
+// Force sums in 32.32 fixed point with 64-bit integer atomics: integer
+// addition is exact and associative, so a sum does not depend on the order
+// in which warps add their terms. A term must be finite and at most kFixMax
+// in magnitude (2^24: up to 128 such terms fit the 64-bit sum).
+constexpr float kFixScale = 4294967296.f;     // 2^32 per unit
+constexpr float kFixMax = 16777216.f;
+__device__ __forceinline__ bool fix_ok(float v) { return fabsf(v) < kFixMax; }   // false for NaN too
+__device__ __forceinline__ long long to_fix(float v) { return __float2ll_rn(v * kFixScale); }
+__device__ __forceinline__ void fix_add(unsigned long long *dst, long long q) {
+    atomicAdd(dst, (unsigned long long)q);
+}
+__device__ __forceinline__ float fix_to_float(long long q) { return (float)((double)q * (1.0 / 4294967296.0)); }
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(DMTS_FULL, v, o);

@@ -67,6 +67,7 @@ struct Workspace {
     Buf ms_scratch;   // per-part sums of the mean subtraction
     Buf nc_w;         // per-atom virial proxy of the fast force
     Buf cons_w;       // per-atom virial of the conservative force
+    Buf cons_ffix, cons_wfix;   // the adjoint's forces and virial in 32.32 fixed point, zero between evaluations
     Buf nc_w_last;    // per-replica fast-force virial of the last inner step
     // distillation of the NC model: residual, q/k-row and feature gradients,
     // pre-activation, blob-shaped weight gradient, Adam moments, split sums
@@ -76,7 +77,7 @@ struct Workspace {
         Buf *all[] = {&s, &A, &q, &h, &act, &u, &gz, &gs0, &gs1, &gA, &e_atom, &ftmp, &atom_rep,
                       &nc_s, &nc_q, &nc_act, &nc_qk, &nc_v, &nc_f, &nc_ffix, &nc_sum,
                       &q_bf, &act_bf, &s_bf, &gz_bf, &gs0_bf, &gs1_bf, &nc_q_bf, &nc_act_bf, &nc_s_bf,
-                      &ms_scratch, &nc_w, &cons_w, &nc_w_last,
+                      &ms_scratch, &nc_w, &cons_w, &cons_ffix, &cons_wfix, &nc_w_last,
                       &dist_F, &dist_g, &dist_sq, &dist_gqk, &dist_gs1, &dist_gh, &dist_h, &dist_dw,
                       &adam_m, &adam_v, &dist_part, &dist_A, &dist_gq, &dist_gv};
         for (Buf *b : all) b->release();

@@ -151,18 +151,10 @@ __device__ __forceinline__ float rep_pair(const RepTable &t, int si, int sj, flo
 // the neighbour's tensor-head vectors (its heads), both evaluate the radial
 // part while the row arrives, and each forms the dot products of half of
 // the heads.
-constexpr int NCH_WARPS = 2;
-constexpr float kFixScale = 4294967296.f;     // 2^32 per unit force (kcal/mol/A)
-constexpr float kFixMax = 16777216.f;         // |term| bound (2^24): up to 128 terms fit the 64-bit sums
-
-__device__ __forceinline__ long long to_fix(float v) { return __float2ll_rn(v * kFixScale); }
-__device__ __forceinline__ void fix_add(unsigned long long *dst, long long q) {
-    atomicAdd(dst, (unsigned long long)q);
-}
+constexpr int NCH_WARPS = 1;
 __device__ __forceinline__ double fix_sum_to_double(unsigned long long s) {
     return (double)(long long)s * (1.0 / 4294967296.0);   // exact for |s| < 2^53
 }
-__device__ __forceinline__ float fix_to_float(long long q) { return (float)((double)q * (1.0 / 4294967296.0)); }
 // Mean force of replica r from its exact fixed-point sum (FP64, as used by
 // the subtraction).
 // The sums of the head's forces cancel exactly (every term enters two atoms

@@ -1,7 +1,8 @@
 // Message-passing layer: edge embedding (Bessel x envelope, real SH),
 // segmented scatter-sum with one warp per receiver, and the adjoint (forces
-// and feature gradients) written as an atomic-free gather over the symmetric
-// neighbour list. Node-level MLP contractions: SIMT fp32 GEMM with fused
+// and feature gradients): each pair's force once, from its lower atom, in
+// fixed point; each atom's sender-role gradient gathered over its row of the
+// symmetric neighbour list. Node-level MLP contractions: SIMT fp32 GEMM with fused
 // epilogues.
 #include <type_traits>
 
@@ -214,18 +215,34 @@ __global__ void __launch_bounds__(MP_WARPS * 32) k_mp_fwd(EdgeGeom g, LayerIO io
 }
 
 // ----------------------------------------------------------------- adjoint
-// For atom a and each neighbour j (n = n_aj, r = r_aj), with
+// For atom a and a neighbour j (n = n_aj, r = r_aj), with
 //   Gam[c][lm] = gA_a[lm][c] s_j[c] + (-1)^l gA_j[lm][c] s_a[c],
-// the force is F_a = nu sum_j ( rho n + sum_lm beta_lm dY_lm/dd ), where
+// the pair's force on a (both edges a <- j and j <- a) is
+//   f_aj = nu ( rho n + sum_lm beta_lm dY_lm/dd ),
 //   rho = sum_c sum_l R'_lc sum_m Gam Y_lm,  beta_lm = sum_c Gam R_lc,
 // and the feature gradient of the sender role is
 //   g_s_a[c] += nu sum_j sum_l (-1)^l R_lc sum_m gA_j[lm][c] Y_lm.
-// (Edge j->a has d_ja = -d_aj, Y_lm(-n) = (-1)^l Y_lm(n).)
+// Edge j -> a has d_ja = -d_aj and Y_lm(-n) = (-1)^l Y_lm(n), so
+// Gam_ja = (-1)^l Gam_aj and dY_lm/dd at -d is -(-1)^l dY_lm/dd at d: the
+// pair terms are antisymmetric, f_ja = -f_aj. Each pair's force is formed
+// once, by the warp of its lower atom a < j, and enters F_a with + and F_j
+// with -, in 32.32 fixed point (exact, order-independent sums; every pair's
+// two terms cancel exactly), and so does its virial term. A lower
+// neighbour j < a contributes only its sender-role term to g_s_a (R, no R',
+// no force), and nothing in a layer without that gradient.
 //
 // Shared memory per block (dynamic: above the 48 KB static limit at C = 128,
 // l_max = 2): per warp 32 edge records of packs (f_c B_k, its r-derivative,
 // Y_lm) and of scalars (dY_lm/dd, n, and r for the virial), the receiver's
-// gA_a as packs, and the 32 neighbour indices.
+// gA_a as packs, the 32 neighbour indices, and the lanes' shares of the
+// force of FT pairs (transposed so that one lane adds up each pair).
+constexpr int FT = 16;   // pairs per force reduction
+// One warp per block: how many upper neighbours an atom has varies from atom
+// to atom, and a block keeps its registers and shared memory until its
+// slowest warp is done, so single-warp blocks keep the SM's eight warp slots
+// busy (255 registers a thread allow eight warps per SM either way).
+constexpr int BWD_WARPS = 1;
+
 template <int C, int LMAX, int K, bool VIR>
 struct BwdSmem {
     static constexpr int NL = LMAX + 1, NLM = NL * NL, CPW = C / 32;
@@ -233,17 +250,19 @@ struct BwdSmem {
     static constexpr int NP = Pack<CPW>::NP;
     static constexpr int RS = (2 * K + NLM) | 1;
     static constexpr int GS = (3 * NLM + 3 + (VIR ? 1 : 0)) | 1;
-    static constexpr size_t r_bytes = sizeof(T) * MP_WARPS * 32 * RS;
-    static constexpr size_t ga_bytes = sizeof(T) * MP_WARPS * NLM * NP * 32;
-    static constexpr size_t g_bytes = sizeof(float) * MP_WARPS * 32 * GS;
-    static constexpr size_t bytes = r_bytes + ga_bytes + g_bytes + sizeof(int) * MP_WARPS * 32;
+    static constexpr size_t r_bytes = sizeof(T) * BWD_WARPS * 32 * RS;
+    static constexpr size_t ga_bytes = sizeof(T) * BWD_WARPS * NLM * NP * 32;
+    static constexpr size_t g_bytes = sizeof(float) * BWD_WARPS * 32 * GS;
+    static constexpr size_t j_bytes = sizeof(int) * BWD_WARPS * 32;
+    static constexpr size_t f_bytes = sizeof(float) * BWD_WARPS * 3 * FT * 33;
+    static constexpr size_t bytes = r_bytes + ga_bytes + g_bytes + j_bytes + f_bytes;
 };
 
 // SG = false (io.gs_out == nullptr) skips the sender-role gradient: the
 // first layer's input features are the species embedding, constant in the
 // positions, so nothing consumes it there.
 template <int C, int LMAX, int K, bool VIR, bool SG>
-__global__ void __launch_bounds__(MP_WARPS * 32) k_mp_bwd(EdgeGeom g, LayerIO io) {
+__global__ void __launch_bounds__(BWD_WARPS * 32) k_mp_bwd(EdgeGeom g, LayerIO io) {
     using S = BwdSmem<C, LMAX, K, VIR>;
     using T = typename S::T;
     constexpr int NL = S::NL, NLM = S::NLM, CPW = S::CPW, NP = S::NP, PW = Pack<CPW>::W;
@@ -254,7 +273,9 @@ __global__ void __launch_bounds__(MP_WARPS * 32) k_mp_bwd(EdgeGeom g, LayerIO io
     T (*sh_ga)[NP * 32] = reinterpret_cast<T (*)[NP * 32]>(mp_smem + S::r_bytes) + warp * NLM;
     float (*sh_g)[GS] = reinterpret_cast<float (*)[GS]>(mp_smem + S::r_bytes + S::ga_bytes) + warp * 32;
     int *sh_j = reinterpret_cast<int *>(mp_smem + S::r_bytes + S::ga_bytes + S::g_bytes) + warp * 32;
-    const int wa = blockIdx.x * MP_WARPS + warp;
+    float (*sh_f)[FT][33] =
+        reinterpret_cast<float (*)[FT][33]>(mp_smem + S::r_bytes + S::ga_bytes + S::g_bytes + S::j_bytes) + warp * 3;
+    const int wa = blockIdx.x * BWD_WARPS + warp;
     if (wa >= g.n_atoms || *io.err) return;
     const int a = g.order ? __ldg(g.order + wa) : wa;
 
@@ -278,7 +299,9 @@ __global__ void __launch_bounds__(MP_WARPS * 32) k_mp_bwd(EdgeGeom g, LayerIO io
         gse[p] = vdup<T>(0.f);
         gso[p] = vdup<T>(0.f);
     }
-    float fx = 0.f, fy = 0.f, fz = 0.f, wv = 0.f;
+    // a's side of its pairs, fixed point (on the lanes that add up a pair)
+    long long oa[3] = {0, 0, 0}, ow = 0;
+    bool bad = false;   // a pair term outside the fixed-point range (or not finite)
 
     const int rep = g.atom_rep[a];
     const float bx = g.box[3 * rep], by = g.box[3 * rep + 1], bz = g.box[3 * rep + 2];
@@ -300,9 +323,16 @@ __global__ void __launch_bounds__(MP_WARPS * 32) k_mp_bwd(EdgeGeom g, LayerIO io
             r2 = dx * dx + dy * dy + dz * dz;
             act = r2 < rc2;
         }
-        const unsigned m = __ballot_sync(DMTS_FULL, act);
-        if (act) {
-            const int pos = __popc(m & ((1u << lane) - 1u));
+        // lower neighbours (j < a) first, then the upper ones (the pairs this
+        // warp owns): rows are ascending, so g_s_a takes its terms in row
+        // order whatever the chunk boundaries (which move with the list's
+        // skin entries)
+        const bool up = act && j > a, lo = SG && act && j < a;
+        const unsigned mu = __ballot_sync(DMTS_FULL, up), ml = __ballot_sync(DMTS_FULL, lo);
+        const int n_up = __popc(mu), n_lo = __popc(ml);
+        if (up || lo) {
+            const unsigned lt = (1u << lane) - 1u;
+            const int pos = lo ? __popc(ml & lt) : n_lo + __popc(mu & lt);
             T *rec = sh_r[pos];
             float *ge = sh_g[pos];
             const float r = sqrtf(r2), inv = 1.f / r;
@@ -331,84 +361,168 @@ __global__ void __launch_bounds__(MP_WARPS * 32) k_mp_bwd(EdgeGeom g, LayerIO io
             sh_j[pos] = j;
         }
         __syncwarp();
-        const int na = __popc(m);
+        if (SG) {
+            // lower neighbours: the sender-role gradient only
 #pragma unroll 2
-        for (int t = 0; t < na; ++t) {
-            const int jt = sh_j[t];
-            const T *rec = sh_r[t];
-            const float *ge = sh_g[t];
-            T sj[NP];
-            ldp<CPW>(io.s + (size_t)jt * C + lane * CPW, sj);
-            T gj[NLM][NP];
+            for (int t = 0; t < n_lo; ++t) {
+                const int jt = sh_j[t];
+                const T *rec = sh_r[t];
+                T gj[NLM][NP];
 #pragma unroll
-            for (int lm = 0; lm < NLM; ++lm) ldp<CPW>(io.gA + ((size_t)jt * NLM + lm) * C + lane * CPW, gj[lm]);
-            T y[NLM];
+                for (int lm = 0; lm < NLM; ++lm) ldp<CPW>(io.gA + ((size_t)jt * NLM + lm) * C + lane * CPW, gj[lm]);
 #pragma unroll
-            for (int lm = 0; lm < NLM; ++lm) y[lm] = rec[2 * K + lm];
-            T rho = vdup<T>(0.f), beta[NLM];
+                for (int p = 0; p < NP; ++p) {
 #pragma unroll
-            for (int lm = 0; lm < NLM; ++lm) beta[lm] = vdup<T>(0.f);
+                    for (int l = 0; l < NL; ++l) {
+                        T s0 = vdup<T>(0.f), s2 = vdup<T>(0.f);
 #pragma unroll
-            for (int p = 0; p < NP; ++p) {
-                T R[NL], Rp[NL];
+                        for (int k = 0; k < K; k += 2) {
+                            s0 = vfma(W[l][k][p], rec[k], s0);
+                            s2 = vfma(W[l][k + 1][p], rec[k + 1], s2);
+                        }
+                        const T R = vadd(s0, s2);
+                        T wl = vdup<T>(0.f);
 #pragma unroll
-                for (int l = 0; l < NL; ++l) {
-                    T s0 = vdup<T>(0.f), s1 = vdup<T>(0.f), s2 = vdup<T>(0.f), s3 = vdup<T>(0.f);
-#pragma unroll
-                    for (int k = 0; k < K; k += 2) {
-                        s0 = vfma(W[l][k][p], rec[k], s0);
-                        s1 = vfma(W[l][k][p], rec[K + k], s1);
-                        s2 = vfma(W[l][k + 1][p], rec[k + 1], s2);
-                        s3 = vfma(W[l][k + 1][p], rec[K + k + 1], s3);
-                    }
-                    R[l] = vadd(s0, s2);
-                    Rp[l] = vadd(s1, s3);
-                }
-#pragma unroll
-                for (int l = 0; l < NL; ++l) {
-                    const T sas = (l & 1) ? san[p] : sa[p];
-                    T tl = vdup<T>(0.f), wl = vdup<T>(0.f);
-#pragma unroll
-                    for (int lm = l * l; lm < (l + 1) * (l + 1); ++lm) {
-                        const T gam = vfma(sh_ga[lm][p * 32 + lane], sj[p], vmul(gj[lm][p], sas));
-                        tl = vfma(gam, y[lm], tl);
-                        beta[lm] = vfma(gam, R[l], beta[lm]);
-                        if (SG) wl = vfma(gj[lm][p], y[lm], wl);
-                    }
-                    rho = vfma(Rp[l], tl, rho);
-                    if (SG) {
-                        if (l & 1) gso[p] = vfma(R[l], wl, gso[p]);
-                        else gse[p] = vfma(R[l], wl, gse[p]);
+                        for (int lm = l * l; lm < (l + 1) * (l + 1); ++lm) wl = vfma(gj[lm][p], rec[2 * K + lm], wl);
+                        if (l & 1) gso[p] = vfma(R, wl, gso[p]);
+                        else gse[p] = vfma(R, wl, gse[p]);
                     }
                 }
             }
-            const float rh = vsum(rho);
-            float ex = rh * ge[3 * NLM], ey = rh * ge[3 * NLM + 1], ez = rh * ge[3 * NLM + 2];
+        }
+        for (int t0 = n_lo; t0 < n_lo + n_up; t0 += FT) {
+            const int t1 = min(n_lo + n_up, t0 + FT);
+#pragma unroll 2
+            for (int t = t0; t < t1; ++t) {
+                const int jt = sh_j[t];
+                const T *rec = sh_r[t];
+                const float *ge = sh_g[t];
+                T sj[NP];
+                ldp<CPW>(io.s + (size_t)jt * C + lane * CPW, sj);
+                T gj[NLM][NP];
 #pragma unroll
-            for (int lm = 1; lm < NLM; ++lm) {
-                const float bl = vsum(beta[lm]);
-                ex = fmaf(bl, ge[3 * lm], ex);
-                ey = fmaf(bl, ge[3 * lm + 1], ey);
-                ez = fmaf(bl, ge[3 * lm + 2], ez);
+                for (int lm = 0; lm < NLM; ++lm) ldp<CPW>(io.gA + ((size_t)jt * NLM + lm) * C + lane * CPW, gj[lm]);
+                T y[NLM];
+#pragma unroll
+                for (int lm = 0; lm < NLM; ++lm) y[lm] = rec[2 * K + lm];
+                T rho = vdup<T>(0.f), beta[NLM];
+#pragma unroll
+                for (int lm = 0; lm < NLM; ++lm) beta[lm] = vdup<T>(0.f);
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    T R[NL], Rp[NL];
+#pragma unroll
+                    for (int l = 0; l < NL; ++l) {
+                        T s0 = vdup<T>(0.f), s1 = vdup<T>(0.f), s2 = vdup<T>(0.f), s3 = vdup<T>(0.f);
+#pragma unroll
+                        for (int k = 0; k < K; k += 2) {
+                            s0 = vfma(W[l][k][p], rec[k], s0);
+                            s1 = vfma(W[l][k][p], rec[K + k], s1);
+                            s2 = vfma(W[l][k + 1][p], rec[k + 1], s2);
+                            s3 = vfma(W[l][k + 1][p], rec[K + k + 1], s3);
+                        }
+                        R[l] = vadd(s0, s2);
+                        Rp[l] = vadd(s1, s3);
+                    }
+#pragma unroll
+                    for (int l = 0; l < NL; ++l) {
+                        const T sas = (l & 1) ? san[p] : sa[p];
+                        T tl = vdup<T>(0.f), wl = vdup<T>(0.f);
+#pragma unroll
+                        for (int lm = l * l; lm < (l + 1) * (l + 1); ++lm) {
+                            const T gam = vfma(sh_ga[lm][p * 32 + lane], sj[p], vmul(gj[lm][p], sas));
+                            tl = vfma(gam, y[lm], tl);
+                            beta[lm] = vfma(gam, R[l], beta[lm]);
+                            if (SG) wl = vfma(gj[lm][p], y[lm], wl);
+                        }
+                        rho = vfma(Rp[l], tl, rho);
+                        if (SG) {
+                            if (l & 1) gso[p] = vfma(R[l], wl, gso[p]);
+                            else gse[p] = vfma(R[l], wl, gse[p]);
+                        }
+                    }
+                }
+                // this lane's share (its channels) of the pair's force on a
+                const float rh = vsum(rho);
+                float ex = rh * ge[3 * NLM], ey = rh * ge[3 * NLM + 1], ez = rh * ge[3 * NLM + 2];
+#pragma unroll
+                for (int lm = 1; lm < NLM; ++lm) {
+                    const float bl = vsum(beta[lm]);
+                    ex = fmaf(bl, ge[3 * lm], ex);
+                    ey = fmaf(bl, ge[3 * lm + 1], ey);
+                    ez = fmaf(bl, ge[3 * lm + 2], ez);
+                }
+                sh_f[0][t - t0][lane] = ex;
+                sh_f[1][t - t0][lane] = ey;
+                sh_f[2][t - t0][lane] = ez;
             }
-            fx += ex; fy += ey; fz += ez;
-            // virial proxy: each directed edge's dU/dd . d is counted from both
-            // ends of the pair, hence the half
-            if (VIR) wv = fmaf(0.5f * ge[3 * NLM + 3], ex * ge[3 * NLM] + ey * ge[3 * NLM + 1] + ez * ge[3 * NLM + 2], wv);
+            __syncwarp();
+            // pair t0 + u: lanes u and u + 16 add up lanes 0-15 and 16-31 of
+            // its shares (conflict-free: row stride 33), then lane u the two
+            // halves, in a fixed order
+            const int u = lane & (FT - 1), h = lane / FT;
+            const bool own = t0 + u < t1;
+            float px = 0.f, py = 0.f, pz = 0.f;
+            if (own) {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    px += sh_f[0][u][16 * h + q];
+                    py += sh_f[1][u][16 * h + q];
+                    pz += sh_f[2][u][16 * h + q];
+                }
+            }
+            px += __shfl_down_sync(DMTS_FULL, px, 16);
+            py += __shfl_down_sync(DMTS_FULL, py, 16);
+            pz += __shfl_down_sync(DMTS_FULL, pz, 16);
+            if (own && h == 0) {
+                const int jt = sh_j[t0 + u];
+                px *= io.nu;
+                py *= io.nu;
+                pz *= io.nu;
+                if (fix_ok(px) && fix_ok(py) && fix_ok(pz)) {
+                    const long long qx = to_fix(px), qy = to_fix(py), qz = to_fix(pz);
+                    oa[0] += qx;
+                    oa[1] += qy;
+                    oa[2] += qz;
+                    unsigned long long *fj = io.Ffix + 3 * (size_t)jt;
+                    fix_add(fj, -qx);
+                    fix_add(fj + 1, -qy);
+                    fix_add(fj + 2, -qz);
+                    if (VIR) {
+                        // virial proxy: dU/dd . d of the pair, half to each end
+                        const float *ge = sh_g[t0 + u];
+                        const float wp = 0.5f * ge[3 * NLM + 3] * (px * ge[3 * NLM] + py * ge[3 * NLM + 1] + pz * ge[3 * NLM + 2]);
+                        if (fix_ok(wp)) {
+                            const long long qw = to_fix(wp);
+                            ow += qw;
+                            fix_add(io.Wfix + jt, qw);
+                        } else {
+                            bad = true;
+                        }
+                    }
+                } else {
+                    bad = true;
+                }
+            }
+            __syncwarp();
         }
         __syncwarp();
     }
-    fx = warp_sum(fx); fy = warp_sum(fy); fz = warp_sum(fz);
-    if (VIR) wv = warp_sum(wv);
+    // a's side: the integer sums of the lanes that added up its pairs
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        oa[0] += __shfl_xor_sync(DMTS_FULL, oa[0], o);
+        oa[1] += __shfl_xor_sync(DMTS_FULL, oa[1], o);
+        oa[2] += __shfl_xor_sync(DMTS_FULL, oa[2], o);
+        if (VIR) ow += __shfl_xor_sync(DMTS_FULL, ow, o);
+    }
+    if (__any_sync(DMTS_FULL, bad) && lane == 0) set_error(io.err, (int)DMTS_E_NONFINITE);
     if (lane == 0) {
-        const float nu = io.nu;
-        if (io.accumulate) {
-            io.F[3 * a] += nu * fx; io.F[3 * a + 1] += nu * fy; io.F[3 * a + 2] += nu * fz;
-            if (VIR) io.W[a] += nu * wv;
-        } else {
-            io.F[3 * a] = nu * fx; io.F[3 * a + 1] = nu * fy; io.F[3 * a + 2] = nu * fz;
-            if (VIR) io.W[a] = nu * wv;
-        }
+        unsigned long long *fa = io.Ffix + 3 * (size_t)a;
+        fix_add(fa, oa[0]);
+        fix_add(fa + 1, oa[1]);
+        fix_add(fa + 2, oa[2]);
+        if (VIR) fix_add(io.Wfix + a, ow);
     }
     if (!SG) return;
     T gin[NP], gout[NP];
@@ -423,6 +537,32 @@ __global__ void __launch_bounds__(MP_WARPS * 32) k_mp_bwd(EdgeGeom g, LayerIO io
             for (int hh = 0; hh < PW; ++hh)
                 st_split(io.gs_out_bf16, a, C, lane * CPW + p * PW + hh, vget(gout[p], hh));
     }
+}
+
+// One thread per atom: the adjoint's fixed-point forces (and virial) -> fp32,
+// the words cleared for the next evaluation (also after an aborted one).
+__global__ void k_fix_convert(int n, unsigned long long *__restrict__ Ffix, float *__restrict__ F,
+                              unsigned long long *__restrict__ Wfix, float *__restrict__ W) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const long long q = (long long)Ffix[3 * (size_t)i + c];
+        Ffix[3 * (size_t)i + c] = 0ull;
+        F[3 * (size_t)i + c] = fix_to_float(q);
+    }
+    if (Wfix) {
+        const long long q = (long long)Wfix[i];
+        Wfix[i] = 0ull;
+        W[i] = fix_to_float(q);
+    }
+}
+
+void launch_fix_convert(int n, unsigned long long *Ffix, float *F, unsigned long long *Wfix, float *W,
+                        cudaStream_t st) {
+    if (n == 0) return;
+    k_fix_convert<<<(n + 255) / 256, 256, 0, st>>>(n, Ffix, F, Wfix, W);
+    count_launch();
 }
 
 // In the forward pass 128 channels are split over two blocks (64 per warp):
@@ -445,18 +585,18 @@ static void bwd_launch(const EdgeGeom &g, const LayerIO &io, cudaStream_t st) {
     constexpr size_t smem = BwdSmem<C, LMAX, 8, VIR>::bytes;
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_mp_bwd<C, LMAX, 8, VIR, SG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int blocks = (g.n_atoms + MP_WARPS - 1) / MP_WARPS;
-    k_mp_bwd<C, LMAX, 8, VIR, SG><<<blocks, MP_WARPS * 32, smem, st>>>(g, io);
+    const int blocks = (g.n_atoms + BWD_WARPS - 1) / BWD_WARPS;
+    k_mp_bwd<C, LMAX, 8, VIR, SG><<<blocks, BWD_WARPS * 32, smem, st>>>(g, io);
     count_launch();
 }
 
-// The virial variant (io.W set) and the variant without the sender-role
+// The virial variant (io.Wfix set) and the variant without the sender-role
 // gradient (io.gs_out null) are separate instantiations, so that each
 // carries no register or instruction it does not use.
 template <int C, int LMAX>
 static void bwd_c(const EdgeGeom &g, const LayerIO &io, cudaStream_t st) {
     const bool gs = io.gs_out != nullptr;
-    if (io.W) gs ? bwd_launch<C, LMAX, true, true>(g, io, st) : bwd_launch<C, LMAX, true, false>(g, io, st);
+    if (io.Wfix) gs ? bwd_launch<C, LMAX, true, true>(g, io, st) : bwd_launch<C, LMAX, true, false>(g, io, st);
     else gs ? bwd_launch<C, LMAX, false, true>(g, io, st) : bwd_launch<C, LMAX, false, false>(g, io, st);
 }
 

@@ -33,10 +33,9 @@ struct LayerIO {
     const float *gs_in;      // [N][C]       (backward in)
     float *gs_out;           // [N][C]       (backward out; nullable: not computed)
     __nv_bfloat16 *gs_out_bf16;  // optional split-bf16 copy of gs_out, [N][2C]
-    float *F;                // [N][3]       (backward: accumulated forces)
-    int accumulate;          // backward: 0 write F, 1 add to F (and W)
-    float *W;                // [N] (backward, nullable): per-atom virial proxy, pair form
-    const int *err;
+    unsigned long long *Ffix;  // [N][3] (backward): forces added in 32.32 fixed point
+    unsigned long long *Wfix;  // [N] (backward, nullable): per-atom virial proxy, pair form, fixed point
+    int *err;
 };
 
 template <int CPW>
@@ -77,6 +76,9 @@ void launch_mp_fwd(int C, int lmax, int K, const EdgeGeom &g, const LayerIO &io,
 bool mp_fwd_tc_supported(int C, int K, const LayerIO &io);
 void launch_mp_fwd_tc(int lmax, const EdgeGeom &g, const LayerIO &io, int nseg, int *err, cudaStream_t st);
 void launch_mp_bwd(int C, int lmax, int K, const EdgeGeom &g, const LayerIO &io, cudaStream_t st);
+// The adjoint's fixed-point forces (and virial, Wfix nullable) -> fp32 F and
+// W, the fixed-point words cleared for the next evaluation.
+void launch_fix_convert(int n, unsigned long long *Ffix, float *F, unsigned long long *Wfix, float *W, cudaStream_t st);
 
 // ---------------------------------------------------------------- GEMM ----
 enum EpiMode {
