@@ -227,7 +227,11 @@ dmts_status nbr_build_noalloc(const dmts_system *sys, dmts_nbr *nbr, long long *
  * only). nbr must hold a list with r_list >= model rc (and >= lj_rc with
  * DMTS_WITH_PRIOR), built for the current positions. The forces are the
  * hand-written adjoint of the energy with per-layer recomputation of all
- * edge quantities; only node features are stored. virial: device double
+ * edge quantities; only node features are stored. Each pair's force is
+ * formed once and added to its two atoms in 32.32 fixed point, so the forces
+ * do not depend on the order of the additions (the same bits alone or
+ * batched); a pair term that is not finite or exceeds 2^24 in magnitude
+ * sets DMTS_E_NONFINITE. virial: device double
  * [n_replicas] (may be NULL; needs forces): -sum_i F_i . q_i in pair form,
  * sum over directed edges of dU/dd_ij . d_ij plus the analytic pair terms
  * (Sec. 2 "Computation of the virial term in NPT": the estimator at the

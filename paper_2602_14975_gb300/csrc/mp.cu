@@ -2,8 +2,8 @@
 // segmented scatter-sum with one warp per receiver, and the adjoint (forces
 // and feature gradients): each pair's force once, from its lower atom, in
 // fixed point; each atom's sender-role gradient gathered over its row of the
-// symmetric neighbour list. Node-level MLP contractions: SIMT fp32 GEMM with fused
-// epilogues.
+// symmetric neighbour list. Node-level MLP contractions: SIMT fp32 GEMM with
+// fused epilogues.
 #include <type_traits>
 
 #include "mp.cuh"
