@@ -214,6 +214,54 @@ def test_cons_large_lmax2_c128(water):
     assert rel_maxabs(F, Fo) <= TOL_F32
 
 
+@pytest.mark.parametrize("L,C,lmax", [(2, 32, 0), (2, 32, 2), (3, 128, 1)])
+def test_cons_other_shapes(water, L, C, lmax):
+    """The adjoint's other instantiations against the oracle: one channel per
+    lane (C = 32, scalar arithmetic), l_max = 0 (the pair force along n
+    only) and l_max = 1 at C = 128."""
+    cs = S.cons_spec(L, C, lmax)
+    cb = S.cons_weights(cs, 311)
+    ctx = core.Context(cons=(cs, cb))
+    E, F = _gpu_cons(ctx, [water], with_prior=False)
+    Eo, Fo = O.cons_energy_forces(water, cs, cb)
+    assert abs(E[0] - Eo) <= TOL_F32 * abs(Eo)
+    assert rel_maxabs(F, Fo) <= TOL_F32
+
+
+def _net_within_rounding(F):
+    """|sum_a F_a| against the bound sum_a ulp(F_a) / 2, per component."""
+    F32 = np.asarray(F, dtype=np.float32)
+    net = np.abs(F32.astype(np.float64).sum(axis=0))
+    bound = 0.5 * np.spacing(np.abs(F32)).astype(np.float64).sum(axis=0)
+    return net, bound
+
+
+@pytest.mark.parametrize("which", ["water_fp32", "droplets_fp32", "water_bf16"])
+def test_cons_forces_net_zero_to_rounding(ctx1, water, which):
+    """Each pair's force (Sec. 2, F = -grad U, the adjoint of the message
+    passing) enters its two atoms with opposite signs in 32.32 fixed point,
+    so the fixed-point sums of a replica total exactly zero, and each atom's
+    fp32 force is its sum rounded once: |sum_a F_a| <= sum_a ulp(F_a) / 2
+    per component and replica. A sign, index or ownership slip in the pair
+    terms breaks this by orders of magnitude (the forces are of order 1e-1,
+    the bound of order 1e-6)."""
+    if which == "water_bf16":
+        cs = S.cons_spec(3, 128, 2, bf16=True)
+        ctx = core.Context(cons=(cs, S.cons_weights(cs, 302)))
+    else:
+        ctx = ctx1
+    systems = ([S.capped_molecule_in_droplet(n, seed=70 + n) for n in (20, 61, 33)]
+               if which == "droplets_fp32" else [water])
+    _, F = _gpu_cons(ctx, systems, with_prior=False)
+    off = 0
+    for sy in systems:
+        Fr = F[off:off + sy.n_atoms]
+        net, bound = _net_within_rounding(Fr)
+        assert np.all(net <= bound), (net, bound)
+        assert np.abs(Fr).max() > 1e3 * bound.max()   # the forces are not trivially zero
+        off += sy.n_atoms
+
+
 def test_cons_autograd_function(ctx1, models1, water):
     (cs, cb), _ = models1
     d = core.DeviceSystem(water)
