@@ -508,6 +508,18 @@ int launch_gemm_tc(int M, int N, int K, const __nv_bfloat16 *Act, const __nv_bfl
     for (int b = 16; b <= 256 && b <= N; b += 16)
         if (N % b == 0 && (BN == 0 || std::abs(b - kBNTarget) < std::abs(BN - kBNTarget))) BN = b;
     if (!BN) return -1;
+    // a narrow contraction (one or two column tiles) halves its tiles while
+    // the grid has fewer than two CTAs per SM: these launches are bound by
+    // latency, not by the second read of the activation tile (from L2)
+    static int n_sm = 0;
+    if (!n_sm) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        n_sm = std::max(n_sm, 1);
+    }
+    const int row_tiles = (M + TC_M - 1) / TC_M;
+    while (BN % 32 == 0 && (long long)row_tiles * (N / BN) < 2LL * n_sm) BN /= 2;
     int tmem_cols = 32;
     while (tmem_cols < BN) tmem_cols <<= 1;
     CUtensorMap ma, mb;
