@@ -427,6 +427,7 @@ dmts_status nc_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const i
         !w.nc_act.ensure(sizeof(float) * nc_) || !w.nc_qk.ensure(sizeof(float) * (size_t)N * QKW) ||
         !w.nc_v.ensure(sizeof(float) * (size_t)N * nc_v_stride(m.nl)) || !w.nc_f.ensure(sizeof(float) * 3 * (N + 1)) ||
         !ensure_zeroed(ctx, w.nc_ffix, sizeof(unsigned long long) * 3 * (N + 1), st) ||
+        !ensure_zeroed(ctx, w.nc_next, sizeof(unsigned), st) ||
         !w.nc_sum.ensure(sizeof(unsigned long long) * 3 * (s.n_rep + 1)) ||
         !w.ms_scratch.ensure(mean_sub_scratch_bytes(N, s.n_rep)) ||
         (virial && !w.nc_w.ensure(sizeof(float) * (N + 1))))
@@ -492,6 +493,7 @@ dmts_status nc_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const i
     a.species = s.species;
     a.Ffix = (unsigned long long *)w.nc_ffix.p;
     a.sum = (unsigned long long *)w.nc_sum.p;
+    a.next = (unsigned *)w.nc_next.p;
     a.n_rep = s.n_rep;
     a.W = virial ? (float *)w.nc_w.p : nullptr;
     a.order = s.order;
@@ -503,7 +505,7 @@ dmts_status nc_eval(dmts_ctx *ctx, const SysView &s, const int *row_ptr, const i
         // fp32 forces and the replicas' exact sums; the mean subtraction here
         // or, inside respa_step, in the next integrator launch
         ProfScope ps(ctx, "mean_sub", st);
-        launch_nc_convert(N, s.atom_rep, a.Ffix, (float *)w.nc_f.p, a.sum, st);
+        launch_nc_convert(N, s.atom_rep, a.Ffix, (float *)w.nc_f.p, a.sum, a.next, st);
         if (!(flags & kFlagDeferMean))
             launch_nc_apply(N, s.atom_rep, s.rep_off, s.n_rep, (float *)w.nc_f.p, forces, a.sum, net, ctx->d_err, st);
     }

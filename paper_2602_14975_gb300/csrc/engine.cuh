@@ -61,6 +61,7 @@ struct Workspace {
     Buf s, A, q, h, act, u, gz, gs0, gs1, gA, e_atom, ftmp, atom_rep;
     Buf nc_s, nc_q, nc_act, nc_qk, nc_v, nc_f;
     Buf nc_ffix;      // NC head forces in 32.32 fixed point, zero between evaluations
+    Buf nc_next;      // the NC head's work counter, zero between evaluations
     Buf nc_sum;       // per-replica exact sums of the NC forces (fixed point) of the last evaluation
     // split-bf16 operands of the tensor-core contractions ([rows][2K])
     Buf q_bf, act_bf, s_bf, gz_bf, gs0_bf, gs1_bf, nc_q_bf, nc_act_bf, nc_s_bf;
@@ -75,7 +76,7 @@ struct Workspace {
     Buf dist_A, dist_gq, dist_gv;
     void release_all() {
         Buf *all[] = {&s, &A, &q, &h, &act, &u, &gz, &gs0, &gs1, &gA, &e_atom, &ftmp, &atom_rep,
-                      &nc_s, &nc_q, &nc_act, &nc_qk, &nc_v, &nc_f, &nc_ffix, &nc_sum,
+                      &nc_s, &nc_q, &nc_act, &nc_qk, &nc_v, &nc_f, &nc_ffix, &nc_next, &nc_sum,
                       &q_bf, &act_bf, &s_bf, &gz_bf, &gs0_bf, &gs1_bf, &nc_q_bf, &nc_act_bf, &nc_s_bf,
                       &ms_scratch, &nc_w, &cons_w, &cons_ffix, &cons_wfix, &nc_w_last,
                       &dist_F, &dist_g, &dist_sq, &dist_gqk, &dist_gs1, &dist_gh, &dist_h, &dist_dw,

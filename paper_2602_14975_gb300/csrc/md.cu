@@ -7,6 +7,7 @@
 // the NC model (Sec. 2, "Model training").
 #include <algorithm>
 #include "md.cuh"
+#include "mp.cuh"
 #include "ptx.cuh"
 
 namespace dmts {
@@ -221,222 +222,270 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
     // them for this one's conversion
     if (blockIdx.x == 0 && g.sum)
         for (int t = threadIdx.x; t < 3 * g.n_rep; t += blockDim.x) g.sum[t] = 0ull;
-    const int wa = blockIdx.x * NCH_WARPS + warp;
-    if (wa >= g.n_atoms || *g.err) return;
-    const int a = g.order ? __ldg(g.order + wa) : wa;
+    if (*g.err) return;
+    // The warps take atoms from a counter, in processing order, as they free
+    // up. A warp's first atom's row and first 32 candidates are loaded here,
+    // every later atom's one atom ahead, in stages behind the current atom's
+    // work: the counter at its start, the atom index before its last batch,
+    // the row bounds after it, the candidates after its bonds and their
+    // positions after its force sums.
+    int wa = __shfl_sync(DMTS_FULL, lane == 0 ? (int)atomicAdd(g.next, 1u) : 0, 0);
+    if (wa >= g.n_atoms) return;
     if (lane == 0) {
         mbar_init(bar, 1);
         mbar_init_fence();
     }
-    for (int t = lane; t < QKW; t += 32) qa[t] = g.QK[(size_t)a * QKW + t];
-    for (int t = lane; t < NL * 3; t += 32) va[t] = g.V[(size_t)a * SM::VS + t];
     __syncwarp();
-    const float *ka = qa + H * NC;
-    const int rep = g.atom_rep[a];
-    const float bx = g.box[3 * rep], by = g.box[3 * rep + 1], bz = g.box[3 * rep + 2];
-    const float ibx = bx > 0.f ? 1.f / bx : 0.f, iby = by > 0.f ? 1.f / by : 0.f, ibz = bz > 0.f ? 1.f / bz : 0.f;
-    const float xa = g.x[3 * a], ya = g.x[3 * a + 1], za = g.x[3 * a + 2];
-    const float rc2 = g.rc * g.rc, isnc = rsqrtf((float)NC);
-    const bool with_rep = g.bonds.ptr && g.rep.on;
-    const float rep2 = g.rep.rc * g.rep.rc;
-    const int sa = g.species[a];
-    // bonded partners of a (up to four in registers; more fall back to the table)
-    int bp[4] = {-1, -1, -1, -1}, nbp = 0;
-    if (with_rep) {
-        const int b0 = g.bonds.ptr[a];
-        nbp = g.bonds.ptr[a + 1] - b0;
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            if (q < nbp) bp[q] = g.bonds.idx[b0 + q];
-    }
-    auto bonded = [&](int j) {
-        if (nbp > 4) return is_bonded(g.bonds, a, j);
-        return j == bp[0] || j == bp[1] || j == bp[2] || j == bp[3];
-    };
-    // a's bonds (one per lane): partner position and rest length, loaded now
-    // so that their latency overlaps the pairs' work
-    int nbond = 0;
-    float bjx = 0.f, bjy = 0.f, bjz = 0.f, br0 = 0.f;
-    if (g.bonds.ptr) {
-        const int q0 = g.bonds.ptr[a];
-        nbond = g.bonds.ptr[a + 1] - q0;
-        if (lane < nbond) {
-            const int jb = __ldg(g.bonds.idx + q0 + lane);
-            bjx = __ldg(g.x + 3 * jb);
-            bjy = __ldg(g.x + 3 * jb + 1);
-            bjz = __ldg(g.x + 3 * jb + 2);
-            br0 = __ldg(g.bonds.r0 + q0 + lane);
-        }
-    }
-    long long ox = 0, oy = 0, oz = 0;     // this lane's share of a's side of its pairs, fixed point
-    float wv = 0.f;                       // virial proxy: (F_aj - F_ja) . d_aj (+ repulsion) over a's pairs
-    bool bad = false;                     // a pair term outside the fixed-point range (or not finite)
     uint32_t phase = 0;
-    bool alive = true;
-
-    // one batch: lanes e and e + 16 (e < nb) own queued edge taken + e; the
-    // first stages the row and adds the repulsion, the pair splits the heads
-    const int slot = lane & (BATCH - 1), half = lane / BATCH;
-    auto batch = [&](int taken, int nb) {
-        const int qs = (taken + slot) & 63;
-        const int j = slot < nb ? queue[qs] : -1;
-        fence_proxy_async_smem();      // earlier reads of the rows before the copies overwrite them
-        if (lane == 0) mbar_expect_tx(bar, (uint32_t)nb * SM::ROWB);
+    int a = g.order ? __ldg(g.order + wa) : wa;
+    int beg = g.row_ptr[a], end = g.row_ptr[a + 1];
+    int cj = beg + lane < end ? __ldg(g.col + beg + lane) : -1;
+    float cx = 0.f, cy = 0.f, cz = 0.f;
+    if (cj >= 0) {
+        cx = __ldg(g.x + 3 * cj);
+        cy = __ldg(g.x + 3 * cj + 1);
+        cz = __ldg(g.x + 3 * cj + 2);
+    }
+    for (;;) {
+        const int wn_raw = lane == 0 ? (int)atomicAdd(g.next, 1u) : 0;   // read after the candidates
+        int wn = 0, an = 0, bn = 0, en = 0, cjn = -1;
+        bool more = false;
+        for (int t = lane; t < QKW; t += 32) qa[t] = g.QK[(size_t)a * QKW + t];
+        for (int t = lane; t < NL * 3; t += 32) va[t] = g.V[(size_t)a * SM::VS + t];
         __syncwarp();
-        if (j >= 0 && half == 0) bulk_g2s(smem_u32(rows + slot * RSTR), g.QK + (size_t)j * QKW, SM::ROWB, bar);
-        // the neighbour's tensor-head vectors, for the lane of the pair that
-        // owns the tensor heads (plain loads: 12 bytes per head)
-        float vj[3 * NL];
-#pragma unroll
-        for (int q = 0; q < 3 * NL; ++q) vj[q] = (j >= 0 && half == 1) ? __ldg(g.V + (size_t)j * SM::VS + q) : 0.f;
-        // radial part of the edge while the rows arrive
-        float dx = 0.f, dy = 0.f, dz = 0.f, inv = 1.f, fc = 0.f, Bh[HH], crep = 0.f, r2 = 0.f;
-        if (j >= 0) {
-            dx = qd[3 * qs];
-            dy = qd[3 * qs + 1];
-            dz = qd[3 * qs + 2];
-            r2 = dx * dx + dy * dy + dz * dz;
-            const float r = sqrtf(r2);
-            inv = 1.f / r;
-            if (half == 0 && with_rep && r2 < rep2 && !bonded(j)) {
-                float dE;
-                rep_pair(g.rep, sa, g.species[j], r, &dE);
-                crep = dE * inv;               // F_a = E'(r) d / r, F_j = -F_a
+        const float *ka = qa + H * NC;
+        const int rep = g.atom_rep[a];
+        const float bx = g.box[3 * rep], by = g.box[3 * rep + 1], bz = g.box[3 * rep + 2];
+        const float ibx = bx > 0.f ? 1.f / bx : 0.f, iby = by > 0.f ? 1.f / by : 0.f, ibz = bz > 0.f ? 1.f / bz : 0.f;
+        const float xa = g.x[3 * a], ya = g.x[3 * a + 1], za = g.x[3 * a + 2];
+        const float rc2 = g.rc * g.rc, isnc = rsqrtf((float)NC);
+        const bool with_rep = g.bonds.ptr && g.rep.on;
+        const float rep2 = g.rep.rc * g.rep.rc;
+        const int sa = g.species[a];
+        // bonded partners of a (up to four in registers; more fall back to the table)
+        int bp[4] = {-1, -1, -1, -1}, nbp = 0;
+        if (with_rep) {
+            const int b0 = g.bonds.ptr[a];
+            nbp = g.bonds.ptr[a + 1] - b0;
+    #pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (q < nbp) bp[q] = g.bonds.idx[b0 + q];
+        }
+        auto bonded = [&](int j) {
+            if (nbp > 4) return is_bonded(g.bonds, a, j);
+            return j == bp[0] || j == bp[1] || j == bp[2] || j == bp[3];
+        };
+        // a's bonds (one per lane): partner position and rest length, loaded now
+        // so that their latency overlaps the pairs' work
+        int nbond = 0;
+        float bjx = 0.f, bjy = 0.f, bjz = 0.f, br0 = 0.f;
+        if (g.bonds.ptr) {
+            const int q0 = g.bonds.ptr[a];
+            nbond = g.bonds.ptr[a + 1] - q0;
+            if (lane < nbond) {
+                const int jb = __ldg(g.bonds.idx + q0 + lane);
+                bjx = __ldg(g.x + 3 * jb);
+                bjy = __ldg(g.x + 3 * jb + 1);
+                bjz = __ldg(g.x + 3 * jb + 2);
+                br0 = __ldg(g.bonds.r0 + q0 + lane);
             }
-            float du;
-            fc = envelope(r * g.inv_rc, g.p, &du);
-            float B[K];
-            bessel<K, false>(r, g.inv_rc, g.bnorm, B, nullptr);
-#pragma unroll
-            for (int hl = 0; hl < HH; ++hl)
-                Bh[hl] = half == 0 ? B[hl] : (HH + hl < K ? B[HH + hl < K ? HH + hl : 0] : 0.f);
         }
-        const bool got = __all_sync(DMTS_FULL, mbar_wait(bar, phase));
-        phase ^= 1u;
-        if (!got) {
-            // record the timeout, give the copies in flight a last bounded
-            // wait, and stop
-            if (lane == 0) atomicCAS(g.err, 0, (int)DMTS_E_TIMEOUT);
-            mbar_wait(bar, phase ^ 1u);
-            alive = false;
-            return;
-        }
-        // partial sums over this lane's heads h = half * HH + hl
-        float part[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // Saj, Sja, va (3), vj (3)
-        if (j >= 0) {
-            const float *row = rows + slot * RSTR;
-#pragma unroll
-            for (int hl = 0; hl < HH; ++hl) {
-                const int h = half * HH + hl;
-                if (h < H) {
-                    const float4 *qj4 = reinterpret_cast<const float4 *>(row + h * NC);
-                    const float4 *kj4 = reinterpret_cast<const float4 *>(row + (H + h) * NC);
-                    const float4 *qa4 = reinterpret_cast<const float4 *>(qa + h * NC);
-                    const float4 *ka4 = reinterpret_cast<const float4 *>(ka + h * NC);
-                    float caj = 0.f, cja = 0.f;
-#pragma unroll
-                    for (int q = 0; q < NC / 4; ++q) {
-                        const float4 kj = kj4[q], qj = qj4[q], qi = qa4[q], ki = ka4[q];
-                        caj = fmaf(qi.x, kj.x, fmaf(qi.y, kj.y, fmaf(qi.z, kj.z, fmaf(qi.w, kj.w, caj))));
-                        cja = fmaf(qj.x, ki.x, fmaf(qj.y, ki.y, fmaf(qj.z, ki.z, fmaf(qj.w, ki.w, cja))));
-                    }
-                    caj *= isnc;
-                    cja *= isnc;
-                    if (h < K) {
-                        part[0] = fmaf(caj, Bh[hl], part[0]);
-                        part[1] = fmaf(cja, Bh[hl], part[1]);
-                    } else {
-                        // tensor heads lie in the second lane's half (HH <= K): t is static
-                        const int t = HH + hl - K;
-#pragma unroll
-                        for (int cmp = 0; cmp < 3; ++cmp) {
-                            part[2 + cmp] = fmaf(caj, va[3 * t + cmp], part[2 + cmp]);
-                            part[5 + cmp] = fmaf(cja, vj[3 * t + cmp], part[5 + cmp]);
+        long long ox = 0, oy = 0, oz = 0;     // this lane's share of a's side of its pairs, fixed point
+        float wv = 0.f;                       // virial proxy: (F_aj - F_ja) . d_aj (+ repulsion) over a's pairs
+        bool bad = false;                     // a pair term outside the fixed-point range (or not finite)
+        bool alive = true;
+
+        // one batch: lanes e and e + 16 (e < nb) own queued edge taken + e; the
+        // first stages the row and adds the repulsion, the pair splits the heads
+        const int slot = lane & (BATCH - 1), half = lane / BATCH;
+        auto batch = [&](int taken, int nb) {
+            const int qs = (taken + slot) & 63;
+            const int j = slot < nb ? queue[qs] : -1;
+            fence_proxy_async_smem();      // earlier reads of the rows before the copies overwrite them
+            if (lane == 0) mbar_expect_tx(bar, (uint32_t)nb * SM::ROWB);
+            __syncwarp();
+            if (j >= 0 && half == 0) bulk_g2s(smem_u32(rows + slot * RSTR), g.QK + (size_t)j * QKW, SM::ROWB, bar);
+            // the neighbour's tensor-head vectors, for the lane of the pair that
+            // owns the tensor heads (plain loads: 12 bytes per head)
+            float vj[3 * NL];
+    #pragma unroll
+            for (int q = 0; q < 3 * NL; ++q) vj[q] = (j >= 0 && half == 1) ? __ldg(g.V + (size_t)j * SM::VS + q) : 0.f;
+            // radial part of the edge while the rows arrive
+            float dx = 0.f, dy = 0.f, dz = 0.f, inv = 1.f, fc = 0.f, Bh[HH], crep = 0.f, r2 = 0.f;
+            if (j >= 0) {
+                dx = qd[3 * qs];
+                dy = qd[3 * qs + 1];
+                dz = qd[3 * qs + 2];
+                r2 = dx * dx + dy * dy + dz * dz;
+                const float r = sqrtf(r2);
+                inv = 1.f / r;
+                if (half == 0 && with_rep && r2 < rep2 && !bonded(j)) {
+                    float dE;
+                    rep_pair(g.rep, sa, g.species[j], r, &dE);
+                    crep = dE * inv;               // F_a = E'(r) d / r, F_j = -F_a
+                }
+                float du;
+                fc = envelope(r * g.inv_rc, g.p, &du);
+                float B[K];
+                bessel<K, false>(r, g.inv_rc, g.bnorm, B, nullptr);
+    #pragma unroll
+                for (int hl = 0; hl < HH; ++hl)
+                    Bh[hl] = half == 0 ? B[hl] : (HH + hl < K ? B[HH + hl < K ? HH + hl : 0] : 0.f);
+            }
+            const bool got = __all_sync(DMTS_FULL, mbar_wait(bar, phase));
+            phase ^= 1u;
+            if (!got) {
+                // record the timeout, give the copies in flight a last bounded
+                // wait, and stop
+                if (lane == 0) atomicCAS(g.err, 0, (int)DMTS_E_TIMEOUT);
+                mbar_wait(bar, phase ^ 1u);
+                alive = false;
+                return;
+            }
+            // partial sums over this lane's heads h = half * HH + hl
+            float part[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // Saj, Sja, va (3), vj (3)
+            if (j >= 0) {
+                const float *row = rows + slot * RSTR;
+    #pragma unroll
+                for (int hl = 0; hl < HH; ++hl) {
+                    const int h = half * HH + hl;
+                    if (h < H) {
+                        const float4 *qj4 = reinterpret_cast<const float4 *>(row + h * NC);
+                        const float4 *kj4 = reinterpret_cast<const float4 *>(row + (H + h) * NC);
+                        const float4 *qa4 = reinterpret_cast<const float4 *>(qa + h * NC);
+                        const float4 *ka4 = reinterpret_cast<const float4 *>(ka + h * NC);
+                        float caj = 0.f, cja = 0.f;
+    #pragma unroll
+                        for (int q = 0; q < NC / 4; ++q) {
+                            const float4 kj = kj4[q], qj = qj4[q], qi = qa4[q], ki = ka4[q];
+                            caj = fmaf(qi.x, kj.x, fmaf(qi.y, kj.y, fmaf(qi.z, kj.z, fmaf(qi.w, kj.w, caj))));
+                            cja = fmaf(qj.x, ki.x, fmaf(qj.y, ki.y, fmaf(qj.z, ki.z, fmaf(qj.w, ki.w, cja))));
+                        }
+                        caj *= isnc;
+                        cja *= isnc;
+                        if (h < K) {
+                            part[0] = fmaf(caj, Bh[hl], part[0]);
+                            part[1] = fmaf(cja, Bh[hl], part[1]);
+                        } else {
+                            // tensor heads lie in the second lane's half (HH <= K): t is static
+                            const int t = HH + hl - K;
+    #pragma unroll
+                            for (int cmp = 0; cmp < 3; ++cmp) {
+                                part[2 + cmp] = fmaf(caj, va[3 * t + cmp], part[2 + cmp]);
+                                part[5 + cmp] = fmaf(cja, vj[3 * t + cmp], part[5 + cmp]);
+                            }
                         }
                     }
                 }
             }
-        }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) part[q] += __shfl_xor_sync(DMTS_FULL, part[q], BATCH);
-        if (j >= 0 && half == 0) {
-            const float nx = dx * inv, ny = dy * inv, nz = dz * inv;
-            const float pa = part[0] * fc, pj = part[1] * fc;
-            const float ux = pa * (nx + part[2]) - pj * (-nx + part[5]);
-            const float uy = pa * (ny + part[3]) - pj * (-ny + part[6]);
-            const float uz = pa * (nz + part[4]) - pj * (-nz + part[7]);
-            const float px = fmaf(g.scale, ux, crep * dx), py = fmaf(g.scale, uy, crep * dy),
-                        pz = fmaf(g.scale, uz, crep * dz);
-            wv += fmaf(g.scale, ux * dx + uy * dy + uz * dz, crep * r2);
-            if (fabsf(px) < kFixMax && fabsf(py) < kFixMax && fabsf(pz) < kFixMax) {
-                const long long qx = to_fix(px), qy = to_fix(py), qz = to_fix(pz);
-                ox += qx; oy += qy; oz += qz;
-                unsigned long long *fj = g.Ffix + 3 * (size_t)j;
-                fix_add(fj, -qx); fix_add(fj + 1, -qy); fix_add(fj + 2, -qz);
-            } else {
-                bad = true;   // not finite, or a blow-up beyond the fixed-point range
+    #pragma unroll
+            for (int q = 0; q < 8; ++q) part[q] += __shfl_xor_sync(DMTS_FULL, part[q], BATCH);
+            if (j >= 0 && half == 0) {
+                const float nx = dx * inv, ny = dy * inv, nz = dz * inv;
+                const float pa = part[0] * fc, pj = part[1] * fc;
+                const float ux = pa * (nx + part[2]) - pj * (-nx + part[5]);
+                const float uy = pa * (ny + part[3]) - pj * (-ny + part[6]);
+                const float uz = pa * (nz + part[4]) - pj * (-nz + part[7]);
+                const float px = fmaf(g.scale, ux, crep * dx), py = fmaf(g.scale, uy, crep * dy),
+                            pz = fmaf(g.scale, uz, crep * dz);
+                wv += fmaf(g.scale, ux * dx + uy * dy + uz * dz, crep * r2);
+                if (fabsf(px) < kFixMax && fabsf(py) < kFixMax && fabsf(pz) < kFixMax) {
+                    const long long qx = to_fix(px), qy = to_fix(py), qz = to_fix(pz);
+                    ox += qx; oy += qy; oz += qz;
+                    unsigned long long *fj = g.Ffix + 3 * (size_t)j;
+                    fix_add(fj, -qx); fix_add(fj + 1, -qy); fix_add(fj + 2, -qz);
+                } else {
+                    bad = true;   // not finite, or a blow-up beyond the fixed-point range
+                }
             }
-        }
-        __syncwarp();
-    };
+            __syncwarp();
+        };
 
-    const int beg = g.row_ptr[a], end = g.row_ptr[a + 1];
-    int queued = 0, taken = 0;
-    for (int base = beg; base < end && alive; base += 32) {
-        const int e = base + lane;
-        const int j = e < end ? __ldg(g.col + e) : -1;
-        bool act = false;
-        float dx = 0.f, dy = 0.f, dz = 0.f;
-        if (j > a) {
-            dx = min_img(__ldg(g.x + 3 * j) - xa, bx, ibx);
-            dy = min_img(__ldg(g.x + 3 * j + 1) - ya, by, iby);
-            dz = min_img(__ldg(g.x + 3 * j + 2) - za, bz, ibz);
-            act = dx * dx + dy * dy + dz * dz < rc2;
-        }
-        const unsigned m = __ballot_sync(DMTS_FULL, act);
-        if (act) {
-            const int qs = (queued + __popc(m & ((1u << lane) - 1u))) & 63;
-            queue[qs] = j;
-            qd[3 * qs] = dx;
-            qd[3 * qs + 1] = dy;
-            qd[3 * qs + 2] = dz;
-        }
-        queued += __popc(m);
-        __syncwarp();
-        while (queued - taken >= BATCH && alive) {
-            batch(taken, BATCH);
-            taken += BATCH;
-        }
-    }
-    if (alive && queued > taken) batch(taken, queued - taken);
-    if (!alive) return;
-    float w = wv;
-    if (g.bonds.ptr) {
-        // bonds in fixed point too: the two ends' terms cancel exactly
-        for (int q = lane; q < nbond; q += 32) {
-            float gx, gy, gz, eq, wq;
-            if (q < 32)   // the prefetched bond of this lane
-                bond_term_at(g.bonds.k, bjx, bjy, bjz, br0, xa, ya, za, bx, by, bz, ibx, iby, ibz, gx, gy, gz, eq, wq);
-            else
-                bond_term(g.bonds, g.x, g.bonds.ptr[a] + q, xa, ya, za, bx, by, bz, ibx, iby, ibz, gx, gy, gz, eq, wq);
-            if (fabsf(gx) < kFixMax && fabsf(gy) < kFixMax && fabsf(gz) < kFixMax) {
-                ox += to_fix(gx); oy += to_fix(gy); oz += to_fix(gz);
-            } else {
-                bad = true;
+        int queued = 0, taken = 0;
+        for (int base = beg; base < end && alive; base += 32) {
+            const int e = base + lane;
+            const bool first = base == beg;   // prefetched
+            const int j = first ? cj : (e < end ? __ldg(g.col + e) : -1);
+            bool act = false;
+            float dx = 0.f, dy = 0.f, dz = 0.f;
+            if (j > a) {
+                dx = min_img((first ? cx : __ldg(g.x + 3 * j)) - xa, bx, ibx);
+                dy = min_img((first ? cy : __ldg(g.x + 3 * j + 1)) - ya, by, iby);
+                dz = min_img((first ? cz : __ldg(g.x + 3 * j + 2)) - za, bz, ibz);
+                act = dx * dx + dy * dy + dz * dz < rc2;
             }
-            w += wq;
+            const unsigned m = __ballot_sync(DMTS_FULL, act);
+            if (act) {
+                const int qs = (queued + __popc(m & ((1u << lane) - 1u))) & 63;
+                queue[qs] = j;
+                qd[3 * qs] = dx;
+                qd[3 * qs + 1] = dy;
+                qd[3 * qs + 2] = dz;
+            }
+            queued += __popc(m);
+            __syncwarp();
+            while (queued - taken >= BATCH && alive) {
+                batch(taken, BATCH);
+                taken += BATCH;
+            }
         }
-    }
-    if (__any_sync(DMTS_FULL, bad)) {
-        if (lane == 0) set_error(g.err, DMTS_E_NONFINITE);
-        return;
-    }
-    ox = seg_sum_ll(ox, 0); oy = seg_sum_ll(oy, 0); oz = seg_sum_ll(oz, 0);
-    if (g.W) w = warp_sum(w);
-    if (lane == 0) {
-        unsigned long long *fa = g.Ffix + 3 * (size_t)a;
-        fix_add(fa, ox); fix_add(fa + 1, oy); fix_add(fa + 2, oz);
-        if (g.W) g.W[a] = w;
+        // the next atom
+        wn = __shfl_sync(DMTS_FULL, wn_raw, 0);
+        more = wn < g.n_atoms;
+        if (more) an = g.order ? __ldg(g.order + wn) : wn;
+        if (alive && queued > taken) batch(taken, queued - taken);
+        if (!alive) return;
+        if (more) {   // its row bounds
+            bn = g.row_ptr[an];
+            en = g.row_ptr[an + 1];
+        }
+        float w = wv;
+        if (g.bonds.ptr) {
+            // bonds in fixed point too: the two ends' terms cancel exactly
+            for (int q = lane; q < nbond; q += 32) {
+                float gx, gy, gz, eq, wq;
+                if (q < 32)   // the prefetched bond of this lane
+                    bond_term_at(g.bonds.k, bjx, bjy, bjz, br0, xa, ya, za, bx, by, bz, ibx, iby, ibz, gx, gy, gz, eq,
+                                 wq);
+                else
+                    bond_term(g.bonds, g.x, g.bonds.ptr[a] + q, xa, ya, za, bx, by, bz, ibx, iby, ibz, gx, gy, gz, eq,
+                              wq);
+                if (fabsf(gx) < kFixMax && fabsf(gy) < kFixMax && fabsf(gz) < kFixMax) {
+                    ox += to_fix(gx); oy += to_fix(gy); oz += to_fix(gz);
+                } else {
+                    bad = true;
+                }
+                w += wq;
+            }
+        }
+        if (bn + lane < en) cjn = __ldg(g.col + bn + lane);   // its first candidates
+        if (__any_sync(DMTS_FULL, bad)) {
+            if (lane == 0) set_error(g.err, DMTS_E_NONFINITE);
+            return;
+        }
+        ox = seg_sum_ll(ox, 0); oy = seg_sum_ll(oy, 0); oz = seg_sum_ll(oz, 0);
+        if (g.W) w = warp_sum(w);
+        if (lane == 0) {
+            unsigned long long *fa = g.Ffix + 3 * (size_t)a;
+            fix_add(fa, ox); fix_add(fa + 1, oy); fix_add(fa + 2, oz);
+            if (g.W) g.W[a] = w;
+        }
+        if (!more) break;
+        float cxn = 0.f, cyn = 0.f, czn = 0.f;
+        if (cjn >= 0) {
+            cxn = __ldg(g.x + 3 * cjn);
+            cyn = __ldg(g.x + 3 * cjn + 1);
+            czn = __ldg(g.x + 3 * cjn + 2);
+        }
+        wa = wn;
+        a = an;
+        beg = bn;
+        end = en;
+        cj = cjn;
+        cx = cxn;
+        cy = cyn;
+        cz = czn;
+        __syncwarp();   // this atom's reads of qa, va and the queue are done
     }
 }
 
@@ -445,7 +494,17 @@ static void nc_head_launch(const NCHeadArgs &a, cudaStream_t st) {
     using SM = NCHeadSmem<K, NC, NL>;
     // per launch: the attribute belongs to the current device's context
     cudaFuncSetAttribute(k_nc_head<K, NC, NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes);
-    const int blocks = (a.n_atoms + NCH_WARPS - 1) / NCH_WARPS;
+    // persistent: as many warps as fit on the GPU at once, each taking every
+    // (grid)-th atom
+    static int resident = 0;
+    if (!resident) {
+        int dev = 0, n_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        resident = std::max(1, n_sm * resident_ctas(reinterpret_cast<const void *>(k_nc_head<K, NC, NL>),
+                                                    NCH_WARPS * 32, SM::bytes, dev));
+    }
+    const int blocks = std::min((a.n_atoms + NCH_WARPS - 1) / NCH_WARPS, resident);
     k_nc_head<K, NC, NL><<<blocks, NCH_WARPS * 32, SM::bytes, st>>>(a);
     count_launch();
 }
@@ -994,8 +1053,9 @@ void launch_mean_sub(const float *F_in, float *F_out, const int *rep_off, int n_
 // replica's exact integer sum of the forces added to sum[r] (warp-aggregated
 // 64-bit atomics; integer sums do not depend on their order).
 __global__ void k_nc_convert(int n, const int *__restrict__ atom_rep, unsigned long long *__restrict__ Ffix,
-                             float *__restrict__ F, unsigned long long *__restrict__ sum) {
+                             float *__restrict__ F, unsigned long long *__restrict__ sum, unsigned *__restrict__ next) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0 && next) *next = 0u;   // the head's work counter, for its next launch
     const bool live = i < n;
     const int r = live ? atom_rep[i] : -1;
     long long q[3] = {0, 0, 0};
@@ -1014,9 +1074,9 @@ __global__ void k_nc_convert(int n, const int *__restrict__ atom_rep, unsigned l
 }
 
 void launch_nc_convert(int n, const int *atom_rep, unsigned long long *Ffix, float *F, unsigned long long *sum,
-                       cudaStream_t st) {
+                       unsigned *next, cudaStream_t st) {
     if (n == 0) return;
-    k_nc_convert<<<(n + 255) / 256, 256, 0, st>>>(n, atom_rep, Ffix, F, sum);
+    k_nc_convert<<<(n + 255) / 256, 256, 0, st>>>(n, atom_rep, Ffix, F, sum, next);
     count_launch();
 }
 

@@ -38,6 +38,7 @@ struct NCHeadArgs {
     unsigned long long *Ffix;      // [N][3] forces before mean subtraction, 32.32 fixed point, added to
                                    // (zero on entry; launch_nc_convert converts and clears them)
     unsigned long long *sum;       // [R][3] per-replica exact sums, cleared by the head for launch_nc_convert
+    unsigned *next;                // the head's work counter (atoms taken; zero on entry, cleared by launch_nc_convert)
     int n_rep;
     float *W;                      // nullable [N]: per-atom virial proxy (pair form; each NC pair on its
                                    // lower-index atom)
@@ -106,7 +107,7 @@ void launch_mean_part_off(const int *rep_off, int n_rep, int *part_off, cudaStre
 // The NC head's fixed-point forces -> fp32 F, cleared; sum[r] += the
 // replica's exact integer force sum (sum cleared by the head beforehand).
 void launch_nc_convert(int n, const int *atom_rep, unsigned long long *Ffix, float *F, unsigned long long *sum,
-                       cudaStream_t st);
+                       unsigned *next, cudaStream_t st);
 // F_out = F - mean (replica means from the exact sums: sum / 2^32 / n_r in
 // FP64); net (nullable) [R][3] = the sums in FP64.
 void launch_nc_apply(int n, const int *atom_rep, const int *rep_off, int n_rep, const float *F, float *F_out,

@@ -80,6 +80,10 @@ void launch_mp_bwd(int C, int lmax, int K, const EdgeGeom &g, const LayerIO &io,
 // W, the fixed-point words cleared for the next evaluation.
 void launch_fix_convert(int n, unsigned long long *Ffix, float *F, unsigned long long *Wfix, float *W, cudaStream_t st);
 
+// CTAs of a kernel resident per SM, from its register and shared-memory use
+// and the device's limits (the largest shared-memory carveout).
+int resident_ctas(const void *fn, int threads, size_t dyn_smem, int dev);
+
 // ---------------------------------------------------------------- GEMM ----
 enum EpiMode {
     EPI_STORE = 0,           // out = v

@@ -292,26 +292,6 @@ __global__ void __launch_bounds__(TF_C, 4) k_mp_fwd_tc(EdgeGeom g, LayerIO io, i
     }
 }
 
-// CTAs of a kernel resident per SM, from its register and shared-memory
-// use and the device's limits (the largest shared-memory carveout).
-int resident_ctas(const void *fn, int threads, size_t dyn_smem, int dev) {
-    cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) return 1;
-    int regs_sm = 0, smem_sm = 0, smem_blk_reserved = 0, max_thr = 0, max_blk = 0;
-    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
-    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    cudaDeviceGetAttribute(&smem_blk_reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
-    cudaDeviceGetAttribute(&max_thr, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
-    cudaDeviceGetAttribute(&max_blk, cudaDevAttrMaxBlocksPerMultiprocessor, dev);
-    const int regs_blk = ((fa.numRegs * 32 + 255) / 256 * 256) * ((threads + 31) / 32);
-    const size_t smem_blk = fa.sharedSizeBytes + dyn_smem + smem_blk_reserved;
-    int n = max_blk;
-    if (regs_blk > 0) n = std::min(n, regs_sm / regs_blk);
-    if (smem_blk > 0) n = std::min(n, (int)(smem_sm / smem_blk));
-    n = std::min(n, max_thr / threads);
-    return std::max(n, 1);
-}
-
 template <int LMAX>
 void fwd_tc_launch(const EdgeGeom &g, const LayerIO &io, int nseg, int *err, cudaStream_t st) {
     constexpr size_t smem = FwdTcSmem<LMAX>::bytes;
@@ -333,6 +313,24 @@ void fwd_tc_launch(const EdgeGeom &g, const LayerIO &io, int nseg, int *err, cud
 }
 
 }  // namespace
+
+int resident_ctas(const void *fn, int threads, size_t dyn_smem, int dev) {
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) return 1;
+    int regs_sm = 0, smem_sm = 0, smem_blk_reserved = 0, max_thr = 0, max_blk = 0;
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&smem_blk_reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    cudaDeviceGetAttribute(&max_thr, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+    cudaDeviceGetAttribute(&max_blk, cudaDevAttrMaxBlocksPerMultiprocessor, dev);
+    const int regs_blk = ((fa.numRegs * 32 + 255) / 256 * 256) * ((threads + 31) / 32);
+    const size_t smem_blk = fa.sharedSizeBytes + dyn_smem + smem_blk_reserved;
+    int n = max_blk;
+    if (regs_blk > 0) n = std::min(n, regs_sm / regs_blk);
+    if (smem_blk > 0) n = std::min(n, (int)(smem_sm / smem_blk));
+    n = std::min(n, max_thr / threads);
+    return std::max(n, 1);
+}
 
 bool mp_fwd_tc_supported(int C, int K, const LayerIO &io) { return C == TF_C && K == TF_K && !io.V; }
 
