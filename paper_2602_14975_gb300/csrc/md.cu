@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
         if (with_rep) {
             const int b0 = g.bonds.ptr[a];
             nbp = g.bonds.ptr[a + 1] - b0;
-    #pragma unroll
+#pragma unroll
             for (int q = 0; q < 4; ++q)
                 if (q < nbp) bp[q] = g.bonds.idx[b0 + q];
         }
@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
             // the neighbour's tensor-head vectors, for the lane of the pair that
             // owns the tensor heads (plain loads: 12 bytes per head)
             float vj[3 * NL];
-    #pragma unroll
+#pragma unroll
             for (int q = 0; q < 3 * NL; ++q) vj[q] = (j >= 0 && half == 1) ? __ldg(g.V + (size_t)j * SM::VS + q) : 0.f;
             // radial part of the edge while the rows arrive
             float dx = 0.f, dy = 0.f, dz = 0.f, inv = 1.f, fc = 0.f, Bh[HH], crep = 0.f, r2 = 0.f;
@@ -328,7 +328,7 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
                 fc = envelope(r * g.inv_rc, g.p, &du);
                 float B[K];
                 bessel<K, false>(r, g.inv_rc, g.bnorm, B, nullptr);
-    #pragma unroll
+#pragma unroll
                 for (int hl = 0; hl < HH; ++hl)
                     Bh[hl] = half == 0 ? B[hl] : (HH + hl < K ? B[HH + hl < K ? HH + hl : 0] : 0.f);
             }
@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
             float part[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // Saj, Sja, va (3), vj (3)
             if (j >= 0) {
                 const float *row = rows + slot * RSTR;
-    #pragma unroll
+#pragma unroll
                 for (int hl = 0; hl < HH; ++hl) {
                     const int h = half * HH + hl;
                     if (h < H) {
@@ -355,7 +355,7 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
                         const float4 *qa4 = reinterpret_cast<const float4 *>(qa + h * NC);
                         const float4 *ka4 = reinterpret_cast<const float4 *>(ka + h * NC);
                         float caj = 0.f, cja = 0.f;
-    #pragma unroll
+#pragma unroll
                         for (int q = 0; q < NC / 4; ++q) {
                             const float4 kj = kj4[q], qj = qj4[q], qi = qa4[q], ki = ka4[q];
                             caj = fmaf(qi.x, kj.x, fmaf(qi.y, kj.y, fmaf(qi.z, kj.z, fmaf(qi.w, kj.w, caj))));
@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
                         } else {
                             // tensor heads lie in the second lane's half (HH <= K): t is static
                             const int t = HH + hl - K;
-    #pragma unroll
+#pragma unroll
                             for (int cmp = 0; cmp < 3; ++cmp) {
                                 part[2 + cmp] = fmaf(caj, va[3 * t + cmp], part[2 + cmp]);
                                 part[5 + cmp] = fmaf(cja, vj[3 * t + cmp], part[5 + cmp]);
@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
                     }
                 }
             }
-    #pragma unroll
+#pragma unroll
             for (int q = 0; q < 8; ++q) part[q] += __shfl_xor_sync(DMTS_FULL, part[q], BATCH);
             if (j >= 0 && half == 0) {
                 const float nx = dx * inv, ny = dy * inv, nz = dz * inv;
