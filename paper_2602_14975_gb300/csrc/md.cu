@@ -237,6 +237,8 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
     }
     __syncwarp();
     uint32_t phase = 0;
+    constexpr int QR = (QKW + 31) / 32;   // q/k row values per lane
+    const bool with_rep = g.bonds.ptr && g.rep.on;
     int a = g.order ? __ldg(g.order + wa) : wa;
     int beg = g.row_ptr[a], end = g.row_ptr[a + 1];
     int cj = beg + lane < end ? __ldg(g.col + beg + lane) : -1;
@@ -246,50 +248,59 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
         cy = __ldg(g.x + 3 * cj + 1);
         cz = __ldg(g.x + 3 * cj + 2);
     }
+    // the atom's own values: its q/k row and tensor-head vectors (one share
+    // per lane), position, replica box, species, and its bonds (lane q holds
+    // bond q: partner index, position and rest length)
+    float qr[QR], vr = 0.f;
+#pragma unroll
+    for (int u = 0; u < QR; ++u) qr[u] = lane + 32 * u < QKW ? g.QK[(size_t)a * QKW + lane + 32 * u] : 0.f;
+    if (lane < NL * 3) vr = g.V[(size_t)a * SM::VS + lane];
+    int rep = g.atom_rep[a], sa = g.species[a];
+    float xa = g.x[3 * a], ya = g.x[3 * a + 1], za = g.x[3 * a + 2];
+    float bx = g.box[3 * rep], by = g.box[3 * rep + 1], bz = g.box[3 * rep + 2];
+    int q0 = 0, nbond = 0, jb = -1;
+    float bjx = 0.f, bjy = 0.f, bjz = 0.f, br0 = 0.f;
+    if (g.bonds.ptr) {
+        q0 = g.bonds.ptr[a];
+        nbond = g.bonds.ptr[a + 1] - q0;
+        if (lane < nbond) {
+            jb = __ldg(g.bonds.idx + q0 + lane);
+            bjx = __ldg(g.x + 3 * jb);
+            bjy = __ldg(g.x + 3 * jb + 1);
+            bjz = __ldg(g.x + 3 * jb + 2);
+            br0 = __ldg(g.bonds.r0 + q0 + lane);
+        }
+    }
     for (;;) {
         const int wn_raw = lane == 0 ? (int)atomicAdd(g.next, 1u) : 0;   // read after the candidates
         int wn = 0, an = 0, bn = 0, en = 0, cjn = -1;
         bool more = false;
-        for (int t = lane; t < QKW; t += 32) qa[t] = g.QK[(size_t)a * QKW + t];
-        for (int t = lane; t < NL * 3; t += 32) va[t] = g.V[(size_t)a * SM::VS + t];
+        // the next atom's own values, loaded in the same stages as its row
+        float qrn[QR], vrn = 0.f;
+        int repn = 0, san = 0, q0n = 0, nbondn = 0, jbn = -1;
+        float xan = 0.f, yan = 0.f, zan = 0.f, bxn = 0.f, byn = 0.f, bzn = 0.f;
+#pragma unroll
+        for (int u = 0; u < QR; ++u)
+            if (lane + 32 * u < QKW) qa[lane + 32 * u] = qr[u];
+        if (lane < NL * 3) va[lane] = vr;
         __syncwarp();
         const float *ka = qa + H * NC;
-        const int rep = g.atom_rep[a];
-        const float bx = g.box[3 * rep], by = g.box[3 * rep + 1], bz = g.box[3 * rep + 2];
         const float ibx = bx > 0.f ? 1.f / bx : 0.f, iby = by > 0.f ? 1.f / by : 0.f, ibz = bz > 0.f ? 1.f / bz : 0.f;
-        const float xa = g.x[3 * a], ya = g.x[3 * a + 1], za = g.x[3 * a + 2];
         const float rc2 = g.rc * g.rc, isnc = rsqrtf((float)NC);
-        const bool with_rep = g.bonds.ptr && g.rep.on;
         const float rep2 = g.rep.rc * g.rep.rc;
-        const int sa = g.species[a];
-        // bonded partners of a (up to four in registers; more fall back to the table)
-        int bp[4] = {-1, -1, -1, -1}, nbp = 0;
-        if (with_rep) {
-            const int b0 = g.bonds.ptr[a];
-            nbp = g.bonds.ptr[a + 1] - b0;
+        // bonded partners of a (up to four, from the lanes holding its bonds;
+        // more fall back to the table)
+        int bp[4] = {-1, -1, -1, -1};
+        const int nbp = with_rep ? nbond : 0;
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (q < nbp) bp[q] = g.bonds.idx[b0 + q];
+        for (int q = 0; q < 4; ++q) {
+            const int t = __shfl_sync(DMTS_FULL, jb, q);
+            if (q < nbp) bp[q] = t;
         }
         auto bonded = [&](int j) {
             if (nbp > 4) return is_bonded(g.bonds, a, j);
             return j == bp[0] || j == bp[1] || j == bp[2] || j == bp[3];
         };
-        // a's bonds (one per lane): partner position and rest length, loaded now
-        // so that their latency overlaps the pairs' work
-        int nbond = 0;
-        float bjx = 0.f, bjy = 0.f, bjz = 0.f, br0 = 0.f;
-        if (g.bonds.ptr) {
-            const int q0 = g.bonds.ptr[a];
-            nbond = g.bonds.ptr[a + 1] - q0;
-            if (lane < nbond) {
-                const int jb = __ldg(g.bonds.idx + q0 + lane);
-                bjx = __ldg(g.x + 3 * jb);
-                bjy = __ldg(g.x + 3 * jb + 1);
-                bjz = __ldg(g.x + 3 * jb + 2);
-                br0 = __ldg(g.bonds.r0 + q0 + lane);
-            }
-        }
         long long ox = 0, oy = 0, oz = 0;     // this lane's share of a's side of its pairs, fixed point
         float wv = 0.f;                       // virial proxy: (F_aj - F_ja) . d_aj (+ repulsion) over a's pairs
         bool bad = false;                     // a pair term outside the fixed-point range (or not finite)
@@ -435,9 +446,21 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
         if (more) an = g.order ? __ldg(g.order + wn) : wn;
         if (alive && queued > taken) batch(taken, queued - taken);
         if (!alive) return;
-        if (more) {   // its row bounds
+        if (more) {   // its row bounds and own values
             bn = g.row_ptr[an];
             en = g.row_ptr[an + 1];
+#pragma unroll
+            for (int u = 0; u < QR; ++u) qrn[u] = lane + 32 * u < QKW ? g.QK[(size_t)an * QKW + lane + 32 * u] : 0.f;
+            if (lane < NL * 3) vrn = g.V[(size_t)an * SM::VS + lane];
+            repn = g.atom_rep[an];
+            san = g.species[an];
+            xan = g.x[3 * an];
+            yan = g.x[3 * an + 1];
+            zan = g.x[3 * an + 2];
+            if (g.bonds.ptr) {
+                q0n = g.bonds.ptr[an];
+                nbondn = g.bonds.ptr[an + 1] - q0n;
+            }
         }
         float w = wv;
         if (g.bonds.ptr) {
@@ -458,7 +481,13 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
                 w += wq;
             }
         }
-        if (bn + lane < en) cjn = __ldg(g.col + bn + lane);   // its first candidates
+        if (bn + lane < en) cjn = __ldg(g.col + bn + lane);   // its first candidates, box and bond partners
+        if (more) {
+            bxn = g.box[3 * repn];
+            byn = g.box[3 * repn + 1];
+            bzn = g.box[3 * repn + 2];
+            if (lane < nbondn) jbn = __ldg(g.bonds.idx + q0n + lane);
+        }
         if (__any_sync(DMTS_FULL, bad)) {
             if (lane == 0) set_error(g.err, DMTS_E_NONFINITE);
             return;
@@ -471,11 +500,17 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
             if (g.W) g.W[a] = w;
         }
         if (!more) break;
-        float cxn = 0.f, cyn = 0.f, czn = 0.f;
+        float cxn = 0.f, cyn = 0.f, czn = 0.f, bjxn = 0.f, bjyn = 0.f, bjzn = 0.f, br0n = 0.f;
         if (cjn >= 0) {
             cxn = __ldg(g.x + 3 * cjn);
             cyn = __ldg(g.x + 3 * cjn + 1);
             czn = __ldg(g.x + 3 * cjn + 2);
+        }
+        if (jbn >= 0) {
+            bjxn = __ldg(g.x + 3 * jbn);
+            bjyn = __ldg(g.x + 3 * jbn + 1);
+            bjzn = __ldg(g.x + 3 * jbn + 2);
+            br0n = __ldg(g.bonds.r0 + q0n + lane);
         }
         wa = wn;
         a = an;
@@ -485,6 +520,23 @@ __global__ void __launch_bounds__(NCH_WARPS * 32) k_nc_head(NCHeadArgs g) {
         cx = cxn;
         cy = cyn;
         cz = czn;
+#pragma unroll
+        for (int u = 0; u < QR; ++u) qr[u] = qrn[u];
+        vr = vrn;
+        rep = repn;
+        sa = san;
+        xa = xan;
+        ya = yan;
+        za = zan;
+        bx = bxn;
+        by = byn;
+        bz = bzn;
+        nbond = nbondn;
+        jb = jbn;
+        bjx = bjxn;
+        bjy = bjyn;
+        bjz = bjzn;
+        br0 = br0n;
         __syncwarp();   // this atom's reads of qa, va and the queue are done
     }
 }
