@@ -151,7 +151,9 @@ __device__ __forceinline__ float rep_pair(const RepTable &t, int si, int sj, flo
 // bulk-copies the neighbour's q/k row into shared memory, the second loads
 // the neighbour's tensor-head vectors (its heads), both evaluate the radial
 // part while the row arrives, and each forms the dot products of half of
-// the heads.
+// the heads. The warps are persistent (one per block, as many blocks as fit)
+// and take atoms from a work counter in processing order; each loads its
+// next atom's row, candidates and own values one atom ahead (see the kernel).
 constexpr int NCH_WARPS = 1;
 __device__ __forceinline__ double fix_sum_to_double(unsigned long long s) {
     return (double)(long long)s * (1.0 / 4294967296.0);   // exact for |s| < 2^53
