@@ -41,7 +41,7 @@ PROF_EVERY = 4   # time every 4th outer step of the timed region per kernel
 KCAL_A3_PER_ATM = 101325.0 * 6.02214076e23 * 1e-30 / 4184.0   # 1 atm in kcal/mol/A^3
 
 NCU_TRAFFIC = {
-    "mp_bwd": {"bytes_per_launch": (154544896 + 19223040 + 154177792 + 16382208 + 139640576 + 247808) / 3,
+    "mp_bwd": {"bytes_per_launch": (154229760 + 19248896 + 154260992 + 16390400 + 139650304 + 268544) / 3,
                # the adjoint's code: channel-pack helpers, kernel and launch, the
                # argument structs, the device helpers
                "sources": [("paper_2602_14975_gb300/csrc/mp.cu", ("// ---- channel packs", "// ---- forward")),
@@ -50,7 +50,7 @@ NCU_TRAFFIC = {
                                                                   "#define DMTS_DISPATCH")),
                            ("paper_2602_14975_gb300/csrc/mp.cuh", ("struct EdgeGeom {", "template <int CPW>")),
                            ("paper_2602_14975_gb300/csrc/common.cuh", None)],
-               "sha256": "a360cd877a8170aa8166c867648f18ae72499b7d44ed22caa90d16ff1ba7266e"},
+               "sha256": "8c1a3a7c5d60e748369169f7e9198032650ff7e2427e60f09026a2b70bc7c32c"},
 }
 
 

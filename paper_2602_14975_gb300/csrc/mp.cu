@@ -231,11 +231,11 @@ __global__ void __launch_bounds__(MP_WARPS * 32) k_mp_fwd(EdgeGeom g, LayerIO io
 // neighbour j < a contributes only its sender-role term to g_s_a (R, no R',
 // no force), and nothing in a layer without that gradient.
 //
-// Shared memory per block (dynamic: above the 48 KB static limit at C = 128,
-// l_max = 2): per warp 32 edge records of packs (f_c B_k, its r-derivative,
-// Y_lm) and of scalars (dY_lm/dd, n, and r for the virial), the receiver's
-// gA_a as packs, the 32 neighbour indices, and the lanes' shares of the
-// force of FT pairs (transposed so that one lane adds up each pair).
+// Shared memory per block (one warp; 21.4 KB at C = 128, l_max = 2): 32 edge
+// records of packs (f_c B_k, its r-derivative, Y_lm) and of scalars
+// (dY_lm/dd, n, and r for the virial), the receiver's gA_a as packs, the 32
+// neighbour indices, and the lanes' shares of the force of FT pairs
+// (transposed so that one lane adds up each pair).
 constexpr int FT = 16;   // pairs per force reduction
 // One warp per block: how many upper neighbours an atom has varies from atom
 // to atom, and a block keeps its registers and shared memory until its
