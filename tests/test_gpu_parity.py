@@ -306,6 +306,35 @@ def test_nc_open_boundary_batch(ctx1, models1):
         off += sy.n_atoms
 
 
+def test_pair_once_kernels_on_a_degenerate_batch(ctx1, models1):
+    """The kernels that form each pair once, from its lower atom (the
+    adjoint of the message passing; the NC head, whose persistent warps take
+    atoms from a work counter), on one batch of a lone atom (no pair), an
+    isolated atom pair (one pair: the lower atom's warp forms both atoms'
+    terms) and a droplet: every replica's forces against the oracle, the lone
+    atom's exactly zero."""
+    (cs, cb), (ns, nb_) = models1
+    lone = S.System("lone", np.zeros((1, 3)), np.array([3], np.uint8), np.zeros(1, np.int32),
+                    np.zeros((0, 2), np.int32), np.zeros(0), np.zeros(3))
+    pair = S.System("pair", np.array([[0.0, 0.0, 0.0], [1.2, 0.3, -0.2]]), np.array([3, 0], np.uint8),
+                    np.zeros(2, np.int32), np.zeros((0, 2), np.int32), np.zeros(0), np.zeros(3))
+    systems = [lone, pair, S.capped_molecule_in_droplet(20, seed=5)]
+    d = core.DeviceSystem(systems)
+    nb = core.nbr_build(ctx1, d, 5.5)
+    _, F = core.energy_forces_cons(ctx1, d, nb, with_prior=False)
+    Fn, _ = core.forces_nc(ctx1, d, nb, with_bonds=False)
+    F, Fn = F.cpu().numpy(), Fn.cpu().numpy()
+    assert np.all(F[0] == 0.0) and np.all(Fn[0] == 0.0)
+    off = 1
+    for sy in systems[1:]:
+        n = sy.n_atoms
+        _, Fo = O.cons_energy_forces(sy, cs, cb)
+        Fno, _ = O.nc_forces(sy, ns, nb_, with_bonds=False)
+        assert rel_maxabs(F[off:off + n], Fo) <= TOL_F32
+        assert rel_maxabs(Fn[off:off + n], Fno) <= TOL_F32
+        off += n
+
+
 def _virial_tol(sy, ns, nb_, with_bonds=True):
     # fp32 per-atom terms summed in fp64: 1e-5 of the sum of |F_i| times the
     # list radius bounds the rounding of sum_i w_i
